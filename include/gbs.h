@@ -1,0 +1,167 @@
+/*
+ * gbs.h -- C ABI of the GB300 matrix-P total-count estimator for Gaussian
+ * boson sampling (Drummond, Dellios, Reid, arXiv:2503.12749).
+ *
+ * The library computes, for N squeezed-vacuum inputs (squeezing r_j >= 0)
+ * sent through an M x N linear network T, the binned total-count
+ * distribution P(m) of Eq. total_counts with two phase-space estimators on
+ * the same trajectories:
+ *   - the parity-projected (M = 2) matrix-P estimator, projector g_0 of
+ *     Eq. c-number-variable;
+ *   - the positive-P estimator, same equation with g_0 = 1
+ *     (Eq. phase_space_projector).
+ * Each trajectory draws real input amplitudes alpha, beta from the +P
+ * density of the squeezed vacua ("Applications to GBS"), propagates them as
+ * alpha' = T alpha, beta' = T* beta, and contributes its generating function
+ *   G_mP(z) = cosh(n + (z-1) n_S) / cosh(n),   G_+P(z) = exp((z-1) n_S),
+ *   n = sum_j alpha_j beta_j,  n_S = sum_i alpha'_i beta'_i,
+ * at the K1 roots of unity z_k = exp(2 pi i k / K1).  Sub-ensemble means
+ * (Appendix A: N_R sub-ensembles) are inverted by DFT to P(m) with the
+ * sampling error std_r / sqrt(N_R).
+ *
+ * Conventions
+ *   - Every function returns a status (GBS_OK = 0 or a negative code) and
+ *     never aborts; gbs_last_error() returns a thread-local message for the
+ *     last failure on the calling thread.
+ *   - Host pointers are owned by the caller and only read/written during
+ *     the call.  The library copies T and r at gbs_make_network and owns all
+ *     device memory of a network until gbs_free_network.
+ *   - Work is issued on the CUDA stream given at gbs_make_network (a
+ *     cudaStream_t passed as void*, NULL = legacy default stream).
+ *   - A network object must not be used from two host threads at once.
+ *   - Trajectory e of a run with key `seed` draws its normals from
+ *     Philox-4x32-10 (Salmon et al., SC'11) at counter (e, j); the result of
+ *     a run is therefore fixed by (T, r, seed, sample range) and
+ *     independent of how the range is split into calls.
+ */
+#ifndef GBS_H
+#define GBS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define GBS_OK 0
+#define GBS_EINVAL (-1)     /* invalid argument (sizes, r_j < 0, K1 not a power of two, ...) */
+#define GBS_ENOMEM (-2)     /* device or host allocation failed */
+#define GBS_ECUDA (-3)      /* a CUDA runtime/driver call failed */
+#define GBS_ETIMEOUT (-4)   /* a bounded device-side wait gave up (error flag set by a kernel) */
+#define GBS_ENONFINITE (-5) /* non-finite generating-function sums; the message holds the count */
+#define GBS_ENOTSUP (-6)    /* feature not supported on this device / build */
+
+/* Arithmetic of the propagation GEMM alpha' = T alpha, beta' = T* beta. */
+#define GBS_FP64 0   /* FP64 sampler, FP64 SIMT GEMM, FP64 generating functions */
+#define GBS_BF16X3 2 /* FP32 sampler, tcgen05 BF16 split GEMM with 3 products
+                        (T0 B0 + T0 B1 + T1 B0), FP32 accumulation; FP32
+                        generating functions summed in FP64 */
+#define GBS_BF16X6 3 /* as GBS_BF16X3 with 6 products (adds T1 B1, T0 B2, T2 B0) */
+
+typedef struct gbs_net *gbs_net_t;
+
+/*
+ * gbs_make_network -- upload one network ("Applications to GBS": the
+ * transmission matrix t acting as alpha' = t alpha, beta' = t* beta; loss as
+ * a non-unitary t, "Computational results and losses").
+ *   N, M       input and output mode counts, 1 <= N, M <= 65536.
+ *   T          host, M*N complex numbers row-major, each as (re, im) doubles:
+ *              T[2*(i*N + j)] = Re T_ij, T[2*(i*N + j) + 1] = Im T_ij.
+ *   r          host, N squeezing parameters, each finite and >= 0.
+ *   precision  GBS_FP64, GBS_BF16X3 or GBS_BF16X6.  The BF16 paths split T
+ *              (rounded to FP32) into BF16 planes T = T0 + T1 + T2.
+ *   stream     cudaStream_t (as void*) used for every launch of this network.
+ *   out        receives the handle.
+ * Errors: EINVAL on bad sizes/values/null pointers; ENOMEM; ECUDA;
+ * ENOTSUP when a BF16 precision is requested on a device without tcgen05.
+ */
+int gbs_make_network(int N, int M, const double *T, const double *r, int precision,
+                     void *stream, gbs_net_t *out);
+
+/*
+ * gbs_sample -- draw trajectories first_sample .. first_sample+E-1 and add
+ * their generating functions to the network's sub-ensemble sums
+ * (the ensemble loop: sampling "Applications to GBS", observables
+ * Eq. c-number-variable summed over m as a generating function, sub-ensembles
+ * Appendix A).  Trajectory e belongs to sub-ensemble e mod n_sub.
+ *   seed        Philox key (64 bits).
+ *   E           number of trajectories, >= 0.
+ *   n_sub       number of sub-ensembles N_R, >= 1.
+ *   K1          number of DFT points K+1, a power of two in [2, 2^20].
+ * The first call after make/reset fixes (n_sub, K1); later calls must pass
+ * the same values (EINVAL otherwise).  Asynchronous on the network's stream
+ * except for the first call's allocations.  Errors: EINVAL, ENOMEM, ECUDA,
+ * ETIMEOUT.
+ */
+int gbs_sample(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub,
+               int K1);
+
+/*
+ * gbs_binned_counts -- inverse DFT of the sub-ensemble means and the
+ * statistics over sub-ensembles (Eq. total_counts; errors Appendix A):
+ *   P_r(m) = (1/K1) sum_k <G>_r(z_k) z_k^{-m},  m = m_offset .. m_offset+K1-1,
+ *   P(m) = mean_r Re P_r(m),  sigma(m) = std_r(Re P_r(m)) / sqrt(N_R)
+ * (sample standard deviation; sigma = 0 when N_R = 1).  The result for bin m
+ * is the aliased sum over m + j K1; choose K1 and m_offset to cover the
+ * support.  Output arrays are host buffers of K1 doubles each; any of them
+ * may be NULL to skip it.  Synchronises the network's stream.
+ * Errors: EINVAL (no samples in some sub-ensemble), ENONFINITE, ECUDA.
+ */
+int gbs_binned_counts(gbs_net_t net, int64_t m_offset, double *P_mP, double *sig_mP,
+                      double *P_plusP, double *sig_plusP);
+
+/*
+ * gbs_binned_counts_device -- as gbs_binned_counts, but writes into DEVICE
+ * buffers and does not synchronise: out_dev holds 4*K1 doubles laid out as
+ * [P_mP | sig_mP | P_plusP | sig_plusP].  No non-finite check is made (call
+ * gbs_check_finite for it).  Errors: EINVAL, ECUDA.
+ */
+int gbs_binned_counts_device(gbs_net_t net, int64_t m_offset, double *out_dev);
+
+/*
+ * gbs_check_finite -- count non-finite entries of the sub-ensemble sums
+ * (synchronises).  Returns GBS_OK and *count = 0 when all are finite,
+ * GBS_ENONFINITE with *count > 0 otherwise.
+ */
+int gbs_check_finite(gbs_net_t net, int64_t *count);
+
+/*
+ * gbs_debug_samples -- per-trajectory photon numbers for trajectories
+ * e0 .. e0+count-1 of key `seed`, computed by the same kernels as gbs_sample
+ * (for parity tests): n[count] (input total sum_j alpha_j beta_j) and
+ * nS[2*count] (output total sum_i alpha'_i beta'_i as (re, im)), host
+ * buffers.  Does not touch the sub-ensemble sums.  Synchronises.
+ */
+int gbs_debug_samples(gbs_net_t net, uint64_t seed, uint64_t e0, int64_t count, double *n,
+                      double *nS);
+
+/*
+ * gbs_get_accumulators / gbs_set_accumulators -- the sub-ensemble sums as
+ * host arrays: acc[2][n_sub][K1] complex (re, im) doubles (estimator 0 =
+ * matrix-P, 1 = +P; each the SUM of G(z_k) over the sub-ensemble's
+ * trajectories) and counts[n_sub] (trajectories per sub-ensemble).  Used for
+ * checkpoint/resume and to combine runs.  gbs_set_accumulators also fixes
+ * (n_sub, K1) like a first gbs_sample.  Both synchronise.
+ */
+int gbs_get_accumulators(gbs_net_t net, int *n_sub, int *K1, double *acc, int64_t *counts);
+int gbs_set_accumulators(gbs_net_t net, int n_sub, int K1, const double *acc,
+                         const int64_t *counts);
+
+/* gbs_reset -- clear the sub-ensemble sums and unfix (n_sub, K1). */
+int gbs_reset(gbs_net_t net);
+
+/* gbs_network_info -- N, M, precision and the trajectories per internal chunk. */
+int gbs_network_info(gbs_net_t net, int *N, int *M, int *precision, int64_t *chunk);
+
+/* gbs_free_network -- release all memory of the network (NULL is a no-op). */
+void gbs_free_network(gbs_net_t net);
+
+/* gbs_last_error -- message of the last failure on this thread ("" if none). */
+const char *gbs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBS_H */

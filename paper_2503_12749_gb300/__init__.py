@@ -1,0 +1,216 @@
+"""GB300-native matrix-P total-count estimator for Gaussian boson sampling.
+
+Python binding of the C ABI in ``include/gbs.h`` (libgbs.so, built for
+sm_103a by ``paper_2503_12749_gb300.build``).  The functions below carry the
+ABI's names and only marshal arguments: every step of the estimator runs in
+the library's CUDA kernels.  There is no CPU fallback: if the library cannot
+be loaded, the first call raises.
+
+Typical use::
+
+    import paper_2503_12749_gb300 as gbs
+    net = gbs.gbs_make_network(T, r, gbs.GBS_BF16X3)
+    gbs.gbs_sample(net, seed, 0, E, n_sub, K1)
+    P_mP, s_mP, P_pP, s_pP = gbs.gbs_binned_counts(net, m_offset=0)
+    gbs.gbs_free_network(net)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Tuple
+
+import numpy as np
+
+GBS_OK = 0
+GBS_EINVAL = -1
+GBS_ENOMEM = -2
+GBS_ECUDA = -3
+GBS_ETIMEOUT = -4
+GBS_ENONFINITE = -5
+GBS_ENOTSUP = -6
+
+GBS_FP64 = 0
+GBS_BF16X3 = 2
+GBS_BF16X6 = 3
+
+PRECISIONS = {"fp64": GBS_FP64, "bf16x3": GBS_BF16X3, "bf16x6": GBS_BF16X6}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgbs.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class GbsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[gbs status {code}] {msg}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib as _b
+    return _b.build(force=force)
+
+
+def lib():
+    """The loaded libgbs.so (raises if it is missing or cannot be loaded)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libgbs.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.gbs_make_network.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, vp,
+                                       ctypes.POINTER(vp)]
+        L.gbs_sample.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                 ctypes.c_int, ctypes.c_int]
+        L.gbs_binned_counts.argtypes = [vp, ctypes.c_int64, dp, dp, dp, dp]
+        L.gbs_binned_counts_device.argtypes = [vp, ctypes.c_int64, vp]
+        L.gbs_check_finite.argtypes = [vp, i64p]
+        L.gbs_debug_samples.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, dp,
+                                        dp]
+        L.gbs_get_accumulators.argtypes = [vp, ip, ip, dp, i64p]
+        L.gbs_set_accumulators.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, i64p]
+        L.gbs_reset.argtypes = [vp]
+        L.gbs_network_info.argtypes = [vp, ip, ip, ip, i64p]
+        L.gbs_free_network.argtypes = [vp]
+        L.gbs_free_network.restype = None
+        L.gbs_last_error.argtypes = []
+        L.gbs_last_error.restype = ctypes.c_char_p
+        for name in ("gbs_make_network", "gbs_sample", "gbs_binned_counts",
+                     "gbs_binned_counts_device", "gbs_check_finite", "gbs_debug_samples",
+                     "gbs_get_accumulators", "gbs_set_accumulators", "gbs_reset",
+                     "gbs_network_info"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _check(code: int):
+    if code != GBS_OK:
+        raise GbsError(code, gbs_last_error())
+
+
+def _dptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def gbs_last_error() -> str:
+    return lib().gbs_last_error().decode(errors="replace")
+
+
+class Network:
+    """Handle of a network on the device (owns the C-side gbs_net_t)."""
+
+    def __init__(self, handle: int, N: int, M: int, precision: int, stream: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.N, self.M, self.precision, self.stream = N, M, precision, stream
+
+    def __del__(self):
+        try:
+            if self.handle and self.handle.value:
+                gbs_free_network(self)
+        except Exception:
+            pass
+
+
+def gbs_make_network(T: np.ndarray, r: np.ndarray, precision=GBS_FP64,
+                     stream: int = 0) -> Network:
+    """T: complex (M, N) host array; r: (N,) squeezing; stream: cudaStream_t as int."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    T = np.ascontiguousarray(T, dtype=np.complex128)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    M, N = T.shape
+    if r.shape != (N,):
+        raise ValueError("r must have shape (N,)")
+    Tf = T.view(np.float64)
+    out = ctypes.c_void_p()
+    _check(lib().gbs_make_network(N, M, _dptr(Tf), _dptr(r), int(precision),
+                                  ctypes.c_void_p(stream), ctypes.byref(out)))
+    return Network(out.value, N, M, int(precision), stream)
+
+
+def gbs_sample(net: Network, seed: int, first_sample: int, E: int, n_sub: int, K1: int) -> None:
+    _check(lib().gbs_sample(net.handle, seed, first_sample, E, n_sub, K1))
+
+
+def gbs_binned_counts(net: Network, m_offset: int = 0, K1: Optional[int] = None
+                      ) -> Tuple[np.ndarray, np.ndarray, np.ndarray, np.ndarray]:
+    """(P_mP, sigma_mP, P_plusP, sigma_plusP), each K1 doubles, bins m_offset.."""
+    if K1 is None:
+        K1 = gbs_get_accumulators(net, with_data=False)[1]
+    outs = [np.zeros(K1) for _ in range(4)]
+    _check(lib().gbs_binned_counts(net.handle, m_offset, *[_dptr(o) for o in outs]))
+    return tuple(outs)
+
+
+def gbs_binned_counts_device(net: Network, m_offset: int, out_dev_ptr: int) -> None:
+    _check(lib().gbs_binned_counts_device(net.handle, m_offset, ctypes.c_void_p(out_dev_ptr)))
+
+
+def gbs_check_finite(net: Network) -> int:
+    c = ctypes.c_int64()
+    code = lib().gbs_check_finite(net.handle, ctypes.byref(c))
+    if code not in (GBS_OK, GBS_ENONFINITE):
+        _check(code)
+    return int(c.value)
+
+
+def gbs_debug_samples(net: Network, seed: int, e0: int, count: int):
+    """Per-trajectory (n[count], n_S[count] complex) from the device kernels."""
+    n = np.zeros(count)
+    nS = np.zeros(2 * count)
+    _check(lib().gbs_debug_samples(net.handle, seed, e0, count, _dptr(n), _dptr(nS)))
+    return n, nS.view(np.complex128)
+
+
+def gbs_get_accumulators(net: Network, with_data: bool = True):
+    """(n_sub, K1, acc[2][n_sub][K1] complex, counts[n_sub])."""
+    ns = ctypes.c_int()
+    k1 = ctypes.c_int()
+    _check(lib().gbs_get_accumulators(net.handle, ctypes.byref(ns), ctypes.byref(k1), None, None))
+    if not with_data or ns.value == 0:
+        return ns.value, k1.value, None, None
+    acc = np.zeros(4 * ns.value * k1.value)
+    cnt = np.zeros(ns.value, dtype=np.int64)
+    _check(lib().gbs_get_accumulators(net.handle, ctypes.byref(ns), ctypes.byref(k1), _dptr(acc),
+                                      cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return ns.value, k1.value, acc.view(np.complex128).reshape(2, ns.value, k1.value), cnt
+
+
+def gbs_set_accumulators(net: Network, acc: np.ndarray, counts: np.ndarray) -> None:
+    acc = np.ascontiguousarray(acc, dtype=np.complex128)
+    counts = np.ascontiguousarray(counts, dtype=np.int64)
+    _, n_sub, K1 = acc.shape
+    _check(lib().gbs_set_accumulators(net.handle, n_sub, K1, _dptr(acc.view(np.float64)),
+                                      counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+
+
+def gbs_reset(net: Network) -> None:
+    _check(lib().gbs_reset(net.handle))
+
+
+def gbs_network_info(net: Network):
+    N = ctypes.c_int()
+    M = ctypes.c_int()
+    p = ctypes.c_int()
+    c = ctypes.c_int64()
+    _check(lib().gbs_network_info(net.handle, ctypes.byref(N), ctypes.byref(M), ctypes.byref(p),
+                                  ctypes.byref(c)))
+    return N.value, M.value, p.value, c.value
+
+
+def gbs_free_network(net: Network) -> None:
+    if net.handle and net.handle.value:
+        lib().gbs_free_network(net.handle)
+        net.handle = ctypes.c_void_p()

@@ -1,0 +1,449 @@
+// C ABI of the GB300 matrix-P library (declared in include/gbs.h).
+//
+// Orchestration of the ensemble loop of the matrix phase-space method for
+// Gaussian boson sampling: per chunk of trajectories
+//   K1 sampler -> K2/K3 propagation GEMM + occupation epilogue -> finalize
+//   -> K4 generating functions summed per sub-ensemble,
+// and on request K5 (inverse DFT + statistics).  Every device buffer is
+// owned by the network object; all work runs on the network's stream.
+#include "gbs_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+namespace gbs {
+
+static thread_local char g_err[1024] = "";
+
+int set_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+const char *error_message() { return g_err; }
+
+bool device_has_tcgen05(int device) {
+    int major = 0, minor = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device) != cudaSuccess)
+        return false;
+    if (cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device) != cudaSuccess)
+        return false;
+    return major == 10 && minor == 3;  // this library is built for sm_103a only
+}
+
+namespace {
+
+template <typename T>
+int dev_alloc(T **p, size_t count, const char *what) {
+    *p = nullptr;
+    if (count == 0) return GBS_OK;
+    cudaError_t err = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+    if (err != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return set_error(err == cudaErrorMemoryAllocation ? GBS_ENOMEM : GBS_ECUDA,
+                         "cudaMalloc(%s, %zu bytes) failed: %s", what, count * sizeof(T),
+                         cudaGetErrorString(err));
+    }
+    return GBS_OK;
+}
+
+template <typename T>
+void dev_free(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int64_t pick_chunk(const gbs_net *net) {
+    // trajectories per chunk: sample operand <= 1 GiB, multiple of 128, in [128, 2^17]
+    size_t per_traj;
+    if (net->precision == GBS_FP64)
+        per_traj = (size_t)16 * net->N;
+    else
+        per_traj = (size_t)4 * net->planesB * net->ldK;
+    int64_t c = (int64_t)((size_t)1 << 30) / (int64_t)per_traj;
+    c = std::min<int64_t>(c, (int64_t)1 << 17);
+    c = (c / 128) * 128;
+    return std::max<int64_t>(c, 128);
+}
+
+void release_estimator(gbs_net *net) {
+    dev_free(net->d_acc);
+    dev_free(net->d_counts);
+    dev_free(net->d_tw);
+    dev_free(net->d_wfft);
+    dev_free(net->d_fft0);
+    dev_free(net->d_fft1);
+    dev_free(net->d_out);
+    net->counts.clear();
+    net->est_fixed = false;
+    net->n_sub = 0;
+    net->K1 = 0;
+}
+
+void release_all(gbs_net *net) {
+    release_estimator(net);
+    if (net->tc) tc_plan_destroy(net);
+    dev_free(net->d_sq64);
+    dev_free(net->d_sq32);
+    dev_free(net->d_T64);
+    dev_free(net->d_A);
+    if (net->d_B) cudaFree(net->d_B);
+    net->d_B = nullptr;
+    dev_free(net->d_n);
+    dev_free(net->d_nS_part);
+    dev_free(net->d_nS);
+    dev_free(net->d_win);
+    dev_free(net->d_flags);
+}
+
+int fix_estimator(gbs_net *net, int n_sub, int K1) {
+    if (net->est_fixed) {
+        if (n_sub != net->n_sub || K1 != net->K1)
+            return set_error(GBS_EINVAL,
+                             "n_sub/K1 (%d, %d) differ from the values fixed by the first call "
+                             "(%d, %d); call gbs_reset first",
+                             n_sub, K1, net->n_sub, net->K1);
+        return GBS_OK;
+    }
+    if (n_sub < 1 || n_sub > 65535) return set_error(GBS_EINVAL, "n_sub must be in [1, 65535]");
+    if (!is_pow2(K1) || K1 < 2 || K1 > (1 << 20))
+        return set_error(GBS_EINVAL, "K1 must be a power of two in [2, 2^20]");
+    net->n_sub = n_sub;
+    net->K1 = K1;
+    const size_t accn = (size_t)2 * n_sub * K1;
+    int rc;
+    if ((rc = dev_alloc(&net->d_acc, accn, "acc")) ||
+        (rc = dev_alloc(&net->d_counts, (size_t)n_sub, "counts")) ||
+        (rc = dev_alloc(&net->d_tw, (size_t)K1, "tw")) ||
+        (rc = dev_alloc(&net->d_wfft, (size_t)K1, "wfft")) ||
+        (rc = dev_alloc(&net->d_fft0, accn, "fft0")) ||
+        (rc = dev_alloc(&net->d_fft1, accn, "fft1")) ||
+        (rc = dev_alloc(&net->d_out, (size_t)4 * K1, "out"))) {
+        release_estimator(net);
+        return rc;
+    }
+    GBS_CUDA_TRY(cudaMemsetAsync(net->d_acc, 0, accn * sizeof(double2), net->stream));
+    GBS_CUDA_TRY(cudaMemsetAsync(net->d_counts, 0, (size_t)n_sub * sizeof(int64_t), net->stream));
+    if ((rc = launch_tables(net))) {
+        release_estimator(net);
+        return rc;
+    }
+    net->counts.assign((size_t)n_sub, 0);
+    net->est_fixed = true;
+    return GBS_OK;
+}
+
+// Sampler + propagation + finalize for one chunk of `count` trajectories.
+int run_chunk_front(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) {
+    int rc;
+    if (net->precision == GBS_FP64) {
+        if ((rc = launch_sample_fp64(net, seed, e0, count))) return rc;
+        if ((rc = launch_gemm_fp64(net, count))) return rc;
+    } else {
+        if ((rc = launch_sample_bf16(net, seed, e0, count))) return rc;
+        if ((rc = launch_gemm_tc(net, count))) return rc;
+    }
+    return launch_finalize(net, count);
+}
+
+int validate_net(gbs_net *net) {
+    if (!net) return set_error(GBS_EINVAL, "null network");
+    return GBS_OK;
+}
+
+}  // namespace
+}  // namespace gbs
+
+using namespace gbs;
+
+extern "C" {
+
+const char *gbs_last_error(void) { return error_message(); }
+
+int gbs_make_network(int N, int M, const double *T, const double *r, int precision, void *stream,
+                     gbs_net_t *out) {
+    if (!out) return set_error(GBS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (N < 1 || M < 1 || N > 65536 || M > 65536)
+        return set_error(GBS_EINVAL, "N and M must be in [1, 65536] (got %d, %d)", N, M);
+    if (!T || !r) return set_error(GBS_EINVAL, "T and r must be non-NULL host pointers");
+    if (precision != GBS_FP64 && precision != GBS_BF16X3 && precision != GBS_BF16X6)
+        return set_error(GBS_EINVAL, "unknown precision %d", precision);
+    for (int j = 0; j < N; ++j)
+        if (!std::isfinite(r[j]) || r[j] < 0.0)
+            return set_error(GBS_EINVAL, "r[%d] = %g: squeezing must be finite and >= 0", j, r[j]);
+    for (size_t q = 0; q < (size_t)2 * M * N; ++q)
+        if (!std::isfinite(T[q])) return set_error(GBS_EINVAL, "T has a non-finite entry");
+
+    gbs_net *net = new (std::nothrow) gbs_net();
+    if (!net) return set_error(GBS_ENOMEM, "host allocation failed");
+    net->N = N;
+    net->M = M;
+    net->precision = precision;
+    net->stream = static_cast<cudaStream_t>(stream);
+    int rc = GBS_OK;
+    auto fail = [&](int code) {
+        release_all(net);
+        delete net;
+        return code;
+    };
+    if (cudaGetDevice(&net->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&net->sm_count, cudaDevAttrMultiProcessorCount, net->device) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return fail(set_error(GBS_ECUDA, "no usable CUDA device"));
+    }
+    if (!device_has_tcgen05(net->device))
+        return fail(set_error(GBS_ENOTSUP, "this library is built for sm_103a (GB300) only"));
+    net->mtiles = (M + kFp64TileModes - 1) / kFp64TileModes;
+
+    // sampler coefficients sqrt(s+-/2), s+- = sinh r e^{+-r}
+    std::vector<double2> sq64(N);
+    std::vector<float2> sq32(N);
+    for (int j = 0; j < N; ++j) {
+        const double sp = std::sinh(r[j]) * std::exp(r[j]);
+        const double sm = std::sinh(r[j]) * std::exp(-r[j]);
+        sq64[j] = make_double2(std::sqrt(0.5 * sp), std::sqrt(0.5 * sm));
+        sq32[j] = make_float2((float)sq64[j].x, (float)sq64[j].y);
+    }
+    if ((rc = dev_alloc(&net->d_sq64, (size_t)N, "sq64")) ||
+        (rc = dev_alloc(&net->d_sq32, (size_t)N, "sq32")))
+        return fail(rc);
+    if (cudaMemcpy(net->d_sq64, sq64.data(), sizeof(double2) * N, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(net->d_sq32, sq32.data(), sizeof(float2) * N, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        return fail(set_error(GBS_ECUDA, "upload of sampler coefficients failed"));
+
+    if (precision == GBS_FP64) {
+        std::vector<double> t64((size_t)M * 2 * N);
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < N; ++j) {
+                t64[((size_t)i * 2 + 0) * N + j] = T[2 * ((size_t)i * N + j)];
+                t64[((size_t)i * 2 + 1) * N + j] = T[2 * ((size_t)i * N + j) + 1];
+            }
+        if ((rc = dev_alloc(&net->d_T64, t64.size(), "T64"))) return fail(rc);
+        if (cudaMemcpy(net->d_T64, t64.data(), t64.size() * sizeof(double),
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(set_error(GBS_ECUDA, "upload of T failed"));
+    } else {
+        // A = [Re T_i.; Im T_i.] rows interleaved per output mode, T rounded to
+        // FP32 and split into BF16 planes T = T0 + T1 + T2.
+        net->planesA = 3;
+        net->planesB = (precision == GBS_BF16X3) ? 2 : 3;
+        net->ldK = (N + 7) / 8 * 8;
+        net->rowsA = 2 * M;
+        const size_t plane = (size_t)net->rowsA * net->ldK;
+        std::vector<__nv_bfloat16> a((size_t)net->planesA * plane, __float2bfloat16(0.0f));
+        for (int i = 0; i < M; ++i)
+            for (int c = 0; c < 2; ++c)
+                for (int j = 0; j < N; ++j) {
+                    const float x = (float)T[2 * ((size_t)i * N + j) + c];
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
+                    const float r1 = x - __bfloat162float(h0);
+                    const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+                    const float r2 = r1 - __bfloat162float(h1);
+                    const __nv_bfloat16 h2 = __float2bfloat16_rn(r2);
+                    const size_t o = ((size_t)2 * i + c) * net->ldK + j;
+                    a[o] = h0;
+                    a[plane + o] = h1;
+                    a[2 * plane + o] = h2;
+                }
+        if ((rc = dev_alloc(&net->d_A, a.size(), "A planes"))) return fail(rc);
+        if (cudaMemcpy(net->d_A, a.data(), a.size() * sizeof(__nv_bfloat16),
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(set_error(GBS_ECUDA, "upload of T planes failed"));
+    }
+
+    // chunk workspace
+    net->chunk = pick_chunk(net);
+    if (precision == GBS_FP64) {
+        net->B_bytes = (size_t)net->chunk * 2 * N * sizeof(double);
+    } else {
+        const int64_t tiles = (net->chunk + kTcTileSamples - 1) / kTcTileSamples;
+        net->B_bytes = (size_t)net->planesB * tiles * 256 * net->ldK * sizeof(__nv_bfloat16);
+    }
+    {
+        cudaError_t err = cudaMalloc(&net->d_B, net->B_bytes);
+        if (err != cudaSuccess) {
+            net->d_B = nullptr;
+            cudaGetLastError();
+            return fail(set_error(GBS_ENOMEM, "cudaMalloc(sample operand, %zu bytes): %s",
+                                  net->B_bytes, cudaGetErrorString(err)));
+        }
+        if (cudaMemset(net->d_B, 0, net->B_bytes) != cudaSuccess)
+            return fail(set_error(GBS_ECUDA, "memset of the sample operand failed"));
+    }
+    if ((rc = dev_alloc(&net->d_n, (size_t)net->chunk, "n")) ||
+        (rc = dev_alloc(&net->d_nS_part, (size_t)net->chunk * net->mtiles, "nS_part")) ||
+        (rc = dev_alloc(&net->d_nS, (size_t)net->chunk, "nS")) ||
+        (rc = dev_alloc(&net->d_win, (size_t)net->chunk, "windows")) ||
+        (rc = dev_alloc(&net->d_flags, (size_t)4, "flags")))
+        return fail(rc);
+    if (cudaMemset(net->d_flags, 0, 4 * sizeof(unsigned long long)) != cudaSuccess)
+        return fail(set_error(GBS_ECUDA, "memset of flags failed"));
+    if (precision != GBS_FP64) {
+        if ((rc = tc_plan_create(net))) return fail(rc);
+    }
+    *out = net;
+    return GBS_OK;
+}
+
+int gbs_sample(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub, int K1) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (E < 0) return set_error(GBS_EINVAL, "E must be >= 0");
+    if (first_sample + (uint64_t)E < first_sample)
+        return set_error(GBS_EINVAL, "sample index range overflows 64 bits");
+    if ((rc = fix_estimator(net, n_sub, K1))) return rc;
+    for (int64_t done = 0; done < E; done += net->chunk) {
+        const int64_t c = std::min<int64_t>(net->chunk, E - done);
+        const uint64_t e0 = first_sample + (uint64_t)done;
+        if ((rc = run_chunk_front(net, seed, e0, c))) return rc;
+        if ((rc = launch_gf(net, e0, c))) return rc;
+    }
+    // host mirror of the sub-ensemble sizes
+    const uint64_t ns = (uint64_t)net->n_sub;
+    const uint64_t full = (uint64_t)E / ns, rem = (uint64_t)E % ns;
+    const uint64_t start = first_sample % ns;
+    for (uint64_t q = 0; q < ns; ++q) net->counts[q] += (int64_t)full;
+    for (uint64_t q = 0; q < rem; ++q) net->counts[(start + q) % ns] += 1;
+    return GBS_OK;
+}
+
+int gbs_binned_counts_device(gbs_net_t net, int64_t m_offset, double *out_dev) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (!out_dev) return set_error(GBS_EINVAL, "out_dev is NULL");
+    if (!net->est_fixed) return set_error(GBS_EINVAL, "no samples drawn yet");
+    for (int q = 0; q < net->n_sub; ++q)
+        if (net->counts[q] <= 0)
+            return set_error(GBS_EINVAL, "sub-ensemble %d has no trajectories", q);
+    return launch_invert(net, m_offset, out_dev);
+}
+
+int gbs_check_finite(gbs_net_t net, int64_t *count) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (count) *count = 0;
+    if (!net->est_fixed) return GBS_OK;
+    if ((rc = launch_count_nonfinite(net))) return rc;
+    unsigned long long h = 0;
+    GBS_CUDA_TRY(cudaMemcpyAsync(&h, net->d_flags, sizeof(h), cudaMemcpyDeviceToHost, net->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(net->stream));
+    if (count) *count = (int64_t)h;
+    if (h) return set_error(GBS_ENONFINITE, "%llu non-finite generating-function sums", h);
+    return GBS_OK;
+}
+
+int gbs_binned_counts(gbs_net_t net, int64_t m_offset, double *P_mP, double *sig_mP,
+                      double *P_plusP, double *sig_plusP) {
+    int rc;
+    if ((rc = gbs_binned_counts_device(net, m_offset, net ? net->d_out : nullptr))) return rc;
+    int64_t bad = 0;
+    if ((rc = gbs_check_finite(net, &bad))) return rc;
+    double *dst[4] = {P_mP, sig_mP, P_plusP, sig_plusP};
+    for (int q = 0; q < 4; ++q)
+        if (dst[q])
+            GBS_CUDA_TRY(cudaMemcpyAsync(dst[q], net->d_out + (size_t)q * net->K1,
+                                         sizeof(double) * net->K1, cudaMemcpyDeviceToHost,
+                                         net->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(net->stream));
+    return GBS_OK;
+}
+
+int gbs_debug_samples(gbs_net_t net, uint64_t seed, uint64_t e0, int64_t count, double *n,
+                      double *nS) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (count < 0 || !n || !nS) return set_error(GBS_EINVAL, "bad count or NULL output");
+    const int saved_K1 = net->K1;
+    if (net->K1 == 0) net->K1 = 2;  // finalize computes windows for some K1; unused here
+    for (int64_t done = 0; done < count; done += net->chunk) {
+        const int64_t c = std::min<int64_t>(net->chunk, count - done);
+        if ((rc = run_chunk_front(net, seed, e0 + (uint64_t)done, c))) {
+            net->K1 = saved_K1;
+            return rc;
+        }
+        cudaError_t e1 = cudaMemcpyAsync(n + done, net->d_n, sizeof(double) * c,
+                                         cudaMemcpyDeviceToHost, net->stream);
+        cudaError_t e2 = cudaMemcpyAsync(nS + 2 * done, net->d_nS, sizeof(double2) * c,
+                                         cudaMemcpyDeviceToHost, net->stream);
+        cudaError_t e3 = cudaStreamSynchronize(net->stream);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+            net->K1 = saved_K1;
+            return set_error(GBS_ECUDA, "debug copy failed: %s",
+                             cudaGetErrorString(e3 != cudaSuccess ? e3 : (e2 != cudaSuccess ? e2 : e1)));
+        }
+    }
+    net->K1 = saved_K1;
+    return GBS_OK;
+}
+
+int gbs_get_accumulators(gbs_net_t net, int *n_sub, int *K1, double *acc, int64_t *counts) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (n_sub) *n_sub = net->n_sub;
+    if (K1) *K1 = net->K1;
+    if (!net->est_fixed) return GBS_OK;
+    if (acc)
+        GBS_CUDA_TRY(cudaMemcpyAsync(acc, net->d_acc, sizeof(double2) * 2 * net->n_sub * net->K1,
+                                     cudaMemcpyDeviceToHost, net->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(net->stream));
+    if (counts) std::memcpy(counts, net->counts.data(), sizeof(int64_t) * net->n_sub);
+    return GBS_OK;
+}
+
+int gbs_set_accumulators(gbs_net_t net, int n_sub, int K1, const double *acc,
+                         const int64_t *counts) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (!acc || !counts) return set_error(GBS_EINVAL, "acc and counts must be non-NULL");
+    for (int q = 0; q < n_sub; ++q)
+        if (counts[q] < 0) return set_error(GBS_EINVAL, "negative count");
+    if ((rc = fix_estimator(net, n_sub, K1))) return rc;
+    GBS_CUDA_TRY(cudaMemcpyAsync(net->d_acc, acc, sizeof(double2) * 2 * n_sub * K1,
+                                 cudaMemcpyHostToDevice, net->stream));
+    GBS_CUDA_TRY(cudaMemcpyAsync(net->d_counts, counts, sizeof(int64_t) * n_sub,
+                                 cudaMemcpyHostToDevice, net->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(net->stream));
+    std::memcpy(net->counts.data(), counts, sizeof(int64_t) * n_sub);
+    return GBS_OK;
+}
+
+int gbs_reset(gbs_net_t net) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    GBS_CUDA_TRY(cudaStreamSynchronize(net->stream));
+    release_estimator(net);
+    return GBS_OK;
+}
+
+int gbs_network_info(gbs_net_t net, int *N, int *M, int *precision, int64_t *chunk) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (N) *N = net->N;
+    if (M) *M = net->M;
+    if (precision) *precision = net->precision;
+    if (chunk) *chunk = net->chunk;
+    return GBS_OK;
+}
+
+void gbs_free_network(gbs_net_t net) {
+    if (!net) return;
+    cudaStreamSynchronize(net->stream);
+    release_all(net);
+    delete net;
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+// Internal declarations of the GB300 matrix-P library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gbs.h"
+
+namespace gbs {
+
+// ---------------------------------------------------------------------------
+// Error reporting (thread-local message, see gbs_last_error)
+// ---------------------------------------------------------------------------
+int set_error(int code, const char *fmt, ...);
+const char *error_message();
+
+#define GBS_CUDA_TRY(call)                                                             \
+    do {                                                                               \
+        cudaError_t err__ = (call);                                                    \
+        if (err__ != cudaSuccess)                                                      \
+            return ::gbs::set_error(GBS_ECUDA, "%s failed: %s (%s:%d)", #call,         \
+                                    cudaGetErrorString(err__), __FILE__, __LINE__);    \
+    } while (0)
+
+#define GBS_LAUNCH_CHECK()                                                             \
+    do {                                                                               \
+        cudaError_t err__ = cudaGetLastError();                                        \
+        if (err__ != cudaSuccess)                                                      \
+            return ::gbs::set_error(GBS_ECUDA, "kernel launch failed: %s (%s:%d)",     \
+                                    cudaGetErrorString(err__), __FILE__, __LINE__);    \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Constants
+// ---------------------------------------------------------------------------
+// Terms of a generating function whose log-magnitude is below -60 ln 2
+// (|term| < 2^-60) are not evaluated.
+constexpr double kSkipLog = 41.58883083359672;  // 60 * ln 2
+constexpr int kFp64TileModes = 64;              // output modes per FP64 GEMM tile
+constexpr int kFp64TileSamples = 32;            // samples per FP64 GEMM tile
+constexpr int kTcTileModes = 64;                // output modes per tcgen05 tile (128 A rows)
+constexpr int kTcTileSamples = 128;             // samples per tcgen05 tile (256 B rows)
+constexpr int kTcBlockK = 64;                   // K elements per pipeline stage (128 B of bf16)
+
+// Per-sample windows of the generating-function evaluation, in units of k:
+// w1 = half-width around theta = 0 (both estimators' e^{(z-1) n_S} term),
+// w2 = half-width around theta = pi (matrix-P's e^{-(z-1) n_S - 2n} term),
+// -1 = empty, >= K1/2 = whole circle.
+struct Window {
+    int w1;
+    int w2;
+};
+
+// ---------------------------------------------------------------------------
+// The network object behind gbs_net_t
+// ---------------------------------------------------------------------------
+struct TcPlan;  // tcgen05 GEMM plan (tensor maps, tiling), defined in k_gemm_tc.cu
+
+}  // namespace gbs
+
+struct gbs_net {
+    int N = 0, M = 0, precision = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0, sm_count = 0;
+
+    // per-mode sampler coefficients: (sqrt(s+/2), sqrt(s-/2)), s+- = sinh r e^{+-r}
+    double2 *d_sq64 = nullptr;
+    float2 *d_sq32 = nullptr;
+
+    // FP64 network operand: [M][2][N], row (i,0) = Re T_i., (i,1) = Im T_i.
+    double *d_T64 = nullptr;
+
+    // BF16 split operands (GBS_BF16X3 / X6): planes of A = [Re T; Im T] rows
+    // interleaved per mode, padded: [planes][rowsA][ldK] bf16
+    __nv_bfloat16 *d_A = nullptr;
+    int planesA = 0, planesB = 0, rowsA = 0, ldK = 0;
+    gbs::TcPlan *tc = nullptr;
+
+    // chunk workspace
+    int64_t chunk = 0;
+    void *d_B = nullptr;  // sample operand
+    size_t B_bytes = 0;
+    double *d_n = nullptr;          // [chunk]
+    double2 *d_nS_part = nullptr;   // [mtiles][chunk]
+    int mtiles = 0;
+    double2 *d_nS = nullptr;        // [chunk]
+    gbs::Window *d_win = nullptr;   // [chunk]
+
+    // estimator state
+    int n_sub = 0, K1 = 0;
+    bool est_fixed = false;
+    double2 *d_acc = nullptr;       // [2][n_sub][K1]
+    int64_t *d_counts = nullptr;    // [n_sub]
+    std::vector<int64_t> counts;    // host mirror, updated per call
+    double2 *d_tw = nullptr;        // [K1]: (cos theta_k - 1, sin theta_k)
+    double2 *d_fft0 = nullptr, *d_fft1 = nullptr;  // [2][n_sub][K1]
+    double2 *d_wfft = nullptr;      // [K1]: e^{-2 pi i k / K1}
+    double *d_out = nullptr;        // [4][K1]
+    unsigned long long *d_flags = nullptr;  // [4]: non-finite count, timeout flag, ...
+};
+
+namespace gbs {
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (each returns a GBS status)
+// ---------------------------------------------------------------------------
+// Sampler: writes the sample operand for trajectories e0..e0+count-1 and n[].
+int launch_sample_fp64(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count);
+int launch_sample_bf16(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count);
+
+// Propagation GEMM with the fused occupation epilogue -> nS_part[mtiles][chunk].
+int launch_gemm_fp64(gbs_net *net, int64_t count);
+int tc_plan_create(gbs_net *net);
+void tc_plan_destroy(gbs_net *net);
+int launch_gemm_tc(gbs_net *net, int64_t count);
+
+// Finalise n_S (fixed-order sum of tile partials) and the evaluation windows.
+int launch_finalize(gbs_net *net, int64_t count);
+
+// Generating functions, summed per sub-ensemble into d_acc.
+int launch_gf(gbs_net *net, uint64_t e0, int64_t count);
+
+// Twiddle tables for K1 points.
+int launch_tables(gbs_net *net);
+
+// Inverse DFT + statistics into out_dev[4][K1].
+int launch_invert(gbs_net *net, int64_t m_offset, double *out_dev);
+
+// Non-finite count of the accumulators into d_flags[0].
+int launch_count_nonfinite(gbs_net *net);
+
+// Device properties helper.
+bool device_has_tcgen05(int device);
+
+}  // namespace gbs

@@ -1,0 +1,134 @@
+// K2 + K3, FP64 path: propagation alpha' = T alpha, beta' = T* beta
+// ("Applications to GBS") as a real GEMM of the row-interleaved operand
+// A = [Re T_i.; Im T_i.] (2M x N) with B = [alpha_e, beta_e] (N x 2E), fused with
+// the occupation epilogue
+//   n'_i = alpha'_i beta'_i = (a_r + i a_i)(b_r - i b_i)
+//        = (a_r b_r + a_i b_i) + i (a_i b_r - a_r b_i),
+//   a = (Re T alpha, Im T alpha)_i, b = (Re T beta, Im T beta)_i,
+// summed over the tile's output modes.  alpha', beta' never leave registers;
+// the kernel writes one partial n_S per (mode tile, trajectory).
+//
+// Tile: 64 output modes x 32 trajectories per 256-thread block; each thread
+// owns 4 modes x 2 trajectories (32 FP64 accumulators).  This path is bound
+// by the FP64 FMA rate.
+#include "gbs_internal.cuh"
+
+namespace gbs {
+namespace {
+
+constexpr int TM = kFp64TileModes;    // 64 modes -> 128 A rows
+constexpr int TS = kFp64TileSamples;  // 32 trajectories -> 64 B rows
+constexpr int KT = 16;                // K per smem stage
+
+__global__ void __launch_bounds__(256) k_gemm_fp64(const double *__restrict__ T64,
+                                                   const double *__restrict__ B, int N, int M,
+                                                   int64_t count, int64_t ld_part,
+                                                   double2 *__restrict__ nS_part) {
+    __shared__ double As[KT][2 * TM + 1];
+    __shared__ double Bs[KT][2 * TS + 1];
+    __shared__ double2 red[16][TS];
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15;  // trajectory pair
+    const int ty = tid >> 4;  // mode quad
+    const int mtile = blockIdx.y;
+    const int i0 = mtile * TM;
+    const int64_t s0 = (int64_t)blockIdx.x * TS;
+
+    double acc[4][2][2][2];  // [mode][Re/Im row][trajectory][alpha/beta]
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int d = 0; d < 2; ++d) acc[a][b][c][d] = 0.0;
+
+    for (int k0 = 0; k0 < N; k0 += KT) {
+        // A tile: 128 rows x 16 k (row = 2*mode_local + re/im), 8 per thread
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int idx = tid + 256 * t;
+            const int row = idx >> 4;
+            const int kk = idx & 15;
+            const int i = i0 + (row >> 1);
+            const int k = k0 + kk;
+            double v = 0.0;
+            if (i < M && k < N) v = T64[((size_t)i * 2 + (row & 1)) * N + k];
+            As[kk][row] = v;
+        }
+        // B tile: 64 rows x 16 k (row = 2*traj_local + alpha/beta), 4 per thread
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int idx = tid + 256 * t;
+            const int row = idx >> 4;
+            const int kk = idx & 15;
+            const int64_t s = s0 + (row >> 1);
+            const int k = k0 + kk;
+            double v = 0.0;
+            if (s < count && k < N) v = B[((size_t)s * 2 + (row & 1)) * N + k];
+            Bs[kk][row] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < KT; ++kk) {
+            double a[8], b[4];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) a[t] = As[kk][ty * 8 + t];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) b[t] = Bs[kk][tx * 4 + t];
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int ri = 0; ri < 2; ++ri)
+#pragma unroll
+                    for (int s = 0; s < 2; ++s)
+#pragma unroll
+                        for (int ab = 0; ab < 2; ++ab)
+                            acc[m][ri][s][ab] = fma(a[2 * m + ri], b[2 * s + ab], acc[m][ri][s][ab]);
+        }
+        __syncthreads();
+    }
+
+    // occupation epilogue: sum of n'_i over this thread's 4 modes
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        double re = 0.0, im = 0.0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const double ar = acc[m][0][s][0], ai = acc[m][1][s][0];
+            const double br = acc[m][0][s][1], bi = acc[m][1][s][1];
+            re += ar * br + ai * bi;
+            im += ai * br - ar * bi;
+        }
+        red[ty][tx * 2 + s] = make_double2(re, im);
+    }
+    __syncthreads();
+    if (tid < TS) {
+        double re = 0.0, im = 0.0;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            re += red[t][tid].x;
+            im += red[t][tid].y;
+        }
+        const int64_t s = s0 + tid;
+        if (s < count) nS_part[(size_t)mtile * ld_part + s] = make_double2(re, im);
+    }
+}
+
+}  // namespace
+
+int launch_gemm_fp64(gbs_net *net, int64_t count) {
+    if (count <= 0) return GBS_OK;
+    const int64_t sblocks = (count + TS - 1) / TS;
+    if (sblocks > 0x7fffffff) return set_error(GBS_EINVAL, "chunk too large");
+    dim3 grid((unsigned)sblocks, (unsigned)net->mtiles);
+    k_gemm_fp64<<<grid, 256, 0, net->stream>>>(net->d_T64, static_cast<const double *>(net->d_B),
+                                                net->N, net->M, count, net->chunk,
+                                                net->d_nS_part);
+    GBS_LAUNCH_CHECK();
+    return GBS_OK;
+}
+
+}  // namespace gbs

@@ -1,0 +1,402 @@
+// K2 + K3, BF16 split path: propagation alpha' = T alpha, beta' = T* beta
+// ("Applications to GBS") on the tcgen05 tensor cores, fused with the
+// occupation epilogue n'_i = alpha'_i beta'_i and its sum over the tile's
+// output modes.
+//
+// GEMM: C = A B^T with A = [Re T_i.; Im T_i.] (rows interleaved per output
+// mode, 2M x N) and B = per 128-trajectory tile [alpha rows; beta rows]
+// (256 x N), both K-major BF16.  FP32-level accuracy comes from splitting
+// A = A0 + A1 + A2 and B = B0 + B1 + B2 into BF16 planes and summing the
+// products A_i B_j with i + j <= 1 (3 products) or i + j <= 2 (6 products),
+// all into one FP32 accumulator (the split-precision pattern, e.g. Henry,
+// Tang, Heinecke, "Leveraging the bfloat16 artificial intelligence datatype
+// for higher-precision computations", ARITH 2019).
+//
+// Kernel structure (one CTA per SM, persistent over tiles):
+//   warp 0      TMA producer: per (product, 64-wide K block) one A box
+//               (64 x 128) and one B box (64 x 256), 128-byte swizzle, into a
+//               4-stage shared-memory ring;
+//   warp 1      allocates 512 TMEM columns; one thread issues
+//               tcgen05.mma M=128 N=256 K=16 into one of two 256-column
+//               accumulators and commits stage releases / tile completion;
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator (TMEM lane = A row,
+//               columns 0..127 = alpha' parts, 128..255 = beta' parts of the
+//               tile's 128 trajectories), occupations, butterfly
+//               transpose-reduction over the 32 lanes of each warp, then the
+//               4 warps in a fixed order -> one n_S partial per (mode tile,
+//               trajectory).  alpha', beta' never leave the SM.
+// Every mbarrier wait is bounded; on a timeout the kernel raises an error
+// flag, drains its own TMA loads and MMAs, frees TMEM and returns.
+#include "gbs_internal.cuh"
+#include "tc_ptx.cuh"
+
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+namespace gbs {
+
+struct TcPlan {
+    CUtensorMap mapA[3];
+    CUtensorMap mapB[3];
+    int P = 0;
+    int ia[6] = {0, 0, 0, 0, 0, 0};
+    int ib[6] = {0, 0, 0, 0, 0, 0};
+    int64_t rowsB = 0;
+    bool attr_set = false;
+};
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kABytes = 128 * 128;  // 128 rows x 64 bf16
+constexpr int kBBytes = 256 * 128;  // 256 rows x 64 bf16
+constexpr int kStageBytes = kABytes + kBBytes;
+constexpr int kBarBytes = 1024;
+constexpr int kRedBytes = 4 * 128 * 8;  // float2 [4][128]
+constexpr int kSmemBytes = 1024 + kStages * kStageBytes + kBarBytes + kRedBytes;
+constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(128, 256);
+constexpr int kEpiThreads = 128;
+
+struct TcParams {
+    int KB;  // 64-wide K blocks
+    int P;   // products
+    int ia[6];
+    int ib[6];
+    int mtiles;
+    int stiles;
+    int64_t count;
+    int64_t ld_part;
+    double2 *nS_part;
+    unsigned long long *err;
+};
+
+__device__ __forceinline__ void named_bar_sync(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+__global__ void __launch_bounds__(192, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+              const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
+              const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2,
+              const TcParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + kStages * kABytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+    uint64_t *full = bars;
+    uint64_t *empty = bars + kStages;
+    uint64_t *tfull = bars + 2 * kStages;
+    uint64_t *tempty = bars + 2 * kStages + 2;
+    uint64_t *drain = bars + 2 * kStages + 4;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 5);
+    int *s_ok = reinterpret_cast<int *>(bars + 2 * kStages + 6);
+    float2 *red = reinterpret_cast<float2 *>(smem + kStages * kStageBytes + kBarBytes);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    volatile unsigned long long *err = p.err;
+
+    const CUtensorMap *mapsA[3] = {&mA0, &mA1, &mA2};
+    const CUtensorMap *mapsB[3] = {&mB0, &mB1, &mB2};
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            ptx::mbar_init(ptx::smem_u32(&full[s]), 1);
+            ptx::mbar_init(ptx::smem_u32(&empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(ptx::smem_u32(&tfull[b]), 1);
+            ptx::mbar_init(ptx::smem_u32(&tempty[b]), kEpiThreads);
+        }
+        ptx::mbar_init(ptx::smem_u32(drain), 1);
+        ptx::fence_barrier_init();
+        for (int q = 0; q < p.P; ++q) {
+            ptx::prefetch_tmap(mapsA[p.ia[q]]);
+            ptx::prefetch_tmap(mapsB[p.ib[q]]);
+        }
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(ptx::smem_u32(tmem_slot), 512);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    const int ntiles = p.mtiles * p.stiles;
+    const int iters = p.P * p.KB;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------------------------------------------- TMA producer
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t used = 0, last_phase = 0;  // stages ever filled, parity of their last fill
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+                const int mt = tile % p.mtiles;
+                const int st = tile / p.mtiles;
+                for (int it = 0; it < iters; ++it) {
+                    const int pr = it / p.KB;
+                    const int kb = it - pr * p.KB;
+                    if (!ptx::mbar_wait(ptx::smem_u32(&empty[stage]), phase ^ 1u, err)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = ptx::smem_u32(&full[stage]);
+                    ptx::mbar_arrive_expect_tx(fb, kStageBytes);
+                    ptx::tma_load_2d(ptx::smem_u32(sA + stage * kABytes), mapsA[p.ia[pr]], fb,
+                                     kb * 64, mt * 128);
+                    ptx::tma_load_2d(ptx::smem_u32(sB + stage * kBBytes), mapsB[p.ib[pr]], fb,
+                                     kb * 64, st * 256);
+                    used |= 1u << stage;
+                    last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            // drain: every load issued by this thread has landed before exit
+            for (int s = 0; s < kStages; ++s)
+                if (used & (1u << s))
+                    ptx::mbar_wait(ptx::smem_u32(&full[s]), (last_phase >> s) & 1u, err,
+                                   200000000ull);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------------------------------------------- MMA issuer
+            int stage = 0;
+            uint32_t phase = 0;
+            int lt = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++lt) {
+                const int b = lt & 1;
+                const uint32_t tph = (uint32_t)(lt >> 1) & 1u;
+                if (!ptx::mbar_wait(ptx::smem_u32(&tempty[b]), tph ^ 1u, err)) break;
+                ptx::tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(b * 256);
+                for (int it = 0; it < iters; ++it) {
+                    if (!ptx::mbar_wait(ptx::smem_u32(&full[stage]), phase, err)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint32_t a0 = ptx::smem_u32(sA + stage * kABytes);
+                    const uint32_t b0 = ptx::smem_u32(sB + stage * kBBytes);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        ptx::mma_bf16(d, ptx::desc_k_sw128(a0 + kk * 32),
+                                      ptx::desc_k_sw128(b0 + kk * 32), kIdesc,
+                                      (it | kk) != 0 ? 1u : 0u);
+                    ptx::mma_commit(ptx::smem_u32(&empty[stage]));
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (ok) ptx::mma_commit(ptx::smem_u32(&tfull[b]));
+            }
+            // drain: all MMAs issued by this thread have completed
+            ptx::mma_commit(ptx::smem_u32(drain));
+            ptx::mbar_wait(ptx::smem_u32(drain), 0u, err, 200000000ull);
+        }
+    } else {
+        // -------------------------------------------------------- epilogue
+        const int quarter = warp & 3;  // TMEM lanes this warp may access
+        const int row = quarter * 32 + lane;
+        const bool im_row = (row & 1) != 0;  // odd A rows hold Im T_i.
+        const int et = threadIdx.x - 64;     // 0..127
+        int lt = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+            const int b = lt & 1;
+            const uint32_t tph = (uint32_t)(lt >> 1) & 1u;
+            if (et == 0) *s_ok = ptx::mbar_wait(ptx::smem_u32(&tfull[b]), tph, err) ? 1 : 0;
+            named_bar_sync(1, kEpiThreads);
+            if (!*s_ok) break;
+            ptx::tc_fence_after();
+            const int mt = tile % p.mtiles;
+            const int st = tile / p.mtiles;
+            const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+#pragma unroll 1
+            for (int g = 0; g < 4; ++g) {
+                float va[32], vb[32];
+                ptx::tmem_ld32(tbase + (uint32_t)(g * 32), va);
+                ptx::tmem_ld32(tbase + (uint32_t)(128 + g * 32), vb);
+                ptx::tmem_ld_wait();
+                // occupations of this row: real part a*b (own row), imaginary
+                // part from the partner row (Re <-> Im of the same mode)
+                float v[64];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const float pb = __shfl_xor_sync(0xffffffffu, vb[q], 1);
+                    v[2 * q] = va[q] * vb[q];
+                    v[2 * q + 1] = im_row ? va[q] * pb : -va[q] * pb;
+                }
+                // butterfly transpose-reduction: lane l ends with (re, im) of trajectory g*32+l
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const bool up = (lane & 16) != 0;
+                    const float send = up ? v[i] : v[i + 32];
+                    const float keep = up ? v[i + 32] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const bool up = (lane & 8) != 0;
+                    const float send = up ? v[i] : v[i + 16];
+                    const float keep = up ? v[i + 16] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const bool up = (lane & 4) != 0;
+                    const float send = up ? v[i] : v[i + 8];
+                    const float keep = up ? v[i + 8] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const bool up = (lane & 2) != 0;
+                    const float send = up ? v[i] : v[i + 4];
+                    const float keep = up ? v[i + 4] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const bool up = (lane & 1) != 0;
+                    const float send = up ? v[i] : v[i + 2];
+                    const float keep = up ? v[i + 2] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+                }
+                red[quarter * 128 + g * 32 + lane] = make_float2(v[0], v[1]);
+            }
+            // accumulator buffer b may be overwritten by the next tile's MMAs
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(ptx::smem_u32(&tempty[b]));
+            named_bar_sync(1, kEpiThreads);
+            {
+                const int q = et;
+                double re = 0.0, im = 0.0;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const float2 x = red[w * 128 + q];
+                    re += (double)x.x;
+                    im += (double)x.y;
+                }
+                const int64_t s = (int64_t)st * 128 + q;
+                if (s < p.count) p.nS_part[(size_t)mt * p.ld_part + s] = make_double2(re, im);
+            }
+            named_bar_sync(1, kEpiThreads);
+        }
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem_base, 512);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+int encode_2d(CUtensorMap *map, void *base, uint64_t inner, uint64_t rows, uint64_t row_bytes,
+              uint32_t box_inner, uint32_t box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+    if (!enc) return set_error(GBS_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {box_inner, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(GBS_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return GBS_OK;
+}
+
+}  // namespace
+
+int tc_plan_create(gbs_net *net) {
+    TcPlan *plan = new (std::nothrow) TcPlan();
+    if (!plan) return set_error(GBS_ENOMEM, "host allocation failed");
+    net->tc = plan;
+    const size_t planeA = (size_t)net->rowsA * net->ldK;
+    const int64_t tiles = (net->chunk + kTcTileSamples - 1) / kTcTileSamples;
+    plan->rowsB = tiles * 256;
+    const size_t planeB = (size_t)plan->rowsB * net->ldK;
+    int rc;
+    for (int q = 0; q < 3; ++q) {
+        if ((rc = encode_2d(&plan->mapA[q], net->d_A + q * planeA, (uint64_t)net->N,
+                            (uint64_t)net->rowsA, (uint64_t)net->ldK * 2, 64, 128)))
+            return rc;
+        __nv_bfloat16 *bbase = static_cast<__nv_bfloat16 *>(net->d_B) +
+                               (q < net->planesB ? q : 0) * planeB;
+        if ((rc = encode_2d(&plan->mapB[q], bbase, (uint64_t)net->N, (uint64_t)plan->rowsB,
+                            (uint64_t)net->ldK * 2, 64, 256)))
+            return rc;
+    }
+    // products A_i B_j: i + j <= 1, then (6 products) i + j == 2
+    const int ia6[6] = {0, 0, 1, 1, 0, 2};
+    const int ib6[6] = {0, 1, 0, 1, 2, 0};
+    plan->P = (net->precision == GBS_BF16X3) ? 3 : 6;
+    for (int q = 0; q < plan->P; ++q) {
+        plan->ia[q] = ia6[q];
+        plan->ib[q] = ib6[q];
+    }
+    return GBS_OK;
+}
+
+void tc_plan_destroy(gbs_net *net) {
+    delete net->tc;
+    net->tc = nullptr;
+}
+
+int launch_gemm_tc(gbs_net *net, int64_t count) {
+    if (count <= 0) return GBS_OK;
+    TcPlan *plan = net->tc;
+    if (!plan) return set_error(GBS_EINVAL, "no tensor-core plan");
+    if (!plan->attr_set) {
+        GBS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kSmemBytes));
+        plan->attr_set = true;
+    }
+    TcParams p;
+    p.KB = (net->N + kTcBlockK - 1) / kTcBlockK;
+    p.P = plan->P;
+    for (int q = 0; q < 6; ++q) {
+        p.ia[q] = plan->ia[q];
+        p.ib[q] = plan->ib[q];
+    }
+    p.mtiles = net->mtiles;
+    p.stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
+    p.count = count;
+    p.ld_part = net->chunk;
+    p.nS_part = net->d_nS_part;
+    p.err = net->d_flags + 1;
+    const int64_t ntiles = (int64_t)p.mtiles * p.stiles;
+    const int grid = (int)std::min<int64_t>(ntiles, net->sm_count);
+    k_gemm_tc<<<grid, 192, kSmemBytes, net->stream>>>(plan->mapA[0], plan->mapA[1], plan->mapA[2],
+                                                      plan->mapB[0], plan->mapB[1], plan->mapB[2],
+                                                      p);
+    GBS_LAUNCH_CHECK();
+    return GBS_OK;
+}
+
+}  // namespace gbs

@@ -1,0 +1,219 @@
+// K4: per-trajectory generating functions and their sub-ensemble sums.
+//
+// For trajectory e with input total n = alpha.beta (real) and output total
+// n_S = alpha'.beta' = x + i y, and z_k = e^{i theta_k}, theta_k = 2 pi k / K1,
+// the c-number projector of Eq. c-number-variable summed over m gives
+//   G_mP(z) = cosh(n + (z-1) n_S) / cosh(n)               (matrix-P, M = 2)
+//   G_+P(z) = exp((z-1) n_S)                              (+P, g_0 = 1)
+// With L = (z-1) n_S = l1 + i phi,
+//   l1  = (cos theta - 1) x - sin theta y,  phi = sin theta x + (cos theta - 1) y,
+// and numerator and denominator of cosh(n+L)/cosh(n) multiplied by e^{-|n|}:
+//   G_mP = [e^{l1 + c1} e^{i phi} + e^{-l1 + c2} e^{-i phi}] / (1 + e^{-2|n|}),
+//   c1 = min(0, 2n),  c2 = -2 max(n, 0),
+//   G_+P = e^{l1} e^{i phi}.
+// Terms below 2^-60 are skipped: per trajectory, finalize() derives from
+// (n, x, y) two windows of k (around theta = 0 for the e^{l1} terms, around
+// theta = pi for the e^{-l1} term) outside which each term is provably
+// smaller than 2^-60, using |sin theta| <= sqrt(2 (1 - cos theta)).
+//
+// Work split: one thread per k, one block per (256 consecutive k,
+// sub-ensemble r); each thread loops over the sub-ensemble's trajectories of
+// the chunk in increasing order and adds its sums to acc[est][r][k], so every
+// sum is formed in a fixed order (bitwise reproducible for a fixed chunking).
+// Trajectory e belongs to sub-ensemble e mod n_sub.
+#include "gbs_internal.cuh"
+
+#include <algorithm>
+
+namespace gbs {
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+__device__ __forceinline__ int half_width(double cstar, int K1) {
+    // largest |delta theta| with 1 - cos(delta theta) <= cstar, in k units, +1 margin
+    const int half = K1 >> 1;
+    if (!(cstar < 2.0)) return half;  // also catches NaN
+    const double th = 2.0 * asin(sqrt(0.5 * cstar));
+    const double w = floor(th * (double)K1 / kTwoPi) + 1.0;
+    return w >= (double)half ? half : (int)w;
+}
+
+__device__ __forceinline__ Window windows_for(double n, double x, double y, int K1) {
+    const double T = kSkipLog;
+    const double ay = fabs(y);
+    const int half = K1 >> 1;
+    Window w;
+    // e^{l1} terms: l1 <= -c x + sqrt(2c)|y|, c = 1 - cos theta
+    if (!(x > 0.0)) {
+        w.w1 = half;
+    } else {
+        const double u = (1.4142135623730951 * ay + sqrt(2.0 * y * y + 4.0 * x * T)) / (2.0 * x);
+        w.w1 = half_width(u * u, K1);
+    }
+    // e^{-l1 + c2} term: -l1 + c2 <= (2 - c')x + sqrt(2c')|y| + c2, c' = 1 + cos theta
+    const double c2 = -2.0 * fmax(n, 0.0);
+    if (!(x > 0.0)) {
+        w.w2 = (ay + c2 >= -T) ? half : -1;
+    } else {
+        const double D = 2.0 * x + c2 + T;
+        const double disc = 2.0 * y * y + 4.0 * x * D;
+        if (disc < 0.0) {
+            w.w2 = -1;
+        } else {
+            const double u = (1.4142135623730951 * ay + sqrt(disc)) / (2.0 * x);
+            w.w2 = (u < 0.0) ? -1 : half_width(u * u, K1);
+        }
+    }
+    return w;
+}
+
+__global__ void k_finalize(const double2 *__restrict__ part, int mtiles, int64_t ld,
+                           const double *__restrict__ n, int64_t count, int K1,
+                           double2 *__restrict__ nS, Window *__restrict__ win) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int t = 0; t < mtiles; ++t) {
+            const double2 p = part[(size_t)t * ld + i];
+            re += p.x;
+            im += p.y;
+        }
+        nS[i] = make_double2(re, im);
+        win[i] = windows_for(n[i], re, im, K1);
+    }
+}
+
+__device__ __forceinline__ int dist0(int k, int K1) { return k <= (K1 >> 1) ? k : K1 - k; }
+
+__device__ __forceinline__ int dist_pi(int k, int K1) {
+    const int d = k - (K1 >> 1);
+    return d < 0 ? -d : d;
+}
+
+// FP64 evaluation (GBS_FP64).
+__global__ void __launch_bounds__(256) k_gf_fp64(const double *__restrict__ n_in,
+                                                 const double2 *__restrict__ nS_in,
+                                                 const Window *__restrict__ win_in,
+                                                 int64_t count, uint64_t e0, int n_sub, int K1,
+                                                 const double2 *__restrict__ tw,
+                                                 double2 *__restrict__ acc,
+                                                 int64_t *__restrict__ counts) {
+    __shared__ double s_x[256], s_y[256], s_c1[256], s_c2[256], s_inv[256];
+    __shared__ int s_w1[256], s_w2[256];
+
+    const int r = blockIdx.y;
+    const int kb0 = blockIdx.x * 256;
+    const int kb1 = min(kb0 + 256, K1);
+    const int k = kb0 + threadIdx.x;
+    const bool kvalid = k < K1;
+    const int d0 = kvalid ? dist0(k, K1) : 0x3fffffff;
+    const int dpi = kvalid ? dist_pi(k, K1) : 0x3fffffff;
+    // block-wide minimum distances (for tile skipping)
+    const int bd0 = min(dist0(kb0, K1), dist0(kb1 - 1, K1));
+    const int half = K1 >> 1;
+    const int bdpi = (half >= kb0 && half < kb1) ? 0 : min(dist_pi(kb0, K1), dist_pi(kb1 - 1, K1));
+
+    const int64_t first = (int64_t)(((uint64_t)r + (uint64_t)n_sub - e0 % (uint64_t)n_sub) %
+                                    (uint64_t)n_sub);
+    const int64_t cnt_r = first < count ? (count - 1 - first) / n_sub + 1 : 0;
+
+    double2 t = kvalid ? tw[k] : make_double2(0.0, 0.0);
+    const double cm1 = t.x, sn = t.y;
+    double am_re = 0.0, am_im = 0.0, ap_re = 0.0, ap_im = 0.0;
+
+    for (int64_t base = 0; base < cnt_r; base += 256) {
+        const int64_t q = base + threadIdx.x;
+        int hit = 0;
+        if (q < cnt_r) {
+            const int64_t i = first + q * n_sub;
+            const double nn = n_in[i];
+            const double2 s = nS_in[i];
+            const Window w = win_in[i];
+            s_x[threadIdx.x] = s.x;
+            s_y[threadIdx.x] = s.y;
+            s_c1[threadIdx.x] = fmin(0.0, 2.0 * nn);
+            s_c2[threadIdx.x] = -2.0 * fmax(nn, 0.0);
+            s_inv[threadIdx.x] = 1.0 / (1.0 + exp(-2.0 * fabs(nn)));
+            s_w1[threadIdx.x] = w.w1;
+            s_w2[threadIdx.x] = w.w2;
+            hit = (bd0 <= w.w1) || (bdpi <= w.w2);
+        }
+        if (!__syncthreads_or(hit)) continue;
+        const int ntile = (cnt_r - base) < 256 ? (int)(cnt_r - base) : 256;
+        if (kvalid) {
+            for (int j = 0; j < ntile; ++j) {
+                const bool in1 = d0 <= s_w1[j];
+                const bool in2 = dpi <= s_w2[j];
+                if (!(in1 || in2)) continue;
+                const double x = s_x[j], y = s_y[j];
+                const double l1 = cm1 * x - sn * y;
+                const double ph = sn * x + cm1 * y;
+                double sp, cp;
+                sincos(ph, &sp, &cp);
+                double e1 = 0.0, e2 = 0.0;
+                if (in1) {
+                    const double c1 = s_c1[j];
+                    e1 = exp(l1 + c1);
+                    const double gp = (c1 == 0.0) ? e1 : exp(l1);
+                    ap_re += gp * cp;
+                    ap_im += gp * sp;
+                }
+                if (in2) e2 = exp(-l1 + s_c2[j]);
+                const double inv = s_inv[j];
+                am_re += (e1 + e2) * cp * inv;
+                am_im += (e1 - e2) * sp * inv;
+            }
+        }
+        __syncthreads();
+    }
+    if (kvalid) {
+        double2 *a0 = acc + (size_t)r * K1 + k;
+        double2 *a1 = acc + ((size_t)n_sub + r) * K1 + k;
+        const double2 o0 = *a0, o1 = *a1;
+        *a0 = make_double2(o0.x + am_re, o0.y + am_im);
+        *a1 = make_double2(o1.x + ap_re, o1.y + ap_im);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) counts[r] += cnt_r;
+}
+
+__global__ void k_tables(int K1, double2 *__restrict__ tw, double2 *__restrict__ wfft) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K1; k += gridDim.x * blockDim.x) {
+        const double f = (double)k / (double)K1;
+        double sh, ch, s2, c2;
+        sincospi(f, &sh, &ch);        // theta/2 = pi k / K1
+        sincospi(2.0 * f, &s2, &c2);  // theta = 2 pi k / K1
+        tw[k] = make_double2(-2.0 * sh * sh, s2);  // (cos theta - 1, sin theta)
+        wfft[k] = make_double2(c2, -s2);           // e^{-i theta}
+    }
+}
+
+}  // namespace
+
+int launch_finalize(gbs_net *net, int64_t count) {
+    if (count <= 0) return GBS_OK;
+    int blocks = (int)std::min<int64_t>((count + 255) / 256, (int64_t)net->sm_count * 8);
+    k_finalize<<<blocks, 256, 0, net->stream>>>(net->d_nS_part, net->mtiles, net->chunk, net->d_n,
+                                                 count, net->K1, net->d_nS, net->d_win);
+    GBS_LAUNCH_CHECK();
+    return GBS_OK;
+}
+
+int launch_gf(gbs_net *net, uint64_t e0, int64_t count) {
+    if (count <= 0) return GBS_OK;
+    dim3 grid((unsigned)((net->K1 + 255) / 256), (unsigned)net->n_sub);
+    k_gf_fp64<<<grid, 256, 0, net->stream>>>(net->d_n, net->d_nS, net->d_win, count, e0,
+                                               net->n_sub, net->K1, net->d_tw, net->d_acc,
+                                               net->d_counts);
+    GBS_LAUNCH_CHECK();
+    return GBS_OK;
+}
+
+int launch_tables(gbs_net *net) {
+    const int blocks = (net->K1 + 255) / 256;
+    k_tables<<<blocks, 256, 0, net->stream>>>(net->K1, net->d_tw, net->d_wfft);
+    GBS_LAUNCH_CHECK();
+    return GBS_OK;
+}
+
+}  // namespace gbs

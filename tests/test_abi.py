@@ -1,0 +1,59 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+function that include/gbs.h declares.  No compute call is made here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "gbs.h")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbs_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    import shutil
+    if not (shutil.which("nvcc") or os.path.exists("/usr/local/cuda/bin/nvcc")):
+        pytest.skip("nvcc not available")
+    from paper_2503_12749_gb300 import buildlib
+    return buildlib.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("gbs_make_network", "gbs_sample", "gbs_binned_counts", "gbs_free_network",
+                     "gbs_last_error", "gbs_debug_samples"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True)
+    exported = set(re.findall(r"\bT (gbs_[a-z0-9_]+)\b", out.stdout))
+    assert set(_declared()) <= exported
+
+
+def test_binding_mirrors_abi_names():
+    import paper_2503_12749_gb300 as g
+    for name in _declared():
+        assert hasattr(g, name), name
+
+
+def test_last_error_is_callable_without_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.gbs_last_error.restype = ctypes.c_char_p
+    assert isinstance(lib.gbs_last_error(), bytes)
+    # argument validation runs before any device call
+    lib.gbs_make_network.restype = ctypes.c_int
+    out = ctypes.c_void_p()
+    code = lib.gbs_make_network(0, 0, None, None, 0, None, ctypes.byref(out))
+    assert code == -1
