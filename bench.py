@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Throughput of the matrix-P total-count estimator on GB300.
+
+One step = one pass of the whole estimator over one batch of E synthetic
+trajectories of the named workload, on a network already resident on the
+device: sampler -> propagation GEMM + occupation epilogue -> per-trajectory
+finalize -> generating functions summed per sub-ensemble -> inverse DFT and
+statistics of P(m).  Metric: trajectories per second (whole job).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbs|reference]
+       [--workload m1000] [--precision bf16x3]
+Under torchrun (N > 1) every rank runs the same per-rank workload on its own
+GPU with disjoint trajectory ranges (weak scaling); the sub-ensemble sums are
+combined once after the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "matrix-P samples/sec and binned-P(m) wall time per N-mode network at |dP|/sigma<=1"
+UNIT = "samples/s"
+
+# DRAM bytes per launch of the GEMM kernel from an ncu capture (None until a
+# capture of the current kernel exists; see profiles/).
+GEMM_TRAFFIC_BYTES_PER_SAMPLE = None
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        top = max(sm)
+        loaded = [s for s in sm if s >= 0.5 * top] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def accuracy_summary(P, sigma, Pref, bulk=1e-7):
+    """|dP|/sigma statistics of a sampled P(m) against the exact distribution."""
+    import numpy as np
+    z = (P - Pref) / np.maximum(sigma, 1e-13)
+    sel = Pref > bulk
+    return {"bins": int(sel.sum()), "max_abs_z": float(np.max(np.abs(z[sel]))),
+            "chi2_per_bin": float(np.mean(z[sel] ** 2)),
+            "frac_within_1sigma": float(np.mean(np.abs(z[sel]) <= 1.0)),
+            "max_sigma": float(np.max(sigma)), "sum_P": float(np.sum(P)),
+            "reference": "exact uniform-loss distribution (determinant GF, aliased to K1)"}
+
+
+def run_oracle_sample(T, r, seed, e0, E, n_sub, K1, threads=0):
+    """The oracle's per-trajectory work on E trajectories (samples + GF sums)."""
+    import oracle
+    n, nS = oracle.samples(T, r, seed, e0, E, threads)
+    oracle.accumulate_gf(n, nS, e0, n_sub, K1, threads)
+
+
+def reference_arm(args, wl_def):
+    """The oracle timed on the host cores on bounded samples of the workload."""
+    import oracle
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    oracle.build()
+    net = wl_def.network()
+    cores = oracle.max_threads()
+    Es = args.ref_samples
+    for s in range(args.warmup):
+        run_oracle_sample(net.T, net.r, net.seed_s, s * Es, Es, wl_def.n_sub, wl_def.K1)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        run_oracle_sample(net.T, net.r, net.seed_s, (args.warmup + s) * Es, Es, wl_def.n_sub,
+                          wl_def.K1)
+    dt = time.perf_counter() - t0
+    value = Es * args.steps / dt
+    sample = (f"{Es} trajectories per step of {wl_def.name} (sampling, propagation and "
+              f"generating-function sums; the one-off inverse DFT is excluded)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl_def.name, "precision": "fp64 (CPU oracle)",
+                   "samples_per_step": Es},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def gbs_arm(args, wl_def):
+    import numpy as np
+    import torch
+
+    import paper_2503_12749_gb300 as gbs
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend="nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    gbs.build()
+    precision = args.precision or wl_def.precision
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+    netdef = wl_def.network()
+    E, n_sub, K1 = wl_def.E, wl_def.n_sub, wl_def.K1
+    if args.samples:
+        E = args.samples
+    net = gbs.gbs_make_network(netdef.T, netdef.r, precision, sptr)
+    out = torch.empty(4 * K1, dtype=torch.float64, device="cuda")
+    seed = netdef.seed_s
+    # rank r draws trajectories [r * R, (r + 1) * R) with R = (W + K) * E
+    base = rank * (args.warmup + args.steps) * E
+
+    def step(s):
+        gbs.gbs_sample(net, seed, base + s * E, E, n_sub, K1)
+        gbs.gbs_binned_counts_device(net, 0, out.data_ptr())
+
+    with torch.cuda.stream(stream):
+        for s in range(args.warmup):
+            step(s)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    gbs.gbs_profile_enable(net, True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev0.record(stream)
+    for s in range(args.steps):
+        step(args.warmup + s)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    prof = gbs.gbs_profile_read(net)
+    gbs.gbs_profile_enable(net, False)
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        # combine sub-ensemble sums of all ranks (the estimator's one exchange)
+        _, _, acc, cnt = gbs.gbs_get_accumulators(net)
+        ta = torch.from_numpy(acc.view(np.float64).copy()).cuda()
+        tc = torch.from_numpy(cnt.copy()).cuda()
+        dist.all_reduce(ta)
+        dist.all_reduce(tc)
+        gbs.gbs_set_accumulators(net, ta.cpu().numpy().view(np.complex128).reshape(acc.shape),
+                                 tc.cpu().numpy())
+    ms_step = ms_total / args.steps
+    value = world * E * args.steps / (ms_total / 1e3)
+
+    # accuracy of the run's P(m) (all warm-up and timed trajectories) vs exact
+    import oracle.exact as ex
+    P = gbs.gbs_binned_counts(net, 0, K1)
+    mu = ex.eigenvalues_uniform_loss(netdef.r, wl_def.t2)
+    Pex = ex.exact_distribution(mu, K1).real
+    acc_summary = accuracy_summary(P[0], P[1], Pex)
+
+    # roofline of the dominant kernel (the propagation GEMM)
+    peaks, peak_kind = _peaks()
+    gemm_ms, gemm_launches = prof["gemm"]
+    flops = 8.0 * netdef.M * netdef.N * E * args.steps
+    tc_path = precision != "fp64"
+    P_products = {"bf16x3": 3, "bf16x6": 6}.get(precision, 1)
+    if tc_path:
+        achieved = flops / (gemm_ms / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{peak_kind} bf16 sustained (kernel timed inside a long step)",
+                "algorithmic_flops_per_sample": 8 * netdef.M * netdef.N,
+                "mma_products": P_products, "mma_issued_frac": P_products * achieved / peak,
+                "kernel": "k_gemm_tc", "launches": gemm_launches,
+                "avg_launch_ms": gemm_ms / max(gemm_launches, 1)}
+        if GEMM_TRAFFIC_BYTES_PER_SAMPLE is not None:
+            roof["traffic"] = GEMM_TRAFFIC_BYTES_PER_SAMPLE * E * args.steps / max(gemm_launches, 1)
+    else:
+        achieved = flops / (gemm_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "kernel": "k_gemm_fp64",
+                "peak_source": "FP64 FMA pipe (see DESIGN.md)"}
+    phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+              for k, v in prof.items()}
+    launches = int(sum(v[1] for v in prof.values()))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16x3": "bf16x3 split (fp32 accumulate, f64 sums)",
+                  "bf16x6": "bf16x6 split (fp32 accumulate, f64 sums)"}.get(precision, "f64"),
+        "data": "synthetic",
+        "config": {"workload": wl_def.name, "precision": precision, "samples_per_step": E,
+                   "n_sub": n_sub, "K1": K1, "N": netdef.N, "M": netdef.M,
+                   "l2": "inputs larger than L2 (sample operand of a chunk > 129 MB, "
+                         "written and read every chunk)",
+                   "network": "Haar U (QR of seeded complex Gaussian, phase-fixed), "
+                              f"T = sqrt({wl_def.t2}) U",
+                   "binned_P_wall_ms": ms_step},
+        "roofline": roof,
+        "phases": phases,
+        "accuracy_vs_exact": acc_summary,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+    # end to end through the C ABI with host buffers: upload the network,
+    # sample, invert and read P(m) back, every step
+    if not args.no_e2e and rank == 0:
+        Tn = np.ascontiguousarray(netdef.T)
+        rn = np.ascontiguousarray(netdef.r)
+        h2d = Tn.nbytes + rn.nbytes
+        d2h = 4 * K1 * 8
+
+        def e2e_step(s):
+            n2 = gbs.gbs_make_network(Tn, rn, precision, sptr)
+            gbs.gbs_sample(n2, seed, s * E, E, n_sub, K1)
+            res = gbs.gbs_binned_counts(n2, 0, K1)
+            gbs.gbs_free_network(n2)
+            return res
+
+        e2e_step(0)
+        t0 = time.perf_counter()
+        ne = max(1, min(3, args.steps))
+        for s in range(ne):
+            e2e_step(1 + s)
+        dt = time.perf_counter() - t0
+        line["e2e"] = {"value": E * ne / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h,
+                       "what": "gbs_make_network (host T, r) + gbs_sample + gbs_binned_counts "
+                               "(host outputs) + gbs_free_network per step, wall clock"}
+
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        import oracle
+        oracle.build()
+        Es = args.cpu_samples
+        run_oracle_sample(netdef.T, netdef.r, seed, 0, 64, n_sub, K1)
+        t0 = time.perf_counter()
+        run_oracle_sample(netdef.T, netdef.r, seed, 0, Es, n_sub, K1)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {
+            "value": Es / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{Es} trajectories of {wl_def.name}: sampling, propagation and "
+                      f"generating-function sums ({dt:.1f} s); inverse DFT excluded"}
+
+    gbs.gbs_free_network(net)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    import workloads as wl
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
+    ap.add_argument("--workload", default="m1000", choices=sorted(wl.NAMED))
+    ap.add_argument("--precision", default=None, choices=["fp64", "bf16x3", "bf16x6"])
+    ap.add_argument("--samples", type=int, default=0, help="override trajectories per step")
+    ap.add_argument("--ref-samples", type=int, default=2048)
+    ap.add_argument("--cpu-samples", type=int, default=8192)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wl_def = wl.NAMED[args.workload]
+    if args.impl == "reference":
+        return reference_arm(args, wl_def)
+    return gbs_arm(args, wl_def)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

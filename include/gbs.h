@@ -154,6 +154,25 @@ int gbs_reset(gbs_net_t net);
 /* gbs_network_info -- N, M, precision and the trajectories per internal chunk. */
 int gbs_network_info(gbs_net_t net, int *N, int *M, int *precision, int64_t *chunk);
 
+/*
+ * Kernel-phase timing (instrumentation, not part of the method).  When
+ * enabled, every kernel launch of the network is bracketed by CUDA events
+ * recorded on the network's stream and attributed to a phase:
+ */
+#define GBS_PHASE_SAMPLE 0   /* phase-space input sampler */
+#define GBS_PHASE_GEMM 1     /* propagation GEMM + occupation epilogue */
+#define GBS_PHASE_FINALIZE 2 /* per-trajectory n_S sum and evaluation windows */
+#define GBS_PHASE_GF 3       /* generating functions summed per sub-ensemble */
+#define GBS_PHASE_INVERT 4   /* inverse DFT and statistics */
+#define GBS_NPHASES 5
+/* gbs_profile_enable -- start (enable != 0) or stop recording; starting
+ * discards earlier records. */
+int gbs_profile_enable(gbs_net_t net, int enable);
+/* gbs_profile_read -- synchronise, then return per phase the summed event
+ * time in milliseconds (ms[GBS_NPHASES]) and the number of kernel launches
+ * (launches[GBS_NPHASES]) since the last enable/read; clears the records. */
+int gbs_profile_read(gbs_net_t net, double *ms, int64_t *launches);
+
 /* gbs_free_network -- release all memory of the network (NULL is a no-op). */
 void gbs_free_network(gbs_net_t net);
 

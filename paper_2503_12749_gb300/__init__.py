@@ -80,6 +80,8 @@ def lib():
         L.gbs_set_accumulators.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, i64p]
         L.gbs_reset.argtypes = [vp]
         L.gbs_network_info.argtypes = [vp, ip, ip, ip, i64p]
+        L.gbs_profile_enable.argtypes = [vp, ctypes.c_int]
+        L.gbs_profile_read.argtypes = [vp, dp, i64p]
         L.gbs_free_network.argtypes = [vp]
         L.gbs_free_network.restype = None
         L.gbs_last_error.argtypes = []
@@ -87,7 +89,7 @@ def lib():
         for name in ("gbs_make_network", "gbs_sample", "gbs_binned_counts",
                      "gbs_binned_counts_device", "gbs_check_finite", "gbs_debug_samples",
                      "gbs_get_accumulators", "gbs_set_accumulators", "gbs_reset",
-                     "gbs_network_info"):
+                     "gbs_network_info", "gbs_profile_enable", "gbs_profile_read"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -208,6 +210,23 @@ def gbs_network_info(net: Network):
     _check(lib().gbs_network_info(net.handle, ctypes.byref(N), ctypes.byref(M), ctypes.byref(p),
                                   ctypes.byref(c)))
     return N.value, M.value, p.value, c.value
+
+
+GBS_NPHASES = 5
+PHASES = ("sample", "gemm", "finalize", "gf", "invert")
+
+
+def gbs_profile_enable(net: Network, enable: bool = True) -> None:
+    _check(lib().gbs_profile_enable(net.handle, 1 if enable else 0))
+
+
+def gbs_profile_read(net: Network):
+    """{phase: (milliseconds, launches)} since the last enable/read."""
+    ms = np.zeros(GBS_NPHASES)
+    ln = np.zeros(GBS_NPHASES, dtype=np.int64)
+    _check(lib().gbs_profile_read(net.handle, _dptr(ms),
+                                  ln.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return {PHASES[i]: (float(ms[i]), int(ln[i])) for i in range(GBS_NPHASES)}
 
 
 def gbs_free_network(net: Network) -> None:

@@ -1,0 +1,149 @@
+// Double-float arithmetic on the FP32 pipes: a value is the unevaluated sum
+// hi + lo of two floats (|lo| <= ulp(hi)/2), giving ~2^-46 relative
+// precision at FP32 issue rates.  Error-free transformations: Knuth's
+// two-sum, Dekker's fast two-sum, and the two-product via a fused
+// multiply-add (Dekker 1971; Knuth, TAOCP vol. 2, 4.2.2).  exp and sin/cos are
+// Cody-Waite range reductions (constants split into 12-bit pieces on the
+// host so that k * piece is exact) followed by Taylor series of the
+// reduced argument, evaluated by Horner's rule: the leading terms in
+// double-float, the terms below 2^-28 of the result in plain FP32.
+#pragma once
+
+#include <cstdint>
+
+namespace gbs {
+
+struct df {
+    float hi, lo;
+};
+
+// Range-reduction constants, computed on the host (see make_df_consts()).
+struct DfConsts {
+    float ln2_1, ln2_2, ln2_3;             // ln 2 = ln2_1 + ln2_2 + ln2_3
+    float pio2_1, pio2_2, pio2_3, pio2_4;  // pi / 2 = sum of the four
+    float inv_fact_hi[18], inv_fact_lo[18];  // 1 / k! as double-float, k = 0..17
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = a + b;
+    const float e = b - (s - a);
+    return {s, e};
+}
+
+__device__ __forceinline__ df df_two_prod(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    return {p, e};
+}
+
+__device__ __forceinline__ df df_add(df x, df y) {
+    const df s = df_two_sum(x.hi, y.hi);
+    const float e = s.lo + (x.lo + y.lo);
+    return df_fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ df df_add_f(df x, float y) {
+    const df s = df_two_sum(x.hi, y);
+    return df_fast_two_sum(s.hi, s.lo + x.lo);
+}
+
+__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
+
+__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
+
+__device__ __forceinline__ df df_mul(df x, df y) {
+    const df p = df_two_prod(x.hi, y.hi);
+    const float e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo));
+    return df_fast_two_sum(p.hi, e);
+}
+
+__device__ __forceinline__ df df_mul_f(df x, float y) {
+    const df p = df_two_prod(x.hi, y);
+    return df_fast_two_sum(p.hi, fmaf(x.lo, y, p.lo));
+}
+
+__device__ __forceinline__ df df_from_double(double v) {
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
+__device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
+
+__device__ __forceinline__ df df_fact(const DfConsts &K, int k) {
+    return {K.inv_fact_hi[k], K.inv_fact_lo[k]};
+}
+
+// e^a for a.hi in [-87, 88].  a = k ln2 + r, |r| <= ln2/2 + tiny;
+// e^r = sum_{j<=13} r^j/j! (remainder < 4e-18): j <= 8 in double-float,
+// j = 9..13 in FP32.  Then scaled by 2^k.
+__device__ __forceinline__ df df_exp(df a, const DfConsts &K) {
+    const float kf = rintf(a.hi * 1.44269504088896340736f);
+    df r = df_two_sum(fmaf(-kf, K.ln2_1, a.hi), a.lo);  // first product exact
+    r = df_add_f(r, -kf * K.ln2_2);                      // exact product
+    r = df_add_f(r, -kf * K.ln2_3);
+    const float x = r.hi;
+    // FP32 tail: sum_{j=9..13} x^{j-9}/j!
+    float t = K.inv_fact_hi[13];
+    t = fmaf(t, x, K.inv_fact_hi[12]);
+    t = fmaf(t, x, K.inv_fact_hi[11]);
+    t = fmaf(t, x, K.inv_fact_hi[10]);
+    t = fmaf(t, x, K.inv_fact_hi[9]);
+    df p = df_add_f(df_fact(K, 8), t * x);
+#pragma unroll
+    for (int j = 7; j >= 0; --j) p = df_add(df_fact(K, j), df_mul(p, r));
+    const int ki = (int)kf;
+    const float scale = __int_as_float((ki + 127) << 23);
+    return {p.hi * scale, p.lo * scale};
+}
+
+// sin and cos of phi for |phi.hi| < 6000 (quadrant count < 2^12, so the
+// products with the 12-bit pieces of pi/2 are exact).  phi = q pi/2 + s,
+// |s| <= pi/4; with x = s^2 (<= 0.62):
+//   sin s = s (1 - x/3! + x^2/5! - ... + x^8/17!),  remainder < 1e-19,
+//   cos s = 1 - x/2! + x^2/4! - ... + x^8/16!,      remainder < 3e-18,
+// the terms from x^5/11! (sin) and x^6/12! (cos) on in FP32.
+__device__ __forceinline__ void df_sincos(df phi, const DfConsts &K, df &s_out, df &c_out) {
+    const float qf = rintf(phi.hi * 0.636619772367581343076f);
+    df s = df_two_sum(fmaf(-qf, K.pio2_1, phi.hi), phi.lo);
+    s = df_add_f(s, -qf * K.pio2_2);
+    s = df_add_f(s, -qf * K.pio2_3);
+    s = df_add_f(s, -qf * K.pio2_4);
+    const df x = df_mul(s, s);
+    const float xf = x.hi;
+    // sine: FP32 tail 1/11! - x (1/13! - x (1/15! - x/17!))
+    float t = K.inv_fact_hi[17];
+    t = fmaf(-t, xf, K.inv_fact_hi[15]);
+    t = fmaf(-t, xf, K.inv_fact_hi[13]);
+    t = fmaf(-t, xf, K.inv_fact_hi[11]);
+    df ps = df_add_f(df_fact(K, 9), -t * xf);
+    ps = df_sub(df_fact(K, 7), df_mul(ps, x));
+    ps = df_sub(df_fact(K, 5), df_mul(ps, x));
+    ps = df_sub(df_fact(K, 3), df_mul(ps, x));
+    ps = df_sub(df_fact(K, 1), df_mul(ps, x));
+    const df sn = df_mul(ps, s);
+    // cosine: FP32 tail 1/12! - x (1/14! - x/16!)
+    float u = K.inv_fact_hi[16];
+    u = fmaf(-u, xf, K.inv_fact_hi[14]);
+    u = fmaf(-u, xf, K.inv_fact_hi[12]);
+    df pc = df_add_f(df_fact(K, 10), -u * xf);
+    pc = df_sub(df_fact(K, 8), df_mul(pc, x));
+    pc = df_sub(df_fact(K, 6), df_mul(pc, x));
+    pc = df_sub(df_fact(K, 4), df_mul(pc, x));
+    pc = df_sub(df_fact(K, 2), df_mul(pc, x));
+    pc = df_sub(df_fact(K, 0), df_mul(pc, x));
+    switch (((int)qf) & 3) {
+        case 0: s_out = sn; c_out = pc; break;
+        case 1: s_out = pc; c_out = df_neg(sn); break;
+        case 2: s_out = df_neg(sn); c_out = df_neg(pc); break;
+        default: s_out = df_neg(pc); c_out = sn; break;
+    }
+}
+
+}  // namespace gbs

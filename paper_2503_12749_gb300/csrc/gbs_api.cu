@@ -38,7 +38,38 @@ bool device_has_tcgen05(int device) {
     return major == 10 && minor == 3;  // this library is built for sm_103a only
 }
 
+void prof_mark(gbs_net *net, int phase, int launches_if_stop, bool start) {
+    Profiler &pr = net->prof;
+    if (!pr.on) return;
+    cudaEvent_t ev;
+    if (!pr.pool.empty()) {
+        ev = pr.pool.back();
+        pr.pool.pop_back();
+    } else if (cudaEventCreate(&ev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaEventRecord(ev, net->stream);
+    pr.marks[phase].push_back(ev);
+    if (!start) pr.launches[phase] += launches_if_stop;
+}
+
 namespace {
+
+void prof_clear(gbs_net *net) {
+    Profiler &pr = net->prof;
+    for (int ph = 0; ph < GBS_NPHASES; ++ph) {
+        for (cudaEvent_t e : pr.marks[ph]) pr.pool.push_back(e);
+        pr.marks[ph].clear();
+        pr.launches[ph] = 0;
+    }
+}
+
+void prof_destroy(gbs_net *net) {
+    prof_clear(net);
+    for (cudaEvent_t e : net->prof.pool) cudaEventDestroy(e);
+    net->prof.pool.clear();
+}
 
 template <typename T>
 int dev_alloc(T **p, size_t count, const char *what) {
@@ -92,6 +123,7 @@ void release_estimator(gbs_net *net) {
 
 void release_all(gbs_net *net) {
     release_estimator(net);
+    prof_destroy(net);
     if (net->tc) tc_plan_destroy(net);
     dev_free(net->d_sq64);
     dev_free(net->d_sq32);
@@ -146,14 +178,19 @@ int fix_estimator(gbs_net *net, int n_sub, int K1) {
 // Sampler + propagation + finalize for one chunk of `count` trajectories.
 int run_chunk_front(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) {
     int rc;
-    if (net->precision == GBS_FP64) {
-        if ((rc = launch_sample_fp64(net, seed, e0, count))) return rc;
-        if ((rc = launch_gemm_fp64(net, count))) return rc;
-    } else {
-        if ((rc = launch_sample_bf16(net, seed, e0, count))) return rc;
-        if ((rc = launch_gemm_tc(net, count))) return rc;
-    }
-    return launch_finalize(net, count);
+    const bool fp64 = net->precision == GBS_FP64;
+    prof_mark(net, GBS_PHASE_SAMPLE, 0, true);
+    rc = fp64 ? launch_sample_fp64(net, seed, e0, count) : launch_sample_bf16(net, seed, e0, count);
+    if (rc) return rc;
+    prof_mark(net, GBS_PHASE_SAMPLE, 1, false);
+    prof_mark(net, GBS_PHASE_GEMM, 0, true);
+    rc = fp64 ? launch_gemm_fp64(net, count) : launch_gemm_tc(net, count);
+    if (rc) return rc;
+    prof_mark(net, GBS_PHASE_GEMM, 1, false);
+    prof_mark(net, GBS_PHASE_FINALIZE, 0, true);
+    if ((rc = launch_finalize(net, count))) return rc;
+    prof_mark(net, GBS_PHASE_FINALIZE, 1, false);
+    return GBS_OK;
 }
 
 int validate_net(gbs_net *net) {
@@ -310,7 +347,9 @@ int gbs_sample(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, i
         const int64_t c = std::min<int64_t>(net->chunk, E - done);
         const uint64_t e0 = first_sample + (uint64_t)done;
         if ((rc = run_chunk_front(net, seed, e0, c))) return rc;
+        prof_mark(net, GBS_PHASE_GF, 0, true);
         if ((rc = launch_gf(net, e0, c))) return rc;
+        prof_mark(net, GBS_PHASE_GF, 1, false);
     }
     // host mirror of the sub-ensemble sizes
     const uint64_t ns = (uint64_t)net->n_sub;
@@ -329,7 +368,12 @@ int gbs_binned_counts_device(gbs_net_t net, int64_t m_offset, double *out_dev) {
     for (int q = 0; q < net->n_sub; ++q)
         if (net->counts[q] <= 0)
             return set_error(GBS_EINVAL, "sub-ensemble %d has no trajectories", q);
-    return launch_invert(net, m_offset, out_dev);
+    int log2k = 0;
+    while ((1 << log2k) < net->K1) ++log2k;
+    prof_mark(net, GBS_PHASE_INVERT, 0, true);
+    if ((rc = launch_invert(net, m_offset, out_dev))) return rc;
+    prof_mark(net, GBS_PHASE_INVERT, 2 + log2k, false);
+    return GBS_OK;
 }
 
 int gbs_check_finite(gbs_net_t net, int64_t *count) {
@@ -436,6 +480,34 @@ int gbs_network_info(gbs_net_t net, int *N, int *M, int *precision, int64_t *chu
     if (M) *M = net->M;
     if (precision) *precision = net->precision;
     if (chunk) *chunk = net->chunk;
+    return GBS_OK;
+}
+
+int gbs_profile_enable(gbs_net_t net, int enable) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    GBS_CUDA_TRY(cudaStreamSynchronize(net->stream));
+    prof_clear(net);
+    net->prof.on = enable != 0;
+    return GBS_OK;
+}
+
+int gbs_profile_read(gbs_net_t net, double *ms, int64_t *launches) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    GBS_CUDA_TRY(cudaStreamSynchronize(net->stream));
+    for (int ph = 0; ph < GBS_NPHASES; ++ph) {
+        double tot = 0.0;
+        const std::vector<cudaEvent_t> &m = net->prof.marks[ph];
+        for (size_t q = 0; q + 1 < m.size(); q += 2) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, m[q], m[q + 1]) == cudaSuccess) tot += t;
+            else cudaGetLastError();
+        }
+        if (ms) ms[ph] = tot;
+        if (launches) launches[ph] = net->prof.launches[ph];
+    }
+    prof_clear(net);
     return GBS_OK;
 }
 

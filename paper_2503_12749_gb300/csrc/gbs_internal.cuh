@@ -59,6 +59,14 @@ struct Window {
 // ---------------------------------------------------------------------------
 struct TcPlan;  // tcgen05 GEMM plan (tensor maps, tiling), defined in k_gemm_tc.cu
 
+// CUDA-event timing of kernel phases (gbs_profile_*).
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<cudaEvent_t> marks[GBS_NPHASES];  // start, stop, start, stop, ...
+    int64_t launches[GBS_NPHASES] = {0, 0, 0, 0, 0};
+};
+
 }  // namespace gbs
 
 struct gbs_net {
@@ -100,6 +108,8 @@ struct gbs_net {
     double2 *d_wfft = nullptr;      // [K1]: e^{-2 pi i k / K1}
     double *d_out = nullptr;        // [4][K1]
     unsigned long long *d_flags = nullptr;  // [4]: non-finite count, timeout flag, ...
+
+    gbs::Profiler prof;
 };
 
 namespace gbs {
@@ -131,6 +141,9 @@ int launch_invert(gbs_net *net, int64_t m_offset, double *out_dev);
 
 // Non-finite count of the accumulators into d_flags[0].
 int launch_count_nonfinite(gbs_net *net);
+
+// Phase timing: bracket the launches of one phase (no-ops when disabled).
+void prof_mark(gbs_net *net, int phase, int launches_if_stop, bool start);
 
 // Device properties helper.
 bool device_has_tcgen05(int device);

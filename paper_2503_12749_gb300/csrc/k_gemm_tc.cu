@@ -7,24 +7,34 @@
 // mode, 2M x N) and B = per 128-trajectory tile [alpha rows; beta rows]
 // (256 x N), both K-major BF16.  FP32-level accuracy comes from splitting
 // A = A0 + A1 + A2 and B = B0 + B1 + B2 into BF16 planes and summing the
-// products A_i B_j with i + j <= 1 (3 products) or i + j <= 2 (6 products),
-// all into one FP32 accumulator (the split-precision pattern, e.g. Henry,
-// Tang, Heinecke, "Leveraging the bfloat16 artificial intelligence datatype
-// for higher-precision computations", ARITH 2019).
+// products A_i B_j with i + j <= 1 (3 products) or i + j <= 2 (6 products)
+// (the split-precision pattern, e.g. Henry, Tang, Heinecke, "Leveraging the
+// bfloat16 artificial intelligence datatype for higher-precision
+// computations", ARITH 2019).
 //
-// Kernel structure (one CTA per SM, persistent over tiles):
-//   warp 0      TMA producer: per (product, 64-wide K block) one A box
+// Accumulator promotion: the tensor core's FP32 accumulation truncates each
+// MMA's result, a bias of ~1 ulp of the running sum per instruction that
+// grows linearly with the number of MMAs chained into one accumulator
+// (measured: ~2^-24 of the amplitude scale per instruction).  So each
+// 64-wide K block's products (4 x products MMAs) go into a fresh TMEM
+// accumulator, and the epilogue warps add every block's result into FP32
+// registers with round-to-nearest (the promotion interval idea of, e.g.,
+// the DeepSeek-V3 report's FP8 GEMMs).  Two TMEM buffers alternate per K
+// block, so the MMAs of block s+1 overlap the promotion of block s.
+//
+// Kernel structure (one CTA per SM, persistent over tiles, 320 threads):
+//   warp 0      TMA producer: per (64-wide K block, product) one A box
 //               (64 x 128) and one B box (64 x 256), 128-byte swizzle, into a
 //               4-stage shared-memory ring;
 //   warp 1      allocates 512 TMEM columns; one thread issues
-//               tcgen05.mma M=128 N=256 K=16 into one of two 256-column
-//               accumulators and commits stage releases / tile completion;
-//   warps 2..5  epilogue: tcgen05.ld of the accumulator (TMEM lane = A row,
-//               columns 0..127 = alpha' parts, 128..255 = beta' parts of the
-//               tile's 128 trajectories), occupations, butterfly
-//               transpose-reduction over the 32 lanes of each warp, then the
-//               4 warps in a fixed order -> one n_S partial per (mode tile,
-//               trajectory).  alpha', beta' never leave the SM.
+//               tcgen05.mma M=128 N=256 K=16 into the K block's buffer;
+//   warps 2..9  epilogue: warp w reads TMEM lanes 32 (w mod 4).. (its A rows)
+//               and half (w - 2) / 4 of the tile's trajectories: running
+//               sums of 64 alpha' and 64 beta' columns per thread.  After the
+//               last K block: occupations, butterfly transpose-reduction over
+//               the 32 lanes, then the 4 lane quarters in a fixed order -> one
+//               n_S partial per (mode tile, trajectory).  alpha', beta' never
+//               leave the SM.
 // Every mbarrier wait is bounded; on a timeout the kernel raises an error
 // flag, drains its own TMA loads and MMAs, frees TMEM and returns.
 #include "gbs_internal.cuh"
@@ -53,10 +63,12 @@ constexpr int kABytes = 128 * 128;  // 128 rows x 64 bf16
 constexpr int kBBytes = 256 * 128;  // 256 rows x 64 bf16
 constexpr int kStageBytes = kABytes + kBBytes;
 constexpr int kBarBytes = 1024;
-constexpr int kRedBytes = 4 * 128 * 8;  // float2 [4][128]
+constexpr int kRedBytes = 4 * 128 * 2 * 4;  // float [4 quarters][128 trajectories][re, im]
 constexpr int kSmemBytes = 1024 + kStages * kStageBytes + kBarBytes + kRedBytes;
 constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(128, 256);
-constexpr int kEpiThreads = 128;
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreads = 64 + kEpiThreads;
 
 struct TcParams {
     int KB;  // 64-wide K blocks
@@ -75,7 +87,46 @@ __device__ __forceinline__ void named_bar_sync(int id, int threads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
-__global__ void __launch_bounds__(192, 1)
+// Butterfly transpose-reduction of 32 values per lane over the warp: on
+// return v[0] of lane l holds the sum over all lanes of input value l.
+__device__ __forceinline__ void warp_transpose_reduce32(float (&v)[32], int lane) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const bool up = (lane & 16) != 0;
+        const float send = up ? v[i] : v[i + 16];
+        const float keep = up ? v[i + 16] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool up = (lane & 8) != 0;
+        const float send = up ? v[i] : v[i + 8];
+        const float keep = up ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = (lane & 4) != 0;
+        const float send = up ? v[i] : v[i + 4];
+        const float keep = up ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = (lane & 2) != 0;
+        const float send = up ? v[i] : v[i + 2];
+        const float keep = up ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    {
+        const bool up = (lane & 1) != 0;
+        const float send = up ? v[0] : v[1];
+        const float keep = up ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
               const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
               const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2,
@@ -92,8 +143,7 @@ __global__ void __launch_bounds__(192, 1)
     uint64_t *tempty = bars + 2 * kStages + 2;
     uint64_t *drain = bars + 2 * kStages + 4;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 5);
-    int *s_ok = reinterpret_cast<int *>(bars + 2 * kStages + 6);
-    float2 *red = reinterpret_cast<float2 *>(smem + kStages * kStageBytes + kBarBytes);
+    float *red = reinterpret_cast<float *>(smem + kStages * kStageBytes + kBarBytes);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -128,7 +178,6 @@ __global__ void __launch_bounds__(192, 1)
     const uint32_t tmem_base = *tmem_slot;
 
     const int ntiles = p.mtiles * p.stiles;
-    const int iters = p.P * p.KB;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -140,24 +189,24 @@ __global__ void __launch_bounds__(192, 1)
             for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
                 const int mt = tile % p.mtiles;
                 const int st = tile / p.mtiles;
-                for (int it = 0; it < iters; ++it) {
-                    const int pr = it / p.KB;
-                    const int kb = it - pr * p.KB;
-                    if (!ptx::mbar_wait(ptx::smem_u32(&empty[stage]), phase ^ 1u, err)) {
-                        ok = false;
-                        break;
-                    }
-                    const uint32_t fb = ptx::smem_u32(&full[stage]);
-                    ptx::mbar_arrive_expect_tx(fb, kStageBytes);
-                    ptx::tma_load_2d(ptx::smem_u32(sA + stage * kABytes), mapsA[p.ia[pr]], fb,
-                                     kb * 64, mt * 128);
-                    ptx::tma_load_2d(ptx::smem_u32(sB + stage * kBBytes), mapsB[p.ib[pr]], fb,
-                                     kb * 64, st * 256);
-                    used |= 1u << stage;
-                    last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
-                    if (++stage == kStages) {
-                        stage = 0;
-                        phase ^= 1u;
+                for (int kb = 0; ok && kb < p.KB; ++kb) {
+                    for (int pr = 0; pr < p.P; ++pr) {
+                        if (!ptx::mbar_wait(ptx::smem_u32(&empty[stage]), phase ^ 1u, err)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t fb = ptx::smem_u32(&full[stage]);
+                        ptx::mbar_arrive_expect_tx(fb, kStageBytes);
+                        ptx::tma_load_2d(ptx::smem_u32(sA + stage * kABytes), mapsA[p.ia[pr]], fb,
+                                         kb * 64, mt * 128);
+                        ptx::tma_load_2d(ptx::smem_u32(sB + stage * kBBytes), mapsB[p.ib[pr]], fb,
+                                         kb * 64, st * 256);
+                        used |= 1u << stage;
+                        last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
+                        if (++stage == kStages) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
                     }
                 }
             }
@@ -172,34 +221,38 @@ __global__ void __launch_bounds__(192, 1)
             // ---------------------------------------------------- MMA issuer
             int stage = 0;
             uint32_t phase = 0;
-            int lt = 0;
+            uint32_t seg = 0;  // K blocks issued so far (selects the TMEM buffer)
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++lt) {
-                const int b = lt & 1;
-                const uint32_t tph = (uint32_t)(lt >> 1) & 1u;
-                if (!ptx::mbar_wait(ptx::smem_u32(&tempty[b]), tph ^ 1u, err)) break;
-                ptx::tc_fence_after();
-                const uint32_t d = tmem_base + (uint32_t)(b * 256);
-                for (int it = 0; it < iters; ++it) {
-                    if (!ptx::mbar_wait(ptx::smem_u32(&full[stage]), phase, err)) {
+            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+                for (int kb = 0; ok && kb < p.KB; ++kb, ++seg) {
+                    const uint32_t b = seg & 1u;
+                    if (!ptx::mbar_wait(ptx::smem_u32(&tempty[b]), ((seg >> 1) & 1u) ^ 1u, err)) {
                         ok = false;
                         break;
                     }
                     ptx::tc_fence_after();
-                    const uint32_t a0 = ptx::smem_u32(sA + stage * kABytes);
-                    const uint32_t b0 = ptx::smem_u32(sB + stage * kBBytes);
+                    const uint32_t d = tmem_base + b * 256u;
+                    for (int pr = 0; pr < p.P; ++pr) {
+                        if (!ptx::mbar_wait(ptx::smem_u32(&full[stage]), phase, err)) {
+                            ok = false;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                        const uint32_t a0 = ptx::smem_u32(sA + stage * kABytes);
+                        const uint32_t b0 = ptx::smem_u32(sB + stage * kBBytes);
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        ptx::mma_bf16(d, ptx::desc_k_sw128(a0 + kk * 32),
-                                      ptx::desc_k_sw128(b0 + kk * 32), kIdesc,
-                                      (it | kk) != 0 ? 1u : 0u);
-                    ptx::mma_commit(ptx::smem_u32(&empty[stage]));
-                    if (++stage == kStages) {
-                        stage = 0;
-                        phase ^= 1u;
+                        for (int kk = 0; kk < 4; ++kk)
+                            ptx::mma_bf16(d, ptx::desc_k_sw128(a0 + kk * 32),
+                                          ptx::desc_k_sw128(b0 + kk * 32), kIdesc,
+                                          (pr | kk) != 0 ? 1u : 0u);
+                        ptx::mma_commit(ptx::smem_u32(&empty[stage]));
+                        if (++stage == kStages) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
                     }
+                    if (ok) ptx::mma_commit(ptx::smem_u32(&tfull[b]));
                 }
-                if (ok) ptx::mma_commit(ptx::smem_u32(&tfull[b]));
             }
             // drain: all MMAs issued by this thread have completed
             ptx::mma_commit(ptx::smem_u32(drain));
@@ -207,88 +260,76 @@ __global__ void __launch_bounds__(192, 1)
         }
     } else {
         // -------------------------------------------------------- epilogue
-        const int quarter = warp & 3;  // TMEM lanes this warp may access
-        const int row = quarter * 32 + lane;
+        const int quarter = warp & 3;        // TMEM lanes this warp may access
+        const int half = (warp - 2) >> 2;    // which 64 trajectories of the tile
+        const int row = quarter * 32 + lane; // A row of the tile = TMEM lane
         const bool im_row = (row & 1) != 0;  // odd A rows hold Im T_i.
-        const int et = threadIdx.x - 64;     // 0..127
-        int lt = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-            const int b = lt & 1;
-            const uint32_t tph = (uint32_t)(lt >> 1) & 1u;
-            if (et == 0) *s_ok = ptx::mbar_wait(ptx::smem_u32(&tfull[b]), tph, err) ? 1 : 0;
-            named_bar_sync(1, kEpiThreads);
-            if (!*s_ok) break;
-            ptx::tc_fence_after();
+        const int et = threadIdx.x - 64;     // 0..255
+        const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        uint32_t seg = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             const int mt = tile % p.mtiles;
             const int st = tile / p.mtiles;
-            const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
-#pragma unroll 1
-            for (int g = 0; g < 4; ++g) {
-                float va[32], vb[32];
-                ptx::tmem_ld32(tbase + (uint32_t)(g * 32), va);
-                ptx::tmem_ld32(tbase + (uint32_t)(128 + g * 32), vb);
-                ptx::tmem_ld_wait();
-                // occupations of this row: real part a*b (own row), imaginary
-                // part from the partner row (Re <-> Im of the same mode)
-                float v[64];
+            float ra[64], rb[64];  // running alpha', beta' parts of this row
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const float pb = __shfl_xor_sync(0xffffffffu, vb[q], 1);
-                    v[2 * q] = va[q] * vb[q];
-                    v[2 * q + 1] = im_row ? va[q] * pb : -va[q] * pb;
-                }
-                // butterfly transpose-reduction: lane l ends with (re, im) of trajectory g*32+l
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const bool up = (lane & 16) != 0;
-                    const float send = up ? v[i] : v[i + 32];
-                    const float keep = up ? v[i + 32] : v[i];
-                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-                }
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const bool up = (lane & 8) != 0;
-                    const float send = up ? v[i] : v[i + 16];
-                    const float keep = up ? v[i + 16] : v[i];
-                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const bool up = (lane & 4) != 0;
-                    const float send = up ? v[i] : v[i + 8];
-                    const float keep = up ? v[i + 8] : v[i];
-                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const bool up = (lane & 2) != 0;
-                    const float send = up ? v[i] : v[i + 4];
-                    const float keep = up ? v[i + 4] : v[i];
-                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-                }
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const bool up = (lane & 1) != 0;
-                    const float send = up ? v[i] : v[i + 2];
-                    const float keep = up ? v[i + 2] : v[i];
-                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
-                }
-                red[quarter * 128 + g * 32 + lane] = make_float2(v[0], v[1]);
+            for (int i = 0; i < 64; ++i) {
+                ra[i] = 0.0f;
+                rb[i] = 0.0f;
             }
-            // accumulator buffer b may be overwritten by the next tile's MMAs
-            ptx::tc_fence_before();
-            ptx::mbar_arrive(ptx::smem_u32(&tempty[b]));
+            for (int kb = 0; kb < p.KB; ++kb, ++seg) {
+                const uint32_t b = seg & 1u;
+                // on a timeout every epilogue thread keeps going (without
+                // waiting) so that all of them reach the same barriers
+                ptx::mbar_wait(ptx::smem_u32(&tfull[b]), (seg >> 1) & 1u, err);
+                ptx::tc_fence_after();
+                const uint32_t tb = lane_base + b * 256u + (uint32_t)(half * 64);
+                float t[32];
+                ptx::tmem_ld32(tb, t);
+                ptx::tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 32; ++i) ra[i] += t[i];
+                ptx::tmem_ld32(tb + 32u, t);
+                ptx::tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 32; ++i) ra[32 + i] += t[i];
+                ptx::tmem_ld32(tb + 128u, t);
+                ptx::tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 32; ++i) rb[i] += t[i];
+                ptx::tmem_ld32(tb + 160u, t);
+                ptx::tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 32; ++i) rb[32 + i] += t[i];
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(ptx::smem_u32(&tempty[b]));
+            }
+            // occupations of this row for the thread's 64 trajectories, in
+            // groups of 16: real part a*b from the own row, imaginary part with
+            // the partner row (Re <-> Im of the same mode, lane ^ 1)
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                float v[32];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const float a = ra[g * 16 + q];
+                    const float bb = rb[g * 16 + q];
+                    const float pb = __shfl_xor_sync(0xffffffffu, bb, 1);
+                    v[2 * q] = a * bb;
+                    v[2 * q + 1] = im_row ? a * pb : -a * pb;
+                }
+                warp_transpose_reduce32(v, lane);
+                const int traj = half * 64 + g * 16 + (lane >> 1);
+                red[(quarter * 128 + traj) * 2 + (lane & 1)] = v[0];
+            }
             named_bar_sync(1, kEpiThreads);
-            {
-                const int q = et;
+            if (et < 128) {
                 double re = 0.0, im = 0.0;
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
-                    const float2 x = red[w * 128 + q];
-                    re += (double)x.x;
-                    im += (double)x.y;
+                    re += (double)red[(w * 128 + et) * 2];
+                    im += (double)red[(w * 128 + et) * 2 + 1];
                 }
-                const int64_t s = (int64_t)st * 128 + q;
+                const int64_t s = (int64_t)st * 128 + et;
                 if (s < p.count) p.nS_part[(size_t)mt * p.ld_part + s] = make_double2(re, im);
             }
             named_bar_sync(1, kEpiThreads);
@@ -352,13 +393,16 @@ int tc_plan_create(gbs_net *net) {
                             (uint64_t)net->ldK * 2, 64, 256)))
             return rc;
     }
-    // products A_i B_j: i + j <= 1, then (6 products) i + j == 2
-    const int ia6[6] = {0, 0, 1, 1, 0, 2};
-    const int ib6[6] = {0, 1, 0, 1, 2, 0};
+    // products A_i B_j with i + j <= 1 (3) or <= 2 (6), issued smallest
+    // first: the correction products accumulate while the accumulator is
+    // small, and only the 4 MMAs of the dominant A0 B0 product truncate at
+    // the full magnitude of the K block's sum
+    const int ia3[3] = {0, 1, 0}, ib3[3] = {1, 0, 0};
+    const int ia6[6] = {1, 0, 2, 0, 1, 0}, ib6[6] = {1, 2, 0, 1, 0, 0};
     plan->P = (net->precision == GBS_BF16X3) ? 3 : 6;
     for (int q = 0; q < plan->P; ++q) {
-        plan->ia[q] = ia6[q];
-        plan->ib[q] = ib6[q];
+        plan->ia[q] = plan->P == 3 ? ia3[q] : ia6[q];
+        plan->ib[q] = plan->P == 3 ? ib3[q] : ib6[q];
     }
     return GBS_OK;
 }
@@ -392,7 +436,7 @@ int launch_gemm_tc(gbs_net *net, int64_t count) {
     p.err = net->d_flags + 1;
     const int64_t ntiles = (int64_t)p.mtiles * p.stiles;
     const int grid = (int)std::min<int64_t>(ntiles, net->sm_count);
-    k_gemm_tc<<<grid, 192, kSmemBytes, net->stream>>>(plan->mapA[0], plan->mapA[1], plan->mapA[2],
+    k_gemm_tc<<<grid, kThreads, kSmemBytes, net->stream>>>(plan->mapA[0], plan->mapA[1], plan->mapA[2],
                                                       plan->mapB[0], plan->mapB[1], plan->mapB[2],
                                                       p);
     GBS_LAUNCH_CHECK();

@@ -22,8 +22,10 @@
 // sum is formed in a fixed order (bitwise reproducible for a fixed chunking).
 // Trajectory e belongs to sub-ensemble e mod n_sub.
 #include "gbs_internal.cuh"
+#include "dfloat.cuh"
 
 #include <algorithm>
+#include <cmath>
 
 namespace gbs {
 namespace {
@@ -177,6 +179,165 @@ __global__ void __launch_bounds__(256) k_gf_fp64(const double *__restrict__ n_in
     if (blockIdx.x == 0 && threadIdx.x == 0) counts[r] += cnt_r;
 }
 
+// Double-float evaluation (BF16 split paths).  Each generating-function
+// term enters the sub-ensemble sums, so its rounding error is an absolute
+// error of P(m) at every m; the far-tail bins have sampling errors of
+// 1e-10 and below, so the terms need FP64-class accuracy.  GB300's FP64 rate
+// is low, so the same formulas are evaluated in double-float arithmetic on
+// the FP32 pipes (dfloat.cuh, ~2^-46 relative): l1, phi, e^{l1 + c1},
+// e^{-l1 + c2}, e^{l1}, sin phi, cos phi.  Arguments outside the
+// double-float ranges (|phi| >= 6000, exponents >= 80: only the +P heavy
+// tail) are evaluated in FP64 and added to the FP64 sums directly.  Per thread, double-float partial sums over 64
+// trajectories are added to FP64 accumulators.
+__device__ __forceinline__ df df_exp_small(df a, const DfConsts &K) {
+    return a.hi < -87.0f ? df{0.0f, 0.0f} : df_exp(a, K);  // below 1e-37: nothing
+}
+
+__global__ void __launch_bounds__(256) k_gf_df(const double *__restrict__ n_in,
+                                               const double2 *__restrict__ nS_in,
+                                               const Window *__restrict__ win_in,
+                                               int64_t count, uint64_t e0, int n_sub, int K1,
+                                               const double2 *__restrict__ tw, const DfConsts K,
+                                               double2 *__restrict__ acc,
+                                               int64_t *__restrict__ counts) {
+    constexpr int TILE = 64;
+    __shared__ df s_x[TILE], s_y[TILE], s_c1[TILE], s_c2[TILE], s_inv[TILE];
+    __shared__ double s_xd[TILE], s_yd[TILE], s_c1d[TILE], s_c2d[TILE];
+    __shared__ int s_w1[TILE], s_w2[TILE];
+
+    const int r = blockIdx.y;
+    const int kb0 = blockIdx.x * 256;
+    const int kb1 = min(kb0 + 256, K1);
+    const int k = kb0 + threadIdx.x;
+    const bool kvalid = k < K1;
+    const int d0 = kvalid ? dist0(k, K1) : 0x3fffffff;
+    const int dpi = kvalid ? dist_pi(k, K1) : 0x3fffffff;
+    const int bd0 = min(dist0(kb0, K1), dist0(kb1 - 1, K1));
+    const int half = K1 >> 1;
+    const int bdpi = (half >= kb0 && half < kb1) ? 0 : min(dist_pi(kb0, K1), dist_pi(kb1 - 1, K1));
+
+    const int64_t first = (int64_t)(((uint64_t)r + (uint64_t)n_sub - e0 % (uint64_t)n_sub) %
+                                    (uint64_t)n_sub);
+    const int64_t cnt_r = first < count ? (count - 1 - first) / n_sub + 1 : 0;
+
+    const double2 t = kvalid ? tw[k] : make_double2(0.0, 0.0);
+    const double cm1d = t.x, snd = t.y;
+    const df cm1 = df_from_double(t.x), sn = df_from_double(t.y);
+    double am_re = 0.0, am_im = 0.0, ap_re = 0.0, ap_im = 0.0;
+
+    for (int64_t base = 0; base < cnt_r; base += TILE) {
+        const int64_t q = base + threadIdx.x;
+        int hit = 0;
+        if (threadIdx.x < TILE && q < cnt_r) {
+            const int64_t i = first + q * n_sub;
+            const double nn = n_in[i];
+            const double2 sv = nS_in[i];
+            const Window w = win_in[i];
+            const double c1 = fmin(0.0, 2.0 * nn), c2 = -2.0 * fmax(nn, 0.0);
+            s_x[threadIdx.x] = df_from_double(sv.x);
+            s_y[threadIdx.x] = df_from_double(sv.y);
+            s_c1[threadIdx.x] = df_from_double(c1);
+            s_c2[threadIdx.x] = df_from_double(c2);
+            s_inv[threadIdx.x] = df_from_double(1.0 / (1.0 + exp(-2.0 * fabs(nn))));
+            s_xd[threadIdx.x] = sv.x;
+            s_yd[threadIdx.x] = sv.y;
+            s_c1d[threadIdx.x] = c1;
+            s_c2d[threadIdx.x] = c2;
+            s_w1[threadIdx.x] = w.w1;
+            s_w2[threadIdx.x] = w.w2;
+            hit = (bd0 <= w.w1) || (bdpi <= w.w2);
+        }
+        if (!__syncthreads_or(hit)) continue;
+        const int ntile = (cnt_r - base) < TILE ? (int)(cnt_r - base) : TILE;
+        if (kvalid) {
+            df pm_re = {0.0f, 0.0f}, pm_im = {0.0f, 0.0f}, pp_re = {0.0f, 0.0f},
+               pp_im = {0.0f, 0.0f};
+            for (int j = 0; j < ntile; ++j) {
+                const bool in1 = d0 <= s_w1[j];
+                const bool in2 = dpi <= s_w2[j];
+                if (!(in1 || in2)) continue;
+                const df x = s_x[j], y = s_y[j];
+                const df l1 = df_sub(df_mul(cm1, x), df_mul(sn, y));     // (cos-1) x - sin y
+                const df ph = df_add(df_mul(sn, x), df_mul(cm1, y));     // sin x + (cos-1) y
+                const df c1 = s_c1[j];
+                const df a1 = df_add(l1, c1);
+                const df a2 = df_add(df_neg(l1), s_c2[j]);
+                const bool big = fabsf(ph.hi) >= 6000.0f ||
+                                 (in1 && (a1.hi >= 80.0f || l1.hi >= 80.0f)) ||
+                                 (in2 && a2.hi >= 80.0f);
+                if (big) {
+                    // outside the double-float ranges (+P heavy tail, huge
+                    // phases): this pair in FP64, straight into the FP64 sums
+                    const double xd = s_xd[j], yd = s_yd[j];
+                    const double l1d = cm1d * xd - snd * yd;
+                    double sd, cd;
+                    sincos(snd * xd + cm1d * yd, &sd, &cd);
+                    double e1d = 0.0, e2d = 0.0;
+                    if (in1) {
+                        e1d = exp(l1d + s_c1d[j]);
+                        const double gp = (s_c1d[j] == 0.0) ? e1d : exp(l1d);
+                        ap_re += gp * cd;
+                        ap_im += gp * sd;
+                    }
+                    if (in2) e2d = exp(-l1d + s_c2d[j]);
+                    const double inv = df_to_double(s_inv[j]);
+                    am_re += (e1d + e2d) * cd * inv;
+                    am_im += (e1d - e2d) * sd * inv;
+                    continue;
+                }
+                df sp, cp;
+                df_sincos(ph, K, sp, cp);
+                df e1 = {0.0f, 0.0f}, e2 = {0.0f, 0.0f};
+                if (in1) {
+                    e1 = df_exp_small(a1, K);
+                    const df gp = (c1.hi == 0.0f) ? e1 : df_exp_small(l1, K);
+                    pp_re = df_add(pp_re, df_mul(gp, cp));
+                    pp_im = df_add(pp_im, df_mul(gp, sp));
+                }
+                if (in2) e2 = df_exp_small(a2, K);
+                const df inv = s_inv[j];
+                pm_re = df_add(pm_re, df_mul(df_mul(df_add(e1, e2), inv), cp));
+                pm_im = df_add(pm_im, df_mul(df_mul(df_sub(e1, e2), inv), sp));
+            }
+            am_re += df_to_double(pm_re);
+            am_im += df_to_double(pm_im);
+            ap_re += df_to_double(pp_re);
+            ap_im += df_to_double(pp_im);
+        }
+        __syncthreads();
+    }
+    if (kvalid) {
+        double2 *a0 = acc + (size_t)r * K1 + k;
+        double2 *a1 = acc + ((size_t)n_sub + r) * K1 + k;
+        const double2 o0 = *a0, o1 = *a1;
+        *a0 = make_double2(o0.x + am_re, o0.y + am_im);
+        *a1 = make_double2(o1.x + ap_re, o1.y + ap_im);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) counts[r] += cnt_r;
+}
+
+// Float pieces of ln 2 and pi/2 for exact Cody-Waite products (12
+// significant bits each except the last), split from the constants'
+// decimal expansions at 80 digits; factorial reciprocals as double-float.
+DfConsts make_df_consts() {
+    DfConsts K;
+    K.ln2_1 = 0x1.62ep-1f;
+    K.ln2_2 = 0x1.0cp-15f;
+    K.ln2_3 = -0x1.05c61p-29f;
+    K.pio2_1 = 0x1.922p+0f;
+    K.pio2_2 = -0x1.2aep-18f;
+    K.pio2_3 = -0x1.deap-31f;
+    K.pio2_4 = 0x1.184698p-44f;
+    double f = 1.0;
+    for (int k = 0; k < 18; ++k) {
+        if (k > 0) f *= (double)k;
+        const double v = 1.0 / f;
+        K.inv_fact_hi[k] = (float)v;
+        K.inv_fact_lo[k] = (float)(v - (double)K.inv_fact_hi[k]);
+    }
+    return K;
+}
+
 __global__ void k_tables(int K1, double2 *__restrict__ tw, double2 *__restrict__ wfft) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K1; k += gridDim.x * blockDim.x) {
         const double f = (double)k / (double)K1;
@@ -202,9 +363,16 @@ int launch_finalize(gbs_net *net, int64_t count) {
 int launch_gf(gbs_net *net, uint64_t e0, int64_t count) {
     if (count <= 0) return GBS_OK;
     dim3 grid((unsigned)((net->K1 + 255) / 256), (unsigned)net->n_sub);
-    k_gf_fp64<<<grid, 256, 0, net->stream>>>(net->d_n, net->d_nS, net->d_win, count, e0,
-                                               net->n_sub, net->K1, net->d_tw, net->d_acc,
-                                               net->d_counts);
+    if (net->precision == GBS_FP64) {
+        k_gf_fp64<<<grid, 256, 0, net->stream>>>(net->d_n, net->d_nS, net->d_win, count, e0,
+                                                   net->n_sub, net->K1, net->d_tw, net->d_acc,
+                                                   net->d_counts);
+    } else {
+        static const DfConsts K = make_df_consts();
+        k_gf_df<<<grid, 256, 0, net->stream>>>(net->d_n, net->d_nS, net->d_win, count, e0,
+                                                 net->n_sub, net->K1, net->d_tw, K, net->d_acc,
+                                                 net->d_counts);
+    }
     GBS_LAUNCH_CHECK();
     return GBS_OK;
 }

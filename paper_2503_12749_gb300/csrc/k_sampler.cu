@@ -73,9 +73,14 @@ __device__ __forceinline__ void normals_fp32(uint64_t seed, uint64_t e, uint32_t
                                              float &w2) {
     uint32_t c0 = (uint32_t)e, c1 = (uint32_t)(e >> 32), c2 = j, c3 = 0u;
     philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+    // ln(u1): for u1 > 1/2 use log1p(-(1 - u1)); 1 - u1 is the same 53-bit
+    // construction applied to the complemented words, so it is formed exactly
+    // before rounding and keeps full FP32 relative precision near u1 = 1.
     const float u1 = uniform53_f(c0, c1);
+    const float v1 = uniform53_f(~c0, ~c1);
+    const float lnu = (v1 < 0.5f) ? log1pf(-v1) : logf(u1);
     const float u2 = uniform53_f(c2, c3);
-    const float rho = sqrtf(-2.0f * logf(u1));
+    const float rho = sqrtf(-2.0f * lnu);
     float s, c;
     sincospif(2.0f * u2, &s, &c);
     w1 = rho * c;
