@@ -120,6 +120,31 @@ int gbs_binned_counts(gbs_net_t net, int64_t m_offset, double *P_mP, double *sig
 int gbs_binned_counts_device(gbs_net_t net, int64_t m_offset, double *out_dev);
 
 /*
+ * gbs_binned_counts_noalloc -- the same inversion and statistics as
+ * gbs_binned_counts_device, for callers that must not allocate device
+ * memory: for example a process whose device memory is owned entirely by
+ * another allocator (a framework's caching pool or a pool reserved at
+ * start-up), where a cudaMalloc outside that allocator fails or fragments
+ * memory, or a latency-critical loop in which cudaMalloc/cudaFree would
+ * synchronise the device.  The paper has no counterpart; it is a service of
+ * this library.
+ *   acc_dev     device, [2][n_sub][K1] complex sums as (re, im) doubles, the
+ *               layout gbs_get_accumulators returns (estimator 0 = matrix-P).
+ *   counts_dev  device, n_sub trajectory counts (each > 0; a zero count gives
+ *               non-finite output).
+ *   out_dev     device, 4*K1 doubles [P_mP | sig_mP | P_plusP | sig_plusP].
+ *   stream      cudaStream_t (as void*) for the launches; asynchronous.
+ * Work space is one fixed array inside the library (not allocated by the
+ * call): 2 * n_sub * K1 <= 2^20 and K1 <= 2^16 (33 MB of device memory held
+ * by every GPU that loads the library until exit); larger sizes return
+ * GBS_EINVAL.  The first call on a device looks up the array's device address
+ * (make it before capturing any stream).  Calls share the array: two calls
+ * that run at the same time on one GPU race.  No network object is needed.
+ */
+int gbs_binned_counts_noalloc(const double *acc_dev, const int64_t *counts_dev, int n_sub,
+                              int K1, int64_t m_offset, double *out_dev, void *stream);
+
+/*
  * gbs_check_finite -- count non-finite entries of the sub-ensemble sums
  * (synchronises).  Returns GBS_OK and *count = 0 when all are finite,
  * GBS_ENONFINITE with *count > 0 otherwise.

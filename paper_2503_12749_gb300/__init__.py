@@ -80,6 +80,8 @@ def lib():
         L.gbs_set_accumulators.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, i64p]
         L.gbs_reset.argtypes = [vp]
         L.gbs_network_info.argtypes = [vp, ip, ip, ip, i64p]
+        L.gbs_binned_counts_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int64, vp, vp]
         L.gbs_profile_enable.argtypes = [vp, ctypes.c_int]
         L.gbs_profile_read.argtypes = [vp, dp, i64p]
         L.gbs_free_network.argtypes = [vp]
@@ -89,7 +91,8 @@ def lib():
         for name in ("gbs_make_network", "gbs_sample", "gbs_binned_counts",
                      "gbs_binned_counts_device", "gbs_check_finite", "gbs_debug_samples",
                      "gbs_get_accumulators", "gbs_set_accumulators", "gbs_reset",
-                     "gbs_network_info", "gbs_profile_enable", "gbs_profile_read"):
+                     "gbs_network_info", "gbs_profile_enable", "gbs_profile_read",
+                     "gbs_binned_counts_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -158,6 +161,15 @@ def gbs_binned_counts(net: Network, m_offset: int = 0, K1: Optional[int] = None
 
 def gbs_binned_counts_device(net: Network, m_offset: int, out_dev_ptr: int) -> None:
     _check(lib().gbs_binned_counts_device(net.handle, m_offset, ctypes.c_void_p(out_dev_ptr)))
+
+
+def gbs_binned_counts_noalloc(acc_dev_ptr: int, counts_dev_ptr: int, n_sub: int, K1: int,
+                              m_offset: int, out_dev_ptr: int, stream: int = 0) -> None:
+    """Inversion of caller-owned device sums into a caller-owned device
+    buffer; the library allocates nothing (fixed internal work space)."""
+    _check(lib().gbs_binned_counts_noalloc(ctypes.c_void_p(acc_dev_ptr),
+                                           ctypes.c_void_p(counts_dev_ptr), n_sub, K1, m_offset,
+                                           ctypes.c_void_p(out_dev_ptr), ctypes.c_void_p(stream)))
 
 
 def gbs_check_finite(net: Network) -> int:
