@@ -135,6 +135,7 @@ void release_all(gbs_net *net) {
     dev_free(net->d_nS_part);
     dev_free(net->d_nS);
     dev_free(net->d_win);
+    dev_free(net->d_wmax);
     dev_free(net->d_flags);
 }
 
@@ -325,6 +326,7 @@ int gbs_make_network(int N, int M, const double *T, const double *r, int precisi
         (rc = dev_alloc(&net->d_nS_part, (size_t)net->chunk * net->mtiles, "nS_part")) ||
         (rc = dev_alloc(&net->d_nS, (size_t)net->chunk, "nS")) ||
         (rc = dev_alloc(&net->d_win, (size_t)net->chunk, "windows")) ||
+        (rc = dev_alloc(&net->d_wmax, (size_t)2, "window union")) ||
         (rc = dev_alloc(&net->d_flags, (size_t)4, "flags")))
         return fail(rc);
     if (cudaMemset(net->d_flags, 0, 4 * sizeof(unsigned long long)) != cudaSuccess)

@@ -96,6 +96,7 @@ struct gbs_net {
     int mtiles = 0;
     double2 *d_nS = nullptr;        // [chunk]
     gbs::Window *d_win = nullptr;   // [chunk]
+    int *d_wmax = nullptr;          // [2]: union of the chunk's windows (max w1, max w2)
 
     // estimator state
     int n_sub = 0, K1 = 0;

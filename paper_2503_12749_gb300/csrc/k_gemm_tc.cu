@@ -16,18 +16,21 @@
 // MMA's result, a bias of ~1 ulp of the running sum per instruction that
 // grows linearly with the number of MMAs chained into one accumulator
 // (measured: ~2^-24 of the amplitude scale per instruction).  So each
-// 64-wide K block's products (4 x products MMAs) go into a fresh TMEM
-// accumulator, and the epilogue warps add every block's result into FP32
+// 64-wide K segment's products go into a fresh TMEM accumulator, and the
+// epilogue warps add every segment's result into FP32
 // registers with round-to-nearest (the promotion interval idea of, e.g.,
-// the DeepSeek-V3 report's FP8 GEMMs).  Two TMEM buffers alternate per K
-// block, so the MMAs of block s+1 overlap the promotion of block s.
+// the DeepSeek-V3 report's FP8 GEMMs).  Two TMEM buffers alternate per
+// segment of 64 K, so the MMAs of segment s+1 overlap the promotion of s.
 //
 // Kernel structure (one CTA per SM, persistent over tiles, 320 threads):
-//   warp 0      TMA producer: per (64-wide K block, product) one A box
-//               (64 x 128) and one B box (64 x 256), 128-byte swizzle, into a
-//               4-stage shared-memory ring;
+//   warp 0      TMA producer: per 32-wide K block one box per BF16 plane used
+//               (A: 32 x 128, B: 32 x 256, 64-byte swizzle), every plane loaded
+//               once per K block, into a 4-stage (3 products) or 3-stage
+//               (6 products) shared-memory ring;
 //   warp 1      allocates 512 TMEM columns; one thread issues
-//               tcgen05.mma M=128 N=256 K=16 into the K block's buffer;
+//               tcgen05.mma M=128 N=256 K=16, per segment of two K blocks the
+//               correction products first and A0 B0 last, into the segment's
+//               buffer;
 //   warps 2..9  epilogue: warp w reads TMEM lanes 32 (w mod 4).. (its A rows)
 //               and half (w - 2) / 4 of the tile's trajectories: running
 //               sums of 64 alpha' and 64 beta' columns per thread.  After the
@@ -58,20 +61,29 @@ struct TcPlan {
 
 namespace {
 
-constexpr int kStages = 4;
-constexpr int kABytes = 128 * 128;  // 128 rows x 64 bf16
-constexpr int kBBytes = 256 * 128;  // 256 rows x 64 bf16
-constexpr int kStageBytes = kABytes + kBBytes;
+// One pipeline stage holds every BF16 plane of one 32-wide K block: A planes
+// of 128 rows x 64 B, B planes of 256 rows x 64 B (64-byte swizzle).
+template <int P>
+struct Cfg {
+    static constexpr int kPlanes = (P == 3) ? 2 : 3;  // planes of A and of B used
+    static constexpr int kAPlane = 128 * 64;
+    static constexpr int kBPlane = 256 * 64;
+    static constexpr int kStageBytes = kPlanes * (kAPlane + kBPlane);
+    static constexpr int kStages = (P == 3) ? 4 : 3;
+};
 constexpr int kBarBytes = 1024;
 constexpr int kRedBytes = 4 * 128 * 2 * 4;  // float [4 quarters][128 trajectories][re, im]
-constexpr int kSmemBytes = 1024 + kStages * kStageBytes + kBarBytes + kRedBytes;
+template <int P>
+constexpr int smem_bytes() {
+    return 1024 + Cfg<P>::kStages * Cfg<P>::kStageBytes + kBarBytes + kRedBytes;
+}
 constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(128, 256);
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
 
 struct TcParams {
-    int KB;  // 64-wide K blocks
+    int KB;  // 32-wide K blocks
     int P;   // products
     int ia[6];
     int ib[6];
@@ -126,31 +138,37 @@ __device__ __forceinline__ void warp_transpose_reduce32(float (&v)[32], int lane
     }
 }
 
+template <int P>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
               const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
               const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2,
               const TcParams p) {
+    using C = Cfg<P>;
+    constexpr int kStages = C::kStages;
+    constexpr int kPl = C::kPlanes;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    uint8_t *sA = smem;
-    uint8_t *sB = smem + kStages * kABytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+    // stage s: [A plane 0..kPl-1][B plane 0..kPl-1]
+    auto a_tile = [&](int stage, int plane) {
+        return smem + stage * C::kStageBytes + plane * C::kAPlane;
+    };
+    auto b_tile = [&](int stage, int plane) {
+        return smem + stage * C::kStageBytes + kPl * C::kAPlane + plane * C::kBPlane;
+    };
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * C::kStageBytes);
     uint64_t *full = bars;
     uint64_t *empty = bars + kStages;
     uint64_t *tfull = bars + 2 * kStages;
     uint64_t *tempty = bars + 2 * kStages + 2;
     uint64_t *drain = bars + 2 * kStages + 4;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 5);
-    float *red = reinterpret_cast<float *>(smem + kStages * kStageBytes + kBarBytes);
+    float *red = reinterpret_cast<float *>(smem + kStages * C::kStageBytes + kBarBytes);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     volatile unsigned long long *err = p.err;
-
-    const CUtensorMap *mapsA[3] = {&mA0, &mA1, &mA2};
-    const CUtensorMap *mapsB[3] = {&mB0, &mB1, &mB2};
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -163,9 +181,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ptx::mbar_init(ptx::smem_u32(drain), 1);
         ptx::fence_barrier_init();
-        for (int q = 0; q < p.P; ++q) {
-            ptx::prefetch_tmap(mapsA[p.ia[q]]);
-            ptx::prefetch_tmap(mapsB[p.ib[q]]);
+        ptx::prefetch_tmap(&mA0);
+        ptx::prefetch_tmap(&mA1);
+        ptx::prefetch_tmap(&mB0);
+        ptx::prefetch_tmap(&mB1);
+        if (kPl > 2) {
+            ptx::prefetch_tmap(&mA2);
+            ptx::prefetch_tmap(&mB2);
         }
     }
     if (warp == 1) {
@@ -178,6 +200,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem_base = *tmem_slot;
 
     const int ntiles = p.mtiles * p.stiles;
+    const int nseg = (p.KB + 1) / 2;  // promotion segments of two 32-wide K blocks
 
     if (warp == 0) {
         if (lane == 0) {
@@ -189,24 +212,28 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
                 const int mt = tile % p.mtiles;
                 const int st = tile / p.mtiles;
-                for (int kb = 0; ok && kb < p.KB; ++kb) {
-                    for (int pr = 0; pr < p.P; ++pr) {
-                        if (!ptx::mbar_wait(ptx::smem_u32(&empty[stage]), phase ^ 1u, err)) {
-                            ok = false;
-                            break;
-                        }
-                        const uint32_t fb = ptx::smem_u32(&full[stage]);
-                        ptx::mbar_arrive_expect_tx(fb, kStageBytes);
-                        ptx::tma_load_2d(ptx::smem_u32(sA + stage * kABytes), mapsA[p.ia[pr]], fb,
-                                         kb * 64, mt * 128);
-                        ptx::tma_load_2d(ptx::smem_u32(sB + stage * kBBytes), mapsB[p.ib[pr]], fb,
-                                         kb * 64, st * 256);
-                        used |= 1u << stage;
-                        last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
-                        if (++stage == kStages) {
-                            stage = 0;
-                            phase ^= 1u;
-                        }
+                for (int kb = 0; kb < p.KB; ++kb) {
+                    if (!ptx::mbar_wait(ptx::smem_u32(&empty[stage]), phase ^ 1u, err)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = ptx::smem_u32(&full[stage]);
+                    ptx::mbar_arrive_expect_tx(fb, C::kStageBytes);
+                    ptx::tma_load_2d(ptx::smem_u32(a_tile(stage, 0)), &mA0, fb, kb * 32, mt * 128);
+                    ptx::tma_load_2d(ptx::smem_u32(a_tile(stage, 1)), &mA1, fb, kb * 32, mt * 128);
+                    if (kPl > 2)
+                        ptx::tma_load_2d(ptx::smem_u32(a_tile(stage, 2)), &mA2, fb, kb * 32,
+                                         mt * 128);
+                    ptx::tma_load_2d(ptx::smem_u32(b_tile(stage, 0)), &mB0, fb, kb * 32, st * 256);
+                    ptx::tma_load_2d(ptx::smem_u32(b_tile(stage, 1)), &mB1, fb, kb * 32, st * 256);
+                    if (kPl > 2)
+                        ptx::tma_load_2d(ptx::smem_u32(b_tile(stage, 2)), &mB2, fb, kb * 32,
+                                         st * 256);
+                    used |= 1u << stage;
+                    last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
                     }
                 }
             }
@@ -219,39 +246,55 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------- MMA issuer
+            // Per segment (two K blocks): the correction products of both
+            // blocks first, then A0 B0 of both, into a fresh accumulator.
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t seg = 0;  // K blocks issued so far (selects the TMEM buffer)
+            uint32_t seg = 0;  // segments issued so far (selects the TMEM buffer)
             bool ok = true;
             for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-                for (int kb = 0; ok && kb < p.KB; ++kb, ++seg) {
+                for (int sg = 0; ok && sg < nseg; ++sg, ++seg) {
                     const uint32_t b = seg & 1u;
                     if (!ptx::mbar_wait(ptx::smem_u32(&tempty[b]), ((seg >> 1) & 1u) ^ 1u, err)) {
                         ok = false;
                         break;
                     }
-                    ptx::tc_fence_after();
-                    const uint32_t d = tmem_base + b * 256u;
-                    for (int pr = 0; pr < p.P; ++pr) {
-                        if (!ptx::mbar_wait(ptx::smem_u32(&full[stage]), phase, err)) {
+                    const int nst = (2 * sg + 1 < p.KB) ? 2 : 1;
+                    int stg[2];
+                    stg[0] = stage;
+                    stg[1] = (stage + 1 == kStages) ? 0 : stage + 1;
+                    for (int q = 0; q < nst; ++q) {
+                        // stage stg[q] has fill parity phase (q = 0) or, after a wrap, phase ^ 1
+                        const uint32_t par = (q == 1 && stg[1] == 0) ? (phase ^ 1u) : phase;
+                        if (!ptx::mbar_wait(ptx::smem_u32(&full[stg[q]]), par, err)) {
                             ok = false;
                             break;
                         }
-                        ptx::tc_fence_after();
-                        const uint32_t a0 = ptx::smem_u32(sA + stage * kABytes);
-                        const uint32_t b0 = ptx::smem_u32(sB + stage * kBBytes);
+                    }
+                    if (!ok) break;
+                    ptx::tc_fence_after();
+                    const uint32_t d = tmem_base + b * 256u;
+                    uint32_t acc = 0u;
+                    for (int pr = 0; pr < P; ++pr) {
+                        for (int q = 0; q < nst; ++q) {
+                            const uint32_t a0 = ptx::smem_u32(a_tile(stg[q], p.ia[pr]));
+                            const uint32_t b0 = ptx::smem_u32(b_tile(stg[q], p.ib[pr]));
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            ptx::mma_bf16(d, ptx::desc_k_sw128(a0 + kk * 32),
-                                          ptx::desc_k_sw128(b0 + kk * 32), kIdesc,
-                                          (pr | kk) != 0 ? 1u : 0u);
-                        ptx::mma_commit(ptx::smem_u32(&empty[stage]));
+                            for (int kk = 0; kk < 2; ++kk) {
+                                ptx::mma_bf16(d, ptx::desc_k_sw64(a0 + kk * 32),
+                                              ptx::desc_k_sw64(b0 + kk * 32), kIdesc, acc);
+                                acc = 1u;
+                            }
+                        }
+                    }
+                    for (int q = 0; q < nst; ++q) ptx::mma_commit(ptx::smem_u32(&empty[stg[q]]));
+                    ptx::mma_commit(ptx::smem_u32(&tfull[b]));
+                    for (int q = 0; q < nst; ++q) {
                         if (++stage == kStages) {
                             stage = 0;
                             phase ^= 1u;
                         }
                     }
-                    if (ok) ptx::mma_commit(ptx::smem_u32(&tfull[b]));
                 }
             }
             // drain: all MMAs issued by this thread have completed
@@ -276,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ra[i] = 0.0f;
                 rb[i] = 0.0f;
             }
-            for (int kb = 0; kb < p.KB; ++kb, ++seg) {
+            for (int sg = 0; sg < nseg; ++sg, ++seg) {
                 const uint32_t b = seg & 1u;
                 // on a timeout every epilogue thread keeps going (without
                 // waiting) so that all of them reach the same barriers
@@ -359,6 +402,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 int encode_2d(CUtensorMap *map, void *base, uint64_t inner, uint64_t rows, uint64_t row_bytes,
               uint32_t box_inner, uint32_t box_rows) {
+    // box_inner = 32 bf16 = 64 bytes per row: the 64-byte swizzle
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
     if (!enc) return set_error(GBS_ECUDA, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[2] = {inner, rows};
@@ -366,7 +410,7 @@ int encode_2d(CUtensorMap *map, void *base, uint64_t inner, uint64_t rows, uint6
     cuuint32_t box[2] = {box_inner, box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(GBS_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return GBS_OK;
@@ -385,12 +429,12 @@ int tc_plan_create(gbs_net *net) {
     int rc;
     for (int q = 0; q < 3; ++q) {
         if ((rc = encode_2d(&plan->mapA[q], net->d_A + q * planeA, (uint64_t)net->N,
-                            (uint64_t)net->rowsA, (uint64_t)net->ldK * 2, 64, 128)))
+                            (uint64_t)net->rowsA, (uint64_t)net->ldK * 2, 32, 128)))
             return rc;
         __nv_bfloat16 *bbase = static_cast<__nv_bfloat16 *>(net->d_B) +
                                (q < net->planesB ? q : 0) * planeB;
         if ((rc = encode_2d(&plan->mapB[q], bbase, (uint64_t)net->N, (uint64_t)plan->rowsB,
-                            (uint64_t)net->ldK * 2, 64, 256)))
+                            (uint64_t)net->ldK * 2, 32, 256)))
             return rc;
     }
     // products A_i B_j with i + j <= 1 (3) or <= 2 (6), issued smallest
@@ -417,12 +461,16 @@ int launch_gemm_tc(gbs_net *net, int64_t count) {
     TcPlan *plan = net->tc;
     if (!plan) return set_error(GBS_EINVAL, "no tensor-core plan");
     if (!plan->attr_set) {
-        GBS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          kSmemBytes));
+        GBS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<3>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          smem_bytes<3>()));
+        GBS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<6>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          smem_bytes<6>()));
         plan->attr_set = true;
     }
     TcParams p;
-    p.KB = (net->N + kTcBlockK - 1) / kTcBlockK;
+    p.KB = (net->N + 31) / 32;
     p.P = plan->P;
     for (int q = 0; q < 6; ++q) {
         p.ia[q] = plan->ia[q];
@@ -436,9 +484,14 @@ int launch_gemm_tc(gbs_net *net, int64_t count) {
     p.err = net->d_flags + 1;
     const int64_t ntiles = (int64_t)p.mtiles * p.stiles;
     const int grid = (int)std::min<int64_t>(ntiles, net->sm_count);
-    k_gemm_tc<<<grid, kThreads, kSmemBytes, net->stream>>>(plan->mapA[0], plan->mapA[1], plan->mapA[2],
-                                                      plan->mapB[0], plan->mapB[1], plan->mapB[2],
-                                                      p);
+    if (plan->P == 3)
+        k_gemm_tc<3><<<grid, kThreads, smem_bytes<3>(), net->stream>>>(
+            plan->mapA[0], plan->mapA[1], plan->mapA[2], plan->mapB[0], plan->mapB[1],
+            plan->mapB[2], p);
+    else
+        k_gemm_tc<6><<<grid, kThreads, smem_bytes<6>(), net->stream>>>(
+            plan->mapA[0], plan->mapA[1], plan->mapA[2], plan->mapB[0], plan->mapB[1],
+            plan->mapB[2], p);
     GBS_LAUNCH_CHECK();
     return GBS_OK;
 }

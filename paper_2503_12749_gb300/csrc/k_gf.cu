@@ -72,7 +72,9 @@ __device__ __forceinline__ Window windows_for(double n, double x, double y, int 
 
 __global__ void k_finalize(const double2 *__restrict__ part, int mtiles, int64_t ld,
                            const double *__restrict__ n, int64_t count, int K1,
-                           double2 *__restrict__ nS, Window *__restrict__ win) {
+                           double2 *__restrict__ nS, Window *__restrict__ win,
+                           int *__restrict__ wmax) {
+    int m1 = -1, m2 = -1;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
         double re = 0.0, im = 0.0;
@@ -82,7 +84,18 @@ __global__ void k_finalize(const double2 *__restrict__ part, int mtiles, int64_t
             im += p.y;
         }
         nS[i] = make_double2(re, im);
-        win[i] = windows_for(n[i], re, im, K1);
+        const Window w = windows_for(n[i], re, im, K1);
+        win[i] = w;
+        m1 = max(m1, w.w1);
+        m2 = max(m2, w.w2);
+    }
+    // union of the chunk's windows: the generating-function kernel only
+    // assigns threads to k inside it
+    m1 = __reduce_max_sync(0xffffffffu, m1);
+    m2 = __reduce_max_sync(0xffffffffu, m2);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&wmax[0], m1);
+        atomicMax(&wmax[1], m2);
     }
 }
 
@@ -193,28 +206,53 @@ __device__ __forceinline__ df df_exp_small(df a, const DfConsts &K) {
     return a.hi < -87.0f ? df{0.0f, 0.0f} : df_exp(a, K);  // below 1e-37: nothing
 }
 
-__global__ void __launch_bounds__(256) k_gf_df(const double *__restrict__ n_in,
-                                               const double2 *__restrict__ nS_in,
-                                               const Window *__restrict__ win_in,
-                                               int64_t count, uint64_t e0, int n_sub, int K1,
-                                               const double2 *__restrict__ tw, const DfConsts K,
-                                               double2 *__restrict__ acc,
-                                               int64_t *__restrict__ counts) {
-    constexpr int TILE = 64;
-    __shared__ df s_x[TILE], s_y[TILE], s_c1[TILE], s_c2[TILE], s_inv[TILE];
-    __shared__ double s_xd[TILE], s_yd[TILE], s_c1d[TILE], s_c2d[TILE];
-    __shared__ int s_w1[TILE], s_w2[TILE];
+// k of slot i: slots enumerate the union window around theta = 0
+// (k = -W1..W1 mod K1) and then the one around theta = pi (K1/2-W2..K1/2+W2);
+// when the two cover the circle the mapping is k = i.  Returns -1 past the end.
+__device__ __forceinline__ int slot_to_k(int i, int K1, int W1, int W2) {
+    const int half = K1 >> 1;
+    const int n1 = W1 >= half ? K1 : 2 * W1 + 1;
+    const int n2 = W2 < 0 ? 0 : (W2 >= half ? K1 : 2 * W2 + 1);
+    if (n1 + n2 >= K1) return i < K1 ? i : -1;
+    if (i < n1) {
+        const int k = i - W1;
+        return k < 0 ? k + K1 : k;
+    }
+    if (i < n1 + n2) return half - W2 + (i - n1);
+    return -1;
+}
+
+constexpr int kGfSlots = 128;   // k slots per block
+constexpr int kGfGroups = 4;    // trajectory groups per block (warps per slot range: 4 x 4)
+constexpr int kGfTile = 128;    // trajectories staged in shared memory per tile
+
+__global__ void __launch_bounds__(kGfSlots * kGfGroups, 1)
+    k_gf_df(const double *__restrict__ n_in, const double2 *__restrict__ nS_in,
+            const Window *__restrict__ win_in, const int *__restrict__ wmax, int64_t count,
+            uint64_t e0, int n_sub, int K1, const double2 *__restrict__ tw, const DfConsts K,
+            double2 *__restrict__ acc, int64_t *__restrict__ counts) {
+    __shared__ df s_x[kGfTile], s_y[kGfTile], s_c1[kGfTile], s_c2[kGfTile], s_inv[kGfTile];
+    __shared__ double s_xd[kGfTile], s_yd[kGfTile], s_c1d[kGfTile], s_c2d[kGfTile];
+    __shared__ int s_w1[kGfTile], s_w2[kGfTile];
+    __shared__ double s_red[kGfGroups][4][kGfSlots];
 
     const int r = blockIdx.y;
-    const int kb0 = blockIdx.x * 256;
-    const int kb1 = min(kb0 + 256, K1);
-    const int k = kb0 + threadIdx.x;
-    const bool kvalid = k < K1;
+    const int W1 = wmax[0], W2 = wmax[1];
+    const int slot = threadIdx.x % kGfSlots;
+    const int grp = threadIdx.x / kGfSlots;
+    const int k = slot_to_k(blockIdx.x * kGfSlots + slot, K1, W1, W2);
+    const int first_k = slot_to_k(blockIdx.x * kGfSlots, K1, W1, W2);
+    if (first_k < 0) {  // the block lies past the union window: nothing to add
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const int64_t f = (int64_t)(((uint64_t)r + (uint64_t)n_sub - e0 % (uint64_t)n_sub) %
+                                        (uint64_t)n_sub);
+            counts[r] += f < count ? (count - 1 - f) / n_sub + 1 : 0;
+        }
+        return;
+    }
+    const bool kvalid = k >= 0;
     const int d0 = kvalid ? dist0(k, K1) : 0x3fffffff;
     const int dpi = kvalid ? dist_pi(k, K1) : 0x3fffffff;
-    const int bd0 = min(dist0(kb0, K1), dist0(kb1 - 1, K1));
-    const int half = K1 >> 1;
-    const int bdpi = (half >= kb0 && half < kb1) ? 0 : min(dist_pi(kb0, K1), dist_pi(kb1 - 1, K1));
 
     const int64_t first = (int64_t)(((uint64_t)r + (uint64_t)n_sub - e0 % (uint64_t)n_sub) %
                                     (uint64_t)n_sub);
@@ -225,10 +263,9 @@ __global__ void __launch_bounds__(256) k_gf_df(const double *__restrict__ n_in,
     const df cm1 = df_from_double(t.x), sn = df_from_double(t.y);
     double am_re = 0.0, am_im = 0.0, ap_re = 0.0, ap_im = 0.0;
 
-    for (int64_t base = 0; base < cnt_r; base += TILE) {
+    for (int64_t base = 0; base < cnt_r; base += kGfTile) {
         const int64_t q = base + threadIdx.x;
-        int hit = 0;
-        if (threadIdx.x < TILE && q < cnt_r) {
+        if (threadIdx.x < kGfTile && q < cnt_r) {
             const int64_t i = first + q * n_sub;
             const double nn = n_in[i];
             const double2 sv = nS_in[i];
@@ -245,20 +282,19 @@ __global__ void __launch_bounds__(256) k_gf_df(const double *__restrict__ n_in,
             s_c2d[threadIdx.x] = c2;
             s_w1[threadIdx.x] = w.w1;
             s_w2[threadIdx.x] = w.w2;
-            hit = (bd0 <= w.w1) || (bdpi <= w.w2);
         }
-        if (!__syncthreads_or(hit)) continue;
-        const int ntile = (cnt_r - base) < TILE ? (int)(cnt_r - base) : TILE;
+        __syncthreads();
+        const int ntile = (cnt_r - base) < kGfTile ? (int)(cnt_r - base) : kGfTile;
         if (kvalid) {
             df pm_re = {0.0f, 0.0f}, pm_im = {0.0f, 0.0f}, pp_re = {0.0f, 0.0f},
                pp_im = {0.0f, 0.0f};
-            for (int j = 0; j < ntile; ++j) {
+            for (int j = grp; j < ntile; j += kGfGroups) {
                 const bool in1 = d0 <= s_w1[j];
                 const bool in2 = dpi <= s_w2[j];
                 if (!(in1 || in2)) continue;
                 const df x = s_x[j], y = s_y[j];
-                const df l1 = df_sub(df_mul(cm1, x), df_mul(sn, y));     // (cos-1) x - sin y
-                const df ph = df_add(df_mul(sn, x), df_mul(cm1, y));     // sin x + (cos-1) y
+                const df l1 = df_sub(df_mul(cm1, x), df_mul(sn, y));  // (cos-1) x - sin y
+                const df ph = df_add(df_mul(sn, x), df_mul(cm1, y));  // sin x + (cos-1) y
                 const df c1 = s_c1[j];
                 const df a1 = df_add(l1, c1);
                 const df a2 = df_add(df_neg(l1), s_c2[j]);
@@ -306,12 +342,26 @@ __global__ void __launch_bounds__(256) k_gf_df(const double *__restrict__ n_in,
         }
         __syncthreads();
     }
-    if (kvalid) {
+    // combine the trajectory groups in a fixed order
+    s_red[grp][0][slot] = am_re;
+    s_red[grp][1][slot] = am_im;
+    s_red[grp][2][slot] = ap_re;
+    s_red[grp][3][slot] = ap_im;
+    __syncthreads();
+    if (grp == 0 && kvalid) {
+        double v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            double sum = 0.0;
+#pragma unroll
+            for (int g = 0; g < kGfGroups; ++g) sum += s_red[g][c][slot];
+            v[c] = sum;
+        }
         double2 *a0 = acc + (size_t)r * K1 + k;
         double2 *a1 = acc + ((size_t)n_sub + r) * K1 + k;
         const double2 o0 = *a0, o1 = *a1;
-        *a0 = make_double2(o0.x + am_re, o0.y + am_im);
-        *a1 = make_double2(o1.x + ap_re, o1.y + ap_im);
+        *a0 = make_double2(o0.x + v[0], o0.y + v[1]);
+        *a1 = make_double2(o1.x + v[2], o1.y + v[3]);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) counts[r] += cnt_r;
 }
@@ -353,9 +403,11 @@ __global__ void k_tables(int K1, double2 *__restrict__ tw, double2 *__restrict__
 
 int launch_finalize(gbs_net *net, int64_t count) {
     if (count <= 0) return GBS_OK;
+    GBS_CUDA_TRY(cudaMemsetAsync(net->d_wmax, 0xff, 2 * sizeof(int), net->stream));  // -1, -1
     int blocks = (int)std::min<int64_t>((count + 255) / 256, (int64_t)net->sm_count * 8);
     k_finalize<<<blocks, 256, 0, net->stream>>>(net->d_nS_part, net->mtiles, net->chunk, net->d_n,
-                                                 count, net->K1, net->d_nS, net->d_win);
+                                                 count, net->K1, net->d_nS, net->d_win,
+                                                 net->d_wmax);
     GBS_LAUNCH_CHECK();
     return GBS_OK;
 }
@@ -369,9 +421,10 @@ int launch_gf(gbs_net *net, uint64_t e0, int64_t count) {
                                                    net->d_counts);
     } else {
         static const DfConsts K = make_df_consts();
-        k_gf_df<<<grid, 256, 0, net->stream>>>(net->d_n, net->d_nS, net->d_win, count, e0,
-                                                 net->n_sub, net->K1, net->d_tw, K, net->d_acc,
-                                                 net->d_counts);
+        dim3 g2((unsigned)((net->K1 + kGfSlots - 1) / kGfSlots), (unsigned)net->n_sub);
+        k_gf_df<<<g2, kGfSlots * kGfGroups, 0, net->stream>>>(
+            net->d_n, net->d_nS, net->d_win, net->d_wmax, count, e0, net->n_sub, net->K1,
+            net->d_tw, K, net->d_acc, net->d_counts);
     }
     GBS_LAUNCH_CHECK();
     return GBS_OK;

@@ -167,6 +167,17 @@ __device__ __forceinline__ uint64_t desc_k_sw128(uint32_t saddr) {
     return d;
 }
 
+// The same for tiles stored with the 64-byte swizzle (rows of 64 B, 8-row
+// atoms of 512 B): stride byte offset 512, swizzle mode 4.
+__device__ __forceinline__ uint64_t desc_k_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)4u << 61;
+    return d;
+}
+
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
 // and B (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28.
