@@ -22,7 +22,12 @@
 // the DeepSeek-V3 report's FP8 GEMMs).  Two TMEM buffers alternate per
 // segment of 64 K, so the MMAs of segment s+1 overlap the promotion of s.
 //
-// Kernel structure (one CTA per SM, persistent over tiles, 320 threads):
+// Kernel structure (one CTA per SM, clusters of 2 CTAs, persistent over tile
+// groups, 320 threads).  The CTAs of a cluster compute mode tiles 2g, 2g+1
+// of the same trajectory tile: each loads its own A planes and half of the
+// B planes, which TMA multicasts into both CTAs' shared memory, so the L2
+// delivers each B tile once per pair.  A stage is refilled only after
+// every CTA's MMAs released it (their commits arrive on all CTAs' barriers).
 //   warp 0      TMA producer: per 32-wide K block one box per BF16 plane used
 //               (A: 32 x 128, B: 32 x 256, 64-byte swizzle), every plane loaded
 //               once per K block, into a 4-stage (3 products) or 3-stage
@@ -78,6 +83,8 @@ constexpr int smem_bytes() {
     return 1024 + Cfg<P>::kStages * Cfg<P>::kStageBytes + kBarBytes + kRedBytes;
 }
 constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(128, 256);
+constexpr int kCluster = 2;  // CTAs sharing one trajectory tile's B operand
+constexpr uint16_t kClusterMask = (1u << kCluster) - 1;
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
@@ -173,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             ptx::mbar_init(ptx::smem_u32(&full[s]), 1);
-            ptx::mbar_init(ptx::smem_u32(&empty[s]), 1);
+            ptx::mbar_init(ptx::smem_u32(&empty[s]), kCluster);  // released by every CTA of the cluster
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(ptx::smem_u32(&tfull[b]), 1);
@@ -196,10 +203,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     ptx::tc_fence_before();
     __syncthreads();
+    ptx::cluster_sync();  // the peer's barriers exist before anything is multicast to them
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    const int ntiles = p.mtiles * p.stiles;
+    // A cluster of kCluster CTAs works on a tile group: the same trajectory
+    // tile, mode tiles kCluster*g + rank; each CTA loads 1/kCluster of the B
+    // rows and multicasts them to all.
+    const uint32_t rank = ptx::cluster_ctarank();
+    const int cluster = blockIdx.x / kCluster;
+    const int nclusters = gridDim.x / kCluster;
+    const int mpairs = (p.mtiles + kCluster - 1) / kCluster;
+    const int ntiles = mpairs * p.stiles;
     const int nseg = (p.KB + 1) / 2;  // promotion segments of two 32-wide K blocks
 
     if (warp == 0) {
@@ -209,9 +224,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase = 0;
             uint32_t used = 0, last_phase = 0;  // stages ever filled, parity of their last fill
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-                const int mt = tile % p.mtiles;
-                const int st = tile / p.mtiles;
+            for (int tile = cluster; ok && tile < ntiles; tile += nclusters) {
+                const int mt = kCluster * (tile % mpairs) + (int)rank;  // >= p.mtiles: A reads zeros
+                const int st = tile / mpairs;
                 for (int kb = 0; kb < p.KB; ++kb) {
                     if (!ptx::mbar_wait(ptx::smem_u32(&empty[stage]), phase ^ 1u, err)) {
                         ok = false;
@@ -224,11 +239,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (kPl > 2)
                         ptx::tma_load_2d(ptx::smem_u32(a_tile(stage, 2)), &mA2, fb, kb * 32,
                                          mt * 128);
-                    ptx::tma_load_2d(ptx::smem_u32(b_tile(stage, 0)), &mB0, fb, kb * 32, st * 256);
-                    ptx::tma_load_2d(ptx::smem_u32(b_tile(stage, 1)), &mB1, fb, kb * 32, st * 256);
+                    const int brow = st * 256 + (int)rank * (256 / kCluster);
+                    const uint32_t bpart = rank * (uint32_t)(C::kBPlane / kCluster);
+                    ptx::tma_load_2d_mc(ptx::smem_u32(b_tile(stage, 0)) + bpart, &mB0, fb, kb * 32,
+                                        brow, kClusterMask);
+                    ptx::tma_load_2d_mc(ptx::smem_u32(b_tile(stage, 1)) + bpart, &mB1, fb, kb * 32,
+                                        brow, kClusterMask);
                     if (kPl > 2)
-                        ptx::tma_load_2d(ptx::smem_u32(b_tile(stage, 2)), &mB2, fb, kb * 32,
-                                         st * 256);
+                        ptx::tma_load_2d_mc(ptx::smem_u32(b_tile(stage, 2)) + bpart, &mB2, fb,
+                                            kb * 32, brow, kClusterMask);
                     used |= 1u << stage;
                     last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
                     if (++stage == kStages) {
@@ -237,11 +256,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
             }
-            // drain: every load issued by this thread has landed before exit
+            // drain: every load issued by this thread has landed, and both
+            // CTAs' MMAs have released every stage (their arrivals are in)
             for (int s = 0; s < kStages; ++s)
-                if (used & (1u << s))
+                if (used & (1u << s)) {
                     ptx::mbar_wait(ptx::smem_u32(&full[s]), (last_phase >> s) & 1u, err,
                                    200000000ull);
+                    ptx::mbar_wait(ptx::smem_u32(&empty[s]), (last_phase >> s) & 1u, err,
+                                   200000000ull);
+                }
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -252,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase = 0;
             uint32_t seg = 0;  // segments issued so far (selects the TMEM buffer)
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+            for (int tile = cluster; ok && tile < ntiles; tile += nclusters) {
                 for (int sg = 0; ok && sg < nseg; ++sg, ++seg) {
                     const uint32_t b = seg & 1u;
                     if (!ptx::mbar_wait(ptx::smem_u32(&tempty[b]), ((seg >> 1) & 1u) ^ 1u, err)) {
@@ -287,7 +310,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                         }
                     }
-                    for (int q = 0; q < nst; ++q) ptx::mma_commit(ptx::smem_u32(&empty[stg[q]]));
+                    // the stage is free once every CTA's MMAs have read it
+                    for (int q = 0; q < nst; ++q)
+                        ptx::mma_commit_mc(ptx::smem_u32(&empty[stg[q]]), kClusterMask);
                     ptx::mma_commit(ptx::smem_u32(&tfull[b]));
                     for (int q = 0; q < nst; ++q) {
                         if (++stage == kStages) {
@@ -310,9 +335,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int et = threadIdx.x - 64;     // 0..255
         const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
         uint32_t seg = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            const int mt = tile % p.mtiles;
-            const int st = tile / p.mtiles;
+        for (int tile = cluster; tile < ntiles; tile += nclusters) {
+            const int mt = kCluster * (tile % mpairs) + (int)rank;
+            const int st = tile / mpairs;
             float ra[64], rb[64];  // running alpha', beta' parts of this row
 #pragma unroll
             for (int i = 0; i < 64; ++i) {
@@ -373,7 +398,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     im += (double)red[(w * 128 + et) * 2 + 1];
                 }
                 const int64_t s = (int64_t)st * 128 + et;
-                if (s < p.count) p.nS_part[(size_t)mt * p.ld_part + s] = make_double2(re, im);
+                if (s < p.count && mt < p.mtiles)
+                    p.nS_part[(size_t)mt * p.ld_part + s] = make_double2(re, im);
             }
             named_bar_sync(1, kEpiThreads);
         }
@@ -381,6 +407,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     ptx::tc_fence_before();
     __syncthreads();
+    // no multicast or remote arrive from the peer is in flight past this point
+    ptx::cluster_sync();
     if (warp == 1) {
         ptx::tc_fence_after();
         ptx::tmem_dealloc(tmem_base, 512);
@@ -429,12 +457,12 @@ int tc_plan_create(gbs_net *net) {
     int rc;
     for (int q = 0; q < 3; ++q) {
         if ((rc = encode_2d(&plan->mapA[q], net->d_A + q * planeA, (uint64_t)net->N,
-                            (uint64_t)net->rowsA, (uint64_t)net->ldK * 2, 32, 128)))
+                            (uint64_t)net->rowsA, (uint64_t)net->ldK * 2, 32, 256 / kCluster)))
             return rc;
         __nv_bfloat16 *bbase = static_cast<__nv_bfloat16 *>(net->d_B) +
                                (q < net->planesB ? q : 0) * planeB;
         if ((rc = encode_2d(&plan->mapB[q], bbase, (uint64_t)net->N, (uint64_t)plan->rowsB,
-                            (uint64_t)net->ldK * 2, 32, 256)))
+                            (uint64_t)net->ldK * 2, 32, 256 / kCluster)))
             return rc;
     }
     // products A_i B_j with i + j <= 1 (3) or <= 2 (6), issued smallest
@@ -482,16 +510,29 @@ int launch_gemm_tc(gbs_net *net, int64_t count) {
     p.ld_part = net->chunk;
     p.nS_part = net->d_nS_part;
     p.err = net->d_flags + 1;
-    const int64_t ntiles = (int64_t)p.mtiles * p.stiles;
-    const int grid = (int)std::min<int64_t>(ntiles, net->sm_count);
+    const int64_t ntiles = (int64_t)((p.mtiles + kCluster - 1) / kCluster) * p.stiles;
+    const int clusters = (int)std::min<int64_t>(ntiles, net->sm_count / kCluster);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kCluster * clusters);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = plan->P == 3 ? smem_bytes<3>() : smem_bytes<6>();
+    cfg.stream = net->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t le;
     if (plan->P == 3)
-        k_gemm_tc<3><<<grid, kThreads, smem_bytes<3>(), net->stream>>>(
-            plan->mapA[0], plan->mapA[1], plan->mapA[2], plan->mapB[0], plan->mapB[1],
-            plan->mapB[2], p);
+        le = cudaLaunchKernelEx(&cfg, k_gemm_tc<3>, plan->mapA[0], plan->mapA[1], plan->mapA[2],
+                                plan->mapB[0], plan->mapB[1], plan->mapB[2], p);
     else
-        k_gemm_tc<6><<<grid, kThreads, smem_bytes<6>(), net->stream>>>(
-            plan->mapA[0], plan->mapA[1], plan->mapA[2], plan->mapB[0], plan->mapB[1],
-            plan->mapB[2], p);
+        le = cudaLaunchKernelEx(&cfg, k_gemm_tc<6>, plan->mapA[0], plan->mapA[1], plan->mapA[2],
+                                plan->mapB[0], plan->mapB[1], plan->mapB[2], p);
+    if (le != cudaSuccess)
+        return set_error(GBS_ECUDA, "cluster launch of the GEMM failed: %s", cudaGetErrorString(le));
     GBS_LAUNCH_CHECK();
     return GBS_OK;
 }
