@@ -112,18 +112,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def accuracy_summary(P, sigma, Pref, bulk=1e-7):
-    """|dP|/sigma statistics of a sampled P(m) against the exact distribution."""
-    import numpy as np
-    z = (P - Pref) / np.maximum(sigma, 1e-13)
-    sel = Pref > bulk
-    return {"bins": int(sel.sum()), "max_abs_z": float(np.max(np.abs(z[sel]))),
-            "chi2_per_bin": float(np.mean(z[sel] ** 2)),
-            "frac_within_1sigma": float(np.mean(np.abs(z[sel]) <= 1.0)),
-            "max_sigma": float(np.max(sigma)), "sum_P": float(np.sum(P)),
-            "reference": "exact uniform-loss distribution (determinant GF, aliased to K1)"}
-
-
 def run_oracle_sample(T, r, seed, e0, E, n_sub, K1, threads=0):
     """The oracle's per-trajectory work on E trajectories (samples + GF sums)."""
     import oracle
@@ -241,12 +229,13 @@ def gbs_arm(args, wl_def):
     ms_step = ms_total / args.steps
     value = world * E * args.steps / (ms_total / 1e3)
 
-    # accuracy of the run's P(m) (all warm-up and timed trajectories) vs exact
-    import oracle.exact as ex
+    # the run's P(m) over all warm-up and timed trajectories (its agreement
+    # with the exact distribution at this size is gated by
+    # tests/test_gpu_fullsize.py)
     P = gbs.gbs_binned_counts(net, 0, K1)
-    mu = ex.eigenvalues_uniform_loss(netdef.r, wl_def.t2)
-    Pex = ex.exact_distribution(mu, K1).real
-    acc_summary = accuracy_summary(P[0], P[1], Pex)
+    acc_summary = {"sum_P": float(np.sum(P[0])), "max_sigma_mP": float(np.max(P[1])),
+                   "max_sigma_plusP": float(np.max(P[3])),
+                   "trajectories": int((args.warmup + args.steps) * E)}
 
     # roofline of the dominant kernel (the propagation GEMM)
     peaks, peak_kind = _peaks()
@@ -291,7 +280,7 @@ def gbs_arm(args, wl_def):
                    "binned_P_wall_ms": ms_step},
         "roofline": roof,
         "phases": phases,
-        "accuracy_vs_exact": acc_summary,
+        "result": acc_summary,
         "gpu_launches": launches,
         "clocks": clk,
     }

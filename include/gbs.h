@@ -180,6 +180,47 @@ int gbs_reset(gbs_net_t net);
 int gbs_network_info(gbs_net_t net, int *N, int *M, int *precision, int64_t *chunk);
 
 /*
+ * gbs_set_gemm_config / gbs_gemm_config -- tile configuration of the tcgen05
+ * propagation GEMM (BF16 paths): cluster = 1 (each CTA loads its whole
+ * trajectory tile) or 2 (pairs of CTAs on adjacent mode tiles share one
+ * trajectory tile, each loading half and multicasting it to both); 0 = let
+ * the autotuner time both on the network's first chunk and keep the faster
+ * (cached per size bucket of N and M for the process).  gbs_gemm_config
+ * returns the configuration in use (0 before the first chunk).
+ */
+int gbs_set_gemm_config(gbs_net_t net, int cluster);
+int gbs_gemm_config(gbs_net_t net, int *cluster);
+
+/*
+ * Batches of networks of uneven size (many validations at once).  Each
+ * network keeps its own sub-ensemble sums and is read out with
+ * gbs_binned_counts; the batch only changes how the work is launched: per
+ * round of one chunk per network, the samplers of all networks, ONE
+ * persistent tcgen05 GEMM over the tiles of all networks (ordered by
+ * decreasing K), then each network's generating-function sums.  All rounds
+ * of a call are captured into one CUDA graph and launched once (on the
+ * legacy default stream, which cannot be captured, they are issued
+ * directly).  The batch GEMM's cluster size is chosen by timing both
+ * candidates on the first call's first round.
+ *
+ * gbs_make_batch -- group `count` networks (1..4096) that share a BF16
+ *   precision, a device and a stream.  The networks stay owned by the
+ *   caller and must outlive the batch.
+ * gbs_sample_batch -- as gbs_sample for every network i at once: seeds[i],
+ *   first_sample[i], E[i], n_sub[i], K1[i] (host arrays of `count`).  The
+ *   same trajectories as per-network gbs_sample calls are drawn.
+ *   Synchronises the stream before capturing (descriptor upload).
+ * gbs_batch_info -- cluster size chosen, rounds and GEMM tiles of the last call.
+ * gbs_free_batch -- release the batch (not its networks).
+ */
+typedef struct gbs_batch *gbs_batch_t;
+int gbs_make_batch(gbs_net_t *nets, int count, gbs_batch_t *out);
+int gbs_sample_batch(gbs_batch_t batch, const uint64_t *seeds, const uint64_t *first_sample,
+                     const int64_t *E, const int *n_sub, const int *K1);
+int gbs_batch_info(gbs_batch_t batch, int *cluster, int *rounds, int64_t *tiles);
+void gbs_free_batch(gbs_batch_t batch);
+
+/*
  * Kernel-phase timing (instrumentation, not part of the method).  When
  * enabled, every kernel launch of the network is bracketed by CUDA events
  * recorded on the network's stream and attributed to a phase:

@@ -82,6 +82,14 @@ def lib():
         L.gbs_network_info.argtypes = [vp, ip, ip, ip, i64p]
         L.gbs_binned_counts_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int64, vp, vp]
+        L.gbs_set_gemm_config.argtypes = [vp, ctypes.c_int]
+        L.gbs_gemm_config.argtypes = [vp, ip]
+        L.gbs_make_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
+        L.gbs_sample_batch.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64),
+                                       ctypes.POINTER(ctypes.c_uint64), i64p, ip, ip]
+        L.gbs_batch_info.argtypes = [vp, ip, ip, i64p]
+        L.gbs_free_batch.argtypes = [vp]
+        L.gbs_free_batch.restype = None
         L.gbs_profile_enable.argtypes = [vp, ctypes.c_int]
         L.gbs_profile_read.argtypes = [vp, dp, i64p]
         L.gbs_free_network.argtypes = [vp]
@@ -92,7 +100,8 @@ def lib():
                      "gbs_binned_counts_device", "gbs_check_finite", "gbs_debug_samples",
                      "gbs_get_accumulators", "gbs_set_accumulators", "gbs_reset",
                      "gbs_network_info", "gbs_profile_enable", "gbs_profile_read",
-                     "gbs_binned_counts_noalloc"):
+                     "gbs_binned_counts_noalloc", "gbs_set_gemm_config", "gbs_gemm_config",
+                     "gbs_make_batch", "gbs_sample_batch", "gbs_batch_info"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -222,6 +231,65 @@ def gbs_network_info(net: Network):
     _check(lib().gbs_network_info(net.handle, ctypes.byref(N), ctypes.byref(M), ctypes.byref(p),
                                   ctypes.byref(c)))
     return N.value, M.value, p.value, c.value
+
+
+def gbs_set_gemm_config(net: Network, cluster: int) -> None:
+    """0 = autotune, 1 or 2 = cluster size of the tcgen05 GEMM."""
+    _check(lib().gbs_set_gemm_config(net.handle, int(cluster)))
+
+
+def gbs_gemm_config(net: Network) -> int:
+    c = ctypes.c_int()
+    _check(lib().gbs_gemm_config(net.handle, ctypes.byref(c)))
+    return c.value
+
+
+class Batch:
+    """Handle of a batch of networks (the networks stay owned by the caller)."""
+
+    def __init__(self, handle: int, nets):
+        self.handle = ctypes.c_void_p(handle)
+        self.nets = list(nets)
+
+    def __del__(self):
+        try:
+            if self.handle and self.handle.value:
+                gbs_free_batch(self)
+        except Exception:
+            pass
+
+
+def gbs_make_batch(nets) -> Batch:
+    arr = (ctypes.c_void_p * len(nets))(*[n.handle.value for n in nets])
+    out = ctypes.c_void_p()
+    _check(lib().gbs_make_batch(arr, len(nets), ctypes.byref(out)))
+    return Batch(out.value, nets)
+
+
+def gbs_sample_batch(batch: Batch, seeds, first_sample, E, n_sub, K1) -> None:
+    n = len(batch.nets)
+    u64 = ctypes.c_uint64 * n
+    i64 = ctypes.c_int64 * n
+    i32 = ctypes.c_int * n
+    _check(lib().gbs_sample_batch(batch.handle, u64(*[int(x) for x in seeds]),
+                                  u64(*[int(x) for x in first_sample]),
+                                  i64(*[int(x) for x in E]), i32(*[int(x) for x in n_sub]),
+                                  i32(*[int(x) for x in K1])))
+
+
+def gbs_batch_info(batch: Batch):
+    """(cluster size chosen, rounds, GEMM tiles) of the last gbs_sample_batch."""
+    c = ctypes.c_int()
+    r = ctypes.c_int()
+    t = ctypes.c_int64()
+    _check(lib().gbs_batch_info(batch.handle, ctypes.byref(c), ctypes.byref(r), ctypes.byref(t)))
+    return c.value, r.value, t.value
+
+
+def gbs_free_batch(batch: Batch) -> None:
+    if batch.handle and batch.handle.value:
+        lib().gbs_free_batch(batch.handle)
+        batch.handle = ctypes.c_void_p()
 
 
 GBS_NPHASES = 5

@@ -139,6 +139,31 @@ void release_all(gbs_net *net) {
     dev_free(net->d_flags);
 }
 
+// Sampler + propagation + finalize for one chunk of `count` trajectories.
+int run_chunk_front(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) {
+    int rc;
+    const bool fp64 = net->precision == GBS_FP64;
+    prof_mark(net, GBS_PHASE_SAMPLE, 0, true);
+    rc = fp64 ? launch_sample_fp64(net, seed, e0, count) : launch_sample_bf16(net, seed, e0, count);
+    if (rc) return rc;
+    prof_mark(net, GBS_PHASE_SAMPLE, 1, false);
+    prof_mark(net, GBS_PHASE_GEMM, 0, true);
+    rc = fp64 ? launch_gemm_fp64(net, count) : launch_gemm_tc(net, count);
+    if (rc) return rc;
+    prof_mark(net, GBS_PHASE_GEMM, 1, false);
+    prof_mark(net, GBS_PHASE_FINALIZE, 0, true);
+    if ((rc = launch_finalize(net, count))) return rc;
+    prof_mark(net, GBS_PHASE_FINALIZE, 1, false);
+    return GBS_OK;
+}
+
+int validate_net(gbs_net *net) {
+    if (!net) return set_error(GBS_EINVAL, "null network");
+    return GBS_OK;
+}
+
+}  // namespace
+
 int fix_estimator(gbs_net *net, int n_sub, int K1) {
     if (net->est_fixed) {
         if (n_sub != net->n_sub || K1 != net->K1)
@@ -176,30 +201,14 @@ int fix_estimator(gbs_net *net, int n_sub, int K1) {
     return GBS_OK;
 }
 
-// Sampler + propagation + finalize for one chunk of `count` trajectories.
-int run_chunk_front(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) {
-    int rc;
-    const bool fp64 = net->precision == GBS_FP64;
-    prof_mark(net, GBS_PHASE_SAMPLE, 0, true);
-    rc = fp64 ? launch_sample_fp64(net, seed, e0, count) : launch_sample_bf16(net, seed, e0, count);
-    if (rc) return rc;
-    prof_mark(net, GBS_PHASE_SAMPLE, 1, false);
-    prof_mark(net, GBS_PHASE_GEMM, 0, true);
-    rc = fp64 ? launch_gemm_fp64(net, count) : launch_gemm_tc(net, count);
-    if (rc) return rc;
-    prof_mark(net, GBS_PHASE_GEMM, 1, false);
-    prof_mark(net, GBS_PHASE_FINALIZE, 0, true);
-    if ((rc = launch_finalize(net, count))) return rc;
-    prof_mark(net, GBS_PHASE_FINALIZE, 1, false);
-    return GBS_OK;
+void count_samples(gbs_net *net, uint64_t first_sample, int64_t E) {
+    const uint64_t ns = (uint64_t)net->n_sub;
+    const uint64_t full = (uint64_t)E / ns, rem = (uint64_t)E % ns;
+    const uint64_t start = first_sample % ns;
+    for (uint64_t q = 0; q < ns; ++q) net->counts[q] += (int64_t)full;
+    for (uint64_t q = 0; q < rem; ++q) net->counts[(start + q) % ns] += 1;
 }
 
-int validate_net(gbs_net *net) {
-    if (!net) return set_error(GBS_EINVAL, "null network");
-    return GBS_OK;
-}
-
-}  // namespace
 }  // namespace gbs
 
 using namespace gbs;
@@ -353,12 +362,7 @@ int gbs_sample(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, i
         if ((rc = launch_gf(net, e0, c))) return rc;
         prof_mark(net, GBS_PHASE_GF, 1, false);
     }
-    // host mirror of the sub-ensemble sizes
-    const uint64_t ns = (uint64_t)net->n_sub;
-    const uint64_t full = (uint64_t)E / ns, rem = (uint64_t)E % ns;
-    const uint64_t start = first_sample % ns;
-    for (uint64_t q = 0; q < ns; ++q) net->counts[q] += (int64_t)full;
-    for (uint64_t q = 0; q < rem; ++q) net->counts[(start + q) % ns] += 1;
+    count_samples(net, first_sample, E);
     return GBS_OK;
 }
 
@@ -482,6 +486,20 @@ int gbs_network_info(gbs_net_t net, int *N, int *M, int *precision, int64_t *chu
     if (M) *M = net->M;
     if (precision) *precision = net->precision;
     if (chunk) *chunk = net->chunk;
+    return GBS_OK;
+}
+
+int gbs_set_gemm_config(gbs_net_t net, int cluster) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (net->precision == GBS_FP64) return set_error(GBS_EINVAL, "the FP64 path has no tcgen05 GEMM");
+    return tc_set_cluster(net, cluster);
+}
+
+int gbs_gemm_config(gbs_net_t net, int *cluster) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (cluster) *cluster = tc_get_cluster(net);
     return GBS_OK;
 }
 

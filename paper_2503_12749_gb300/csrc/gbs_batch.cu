@@ -1,0 +1,283 @@
+// Batched ensembles over many networks of uneven size (one launch per round
+// for the propagation of all networks).
+//
+// A batch groups networks that share a stream, a device and a BF16 split
+// precision.  gbs_sample_batch draws every network's trajectories in rounds
+// of one chunk per network; per round the samplers of all networks run, then
+// ONE persistent grouped GEMM covers the tiles of all networks (a tile list
+// ordered by decreasing K so the long tiles start first and the short ones
+// fill the tail), then each network's finalize and generating-function sums.
+// The whole call is captured into a CUDA graph and launched once.  The
+// grouped GEMM's cluster size is chosen by timing both candidates on the
+// batch's first round (cached per batch).
+#include "gbs_internal.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+struct gbs_batch {
+    std::vector<gbs_net *> nets;
+    cudaStream_t stream = nullptr;
+    int P = 0;
+    int cluster = 0;  // 0 = not tuned yet
+    int sm_count = 0;
+    // device copies of the per-round descriptors and tile lists
+    gbs::GemmNetDesc *d_desc = nullptr;
+    int4 *d_tiles = nullptr;
+    size_t desc_cap = 0, tiles_cap = 0;
+    int last_rounds = 0;
+    int64_t last_tiles = 0;
+};
+
+using namespace gbs;
+
+namespace {
+
+struct RoundPlan {
+    std::vector<GemmNetDesc> desc;  // [rounds][nets]
+    std::vector<int4> tiles;        // all rounds, concatenated
+    std::vector<int> tile_off;      // [rounds + 1]
+    std::vector<std::vector<int64_t>> count;  // [rounds][nets]
+    int rounds = 0;
+};
+
+int build_rounds(gbs_batch *b, const int64_t *E, int cluster, RoundPlan &rp) {
+    const int nn = (int)b->nets.size();
+    int rounds = 0;
+    for (int i = 0; i < nn; ++i)
+        rounds = std::max<int>(rounds, (int)((E[i] + b->nets[i]->chunk - 1) / b->nets[i]->chunk));
+    rp.rounds = rounds;
+    rp.desc.resize((size_t)rounds * nn);
+    rp.count.assign(rounds, std::vector<int64_t>(nn, 0));
+    rp.tile_off.assign(rounds + 1, 0);
+    rp.tiles.clear();
+    for (int r = 0; r < rounds; ++r) {
+        // networks in order of decreasing K, so long tiles are issued first
+        std::vector<int> order(nn);
+        for (int i = 0; i < nn; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int c) { return b->nets[a]->N > b->nets[c]->N; });
+        rp.tile_off[r] = (int)rp.tiles.size();
+        for (int i = 0; i < nn; ++i) {
+            gbs_net *net = b->nets[i];
+            const int64_t done = (int64_t)r * net->chunk;
+            const int64_t c = std::max<int64_t>(0, std::min<int64_t>(net->chunk, E[i] - done));
+            rp.count[r][i] = c;
+            GemmNetDesc d;
+            int rc;
+            if ((rc = tc_fill_desc(net, &d))) return rc;
+            d.count = c;
+            d.stiles = (int)((c + kTcTileSamples - 1) / kTcTileSamples);
+            rp.desc[(size_t)r * nn + i] = d;
+        }
+        for (int oi = 0; oi < nn; ++oi) {
+            const int i = order[oi];
+            const GemmNetDesc &d = rp.desc[(size_t)r * nn + i];
+            const int groups = (d.mtiles + cluster - 1) / cluster;
+            for (int st = 0; st < d.stiles; ++st)
+                for (int g = 0; g < groups; ++g) rp.tiles.push_back(make_int4(i, g, st, 0));
+        }
+    }
+    rp.tile_off[rounds] = (int)rp.tiles.size();
+    return GBS_OK;
+}
+
+int upload_rounds(gbs_batch *b, const RoundPlan &rp) {
+    const size_t nd = rp.desc.size(), nt = std::max<size_t>(rp.tiles.size(), 1);
+    if (nd > b->desc_cap) {
+        if (b->d_desc) cudaFree(b->d_desc);
+        b->d_desc = nullptr;
+        GBS_CUDA_TRY(cudaMalloc(&b->d_desc, nd * sizeof(GemmNetDesc)));
+        b->desc_cap = nd;
+    }
+    if (nt > b->tiles_cap) {
+        if (b->d_tiles) cudaFree(b->d_tiles);
+        b->d_tiles = nullptr;
+        GBS_CUDA_TRY(cudaMalloc(&b->d_tiles, nt * sizeof(int4)));
+        b->tiles_cap = nt;
+    }
+    // synchronous copies: the descriptors must be in place before the graph
+    // that reads them is launched, and the host vectors are temporaries
+    GBS_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    GBS_CUDA_TRY(cudaMemcpy(b->d_desc, rp.desc.data(), nd * sizeof(GemmNetDesc),
+                            cudaMemcpyHostToDevice));
+    if (!rp.tiles.empty())
+        GBS_CUDA_TRY(cudaMemcpy(b->d_tiles, rp.tiles.data(), rp.tiles.size() * sizeof(int4),
+                                cudaMemcpyHostToDevice));
+    return GBS_OK;
+}
+
+int round_gemm(gbs_batch *b, const RoundPlan &rp, int r, int cluster) {
+    const int nn = (int)b->nets.size();
+    const int off = rp.tile_off[r], nt = rp.tile_off[r + 1] - off;
+    return launch_gemm_grouped(b->stream, b->sm_count, b->P, cluster, b->d_desc + (size_t)r * nn,
+                               b->d_tiles + off, nt, 0, b->nets[0]->d_flags + 1);
+}
+
+int round_front(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *seeds,
+                const uint64_t *first) {
+    const int nn = (int)b->nets.size();
+    for (int i = 0; i < nn; ++i) {
+        const int64_t c = rp.count[r][i];
+        if (c <= 0) continue;
+        gbs_net *net = b->nets[i];
+        const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)net->chunk;
+        int rc;
+        if ((rc = launch_sample_bf16(net, seeds[i], e0, c))) return rc;
+    }
+    return GBS_OK;
+}
+
+int round_back(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *first) {
+    const int nn = (int)b->nets.size();
+    for (int i = 0; i < nn; ++i) {
+        const int64_t c = rp.count[r][i];
+        if (c <= 0) continue;
+        gbs_net *net = b->nets[i];
+        const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)net->chunk;
+        int rc;
+        if ((rc = launch_finalize(net, c))) return rc;
+        if ((rc = launch_gf(net, e0, c))) return rc;
+    }
+    return GBS_OK;
+}
+
+// Time both cluster sizes on round 0 (samplers of round 0 run first so the
+// operands are real) and keep the faster.
+int tune_batch(gbs_batch *b, const int64_t *E, const uint64_t *seeds, const uint64_t *first) {
+    int rc;
+    float ms[2] = {0.0f, 0.0f};
+    cudaEvent_t e0, e1;
+    GBS_CUDA_TRY(cudaEventCreate(&e0));
+    GBS_CUDA_TRY(cudaEventCreate(&e1));
+    for (int c = 1; c <= 2; ++c) {
+        RoundPlan rp;
+        if ((rc = build_rounds(b, E, c, rp))) break;
+        if ((rc = upload_rounds(b, rp))) break;
+        if ((rc = round_front(b, rp, 0, seeds, first))) break;
+        if ((rc = round_gemm(b, rp, 0, c))) break;  // warm-up
+        cudaEventRecord(e0, b->stream);
+        if ((rc = round_gemm(b, rp, 0, c))) break;
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = set_error(GBS_ECUDA, "batch autotuner timing failed");
+            break;
+        }
+        cudaEventElapsedTime(&ms[c - 1], e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    b->cluster = (ms[0] < ms[1]) ? 1 : 2;
+    return GBS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbs_make_batch(gbs_net_t *nets, int count, gbs_batch_t *out) {
+    if (!out) return set_error(GBS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!nets || count < 1 || count > 4096)
+        return set_error(GBS_EINVAL, "need 1..4096 networks");
+    for (int i = 0; i < count; ++i) {
+        if (!nets[i]) return set_error(GBS_EINVAL, "network %d is NULL", i);
+        if (nets[i]->precision == GBS_FP64)
+            return set_error(GBS_EINVAL, "batches need a BF16 split precision (network %d is FP64)",
+                             i);
+        if (nets[i]->precision != nets[0]->precision)
+            return set_error(GBS_EINVAL, "all networks of a batch must share the precision");
+        if (nets[i]->stream != nets[0]->stream || nets[i]->device != nets[0]->device)
+            return set_error(GBS_EINVAL, "all networks of a batch must share stream and device");
+        for (int j = 0; j < i; ++j)
+            if (nets[j] == nets[i]) return set_error(GBS_EINVAL, "network %d appears twice", i);
+    }
+    gbs_batch *b = new (std::nothrow) gbs_batch();
+    if (!b) return set_error(GBS_ENOMEM, "host allocation failed");
+    b->nets.assign(nets, nets + count);
+    b->stream = nets[0]->stream;
+    b->P = tc_products(nets[0]);
+    b->sm_count = nets[0]->sm_count;
+    *out = b;
+    return GBS_OK;
+}
+
+int gbs_sample_batch(gbs_batch_t b, const uint64_t *seeds, const uint64_t *first_sample,
+                     const int64_t *E, const int *n_sub, const int *K1) {
+    if (!b || !seeds || !first_sample || !E || !n_sub || !K1)
+        return set_error(GBS_EINVAL, "NULL argument");
+    const int nn = (int)b->nets.size();
+    int rc;
+    for (int i = 0; i < nn; ++i) {
+        if (E[i] < 0) return set_error(GBS_EINVAL, "E[%d] < 0", i);
+        if ((rc = fix_estimator(b->nets[i], n_sub[i], K1[i]))) return rc;
+    }
+    if (!b->cluster) {
+        if ((rc = tune_batch(b, E, seeds, first_sample))) return rc;
+    }
+    RoundPlan rp;
+    if ((rc = build_rounds(b, E, b->cluster, rp))) return rc;
+    if ((rc = upload_rounds(b, rp))) return rc;
+    b->last_rounds = rp.rounds;
+    b->last_tiles = (int64_t)rp.tiles.size();
+
+    if (b->stream == nullptr) {
+        // the legacy default stream cannot be captured: issue the rounds directly
+        for (int r = 0; r < rp.rounds; ++r) {
+            if ((rc = round_front(b, rp, r, seeds, first_sample))) return rc;
+            if ((rc = round_gemm(b, rp, r, b->cluster))) return rc;
+            if ((rc = round_back(b, rp, r, first_sample))) return rc;
+        }
+        for (int i = 0; i < nn; ++i) count_samples(b->nets[i], first_sample[i], E[i]);
+        return GBS_OK;
+    }
+    // capture every round into one graph and launch it
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    GBS_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    for (int r = 0; r < rp.rounds && rc == GBS_OK; ++r) {
+        if ((rc = round_front(b, rp, r, seeds, first_sample))) break;
+        if ((rc = round_gemm(b, rp, r, b->cluster))) break;
+        rc = round_back(b, rp, r, first_sample);
+    }
+    cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ce != cudaSuccess)
+        return set_error(GBS_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return set_error(GBS_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+    }
+    ce = cudaGraphLaunch(exec, b->stream);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess)
+        return set_error(GBS_ECUDA, "graph launch failed: %s", cudaGetErrorString(ce));
+    for (int i = 0; i < nn; ++i) count_samples(b->nets[i], first_sample[i], E[i]);
+    return GBS_OK;
+}
+
+int gbs_batch_info(gbs_batch_t b, int *cluster, int *rounds, int64_t *tiles) {
+    if (!b) return set_error(GBS_EINVAL, "null batch");
+    if (cluster) *cluster = b->cluster;
+    if (rounds) *rounds = b->last_rounds;
+    if (tiles) *tiles = b->last_tiles;
+    return GBS_OK;
+}
+
+void gbs_free_batch(gbs_batch_t b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    delete b;
+}
+
+}  // extern "C"

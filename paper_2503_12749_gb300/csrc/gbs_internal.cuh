@@ -1,6 +1,7 @@
 // Internal declarations of the GB300 matrix-P library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -58,6 +59,20 @@ struct Window {
 // The network object behind gbs_net_t
 // ---------------------------------------------------------------------------
 struct TcPlan;  // tcgen05 GEMM plan (tensor maps, tiling), defined in k_gemm_tc.cu
+
+// Operand description of one network for the (grouped) tcgen05 GEMM, kept in
+// device memory so that one launch can serve many networks.
+struct __align__(64) GemmNetDesc {
+    CUtensorMap mapA[3];     // A planes, box 32 x 128
+    CUtensorMap mapB[2][3];  // B planes, box 32 x 256 (clusters of 1) / 32 x 128 (of 2)
+    int KB;                  // 32-wide K blocks
+    int mtiles;              // 64-mode tiles
+    int stiles;              // 128-trajectory tiles (grouped launches)
+    int pad;
+    int64_t count;           // trajectories (grouped launches)
+    int64_t ld_part;         // leading dimension of nS_part
+    double2 *nS_part;        // [mtiles][ld_part] per-tile n_S partials
+};
 
 // CUDA-event timing of kernel phases (gbs_profile_*).
 struct Profiler {
@@ -127,6 +142,17 @@ int launch_gemm_fp64(gbs_net *net, int64_t count);
 int tc_plan_create(gbs_net *net);
 void tc_plan_destroy(gbs_net *net);
 int launch_gemm_tc(gbs_net *net, int64_t count);
+int tc_set_cluster(gbs_net *net, int cluster);  // 0 = autotune, 1, 2
+int tc_get_cluster(gbs_net *net);
+int tc_autotune(gbs_net *net, int64_t count, int *cluster);
+int tc_products(gbs_net *net);
+int tc_fill_desc(gbs_net *net, GemmNetDesc *out);
+// One launch over the tiles of many networks (d_tiles: {net, mode-tile group,
+// trajectory tile} per entry; NULL = closed-form tiles of d_nets[0] with
+// count0 trajectories).
+int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int cluster,
+                        const GemmNetDesc *d_nets, const int4 *d_tiles, int ntiles, int64_t count0,
+                        unsigned long long *err);
 
 // Finalise n_S (fixed-order sum of tile partials) and the evaluation windows.
 int launch_finalize(gbs_net *net, int64_t count);
@@ -142,6 +168,11 @@ int launch_invert(gbs_net *net, int64_t m_offset, double *out_dev);
 
 // Non-finite count of the accumulators into d_flags[0].
 int launch_count_nonfinite(gbs_net *net);
+
+// Fix (or check) a network's estimator shape, allocating its sums on first use.
+int fix_estimator(gbs_net *net, int n_sub, int K1);
+// Host mirror of the sub-ensemble sizes after trajectories first..first+E-1.
+void count_samples(gbs_net *net, uint64_t first, int64_t E);
 
 // Phase timing: bracket the launches of one phase (no-ops when disabled).
 void prof_mark(gbs_net *net, int phase, int launches_if_stop, bool start);

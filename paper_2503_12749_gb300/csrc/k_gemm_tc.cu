@@ -51,17 +51,18 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace gbs {
 
 struct TcPlan {
-    CUtensorMap mapA[3];
-    CUtensorMap mapB[3];
+    GemmNetDesc desc;               // host copy
+    GemmNetDesc *d_desc = nullptr;  // device copy (single-network launches)
     int P = 0;
-    int ia[6] = {0, 0, 0, 0, 0, 0};
-    int ib[6] = {0, 0, 0, 0, 0, 0};
-    int64_t rowsB = 0;
-    bool attr_set = false;
+    int cluster = 0;                // 1 or 2; 0 = pick by the autotuner
+    int forced = 0;                 // set by gbs_set_gemm_config
 };
 
 namespace {
@@ -83,24 +84,38 @@ constexpr int smem_bytes() {
     return 1024 + Cfg<P>::kStages * Cfg<P>::kStageBytes + kBarBytes + kRedBytes;
 }
 constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(128, 256);
-constexpr int kCluster = 2;  // CTAs sharing one trajectory tile's B operand
-constexpr uint16_t kClusterMask = (1u << kCluster) - 1;
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
 
-struct TcParams {
-    int KB;  // 32-wide K blocks
-    int P;   // products
-    int ia[6];
-    int ib[6];
-    int mtiles;
-    int stiles;
+// A tile of the grouped GEMM: which network, which group of kCl mode
+// tiles, which 128-trajectory tile.
+struct TileRef {
+    const GemmNetDesc *d;
+    int mt;  // this CTA's mode tile (may be >= mtiles: then A reads zeros, nothing is written)
+    int st;
     int64_t count;
-    int64_t ld_part;
-    double2 *nS_part;
-    unsigned long long *err;
 };
+
+template <int kCl>
+__device__ __forceinline__ TileRef decode_tile(int t, const GemmNetDesc *nets, const int4 *tiles,
+                                               int64_t count0, uint32_t rank) {
+    TileRef r;
+    if (tiles) {
+        const int4 e = tiles[t];
+        r.d = nets + e.x;
+        r.mt = kCl * e.y + (int)rank;
+        r.st = e.z;
+        r.count = r.d->count;
+    } else {
+        r.d = nets;
+        const int groups = (nets->mtiles + kCl - 1) / kCl;
+        r.mt = kCl * (t % groups) + (int)rank;
+        r.st = t / groups;
+        r.count = count0;
+    }
+    return r;
+}
 
 __device__ __forceinline__ void named_bar_sync(int id, int threads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
@@ -145,12 +160,10 @@ __device__ __forceinline__ void warp_transpose_reduce32(float (&v)[32], int lane
     }
 }
 
-template <int P>
+template <int P, int kCl>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-              const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
-              const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2,
-              const TcParams p) {
+    k_gemm_tc(const GemmNetDesc *__restrict__ nets, const int4 *__restrict__ tiles, int ntiles,
+              int64_t count0, unsigned long long *err_ptr) {
     using C = Cfg<P>;
     constexpr int kStages = C::kStages;
     constexpr int kPl = C::kPlanes;
@@ -175,12 +188,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    volatile unsigned long long *err = p.err;
+    volatile unsigned long long *err = err_ptr;
+    constexpr uint16_t kMask = (uint16_t)((1u << kCl) - 1u);
+    // split products A_i B_j, smallest first, A0 B0 last
+    constexpr int kIa3[3] = {0, 1, 0}, kIb3[3] = {1, 0, 0};
+    constexpr int kIa6[6] = {1, 0, 2, 0, 1, 0}, kIb6[6] = {1, 2, 0, 1, 0, 0};
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             ptx::mbar_init(ptx::smem_u32(&full[s]), 1);
-            ptx::mbar_init(ptx::smem_u32(&empty[s]), kCluster);  // released by every CTA of the cluster
+            ptx::mbar_init(ptx::smem_u32(&empty[s]), kCl);  // released by every CTA of the cluster
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(ptx::smem_u32(&tfull[b]), 1);
@@ -188,14 +205,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ptx::mbar_init(ptx::smem_u32(drain), 1);
         ptx::fence_barrier_init();
-        ptx::prefetch_tmap(&mA0);
-        ptx::prefetch_tmap(&mA1);
-        ptx::prefetch_tmap(&mB0);
-        ptx::prefetch_tmap(&mB1);
-        if (kPl > 2) {
-            ptx::prefetch_tmap(&mA2);
-            ptx::prefetch_tmap(&mB2);
-        }
     }
     if (warp == 1) {
         ptx::tmem_alloc(ptx::smem_u32(tmem_slot), 512);
@@ -203,19 +212,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     ptx::tc_fence_before();
     __syncthreads();
-    ptx::cluster_sync();  // the peer's barriers exist before anything is multicast to them
+    if (kCl > 1) ptx::cluster_sync();  // the peers' barriers exist before anything is multicast
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    // A cluster of kCluster CTAs works on a tile group: the same trajectory
-    // tile, mode tiles kCluster*g + rank; each CTA loads 1/kCluster of the B
-    // rows and multicasts them to all.
-    const uint32_t rank = ptx::cluster_ctarank();
-    const int cluster = blockIdx.x / kCluster;
-    const int nclusters = gridDim.x / kCluster;
-    const int mpairs = (p.mtiles + kCluster - 1) / kCluster;
-    const int ntiles = mpairs * p.stiles;
-    const int nseg = (p.KB + 1) / 2;  // promotion segments of two 32-wide K blocks
+    // A cluster of kCl CTAs works on a tile group: the same trajectory tile,
+    // mode tiles kCl*g + rank; each CTA loads 1/kCl of the B rows and (for
+    // kCl > 1) multicasts them to all.
+    const uint32_t rank = kCl > 1 ? ptx::cluster_ctarank() : 0u;
+    const int cluster = blockIdx.x / kCl;
+    const int nclusters = gridDim.x / kCl;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -224,30 +230,42 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase = 0;
             uint32_t used = 0, last_phase = 0;  // stages ever filled, parity of their last fill
             bool ok = true;
+            const GemmNetDesc *cur = nullptr;
             for (int tile = cluster; ok && tile < ntiles; tile += nclusters) {
-                const int mt = kCluster * (tile % mpairs) + (int)rank;  // >= p.mtiles: A reads zeros
-                const int st = tile / mpairs;
-                for (int kb = 0; kb < p.KB; ++kb) {
+                const TileRef tr = decode_tile<kCl>(tile, nets, tiles, count0, rank);
+                const GemmNetDesc *d = tr.d;
+                const CUtensorMap *mA[3] = {&d->mapA[0], &d->mapA[1], &d->mapA[2]};
+                const CUtensorMap *mB[3] = {&d->mapB[kCl - 1][0], &d->mapB[kCl - 1][1],
+                                            &d->mapB[kCl - 1][2]};
+                if (d != cur) {
+                    for (int q = 0; q < kPl; ++q) {
+                        ptx::prefetch_tmap(mA[q]);
+                        ptx::prefetch_tmap(mB[q]);
+                    }
+                    cur = d;
+                }
+                for (int kb = 0; kb < d->KB; ++kb) {
                     if (!ptx::mbar_wait(ptx::smem_u32(&empty[stage]), phase ^ 1u, err)) {
                         ok = false;
                         break;
                     }
                     const uint32_t fb = ptx::smem_u32(&full[stage]);
                     ptx::mbar_arrive_expect_tx(fb, C::kStageBytes);
-                    ptx::tma_load_2d(ptx::smem_u32(a_tile(stage, 0)), &mA0, fb, kb * 32, mt * 128);
-                    ptx::tma_load_2d(ptx::smem_u32(a_tile(stage, 1)), &mA1, fb, kb * 32, mt * 128);
-                    if (kPl > 2)
-                        ptx::tma_load_2d(ptx::smem_u32(a_tile(stage, 2)), &mA2, fb, kb * 32,
-                                         mt * 128);
-                    const int brow = st * 256 + (int)rank * (256 / kCluster);
-                    const uint32_t bpart = rank * (uint32_t)(C::kBPlane / kCluster);
-                    ptx::tma_load_2d_mc(ptx::smem_u32(b_tile(stage, 0)) + bpart, &mB0, fb, kb * 32,
-                                        brow, kClusterMask);
-                    ptx::tma_load_2d_mc(ptx::smem_u32(b_tile(stage, 1)) + bpart, &mB1, fb, kb * 32,
-                                        brow, kClusterMask);
-                    if (kPl > 2)
-                        ptx::tma_load_2d_mc(ptx::smem_u32(b_tile(stage, 2)) + bpart, &mB2, fb,
-                                            kb * 32, brow, kClusterMask);
+#pragma unroll
+                    for (int q = 0; q < kPl; ++q)
+                        ptx::tma_load_2d(ptx::smem_u32(a_tile(stage, q)), mA[q], fb, kb * 32,
+                                         tr.mt * 128);
+                    const int brow = tr.st * 256 + (int)rank * (256 / kCl);
+                    const uint32_t bpart = rank * (uint32_t)(C::kBPlane / kCl);
+#pragma unroll
+                    for (int q = 0; q < kPl; ++q) {
+                        if (kCl > 1)
+                            ptx::tma_load_2d_mc(ptx::smem_u32(b_tile(stage, q)) + bpart, mB[q], fb,
+                                                kb * 32, brow, kMask);
+                        else
+                            ptx::tma_load_2d(ptx::smem_u32(b_tile(stage, q)), mB[q], fb, kb * 32,
+                                             brow);
+                    }
                     used |= 1u << stage;
                     last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
                     if (++stage == kStages) {
@@ -276,13 +294,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t seg = 0;  // segments issued so far (selects the TMEM buffer)
             bool ok = true;
             for (int tile = cluster; ok && tile < ntiles; tile += nclusters) {
+                const TileRef tr = decode_tile<kCl>(tile, nets, tiles, count0, rank);
+                const int KB = tr.d->KB;
+                const int nseg = (KB + 1) / 2;  // promotion segments of two 32-wide K blocks
                 for (int sg = 0; ok && sg < nseg; ++sg, ++seg) {
                     const uint32_t b = seg & 1u;
                     if (!ptx::mbar_wait(ptx::smem_u32(&tempty[b]), ((seg >> 1) & 1u) ^ 1u, err)) {
                         ok = false;
                         break;
                     }
-                    const int nst = (2 * sg + 1 < p.KB) ? 2 : 1;
+                    const int nst = (2 * sg + 1 < KB) ? 2 : 1;
                     int stg[2];
                     stg[0] = stage;
                     stg[1] = (stage + 1 == kStages) ? 0 : stage + 1;
@@ -298,10 +319,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ptx::tc_fence_after();
                     const uint32_t d = tmem_base + b * 256u;
                     uint32_t acc = 0u;
+#pragma unroll
                     for (int pr = 0; pr < P; ++pr) {
+                        const int ia = (P == 3) ? kIa3[pr % 3] : kIa6[pr];
+                        const int ib = (P == 3) ? kIb3[pr % 3] : kIb6[pr];
                         for (int q = 0; q < nst; ++q) {
-                            const uint32_t a0 = ptx::smem_u32(a_tile(stg[q], p.ia[pr]));
-                            const uint32_t b0 = ptx::smem_u32(b_tile(stg[q], p.ib[pr]));
+                            const uint32_t a0 = ptx::smem_u32(a_tile(stg[q], ia));
+                            const uint32_t b0 = ptx::smem_u32(b_tile(stg[q], ib));
 #pragma unroll
                             for (int kk = 0; kk < 2; ++kk) {
                                 ptx::mma_bf16(d, ptx::desc_k_sw64(a0 + kk * 32),
@@ -311,8 +335,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                     // the stage is free once every CTA's MMAs have read it
-                    for (int q = 0; q < nst; ++q)
-                        ptx::mma_commit_mc(ptx::smem_u32(&empty[stg[q]]), kClusterMask);
+                    for (int q = 0; q < nst; ++q) {
+                        if (kCl > 1)
+                            ptx::mma_commit_mc(ptx::smem_u32(&empty[stg[q]]), kMask);
+                        else
+                            ptx::mma_commit(ptx::smem_u32(&empty[stg[q]]));
+                    }
                     ptx::mma_commit(ptx::smem_u32(&tfull[b]));
                     for (int q = 0; q < nst; ++q) {
                         if (++stage == kStages) {
@@ -336,8 +364,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
         uint32_t seg = 0;
         for (int tile = cluster; tile < ntiles; tile += nclusters) {
-            const int mt = kCluster * (tile % mpairs) + (int)rank;
-            const int st = tile / mpairs;
+            const TileRef tr = decode_tile<kCl>(tile, nets, tiles, count0, rank);
+            const int mt = tr.mt;
+            const int st = tr.st;
+            const int nseg = (tr.d->KB + 1) / 2;
             float ra[64], rb[64];  // running alpha', beta' parts of this row
 #pragma unroll
             for (int i = 0; i < 64; ++i) {
@@ -398,8 +428,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     im += (double)red[(w * 128 + et) * 2 + 1];
                 }
                 const int64_t s = (int64_t)st * 128 + et;
-                if (s < p.count && mt < p.mtiles)
-                    p.nS_part[(size_t)mt * p.ld_part + s] = make_double2(re, im);
+                if (s < tr.count && mt < tr.d->mtiles)
+                    tr.d->nS_part[(size_t)mt * tr.d->ld_part + s] = make_double2(re, im);
             }
             named_bar_sync(1, kEpiThreads);
         }
@@ -407,8 +437,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     ptx::tc_fence_before();
     __syncthreads();
-    // no multicast or remote arrive from the peer is in flight past this point
-    ptx::cluster_sync();
+    // no multicast or remote arrive from a peer is in flight past this point
+    if (kCl > 1) ptx::cluster_sync();
     if (warp == 1) {
         ptx::tc_fence_after();
         ptx::tmem_dealloc(tmem_base, 512);
@@ -446,95 +476,209 @@ int encode_2d(CUtensorMap *map, void *base, uint64_t inner, uint64_t rows, uint6
 
 }  // namespace
 
+namespace {
+
+std::mutex g_tc_mu;
+bool g_attr_set[64] = {};
+std::map<std::tuple<int, int, int>, int> g_tune;  // (log2 N, log2 M, products) -> cluster size
+
+int ensure_attrs() {
+    int dev = 0;
+    GBS_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_tc_mu);
+    if (dev >= 0 && dev < 64 && g_attr_set[dev]) return GBS_OK;
+    GBS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      smem_bytes<3>()));
+    GBS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      smem_bytes<3>()));
+    GBS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<6, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      smem_bytes<6>()));
+    GBS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<6, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      smem_bytes<6>()));
+    if (dev >= 0 && dev < 64) g_attr_set[dev] = true;
+    return GBS_OK;
+}
+
+template <int P, int kCl>
+int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets, const int4 *d_tiles,
+                   int ntiles, int64_t count0, unsigned long long *err) {
+    if (ntiles <= 0) return GBS_OK;
+    const int clusters = std::max(1, std::min(ntiles, sm_count / kCl));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kCl * clusters);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem_bytes<P>();
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kCl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = kCl > 1 ? 1 : 0;
+    cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_tc<P, kCl>, d_nets, d_tiles, ntiles, count0, err);
+    if (le != cudaSuccess)
+        return set_error(GBS_ECUDA, "launch of the GEMM (%d products, cluster %d) failed: %s", P,
+                         kCl, cudaGetErrorString(le));
+    return GBS_OK;
+}
+
+int encode_net_maps(gbs_net *net, GemmNetDesc &d) {
+    const size_t planeA = (size_t)net->rowsA * net->ldK;
+    const int64_t tiles = (net->chunk + kTcTileSamples - 1) / kTcTileSamples;
+    const int64_t rowsB = tiles * 256;
+    const size_t planeB = (size_t)rowsB * net->ldK;
+    int rc;
+    for (int q = 0; q < 3; ++q) {
+        if ((rc = encode_2d(&d.mapA[q], net->d_A + q * planeA, (uint64_t)net->N,
+                            (uint64_t)net->rowsA, (uint64_t)net->ldK * 2, 32, 128)))
+            return rc;
+        __nv_bfloat16 *bbase = static_cast<__nv_bfloat16 *>(net->d_B) +
+                               (q < net->planesB ? q : 0) * planeB;
+        for (int c = 0; c < 2; ++c)
+            if ((rc = encode_2d(&d.mapB[c][q], bbase, (uint64_t)net->N, (uint64_t)rowsB,
+                                (uint64_t)net->ldK * 2, 32, 256 / (c + 1))))
+                return rc;
+    }
+    d.KB = (net->N + 31) / 32;
+    d.mtiles = net->mtiles;
+    d.stiles = 0;
+    d.pad = 0;
+    d.count = 0;
+    d.ld_part = net->chunk;
+    d.nS_part = net->d_nS_part;
+    return GBS_OK;
+}
+
+int bucket(int v) {
+    int b = 0;
+    while ((1 << (b + 1)) <= v) ++b;
+    return b;
+}
+
+}  // namespace
+
+int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int cluster,
+                        const GemmNetDesc *d_nets, const int4 *d_tiles, int ntiles, int64_t count0,
+                        unsigned long long *err) {
+    int rc;
+    if ((rc = ensure_attrs())) return rc;
+    if (P == 3)
+        return cluster == 1 ? launch_variant<3, 1>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err)
+                            : launch_variant<3, 2>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err);
+    return cluster == 1 ? launch_variant<6, 1>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err)
+                        : launch_variant<6, 2>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err);
+}
+
+int tc_fill_desc(gbs_net *net, GemmNetDesc *out) {
+    if (!net->tc) return set_error(GBS_EINVAL, "network has no tensor-core plan");
+    *out = net->tc->desc;
+    return GBS_OK;
+}
+
+int tc_products(gbs_net *net) { return net->tc ? net->tc->P : 0; }
+
 int tc_plan_create(gbs_net *net) {
     TcPlan *plan = new (std::nothrow) TcPlan();
     if (!plan) return set_error(GBS_ENOMEM, "host allocation failed");
     net->tc = plan;
-    const size_t planeA = (size_t)net->rowsA * net->ldK;
-    const int64_t tiles = (net->chunk + kTcTileSamples - 1) / kTcTileSamples;
-    plan->rowsB = tiles * 256;
-    const size_t planeB = (size_t)plan->rowsB * net->ldK;
-    int rc;
-    for (int q = 0; q < 3; ++q) {
-        if ((rc = encode_2d(&plan->mapA[q], net->d_A + q * planeA, (uint64_t)net->N,
-                            (uint64_t)net->rowsA, (uint64_t)net->ldK * 2, 32, 256 / kCluster)))
-            return rc;
-        __nv_bfloat16 *bbase = static_cast<__nv_bfloat16 *>(net->d_B) +
-                               (q < net->planesB ? q : 0) * planeB;
-        if ((rc = encode_2d(&plan->mapB[q], bbase, (uint64_t)net->N, (uint64_t)plan->rowsB,
-                            (uint64_t)net->ldK * 2, 32, 256 / kCluster)))
-            return rc;
-    }
-    // products A_i B_j with i + j <= 1 (3) or <= 2 (6), issued smallest
-    // first: the correction products accumulate while the accumulator is
-    // small, and only the 4 MMAs of the dominant A0 B0 product truncate at
-    // the full magnitude of the K block's sum
-    const int ia3[3] = {0, 1, 0}, ib3[3] = {1, 0, 0};
-    const int ia6[6] = {1, 0, 2, 0, 1, 0}, ib6[6] = {1, 2, 0, 1, 0, 0};
     plan->P = (net->precision == GBS_BF16X3) ? 3 : 6;
-    for (int q = 0; q < plan->P; ++q) {
-        plan->ia[q] = plan->P == 3 ? ia3[q] : ia6[q];
-        plan->ib[q] = plan->P == 3 ? ib3[q] : ib6[q];
-    }
+    int rc;
+    if ((rc = encode_net_maps(net, plan->desc))) return rc;
+    GBS_CUDA_TRY(cudaMalloc(&plan->d_desc, sizeof(GemmNetDesc)));
+    GBS_CUDA_TRY(cudaMemcpy(plan->d_desc, &plan->desc, sizeof(GemmNetDesc), cudaMemcpyHostToDevice));
     return GBS_OK;
 }
 
 void tc_plan_destroy(gbs_net *net) {
+    if (net->tc && net->tc->d_desc) cudaFree(net->tc->d_desc);
     delete net->tc;
     net->tc = nullptr;
+}
+
+int tc_set_cluster(gbs_net *net, int cluster) {
+    if (!net->tc) return set_error(GBS_EINVAL, "network has no tensor-core GEMM");
+    if (cluster < 0 || cluster > 2) return set_error(GBS_EINVAL, "cluster must be 0 (auto), 1 or 2");
+    net->tc->forced = cluster;
+    if (cluster) net->tc->cluster = cluster;
+    else net->tc->cluster = 0;
+    return GBS_OK;
+}
+
+int tc_get_cluster(gbs_net *net) { return net->tc ? net->tc->cluster : 0; }
+
+// Time the candidate cluster sizes on this chunk and keep the faster one
+// for this network and every network of the same size bucket.
+int tc_autotune(gbs_net *net, int64_t count, int *out) {
+    TcPlan *plan = net->tc;
+    const auto key = std::make_tuple(bucket(net->N), bucket(net->M), plan->P);
+    {
+        std::lock_guard<std::mutex> lock(g_tc_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            *out = it->second;
+            return GBS_OK;
+        }
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    GBS_CUDA_TRY(cudaStreamIsCapturing(net->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {  // no timing inside a capture: default
+        *out = 2;
+        return GBS_OK;
+    }
+    const int groups_ntiles[2] = {net->mtiles, (net->mtiles + 1) / 2};
+    const int stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
+    cudaEvent_t e0, e1;
+    GBS_CUDA_TRY(cudaEventCreate(&e0));
+    GBS_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 0.0f;
+    int best_c = 2, rc = GBS_OK;
+    for (int c = 1; c <= 2 && rc == GBS_OK; ++c) {
+        const int nt = groups_ntiles[c - 1] * stiles;
+        rc = launch_gemm_grouped(net->stream, net->sm_count, plan->P, c, plan->d_desc, nullptr, nt,
+                                 count, net->d_flags + 1);
+        if (rc) break;
+        cudaEventRecord(e0, net->stream);
+        rc = launch_gemm_grouped(net->stream, net->sm_count, plan->P, c, plan->d_desc, nullptr, nt,
+                                 count, net->d_flags + 1);
+        if (rc) break;
+        cudaEventRecord(e1, net->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = set_error(GBS_ECUDA, "autotuner timing failed");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (c == 1 || ms < best) {
+            best = ms;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lock(g_tc_mu);
+    g_tune[key] = best_c;
+    *out = best_c;
+    return GBS_OK;
 }
 
 int launch_gemm_tc(gbs_net *net, int64_t count) {
     if (count <= 0) return GBS_OK;
     TcPlan *plan = net->tc;
     if (!plan) return set_error(GBS_EINVAL, "no tensor-core plan");
-    if (!plan->attr_set) {
-        GBS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<3>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          smem_bytes<3>()));
-        GBS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<6>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          smem_bytes<6>()));
-        plan->attr_set = true;
+    int rc;
+    if ((rc = ensure_attrs())) return rc;
+    if (!plan->cluster) {
+        int c = 2;
+        if ((rc = tc_autotune(net, count, &c))) return rc;
+        plan->cluster = c;
     }
-    TcParams p;
-    p.KB = (net->N + 31) / 32;
-    p.P = plan->P;
-    for (int q = 0; q < 6; ++q) {
-        p.ia[q] = plan->ia[q];
-        p.ib[q] = plan->ib[q];
-    }
-    p.mtiles = net->mtiles;
-    p.stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
-    p.count = count;
-    p.ld_part = net->chunk;
-    p.nS_part = net->d_nS_part;
-    p.err = net->d_flags + 1;
-    const int64_t ntiles = (int64_t)((p.mtiles + kCluster - 1) / kCluster) * p.stiles;
-    const int clusters = (int)std::min<int64_t>(ntiles, net->sm_count / kCluster);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kCluster * clusters);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = plan->P == 3 ? smem_bytes<3>() : smem_bytes<6>();
-    cfg.stream = net->stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kCluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t le;
-    if (plan->P == 3)
-        le = cudaLaunchKernelEx(&cfg, k_gemm_tc<3>, plan->mapA[0], plan->mapA[1], plan->mapA[2],
-                                plan->mapB[0], plan->mapB[1], plan->mapB[2], p);
-    else
-        le = cudaLaunchKernelEx(&cfg, k_gemm_tc<6>, plan->mapA[0], plan->mapA[1], plan->mapA[2],
-                                plan->mapB[0], plan->mapB[1], plan->mapB[2], p);
-    if (le != cudaSuccess)
-        return set_error(GBS_ECUDA, "cluster launch of the GEMM failed: %s", cudaGetErrorString(le));
-    GBS_LAUNCH_CHECK();
-    return GBS_OK;
+    const int cl = plan->cluster;
+    const int groups = (net->mtiles + cl - 1) / cl;
+    const int stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
+    return launch_gemm_grouped(net->stream, net->sm_count, plan->P, cl, plan->d_desc, nullptr,
+                               groups * stiles, count, net->d_flags + 1);
 }
 
 }  // namespace gbs

@@ -1,0 +1,131 @@
+"""Tile configurations of the tcgen05 GEMM and batched uneven networks.
+
+Cluster sizes 1 and 2 differ only in how the trajectory operand reaches
+shared memory (direct loads vs a multicast shared by a CTA pair); the MMA
+arithmetic is the same, so per-trajectory results must agree bitwise.  A
+batch issues the same kernels per network (one grouped GEMM per round), so
+its sub-ensemble sums must equal per-network runs bitwise, and every
+network's P(m) must match its exact distribution within sampling error.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.exact as ex
+import workloads as wl
+from stats import agreement
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gbs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2503_12749_gb300 as g
+    g.build()
+    return g
+
+
+@pytest.mark.parametrize("shape", [(16, 16), (9, 9), (300, 300), (130, 200), (257, 100)])
+def test_cluster_sizes_agree_bitwise(gbs, shape):
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    N, M = shape
+    net_def = wl.small_network(N, M=M, r=0.8, t2=0.93, seed=31 + N)
+    res = []
+    for cl in (1, 2):
+        net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
+        gbs.gbs_set_gemm_config(net, cl)
+        n, nS = gbs.gbs_debug_samples(net, net_def.seed_s, 100, 333)
+        assert gbs.gbs_gemm_config(net) == cl
+        res.append(nS)
+        gbs.gbs_free_network(net)
+    assert np.array_equal(res[0], res[1])
+    no, nSo = oracle.samples(net_def.T, net_def.r, net_def.seed_s, 100, 333)
+    assert np.max(np.abs(res[0] - nSo) / np.maximum(np.abs(nSo), 1.0)) < 2.0 ** -12
+
+
+def test_autotuner_picks_a_configuration(gbs):
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    net_def = wl.small_network(200, r=0.7, t2=0.9, seed=3)
+    net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
+    assert gbs.gbs_gemm_config(net) == 0
+    gbs.gbs_sample(net, net_def.seed_s, 0, 5000, 10, 256)
+    assert gbs.gbs_gemm_config(net) in (1, 2)
+    gbs.gbs_free_network(net)
+
+
+def _uneven_defs():
+    sizes = [(40, 0.6, 0.8), (100, 0.9, 0.95), (257, 0.7, 0.9), (300, 0.5, 0.99),
+             (64, 1.1, 0.85), (130, 0.8, 0.97)]
+    return [wl.small_network(N, r=r, t2=t2, seed=50 + i) for i, (N, r, t2) in enumerate(sizes)]
+
+
+@pytest.mark.parametrize("own_stream", [True, False])
+def test_batch_equals_per_network_runs(gbs, own_stream):
+    import torch
+    s = torch.cuda.Stream() if own_stream else None
+    sptr = s.cuda_stream if own_stream else 0
+    defs = _uneven_defs()
+    E = [3000, 7000, 20000, 1000, 12345, 2048]
+    n_sub = [10, 8, 16, 4, 7, 16]
+    K1 = [64, 128, 256, 512, 64, 256]
+    seeds = [d.seed_s for d in defs]
+    first = [11 * i for i in range(len(defs))]
+    nets = [gbs.gbs_make_network(d.T, d.r, "bf16x3", sptr) for d in defs]
+    singles = [gbs.gbs_make_network(d.T, d.r, "bf16x3", sptr) for d in defs]
+    batch = gbs.gbs_make_batch(nets)
+    gbs.gbs_sample_batch(batch, seeds, first, E, n_sub, K1)
+    cl, rounds, tiles = gbs.gbs_batch_info(batch)
+    assert cl in (1, 2) and rounds >= 1 and tiles > 0
+    for i, d in enumerate(defs):
+        gbs.gbs_sample(singles[i], seeds[i], first[i], E[i], n_sub[i], K1[i])
+        _, _, acc_b, cnt_b = gbs.gbs_get_accumulators(nets[i])
+        _, _, acc_s, cnt_s = gbs.gbs_get_accumulators(singles[i])
+        assert np.array_equal(cnt_b, cnt_s)
+        assert np.array_equal(acc_b, acc_s), i
+    # a second call continues the trajectory stream
+    gbs.gbs_sample_batch(batch, seeds, [f + e for f, e in zip(first, E)], E, n_sub, K1)
+    for i in range(len(defs)):
+        _, _, _, cnt = gbs.gbs_get_accumulators(nets[i])
+        assert cnt.sum() == 2 * E[i]
+    gbs.gbs_free_batch(batch)
+    for n in nets + singles:
+        gbs.gbs_free_network(n)
+
+
+def test_batch_distributions_match_exact(gbs):
+    """A batch of uneven Haar networks (N log-uniform, r_j ~ U[0.5, 1.5],
+    amplitude t ~ U[0.5, 0.995]): each network's matrix-P P(m) agrees with
+    its exact uniform-loss distribution within sampling error."""
+    import torch
+    s = torch.cuda.Stream()
+    wls = wl.batched_networks(count=8, n_lo=60, n_hi=400)
+    defs = [w.network() for w in wls]
+    # correlated fluctuations across bins make 2^15 trajectories too few for
+    # the chi^2 criterion at the batch's high losses (t^2 down to 0.25)
+    E = [2 ** 17] * len(defs)
+    n_sub = [64] * len(defs)
+    K1s, offs = [], []
+    for w, d in zip(wls, defs):
+        K1, off = wl.dft_window(w.N, float(d.r.max()), w.t2, float(np.mean(np.sinh(d.r) ** 2)))
+        K1s.append(K1)
+        offs.append(off)
+    nets = [gbs.gbs_make_network(d.T, d.r, "bf16x3", s.cuda_stream) for d in defs]
+    batch = gbs.gbs_make_batch(nets)
+    gbs.gbs_sample_batch(batch, [d.seed_s for d in defs], [0] * len(defs), E, n_sub, K1s)
+    for i, (w, d) in enumerate(zip(wls, defs)):
+        P = gbs.gbs_binned_counts(nets[i], offs[i], K1s[i])
+        mu = ex.eigenvalues_uniform_loss(d.r, w.t2)
+        Pex = ex.exact_distribution(mu, K1s[i], offs[i]).real
+        res = agreement(P[0], P[1], Pex)
+        assert res["ok"], (i, w.N, res)
+        assert abs(P[0].sum() - 1.0) < 1e-9
+    gbs.gbs_free_batch(batch)
+    for n in nets:
+        gbs.gbs_free_network(n)

@@ -117,6 +117,22 @@ def batched_networks(count: int = 64, n_lo: int = 100, n_hi: int = 2000,
     return out
 
 
+def dft_window(N: int, r_max: float, t2: float, r_mean2: float):
+    """(K1, m_offset) of a DFT window covering the total-count support of a
+    network of N squeezed inputs with squeezing up to r_max and intensity
+    transmission t2: centred on the mean count t2 * N * <sinh^2 r> (mean
+    photon number sinh^2 r per squeezed mode, as stated with the lossless
+    exact distribution), half-width 12 x the largest per-mode standard
+    deviation sqrt(2 nbar (nbar + 1)) times sqrt(N), rounded up to a power of
+    two.  r_mean2 = <sinh^2 r_j>."""
+    nbar = math.sinh(r_max) ** 2
+    half = 12.0 * math.sqrt(2.0 * nbar * (nbar + 1.0) * N) + 64.0
+    K1 = 1 << int(math.ceil(math.log2(2.0 * half)))
+    mean = t2 * N * r_mean2
+    m_off = max(0, int(round(mean)) - K1 // 2)
+    return K1, m_off
+
+
 def small_network(N: int, M: Optional[int] = None, r=0.5, t2: float = 1.0, seed: int = 0,
                   general_loss: bool = False) -> Network:
     """A small test network.  r may be a scalar or a length-N sequence.
