@@ -332,6 +332,92 @@ def gbs_arm(args, wl_def):
     return 0
 
 
+def batch_arm(args):
+    """64 uneven Haar networks in one batch (the batched-networks workload)."""
+    import numpy as np
+    import torch
+
+    import paper_2503_12749_gb300 as gbs
+    import workloads as wl
+
+    torch.cuda.set_device(0)
+    gbs.build()
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+    wls = wl.batched_networks(count=args.batch_count)
+    defs = [w.network() for w in wls]
+    E = [args.samples or w.E for w in wls]
+    n_sub = [w.n_sub for w in wls]
+    K1s, offs = [], []
+    for w, d in zip(wls, defs):
+        k1, off = wl.dft_window(w.N, float(d.r.max()), w.t2, float(np.mean(np.sinh(d.r) ** 2)))
+        K1s.append(k1)
+        offs.append(off)
+    nets = [gbs.gbs_make_network(d.T, d.r, "bf16x3", sptr) for d in defs]
+    batch = gbs.gbs_make_batch(nets)
+    outs = [torch.empty(4 * k1, dtype=torch.float64, device="cuda") for k1 in K1s]
+    seeds = [d.seed_s for d in defs]
+
+    def step(s):
+        gbs.gbs_sample_batch(batch, seeds, [s * e for e in E], E, n_sub, K1s)
+        for i, net in enumerate(nets):
+            gbs.gbs_binned_counts_device(net, offs[i], outs[i].data_ptr())
+
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for s in range(args.steps):
+        step(args.warmup + s)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    cl, rounds, tiles = gbs.gbs_batch_info(batch)
+    # kernel time of the grouped GEMM: extra steps with phase timing on (the
+    # rounds are then issued one by one rather than as a graph)
+    gbs.gbs_profile_enable(nets[0], True)
+    nprof = 2
+    for s in range(nprof):
+        step(args.warmup + args.steps + s)
+    prof = gbs.gbs_profile_read(nets[0])
+    gbs.gbs_profile_enable(nets[0], False)
+    gemm_ms = prof["gemm"][0] * args.steps / nprof
+    total = sum(E) * args.steps
+    flops = sum(8.0 * d.M * d.N * e for d, e in zip(defs, E)) * args.steps
+    peaks, peak_kind = _peaks()
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    achieved = flops / (gemm_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": total / (ms_total / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3 split (fp32 accumulate, f64 sums)", "data": "synthetic",
+        "config": {"workload": f"batch{len(wls)}: {len(wls)} Haar networks, N=M log-uniform "
+                               "[100,2000], r_j~U[0.5,1.5], t~U[0.5,0.995], E=2^18 each",
+                   "N": [d.N for d in defs], "K1": K1s, "n_sub": n_sub[0],
+                   "samples_per_step": sum(E), "gemm_cluster_chosen": cl, "rounds": rounds,
+                   "gemm_tiles_per_call": tiles,
+                   "note": "one CUDA graph per gbs_sample_batch call; GEMM kernel time from "
+                           "2 further steps issued without the graph under phase timing"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"{peak_kind} bf16 sustained",
+                     "mma_issued_frac": 3 * achieved / peak, "kernel": "k_gemm_tc (grouped)",
+                     "gemm_ms_per_step": gemm_ms / args.steps},
+        "gpu_launches": None, "clocks": clk,
+    }
+    gbs.gbs_free_batch(batch)
+    for n in nets:
+        gbs.gbs_free_network(n)
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     import workloads as wl
     ap = argparse.ArgumentParser()
@@ -339,7 +425,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
-    ap.add_argument("--workload", default="m1000", choices=sorted(wl.NAMED))
+    ap.add_argument("--workload", default="m1000", choices=sorted(wl.NAMED) + ["batch64"])
+    ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--precision", default=None, choices=["fp64", "bf16x3", "bf16x6"])
     ap.add_argument("--samples", type=int, default=0, help="override trajectories per step")
     ap.add_argument("--ref-samples", type=int, default=2048)
@@ -349,6 +436,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "batch64":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference",
+                              "unavailable": "the reference arm is defined for the m1000 workload"}))
+            return 0
+        return batch_arm(args)
     wl_def = wl.NAMED[args.workload]
     if args.impl == "reference":
         return reference_arm(args, wl_def)

@@ -211,6 +211,9 @@ int gbs_gemm_config(gbs_net_t net, int *cluster);
  *   same trajectories as per-network gbs_sample calls are drawn.
  *   Synchronises the stream before capturing (descriptor upload).
  * gbs_batch_info -- cluster size chosen, rounds and GEMM tiles of the last call.
+ * With phase timing enabled on the batch's first network (gbs_profile_enable),
+ * gbs_sample_batch issues its rounds directly instead of as a graph and
+ * attributes the grouped GEMM launches to that network's GEMM phase.
  * gbs_free_batch -- release the batch (not its networks).
  */
 typedef struct gbs_batch *gbs_batch_t;

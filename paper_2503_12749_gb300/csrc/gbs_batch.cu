@@ -112,8 +112,13 @@ int upload_rounds(gbs_batch *b, const RoundPlan &rp) {
 int round_gemm(gbs_batch *b, const RoundPlan &rp, int r, int cluster) {
     const int nn = (int)b->nets.size();
     const int off = rp.tile_off[r], nt = rp.tile_off[r + 1] - off;
-    return launch_gemm_grouped(b->stream, b->sm_count, b->P, cluster, b->d_desc + (size_t)r * nn,
-                               b->d_tiles + off, nt, 0, b->nets[0]->d_flags + 1);
+    gbs_net *n0 = b->nets[0];
+    prof_mark(n0, GBS_PHASE_GEMM, 0, true);
+    const int rc = launch_gemm_grouped(b->stream, b->sm_count, b->P, cluster,
+                                       b->d_desc + (size_t)r * nn, b->d_tiles + off, nt, 0,
+                                       n0->d_flags + 1);
+    prof_mark(n0, GBS_PHASE_GEMM, 1, false);
+    return rc;
 }
 
 int round_front(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *seeds,
@@ -224,8 +229,10 @@ int gbs_sample_batch(gbs_batch_t b, const uint64_t *seeds, const uint64_t *first
     b->last_rounds = rp.rounds;
     b->last_tiles = (int64_t)rp.tiles.size();
 
-    if (b->stream == nullptr) {
-        // the legacy default stream cannot be captured: issue the rounds directly
+    if (b->stream == nullptr || b->nets[0]->prof.on) {
+        // the legacy default stream cannot be captured, and phase timing
+        // (gbs_profile_enable on the first network) needs the launches
+        // bracketed one by one: issue the rounds directly
         for (int r = 0; r < rp.rounds; ++r) {
             if ((rc = round_front(b, rp, r, seeds, first_sample))) return rc;
             if ((rc = round_gemm(b, rp, r, b->cluster))) return rc;
