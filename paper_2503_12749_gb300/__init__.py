@@ -1,6 +1,7 @@
 """GB300-native matrix-P total-count estimator for Gaussian boson sampling.
 
-Python binding of the C ABI in ``include/gbs.h`` (libgbs.so, built for
+Python binding of the C ABI in ``include/gbs.h`` and
+``include/gbs_surrogate.h`` (libgbs.so, built for
 sm_103a by ``paper_2503_12749_gb300.build``).  The functions below carry the
 ABI's names and only marshal arguments: every step of the estimator runs in
 the library's CUDA kernels.  There is no CPU fallback: if the library cannot
@@ -96,12 +97,36 @@ def lib():
         L.gbs_free_network.restype = None
         L.gbs_last_error.argtypes = []
         L.gbs_last_error.restype = ctypes.c_char_p
+        L.gbs_make_network_device.argtypes = [ctypes.c_int, ctypes.c_int, vp, dp, ctypes.c_int,
+                                              vp, ctypes.POINTER(vp)]
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.gbs_mlp_create.argtypes = [ctypes.c_int] * 5 + [vp, ctypes.POINTER(vp)]
+        L.gbs_mlp_param_count.argtypes = [vp, i64p]
+        L.gbs_mlp_set_params.argtypes = [vp, fp]
+        L.gbs_mlp_get_params.argtypes = [vp, fp]
+        L.gbs_mlp_get_adam_state.argtypes = [vp, fp, fp, i64p]
+        L.gbs_mlp_forward.argtypes = [vp, vp, ctypes.c_int, vp]
+        L.gbs_mlp_gradients.argtypes = [vp, vp, vp, ctypes.c_int, dp, fp]
+        L.gbs_mlp_train.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, fp, fp]
+        L.gbs_mlp_free.argtypes = [vp]
+        L.gbs_mlp_free.restype = None
+        L.gbs_surrogate_features.argtypes = [ctypes.c_int, ip, ip, dp, ip, i64p, dp, i64p, vp, vp]
+        L.gbs_surrogate_feature_stats.argtypes = [ctypes.c_int, vp, vp, vp]
+        L.gbs_surrogate_standardize.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp]
+        L.gbs_surrogate_encode.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int64, vp, vp]
+        L.gbs_surrogate_decode.argtypes = [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int64]
         for name in ("gbs_make_network", "gbs_sample", "gbs_binned_counts",
                      "gbs_binned_counts_device", "gbs_check_finite", "gbs_debug_samples",
                      "gbs_get_accumulators", "gbs_set_accumulators", "gbs_reset",
                      "gbs_network_info", "gbs_profile_enable", "gbs_profile_read",
                      "gbs_binned_counts_noalloc", "gbs_set_gemm_config", "gbs_gemm_config",
-                     "gbs_make_batch", "gbs_sample_batch", "gbs_batch_info"):
+                     "gbs_make_batch", "gbs_sample_batch", "gbs_batch_info",
+                     "gbs_make_network_device", "gbs_mlp_create", "gbs_mlp_param_count",
+                     "gbs_mlp_set_params", "gbs_mlp_get_params", "gbs_mlp_get_adam_state",
+                     "gbs_mlp_forward", "gbs_mlp_gradients", "gbs_mlp_train",
+                     "gbs_surrogate_features", "gbs_surrogate_feature_stats",
+                     "gbs_surrogate_standardize", "gbs_surrogate_encode",
+                     "gbs_surrogate_decode"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -151,6 +176,21 @@ def gbs_make_network(T: np.ndarray, r: np.ndarray, precision=GBS_FP64,
     out = ctypes.c_void_p()
     _check(lib().gbs_make_network(N, M, _dptr(Tf), _dptr(r), int(precision),
                                   ctypes.c_void_p(stream), ctypes.byref(out)))
+    return Network(out.value, N, M, int(precision), stream)
+
+
+def gbs_make_network_device(T_dev_ptr: int, M: int, N: int, r: np.ndarray, precision=GBS_FP64,
+                            stream: int = 0) -> Network:
+    """T_dev_ptr: device address of an (M, N) complex128 row-major array."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    if r.shape != (N,):
+        raise ValueError("r must have shape (N,)")
+    out = ctypes.c_void_p()
+    _check(lib().gbs_make_network_device(N, M, ctypes.c_void_p(T_dev_ptr), _dptr(r),
+                                         int(precision), ctypes.c_void_p(stream),
+                                         ctypes.byref(out)))
     return Network(out.value, N, M, int(precision), stream)
 
 
@@ -313,3 +353,148 @@ def gbs_free_network(net: Network) -> None:
     if net.handle and net.handle.value:
         lib().gbs_free_network(net.handle)
         net.handle = ctypes.c_void_p()
+
+
+# ----------------------------------------------------------------------------
+# Learned surrogate (include/gbs_surrogate.h)
+# ----------------------------------------------------------------------------
+GBS_SUR_FEATURES = 10
+GBS_SUR_RECORD = 14
+GBS_SUR_GRID = 256
+GBS_SUR_OUT = 512
+
+
+def _fptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Mlp:
+    """Handle of an MLP on the device (owns the C-side gbs_mlp_t)."""
+
+    def __init__(self, handle: int, in_dim: int, width: int, out_dim: int, layers: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.in_dim, self.width, self.out_dim, self.layers = in_dim, width, out_dim, layers
+
+    def __del__(self):
+        try:
+            if self.handle and self.handle.value:
+                gbs_mlp_free(self)
+        except Exception:
+            pass
+
+
+def gbs_mlp_create(in_dim: int, width: int, out_dim: int, layers: int, max_batch: int,
+                   stream: int = 0) -> Mlp:
+    out = ctypes.c_void_p()
+    _check(lib().gbs_mlp_create(in_dim, width, out_dim, layers, max_batch,
+                                ctypes.c_void_p(stream), ctypes.byref(out)))
+    return Mlp(out.value, in_dim, width, out_dim, layers)
+
+
+def gbs_mlp_param_count(mlp: Mlp) -> int:
+    c = ctypes.c_int64()
+    _check(lib().gbs_mlp_param_count(mlp.handle, ctypes.byref(c)))
+    return int(c.value)
+
+
+def gbs_mlp_set_params(mlp: Mlp, params: np.ndarray) -> None:
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    if params.size != gbs_mlp_param_count(mlp):
+        raise ValueError("wrong parameter count")
+    _check(lib().gbs_mlp_set_params(mlp.handle, _fptr(params)))
+
+
+def gbs_mlp_get_params(mlp: Mlp) -> np.ndarray:
+    out = np.zeros(gbs_mlp_param_count(mlp), dtype=np.float32)
+    _check(lib().gbs_mlp_get_params(mlp.handle, _fptr(out)))
+    return out
+
+
+def gbs_mlp_get_adam_state(mlp: Mlp):
+    """(first moments, second moments, Adam steps taken)."""
+    n = gbs_mlp_param_count(mlp)
+    m1 = np.zeros(n, dtype=np.float32)
+    m2 = np.zeros(n, dtype=np.float32)
+    st = ctypes.c_int64()
+    _check(lib().gbs_mlp_get_adam_state(mlp.handle, _fptr(m1), _fptr(m2), ctypes.byref(st)))
+    return m1, m2, int(st.value)
+
+
+def gbs_mlp_forward(mlp: Mlp, X_dev_ptr: int, batch: int, Y_dev_ptr: int) -> None:
+    _check(lib().gbs_mlp_forward(mlp.handle, ctypes.c_void_p(X_dev_ptr), batch,
+                                 ctypes.c_void_p(Y_dev_ptr)))
+
+
+def gbs_mlp_gradients(mlp: Mlp, X_dev_ptr: int, T_dev_ptr: int, batch: int):
+    """(loss, packed gradient) of one batch."""
+    loss = ctypes.c_double()
+    grad = np.zeros(gbs_mlp_param_count(mlp), dtype=np.float32)
+    _check(lib().gbs_mlp_gradients(mlp.handle, ctypes.c_void_p(X_dev_ptr),
+                                   ctypes.c_void_p(T_dev_ptr), batch, ctypes.byref(loss),
+                                   _fptr(grad)))
+    return float(loss.value), grad
+
+
+def gbs_mlp_train(mlp: Mlp, X_dev_ptr: int, T_dev_ptr: int, batch: int, lr) -> np.ndarray:
+    """len(lr) full-batch Adam steps; returns the loss before each step."""
+    lr = np.ascontiguousarray(lr, dtype=np.float32)
+    hist = np.zeros(lr.size, dtype=np.float32)
+    _check(lib().gbs_mlp_train(mlp.handle, ctypes.c_void_p(X_dev_ptr), ctypes.c_void_p(T_dev_ptr),
+                               batch, int(lr.size), _fptr(lr), _fptr(hist)))
+    return hist
+
+
+def gbs_mlp_free(mlp: Mlp) -> None:
+    if mlp.handle and mlp.handle.value:
+        lib().gbs_mlp_free(mlp.handle)
+        mlp.handle = ctypes.c_void_p()
+
+
+def gbs_surrogate_features(N, M, t, K1, m_off, r_list, feat_dev_ptr: int, stream: int = 0) -> None:
+    """Feature records [count][14] of networks (N[i], M[i], t[i], K1[i],
+    m_off[i], squeezing r_list[i]) into device memory."""
+    count = len(N)
+    i32 = ctypes.c_int * count
+    r_all = np.ascontiguousarray(np.concatenate([np.asarray(r, dtype=np.float64) for r in r_list]))
+    r_off = np.zeros(count + 1, dtype=np.int64)
+    r_off[1:] = np.cumsum([len(r) for r in r_list])
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    mo = np.ascontiguousarray(m_off, dtype=np.int64)
+    _check(lib().gbs_surrogate_features(count, i32(*[int(x) for x in N]),
+                                        i32(*[int(x) for x in M]), _dptr(t),
+                                        i32(*[int(x) for x in K1]),
+                                        mo.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                        _dptr(r_all),
+                                        r_off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                        ctypes.c_void_p(stream), ctypes.c_void_p(feat_dev_ptr)))
+
+
+def gbs_surrogate_feature_stats(count: int, feat_dev_ptr: int, stats_dev_ptr: int,
+                                stream: int = 0) -> None:
+    _check(lib().gbs_surrogate_feature_stats(count, ctypes.c_void_p(feat_dev_ptr),
+                                             ctypes.c_void_p(stream),
+                                             ctypes.c_void_p(stats_dev_ptr)))
+
+
+def gbs_surrogate_standardize(count: int, feat_dev_ptr: int, stats_dev_ptr: int, X_dev_ptr: int,
+                              in_domain_dev_ptr: int = 0, stream: int = 0) -> None:
+    _check(lib().gbs_surrogate_standardize(count, ctypes.c_void_p(feat_dev_ptr),
+                                           ctypes.c_void_p(stats_dev_ptr), ctypes.c_void_p(stream),
+                                           ctypes.c_void_p(X_dev_ptr),
+                                           ctypes.c_void_p(in_domain_dev_ptr or None)))
+
+
+def gbs_surrogate_encode(count: int, feat_dev_ptr: int, P_dev_ptr: int, ldP: int, Y_dev_ptr: int,
+                         stream: int = 0) -> None:
+    _check(lib().gbs_surrogate_encode(count, ctypes.c_void_p(feat_dev_ptr),
+                                      ctypes.c_void_p(P_dev_ptr), ldP, ctypes.c_void_p(stream),
+                                      ctypes.c_void_p(Y_dev_ptr)))
+
+
+def gbs_surrogate_decode(count: int, feat_dev_ptr: int, Y_dev_ptr: int, P_dev_ptr: int, ldP: int,
+                         stream: int = 0) -> None:
+    _check(lib().gbs_surrogate_decode(count, ctypes.c_void_p(feat_dev_ptr),
+                                      ctypes.c_void_p(Y_dev_ptr), ctypes.c_void_p(stream),
+                                      ctypes.c_void_p(P_dev_ptr), ldP))

@@ -39,7 +39,7 @@ def sources():
 
 def _deps():
     return (sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
-            + [os.path.join(INCLUDE, "gbs.h"), os.path.abspath(__file__)])
+            + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
 def up_to_date() -> bool:

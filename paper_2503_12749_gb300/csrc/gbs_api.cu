@@ -157,6 +157,45 @@ int run_chunk_front(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) {
     return GBS_OK;
 }
 
+// T (device, M x N complex, (re, im) interleaved, row-major) -> [M][2][N] FP64.
+__global__ void k_t64_from_dev(const double *__restrict__ T, int N, int M, double *__restrict__ out,
+                               unsigned long long *nonfinite) {
+    const int64_t total = (int64_t)M * N;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / N, j = q % N;
+        const double re = T[2 * q], im = T[2 * q + 1];
+        if (!isfinite(re) || !isfinite(im)) atomicAdd(nonfinite, 1ull);
+        out[(i * 2 + 0) * N + j] = re;
+        out[(i * 2 + 1) * N + j] = im;
+    }
+}
+
+// T (device) -> BF16 planes of A = [Re T_i.; Im T_i.] (rows interleaved per
+// mode, pitch ldK), T rounded to FP32 and split T = T0 + T1 + T2.
+__global__ void k_split_from_dev(const double *__restrict__ T, int N, int M, int ldK,
+                                 __nv_bfloat16 *__restrict__ A, size_t plane,
+                                 unsigned long long *nonfinite) {
+    const int64_t total = (int64_t)M * N;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / N, j = q % N;
+        for (int c = 0; c < 2; ++c) {
+            const double v = T[2 * q + c];
+            if (!isfinite(v)) atomicAdd(nonfinite, 1ull);
+            const float x = __double2float_rn(v);
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
+            const float r1 = x - __bfloat162float(h0);
+            const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+            const float r2 = r1 - __bfloat162float(h1);
+            const size_t o = (size_t)(2 * i + c) * ldK + j;
+            A[o] = h0;
+            A[plane + o] = h1;
+            A[2 * plane + o] = __float2bfloat16_rn(r2);
+        }
+    }
+}
+
 int validate_net(gbs_net *net) {
     if (!net) return set_error(GBS_EINVAL, "null network");
     return GBS_OK;
@@ -217,20 +256,37 @@ extern "C" {
 
 const char *gbs_last_error(void) { return error_message(); }
 
-int gbs_make_network(int N, int M, const double *T, const double *r, int precision, void *stream,
-                     gbs_net_t *out) {
+}  // extern "C"
+
+namespace gbs {
+namespace {
+
+// Counts the non-finite entries found by one of the T conversion kernels.
+int finish_device_T(gbs_net *net, unsigned long long *d_bad) {
+    GBS_LAUNCH_CHECK();
+    unsigned long long bad = 0;
+    GBS_CUDA_TRY(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, net->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(net->stream));
+    if (bad) return set_error(GBS_EINVAL, "T has %llu non-finite entries", bad);
+    return GBS_OK;
+}
+
+// Shared by gbs_make_network (T in host memory) and gbs_make_network_device.
+int make_network(int N, int M, const double *T, bool T_device, const double *r, int precision,
+                 void *stream, gbs_net_t *out) {
     if (!out) return set_error(GBS_EINVAL, "out is NULL");
     *out = nullptr;
     if (N < 1 || M < 1 || N > 65536 || M > 65536)
         return set_error(GBS_EINVAL, "N and M must be in [1, 65536] (got %d, %d)", N, M);
-    if (!T || !r) return set_error(GBS_EINVAL, "T and r must be non-NULL host pointers");
+    if (!T || !r) return set_error(GBS_EINVAL, "T and r must be non-NULL pointers");
     if (precision != GBS_FP64 && precision != GBS_BF16X3 && precision != GBS_BF16X6)
         return set_error(GBS_EINVAL, "unknown precision %d", precision);
     for (int j = 0; j < N; ++j)
         if (!std::isfinite(r[j]) || r[j] < 0.0)
             return set_error(GBS_EINVAL, "r[%d] = %g: squeezing must be finite and >= 0", j, r[j]);
-    for (size_t q = 0; q < (size_t)2 * M * N; ++q)
-        if (!std::isfinite(T[q])) return set_error(GBS_EINVAL, "T has a non-finite entry");
+    if (!T_device)
+        for (size_t q = 0; q < (size_t)2 * M * N; ++q)
+            if (!std::isfinite(T[q])) return set_error(GBS_EINVAL, "T has a non-finite entry");
 
     gbs_net *net = new (std::nothrow) gbs_net();
     if (!net) return set_error(GBS_ENOMEM, "host allocation failed");
@@ -272,7 +328,26 @@ int gbs_make_network(int N, int M, const double *T, const double *r, int precisi
             cudaSuccess)
         return fail(set_error(GBS_ECUDA, "upload of sampler coefficients failed"));
 
-    if (precision == GBS_FP64) {
+    unsigned long long *d_bad = nullptr;
+    if (T_device) {
+        if ((rc = dev_alloc(&d_bad, (size_t)1, "T check")) ) return fail(rc);
+        if (cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), net->stream) != cudaSuccess) {
+            dev_free(d_bad);
+            return fail(set_error(GBS_ECUDA, "memset failed"));
+        }
+    }
+    const int conv_blocks =
+        (int)std::min<int64_t>(((int64_t)M * N + 255) / 256, (int64_t)net->sm_count * 16);
+    if (precision == GBS_FP64 && T_device) {
+        if ((rc = dev_alloc(&net->d_T64, (size_t)M * 2 * N, "T64"))) {
+            dev_free(d_bad);
+            return fail(rc);
+        }
+        k_t64_from_dev<<<conv_blocks, 256, 0, net->stream>>>(T, N, M, net->d_T64, d_bad);
+        rc = finish_device_T(net, d_bad);
+        dev_free(d_bad);
+        if (rc) return fail(rc);
+    } else if (precision == GBS_FP64) {
         std::vector<double> t64((size_t)M * 2 * N);
         for (int i = 0; i < M; ++i)
             for (int j = 0; j < N; ++j) {
@@ -290,6 +365,25 @@ int gbs_make_network(int N, int M, const double *T, const double *r, int precisi
         net->planesB = (precision == GBS_BF16X3) ? 2 : 3;
         net->ldK = (N + 7) / 8 * 8;
         net->rowsA = 2 * M;
+        const size_t plane = (size_t)net->rowsA * net->ldK;
+        if (T_device) {
+            if ((rc = dev_alloc(&net->d_A, (size_t)net->planesA * plane, "A planes"))) {
+                dev_free(d_bad);
+                return fail(rc);
+            }
+            if (cudaMemsetAsync(net->d_A, 0, (size_t)net->planesA * plane * sizeof(__nv_bfloat16),
+                                net->stream) != cudaSuccess) {
+                dev_free(d_bad);
+                return fail(set_error(GBS_ECUDA, "memset of T planes failed"));
+            }
+            k_split_from_dev<<<conv_blocks, 256, 0, net->stream>>>(T, N, M, net->ldK, net->d_A,
+                                                                  plane, d_bad);
+            rc = finish_device_T(net, d_bad);
+            dev_free(d_bad);
+            if (rc) return fail(rc);
+        }
+    }
+    if (precision != GBS_FP64 && !T_device) {
         const size_t plane = (size_t)net->rowsA * net->ldK;
         std::vector<__nv_bfloat16> a((size_t)net->planesA * plane, __float2bfloat16(0.0f));
         for (int i = 0; i < M; ++i)
@@ -345,6 +439,21 @@ int gbs_make_network(int N, int M, const double *T, const double *r, int precisi
     }
     *out = net;
     return GBS_OK;
+}
+
+}  // namespace
+}  // namespace gbs
+
+extern "C" {
+
+int gbs_make_network(int N, int M, const double *T, const double *r, int precision, void *stream,
+                     gbs_net_t *out) {
+    return make_network(N, M, T, false, r, precision, stream, out);
+}
+
+int gbs_make_network_device(int N, int M, const double *T_dev, const double *r, int precision,
+                            void *stream, gbs_net_t *out) {
+    return make_network(N, M, T_dev, true, r, precision, stream, out);
 }
 
 int gbs_sample(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub, int K1) {

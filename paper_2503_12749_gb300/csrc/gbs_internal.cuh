@@ -62,7 +62,7 @@ struct TcPlan;  // tcgen05 GEMM plan (tensor maps, tiling), defined in k_gemm_tc
 
 // Operand description of one network for the (grouped) tcgen05 GEMM, kept in
 // device memory so that one launch can serve many networks.
-struct __align__(64) GemmNetDesc {
+struct __align__(128) GemmNetDesc {
     CUtensorMap mapA[3];     // A planes, box 32 x 128
     CUtensorMap mapB[2][3];  // B planes, box 32 x 256 (clusters of 1) / 32 x 128 (of 2)
     int KB;                  // 32-wide K blocks
@@ -176,6 +176,13 @@ void count_samples(gbs_net *net, uint64_t first, int64_t E);
 
 // Phase timing: bracket the launches of one phase (no-ops when disabled).
 void prof_mark(gbs_net *net, int phase, int launches_if_stop, bool start);
+
+// Tensor map of a row-major BF16 array (rows x inner elements, row pitch
+// row_bytes) read in boxes of box_inner x box_rows with the 64-byte swizzle
+// (box_inner = 32 elements = one 64-byte row).  Out-of-range box rows read as
+// zeros.
+int encode_2d(CUtensorMap *map, void *base, uint64_t inner, uint64_t rows, uint64_t row_bytes,
+              uint32_t box_inner, uint32_t box_rows);
 
 // Device properties helper.
 bool device_has_tcgen05(int device);

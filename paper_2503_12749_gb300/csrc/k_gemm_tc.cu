@@ -445,6 +445,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+}  // namespace
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -460,7 +462,6 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 int encode_2d(CUtensorMap *map, void *base, uint64_t inner, uint64_t rows, uint64_t row_bytes,
               uint32_t box_inner, uint32_t box_rows) {
-    // box_inner = 32 bf16 = 64 bytes per row: the 64-byte swizzle
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
     if (!enc) return set_error(GBS_ECUDA, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[2] = {inner, rows};
@@ -473,8 +474,6 @@ int encode_2d(CUtensorMap *map, void *base, uint64_t inner, uint64_t rows, uint6
     if (r != CUDA_SUCCESS) return set_error(GBS_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return GBS_OK;
 }
-
-}  // namespace
 
 namespace {
 

@@ -152,3 +152,73 @@ def small_network(N: int, M: Optional[int] = None, r=0.5, t2: float = 1.0, seed:
     return Network(T=np.ascontiguousarray(T, dtype=np.complex128),
                    r=np.ascontiguousarray(rr, dtype=np.float64), t2=t2_hint,
                    seed_s=SEED_S_BASE + 500 + seed)
+
+
+# ----------------------------------------------------------------------------
+# Networks of the learned surrogate's training and held-out sets
+# ----------------------------------------------------------------------------
+@dataclasses.dataclass
+class SurrogateNet:
+    """One network of the surrogate workload: N = M modes, squeezing r (N),
+    amplitude transmission t (T = t U), DFT window (K1, m_off), seeds."""
+    N: int
+    r: np.ndarray
+    t: float
+    K1: int
+    m_off: int
+    seed_u: int
+    seed_s: int
+
+    @property
+    def M(self) -> int:
+        return self.N
+
+
+SUR_TRAIN_SEED = SEED_U_BASE + 5000
+SUR_HELDOUT_SEED = SEED_U_BASE + 6000
+
+
+def surrogate_networks(count: int, seed: int = SUR_TRAIN_SEED, n_lo: int = 500,
+                       n_hi: int = 8000) -> List[SurrogateNet]:
+    """N log-uniform in [n_lo, n_hi]; per network c ~ U[0.5, 1.5],
+    delta ~ U[0, 0.3], r_j ~ U[c - delta, c + delta]; t ~ U[0.9, 0.999];
+    window from dft_window.  Network i uses seeds (seed + i, SEED_S_BASE +
+    seed + i)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        c = float(rng.uniform(0.5, 1.5))
+        d = float(rng.uniform(0.0, 0.3))
+        t = float(rng.uniform(0.9, 0.999))
+        r = np.random.default_rng(seed + i + SEED_R_OFFSET).uniform(c - d, c + d, size=n)
+        K1, m_off = dft_window(n, float(r.max()), t * t, float(np.mean(np.sinh(r) ** 2)))
+        out.append(SurrogateNet(n, r, t, K1, m_off, seed + i, SEED_S_BASE + seed + i))
+    return out
+
+
+def fourier_unitary_device(N: int, seed: int, device="cuda"):
+    """U = F diag(e^{i phi}) as a torch complex128 (N, N) tensor on `device`:
+    F_jk = e^{-2 pi i jk / N} / sqrt(N) (the unitary DFT matrix, built from a
+    table of the N roots of unity indexed by jk mod N), phases phi_k ~ U[0, 2pi)
+    from numpy's default_rng(seed).  Exactly unitary up to rounding; its
+    |U_jk|^2 = 1/N like the average of a Haar matrix."""
+    import torch
+    ph = np.random.default_rng(seed).uniform(0.0, 2.0 * math.pi, size=N)
+    roots = np.exp(-2j * math.pi * np.arange(N) / N) / math.sqrt(N)
+    roots_d = torch.from_numpy(roots).to(device)
+    phase_d = torch.from_numpy(np.exp(1j * ph)).to(device)
+    j = torch.arange(N, device=device, dtype=torch.int64)
+    idx = torch.remainder(j[:, None] * j[None, :], N)
+    return roots_d[idx] * phase_d[None, :]
+
+
+def haar_unitary_device(N: int, seed: int, device="cuda"):
+    """The Haar matrix of haar_unitary(N, seed) (same Ginibre draw and phase
+    fix), its QR computed by torch on `device`; equal to it up to rounding."""
+    import torch
+    rng = np.random.default_rng(seed)
+    z = (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))) / math.sqrt(2.0)
+    q, r = torch.linalg.qr(torch.from_numpy(z).to(device))
+    d = torch.diagonal(r)
+    return q * (d / d.abs())[None, :]
