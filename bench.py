@@ -418,6 +418,187 @@ def batch_arm(args):
     return 0
 
 
+SUR_METRIC = "surrogate binned-P(m) predictions/s on held-out networks, judged by matrix-P runs"
+
+
+def surrogate_arm(args):
+    """The learned surrogate at scale: trained on 2000 method-generated
+    distributions (N = M log-uniform [500, 8000]), judged against plain
+    matrix-P runs on 50 held-out Haar networks plus the N = M = 8000, r = 1,
+    t^2 = 0.99 network at E = 2^20.  Timed step: one surrogate prediction of
+    all judged networks (features, standardisation, MLP forward, decode)."""
+    import numpy as np
+    import torch
+
+    import paper_2503_12749_gb300 as gbs
+    from paper_2503_12749_gb300 import surrogate as S
+    import workloads as wl
+
+    torch.cuda.set_device(0)
+    gbs.build()
+    stream = torch.cuda.Stream()
+    E_train = args.sur_train_samples
+    train = wl.surrogate_networks(args.sur_train)
+    fourier = lambda n: (n.t * wl.fourier_unitary_device(n.N, n.seed_u)).contiguous()
+    cache = {}
+
+    def haar(n):
+        if n.seed_u not in cache:
+            cache[n.seed_u] = (n.t * wl.haar_unitary_device(n.N, n.seed_u)).contiguous()
+        return cache[n.seed_u]
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P, _, ld = S.method_distributions(train, E_train, 64, fourier, stream=stream)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    sur = S.Surrogate(max_batch=args.sur_train, stream=stream)
+    t0 = time.perf_counter()
+    fit = sur.fit(train, P, ld, steps=400, lr_max=1e-3, rounds=40)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t0
+    del P
+
+    held = wl.surrogate_networks(args.sur_heldout, seed=wl.SUR_HELDOUT_SEED)
+    big = wl.M8000
+    r8 = np.full(big.N, 1.0)
+    K8, off8 = wl.dft_window(big.N, 1.0, big.t2, math.sinh(1.0) ** 2)
+    net8 = wl.SurrogateNet(big.N, r8, math.sqrt(big.t2), K8, off8, wl.SEED_U_BASE + big.index,
+                           wl.SEED_S_BASE + big.index)
+    judged = held + [net8]
+    # judges: E_judge trajectories per held-out network, 2^20 for the 8000-mode one
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Pj, Sj, ldj = S.method_distributions(held, args.sur_judge_samples, 64, haar, stream=stream)
+    torch.cuda.synchronize()
+    t_judge = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P8, S8, ld8 = S.method_distributions([net8], big.E, 64, haar, stream=stream)
+    torch.cuda.synchronize()
+    t_big = time.perf_counter() - t0
+    ldj = max(ldj, ld8)
+    PJ = torch.zeros(len(judged), ldj, dtype=torch.float64, device="cuda")
+    PJ[:len(held), :Pj.shape[1]] = Pj
+    PJ[len(held), :ld8] = P8[0]
+    sig = [float(Sj[i, :n.K1].max() / Pj[i, :n.K1].max()) for i, n in enumerate(held)]
+    sig.append(float(S8[0, :K8].max() / P8[0, :K8].max()))
+
+    def errs(Pa, nets):
+        return np.array([float((Pa[i, :n.K1] - PJ[i, :n.K1]).abs().max() / PJ[i, :n.K1].max())
+                         for i, n in enumerate(nets)])
+
+    # the method without the surrogate: error of shorter runs against the judges
+    curve = {}
+    for Ec in (2 ** 12, 2 ** 14, 2 ** 16):
+        Pc, _, _ = S.method_distributions(held, Ec, 64, haar, stream=stream)
+        curve[Ec] = float(np.median(errs(Pc, held)))
+        del Pc
+    cache.clear()
+
+    # timed: surrogate predictions of all judged networks
+    def step():
+        return sur.predict(judged, ldj)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        Ps, _, dom = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    ms_dev = ev0.elapsed_time(ev1)
+    ms_step = 1e3 * wall / args.steps     # predict() synchronises: wall clock per step
+    e_sur = errs(Ps, judged)
+    med = float(np.median(e_sur[:len(held)]))
+    # samples a plain run needs for the surrogate's median error (error ~ E^-1/2
+    # through the measured curve's largest E)
+    E_eq = 2 ** 16 * (curve[2 ** 16] / med) ** 2
+    per_sample_s = t_judge / (len(held) * args.sur_judge_samples)
+    flops = 2.0 * (10 * 512 + 2 * 512 * 512 + 512 * 512) * len(judged)
+    peaks, peak_kind = _peaks()
+    line = {
+        "metric": SUR_METRIC, "value": len(judged) / (ms_step / 1e3), "unit": "networks/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 weights, fp32 accumulate (activations as bf16 hi+lo)",
+        "data": "synthetic",
+        "config": {"workload": f"surrogate: 4-layer width-512 MLP trained on {args.sur_train} "
+                               f"matrix-P distributions (N=M log-uniform [500,8000], E={E_train} "
+                               f"each), judged on {len(held)} held-out Haar networks "
+                               f"(E={args.sur_judge_samples}) + N=M=8000 r=1 t^2=0.99 (E={big.E})",
+                   "judged_networks": len(judged), "l2": "inputs smaller than L2 (latency-bound)"},
+        "surrogate": {
+            "train_data_s": t_data, "fit_s": t_fit, "best_round": fit["best_round"],
+            "rounds": fit["rounds"], "val_loss_best": float(np.min(fit["val_loss"])),
+            "heldout_error_median": med,
+            "heldout_error_p90": float(np.percentile(e_sur[:len(held)], 90)),
+            "heldout_error_max": float(np.max(e_sur[:len(held)])),
+            "m8000_error": float(e_sur[-1]), "judge_sigma_median": float(np.median(sig)),
+            "m8000_judge_sigma": sig[-1],
+            "method_error_median_at_E": {str(k): v for k, v in curve.items()},
+            "method_samples_equivalent": E_eq,
+            "method_seconds_per_network_at_equivalent": E_eq * per_sample_s,
+            "surrogate_seconds_per_network": ms_step / 1e3 / len(judged),
+            "gain_time_at_equal_error": E_eq * per_sample_s / (ms_step / 1e3 / len(judged)),
+            "in_domain": int(dom.sum()), "m8000_wall_s": t_big,
+            "error": "max_m |P - P_judge| / max_m P_judge"},
+        "roofline": {"bound": "latency", "achieved": flops / (ms_dev / args.steps / 1e3) / 1e12,
+                     "peak": peaks.get("bf16_tflops"), "unit": "TFLOP/s",
+                     "frac": flops / (ms_dev / args.steps / 1e3) / 1e12 / peaks.get("bf16_tflops"),
+                     "traffic": None, "kernel": "k_mlp_gemm (4 launches per prediction)",
+                     "note": f"{len(judged)} rows per GEMM: launch/latency bound by construction"},
+        "gpu_launches": args.steps * 8,
+        "clocks": clk,
+    }
+    # end to end: the same predictions with the distributions read back to
+    # host memory every step
+    if not args.no_e2e:
+        t0 = time.perf_counter()
+        for _ in range(max(1, min(3, args.steps))):
+            Ph = step()[0].cpu().numpy()
+        dt = (time.perf_counter() - t0) / max(1, min(3, args.steps))
+        line["e2e"] = {"value": len(judged) / dt, "unit": "networks/s",
+                       "h2d_bytes_per_step": int(sum(8 * n.N + 40 for n in judged)),
+                       "d2h_bytes_per_step": int(Ph.nbytes),
+                       "what": "surrogate prediction from host r arrays to host P(m) arrays"}
+    if not args.no_cpu_baseline:
+        import oracle.surrogate as osur
+        params = gbs.gbs_mlp_get_params(sur.mlp).astype(np.float64)
+        dims = [10, 512, 512, 512, 512]
+        layers, o = [], 0
+        for i in range(4):
+            W = params[o:o + dims[i + 1] * dims[i]].reshape(dims[i + 1], dims[i])
+            o += W.size
+            b = params[o:o + dims[i + 1]]
+            o += dims[i + 1]
+            layers.append((osur.bf16_round(W), b))
+        st = sur.stats.cpu().numpy()
+        sample = judged
+        t0 = time.perf_counter()
+        for n in sample:
+            u = osur.features(n.N, n.M, n.r, n.t, n.K1)
+            mu, sd = osur.count_moments(n.r, n.t)
+            x = np.where(st[1] > 1e-12, (u - st[0]) / np.where(st[1] > 1e-12, st[1], 1.0), 0.0)
+            y, _ = osur.forward(layers, x[None, :])
+            osur.decode(y[0], n.m_off, n.K1, mu, sd)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(sample) / dt, "unit": "networks/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"all {len(sample)} judged networks: features, "
+                                          f"FP64 MLP forward, decode ({dt:.2f} s)"}
+    print(json.dumps(line))
+    sur.close()
+    return 0
+
+
 def main():
     import workloads as wl
     ap = argparse.ArgumentParser()
@@ -425,7 +606,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
-    ap.add_argument("--workload", default="m1000", choices=sorted(wl.NAMED) + ["batch64"])
+    ap.add_argument("--workload", default="m1000",
+                    choices=sorted(wl.NAMED) + ["batch64", "surrogate"])
+    ap.add_argument("--sur-train", type=int, default=2000)
+    ap.add_argument("--sur-train-samples", type=int, default=2 ** 16)
+    ap.add_argument("--sur-heldout", type=int, default=50)
+    ap.add_argument("--sur-judge-samples", type=int, default=2 ** 18)
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--precision", default=None, choices=["fp64", "bf16x3", "bf16x6"])
     ap.add_argument("--samples", type=int, default=0, help="override trajectories per step")
@@ -442,6 +628,12 @@ def main():
                               "unavailable": "the reference arm is defined for the m1000 workload"}))
             return 0
         return batch_arm(args)
+    if args.workload == "surrogate":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference",
+                              "unavailable": "the reference arm is defined for the m1000 workload"}))
+            return 0
+        return surrogate_arm(args)
     wl_def = wl.NAMED[args.workload]
     if args.impl == "reference":
         return reference_arm(args, wl_def)
