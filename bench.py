@@ -32,9 +32,12 @@ if ROOT not in sys.path:
 METRIC = "matrix-P samples/sec and binned-P(m) wall time per N-mode network at |dP|/sigma<=1"
 UNIT = "samples/s"
 
-# DRAM bytes per launch of the GEMM kernel from an ncu capture (None until a
-# capture of the current kernel exists; see profiles/).
-GEMM_TRAFFIC_BYTES_PER_SAMPLE = None
+# DRAM bytes (read + write) of the GEMM kernel per trajectory, from the ncu
+# capture of one m1000 BF16x3 launch of 131072 trajectories
+# (profiles/k_gemm_tc_m1000_bf16x3.md: 1.0581 GB read + 0.0356 GB written);
+# the sample operand it reads grows in proportion to the trajectories.  Valid
+# for the workload and kernel version of that capture only.
+GEMM_TRAFFIC_BYTES_PER_SAMPLE = {("m1000", "bf16x3"): (1.058080e9 + 35.579904e6) / 131072}
 
 
 def _env_int(name, default):
@@ -253,8 +256,18 @@ def gbs_arm(args, wl_def):
                 "mma_products": P_products, "mma_issued_frac": P_products * achieved / peak,
                 "kernel": "k_gemm_tc", "launches": gemm_launches,
                 "avg_launch_ms": gemm_ms / max(gemm_launches, 1)}
-        if GEMM_TRAFFIC_BYTES_PER_SAMPLE is not None:
-            roof["traffic"] = GEMM_TRAFFIC_BYTES_PER_SAMPLE * E * args.steps / max(gemm_launches, 1)
+        per_sample = GEMM_TRAFFIC_BYTES_PER_SAMPLE.get((wl_def.name.split(":")[0], precision))
+        if per_sample is not None:
+            roof["traffic"] = per_sample * E * args.steps / max(gemm_launches, 1)
+            roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one " \
+                                     "131072-trajectory launch, scaled to the average launch"
+            # per trajectory: the sample operand (alpha and beta rows, 2 BF16
+            # planes each) and one n_S partial (16 B) per 64-mode tile; per
+            # launch: the 2 T planes the 3 products read
+            planes = 2 if precision == "bf16x3" else 3
+            per_traj = 2 * planes * 2 * netdef.N + 16 * (-(-netdef.M // 64))
+            roof["algorithmic_bytes"] = per_traj * E * args.steps / max(gemm_launches, 1) + \
+                planes * 2 * netdef.M * netdef.N * 2
     else:
         achieved = flops / (gemm_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s",
@@ -378,6 +391,11 @@ def batch_arm(args):
     clk = clocks.stop()
     ms_total = ev0.elapsed_time(ev1)
     cl, rounds, tiles = gbs.gbs_batch_info(batch)
+    # kernels per step: per network and chunk a sampler, a finalize and a
+    # generating-function launch; one grouped GEMM per round; per network the
+    # inversion (prep, log2 K1 FFT passes, statistics)
+    chunks = [-(-e // gbs.gbs_network_info(n)[3]) for e, n in zip(E, nets)]
+    launches_per_step = 3 * sum(chunks) + rounds + sum(int(math.log2(k)) + 2 for k in K1s)
     # kernel time of the grouped GEMM: extra steps with phase timing on (the
     # rounds are then issued one by one rather than as a graph)
     gbs.gbs_profile_enable(nets[0], True)
@@ -409,7 +427,7 @@ def batch_arm(args):
                      "peak_source": f"{peak_kind} bf16 sustained",
                      "mma_issued_frac": 3 * achieved / peak, "kernel": "k_gemm_tc (grouped)",
                      "gemm_ms_per_step": gemm_ms / args.steps},
-        "gpu_launches": None, "clocks": clk,
+        "gpu_launches": launches_per_step * args.steps, "clocks": clk,
     }
     gbs.gbs_free_batch(batch)
     for n in nets:
