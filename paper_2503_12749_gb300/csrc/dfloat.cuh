@@ -22,6 +22,19 @@ struct DfConsts {
     float ln2_1, ln2_2, ln2_3;             // ln 2 = ln2_1 + ln2_2 + ln2_3
     float pio2_1, pio2_2, pio2_3, pio2_4;  // pi / 2 = sum of the four
     float inv_fact_hi[18], inv_fact_lo[18];  // 1 / k! as double-float, k = 0..17
+    // table-driven functions (df_exp_tab, df_sincos_tab)
+    float ln2_64_1, ln2_64_2, ln2_64_3;    // ln 2 / 64 in pieces of <= 11 bits (+ rest)
+    float pi64_1, pi64_2, pi64_3;          // pi / 64 in pieces of <= 18 bits (+ rest)
+    float exp2_hi[64], exp2_lo[64];        // 2^(j/64), j = 0..63
+    float sin_hi[33], sin_lo[33];          // sin(j pi/64), j = -16..16 (index j + 16)
+    float cos_hi[33], cos_lo[33];          // cos(j pi/64)
+};
+
+// The tables of DfConsts copied into shared memory (lanes index them with
+// different j).
+struct DfTables {
+    df exp2[64];
+    df sn[33], cs[33];
 };
 
 __device__ __forceinline__ df df_two_sum(float a, float b) {
@@ -143,6 +156,65 @@ __device__ __forceinline__ void df_sincos(df phi, const DfConsts &K, df &s_out, 
         case 1: s_out = pc; c_out = df_neg(sn); break;
         case 2: s_out = df_neg(sn); c_out = df_neg(pc); break;
         default: s_out = df_neg(pc); c_out = sn; break;
+    }
+}
+
+// Table-driven e^a for a.hi in [-87, 88] (P. T. P. Tang, "Table-driven
+// implementation of the exponential function in IEEE floating-point
+// arithmetic", ACM TOMS 15, 1989): a = (64 m + j) ln2/64 + r, |r| <= ln2/128,
+// e^a = 2^m 2^(j/64) e^r with e^r = 1 + r + r^2 (1/2 + r/6 + r^2/24 + r^3/120)
+// (remainder < 4e-17); r^2 and the leading terms in double-float, the
+// bracket beyond 1/2 in FP32.
+__device__ __forceinline__ df df_exp_tab(df a, const DfTables &T, const DfConsts &K) {
+    const float kf = rintf(a.hi * 92.33248261689366f);  // 64 / ln 2
+    df r = df_two_sum(fmaf(-kf, K.ln2_64_1, a.hi), a.lo);  // exact product
+    r = df_add_f(r, -kf * K.ln2_64_2);                      // exact product
+    r = df_add_f(r, -kf * K.ln2_64_3);
+    const float x = r.hi;
+    const float qt = x * fmaf(fmaf(x, 1.0f / 120.0f, 1.0f / 24.0f), x, 1.0f / 6.0f);
+    const df q = df_fast_two_sum(0.5f, qt);
+    const df p = df_add_f(df_add(r, df_mul(df_mul(r, r), q)), 1.0f);
+    const int n = (int)kf;
+    const df t = df_mul(T.exp2[n & 63], p);
+    const float scale = __int_as_float(((n >> 6) + 127) << 23);
+    return {t.hi * scale, t.lo * scale};
+}
+
+// Table-driven sin and cos of phi for |phi.hi| < 6000: phi = q pi/2 + s
+// (Cody-Waite, as df_sincos), s = j pi/64 + r with |j| <= 16, |r| <= pi/128;
+// sin s = S_j cos r + C_j sin r, cos s = C_j cos r - S_j sin r with
+//   sin r = r (1 - r^2/6 + r^4/120 - r^6/5040),
+//   cos r = 1 - r^2/2 + r^4/24 - r^6/720 + r^8/40320
+// (remainders < 1e-19 relative); the angle-addition table method (e.g.
+// J.-M. Muller, "Elementary Functions", ch. 6).
+__device__ __forceinline__ void df_sincos_tab(df phi, const DfTables &T, const DfConsts &K,
+                                              df &s_out, df &c_out) {
+    const float qf = rintf(phi.hi * 0.636619772367581343076f);
+    df s = df_two_sum(fmaf(-qf, K.pio2_1, phi.hi), phi.lo);
+    s = df_add_f(s, -qf * K.pio2_2);
+    s = df_add_f(s, -qf * K.pio2_3);
+    s = df_add_f(s, -qf * K.pio2_4);
+    float jf = rintf(s.hi * 20.371832715762604f);  // 64 / pi
+    jf = fminf(fmaxf(jf, -16.0f), 16.0f);
+    df r = df_two_sum(fmaf(-jf, K.pi64_1, s.hi), s.lo);  // exact product
+    r = df_add_f(r, -jf * K.pi64_2);                      // exact product
+    r = df_add_f(r, -jf * K.pi64_3);
+    const df r2 = df_mul(r, r);
+    const float x = r2.hi;
+    const float ts = x * x * fmaf(-x, 1.0f / 5040.0f, 1.0f / 120.0f);
+    const df sixth = {-0x1.555556p-3f, 0x1.555556p-28f};  // -1/6
+    const df sr = df_mul(r, df_add_f(df_add_f(df_mul(r2, sixth), ts), 1.0f));
+    const float tc = x * x * fmaf(fmaf(x, 1.0f / 40320.0f, -1.0f / 720.0f), x, 1.0f / 24.0f);
+    const df cr = df_add_f(df_add_f(df{-0.5f * r2.hi, -0.5f * r2.lo}, tc), 1.0f);
+    const int j = (int)jf + 16;
+    const df S = T.sn[j], C = T.cs[j];
+    const df sn = df_add(df_mul(S, cr), df_mul(C, sr));
+    const df cs = df_sub(df_mul(C, cr), df_mul(S, sr));
+    switch (((int)qf) & 3) {
+        case 0: s_out = sn; c_out = cs; break;
+        case 1: s_out = cs; c_out = df_neg(sn); break;
+        case 2: s_out = df_neg(sn); c_out = df_neg(cs); break;
+        default: s_out = df_neg(cs); c_out = sn; break;
     }
 }
 

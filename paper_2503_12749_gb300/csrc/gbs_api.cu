@@ -172,8 +172,9 @@ __global__ void k_t64_from_dev(const double *__restrict__ T, int N, int M, doubl
 }
 
 // T (device) -> BF16 planes of A = [Re T_i.; Im T_i.] (rows interleaved per
-// mode, pitch ldK), T rounded to FP32 and split T = T0 + T1 + T2.
-__global__ void k_split_from_dev(const double *__restrict__ T, int N, int M, int ldK,
+// mode, K-blocked: element (row, j) at ((j / 32) * rows + row) * 32 + j % 32),
+// T rounded to FP32 and split T = T0 + T1 + T2.
+__global__ void k_split_from_dev(const double *__restrict__ T, int N, int M, int rows,
                                  __nv_bfloat16 *__restrict__ A, size_t plane,
                                  unsigned long long *nonfinite) {
     const int64_t total = (int64_t)M * N;
@@ -188,7 +189,7 @@ __global__ void k_split_from_dev(const double *__restrict__ T, int N, int M, int
             const float r1 = x - __bfloat162float(h0);
             const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
             const float r2 = r1 - __bfloat162float(h1);
-            const size_t o = (size_t)(2 * i + c) * ldK + j;
+            const size_t o = ((size_t)(j >> 5) * rows + (size_t)(2 * i + c)) * 32 + (j & 31);
             A[o] = h0;
             A[plane + o] = h1;
             A[2 * plane + o] = __float2bfloat16_rn(r2);
@@ -360,10 +361,12 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
             return fail(set_error(GBS_ECUDA, "upload of T failed"));
     } else {
         // A = [Re T_i.; Im T_i.] rows interleaved per output mode, T rounded to
-        // FP32 and split into BF16 planes T = T0 + T1 + T2.
+        // FP32 and split into BF16 planes T = T0 + T1 + T2, each plane
+        // K-blocked [ldK / 32][rowsA][32] so that a 32-wide K block of
+        // consecutive rows is one contiguous run of memory.
         net->planesA = 3;
         net->planesB = (precision == GBS_BF16X3) ? 2 : 3;
-        net->ldK = (N + 7) / 8 * 8;
+        net->ldK = (N + 31) / 32 * 32;  // K padded to whole 32-wide blocks
         net->rowsA = 2 * M;
         const size_t plane = (size_t)net->rowsA * net->ldK;
         if (T_device) {
@@ -376,7 +379,7 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
                 dev_free(d_bad);
                 return fail(set_error(GBS_ECUDA, "memset of T planes failed"));
             }
-            k_split_from_dev<<<conv_blocks, 256, 0, net->stream>>>(T, N, M, net->ldK, net->d_A,
+            k_split_from_dev<<<conv_blocks, 256, 0, net->stream>>>(T, N, M, net->rowsA, net->d_A,
                                                                   plane, d_bad);
             rc = finish_device_T(net, d_bad);
             dev_free(d_bad);
@@ -395,7 +398,8 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
                     const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
                     const float r2 = r1 - __bfloat162float(h1);
                     const __nv_bfloat16 h2 = __float2bfloat16_rn(r2);
-                    const size_t o = ((size_t)2 * i + c) * net->ldK + j;
+                    const size_t o =
+                        ((size_t)(j >> 5) * net->rowsA + (size_t)(2 * i + c)) * 32 + (j & 31);
                     a[o] = h0;
                     a[plane + o] = h1;
                     a[2 * plane + o] = h2;

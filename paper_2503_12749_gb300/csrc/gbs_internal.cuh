@@ -63,8 +63,8 @@ struct TcPlan;  // tcgen05 GEMM plan (tensor maps, tiling), defined in k_gemm_tc
 // Operand description of one network for the (grouped) tcgen05 GEMM, kept in
 // device memory so that one launch can serve many networks.
 struct __align__(128) GemmNetDesc {
-    CUtensorMap mapA[3];     // A planes, box 32 x 128
-    CUtensorMap mapB[2][3];  // B planes, box 32 x 256 (clusters of 1) / 32 x 128 (of 2)
+    CUtensorMap mapA[3];     // A planes [K/32][rows][32], box 32 x 128 x 1
+    CUtensorMap mapB[2][3];  // B planes, box 32 x 256 x 1 (clusters of 1) / 32 x 128 x 1 (of 2)
     int KB;                  // 32-wide K blocks
     int mtiles;              // 64-mode tiles
     int stiles;              // 128-trajectory tiles (grouped launches)
@@ -97,7 +97,8 @@ struct gbs_net {
     double *d_T64 = nullptr;
 
     // BF16 split operands (GBS_BF16X3 / X6): planes of A = [Re T; Im T] rows
-    // interleaved per mode, padded: [planes][rowsA][ldK] bf16
+    // interleaved per mode, K-blocked: [planes][ldK / 32][rowsA][32] bf16,
+    // ldK = N rounded up to a multiple of 32 (the sample operand likewise)
     __nv_bfloat16 *d_A = nullptr;
     int planesA = 0, planesB = 0, rowsA = 0, ldK = 0;
     gbs::TcPlan *tc = nullptr;

@@ -29,7 +29,10 @@
 // delivers each B tile once per pair.  A stage is refilled only after
 // every CTA's MMAs released it (their commits arrive on all CTAs' barriers).
 //   warp 0      TMA producer: per 32-wide K block one box per BF16 plane used
-//               (A: 32 x 128, B: 32 x 256, 64-byte swizzle), every plane loaded
+//               (A: 32 x 128, B: 32 x 256, 64-byte swizzle; the operands are
+//               stored K-blocked, [K/32][rows][32], so each box is one
+//               contiguous run of 8 or 16 KB and no row fetch moves unused
+//               bytes), every plane loaded
 //               once per K block, into a 4-stage (3 products) or 3-stage
 //               (6 products) shared-memory ring;
 //   warp 1      allocates 512 TMEM columns; one thread issues
@@ -251,20 +254,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     const uint32_t fb = ptx::smem_u32(&full[stage]);
                     ptx::mbar_arrive_expect_tx(fb, C::kStageBytes);
+                    // operands are K-blocked ([K/32][rows][32]): each box is
+                    // one contiguous block of global memory
 #pragma unroll
                     for (int q = 0; q < kPl; ++q)
-                        ptx::tma_load_2d(ptx::smem_u32(a_tile(stage, q)), mA[q], fb, kb * 32,
-                                         tr.mt * 128);
+                        ptx::tma_load_3d(ptx::smem_u32(a_tile(stage, q)), mA[q], fb, 0,
+                                         tr.mt * 128, kb);
                     const int brow = tr.st * 256 + (int)rank * (256 / kCl);
                     const uint32_t bpart = rank * (uint32_t)(C::kBPlane / kCl);
 #pragma unroll
                     for (int q = 0; q < kPl; ++q) {
                         if (kCl > 1)
-                            ptx::tma_load_2d_mc(ptx::smem_u32(b_tile(stage, q)) + bpart, mB[q], fb,
-                                                kb * 32, brow, kMask);
+                            ptx::tma_load_3d_mc(ptx::smem_u32(b_tile(stage, q)) + bpart, mB[q], fb,
+                                                0, brow, kb, kMask);
                         else
-                            ptx::tma_load_2d(ptx::smem_u32(b_tile(stage, q)), mB[q], fb, kb * 32,
-                                             brow);
+                            ptx::tma_load_3d(ptx::smem_u32(b_tile(stage, q)), mB[q], fb, 0, brow,
+                                             kb);
                     }
                     used |= 1u << stage;
                     last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
@@ -522,21 +527,39 @@ int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets,
     return GBS_OK;
 }
 
+// Tensor map of a K-blocked BF16 plane [KB][rows][32] read in boxes of
+// 32 x box_rows x 1 (one K block of box_rows rows: box_rows * 64 contiguous
+// bytes), 64-byte swizzle.  Out-of-range rows read as zeros.
+int encode_kblocked(CUtensorMap *map, void *base, uint64_t rows, uint64_t KB, uint32_t box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+    if (!enc) return set_error(GBS_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[3] = {32, rows, KB};
+    cuuint64_t strides[2] = {64, rows * 64};
+    cuuint32_t box[3] = {32, box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(GBS_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return GBS_OK;
+}
+
 int encode_net_maps(gbs_net *net, GemmNetDesc &d) {
+    const int KB = net->ldK / 32;
     const size_t planeA = (size_t)net->rowsA * net->ldK;
     const int64_t tiles = (net->chunk + kTcTileSamples - 1) / kTcTileSamples;
     const int64_t rowsB = tiles * 256;
     const size_t planeB = (size_t)rowsB * net->ldK;
     int rc;
     for (int q = 0; q < 3; ++q) {
-        if ((rc = encode_2d(&d.mapA[q], net->d_A + q * planeA, (uint64_t)net->N,
-                            (uint64_t)net->rowsA, (uint64_t)net->ldK * 2, 32, 128)))
+        if ((rc = encode_kblocked(&d.mapA[q], net->d_A + q * planeA, (uint64_t)net->rowsA,
+                                  (uint64_t)KB, 128)))
             return rc;
         __nv_bfloat16 *bbase = static_cast<__nv_bfloat16 *>(net->d_B) +
                                (q < net->planesB ? q : 0) * planeB;
         for (int c = 0; c < 2; ++c)
-            if ((rc = encode_2d(&d.mapB[c][q], bbase, (uint64_t)net->N, (uint64_t)rowsB,
-                                (uint64_t)net->ldK * 2, 32, 256 / (c + 1))))
+            if ((rc = encode_kblocked(&d.mapB[c][q], bbase, (uint64_t)rowsB, (uint64_t)KB,
+                                      256 / (c + 1))))
                 return rc;
     }
     d.KB = (net->N + 31) / 32;

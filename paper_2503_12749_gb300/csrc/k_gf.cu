@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(256) k_gf_fp64(const double *__restrict__ n_in
 // double-float ranges (|phi| >= 6000, exponents >= 80: only the +P heavy
 // tail) are evaluated in FP64 and added to the FP64 sums directly.  Per thread, double-float partial sums over 64
 // trajectories are added to FP64 accumulators.
-__device__ __forceinline__ df df_exp_small(df a, const DfConsts &K) {
-    return a.hi < -87.0f ? df{0.0f, 0.0f} : df_exp(a, K);  // below 1e-37: nothing
+__device__ __forceinline__ df df_exp_small(df a, const DfTables &T, const DfConsts &K) {
+    return a.hi < -87.0f ? df{0.0f, 0.0f} : df_exp_tab(a, T, K);  // below 1e-37: nothing
 }
 
 // k of slot i: slots enumerate the union window around theta = 0
@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 1)
     __shared__ double s_xd[kGfTile], s_yd[kGfTile], s_c1d[kGfTile], s_c2d[kGfTile];
     __shared__ int s_w1[kGfTile], s_w2[kGfTile];
     __shared__ double s_red[kGfGroups][4][kGfSlots];
+    __shared__ DfTables s_tab;
 
     const int r = blockIdx.y;
     const int W1 = wmax[0], W2 = wmax[1];
@@ -253,6 +254,11 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 1)
     const bool kvalid = k >= 0;
     const int d0 = kvalid ? dist0(k, K1) : 0x3fffffff;
     const int dpi = kvalid ? dist_pi(k, K1) : 0x3fffffff;
+    if (threadIdx.x < 64) s_tab.exp2[threadIdx.x] = df{K.exp2_hi[threadIdx.x], K.exp2_lo[threadIdx.x]};
+    if (threadIdx.x < 33) {
+        s_tab.sn[threadIdx.x] = df{K.sin_hi[threadIdx.x], K.sin_lo[threadIdx.x]};
+        s_tab.cs[threadIdx.x] = df{K.cos_hi[threadIdx.x], K.cos_lo[threadIdx.x]};
+    }  // visible after the first __syncthreads of the tile loop
 
     const int64_t first = (int64_t)(((uint64_t)r + (uint64_t)n_sub - e0 % (uint64_t)n_sub) %
                                     (uint64_t)n_sub);
@@ -322,15 +328,15 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 1)
                     continue;
                 }
                 df sp, cp;
-                df_sincos(ph, K, sp, cp);
+                df_sincos_tab(ph, s_tab, K, sp, cp);
                 df e1 = {0.0f, 0.0f}, e2 = {0.0f, 0.0f};
                 if (in1) {
-                    e1 = df_exp_small(a1, K);
-                    const df gp = (c1.hi == 0.0f) ? e1 : df_exp_small(l1, K);
+                    e1 = df_exp_small(a1, s_tab, K);
+                    const df gp = (c1.hi == 0.0f) ? e1 : df_exp_small(l1, s_tab, K);
                     pp_re = df_add(pp_re, df_mul(gp, cp));
                     pp_im = df_add(pp_im, df_mul(gp, sp));
                 }
-                if (in2) e2 = df_exp_small(a2, K);
+                if (in2) e2 = df_exp_small(a2, s_tab, K);
                 const df inv = s_inv[j];
                 pm_re = df_add(pm_re, df_mul(df_mul(df_add(e1, e2), inv), cp));
                 pm_im = df_add(pm_im, df_mul(df_mul(df_sub(e1, e2), inv), sp));
@@ -384,6 +390,27 @@ DfConsts make_df_consts() {
         const double v = 1.0 / f;
         K.inv_fact_hi[k] = (float)v;
         K.inv_fact_lo[k] = (float)(v - (double)K.inv_fact_hi[k]);
+    }
+    // ln 2 / 64 and pi / 64 in pieces whose products with the table index
+    // (|n| < 2^13, |j| <= 16) are exact, from 60-digit expansions
+    K.ln2_64_1 = 0x1.63p-7f;
+    K.ln2_64_2 = -0x1.bdp-19f;
+    K.ln2_64_3 = -0x1.05c61p-35f;
+    K.pi64_1 = 0x1.921f8p-5f;
+    K.pi64_2 = 0x1.aa22p-24f;
+    K.pi64_3 = 0x1.68c234p-44f;
+    for (int j = 0; j < 64; ++j) {
+        const double v = std::exp2((double)j / 64.0);
+        K.exp2_hi[j] = (float)v;
+        K.exp2_lo[j] = (float)(v - (double)K.exp2_hi[j]);
+    }
+    const double pi = 3.14159265358979323846264338327950288;
+    for (int j = -16; j <= 16; ++j) {
+        const double sv = std::sin((double)j * pi / 64.0), cv = std::cos((double)j * pi / 64.0);
+        K.sin_hi[j + 16] = (float)sv;
+        K.sin_lo[j + 16] = (float)(sv - (double)K.sin_hi[j + 16]);
+        K.cos_hi[j + 16] = (float)cv;
+        K.cos_lo[j + 16] = (float)(cv - (double)K.cos_hi[j + 16]);
     }
     return K;
 }

@@ -14,8 +14,9 @@
 // Layouts written:
 //   FP64 path: B[e][c][N] doubles, c = 0 (alpha), 1 (beta).
 //   BF16 path: per 128-trajectory tile, 256 rows (128 alpha rows, then 128
-//   beta rows), each row ldK bf16; planes B0 = bf16(x), B1 = bf16(x - B0),
-//   B2 = bf16(x - B0 - B1) stored plane-major [planesB][rows][ldK].
+//   beta rows); planes B0 = bf16(x), B1 = bf16(x - B0), B2 = bf16(x - B0 -
+//   B1) stored plane-major, each plane K-blocked [ldK / 32][rows][32]
+//   (mode j of row q at ((j / 32) * rows + q) * 32 + j % 32).
 // Both also write n_e = sum_j alpha_j beta_j (FP64 result).
 #include "gbs_internal.cuh"
 
@@ -129,8 +130,9 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16 &h0, __nv_bfloat16
 }
 
 __global__ void k_sample_bf16(const float2 *__restrict__ sq, int N, int ldK, int planesB,
-                              size_t plane_stride, uint64_t seed, uint64_t e0, int64_t count,
-                              __nv_bfloat16 *__restrict__ B, double *__restrict__ n_out) {
+                              size_t plane_stride, size_t rows, uint64_t seed, uint64_t e0,
+                              int64_t count, __nv_bfloat16 *__restrict__ B,
+                              double *__restrict__ n_out) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -138,8 +140,8 @@ __global__ void k_sample_bf16(const float2 *__restrict__ sq, int N, int ldK, int
         const uint64_t e = e0 + (uint64_t)i;
         const int64_t tile = i >> 7;
         const int q = (int)(i & 127);
-        const size_t row_a = (size_t)(tile * 256 + q) * ldK;
-        const size_t row_b = (size_t)(tile * 256 + 128 + q) * ldK;
+        const size_t row_a = (size_t)(tile * 256 + q) * 32;
+        const size_t row_b = (size_t)(tile * 256 + 128 + q) * 32;
         // Kahan-compensated FP32 partial of sum_j alpha_j beta_j
         float s = 0.0f, comp = 0.0f;
         for (int j0 = 4 * lane; j0 < N; j0 += 128) {
@@ -163,19 +165,22 @@ __global__ void k_sample_bf16(const float2 *__restrict__ sq, int N, int ldK, int
                 split3(b, b0[t], b1[t], b2[t]);
             }
             if (j0 + 3 < ldK) {
-                // ldK is a multiple of 8, j0 a multiple of 4: 8-byte aligned stores
-                *reinterpret_cast<uint2 *>(B + row_a + j0) = *reinterpret_cast<uint2 *>(a0);
-                *reinterpret_cast<uint2 *>(B + row_b + j0) = *reinterpret_cast<uint2 *>(b0);
+                // ldK is a multiple of 32 and j0 of 4: the 4 modes lie in one
+                // K block, 8-byte aligned
+                const size_t blk = (size_t)(j0 >> 5) * rows * 32 + (size_t)(j0 & 31);
+                const size_t oa = blk + row_a, ob = blk + row_b;
+                *reinterpret_cast<uint2 *>(B + oa) = *reinterpret_cast<uint2 *>(a0);
+                *reinterpret_cast<uint2 *>(B + ob) = *reinterpret_cast<uint2 *>(b0);
                 if (planesB > 1) {
-                    *reinterpret_cast<uint2 *>(B + plane_stride + row_a + j0) =
+                    *reinterpret_cast<uint2 *>(B + plane_stride + oa) =
                         *reinterpret_cast<uint2 *>(a1);
-                    *reinterpret_cast<uint2 *>(B + plane_stride + row_b + j0) =
+                    *reinterpret_cast<uint2 *>(B + plane_stride + ob) =
                         *reinterpret_cast<uint2 *>(b1);
                 }
                 if (planesB > 2) {
-                    *reinterpret_cast<uint2 *>(B + 2 * plane_stride + row_a + j0) =
+                    *reinterpret_cast<uint2 *>(B + 2 * plane_stride + oa) =
                         *reinterpret_cast<uint2 *>(a2);
-                    *reinterpret_cast<uint2 *>(B + 2 * plane_stride + row_b + j0) =
+                    *reinterpret_cast<uint2 *>(B + 2 * plane_stride + ob) =
                         *reinterpret_cast<uint2 *>(b2);
                 }
             }
@@ -211,9 +216,10 @@ int launch_sample_bf16(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) 
     if (count <= 0) return GBS_OK;
     const int threads = 256;
     const int64_t tiles = (net->chunk + kTcTileSamples - 1) / kTcTileSamples;
-    const size_t plane_stride = (size_t)tiles * 256 * net->ldK;
+    const size_t rows = (size_t)tiles * 256;
+    const size_t plane_stride = rows * net->ldK;
     k_sample_bf16<<<grid_for_warps(net, count, threads), threads, 0, net->stream>>>(
-        net->d_sq32, net->N, net->ldK, net->planesB, plane_stride, seed, e0, count,
+        net->d_sq32, net->N, net->ldK, net->planesB, plane_stride, rows, seed, e0, count,
         static_cast<__nv_bfloat16 *>(net->d_B), net->d_n);
     GBS_LAUNCH_CHECK();
     return GBS_OK;

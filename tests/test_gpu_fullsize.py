@@ -10,6 +10,8 @@ At these sizes the oracle cannot run the whole ensemble, so:
     trajectories (|dP| <= sigma_FP64 on every bin) at the full N;
   * sum_m P(m) = 1 and the uniform-loss identity n_S = t^2 n per trajectory.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -82,3 +84,37 @@ def test_split_precision_gate_at_full_N(gbs, name):
         ratio = np.abs(res["bf16x3"][est] - res["fp64"][est]) / np.maximum(res["fp64"][est + 1],
                                                                             1e-13)
         assert ratio.max() <= 1.0, (name, est, ratio.max())
+
+
+@pytest.mark.slow
+def test_m8000_workload(gbs):
+    """N = M = 8000, r = 1, t^2 = 0.99, E = 2^20, K1 = 16384: sampled
+    trajectories against the oracle, the whole ensemble against the exact
+    distribution.  The Haar matrix is the QR of the workload's seeded Ginibre
+    draw computed on the GPU (equal to the host QR up to rounding); both sides
+    use the same T."""
+    import torch
+    w = wl.NAMED["m8000"]
+    T = (math.sqrt(w.t2) * wl.haar_unitary_device(w.N, wl.SEED_U_BASE + w.index)).cpu().numpy()
+    T = np.ascontiguousarray(T)
+    r = np.full(w.N, 1.0)
+    seed = wl.SEED_S_BASE + w.index
+    s = torch.cuda.Stream()
+    net = gbs.gbs_make_network(T, r, "bf16x3", s.cuda_stream)
+    for e in (0, 123457, w.E - 1):
+        n, nS = gbs.gbs_debug_samples(net, seed, e, 1)
+        no, nSo = oracle.samples(T, r, seed, e, 1)
+        _, _, ap, bp = oracle.sample_amplitudes(T, r, seed, e)
+        S = float(np.sum(np.abs(ap) * np.abs(bp)))
+        assert abs(nS[0] - nSo[0]) <= 2.0 ** -14 * S, (e, nS[0], nSo[0])
+        assert abs(n[0] - no[0]) <= 1e-5 * max(abs(no[0]), 1.0)
+    gbs.gbs_sample(net, seed, 0, w.E, w.n_sub, w.K1)
+    P = gbs.gbs_binned_counts(net, 0, w.K1)
+    gbs.gbs_free_network(net)
+    mu = ex.eigenvalues_uniform_loss(r, w.t2)
+    z = ex.roots_of_unity(w.K1)
+    G = np.concatenate([ex.gf_from_eigenvalues(mu, z[a:a + 256]) for a in range(0, w.K1, 256)])
+    Pex = ex.distribution_from_gf(G).real
+    res = agreement(P[0], P[1], Pex)
+    assert res["ok"], res
+    assert abs(P[0].sum() - 1.0) < 1e-9
