@@ -88,6 +88,24 @@ __device__ __forceinline__ void normals_fp32(uint64_t seed, uint64_t e, uint32_t
     w2 = rho * s;
 }
 
+// The same normals with the SFU approximations of ln and sin/cos (absolute
+// errors ~2^-21 on these arguments) for the 3-product BF16 path, whose sample
+// operand keeps two BF16 planes (~16 significant bits) of each amplitude:
+// 2 pi u2 is shifted to [-pi, pi) (sin and cos change sign) where the SFU
+// sine and cosine are specified.
+__device__ __forceinline__ void normals_fp32_sfu(uint64_t seed, uint64_t e, uint32_t j, float &w1,
+                                                 float &w2) {
+    uint32_t c0 = (uint32_t)e, c1 = (uint32_t)(e >> 32), c2 = j, c3 = 0u;
+    philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const float u1 = uniform53_f(c0, c1);
+    const float u2 = uniform53_f(c2, c3);
+    const float rho = sqrtf(-2.0f * __logf(u1));
+    float s, c;
+    __sincosf(6.283185307179586f * (u2 - 0.5f), &s, &c);
+    w1 = -rho * c;
+    w2 = -rho * s;
+}
+
 // ---------------------------------------------------------------------------
 // FP64 path: one warp per trajectory, lanes stride over input modes.
 // ---------------------------------------------------------------------------
@@ -129,6 +147,7 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16 &h0, __nv_bfloat16
     h2 = __float2bfloat16_rn(r2);
 }
 
+template <bool kSfu>
 __global__ void k_sample_bf16(const float2 *__restrict__ sq, int N, int ldK, int planesB,
                               size_t plane_stride, size_t rows, uint64_t seed, uint64_t e0,
                               int64_t count, __nv_bfloat16 *__restrict__ B,
@@ -152,7 +171,10 @@ __global__ void k_sample_bf16(const float2 *__restrict__ sq, int N, int ldK, int
                 float a = 0.0f, b = 0.0f;
                 if (j < N) {
                     float w1, w2;
-                    normals_fp32(seed, e, (uint32_t)j, w1, w2);
+                    if (kSfu)
+                        normals_fp32_sfu(seed, e, (uint32_t)j, w1, w2);
+                    else
+                        normals_fp32(seed, e, (uint32_t)j, w1, w2);
                     const float2 c = sq[j];
                     a = fmaf(c.x, w1, c.y * w2);
                     b = fmaf(c.x, w1, -c.y * w2);
@@ -218,7 +240,8 @@ int launch_sample_bf16(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) 
     const int64_t tiles = (net->chunk + kTcTileSamples - 1) / kTcTileSamples;
     const size_t rows = (size_t)tiles * 256;
     const size_t plane_stride = rows * net->ldK;
-    k_sample_bf16<<<grid_for_warps(net, count, threads), threads, 0, net->stream>>>(
+    auto kern = net->planesB == 2 ? k_sample_bf16<true> : k_sample_bf16<false>;
+    kern<<<grid_for_warps(net, count, threads), threads, 0, net->stream>>>(
         net->d_sq32, net->N, net->ldK, net->planesB, plane_stride, rows, seed, e0, count,
         static_cast<__nv_bfloat16 *>(net->d_B), net->d_n);
     GBS_LAUNCH_CHECK();
