@@ -185,8 +185,9 @@ def gbs_arm(args, wl_def):
     net = gbs.gbs_make_network(netdef.T, netdef.r, precision, sptr)
     out = torch.empty(4 * K1, dtype=torch.float64, device="cuda")
     seed = netdef.seed_s
-    # rank r draws trajectories [r * R, (r + 1) * R) with R = (W + K) * E
-    base = rank * (args.warmup + args.steps) * E
+    # rank r draws trajectories [r * R, (r + 1) * R) with R = (W + K + 2) * E
+    # (warm-up, timed and 2 phase-timing steps)
+    base = rank * (args.warmup + args.steps + 2) * E
 
     def step(s):
         gbs.gbs_sample(net, seed, base + s * E, E, n_sub, K1)
@@ -200,7 +201,6 @@ def gbs_arm(args, wl_def):
         dist.barrier()
     clocks = ClockSampler(dev)
     clocks.start()
-    gbs.gbs_profile_enable(net, True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -213,10 +213,18 @@ def gbs_arm(args, wl_def):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    prof = gbs.gbs_profile_read(net)
-    gbs.gbs_profile_enable(net, False)
     clk = clocks.stop()
     ms_total = ev0.elapsed_time(ev1)
+    # kernel times per phase: further steps with phase timing on (events
+    # around every phase), scaled to the timed steps
+    nprof = 2
+    gbs.gbs_profile_enable(net, True)
+    for s in range(nprof):
+        step(args.warmup + args.steps + s)
+    torch.cuda.synchronize()
+    prof = gbs.gbs_profile_read(net)
+    gbs.gbs_profile_enable(net, False)
+    prof = {k: (v[0] * args.steps / nprof, v[1] * args.steps // nprof) for k, v in prof.items()}
     if dist:
         t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -238,7 +246,7 @@ def gbs_arm(args, wl_def):
     P = gbs.gbs_binned_counts(net, 0, K1)
     acc_summary = {"sum_P": float(np.sum(P[0])), "max_sigma_mP": float(np.max(P[1])),
                    "max_sigma_plusP": float(np.max(P[3])),
-                   "trajectories": int((args.warmup + args.steps) * E)}
+                   "trajectories": int((args.warmup + args.steps + nprof) * E)}
 
     # roofline of the dominant kernel (the propagation GEMM)
     peaks, peak_kind = _peaks()
@@ -290,7 +298,9 @@ def gbs_arm(args, wl_def):
                          "written and read every chunk)",
                    "network": "Haar U (QR of seeded complex Gaussian, phase-fixed), "
                               f"T = sqrt({wl_def.t2}) U",
-                   "binned_P_wall_ms": ms_step},
+                   "binned_P_wall_ms": ms_step,
+                   "phases_from": "2 further steps with phase timing (CUDA events around "
+                                  "each phase), scaled to the timed steps"},
         "roofline": roof,
         "phases": phases,
         "result": acc_summary,
