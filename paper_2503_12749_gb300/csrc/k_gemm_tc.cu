@@ -36,9 +36,11 @@
 //               once per K block, into a 4-stage (3 products) or 3-stage
 //               (6 products) shared-memory ring;
 //   warp 1      allocates 512 TMEM columns; one thread issues
-//               tcgen05.mma M=128 N=256 K=16, per segment of two K blocks the
-//               correction products first and A0 B0 last, into the segment's
-//               buffer;
+//               tcgen05.mma M=128 N=256 K=16 into the segment's buffer: with
+//               6 products, per segment of two K blocks the correction
+//               products of both blocks first and A0 B0 last; with 3
+//               products, block by block as the stages land (A1 B0, A0 B1,
+//               A0 B0), releasing each stage at once;
 //   warps 2..9  epilogue: warp w reads TMEM lanes 32 (w mod 4).. (its A rows)
 //               and half (w - 2) / 4 of the tile's trajectories: running
 //               sums of 64 alpha' and 64 beta' columns per thread.  After the
@@ -309,6 +311,43 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     const int nst = (2 * sg + 1 < KB) ? 2 : 1;
+                    if (P == 3) {
+                        // 3 products: each K block's MMAs as soon as its
+                        // stage lands (small products first within the
+                        // block), the stage released right after, so the
+                        // producer refills 3 stages ahead instead of 2
+                        const uint32_t d = tmem_base + b * 256u;
+                        uint32_t acc = 0u;
+                        for (int q = 0; q < nst; ++q) {
+                            if (!ptx::mbar_wait(ptx::smem_u32(&full[stage]), phase, err)) {
+                                ok = false;
+                                break;
+                            }
+                            ptx::tc_fence_after();
+#pragma unroll
+                            for (int pr = 0; pr < 3; ++pr) {
+                                const uint32_t a0 = ptx::smem_u32(a_tile(stage, kIa3[pr]));
+                                const uint32_t b0 = ptx::smem_u32(b_tile(stage, kIb3[pr]));
+#pragma unroll
+                                for (int kk = 0; kk < 2; ++kk) {
+                                    ptx::mma_bf16(d, ptx::desc_k_sw64(a0 + kk * 32),
+                                                  ptx::desc_k_sw64(b0 + kk * 32), kIdesc, acc);
+                                    acc = 1u;
+                                }
+                            }
+                            if (kCl > 1)
+                                ptx::mma_commit_mc(ptx::smem_u32(&empty[stage]), kMask);
+                            else
+                                ptx::mma_commit(ptx::smem_u32(&empty[stage]));
+                            if (++stage == kStages) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                        }
+                        if (!ok) break;
+                        ptx::mma_commit(ptx::smem_u32(&tfull[b]));
+                        continue;
+                    }
                     int stg[2];
                     stg[0] = stage;
                     stg[1] = (stage + 1 == kStages) ? 0 : stage + 1;
