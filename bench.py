@@ -34,10 +34,10 @@ UNIT = "samples/s"
 
 # DRAM bytes (read + write) of the GEMM kernel per trajectory, from the ncu
 # capture of one m1000 BF16x3 launch of 131072 trajectories
-# (profiles/k_gemm_tc_m1000_bf16x3.md: 1.0581 GB read + 0.0356 GB written);
+# (profiles/k_gemm_tc_m1000_bf16x3.md: 1.0845 GB read + 0.0360 GB written);
 # the sample operand it reads grows in proportion to the trajectories.  Valid
 # for the workload and kernel version of that capture only.
-GEMM_TRAFFIC_BYTES_PER_SAMPLE = {("m1000", "bf16x3"): (1.058080e9 + 35.579904e6) / 131072}
+GEMM_TRAFFIC_BYTES_PER_SAMPLE = {("m1000", "bf16x3"): (1.084537e9 + 36.007936e6) / 131072}
 
 
 def _env_int(name, default):
@@ -263,6 +263,7 @@ def gbs_arm(args, wl_def):
                 "algorithmic_flops_per_sample": 8 * netdef.M * netdef.N,
                 "mma_products": P_products, "mma_issued_frac": P_products * achieved / peak,
                 "kernel": "k_gemm_tc", "launches": gemm_launches,
+                "cluster": gbs.gbs_gemm_config(net),
                 "avg_launch_ms": gemm_ms / max(gemm_launches, 1)}
         per_sample = GEMM_TRAFFIC_BYTES_PER_SAMPLE.get((wl_def.name.split(":")[0], precision))
         if per_sample is not None:
