@@ -187,7 +187,8 @@ def gbs_arm(args, wl_def):
     seed = netdef.seed_s
     # rank r draws trajectories [r * R, (r + 1) * R) with R = (W + K + 2) * E
     # (warm-up, timed and 2 phase-timing steps)
-    base = rank * (args.warmup + args.steps + 2) * E
+    from paper_2503_12749_gb300 import distributed as gdist
+    base, _ = gdist.rank_range(rank, world, (args.warmup + args.steps + 2) * E)
 
     def step(s):
         gbs.gbs_sample(net, seed, base + s * E, E, n_sub, K1)
@@ -231,12 +232,8 @@ def gbs_arm(args, wl_def):
         ms_total = float(t.item())
         # combine sub-ensemble sums of all ranks (the estimator's one exchange)
         _, _, acc, cnt = gbs.gbs_get_accumulators(net)
-        ta = torch.from_numpy(acc.view(np.float64).copy()).cuda()
-        tc = torch.from_numpy(cnt.copy()).cuda()
-        dist.all_reduce(ta)
-        dist.all_reduce(tc)
-        gbs.gbs_set_accumulators(net, ta.cpu().numpy().view(np.complex128).reshape(acc.shape),
-                                 tc.cpu().numpy())
+        acc_all, cnt_all = gdist.combine_accumulators(acc, cnt, device="cuda")
+        gbs.gbs_set_accumulators(net, acc_all, cnt_all)
     ms_step = ms_total / args.steps
     value = world * E * args.steps / (ms_total / 1e3)
 
