@@ -109,6 +109,46 @@ int gbs_sample(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, i
                int K1);
 
 /*
+ * gbs_make_network_binned -- a network whose output modes are divided into
+ * two bins S_1, S_2 for the joint distribution G(m_1, m_2) of Eq.
+ * General_GCP with d = 2 and every mode binned ("Higher-dimensional
+ * binning").  bin: host, M ints, bin[i] = 0 (S_1) or 1 (S_2), both bins
+ * non-empty.  Other arguments as gbs_make_network.  The library stores the
+ * rows of each bin contiguously, padded with zero rows to whole 64-mode
+ * tiles, so gbs_network_info reports the padded M; gbs_sample still gives
+ * the total-count distribution.  Errors as gbs_make_network.
+ */
+int gbs_make_network_binned(int N, int M, const double *T, const double *r, const int *bin,
+                            int precision, void *stream, gbs_net_t *out);
+
+/*
+ * gbs_sample_2d -- trajectories first..first+E-1 of a binned network into
+ * the two-bin sums: per trajectory the generating function
+ *   G_mP(z_1, z_2) = cosh(n + (z_1-1) n_S1 + (z_2-1) n_S2) / cosh(n),
+ *   G_+P(z_1, z_2) = exp((z_1-1) n_S1 + (z_2-1) n_S2),
+ * n_Sb = sum over the output modes i of bin b of alpha'_i beta'_i, at
+ * z_b = exp(2 pi i k_b / K_b) (the one-bin form of Eq. c-number-variable
+ * with the exponent summed over the bins), summed per sub-ensemble (e mod
+ * n_sub).  K1, K2: powers of two, K1 K2 <= 2^22; the first call fixes
+ * (n_sub, K1, K2) until gbs_reset.  Generating functions in FP64 for every
+ * precision.  Errors: EINVAL (not a binned network, sizes), ENOMEM, ECUDA.
+ */
+int gbs_sample_2d(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub,
+                  int K1, int K2);
+
+/*
+ * gbs_binned_counts_2d -- the two-dimensional inverse DFT of the two-bin
+ * sums and their statistics over sub-ensembles:
+ *   P_r(m_1, m_2) = (1/(K1 K2)) sum_k <G>_r(z) z_1^{-m_1} z_2^{-m_2},
+ * m_b = m_b_offset .. m_b_offset + K_b - 1, P = mean_r Re P_r, sigma =
+ * std_r / sqrt(N_R).  Host outputs of K1*K2 doubles each, [m_1][m_2]
+ * row-major; any may be NULL.  Synchronises the stream.  Errors: EINVAL,
+ * ECUDA.
+ */
+int gbs_binned_counts_2d(gbs_net_t net, int64_t m1_offset, int64_t m2_offset, double *P_mP,
+                         double *sig_mP, double *P_plusP, double *sig_plusP);
+
+/*
  * gbs_binned_counts -- inverse DFT of the sub-ensemble means and the
  * statistics over sub-ensembles (Eq. total_counts; errors Appendix A):
  *   P_r(m) = (1/K1) sum_k <G>_r(z_k) z_k^{-m},  m = m_offset .. m_offset+K1-1,

@@ -84,6 +84,11 @@ def lib():
         L.gbs_binned_counts_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int64, vp, vp]
         L.gbs_set_gemm_config.argtypes = [vp, ctypes.c_int]
+        L.gbs_make_network_binned.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ip, ctypes.c_int,
+                                              vp, ctypes.POINTER(vp)]
+        L.gbs_sample_2d.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.gbs_binned_counts_2d.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp]
         L.gbs_gemm_config.argtypes = [vp, ip]
         L.gbs_make_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
         L.gbs_sample_batch.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64),
@@ -121,7 +126,8 @@ def lib():
                      "gbs_network_info", "gbs_profile_enable", "gbs_profile_read",
                      "gbs_binned_counts_noalloc", "gbs_set_gemm_config", "gbs_gemm_config",
                      "gbs_make_batch", "gbs_sample_batch", "gbs_batch_info",
-                     "gbs_make_network_device", "gbs_mlp_create", "gbs_mlp_param_count",
+                     "gbs_make_network_device", "gbs_make_network_binned", "gbs_sample_2d",
+                     "gbs_binned_counts_2d", "gbs_mlp_create", "gbs_mlp_param_count",
                      "gbs_mlp_set_params", "gbs_mlp_get_params", "gbs_mlp_get_adam_state",
                      "gbs_mlp_forward", "gbs_mlp_gradients", "gbs_mlp_train",
                      "gbs_surrogate_features", "gbs_surrogate_feature_stats",
@@ -192,6 +198,37 @@ def gbs_make_network_device(T_dev_ptr: int, M: int, N: int, r: np.ndarray, preci
                                          int(precision), ctypes.c_void_p(stream),
                                          ctypes.byref(out)))
     return Network(out.value, N, M, int(precision), stream)
+
+
+def gbs_make_network_binned(T: np.ndarray, r: np.ndarray, bins, precision=GBS_FP64,
+                            stream: int = 0) -> Network:
+    """T: complex (M, N); bins: M ints in {0, 1} (the bin of each output mode)."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    T = np.ascontiguousarray(T, dtype=np.complex128)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    b = np.ascontiguousarray(bins, dtype=np.int32)
+    M, N = T.shape
+    if r.shape != (N,) or b.shape != (M,):
+        raise ValueError("r must have shape (N,) and bins (M,)")
+    out = ctypes.c_void_p()
+    _check(lib().gbs_make_network_binned(N, M, _dptr(T.view(np.float64)), _dptr(r),
+                                         b.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                         int(precision), ctypes.c_void_p(stream),
+                                         ctypes.byref(out)))
+    return Network(out.value, N, M, int(precision), stream)
+
+
+def gbs_sample_2d(net: Network, seed: int, first_sample: int, E: int, n_sub: int, K1: int,
+                  K2: int) -> None:
+    _check(lib().gbs_sample_2d(net.handle, seed, first_sample, E, n_sub, K1, K2))
+
+
+def gbs_binned_counts_2d(net: Network, K1: int, K2: int, m1_offset: int = 0, m2_offset: int = 0):
+    """(P_mP, sigma_mP, P_plusP, sigma_plusP), each (K1, K2)."""
+    outs = [np.zeros(K1 * K2) for _ in range(4)]
+    _check(lib().gbs_binned_counts_2d(net.handle, m1_offset, m2_offset, *[_dptr(o) for o in outs]))
+    return tuple(o.reshape(K1, K2) for o in outs)
 
 
 def gbs_sample(net: Network, seed: int, first_sample: int, E: int, n_sub: int, K1: int) -> None:

@@ -119,6 +119,16 @@ void release_estimator(gbs_net *net) {
     net->est_fixed = false;
     net->n_sub = 0;
     net->K1 = 0;
+    dev_free(net->d_acc2);
+    dev_free(net->d_counts2);
+    dev_free(net->d_tw2);
+    dev_free(net->d_wf2);
+    dev_free(net->d_f2a);
+    dev_free(net->d_f2b);
+    dev_free(net->d_out2);
+    net->counts2.clear();
+    net->est2_fixed = false;
+    net->n_sub2 = net->Ka = net->Kb = 0;
 }
 
 void release_all(gbs_net *net) {
@@ -137,6 +147,9 @@ void release_all(gbs_net *net) {
     dev_free(net->d_win);
     dev_free(net->d_wmax);
     dev_free(net->d_flags);
+    dev_free(net->d_nS2);
+    dev_free(net->d_win2);
+    dev_free(net->d_wmax2);
 }
 
 // Sampler + propagation + finalize for one chunk of `count` trajectories.
@@ -195,6 +208,50 @@ __global__ void k_split_from_dev(const double *__restrict__ T, int N, int M, int
             A[2 * plane + o] = __float2bfloat16_rn(r2);
         }
     }
+}
+
+// Sampler + propagation + two-bin finalize for one chunk.
+int run_chunk_front2d(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) {
+    int rc;
+    const bool fp64 = net->precision == GBS_FP64;
+    rc = fp64 ? launch_sample_fp64(net, seed, e0, count) : launch_sample_bf16(net, seed, e0, count);
+    if (rc) return rc;
+    rc = fp64 ? launch_gemm_fp64(net, count) : launch_gemm_tc(net, count);
+    if (rc) return rc;
+    return launch_finalize2d(net, count);
+}
+
+int fix_estimator2d(gbs_net *net, int n_sub, int Ka, int Kb) {
+    if (net->est2_fixed) {
+        if (n_sub != net->n_sub2 || Ka != net->Ka || Kb != net->Kb)
+            return set_error(GBS_EINVAL,
+                             "n_sub/K1/K2 (%d, %d, %d) differ from the values fixed by the first "
+                             "call (%d, %d, %d); call gbs_reset first",
+                             n_sub, Ka, Kb, net->n_sub2, net->Ka, net->Kb);
+        return GBS_OK;
+    }
+    if (n_sub < 1 || n_sub > 65535) return set_error(GBS_EINVAL, "n_sub must be in [1, 65535]");
+    if (!is_pow2(Ka) || !is_pow2(Kb) || Ka < 2 || Kb < 2 || (int64_t)Ka * Kb > (1 << 22))
+        return set_error(GBS_EINVAL, "K1, K2 must be powers of two >= 2 with K1 K2 <= 2^22");
+    net->n_sub2 = n_sub;
+    net->Ka = Ka;
+    net->Kb = Kb;
+    const size_t accn = (size_t)2 * n_sub * Ka * Kb;
+    int rc;
+    if ((rc = dev_alloc(&net->d_acc2, accn, "acc2")) ||
+        (rc = dev_alloc(&net->d_counts2, (size_t)n_sub, "counts2")) ||
+        (rc = dev_alloc(&net->d_tw2, (size_t)(Ka + Kb), "tw2")) ||
+        (rc = dev_alloc(&net->d_wf2, (size_t)(Ka + Kb), "wf2")) ||
+        (rc = dev_alloc(&net->d_f2a, accn, "fft2a")) ||
+        (rc = dev_alloc(&net->d_f2b, accn, "fft2b")) ||
+        (rc = dev_alloc(&net->d_out2, (size_t)4 * Ka * Kb, "out2")))
+        return rc;
+    GBS_CUDA_TRY(cudaMemsetAsync(net->d_acc2, 0, accn * sizeof(double2), net->stream));
+    GBS_CUDA_TRY(cudaMemsetAsync(net->d_counts2, 0, (size_t)n_sub * sizeof(int64_t), net->stream));
+    if ((rc = launch_tables2d(net))) return rc;
+    net->counts2.assign((size_t)n_sub, 0);
+    net->est2_fixed = true;
+    return GBS_OK;
 }
 
 int validate_net(gbs_net *net) {
@@ -460,6 +517,46 @@ int gbs_make_network_device(int N, int M, const double *T_dev, const double *r, 
     return make_network(N, M, T_dev, true, r, precision, stream, out);
 }
 
+int gbs_make_network_binned(int N, int M, const double *T, const double *r, const int *bin,
+                            int precision, void *stream, gbs_net_t *out) {
+    if (!out) return set_error(GBS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (N < 1 || M < 2 || N > 65536 || M > 65536)
+        return set_error(GBS_EINVAL, "N in [1, 65536] and M in [2, 65536] required");
+    if (!T || !r || !bin) return set_error(GBS_EINVAL, "T, r and bin must be non-NULL host pointers");
+    int Mb[2] = {0, 0};
+    for (int i = 0; i < M; ++i) {
+        if (bin[i] != 0 && bin[i] != 1) return set_error(GBS_EINVAL, "bin[%d] = %d: must be 0 or 1", i, bin[i]);
+        ++Mb[bin[i]];
+    }
+    if (!Mb[0] || !Mb[1]) return set_error(GBS_EINVAL, "both bins need at least one output mode");
+    // rows of bin 1, zero rows to a whole tile, rows of bin 2, zero rows
+    const int pad0 = (Mb[0] + kFp64TileModes - 1) / kFp64TileModes * kFp64TileModes;
+    const int pad1 = (Mb[1] + kFp64TileModes - 1) / kFp64TileModes * kFp64TileModes;
+    const int Mp = pad0 + pad1;
+    if (Mp > 65536) return set_error(GBS_EINVAL, "padded output modes exceed 65536");
+    std::vector<double> Tp((size_t)2 * Mp * N, 0.0);
+    int next[2] = {0, pad0};
+    for (int i = 0; i < M; ++i) {
+        const int row = next[bin[i]]++;
+        std::copy(T + (size_t)2 * i * N, T + (size_t)2 * (i + 1) * N, Tp.begin() + (size_t)2 * row * N);
+    }
+    gbs_net_t net = nullptr;
+    int rc = make_network(N, Mp, Tp.data(), false, r, precision, stream, &net);
+    if (rc) return rc;
+    net->nbins = 2;
+    net->bin_tile0 = pad0 / kFp64TileModes;
+    net->M_user = M;
+    if ((rc = dev_alloc(&net->d_nS2, (size_t)2 * net->chunk, "nS2")) ||
+        (rc = dev_alloc(&net->d_win2, (size_t)net->chunk, "windows2")) ||
+        (rc = dev_alloc(&net->d_wmax2, (size_t)4, "window union 2"))) {
+        gbs_free_network(net);
+        return rc;
+    }
+    *out = net;
+    return GBS_OK;
+}
+
 int gbs_sample(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub, int K1) {
     int rc;
     if ((rc = validate_net(net))) return rc;
@@ -581,6 +678,48 @@ int gbs_set_accumulators(gbs_net_t net, int n_sub, int K1, const double *acc,
                                  cudaMemcpyHostToDevice, net->stream));
     GBS_CUDA_TRY(cudaStreamSynchronize(net->stream));
     std::memcpy(net->counts.data(), counts, sizeof(int64_t) * n_sub);
+    return GBS_OK;
+}
+
+int gbs_sample_2d(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub,
+                  int K1, int K2) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (net->nbins != 2) return set_error(GBS_EINVAL, "the network has no output bins (gbs_make_network_binned)");
+    if (E < 0) return set_error(GBS_EINVAL, "E must be >= 0");
+    if (first_sample + (uint64_t)E < first_sample)
+        return set_error(GBS_EINVAL, "sample index range overflows 64 bits");
+    if ((rc = fix_estimator2d(net, n_sub, K1, K2))) return rc;
+    for (int64_t done = 0; done < E; done += net->chunk) {
+        const int64_t c = std::min<int64_t>(net->chunk, E - done);
+        const uint64_t e0 = first_sample + (uint64_t)done;
+        if ((rc = run_chunk_front2d(net, seed, e0, c))) return rc;
+        if ((rc = launch_gf2d(net, e0, c))) return rc;
+    }
+    const uint64_t ns = (uint64_t)net->n_sub2;
+    const uint64_t full = (uint64_t)E / ns, rem = (uint64_t)E % ns;
+    const uint64_t start = first_sample % ns;
+    for (uint64_t q = 0; q < ns; ++q) net->counts2[q] += (int64_t)full;
+    for (uint64_t q = 0; q < rem; ++q) net->counts2[(start + q) % ns] += 1;
+    return GBS_OK;
+}
+
+int gbs_binned_counts_2d(gbs_net_t net, int64_t m1_offset, int64_t m2_offset, double *P_mP,
+                         double *sig_mP, double *P_plusP, double *sig_plusP) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (!net->est2_fixed) return set_error(GBS_EINVAL, "no two-bin samples drawn yet");
+    for (int q = 0; q < net->n_sub2; ++q)
+        if (net->counts2[q] <= 0)
+            return set_error(GBS_EINVAL, "sub-ensemble %d has no trajectories", q);
+    if ((rc = launch_invert2d(net, m1_offset, m2_offset, net->d_out2))) return rc;
+    const size_t grid = (size_t)net->Ka * net->Kb;
+    double *dst[4] = {P_mP, sig_mP, P_plusP, sig_plusP};
+    for (int q = 0; q < 4; ++q)
+        if (dst[q])
+            GBS_CUDA_TRY(cudaMemcpyAsync(dst[q], net->d_out2 + q * grid, sizeof(double) * grid,
+                                         cudaMemcpyDeviceToHost, net->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(net->stream));
     return GBS_OK;
 }
 

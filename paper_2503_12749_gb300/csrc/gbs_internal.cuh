@@ -55,6 +55,13 @@ struct Window {
     int w2;
 };
 
+// Two-bin windows: half-widths in k_1 and k_2 of the e^{L} term around
+// (0, 0) and of the e^{-L} term around (pi, pi); -1 = empty.
+struct Window2 {
+    int w1a, w1b;
+    int w2a, w2b;
+};
+
 // ---------------------------------------------------------------------------
 // The network object behind gbs_net_t
 // ---------------------------------------------------------------------------
@@ -127,6 +134,26 @@ struct gbs_net {
     unsigned long long *d_flags = nullptr;  // [4]: non-finite count, timeout flag, ...
 
     gbs::Profiler prof;
+
+    // Two output bins (gbs_make_network_binned): the output modes of bin 1
+    // and of bin 2 are stored as consecutive rows, each bin padded with zero
+    // rows to whole 64-mode tiles; tiles [0, bin_tile0) are bin 1.
+    int nbins = 1;
+    int bin_tile0 = 0;
+    int M_user = 0;  // output modes as given (M includes the padding rows)
+    // two-bin estimator state (gbs_sample_2d)
+    double2 *d_nS2 = nullptr;       // [chunk][2]: n_S1, n_S2
+    gbs::Window2 *d_win2 = nullptr; // [chunk]
+    int *d_wmax2 = nullptr;         // [4]: union of the chunk's windows
+    bool est2_fixed = false;
+    int n_sub2 = 0, Ka = 0, Kb = 0;
+    double2 *d_acc2 = nullptr;      // [2][n_sub2][Ka][Kb]
+    int64_t *d_counts2 = nullptr;   // [n_sub2]
+    std::vector<int64_t> counts2;
+    double2 *d_tw2 = nullptr;       // [Ka + Kb]: (cos theta - 1, sin theta) of each dimension
+    double2 *d_wf2 = nullptr;       // [Ka + Kb]: e^{-i theta}
+    double2 *d_f2a = nullptr, *d_f2b = nullptr;  // [2][n_sub2][Ka * Kb] FFT work
+    double *d_out2 = nullptr;       // [4][Ka * Kb]
 };
 
 namespace gbs {
@@ -169,6 +196,20 @@ int launch_invert(gbs_net *net, int64_t m_offset, double *out_dev);
 
 // Non-finite count of the accumulators into d_flags[0].
 int launch_count_nonfinite(gbs_net *net);
+
+// Forward DFTs of length K (a power of two) over `batch` contiguous rows of
+// x (radix-2 Stockham passes alternating between x and y); *result is the
+// buffer holding the output.
+int launch_fft_rows(const double2 *wfft, int K, int64_t batch, double2 *x, double2 *y,
+                    double2 **result, cudaStream_t stream, int sm_count);
+
+// Two-bin estimator (k_bin2d.cu): finalize (per-bin n_S and windows),
+// generating functions on the (Ka x Kb) grid, and the two-dimensional
+// inversion into out_dev[4][Ka * Kb].
+int launch_finalize2d(gbs_net *net, int64_t count);
+int launch_gf2d(gbs_net *net, uint64_t e0, int64_t count);
+int launch_tables2d(gbs_net *net);
+int launch_invert2d(gbs_net *net, int64_t m1_off, int64_t m2_off, double *out_dev);
 
 // Fix (or check) a network's estimator shape, allocating its sums on first use.
 int fix_estimator(gbs_net *net, int n_sub, int K1);

@@ -116,6 +116,23 @@ int launch_invert(gbs_net *net, int64_t m_offset, double *out_dev) {
     return GBS_OK;
 }
 
+int launch_fft_rows(const double2 *wfft, int K, int64_t batch, double2 *x, double2 *y,
+                    double2 **result, cudaStream_t stream, int sm_count) {
+    const int64_t work = batch * (K / 2);
+    int64_t b = (work + 255) / 256;
+    if (b > (int64_t)sm_count * 8) b = (int64_t)sm_count * 8;
+    if (b < 1) b = 1;
+    for (int Ns = 1; Ns < K; Ns <<= 1) {
+        k_stockham<<<(int)b, 256, 0, stream>>>(x, y, K, Ns, batch, wfft);
+        GBS_LAUNCH_CHECK();
+        double2 *tmp = x;
+        x = y;
+        y = tmp;
+    }
+    *result = x;
+    return GBS_OK;
+}
+
 int launch_count_nonfinite(gbs_net *net) {
     GBS_CUDA_TRY(cudaMemsetAsync(net->d_flags, 0, sizeof(unsigned long long), net->stream));
     const int64_t total = (int64_t)2 * net->n_sub * net->K1;
