@@ -447,8 +447,8 @@ def batch_arm(args):
 def bin2d_arm(args):
     """The paper's two-bin example ("Higher-dimensional binning", Fig. 3):
     lossless 200-mode Haar network, r = 0.5, bins {1..100} and {101..200},
-    E = 1.2e6 per step, K1 = K2 = 128, N_R = 100, BF16x3 propagation, FP64
-    generating functions.  One step = gbs_sample_2d of E trajectories and the
+    E = 1.2e6 per step, K1 = K2 = 128, N_R = 100, BF16x3 propagation,
+    double-float generating functions.  One step = gbs_sample_2d of E trajectories and the
     two-dimensional inversion."""
     import numpy as np
     import torch
@@ -485,7 +485,8 @@ def bin2d_arm(args):
         "value": E / (ms_step / 1e3), "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16x3 GEMM, f64 generating functions and DFT", "data": "synthetic",
+        "dtype": "bf16x3 GEMM, double-float generating functions, f64 sums and DFT",
+        "data": "synthetic",
         "config": {"workload": "bin2d: N=M=200 Haar lossless, r=0.5, bins 100+100, E=1.2e6, "
                                "K1=K2=128, N_R=100", "samples_per_step": E,
                    "timing": "wall clock per step; each step ends with the synchronous "
@@ -495,8 +496,10 @@ def bin2d_arm(args):
                    "max_abs_P_odd_total": float(np.max(np.abs(
                        P[0][(np.add.outer(np.arange(K), np.arange(K)) % 2) == 1])))},
         "roofline": {"bound": "alu", "achieved": None, "peak": None, "unit": None,
-                     "frac": None, "traffic": None, "kernel": "k_gf2d (FP64)",
-                     "note": "two-bin generating functions evaluated in FP64; see DESIGN.md"},
+                     "frac": None, "traffic": None, "kernel": "k_gf2d_df",
+                     "note": "issue-bound double-float generating functions on the FP32 "
+                             "pipes, like the one-bin k_gf_df (see profiles/); not measured "
+                             "separately for this workload"},
         "gpu_launches": None, "clocks": clk,
     }
     gbs.gbs_free_network(net)

@@ -130,8 +130,9 @@ int gbs_make_network_binned(int N, int M, const double *T, const double *r, cons
  * z_b = exp(2 pi i k_b / K_b) (the one-bin form of Eq. c-number-variable
  * with the exponent summed over the bins), summed per sub-ensemble (e mod
  * n_sub).  K1, K2: powers of two, K1 K2 <= 2^22; the first call fixes
- * (n_sub, K1, K2) until gbs_reset.  Generating functions in FP64 for every
- * precision.  Errors: EINVAL (not a binned network, sizes), ENOMEM, ECUDA.
+ * (n_sub, K1, K2) until gbs_reset.  Generating functions in FP64 (FP64
+ * networks) or double-float (BF16 networks), summed in FP64.  Errors: EINVAL
+ * (not a binned network, sizes), ENOMEM, ECUDA.
  */
 int gbs_sample_2d(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub,
                   int K1, int K2);

@@ -30,6 +30,9 @@ struct DfConsts {
     float cos_hi[33], cos_lo[33];          // cos(j pi/64)
 };
 
+// The constants and tables above (host; k_gf.cu).
+DfConsts make_df_consts();
+
 // The tables of DfConsts copied into shared memory (lanes index them with
 // different j).
 struct DfTables {

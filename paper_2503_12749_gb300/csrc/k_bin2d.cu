@@ -11,7 +11,10 @@
 // one-bin GEMM unchanged: the rows of each bin are contiguous and padded to
 // whole 64-mode tiles, so its per-tile partials sum to n_S1 and n_S2.
 //
-// Evaluated in FP64 on a (Ka x Kb) grid of z_b = e^{i theta_b}; with
+// Evaluated on a (Ka x Kb) grid of z_b = e^{i theta_b} in FP64 (FP64
+// networks) or in double-float on the FP32 pipes (BF16 networks, the
+// one-bin kernel's table-driven exp and sin/cos, FP64 for arguments beyond
+// their ranges); with
 // L = l + i phi the same stable form as the one-bin kernels,
 //   G_mP = [e^{l + c1} e^{i phi} + e^{-l + c2} e^{-i phi}] / (1 + e^{-2|n|}),
 // c1 = min(0, 2n), c2 = -2 max(n, 0).  Terms below 2^-60 are skipped with
@@ -21,6 +24,7 @@
 // theta_2 and for the e^{-L} term around (pi, pi).  Sub-ensemble sums are
 // inverted by a two-dimensional FFT (rows, transpose, rows).
 #include "gbs_internal.cuh"
+#include "dfloat.cuh"
 
 #include <cmath>
 
@@ -228,6 +232,136 @@ __global__ void __launch_bounds__(kG2Threads)
     }
 }
 
+// The same sums in double-float arithmetic (BF16 networks).
+__global__ void __launch_bounds__(kG2Threads)
+    k_gf2d_df(const double *__restrict__ n_in, const double2 *__restrict__ nS2,
+              const Window2 *__restrict__ win_in, const int *__restrict__ wmax, int64_t count,
+              uint64_t e0, int n_sub, int Ka, int Kb, const double2 *__restrict__ tw,
+              const DfConsts K, double2 *__restrict__ acc, int64_t *__restrict__ counts) {
+    __shared__ df s_x1[kG2Tile], s_y1[kG2Tile], s_x2[kG2Tile], s_y2[kG2Tile];
+    __shared__ df s_c1[kG2Tile], s_c2[kG2Tile], s_inv[kG2Tile];
+    __shared__ double s_n[kG2Tile];
+    __shared__ double2 s_s1[kG2Tile], s_s2[kG2Tile];
+    __shared__ Window2 s_w[kG2Tile];
+    __shared__ DfTables s_tab;
+    const int r = blockIdx.y;
+    const int W1a = wmax[0], W1b = wmax[1], W2a = wmax[2], W2b = wmax[3];
+    const int Sa = slots_of(Ka, W1a, W2a), Sb = slots_of(Kb, W1b, W2b);
+    const int64_t slot = (int64_t)blockIdx.x * kG2Threads + threadIdx.x;
+    const int64_t first = (int64_t)(((uint64_t)r + (uint64_t)n_sub - e0 % (uint64_t)n_sub) %
+                                    (uint64_t)n_sub);
+    const int64_t cnt_r = first < count ? (count - 1 - first) / n_sub + 1 : 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) counts[r] += cnt_r;
+    if ((int64_t)blockIdx.x * kG2Threads >= (int64_t)Sa * Sb) return;  // block past the grid
+    if (threadIdx.x < 64) s_tab.exp2[threadIdx.x] = df{K.exp2_hi[threadIdx.x], K.exp2_lo[threadIdx.x]};
+    if (threadIdx.x < 33) {
+        s_tab.sn[threadIdx.x] = df{K.sin_hi[threadIdx.x], K.sin_lo[threadIdx.x]};
+        s_tab.cs[threadIdx.x] = df{K.cos_hi[threadIdx.x], K.cos_lo[threadIdx.x]};
+    }  // visible after the first __syncthreads of the tile loop
+    const bool valid = slot < (int64_t)Sa * Sb;
+    const int k1 = valid ? slot_k((int)(slot / Sb), Ka, W1a, W2a) : 0;
+    const int k2 = valid ? slot_k((int)(slot % Sb), Kb, W1b, W2b) : 0;
+    const int a0 = valid ? d0(k1, Ka) : 0x3fffffff, b0 = valid ? d0(k2, Kb) : 0x3fffffff;
+    const int api = valid ? dpi(k1, Ka) : 0x3fffffff, bpi = valid ? dpi(k2, Kb) : 0x3fffffff;
+    const double2 tad = tw[k1], tbd = tw[Ka + k2];
+    const df cma = df_from_double(tad.x), sna = df_from_double(tad.y);
+    const df cmb = df_from_double(tbd.x), snb = df_from_double(tbd.y);
+    double am_re = 0.0, am_im = 0.0, ap_re = 0.0, ap_im = 0.0;
+    for (int64_t base = 0; base < cnt_r; base += kG2Tile) {
+        const int64_t q = base + threadIdx.x;
+        if (q < cnt_r) {
+            const int64_t i = first + q * n_sub;
+            const double nn = n_in[i];
+            const double2 v1 = nS2[2 * i], v2 = nS2[2 * i + 1];
+            s_x1[threadIdx.x] = df_from_double(v1.x);
+            s_y1[threadIdx.x] = df_from_double(v1.y);
+            s_x2[threadIdx.x] = df_from_double(v2.x);
+            s_y2[threadIdx.x] = df_from_double(v2.y);
+            s_c1[threadIdx.x] = df_from_double(fmin(0.0, 2.0 * nn));
+            s_c2[threadIdx.x] = df_from_double(-2.0 * fmax(nn, 0.0));
+            s_inv[threadIdx.x] = df_from_double(1.0 / (1.0 + exp(-2.0 * fabs(nn))));
+            s_n[threadIdx.x] = nn;
+            s_s1[threadIdx.x] = v1;
+            s_s2[threadIdx.x] = v2;
+            s_w[threadIdx.x] = win_in[i];
+        }
+        __syncthreads();
+        const int ntile = (cnt_r - base) < kG2Tile ? (int)(cnt_r - base) : kG2Tile;
+        if (valid) {
+            df pm_re = {0.0f, 0.0f}, pm_im = {0.0f, 0.0f}, pp_re = {0.0f, 0.0f},
+               pp_im = {0.0f, 0.0f};
+            for (int j = 0; j < ntile; ++j) {
+                const Window2 w = s_w[j];
+                const bool in1 = a0 <= w.w1a && b0 <= w.w1b;
+                const bool in2 = api <= w.w2a && bpi <= w.w2b;
+                if (!(in1 || in2)) continue;
+                const df x1 = s_x1[j], y1 = s_y1[j], x2 = s_x2[j], y2 = s_y2[j];
+                const df l = df_add(df_sub(df_mul(cma, x1), df_mul(sna, y1)),
+                                    df_sub(df_mul(cmb, x2), df_mul(snb, y2)));
+                const df ph = df_add(df_add(df_mul(sna, x1), df_mul(cma, y1)),
+                                     df_add(df_mul(snb, x2), df_mul(cmb, y2)));
+                const df c1 = s_c1[j];
+                const df a1 = df_add(l, c1);
+                const df a2 = df_add(df_neg(l), s_c2[j]);
+                const bool big = fabsf(ph.hi) >= 6000.0f ||
+                                 (in1 && (a1.hi >= 80.0f || l.hi >= 80.0f)) ||
+                                 (in2 && a2.hi >= 80.0f);
+                if (big) {
+                    // outside the double-float ranges: this pair in FP64
+                    const double2 v1 = s_s1[j], v2 = s_s2[j];
+                    const double nn = s_n[j];
+                    const double ld = (tad.x * v1.x - tad.y * v1.y) + (tbd.x * v2.x - tbd.y * v2.y);
+                    const double pd = (tad.y * v1.x + tad.x * v1.y) + (tbd.y * v2.x + tbd.x * v2.y);
+                    double sd, cd;
+                    sincos(pd, &sd, &cd);
+                    const double c1d = fmin(0.0, 2.0 * nn), c2d = -2.0 * fmax(nn, 0.0);
+                    double e1d = 0.0, e2d = 0.0;
+                    if (in1) {
+                        e1d = exp(ld + c1d);
+                        const double gp = (c1d == 0.0) ? e1d : exp(ld);
+                        ap_re += gp * cd;
+                        ap_im += gp * sd;
+                    }
+                    if (in2) e2d = exp(-ld + c2d);
+                    const double inv = df_to_double(s_inv[j]);
+                    am_re += (e1d + e2d) * cd * inv;
+                    am_im += (e1d - e2d) * sd * inv;
+                    continue;
+                }
+                df sp, cp;
+                df_sincos_tab(ph, s_tab, K, sp, cp);
+                const df inv = s_inv[j];
+                df e1 = {0.0f, 0.0f}, e2 = {0.0f, 0.0f};
+                if (in1) {
+                    e1 = a1.hi < -87.0f ? df{0.0f, 0.0f} : df_exp_tab(a1, s_tab, K);
+                    const df gp = (c1.hi == 0.0f)
+                                      ? e1
+                                      : (l.hi < -87.0f ? df{0.0f, 0.0f} : df_exp_tab(l, s_tab, K));
+                    pp_re = df_add(pp_re, df_mul(gp, cp));
+                    pp_im = df_add(pp_im, df_mul(gp, sp));
+                }
+                if (in2) e2 = a2.hi < -87.0f ? df{0.0f, 0.0f} : df_exp_tab(a2, s_tab, K);
+                pm_re = df_add(pm_re, df_mul(df_mul(df_add(e1, e2), inv), cp));
+                pm_im = df_add(pm_im, df_mul(df_mul(df_sub(e1, e2), inv), sp));
+            }
+            am_re += df_to_double(pm_re);
+            am_im += df_to_double(pm_im);
+            ap_re += df_to_double(pp_re);
+            ap_im += df_to_double(pp_im);
+        }
+        __syncthreads();
+    }
+    if (valid) {
+        const size_t grid = (size_t)Ka * Kb;
+        const size_t o = (size_t)k1 * Kb + k2;
+        double2 *p0 = acc + (size_t)r * grid + o;
+        double2 *p1 = acc + ((size_t)n_sub + r) * grid + o;
+        const double2 v0 = *p0, v1 = *p1;
+        *p0 = make_double2(v0.x + am_re, v0.y + am_im);
+        *p1 = make_double2(v1.x + ap_re, v1.y + ap_im);
+    }
+}
+
 __global__ void k_tables2d(int Ka, int Kb, double2 *__restrict__ tw, double2 *__restrict__ wf) {
     const int total = Ka + Kb;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -325,9 +459,18 @@ int launch_gf2d(gbs_net *net, uint64_t e0, int64_t count) {
     // blocks for the whole grid; blocks past the chunk's union window return
     const int64_t cells = (int64_t)net->Ka * net->Kb;
     dim3 grid((unsigned)((cells + kG2Threads - 1) / kG2Threads), (unsigned)net->n_sub2);
-    k_gf2d<<<grid, kG2Threads, 0, net->stream>>>(net->d_n, net->d_nS2, net->d_win2, net->d_wmax2,
-                                                  count, e0, net->n_sub2, net->Ka, net->Kb,
-                                                  net->d_tw2, net->d_acc2, net->d_counts2);
+    if (net->precision == GBS_FP64) {
+        k_gf2d<<<grid, kG2Threads, 0, net->stream>>>(net->d_n, net->d_nS2, net->d_win2,
+                                                      net->d_wmax2, count, e0, net->n_sub2,
+                                                      net->Ka, net->Kb, net->d_tw2, net->d_acc2,
+                                                      net->d_counts2);
+    } else {
+        static const DfConsts K = make_df_consts();
+        k_gf2d_df<<<grid, kG2Threads, 0, net->stream>>>(net->d_n, net->d_nS2, net->d_win2,
+                                                         net->d_wmax2, count, e0, net->n_sub2,
+                                                         net->Ka, net->Kb, net->d_tw2, K,
+                                                         net->d_acc2, net->d_counts2);
+    }
     GBS_LAUNCH_CHECK();
     return GBS_OK;
 }

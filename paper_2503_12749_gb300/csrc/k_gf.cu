@@ -384,6 +384,8 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 1)
     if (blockIdx.x == 0 && threadIdx.x == 0) counts[r] += cnt_r;
 }
 
+}  // namespace
+
 // Float pieces of ln 2 and pi/2 for exact Cody-Waite products (12
 // significant bits each except the last), split from the constants'
 // decimal expansions at 80 digits; factorial reciprocals as double-float.
@@ -426,6 +428,8 @@ DfConsts make_df_consts() {
     }
     return K;
 }
+
+namespace {
 
 __global__ void k_tables(int K1, double2 *__restrict__ tw, double2 *__restrict__ wfft) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K1; k += gridDim.x * blockDim.x) {
