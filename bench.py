@@ -507,6 +507,91 @@ def bin2d_arm(args):
     return 0
 
 
+# Appendix B, Fig. 6: m_max (total-count probability 1e-7) for M = 128 ... 8192
+# (left, lossless r = 0.89, with m_min) and for M = 16 ... 1024 (right caption)
+FIG6_LEFT = {"M": [128, 256, 512, 1024, 2048, 4096, 8192],
+             "m_max": [273, 450, 776, 1388, 2562, 4831, 9267],
+             "m_min": [37, 122, 318, 755, 1678, 3605, 7561]}
+FIG6_RIGHT = {"M": [16, 32, 64, 128, 256, 512, 1024],
+              "m_max": [85, 118, 174, 273, 450, 776, 1388]}
+
+
+def fig6_arm(args):
+    """Appendix B's scaling experiments with E_S = 1.2e6 samples per network
+    (N_R = 120 sub-ensembles): left, the time per network of lossless Haar
+    networks with r = 0.89 for M = 128 ... 8192 over the window [m_min,
+    m_max]; right, max sigma_T of the matrix-P P(m) for M = 16 ... 1024 with
+    r_i = 0.89 + 0.1 w_i (w_i standard normal) and amplitude transmissions
+    t = 1, 0.995 and 1 - 1/m_max."""
+    import numpy as np
+    import torch
+
+    import paper_2503_12749_gb300 as gbs
+    import workloads as wl
+
+    torch.cuda.set_device(0)
+    gbs.build()
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    E = args.samples or 1_200_000
+    n_sub = 120
+
+    def pow2(v):
+        return 1 << int(math.ceil(math.log2(max(v, 2))))
+
+    left = []
+    for M, mx, mn in zip(FIG6_LEFT["M"], FIG6_LEFT["m_max"], FIG6_LEFT["m_min"]):
+        U = wl.haar_unitary_device(M, wl.SEED_U_BASE + 7000 + M).contiguous()
+        K1 = pow2(mx - mn + 1)
+        net = gbs.gbs_make_network_device(U.data_ptr(), M, M, np.full(M, 0.89), "bf16x3", sp)
+        del U
+        seed = wl.SEED_S_BASE + 7000 + M
+        gbs.gbs_sample(net, seed, 0, 2 ** 14, n_sub, K1)   # warm-up (tuning, allocations)
+        gbs.gbs_reset(net)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gbs.gbs_sample(net, seed, 0, E, n_sub, K1)
+        P = gbs.gbs_binned_counts(net, mn, K1)
+        dt = time.perf_counter() - t0
+        gbs.gbs_free_network(net)
+        left.append({"M": M, "K1": K1, "m_off": mn, "seconds": dt, "samples_per_s": E / dt,
+                     "max_sigma": float(P[1].max())})
+    right = []
+    for M, mx in zip(FIG6_RIGHT["M"], FIG6_RIGHT["m_max"]):
+        U = wl.haar_unitary(M, wl.SEED_U_BASE + 8000 + M)
+        w = np.random.default_rng(wl.SEED_U_BASE + 8000 + M + wl.SEED_R_OFFSET).standard_normal(M)
+        r = np.maximum(0.89 + 0.1 * w, 0.0)
+        K1 = pow2(mx + 1)
+        row = {"M": M, "m_max": mx, "K1": K1}
+        for name, t in (("t=1", 1.0), ("t=0.995", 0.995), ("t=1-1/m_max", 1.0 - 1.0 / mx)):
+            net = gbs.gbs_make_network(t * U, r, "bf16x3", sp)
+            gbs.gbs_sample(net, wl.SEED_S_BASE + 8000 + M, 0, E, n_sub, K1)
+            P = gbs.gbs_binned_counts(net, 0, K1)
+            gbs.gbs_free_network(net)
+            row[name] = float(P[1].max())
+        right.append(row)
+    big = left[-1]
+    line = {
+        "metric": "Appendix B scaling: matrix-P time per 1.2e6-sample network vs M, and max "
+                  "sampling error vs M",
+        "value": big["samples_per_s"], "unit": "samples/s (M = 8192 network)", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * big["seconds"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3 split (fp32 accumulate, f64 sums)",
+        "data": "synthetic",
+        "config": {"workload": "fig6: E_S=1.2e6, N_R=120; left: lossless Haar r=0.89, "
+                               "M=128..8192, window [m_min, m_max]; right: r_i=0.89+0.1 w_i, "
+                               "t in {1, 0.995, 1-1/m_max}, M=16..1024",
+                   "timing": "wall clock of gbs_sample + gbs_binned_counts per network, "
+                             "network resident"},
+        "left": left, "right": right,
+        "result": {"max_sigma_decreases_with_M": {
+            k: bool(right[-1][k] < right[0][k]) for k in ("t=1", "t=0.995", "t=1-1/m_max")}},
+        "roofline": None, "gpu_launches": None,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 SUR_METRIC = "surrogate binned-P(m) predictions/s on held-out networks, judged by matrix-P runs"
 
 
@@ -696,7 +781,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
     ap.add_argument("--workload", default="m1000",
-                    choices=sorted(wl.NAMED) + ["batch64", "surrogate", "bin2d"])
+                    choices=sorted(wl.NAMED) + ["batch64", "surrogate", "bin2d", "fig6"])
     ap.add_argument("--sur-train", type=int, default=2000)
     ap.add_argument("--sur-train-samples", type=int, default=2 ** 16)
     ap.add_argument("--sur-heldout", type=int, default=50)
@@ -717,6 +802,12 @@ def main():
                               "unavailable": "the reference arm is defined for the m1000 workload"}))
             return 0
         return batch_arm(args)
+    if args.workload == "fig6":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference",
+                              "unavailable": "the reference arm is defined for the m1000 workload"}))
+            return 0
+        return fig6_arm(args)
     if args.workload == "bin2d":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference",

@@ -150,6 +150,23 @@ int gbs_binned_counts_2d(gbs_net_t net, int64_t m1_offset, int64_t m2_offset, do
                          double *sig_mP, double *P_plusP, double *sig_plusP);
 
 /*
+ * gbs_histogram -- probability densities of per-trajectory observables
+ * (Appendix A, Eq. gen_probability_density): for trajectories
+ * first..first+E-1 (the same trajectories gbs_sample would draw) and each
+ * count m[q], the real parts of the matrix-P projector
+ *   G_0(m) = [e^{-n_S} n_S^m e^{n} + e^{n_S} (-n_S)^m e^{-n}] / (m! 2 cosh n)
+ * and of the +P projector G_+(m) = n_S^m e^{-n_S} / m! (Eq.
+ * phase_space_projector) are counted in nbins equal bins of [lo, hi).
+ *   m, nm     host, 1 <= nm <= 16 counts; 2 nm (nbins + 2) <= 12288.
+ *   counts    host, [2][nm][nbins + 2] (matrix-P first); per row bin 0 counts
+ *             values below lo (and NaN), bin nbins + 1 values >= hi.
+ * Independent of the sub-ensemble sums.  Synchronises.  Errors: EINVAL,
+ * ENOMEM, ECUDA.  The density of bin j is counts / (E * (hi - lo) / nbins).
+ */
+int gbs_histogram(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, const int *m,
+                  int nm, double lo, double hi, int nbins, int64_t *counts);
+
+/*
  * gbs_binned_counts -- inverse DFT of the sub-ensemble means and the
  * statistics over sub-ensembles (Eq. total_counts; errors Appendix A):
  *   P_r(m) = (1/K1) sum_k <G>_r(z_k) z_k^{-m},  m = m_offset .. m_offset+K1-1,

@@ -86,6 +86,9 @@ def lib():
         L.gbs_set_gemm_config.argtypes = [vp, ctypes.c_int]
         L.gbs_make_network_binned.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ip, ctypes.c_int,
                                               vp, ctypes.POINTER(vp)]
+        L.gbs_histogram.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ip,
+                                    ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                    i64p]
         L.gbs_sample_2d.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.gbs_binned_counts_2d.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp]
@@ -127,7 +130,7 @@ def lib():
                      "gbs_binned_counts_noalloc", "gbs_set_gemm_config", "gbs_gemm_config",
                      "gbs_make_batch", "gbs_sample_batch", "gbs_batch_info",
                      "gbs_make_network_device", "gbs_make_network_binned", "gbs_sample_2d",
-                     "gbs_binned_counts_2d", "gbs_mlp_create", "gbs_mlp_param_count",
+                     "gbs_binned_counts_2d", "gbs_histogram", "gbs_mlp_create", "gbs_mlp_param_count",
                      "gbs_mlp_set_params", "gbs_mlp_get_params", "gbs_mlp_get_adam_state",
                      "gbs_mlp_forward", "gbs_mlp_gradients", "gbs_mlp_train",
                      "gbs_surrogate_features", "gbs_surrogate_feature_stats",
@@ -217,6 +220,18 @@ def gbs_make_network_binned(T: np.ndarray, r: np.ndarray, bins, precision=GBS_FP
                                          int(precision), ctypes.c_void_p(stream),
                                          ctypes.byref(out)))
     return Network(out.value, N, M, int(precision), stream)
+
+
+def gbs_histogram(net: Network, seed: int, first_sample: int, E: int, m, lo: float, hi: float,
+                  nbins: int) -> np.ndarray:
+    """Counts [2][len(m)][nbins + 2] of Re G_0(m) (matrix-P) and Re G_+(m)
+    over trajectories first_sample..first_sample+E-1 (bin 0: below lo, last: >= hi)."""
+    mm = (ctypes.c_int * len(m))(*[int(x) for x in m])
+    out = np.zeros(2 * len(m) * (nbins + 2), dtype=np.int64)
+    _check(lib().gbs_histogram(net.handle, seed, first_sample, E, mm, len(m), float(lo),
+                               float(hi), nbins,
+                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return out.reshape(2, len(m), nbins + 2)
 
 
 def gbs_sample_2d(net: Network, seed: int, first_sample: int, E: int, n_sub: int, K1: int,

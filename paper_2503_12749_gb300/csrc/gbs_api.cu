@@ -650,6 +650,53 @@ int gbs_debug_samples(gbs_net_t net, uint64_t seed, uint64_t e0, int64_t count, 
     return GBS_OK;
 }
 
+int gbs_histogram(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, const int *m,
+                  int nm, double lo, double hi, int nbins, int64_t *counts) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (E < 0 || !m || !counts) return set_error(GBS_EINVAL, "bad E or NULL m/counts");
+    if (nm < 1 || nm > kHistMaxM) return set_error(GBS_EINVAL, "nm must be in [1, %d]", kHistMaxM);
+    if (nbins < 1 || nbins > kHistMaxBins)
+        return set_error(GBS_EINVAL, "nbins must be in [1, %d]", kHistMaxBins);
+    if (!(std::isfinite(lo) && std::isfinite(hi) && hi > lo))
+        return set_error(GBS_EINVAL, "need finite lo < hi");
+    if ((size_t)2 * nm * (nbins + 2) * sizeof(unsigned int) > 48 * 1024)
+        return set_error(GBS_EINVAL, "2 * nm * (nbins + 2) must be <= 12288 (shared-memory counts)");
+    HistSpec spec = {};
+    for (int q = 0; q < nm; ++q) {
+        if (m[q] < 0 || m[q] > 100000) return set_error(GBS_EINVAL, "m[%d] out of range", q);
+        spec.m[q] = m[q];
+    }
+    spec.nm = nm;
+    spec.nbins = nbins;
+    spec.lo = lo;
+    spec.hi = hi;
+    const size_t total = (size_t)2 * nm * (nbins + 2);
+    unsigned long long *d_cnt = nullptr;
+    if ((rc = dev_alloc(&d_cnt, total, "histogram"))) return rc;
+    if (cudaMemsetAsync(d_cnt, 0, total * sizeof(unsigned long long), net->stream) != cudaSuccess)
+        rc = set_error(GBS_ECUDA, "memset of the histogram failed");
+    const int saved_K1 = net->K1;
+    if (net->K1 == 0) net->K1 = 2;  // finalize computes windows for some K1; unused here
+    for (int64_t done = 0; !rc && done < E; done += net->chunk) {
+        const int64_t c = std::min<int64_t>(net->chunk, E - done);
+        rc = run_chunk_front(net, seed, first_sample + (uint64_t)done, c);
+        if (!rc) rc = launch_histogram(net, c, spec, d_cnt);
+    }
+    net->K1 = saved_K1;
+    if (!rc) {
+        std::vector<unsigned long long> h(total);
+        if (cudaMemcpyAsync(h.data(), d_cnt, total * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, net->stream) != cudaSuccess ||
+            cudaStreamSynchronize(net->stream) != cudaSuccess)
+            rc = set_error(GBS_ECUDA, "histogram copy failed");
+        else
+            for (size_t q = 0; q < total; ++q) counts[q] = (int64_t)h[q];
+    }
+    dev_free(d_cnt);
+    return rc;
+}
+
 int gbs_get_accumulators(gbs_net_t net, int *n_sub, int *K1, double *acc, int64_t *counts) {
     int rc;
     if ((rc = validate_net(net))) return rc;

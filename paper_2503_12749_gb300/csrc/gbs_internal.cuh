@@ -203,6 +203,20 @@ int launch_count_nonfinite(gbs_net *net);
 int launch_fft_rows(const double2 *wfft, int K, int64_t batch, double2 *x, double2 *y,
                     double2 **result, cudaStream_t stream, int sm_count);
 
+// Histograms of per-trajectory projectors (k_hist.cu, Appendix A).
+constexpr int kHistMaxM = 16;
+constexpr int kHistMaxBins = 4096;
+struct HistSpec {
+    int m[kHistMaxM];
+    int nm;
+    int nbins;
+    double lo, hi;
+};
+// Adds the chunk's trajectories (d_n, d_nS) to out_dev[2][nm][nbins + 2]
+// (matrix-P first; bin 0 = below lo, nbins + 1 = at or above hi).
+int launch_histogram(gbs_net *net, int64_t count, const HistSpec &spec,
+                     unsigned long long *out_dev);
+
 // Two-bin estimator (k_bin2d.cu): finalize (per-bin n_S and windows),
 // generating functions on the (Ka x Kb) grid, and the two-dimensional
 // inversion into out_dev[4][Ka * Kb].
