@@ -150,6 +150,30 @@ int gbs_binned_counts_2d(gbs_net_t net, int64_t m1_offset, int64_t m2_offset, do
                          double *sig_mP, double *P_plusP, double *sig_plusP);
 
 /*
+ * gbs_moments -- normally-ordered moments and single-mode count marginals of
+ * every output mode j ("Photon-counting observables") from trajectories
+ * first..first+E-1 (the trajectories gbs_sample draws):
+ *   Eq. moment, M = 2 parity case (Omega_00 = 1, T_0 = tanh n):
+ *     <:n_j^m:> = < (n'_j)^m tanh(n)^(m mod 2) >  (matrix-P),
+ *                 < (n'_j)^m >                    (+P),      m = 1..mmax;
+ *   P_j(c) = < G(c) > with the projector of Eq. projection_op for S = {j},
+ *     per trajectory Eq. c-number-variable with n_S = n'_j (matrix-P) and
+ *     Eq. phase_space_projector (+P),                        c = 0..cmax;
+ * n = sum_k alpha_k beta_k, n'_j = alpha'_j beta'_j.  Estimates are the mean
+ * over sub-ensembles (trajectory e -> e mod n_sub) of the real part of the
+ * sub-ensemble means, errors std_r / sqrt(n_sub) (0 for n_sub = 1).
+ *   mmax   1..8;  cmax 0..15;  n_sub 1..65535 with E >= n_sub.
+ *   mom, sig_mom     host, [2][M][mmax] (matrix-P first), m = 1..mmax;
+ *   marg, sig_marg   host, [2][M][cmax + 1];  any output may be NULL.
+ * Independent of the sub-ensemble sums of gbs_sample (nothing accumulates
+ * across calls).  Per trajectory and mode in FP32 on the BF16 paths (FP64
+ * for magnitudes |n'| > 40), FP64 on the FP64 path; sums in FP64.
+ * Unbinned networks only.  Synchronises.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int gbs_moments(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub,
+                int mmax, int cmax, double *mom, double *sig_mom, double *marg, double *sig_marg);
+
+/*
  * gbs_histogram -- probability densities of per-trajectory observables
  * (Appendix A, Eq. gen_probability_density): for trajectories
  * first..first+E-1 (the same trajectories gbs_sample would draw) and each
@@ -231,6 +255,15 @@ int gbs_debug_samples(gbs_net_t net, uint64_t seed, uint64_t e0, int64_t count, 
                       double *nS);
 
 /*
+ * gbs_debug_occupations -- the per-mode occupations n'_i = alpha'_i beta'_i
+ * ("Applications to GBS") of trajectories e0 .. e0+count-1, as written by
+ * the propagation GEMM's epilogue for gbs_moments: occ, host,
+ * [M][count] complex as (re, im) pairs (FP32 values on the BF16 paths).
+ * Unbinned networks only.  Synchronises.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int gbs_debug_occupations(gbs_net_t net, uint64_t seed, uint64_t e0, int64_t count, double *occ);
+
+/*
  * gbs_get_accumulators / gbs_set_accumulators -- the sub-ensemble sums as
  * host arrays: acc[2][n_sub][K1] complex (re, im) doubles (estimator 0 =
  * matrix-P, 1 = +P; each the SUM of G(z_k) over the sub-ensemble's
@@ -302,7 +335,9 @@ void gbs_free_batch(gbs_batch_t batch);
 #define GBS_PHASE_FINALIZE 2 /* per-trajectory n_S sum and evaluation windows */
 #define GBS_PHASE_GF 3       /* generating functions summed per sub-ensemble */
 #define GBS_PHASE_INVERT 4   /* inverse DFT and statistics */
-#define GBS_NPHASES 5
+#define GBS_PHASE_MOMENTS 5  /* moments / marginals: per-trajectory parameters,
+                                per-mode sums, statistics (gbs_moments) */
+#define GBS_NPHASES 6
 /* gbs_profile_enable -- start (enable != 0) or stop recording; starting
  * discards earlier records. */
 int gbs_profile_enable(gbs_net_t net, int enable);

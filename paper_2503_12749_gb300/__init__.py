@@ -89,6 +89,10 @@ def lib():
         L.gbs_histogram.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ip,
                                     ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                     i64p]
+        L.gbs_moments.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+        L.gbs_debug_occupations.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                            dp]
         L.gbs_sample_2d.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.gbs_binned_counts_2d.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp]
@@ -130,7 +134,8 @@ def lib():
                      "gbs_binned_counts_noalloc", "gbs_set_gemm_config", "gbs_gemm_config",
                      "gbs_make_batch", "gbs_sample_batch", "gbs_batch_info",
                      "gbs_make_network_device", "gbs_make_network_binned", "gbs_sample_2d",
-                     "gbs_binned_counts_2d", "gbs_histogram", "gbs_mlp_create", "gbs_mlp_param_count",
+                     "gbs_binned_counts_2d", "gbs_histogram", "gbs_moments",
+                     "gbs_debug_occupations", "gbs_mlp_create", "gbs_mlp_param_count",
                      "gbs_mlp_set_params", "gbs_mlp_get_params", "gbs_mlp_get_adam_state",
                      "gbs_mlp_forward", "gbs_mlp_gradients", "gbs_mlp_train",
                      "gbs_surrogate_features", "gbs_surrogate_feature_stats",
@@ -232,6 +237,31 @@ def gbs_histogram(net: Network, seed: int, first_sample: int, E: int, m, lo: flo
                                float(hi), nbins,
                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
     return out.reshape(2, len(m), nbins + 2)
+
+
+def gbs_moments(net: Network, seed: int, first_sample: int, E: int, n_sub: int, mmax: int,
+                cmax: int):
+    """(mom, sig_mom, marg, sig_marg): normally-ordered moments <:n_j^m:>,
+    m = 1..mmax, as [2][M][mmax] and single-mode marginals P_j(c),
+    c = 0..cmax, as [2][M][cmax + 1] (index 0 matrix-P, 1 +P), over
+    trajectories first_sample..first_sample+E-1 with n_sub sub-ensembles."""
+    _, M, _, _ = gbs_network_info(net)
+    mom = np.zeros(2 * M * mmax)
+    smom = np.zeros(2 * M * mmax)
+    marg = np.zeros(2 * M * (cmax + 1))
+    smarg = np.zeros(2 * M * (cmax + 1))
+    _check(lib().gbs_moments(net.handle, seed, first_sample, E, n_sub, mmax, cmax, _dptr(mom),
+                             _dptr(smom), _dptr(marg), _dptr(smarg)))
+    return (mom.reshape(2, M, mmax), smom.reshape(2, M, mmax),
+            marg.reshape(2, M, cmax + 1), smarg.reshape(2, M, cmax + 1))
+
+
+def gbs_debug_occupations(net: Network, seed: int, e0: int, count: int) -> np.ndarray:
+    """[M][count] complex: n'_i = alpha'_i beta'_i of trajectories e0..e0+count-1."""
+    _, M, _, _ = gbs_network_info(net)
+    out = np.zeros(2 * M * count)
+    _check(lib().gbs_debug_occupations(net.handle, seed, e0, count, _dptr(out)))
+    return out.view(np.complex128).reshape(M, count)
 
 
 def gbs_sample_2d(net: Network, seed: int, first_sample: int, E: int, n_sub: int, K1: int,
@@ -384,8 +414,8 @@ def gbs_free_batch(batch: Batch) -> None:
         batch.handle = ctypes.c_void_p()
 
 
-GBS_NPHASES = 5
-PHASES = ("sample", "gemm", "finalize", "gf", "invert")
+GBS_NPHASES = 6
+PHASES = ("sample", "gemm", "finalize", "gf", "invert", "moments")
 
 
 def gbs_profile_enable(net: Network, enable: bool = True) -> None:

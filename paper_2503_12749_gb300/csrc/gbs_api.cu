@@ -697,6 +697,171 @@ int gbs_histogram(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E
     return rc;
 }
 
+namespace {
+
+// Sampler and propagation GEMM of one chunk with the per-mode occupations
+// written to occ (FP32 planes for the BF16 paths, FP64 for the FP64 path).
+int run_chunk_occ(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count, void *occ,
+                  int64_t ld_occ) {
+    int rc;
+    const bool fp64 = net->precision == GBS_FP64;
+    const int64_t plane = (int64_t)net->mtiles * 64 * ld_occ;
+    prof_mark(net, GBS_PHASE_SAMPLE, 0, true);
+    rc = fp64 ? launch_sample_fp64(net, seed, e0, count) : launch_sample_bf16(net, seed, e0, count);
+    if (rc) return rc;
+    prof_mark(net, GBS_PHASE_SAMPLE, 1, false);
+    prof_mark(net, GBS_PHASE_GEMM, 0, true);
+    if (fp64) {
+        OccOut64 o;
+        o.p = static_cast<double *>(occ);
+        o.ld = ld_occ;
+        o.plane = plane;
+        rc = launch_gemm_fp64(net, count, o);
+    } else {
+        OccOut o;
+        o.p = static_cast<float *>(occ);
+        o.ld = ld_occ;
+        o.plane = plane;
+        rc = launch_gemm_tc(net, count, o);
+    }
+    if (rc) return rc;
+    prof_mark(net, GBS_PHASE_GEMM, 1, false);
+    return GBS_OK;
+}
+
+// Trajectories per occupation chunk: <= the network's chunk, a multiple of
+// 128, occupation planes <= 2 GiB.
+int64_t occ_chunk(const gbs_net *net, int64_t E) {
+    const size_t elt = net->precision == GBS_FP64 ? sizeof(double) : sizeof(float);
+    const size_t per_traj = (size_t)2 * net->mtiles * 64 * elt;
+    int64_t c = (int64_t)(((size_t)1 << 31) / per_traj);
+    c = std::min<int64_t>(c, net->chunk);
+    c = std::min<int64_t>(c, ((E + 127) / 128) * 128);
+    c = (c / 128) * 128;
+    return std::max<int64_t>(c, 128);
+}
+
+}  // namespace
+
+int gbs_debug_occupations(gbs_net_t net, uint64_t seed, uint64_t e0, int64_t count, double *occ) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (count < 0 || !occ) return set_error(GBS_EINVAL, "bad count or NULL output");
+    if (net->nbins != 1) return set_error(GBS_EINVAL, "occupations of a binned network are not exposed");
+    if (count == 0) return GBS_OK;
+    const bool fp64 = net->precision == GBS_FP64;
+    const int64_t ld = occ_chunk(net, count);
+    const int64_t plane = (int64_t)net->mtiles * 64 * ld;
+    void *d_occ = nullptr;
+    if (fp64) rc = dev_alloc(reinterpret_cast<double **>(&d_occ), (size_t)2 * plane, "occupations");
+    else rc = dev_alloc(reinterpret_cast<float **>(&d_occ), (size_t)2 * plane, "occupations");
+    if (rc) return rc;
+    const size_t elt = fp64 ? sizeof(double) : sizeof(float);
+    std::vector<uint8_t> h((size_t)2 * plane * elt);
+    for (int64_t done = 0; !rc && done < count; done += ld) {
+        const int64_t c = std::min<int64_t>(ld, count - done);
+        rc = run_chunk_occ(net, seed, e0 + (uint64_t)done, c, d_occ, ld);
+        if (rc) break;
+        if (cudaMemcpyAsync(h.data(), d_occ, h.size(), cudaMemcpyDeviceToHost, net->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(net->stream) != cudaSuccess) {
+            rc = set_error(GBS_ECUDA, "occupation copy failed");
+            break;
+        }
+        for (int j = 0; j < net->M; ++j)
+            for (int64_t i = 0; i < c; ++i) {
+                const size_t a = (size_t)j * ld + i, b = (size_t)plane + a;
+                double re, im;
+                if (fp64) {
+                    re = reinterpret_cast<const double *>(h.data())[a];
+                    im = reinterpret_cast<const double *>(h.data())[b];
+                } else {
+                    re = reinterpret_cast<const float *>(h.data())[a];
+                    im = reinterpret_cast<const float *>(h.data())[b];
+                }
+                occ[2 * ((size_t)j * count + done + i)] = re;
+                occ[2 * ((size_t)j * count + done + i) + 1] = im;
+            }
+    }
+    dev_free(d_occ);
+    return rc;
+}
+
+int gbs_moments(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub,
+                int mmax, int cmax, double *mom, double *sig_mom, double *marg, double *sig_marg) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (net->nbins != 1) return set_error(GBS_EINVAL, "moments need an unbinned network");
+    if (mmax < 1 || mmax > 8) return set_error(GBS_EINVAL, "mmax must be in [1, 8]");
+    if (cmax < 0 || cmax > 15) return set_error(GBS_EINVAL, "cmax must be in [0, 15]");
+    if (n_sub < 1 || n_sub > 65535) return set_error(GBS_EINVAL, "n_sub must be in [1, 65535]");
+    if (E < n_sub) return set_error(GBS_EINVAL, "E must be >= n_sub (no empty sub-ensemble)");
+    const bool fp64 = net->precision == GBS_FP64;
+    MomentSpec sp;
+    sp.M = net->M;
+    sp.n_sub = n_sub;
+    sp.mmax = mmax;
+    sp.cmax = cmax;
+    const int Q = moment_quantities(mmax, cmax);
+    const int64_t ld = occ_chunk(net, E);
+    const int64_t plane = (int64_t)net->mtiles * 64 * ld;
+    const size_t nm = (size_t)2 * net->M * mmax, nc = (size_t)2 * net->M * (cmax + 1);
+    void *d_occ = nullptr;
+    uint8_t *d_par = nullptr;
+    double *d_acc = nullptr, *d_out = nullptr;
+    int64_t *d_cnt = nullptr;
+    if (fp64) rc = dev_alloc(reinterpret_cast<double **>(&d_occ), (size_t)2 * plane, "occupations");
+    else rc = dev_alloc(reinterpret_cast<float **>(&d_occ), (size_t)2 * plane, "occupations");
+    if (!rc) rc = dev_alloc(&d_par, (size_t)ld * moment_par_bytes(fp64), "trajectory parameters");
+    if (!rc) rc = dev_alloc(&d_acc, (size_t)n_sub * net->M * Q, "moment sums");
+    if (!rc) rc = dev_alloc(&d_cnt, (size_t)n_sub, "sub-ensemble sizes");
+    if (!rc) rc = dev_alloc(&d_out, 2 * nm + 2 * nc, "moment outputs");
+    if (!rc && cudaMemsetAsync(d_acc, 0, sizeof(double) * n_sub * net->M * Q, net->stream) != cudaSuccess)
+        rc = set_error(GBS_ECUDA, "memset of the moment sums failed");
+    std::vector<int64_t> cnt((size_t)n_sub, E / n_sub);
+    for (int64_t q = 0; q < E % n_sub; ++q) cnt[(size_t)((first_sample + (uint64_t)q) % (uint64_t)n_sub)] += 1;
+    if (!rc && cudaMemcpyAsync(d_cnt, cnt.data(), sizeof(int64_t) * n_sub, cudaMemcpyHostToDevice,
+                               net->stream) != cudaSuccess)
+        rc = set_error(GBS_ECUDA, "copy of the sub-ensemble sizes failed");
+    for (int64_t done = 0; !rc && done < E; done += ld) {
+        const int64_t c = std::min<int64_t>(ld, E - done);
+        const uint64_t e0 = first_sample + (uint64_t)done;
+        rc = run_chunk_occ(net, seed, e0, c, d_occ, ld);
+        if (!rc) {
+            prof_mark(net, GBS_PHASE_MOMENTS, 0, true);
+            rc = launch_moment_prep(net->d_n, c, fp64, d_par, net->stream, net->sm_count);
+        }
+        if (!rc)
+            rc = launch_moments(sp, fp64, d_occ, plane, ld, d_par, c, e0, d_acc, net->stream,
+                                net->sm_count);
+        if (!rc) prof_mark(net, GBS_PHASE_MOMENTS, 2, false);
+    }
+    if (!rc) {
+        prof_mark(net, GBS_PHASE_MOMENTS, 0, true);
+        rc = launch_moment_stats(sp, d_acc, d_cnt, d_out, net->stream, net->sm_count);
+        if (!rc) prof_mark(net, GBS_PHASE_MOMENTS, 1, false);
+    }
+    if (!rc) {
+        std::vector<double> h(2 * nm + 2 * nc);
+        if (cudaMemcpyAsync(h.data(), d_out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                            net->stream) != cudaSuccess ||
+            cudaStreamSynchronize(net->stream) != cudaSuccess)
+            rc = set_error(GBS_ECUDA, "moment copy failed");
+        else {
+            if (mom) std::memcpy(mom, h.data(), sizeof(double) * nm);
+            if (sig_mom) std::memcpy(sig_mom, h.data() + nm, sizeof(double) * nm);
+            if (marg) std::memcpy(marg, h.data() + 2 * nm, sizeof(double) * nc);
+            if (sig_marg) std::memcpy(sig_marg, h.data() + 2 * nm + nc, sizeof(double) * nc);
+        }
+    }
+    dev_free(d_occ);
+    dev_free(d_par);
+    dev_free(d_acc);
+    dev_free(d_cnt);
+    dev_free(d_out);
+    return rc;
+}
+
 int gbs_get_accumulators(gbs_net_t net, int *n_sub, int *K1, double *acc, int64_t *counts) {
     int rc;
     if ((rc = validate_net(net))) return rc;

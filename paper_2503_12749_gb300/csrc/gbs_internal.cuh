@@ -81,12 +81,27 @@ struct __align__(128) GemmNetDesc {
     double2 *nS_part;        // [mtiles][ld_part] per-tile n_S partials
 };
 
+// Optional per-mode occupation output of the propagation GEMMs: n'_i of
+// trajectory s at p[i * ld + s] (real parts) and p[plane + i * ld + s]
+// (imaginary parts), i < mtiles * 64 (the padding modes of the last tile
+// included), s < ld.  p == nullptr: not written.
+struct OccOut {
+    float *p = nullptr;
+    int64_t ld = 0;
+    int64_t plane = 0;
+};
+struct OccOut64 {
+    double *p = nullptr;
+    int64_t ld = 0;
+    int64_t plane = 0;
+};
+
 // CUDA-event timing of kernel phases (gbs_profile_*).
 struct Profiler {
     bool on = false;
     std::vector<cudaEvent_t> pool;
     std::vector<cudaEvent_t> marks[GBS_NPHASES];  // start, stop, start, stop, ...
-    int64_t launches[GBS_NPHASES] = {0, 0, 0, 0, 0};
+    int64_t launches[GBS_NPHASES] = {};
 };
 
 }  // namespace gbs
@@ -166,10 +181,10 @@ int launch_sample_fp64(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count);
 int launch_sample_bf16(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count);
 
 // Propagation GEMM with the fused occupation epilogue -> nS_part[mtiles][chunk].
-int launch_gemm_fp64(gbs_net *net, int64_t count);
+int launch_gemm_fp64(gbs_net *net, int64_t count, OccOut64 occ = OccOut64());
 int tc_plan_create(gbs_net *net);
 void tc_plan_destroy(gbs_net *net);
-int launch_gemm_tc(gbs_net *net, int64_t count);
+int launch_gemm_tc(gbs_net *net, int64_t count, OccOut occ = OccOut());
 int tc_set_cluster(gbs_net *net, int cluster);  // 0 = autotune, 1, 2
 int tc_get_cluster(gbs_net *net);
 int tc_autotune(gbs_net *net, int64_t count, int *cluster);
@@ -180,7 +195,7 @@ int tc_fill_desc(gbs_net *net, GemmNetDesc *out);
 // count0 trajectories).
 int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int cluster,
                         const GemmNetDesc *d_nets, const int4 *d_tiles, int ntiles, int64_t count0,
-                        unsigned long long *err);
+                        unsigned long long *err, OccOut occ = OccOut());
 
 // Finalise n_S (fixed-order sum of tile partials) and the evaluation windows.
 int launch_finalize(gbs_net *net, int64_t count);
@@ -216,6 +231,25 @@ struct HistSpec {
 // (matrix-P first; bin 0 = below lo, nbins + 1 = at or above hi).
 int launch_histogram(gbs_net *net, int64_t count, const HistSpec &spec,
                      unsigned long long *out_dev);
+
+// Moments and single-mode marginals (k_moments.cu).
+struct MomentSpec {
+    int M, n_sub, mmax, cmax;
+};
+// Bytes per trajectory of the per-trajectory parameters; quantities summed
+// per (sub-ensemble, mode) for (mmax, cmax).
+size_t moment_par_bytes(bool fp64);
+int moment_quantities(int mmax, int cmax);
+// Per-trajectory parameters (tanh n, sign n, logs) of the chunk from n[].
+int launch_moment_prep(const double *n, int64_t count, bool fp64, void *par, cudaStream_t stream,
+                       int sm_count);
+// Adds the chunk's trajectories (first global index e0) to acc[n_sub][M][Q].
+int launch_moments(const MomentSpec &sp, bool fp64, const void *occ, int64_t occ_plane,
+                   int64_t ld_occ, const void *par, int64_t count, uint64_t e0, double *acc,
+                   cudaStream_t stream, int sm_count);
+// Means and errors over sub-ensembles into out = [mom, sig_mom, marg, sig_marg].
+int launch_moment_stats(const MomentSpec &sp, const double *acc, const int64_t *cnt, double *out,
+                        cudaStream_t stream, int sm_count);
 
 // Two-bin estimator (k_bin2d.cu): finalize (per-bin n_S and windows),
 // generating functions on the (Ka x Kb) grid, and the two-dimensional

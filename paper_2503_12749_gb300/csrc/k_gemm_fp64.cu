@@ -23,7 +23,7 @@ constexpr int KT = 16;                // K per smem stage
 __global__ void __launch_bounds__(256) k_gemm_fp64(const double *__restrict__ T64,
                                                    const double *__restrict__ B, int N, int M,
                                                    int64_t count, int64_t ld_part,
-                                                   double2 *__restrict__ nS_part) {
+                                                   double2 *__restrict__ nS_part, OccOut64 occ) {
     __shared__ double As[KT][2 * TM + 1];
     __shared__ double Bs[KT][2 * TS + 1];
     __shared__ double2 red[16][TS];
@@ -91,16 +91,25 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const double *__restrict__ T6
         __syncthreads();
     }
 
-    // occupation epilogue: sum of n'_i over this thread's 4 modes
+    // occupation epilogue: sum of n'_i over this thread's 4 modes (and, on
+    // request, each n'_i itself)
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         double re = 0.0, im = 0.0;
+        const int64_t traj = s0 + tx * 2 + s;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const double ar = acc[m][0][s][0], ai = acc[m][1][s][0];
             const double br = acc[m][0][s][1], bi = acc[m][1][s][1];
-            re += ar * br + ai * bi;
-            im += ai * br - ar * bi;
+            const double ore = ar * br + ai * bi;
+            const double oim = ai * br - ar * bi;
+            if (occ.p && traj < count) {
+                double *dst = occ.p + (size_t)(i0 + ty * 4 + m) * occ.ld + traj;
+                dst[0] = ore;
+                dst[occ.plane] = oim;
+            }
+            re += ore;
+            im += oim;
         }
         red[ty][tx * 2 + s] = make_double2(re, im);
     }
@@ -119,14 +128,15 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const double *__restrict__ T6
 
 }  // namespace
 
-int launch_gemm_fp64(gbs_net *net, int64_t count) {
+int launch_gemm_fp64(gbs_net *net, int64_t count, OccOut64 occ) {
     if (count <= 0) return GBS_OK;
+    if (occ.p && occ.ld < count) return set_error(GBS_EINVAL, "occupation ld < count");
     const int64_t sblocks = (count + TS - 1) / TS;
     if (sblocks > 0x7fffffff) return set_error(GBS_EINVAL, "chunk too large");
     dim3 grid((unsigned)sblocks, (unsigned)net->mtiles);
     k_gemm_fp64<<<grid, 256, 0, net->stream>>>(net->d_T64, static_cast<const double *>(net->d_B),
                                                 net->N, net->M, count, net->chunk,
-                                                net->d_nS_part);
+                                                net->d_nS_part, occ);
     GBS_LAUNCH_CHECK();
     return GBS_OK;
 }

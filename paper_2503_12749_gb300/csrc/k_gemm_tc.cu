@@ -168,7 +168,7 @@ __device__ __forceinline__ void warp_transpose_reduce32(float (&v)[32], int lane
 template <int P, int kCl>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const GemmNetDesc *__restrict__ nets, const int4 *__restrict__ tiles, int ntiles,
-              int64_t count0, unsigned long long *err_ptr) {
+              int64_t count0, unsigned long long *err_ptr, OccOut occ) {
     using C = Cfg<P>;
     constexpr int kStages = C::kStages;
     constexpr int kPl = C::kPlanes;
@@ -448,6 +448,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // occupations of this row for the thread's 64 trajectories, in
             // groups of 16: real part a*b from the own row, imaginary part with
             // the partner row (Re <-> Im of the same mode, lane ^ 1)
+            const bool want_occ = occ.p != nullptr && mt < tr.d->mtiles;
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
                 float v[32];
@@ -458,6 +459,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float pb = __shfl_xor_sync(0xffffffffu, bb, 1);
                     v[2 * q] = a * bb;
                     v[2 * q + 1] = im_row ? a * pb : -a * pb;
+                }
+                if (want_occ) {
+                    // per-mode n'_i: the Re row (even lane) completes Re n'_i
+                    // with the Im row's a_i b_i, the Im row (odd lane) Im n'_i
+                    // with the Re row's -a_r b_i; 16 trajectories per lane
+                    float *dst = occ.p + (size_t)(lane & 1) * occ.plane +
+                                 (size_t)(mt * 64 + (row >> 1)) * occ.ld + (size_t)st * 128 +
+                                 half * 64 + g * 16;
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        float o[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int q = q4 * 4 + u;
+                            const float send = im_row ? v[2 * q] : v[2 * q + 1];
+                            const float own = im_row ? v[2 * q + 1] : v[2 * q];
+                            o[u] = own + __shfl_xor_sync(0xffffffffu, send, 1);
+                        }
+                        *reinterpret_cast<float4 *>(dst + q4 * 4) = make_float4(o[0], o[1], o[2], o[3]);
+                    }
                 }
                 warp_transpose_reduce32(v, lane);
                 const int traj = half * 64 + g * 16 + (lane >> 1);
@@ -544,7 +565,7 @@ int ensure_attrs() {
 
 template <int P, int kCl>
 int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets, const int4 *d_tiles,
-                   int ntiles, int64_t count0, unsigned long long *err) {
+                   int ntiles, int64_t count0, unsigned long long *err, OccOut occ) {
     if (ntiles <= 0) return GBS_OK;
     const int clusters = std::max(1, std::min(ntiles, sm_count / kCl));
     cudaLaunchConfig_t cfg = {};
@@ -559,7 +580,7 @@ int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = kCl > 1 ? 1 : 0;
-    cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_tc<P, kCl>, d_nets, d_tiles, ntiles, count0, err);
+    cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_tc<P, kCl>, d_nets, d_tiles, ntiles, count0, err, occ);
     if (le != cudaSuccess)
         return set_error(GBS_ECUDA, "launch of the GEMM (%d products, cluster %d) failed: %s", P,
                          kCl, cudaGetErrorString(le));
@@ -621,14 +642,16 @@ int bucket(int v) {
 
 int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int cluster,
                         const GemmNetDesc *d_nets, const int4 *d_tiles, int ntiles, int64_t count0,
-                        unsigned long long *err) {
+                        unsigned long long *err, OccOut occ) {
     int rc;
     if ((rc = ensure_attrs())) return rc;
+    if (occ.p && (d_tiles || occ.ld % 128 != 0 || occ.ld < count0))
+        return set_error(GBS_EINVAL, "occupation output needs closed-form tiles and ld >= count, ld %% 128 == 0");
     if (P == 3)
-        return cluster == 1 ? launch_variant<3, 1>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err)
-                            : launch_variant<3, 2>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err);
-    return cluster == 1 ? launch_variant<6, 1>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err)
-                        : launch_variant<6, 2>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err);
+        return cluster == 1 ? launch_variant<3, 1>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ)
+                            : launch_variant<3, 2>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ);
+    return cluster == 1 ? launch_variant<6, 1>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ)
+                        : launch_variant<6, 2>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ);
 }
 
 int tc_fill_desc(gbs_net *net, GemmNetDesc *out) {
@@ -724,7 +747,7 @@ int tc_autotune(gbs_net *net, int64_t count, int *out) {
     return GBS_OK;
 }
 
-int launch_gemm_tc(gbs_net *net, int64_t count) {
+int launch_gemm_tc(gbs_net *net, int64_t count, OccOut occ) {
     if (count <= 0) return GBS_OK;
     TcPlan *plan = net->tc;
     if (!plan) return set_error(GBS_EINVAL, "no tensor-core plan");
@@ -739,7 +762,7 @@ int launch_gemm_tc(gbs_net *net, int64_t count) {
     const int groups = (net->mtiles + cl - 1) / cl;
     const int stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
     return launch_gemm_grouped(net->stream, net->sm_count, plan->P, cl, plan->d_desc, nullptr,
-                               groups * stiles, count, net->d_flags + 1);
+                               groups * stiles, count, net->d_flags + 1, occ);
 }
 
 }  // namespace gbs
