@@ -507,6 +507,96 @@ def bin2d_arm(args):
     return 0
 
 
+def moments_arm(args):
+    """Normally-ordered moments <:n_j^m:> (m = 1..4) and single-mode
+    marginals P_j(c) (c = 0..7) of every output mode of the m1000 network
+    (Eq. moment, Eq. projection_op with S = {j}): BF16x3 propagation with
+    the per-mode occupations written by the GEMM, 10^6 trajectories per
+    step, N_R = 100.  One step = one gbs_moments call (synchronous)."""
+    import numpy as np
+    import torch
+
+    import oracle.moments as orc_mo
+    import paper_2503_12749_gb300 as gbs
+    import workloads as wl
+
+    torch.cuda.set_device(0)
+    gbs.build()
+    stream = torch.cuda.Stream()
+    w = wl.M1000
+    netdef = w.network()
+    E = args.samples or w.E
+    n_sub, mmax, cmax = w.n_sub, 4, 7
+    net = gbs.gbs_make_network(netdef.T, netdef.r, "bf16x3", stream.cuda_stream)
+    seed = netdef.seed_s
+
+    def step(s):
+        return gbs.gbs_moments(net, seed, s * E, E, n_sub, mmax, cmax)
+
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        res = step(args.warmup + s)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    ms_step = 1e3 * wall / args.steps
+    nprof = 2
+    gbs.gbs_profile_enable(net, True)
+    for s in range(nprof):
+        step(args.warmup + args.steps + s)
+    prof = gbs.gbs_profile_read(net)
+    gbs.gbs_profile_enable(net, False)
+    phases = {k: {"ms_per_step": v[0] / nprof, "launches_per_step": v[1] / nprof}
+              for k, v in prof.items() if v[1]}
+    mom_ms = phases["moments"]["ms_per_step"]
+    # the run's agreement with the exact Gaussian moments (E1)
+    emom = orc_mo.exact_moments(netdef.T, netdef.r, mmax)
+    z = (res[0][0] - emom) / np.maximum(res[1][0], 1e-300)
+    cpu = None
+    if not args.no_cpu_baseline:
+        Ec = 256
+        t0 = time.perf_counter()
+        orc_mo.run(netdef.T, netdef.r, seed, 0, Ec, 16, mmax, cmax)
+        dt = time.perf_counter() - t0
+        cpu = {"value": Ec / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
+               "sample": f"{Ec} trajectories of the same network (oracle/moments.py: C "
+                         "sampler and propagation, numpy moments and projectors)"}
+    elements = float(E) * w.M
+    line = {
+        "metric": "normally-ordered moments (m<=4) and single-mode marginals (c<=7) of every "
+                  "output mode: matrix-P samples/s",
+        "value": E / (ms_step / 1e3), "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3 GEMM, f32 per-mode values (f64 beyond |n'| = 40), f64 sums",
+        "data": "synthetic",
+        "config": {"workload": "moments: m1000 network N=M=1000 r=1 t2=0.98, E=10^6 per step, "
+                               "N_R=100, mmax=4, cmax=7", "samples_per_step": E,
+                   "timing": "wall clock per step; gbs_moments is synchronous",
+                   "l2": "occupation planes (8 GB per step) larger than L2"},
+        "phases": phases,
+        "roofline": {"bound": "alu", "kernel": "k_moments<float, 4, 7>",
+                     "elements_per_s": elements / (mom_ms / 1e3), "ms_per_step": mom_ms,
+                     "achieved": None, "peak": None, "unit": None, "frac": None,
+                     "traffic": None,
+                     "note": "issue-bound FP32 evaluation, 8 B of occupations read per "
+                             "(mode, trajectory); the step's largest phase is the GEMM "
+                             "(tensor); see profiles/"},
+        "result": {"max_abs_z_matrixP_moments": float(np.max(np.abs(z))),
+                   "mean_z2": float(np.mean(z ** 2))},
+        "cpu_baseline": cpu,
+        "gpu_launches": int(round(sum(v[1] for v in prof.values()) / nprof * args.steps)),
+        "clocks": clk,
+    }
+    gbs.gbs_free_network(net)
+    print(json.dumps(line))
+    return 0
+
+
 # Appendix B, Fig. 6: m_max (total-count probability 1e-7) for M = 128 ... 8192
 # (left, lossless r = 0.89, with m_min) and for M = 16 ... 1024 (right caption)
 FIG6_LEFT = {"M": [128, 256, 512, 1024, 2048, 4096, 8192],
@@ -781,7 +871,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
     ap.add_argument("--workload", default="m1000",
-                    choices=sorted(wl.NAMED) + ["batch64", "surrogate", "bin2d", "fig6"])
+                    choices=sorted(wl.NAMED) + ["batch64", "surrogate", "bin2d", "fig6", "moments"])
     ap.add_argument("--sur-train", type=int, default=2000)
     ap.add_argument("--sur-train-samples", type=int, default=2 ** 16)
     ap.add_argument("--sur-heldout", type=int, default=50)
@@ -814,6 +904,12 @@ def main():
                               "unavailable": "the reference arm is defined for the m1000 workload"}))
             return 0
         return bin2d_arm(args)
+    if args.workload == "moments":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference",
+                              "unavailable": "the reference arm is defined for the m1000 workload"}))
+            return 0
+        return moments_arm(args)
     if args.workload == "surrogate":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference",

@@ -808,12 +808,15 @@ int gbs_moments(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, 
     const size_t nm = (size_t)2 * net->M * mmax, nc = (size_t)2 * net->M * (cmax + 1);
     void *d_occ = nullptr;
     uint8_t *d_par = nullptr;
-    double *d_acc = nullptr, *d_out = nullptr;
+    double *d_acc = nullptr, *d_out = nullptr, *d_scr = nullptr;
+    const int max_seg = moment_max_segments(n_sub, net->M, mmax, cmax);
     int64_t *d_cnt = nullptr;
     if (fp64) rc = dev_alloc(reinterpret_cast<double **>(&d_occ), (size_t)2 * plane, "occupations");
     else rc = dev_alloc(reinterpret_cast<float **>(&d_occ), (size_t)2 * plane, "occupations");
     if (!rc) rc = dev_alloc(&d_par, (size_t)ld * moment_par_bytes(fp64), "trajectory parameters");
     if (!rc) rc = dev_alloc(&d_acc, (size_t)n_sub * net->M * Q, "moment sums");
+    if (!rc && max_seg > 1)
+        rc = dev_alloc(&d_scr, (size_t)max_seg * n_sub * net->M * Q, "moment segment sums");
     if (!rc) rc = dev_alloc(&d_cnt, (size_t)n_sub, "sub-ensemble sizes");
     if (!rc) rc = dev_alloc(&d_out, 2 * nm + 2 * nc, "moment outputs");
     if (!rc && cudaMemsetAsync(d_acc, 0, sizeof(double) * n_sub * net->M * Q, net->stream) != cudaSuccess)
@@ -826,28 +829,36 @@ int gbs_moments(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, 
     for (int64_t done = 0; !rc && done < E; done += ld) {
         const int64_t c = std::min<int64_t>(ld, E - done);
         const uint64_t e0 = first_sample + (uint64_t)done;
+        int nl = 0;
         rc = run_chunk_occ(net, seed, e0, c, d_occ, ld);
         if (!rc) {
             prof_mark(net, GBS_PHASE_MOMENTS, 0, true);
             rc = launch_moment_prep(net->d_n, c, fp64, d_par, net->stream, net->sm_count);
         }
         if (!rc)
-            rc = launch_moments(sp, fp64, d_occ, plane, ld, d_par, c, e0, d_acc, net->stream,
-                                net->sm_count);
-        if (!rc) prof_mark(net, GBS_PHASE_MOMENTS, 2, false);
+            rc = launch_moments(sp, fp64, d_occ, plane, ld, d_par, net->d_n, c, e0, d_acc, d_scr,
+                                max_seg, net->d_flags + 1, net->stream, net->sm_count, &nl);
+        if (!rc) prof_mark(net, GBS_PHASE_MOMENTS, 1 + nl, false);
     }
     if (!rc) {
         prof_mark(net, GBS_PHASE_MOMENTS, 0, true);
-        rc = launch_moment_stats(sp, d_acc, d_cnt, d_out, net->stream, net->sm_count);
+        rc = launch_moment_stats(sp, fp64, d_acc, d_cnt, d_out, net->stream, net->sm_count);
         if (!rc) prof_mark(net, GBS_PHASE_MOMENTS, 1, false);
     }
     if (!rc) {
         std::vector<double> h(2 * nm + 2 * nc);
+        unsigned long long timed_out = 0;
         if (cudaMemcpyAsync(h.data(), d_out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                            net->stream) != cudaSuccess ||
+            cudaMemcpyAsync(&timed_out, net->d_flags + 1, sizeof(timed_out), cudaMemcpyDeviceToHost,
                             net->stream) != cudaSuccess ||
             cudaStreamSynchronize(net->stream) != cudaSuccess)
             rc = set_error(GBS_ECUDA, "moment copy failed");
-        else {
+        else if (timed_out) {
+            cudaMemsetAsync(net->d_flags + 1, 0, sizeof(unsigned long long), net->stream);
+            cudaStreamSynchronize(net->stream);
+            rc = set_error(GBS_ETIMEOUT, "a GEMM or moments kernel gave up waiting on its pipeline");
+        } else {
             if (mom) std::memcpy(mom, h.data(), sizeof(double) * nm);
             if (sig_mom) std::memcpy(sig_mom, h.data() + nm, sizeof(double) * nm);
             if (marg) std::memcpy(marg, h.data() + 2 * nm, sizeof(double) * nc);
@@ -857,6 +868,7 @@ int gbs_moments(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, 
     dev_free(d_occ);
     dev_free(d_par);
     dev_free(d_acc);
+    dev_free(d_scr);
     dev_free(d_cnt);
     dev_free(d_out);
     return rc;

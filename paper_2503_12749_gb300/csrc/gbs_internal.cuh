@@ -243,13 +243,21 @@ int moment_quantities(int mmax, int cmax);
 // Per-trajectory parameters (tanh n, sign n, logs) of the chunk from n[].
 int launch_moment_prep(const double *n, int64_t count, bool fp64, void *par, cudaStream_t stream,
                        int sm_count);
-// Adds the chunk's trajectories (first global index e0) to acc[n_sub][M][Q].
+// Segments of a chunk whose scratch sums (max_seg [n_sub][M][Q] doubles) stay
+// below 1 GiB.
+int moment_max_segments(int n_sub, int M, int mmax, int cmax);
+// Adds the chunk's trajectories (first global index e0; n[] their input
+// totals) to acc[n_sub][M][Q], through scratch[max_seg][n_sub][M][Q] when
+// the chunk is cut into segments; a bounded wait that gives up raises *err;
+// *nlaunch = kernels launched.
 int launch_moments(const MomentSpec &sp, bool fp64, const void *occ, int64_t occ_plane,
-                   int64_t ld_occ, const void *par, int64_t count, uint64_t e0, double *acc,
-                   cudaStream_t stream, int sm_count);
-// Means and errors over sub-ensembles into out = [mom, sig_mom, marg, sig_marg].
-int launch_moment_stats(const MomentSpec &sp, const double *acc, const int64_t *cnt, double *out,
-                        cudaStream_t stream, int sm_count);
+                   int64_t ld_occ, const void *par, const double *n, int64_t count, uint64_t e0,
+                   double *acc, double *scratch, int max_seg, unsigned long long *err,
+                   cudaStream_t stream, int sm_count, int *nlaunch);
+// Means and errors over sub-ensembles into out = [mom, sig_mom, marg, sig_marg]
+// (the sums of BF16 networks hold the marginals without their 1/c!).
+int launch_moment_stats(const MomentSpec &sp, bool fp64, const double *acc, const int64_t *cnt,
+                        double *out, cudaStream_t stream, int sm_count);
 
 // Two-bin estimator (k_bin2d.cu): finalize (per-bin n_S and windows),
 // generating functions on the (Ka x Kb) grid, and the two-dimensional

@@ -6,7 +6,8 @@
 //        = (a_r b_r + a_i b_i) + i (a_i b_r - a_r b_i),
 //   a = (Re T alpha, Im T alpha)_i, b = (Re T beta, Im T beta)_i,
 // summed over the tile's output modes.  alpha', beta' never leave registers;
-// the kernel writes one partial n_S per (mode tile, trajectory).
+// the kernel writes one partial n_S per (mode tile, trajectory) and, on
+// request (moments and marginals), every n'_i.
 //
 // Tile: 64 output modes x 32 trajectories per 256-thread block; each thread
 // owns 4 modes x 2 trajectories (32 FP64 accumulators).  This path is bound

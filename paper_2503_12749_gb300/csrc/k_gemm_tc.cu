@@ -47,7 +47,10 @@
 //               last K block: occupations, butterfly transpose-reduction over
 //               the 32 lanes, then the 4 lane quarters in a fixed order -> one
 //               n_S partial per (mode tile, trajectory).  alpha', beta' never
-//               leave the SM.
+//               leave the SM.  On request (moments and marginals) the
+//               epilogue also writes every n'_i: with 3 products each warp
+//               stages its 32 x 16 values in shared memory and stores rows
+//               of 64 bytes, 8 rows per instruction.
 // Every mbarrier wait is bounded; on a timeout the kernel raises an error
 // flag, drains its own TMA loads and MMAs, frees TMEM and returns.
 #include "gbs_internal.cuh"
@@ -83,13 +86,27 @@ struct Cfg {
     static constexpr int kStages = (P == 3) ? 4 : 3;
 };
 constexpr int kBarBytes = 1024;
+constexpr int kEpiWarpsFwd = 8;  // epilogue warps (kEpiWarps below)
 constexpr int kRedBytes = 4 * 128 * 2 * 4;  // float [4 quarters][128 trajectories][re, im]
+// Occupation staging (3 products only; the 6-product ring leaves no room):
+// per epilogue warp 32 rows (Re/Im plane x 16 modes) of 16 trajectories,
+// rows padded to 20 floats so that the row-wise float4 writes are free of
+// bank conflicts.
+constexpr int kOccRow = 20;
+constexpr int kOccWarpFloats = 32 * kOccRow;
+template <int P>
+constexpr int occ_stage_bytes() {
+    return P == 3 ? kEpiWarpsFwd * kOccWarpFloats * 4 : 0;
+}
 template <int P>
 constexpr int smem_bytes() {
-    return 1024 + Cfg<P>::kStages * Cfg<P>::kStageBytes + kBarBytes + kRedBytes;
+    return 1024 + Cfg<P>::kStages * Cfg<P>::kStageBytes + kBarBytes + kRedBytes +
+           occ_stage_bytes<P>();
 }
+static_assert(smem_bytes<3>() <= 227 * 1024, "shared memory of the 3-product GEMM");
+static_assert(smem_bytes<6>() <= 227 * 1024, "shared memory of the 6-product GEMM");
 constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(128, 256);
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = kEpiWarpsFwd;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
 
@@ -190,6 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *drain = bars + 2 * kStages + 4;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 5);
     float *red = reinterpret_cast<float *>(smem + kStages * C::kStageBytes + kBarBytes);
+    float *ostage = reinterpret_cast<float *>(smem + kStages * C::kStageBytes + kBarBytes + kRedBytes);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -464,9 +482,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // per-mode n'_i: the Re row (even lane) completes Re n'_i
                     // with the Im row's a_i b_i, the Im row (odd lane) Im n'_i
                     // with the Re row's -a_r b_i; 16 trajectories per lane
+                    const size_t tcol = (size_t)st * 128 + half * 64 + g * 16;
                     float *dst = occ.p + (size_t)(lane & 1) * occ.plane +
-                                 (size_t)(mt * 64 + (row >> 1)) * occ.ld + (size_t)st * 128 +
-                                 half * 64 + g * 16;
+                                 (size_t)(mt * 64 + (row >> 1)) * occ.ld + tcol;
+                    float *srow = ostage + (warp - 2) * kOccWarpFloats + lane * kOccRow;
 #pragma unroll
                     for (int q4 = 0; q4 < 4; ++q4) {
                         float o[4];
@@ -477,7 +496,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const float own = im_row ? v[2 * q + 1] : v[2 * q];
                             o[u] = own + __shfl_xor_sync(0xffffffffu, send, 1);
                         }
-                        *reinterpret_cast<float4 *>(dst + q4 * 4) = make_float4(o[0], o[1], o[2], o[3]);
+                        const float4 o4 = make_float4(o[0], o[1], o[2], o[3]);
+                        if (P == 3) *reinterpret_cast<float4 *>(srow + q4 * 4) = o4;
+                        else __stcs(reinterpret_cast<float4 *>(dst + q4 * 4), o4);
+                    }
+                    if (P == 3) {
+                        // rows of 64 bytes out of the staging area: 4 lanes per
+                        // row, 8 rows per store instruction (instead of 32
+                        // rows of 16 bytes)
+                        __syncwarp();
+                        const float *wst = ostage + (warp - 2) * kOccWarpFloats;
+#pragma unroll
+                        for (int pass = 0; pass < 4; ++pass) {
+                            const int sr = pass * 8 + (lane >> 2);  // producing lane
+                            const float4 v4 =
+                                *reinterpret_cast<const float4 *>(wst + sr * kOccRow + (lane & 3) * 4);
+                            float *d = occ.p + (size_t)(sr & 1) * occ.plane +
+                                       (size_t)(mt * 64 + quarter * 16 + (sr >> 1)) * occ.ld + tcol +
+                                       (lane & 3) * 4;
+                            __stcs(reinterpret_cast<float4 *>(d), v4);  // evict-first in L2
+                        }
+                        __syncwarp();
                     }
                 }
                 warp_transpose_reduce32(v, lane);
