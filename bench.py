@@ -480,6 +480,13 @@ def bin2d_arm(args):
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     ms_step = 1e3 * wall / args.steps
+    # kernel launches per step: one further step with phase timing
+    gbs.gbs_reset(net)
+    gbs.gbs_profile_enable(net, True)
+    step(args.warmup + args.steps)
+    prof = gbs.gbs_profile_read(net)
+    gbs.gbs_profile_enable(net, False)
+    launches_per_step = sum(v[1] for v in prof.values())
     line = {
         "metric": "two-bin matrix-P samples/s (joint P(m1, m2) of the paper's 200-mode example)",
         "value": E / (ms_step / 1e3), "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
@@ -500,7 +507,8 @@ def bin2d_arm(args):
                      "note": "issue-bound double-float generating functions on the FP32 "
                              "pipes, like the one-bin k_gf_df (see profiles/); not measured "
                              "separately for this workload"},
-        "gpu_launches": None, "clocks": clk,
+        "phases": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
+        "gpu_launches": launches_per_step * args.steps, "clocks": clk,
     }
     gbs.gbs_free_network(net)
     print(json.dumps(line))
@@ -639,13 +647,17 @@ def fig6_arm(args):
         gbs.gbs_sample(net, seed, 0, 2 ** 14, n_sub, K1)   # warm-up (tuning, allocations)
         gbs.gbs_reset(net)
         torch.cuda.synchronize()
+        # phase events (a few per chunk) count the kernel launches of the run
+        gbs.gbs_profile_enable(net, True)
         t0 = time.perf_counter()
         gbs.gbs_sample(net, seed, 0, E, n_sub, K1)
         P = gbs.gbs_binned_counts(net, mn, K1)
         dt = time.perf_counter() - t0
+        prof = gbs.gbs_profile_read(net)
         gbs.gbs_free_network(net)
         left.append({"M": M, "K1": K1, "m_off": mn, "seconds": dt, "samples_per_s": E / dt,
-                     "max_sigma": float(P[1].max())})
+                     "max_sigma": float(P[1].max()),
+                     "launches": sum(v[1] for v in prof.values())})
     right = []
     for M, mx in zip(FIG6_RIGHT["M"], FIG6_RIGHT["m_max"]):
         U = wl.haar_unitary(M, wl.SEED_U_BASE + 8000 + M)
@@ -676,7 +688,7 @@ def fig6_arm(args):
         "left": left, "right": right,
         "result": {"max_sigma_decreases_with_M": {
             k: bool(right[-1][k] < right[0][k]) for k in ("t=1", "t=0.995", "t=1-1/m_max")}},
-        "roofline": None, "gpu_launches": None,
+        "roofline": None, "gpu_launches": big["launches"],
     }
     print(json.dumps(line))
     return 0

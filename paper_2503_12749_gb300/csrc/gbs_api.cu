@@ -126,6 +126,8 @@ void release_estimator(gbs_net *net) {
     dev_free(net->d_f2a);
     dev_free(net->d_f2b);
     dev_free(net->d_out2);
+    if (net->d_sep2) cudaFree(net->d_sep2);
+    net->d_sep2 = nullptr;
     net->counts2.clear();
     net->est2_fixed = false;
     net->n_sub2 = net->Ka = net->Kb = 0;
@@ -214,11 +216,18 @@ __global__ void k_split_from_dev(const double *__restrict__ T, int N, int M, int
 int run_chunk_front2d(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) {
     int rc;
     const bool fp64 = net->precision == GBS_FP64;
+    prof_mark(net, GBS_PHASE_SAMPLE, 0, true);
     rc = fp64 ? launch_sample_fp64(net, seed, e0, count) : launch_sample_bf16(net, seed, e0, count);
     if (rc) return rc;
+    prof_mark(net, GBS_PHASE_SAMPLE, 1, false);
+    prof_mark(net, GBS_PHASE_GEMM, 0, true);
     rc = fp64 ? launch_gemm_fp64(net, count) : launch_gemm_tc(net, count);
     if (rc) return rc;
-    return launch_finalize2d(net, count);
+    prof_mark(net, GBS_PHASE_GEMM, 1, false);
+    prof_mark(net, GBS_PHASE_FINALIZE, 0, true);
+    if ((rc = launch_finalize2d(net, count))) return rc;
+    prof_mark(net, GBS_PHASE_FINALIZE, 1, false);
+    return GBS_OK;
 }
 
 int fix_estimator2d(gbs_net *net, int n_sub, int Ka, int Kb) {
@@ -246,6 +255,12 @@ int fix_estimator2d(gbs_net *net, int n_sub, int Ka, int Kb) {
         (rc = dev_alloc(&net->d_f2b, accn, "fft2b")) ||
         (rc = dev_alloc(&net->d_out2, (size_t)4 * Ka * Kb, "out2")))
         return rc;
+    if (net->precision != GBS_FP64) {
+        uint8_t *sep = nullptr;
+        if ((rc = dev_alloc(&sep, (size_t)net->chunk * sep2_bytes_per_trajectory(), "sep2")))
+            return rc;
+        net->d_sep2 = sep;
+    }
     GBS_CUDA_TRY(cudaMemsetAsync(net->d_acc2, 0, accn * sizeof(double2), net->stream));
     GBS_CUDA_TRY(cudaMemsetAsync(net->d_counts2, 0, (size_t)n_sub * sizeof(int64_t), net->stream));
     if ((rc = launch_tables2d(net))) return rc;
@@ -597,7 +612,9 @@ int gbs_check_finite(gbs_net_t net, int64_t *count) {
     if ((rc = validate_net(net))) return rc;
     if (count) *count = 0;
     if (!net->est_fixed) return GBS_OK;
+    prof_mark(net, GBS_PHASE_INVERT, 0, true);
     if ((rc = launch_count_nonfinite(net))) return rc;
+    prof_mark(net, GBS_PHASE_INVERT, 1, false);
     unsigned long long h = 0;
     GBS_CUDA_TRY(cudaMemcpyAsync(&h, net->d_flags, sizeof(h), cudaMemcpyDeviceToHost, net->stream));
     GBS_CUDA_TRY(cudaStreamSynchronize(net->stream));
@@ -918,7 +935,9 @@ int gbs_sample_2d(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E
         const int64_t c = std::min<int64_t>(net->chunk, E - done);
         const uint64_t e0 = first_sample + (uint64_t)done;
         if ((rc = run_chunk_front2d(net, seed, e0, c))) return rc;
+        prof_mark(net, GBS_PHASE_GF, 0, true);
         if ((rc = launch_gf2d(net, e0, c))) return rc;
+        prof_mark(net, GBS_PHASE_GF, net->precision == GBS_FP64 ? 1 : 2, false);
     }
     const uint64_t ns = (uint64_t)net->n_sub2;
     const uint64_t full = (uint64_t)E / ns, rem = (uint64_t)E % ns;
@@ -936,7 +955,12 @@ int gbs_binned_counts_2d(gbs_net_t net, int64_t m1_offset, int64_t m2_offset, do
     for (int q = 0; q < net->n_sub2; ++q)
         if (net->counts2[q] <= 0)
             return set_error(GBS_EINVAL, "sub-ensemble %d has no trajectories", q);
+    int lg = 0;
+    for (int v = net->Ka; v > 1; v >>= 1) ++lg;
+    for (int v = net->Kb; v > 1; v >>= 1) ++lg;
+    prof_mark(net, GBS_PHASE_INVERT, 0, true);
     if ((rc = launch_invert2d(net, m1_offset, m2_offset, net->d_out2))) return rc;
+    prof_mark(net, GBS_PHASE_INVERT, 3 + lg, false);  // prep, FFT passes, transpose, stats
     const size_t grid = (size_t)net->Ka * net->Kb;
     double *dst[4] = {P_mP, sig_mP, P_plusP, sig_plusP};
     for (int q = 0; q < 4; ++q)

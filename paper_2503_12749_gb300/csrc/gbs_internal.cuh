@@ -169,6 +169,7 @@ struct gbs_net {
     double2 *d_wf2 = nullptr;       // [Ka + Kb]: e^{-i theta}
     double2 *d_f2a = nullptr, *d_f2b = nullptr;  // [2][n_sub2][Ka * Kb] FFT work
     double *d_out2 = nullptr;       // [4][Ka * Kb]
+    void *d_sep2 = nullptr;         // [chunk] per-trajectory constants (BF16 networks)
 };
 
 namespace gbs {
@@ -264,6 +265,7 @@ int launch_moment_stats(const MomentSpec &sp, bool fp64, const double *acc, cons
 // inversion into out_dev[4][Ka * Kb].
 int launch_finalize2d(gbs_net *net, int64_t count);
 int launch_gf2d(gbs_net *net, uint64_t e0, int64_t count);
+size_t sep2_bytes_per_trajectory();
 int launch_tables2d(gbs_net *net);
 int launch_invert2d(gbs_net *net, int64_t m1_off, int64_t m2_off, double *out_dev);
 

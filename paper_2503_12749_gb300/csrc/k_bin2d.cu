@@ -232,134 +232,300 @@ __global__ void __launch_bounds__(kG2Threads)
     }
 }
 
-// The same sums in double-float arithmetic (BF16 networks).
-__global__ void __launch_bounds__(kG2Threads)
-    k_gf2d_df(const double *__restrict__ n_in, const double2 *__restrict__ nS2,
-              const Window2 *__restrict__ win_in, const int *__restrict__ wmax, int64_t count,
+// The same sums in double-float arithmetic (BF16 networks), from the
+// factorisation of the exponent by bins.  With l_b + i phi_b = (z_b - 1) n_Sb,
+//   e^{L}  = [e^{l_1 + M_2} e^{i phi_1}] [e^{l_2 - M_2} e^{i phi_2}],
+//   inv e^{-L + c2} = [e^{-l_1 + M'_2 + c2 + log inv} e^{-i phi_1}]
+//                     [e^{-l_2 - M'_2} e^{-i phi_2}],
+// M_b = max over theta of l_b (max_term1), M'_b = max of -l_b (max_term2),
+// inv = 1 / (1 + e^{-2|n|}): every bin-2 factor is at most 1 and every
+// bin-1 factor at most e^{M_1 + M_2} (or e^{M'_1 + M'_2 + c2 + log inv}).
+// A trajectory is therefore a pair of vectors per bin on the CTA's slots, and
+// its terms on the CTA's (k_1, k_2) tile are outer products:
+//   G_+P = A_1 A_2,   G_mP = inv e^{c1} A_1 A_2 + B_1 B_2.
+// Per pair this is one or two double-float complex products instead of an
+// exponential and a sine/cosine.  Factors below FP32's normal range (e^-87)
+// are flushed to zero: with the exponents capped at 40 (else the trajectory
+// takes the per-pair FP64 route), a flushed factor drops only terms below
+// e^{40 - 87} < 2^-60, the threshold of the windows.  The sums are kept as
+// +P and (matrix-P - +P): the difference needs only the B_1 B_2 term when
+// inv e^{c1} = 1.
+//
+// CTA: a tile of 32 x 32 (k_1, k_2) slots of one sub-ensemble, 256 threads of
+// 2 x 2 pairs; rounds of 16 trajectories: the bin vectors of the round on the
+// tile's slots are evaluated into shared memory (double-float table exp and
+// sin/cos), then each thread accumulates its pairs in double-float and adds
+// the round to FP64 accumulators, trajectories in increasing order.
+constexpr int kSepTile = 32;     // slots per bin per CTA
+constexpr int kSepThreads = 256; // 16 x 16 threads, 2 x 2 pairs each
+constexpr int kSepRound = 16;    // trajectories per round
+
+// Per-trajectory constants of the factorised evaluation (one pass per chunk):
+// the bins' n_S in double-float and the exponent offsets.
+struct __align__(16) SepTraj {
+    df x1, y1, x2, y2;  // n_S1, n_S2
+    df m2, mp2;         // M_2, M'_2 (offsets of the bin-2 factors)
+    df o1a, o1b;        // offsets of the bin-1 factors: +M_2, +M'_2 + c2 + log inv
+    df rA;              // inv e^{c1} (<= 1)
+    int flags;          // 2: per-pair FP64 route, 4: B term used, 8: rA == 1
+    int pad;
+};
+
+__global__ void k_sep_prep(const double *__restrict__ n_in, const double2 *__restrict__ nS2,
+                           int64_t count, SepTraj *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double nn = n_in[i];
+        const double2 a = nS2[2 * i], b = nS2[2 * i + 1];
+        const double M1 = max_term1(a.x, a.y), M2 = max_term1(b.x, b.y);
+        const double P1 = max_term2(a.x, a.y), P2 = max_term2(b.x, b.y);
+        const double c1 = fmin(0.0, 2.0 * nn), c2 = -2.0 * fmax(nn, 0.0);
+        const double linv = -log1p(exp(-2.0 * fabs(nn)));
+        const double lwB = P1 + P2 + c2 + linv;
+        const bool big = fabs(a.x) + 2.0 * fabs(a.y) >= 6000.0 ||
+                         fabs(b.x) + 2.0 * fabs(b.y) >= 6000.0 || M1 + M2 > 40.0 || lwB > 40.0 ||
+                         !(M1 + M2 >= 0.0);
+        SepTraj st;
+        st.x1 = df_from_double(a.x);
+        st.y1 = df_from_double(a.y);
+        st.x2 = df_from_double(b.x);
+        st.y2 = df_from_double(b.y);
+        st.m2 = df_from_double(M2);
+        st.mp2 = df_from_double(P2);
+        st.o1a = df_from_double(M2);
+        st.o1b = df_from_double(P2 + c2 + linv);
+        const double rA = exp(c1 + linv);
+        st.rA = df_from_double(rA);
+        st.flags = (big ? 2 : 0) | (lwB >= -42.0 ? 4 : 0) | (rA == 1.0 ? 8 : 0);
+        st.pad = 0;
+        out[i] = st;
+    }
+}
+
+// unnormalised double-float complex product a b: (re.hi, re.lo, im.hi, im.lo)
+__device__ __forceinline__ float4 dfc_mul(const float4 a, const float4 b) {
+    const float p1 = a.x * b.x, e1 = fmaf(a.x, b.x, -p1);
+    const float p2 = a.z * b.z, e2 = fmaf(a.z, b.z, -p2);
+    const df sr = df_two_sum(p1, -p2);
+    const float lr = fmaf(a.x, b.y, fmaf(a.y, b.x, e1)) - fmaf(a.z, b.w, fmaf(a.w, b.z, e2)) + sr.lo;
+    const float p3 = a.x * b.z, e3 = fmaf(a.x, b.z, -p3);
+    const float p4 = a.z * b.x, e4 = fmaf(a.z, b.x, -p4);
+    const df si = df_two_sum(p3, p4);
+    const float li = fmaf(a.x, b.w, fmaf(a.y, b.z, e3)) + fmaf(a.z, b.y, fmaf(a.w, b.x, e4)) + si.lo;
+    return make_float4(sr.hi, lr, si.hi, li);
+}
+
+// acc += t (both unnormalised double-float complex)
+__device__ __forceinline__ void dfc_acc(float4 &acc, const float4 t) {
+    const df r = df_two_sum(acc.x, t.x);
+    const df i = df_two_sum(acc.z, t.z);
+    acc = make_float4(r.hi, acc.y + t.y + r.lo, i.hi, acc.w + t.w + i.lo);
+}
+
+__device__ __forceinline__ float4 dfc_scale(const float4 a, const df s) {
+    const df re = df_mul(df{a.x, a.y}, s), im = df_mul(df{a.z, a.w}, s);
+    return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+__device__ __forceinline__ float4 dfc_norm(const float4 a) {
+    const df re = df_fast_two_sum(a.x, a.y), im = df_fast_two_sum(a.z, a.w);
+    return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+constexpr int kSepFlush = 4;  // rounds between additions to the FP64 sums
+
+__global__ void __launch_bounds__(kSepThreads)
+    k_gf2d_df(const SepTraj *__restrict__ sep, const double *__restrict__ n_in,
+              const double2 *__restrict__ nS2, const int *__restrict__ wmax, int64_t count,
               uint64_t e0, int n_sub, int Ka, int Kb, const double2 *__restrict__ tw,
               const DfConsts K, double2 *__restrict__ acc, int64_t *__restrict__ counts) {
-    __shared__ df s_x1[kG2Tile], s_y1[kG2Tile], s_x2[kG2Tile], s_y2[kG2Tile];
-    __shared__ df s_c1[kG2Tile], s_c2[kG2Tile], s_inv[kG2Tile];
-    __shared__ double s_n[kG2Tile];
-    __shared__ double2 s_s1[kG2Tile], s_s2[kG2Tile];
-    __shared__ Window2 s_w[kG2Tile];
+    __shared__ float4 sA1[kSepRound][kSepTile], sB1[kSepRound][kSepTile];
+    __shared__ float4 sA2[kSepRound][kSepTile], sB2[kSepRound][kSepTile];
+    __shared__ SepTraj s_t[kSepRound];
+    __shared__ df s_cm[2][kSepTile], s_sn[2][kSepTile];  // the tile's twiddles per bin
+    __shared__ int s_ok[2][kSepTile];
     __shared__ DfTables s_tab;
     const int r = blockIdx.y;
-    const int W1a = wmax[0], W1b = wmax[1], W2a = wmax[2], W2b = wmax[3];
-    const int Sa = slots_of(Ka, W1a, W2a), Sb = slots_of(Kb, W1b, W2b);
-    const int64_t slot = (int64_t)blockIdx.x * kG2Threads + threadIdx.x;
+    const int tid = threadIdx.x;
     const int64_t first = (int64_t)(((uint64_t)r + (uint64_t)n_sub - e0 % (uint64_t)n_sub) %
                                     (uint64_t)n_sub);
     const int64_t cnt_r = first < count ? (count - 1 - first) / n_sub + 1 : 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) counts[r] += cnt_r;
-    if ((int64_t)blockIdx.x * kG2Threads >= (int64_t)Sa * Sb) return;  // block past the grid
-    if (threadIdx.x < 64) s_tab.exp2[threadIdx.x] = df{K.exp2_hi[threadIdx.x], K.exp2_lo[threadIdx.x]};
-    if (threadIdx.x < 33) {
-        s_tab.sn[threadIdx.x] = df{K.sin_hi[threadIdx.x], K.sin_lo[threadIdx.x]};
-        s_tab.cs[threadIdx.x] = df{K.cos_hi[threadIdx.x], K.cos_lo[threadIdx.x]};
-    }  // visible after the first __syncthreads of the tile loop
-    const bool valid = slot < (int64_t)Sa * Sb;
-    const int k1 = valid ? slot_k((int)(slot / Sb), Ka, W1a, W2a) : 0;
-    const int k2 = valid ? slot_k((int)(slot % Sb), Kb, W1b, W2b) : 0;
-    const int a0 = valid ? d0(k1, Ka) : 0x3fffffff, b0 = valid ? d0(k2, Kb) : 0x3fffffff;
-    const int api = valid ? dpi(k1, Ka) : 0x3fffffff, bpi = valid ? dpi(k2, Kb) : 0x3fffffff;
-    const double2 tad = tw[k1], tbd = tw[Ka + k2];
-    const df cma = df_from_double(tad.x), sna = df_from_double(tad.y);
-    const df cmb = df_from_double(tbd.x), snb = df_from_double(tbd.y);
-    double am_re = 0.0, am_im = 0.0, ap_re = 0.0, ap_im = 0.0;
-    for (int64_t base = 0; base < cnt_r; base += kG2Tile) {
-        const int64_t q = base + threadIdx.x;
-        if (q < cnt_r) {
-            const int64_t i = first + q * n_sub;
-            const double nn = n_in[i];
-            const double2 v1 = nS2[2 * i], v2 = nS2[2 * i + 1];
-            s_x1[threadIdx.x] = df_from_double(v1.x);
-            s_y1[threadIdx.x] = df_from_double(v1.y);
-            s_x2[threadIdx.x] = df_from_double(v2.x);
-            s_y2[threadIdx.x] = df_from_double(v2.y);
-            s_c1[threadIdx.x] = df_from_double(fmin(0.0, 2.0 * nn));
-            s_c2[threadIdx.x] = df_from_double(-2.0 * fmax(nn, 0.0));
-            s_inv[threadIdx.x] = df_from_double(1.0 / (1.0 + exp(-2.0 * fabs(nn))));
-            s_n[threadIdx.x] = nn;
-            s_s1[threadIdx.x] = v1;
-            s_s2[threadIdx.x] = v2;
-            s_w[threadIdx.x] = win_in[i];
+    if (blockIdx.x == 0 && tid == 0) counts[r] += cnt_r;
+    const int W1a = wmax[0], W1b = wmax[1], W2a = wmax[2], W2b = wmax[3];
+    const int Sa = slots_of(Ka, W1a, W2a), Sb = slots_of(Kb, W1b, W2b);
+    const int nta = (Sa + kSepTile - 1) / kSepTile, ntb = (Sb + kSepTile - 1) / kSepTile;
+    if ((int)blockIdx.x >= nta * ntb) return;  // past the union window
+    const int sa0 = (blockIdx.x / ntb) * kSepTile, sb0 = (blockIdx.x % ntb) * kSepTile;
+    if (tid < 64) s_tab.exp2[tid] = df{K.exp2_hi[tid], K.exp2_lo[tid]};
+    if (tid < 33) {
+        s_tab.sn[tid] = df{K.sin_hi[tid], K.sin_lo[tid]};
+        s_tab.cs[tid] = df{K.cos_hi[tid], K.cos_lo[tid]};
+    }
+    if (tid < 2 * kSepTile) {
+        const int bin = tid / kSepTile, sl = tid % kSepTile;
+        const int slot = (bin == 0 ? sa0 : sb0) + sl;
+        const bool ok = slot < (bin == 0 ? Sa : Sb);
+        const int kk = !ok ? 0 : (bin == 0 ? slot_k(slot, Ka, W1a, W2a) : slot_k(slot, Kb, W1b, W2b));
+        const double2 t = tw[(bin == 0 ? 0 : Ka) + kk];
+        s_cm[bin][sl] = df_from_double(t.x);
+        s_sn[bin][sl] = df_from_double(t.y);
+        s_ok[bin][sl] = ok;
+    }
+    // this thread's pairs: bin-1 slots sa0 + 2 ty + p, bin-2 slots sb0 + 2 tx + q
+    const int tx = tid & 15, ty = tid >> 4;
+    int k1[2], k2[2];
+    bool v1[2], v2[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int sa = sa0 + 2 * ty + p, sb = sb0 + 2 * tx + p;
+        v1[p] = sa < Sa;
+        v2[p] = sb < Sb;
+        k1[p] = v1[p] ? slot_k(sa, Ka, W1a, W2a) : 0;
+        k2[p] = v2[p] ? slot_k(sb, Kb, W1b, W2b) : 0;
+    }
+    double dP[2][2][2] = {}, dX[2][2][2] = {};  // +P and (matrix-P - +P), (re, im)
+    float4 aP[2][2], aX[2][2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            aP[p][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            aX[p][q] = aP[p][q];
+        }
+
+    int round = 0;
+    for (int64_t base = 0; base < cnt_r; base += kSepRound, ++round) {
+        const int nr = (int)((cnt_r - base) < kSepRound ? (cnt_r - base) : kSepRound);
+        if (tid < kSepRound) {
+            SepTraj st = {};
+            st.flags = 2 | 16;  // 16: no trajectory
+            if (tid < nr) st = sep[first + (base + tid) * n_sub];
+            s_t[tid] = st;
         }
         __syncthreads();
-        const int ntile = (cnt_r - base) < kG2Tile ? (int)(cnt_r - base) : kG2Tile;
-        if (valid) {
-            df pm_re = {0.0f, 0.0f}, pm_im = {0.0f, 0.0f}, pp_re = {0.0f, 0.0f},
-               pp_im = {0.0f, 0.0f};
-            for (int j = 0; j < ntile; ++j) {
-                const Window2 w = s_w[j];
-                const bool in1 = a0 <= w.w1a && b0 <= w.w1b;
-                const bool in2 = api <= w.w2a && bpi <= w.w2b;
-                if (!(in1 || in2)) continue;
-                const df x1 = s_x1[j], y1 = s_y1[j], x2 = s_x2[j], y2 = s_y2[j];
-                const df l = df_add(df_sub(df_mul(cma, x1), df_mul(sna, y1)),
-                                    df_sub(df_mul(cmb, x2), df_mul(snb, y2)));
-                const df ph = df_add(df_add(df_mul(sna, x1), df_mul(cma, y1)),
-                                     df_add(df_mul(snb, x2), df_mul(cmb, y2)));
-                const df c1 = s_c1[j];
-                const df a1 = df_add(l, c1);
-                const df a2 = df_add(df_neg(l), s_c2[j]);
-                const bool big = fabsf(ph.hi) >= 6000.0f ||
-                                 (in1 && (a1.hi >= 80.0f || l.hi >= 80.0f)) ||
-                                 (in2 && a2.hi >= 80.0f);
-                if (big) {
-                    // outside the double-float ranges: this pair in FP64
-                    const double2 v1 = s_s1[j], v2 = s_s2[j];
-                    const double nn = s_n[j];
-                    const double ld = (tad.x * v1.x - tad.y * v1.y) + (tbd.x * v2.x - tbd.y * v2.y);
-                    const double pd = (tad.y * v1.x + tad.x * v1.y) + (tbd.y * v2.x + tbd.x * v2.y);
-                    double sd, cd;
-                    sincos(pd, &sd, &cd);
-                    const double c1d = fmin(0.0, 2.0 * nn), c2d = -2.0 * fmax(nn, 0.0);
-                    double e1d = 0.0, e2d = 0.0;
-                    if (in1) {
-                        e1d = exp(ld + c1d);
-                        const double gp = (c1d == 0.0) ? e1d : exp(ld);
-                        ap_re += gp * cd;
-                        ap_im += gp * sd;
-                    }
-                    if (in2) e2d = exp(-ld + c2d);
-                    const double inv = df_to_double(s_inv[j]);
-                    am_re += (e1d + e2d) * cd * inv;
-                    am_im += (e1d - e2d) * sd * inv;
-                    continue;
-                }
+        // bin vectors of the round on the tile's slots: item = (trajectory,
+        // bin, slot); A and B share l, phi and the sine/cosine
+        for (int it = tid; it < kSepRound * 2 * kSepTile; it += kSepThreads) {
+            const int j = it / (2 * kSepTile);
+            const int bin = (it / kSepTile) & 1;
+            const int sl = it % kSepTile;
+            const SepTraj &st = s_t[j];
+            float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A;
+            if (!(st.flags & 2) && s_ok[bin][sl]) {
+                const df cm1 = s_cm[bin][sl], sn = s_sn[bin][sl];
+                const df x = bin == 0 ? st.x1 : st.x2, y = bin == 0 ? st.y1 : st.y2;
+                const df l = df_sub(df_mul(cm1, x), df_mul(sn, y));
+                const df ph = df_add(df_mul(sn, x), df_mul(cm1, y));
                 df sp, cp;
                 df_sincos_tab(ph, s_tab, K, sp, cp);
-                const df inv = s_inv[j];
-                df e1 = {0.0f, 0.0f}, e2 = {0.0f, 0.0f};
-                if (in1) {
-                    e1 = a1.hi < -87.0f ? df{0.0f, 0.0f} : df_exp_tab(a1, s_tab, K);
-                    const df gp = (c1.hi == 0.0f)
-                                      ? e1
-                                      : (l.hi < -87.0f ? df{0.0f, 0.0f} : df_exp_tab(l, s_tab, K));
-                    pp_re = df_add(pp_re, df_mul(gp, cp));
-                    pp_im = df_add(pp_im, df_mul(gp, sp));
+                // exponents: bin 1: l + M_2 and -l + M'_2 + c2 + log inv;
+                // bin 2: l - M_2 and -l - M'_2
+                const df ea = bin == 0 ? df_add(l, st.o1a) : df_sub(l, st.m2);
+                const df eb = bin == 0 ? df_sub(st.o1b, l) : df_sub(df_neg(l), st.mp2);
+                if (ea.hi >= -87.0f) {
+                    const df e = df_exp_tab(ea, s_tab, K);
+                    const df re = df_mul(e, cp), im = df_mul(e, sp);
+                    A = make_float4(re.hi, re.lo, im.hi, im.lo);
                 }
-                if (in2) e2 = a2.hi < -87.0f ? df{0.0f, 0.0f} : df_exp_tab(a2, s_tab, K);
-                pm_re = df_add(pm_re, df_mul(df_mul(df_add(e1, e2), inv), cp));
-                pm_im = df_add(pm_im, df_mul(df_mul(df_sub(e1, e2), inv), sp));
+                if ((st.flags & 4) && eb.hi >= -87.0f) {
+                    const df e = df_exp_tab(eb, s_tab, K);
+                    const df re = df_mul(e, cp), im = df_mul(e, sp);
+                    B = make_float4(re.hi, re.lo, -im.hi, -im.lo);
+                }
             }
-            am_re += df_to_double(pm_re);
-            am_im += df_to_double(pm_im);
-            ap_re += df_to_double(pp_re);
-            ap_im += df_to_double(pp_im);
+            if (bin == 0) {
+                sA1[j][sl] = A;
+                sB1[j][sl] = B;
+            } else {
+                sA2[j][sl] = A;
+                sB2[j][sl] = B;
+            }
         }
         __syncthreads();
+        for (int j = 0; j < nr; ++j) {
+            const int flags = s_t[j].flags;
+            if (flags & 2) {
+                // per-pair FP64 route (huge phases or exponents)
+                const int64_t i = first + (base + j) * n_sub;
+                const double nn = n_in[i];
+                const double2 a = nS2[2 * i], b = nS2[2 * i + 1];
+                const double c1d = fmin(0.0, 2.0 * nn), c2d = -2.0 * fmax(nn, 0.0);
+                const double inv = 1.0 / (1.0 + exp(-2.0 * fabs(nn)));
+#pragma unroll
+                for (int p = 0; p < 2; ++p)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        if (!(v1[p] && v2[q])) continue;
+                        const double2 ta = tw[k1[p]], tb = tw[Ka + k2[q]];
+                        const double ld = (ta.x * a.x - ta.y * a.y) + (tb.x * b.x - tb.y * b.y);
+                        const double pd = (ta.y * a.x + ta.x * a.y) + (tb.y * b.x + tb.x * b.y);
+                        double sd, cd;
+                        sincos(pd, &sd, &cd);
+                        const double gp = ld >= -745.0 ? exp(ld) : 0.0;
+                        const double e1 = ld + c1d >= -745.0 ? exp(ld + c1d) : 0.0;
+                        const double e2 = -ld + c2d >= -745.0 ? exp(-ld + c2d) : 0.0;
+                        const double mre = (e1 + e2) * cd * inv, mim = (e1 - e2) * sd * inv;
+                        dP[p][q][0] += gp * cd;
+                        dP[p][q][1] += gp * sd;
+                        dX[p][q][0] += mre - gp * cd;
+                        dX[p][q][1] += mim - gp * sd;
+                    }
+                continue;
+            }
+            const float4 A1[2] = {sA1[j][2 * ty], sA1[j][2 * ty + 1]};
+            const float4 A2[2] = {sA2[j][2 * tx], sA2[j][2 * tx + 1]};
+            const bool rA1 = (flags & 8) != 0;
+            const df rAm1 = rA1 ? df{0.f, 0.f} : df_add_f(s_t[j].rA, -1.0f);
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float4 t = dfc_mul(A1[p], A2[q]);
+                    dfc_acc(aP[p][q], t);
+                    // the matrix-P A term is rA t: (rA - 1) t into the difference
+                    if (!rA1) dfc_acc(aX[p][q], dfc_scale(t, rAm1));
+                }
+            if (flags & 4) {
+                const float4 B1[2] = {sB1[j][2 * ty], sB1[j][2 * ty + 1]};
+                const float4 B2[2] = {sB2[j][2 * tx], sB2[j][2 * tx + 1]};
+#pragma unroll
+                for (int p = 0; p < 2; ++p)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) dfc_acc(aX[p][q], dfc_mul(B1[p], B2[q]));
+            }
+        }
+        // renormalise every round, add to the FP64 sums every kSepFlush rounds
+        const bool flush = (round + 1) % kSepFlush == 0 || base + kSepRound >= cnt_r;
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                aP[p][q] = dfc_norm(aP[p][q]);
+                aX[p][q] = dfc_norm(aX[p][q]);
+                if (flush) {
+                    dP[p][q][0] += (double)aP[p][q].x + (double)aP[p][q].y;
+                    dP[p][q][1] += (double)aP[p][q].z + (double)aP[p][q].w;
+                    dX[p][q][0] += (double)aX[p][q].x + (double)aX[p][q].y;
+                    dX[p][q][1] += (double)aX[p][q].z + (double)aX[p][q].w;
+                    aP[p][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    aX[p][q] = aP[p][q];
+                }
+            }
+        __syncthreads();
     }
-    if (valid) {
-        const size_t grid = (size_t)Ka * Kb;
-        const size_t o = (size_t)k1 * Kb + k2;
-        double2 *p0 = acc + (size_t)r * grid + o;
-        double2 *p1 = acc + ((size_t)n_sub + r) * grid + o;
-        const double2 v0 = *p0, v1 = *p1;
-        *p0 = make_double2(v0.x + am_re, v0.y + am_im);
-        *p1 = make_double2(v1.x + ap_re, v1.y + ap_im);
-    }
+    const size_t grid = (size_t)Ka * Kb;
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (!(v1[p] && v2[q])) continue;
+            const size_t o = (size_t)k1[p] * Kb + k2[q];
+            double2 *pm = acc + (size_t)r * grid + o;
+            double2 *pp = acc + ((size_t)n_sub + r) * grid + o;
+            const double2 vm = *pm, vp = *pp;
+            *pm = make_double2(vm.x + (dP[p][q][0] + dX[p][q][0]), vm.y + (dP[p][q][1] + dX[p][q][1]));
+            *pp = make_double2(vp.x + dP[p][q][0], vp.y + dP[p][q][1]);
+        }
 }
 
 __global__ void k_tables2d(int Ka, int Kb, double2 *__restrict__ tw, double2 *__restrict__ wf) {
@@ -444,6 +610,8 @@ int blocks2(const gbs_net *net, int64_t work) {
 
 }  // namespace
 
+size_t sep2_bytes_per_trajectory() { return sizeof(SepTraj); }
+
 int launch_finalize2d(gbs_net *net, int64_t count) {
     if (count <= 0) return GBS_OK;
     GBS_CUDA_TRY(cudaMemsetAsync(net->d_wmax2, 0xff, 4 * sizeof(int), net->stream));
@@ -466,10 +634,18 @@ int launch_gf2d(gbs_net *net, uint64_t e0, int64_t count) {
                                                       net->d_counts2);
     } else {
         static const DfConsts K = make_df_consts();
-        k_gf2d_df<<<grid, kG2Threads, 0, net->stream>>>(net->d_n, net->d_nS2, net->d_win2,
-                                                         net->d_wmax2, count, e0, net->n_sub2,
-                                                         net->Ka, net->Kb, net->d_tw2, K,
-                                                         net->d_acc2, net->d_counts2);
+        // tiles of 32 x 32 slots over the whole grid; tiles past the chunk's
+        // union window return at once
+        const int64_t tiles = (int64_t)((net->Ka + kSepTile - 1) / kSepTile) *
+                              ((net->Kb + kSepTile - 1) / kSepTile);
+        dim3 g2((unsigned)tiles, (unsigned)net->n_sub2);
+        SepTraj *sep = static_cast<SepTraj *>(net->d_sep2);
+        k_sep_prep<<<blocks2(net, count), 256, 0, net->stream>>>(net->d_n, net->d_nS2, count, sep);
+        GBS_LAUNCH_CHECK();
+        k_gf2d_df<<<g2, kSepThreads, 0, net->stream>>>(sep, net->d_n, net->d_nS2, net->d_wmax2,
+                                                        count, e0, net->n_sub2, net->Ka, net->Kb,
+                                                        net->d_tw2, K, net->d_acc2,
+                                                        net->d_counts2);
     }
     GBS_LAUNCH_CHECK();
     return GBS_OK;
