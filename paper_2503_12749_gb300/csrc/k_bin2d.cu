@@ -251,6 +251,9 @@ __global__ void __launch_bounds__(kG2Threads)
 // +P and (matrix-P - +P): the difference needs only the B_1 B_2 term when
 // inv e^{c1} = 1.
 //
+// A trajectory's A (or B) outer product is left out on a tile where its
+// largest factors multiply to below 2^-63, and formed in FP32 where they
+// multiply to below 2^-25.
 // CTA: a tile of 32 x 32 (k_1, k_2) slots of one sub-ensemble, 256 threads of
 // 2 x 2 pairs; rounds of 16 trajectories: the bin vectors of the round on the
 // tile's slots are evaluated into shared memory (double-float table exp and
@@ -334,7 +337,7 @@ __device__ __forceinline__ float4 dfc_norm(const float4 a) {
 
 constexpr int kSepFlush = 4;  // rounds between additions to the FP64 sums
 
-__global__ void __launch_bounds__(kSepThreads)
+__global__ void __launch_bounds__(kSepThreads, 2)
     k_gf2d_df(const SepTraj *__restrict__ sep, const double *__restrict__ n_in,
               const double2 *__restrict__ nS2, const int *__restrict__ wmax, int64_t count,
               uint64_t e0, int n_sub, int Ka, int Kb, const double2 *__restrict__ tw,
@@ -344,6 +347,7 @@ __global__ void __launch_bounds__(kSepThreads)
     __shared__ SepTraj s_t[kSepRound];
     __shared__ df s_cm[2][kSepTile], s_sn[2][kSepTile];  // the tile's twiddles per bin
     __shared__ int s_ok[2][kSepTile];
+    __shared__ float s_mx[kSepRound][2][2];  // largest |factor| on the tile: [j][bin][A, B]
     __shared__ DfTables s_tab;
     const int r = blockIdx.y;
     const int tid = threadIdx.x;
@@ -384,13 +388,16 @@ __global__ void __launch_bounds__(kSepThreads)
         k2[p] = v2[p] ? slot_k(sb, Kb, W1b, W2b) : 0;
     }
     double dP[2][2][2] = {}, dX[2][2][2] = {};  // +P and (matrix-P - +P), (re, im)
-    float4 aP[2][2], aX[2][2];
+    float4 aP[2][2], aX[2][2];  // double-float sums
+    float2 fP[2][2], fX[2][2];  // FP32 sums of the terms below 2^-24
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             aP[p][q] = make_float4(0.f, 0.f, 0.f, 0.f);
             aX[p][q] = aP[p][q];
+            fP[p][q] = make_float2(0.f, 0.f);
+            fX[p][q] = fP[p][q];
         }
 
     int round = 0;
@@ -440,6 +447,15 @@ __global__ void __launch_bounds__(kSepThreads)
                 sA2[j][sl] = A;
                 sB2[j][sl] = B;
             }
+            // the 32 slots of one (trajectory, bin) are one warp's items
+            const unsigned ma = __float_as_uint(fmaxf(fabsf(A.x), fabsf(A.z)));
+            const unsigned mb = __float_as_uint(fmaxf(fabsf(B.x), fabsf(B.z)));
+            const unsigned wa = __reduce_max_sync(0xffffffffu, ma);
+            const unsigned wb = __reduce_max_sync(0xffffffffu, mb);
+            if (sl == 0) {
+                s_mx[j][bin][0] = __uint_as_float(wa);
+                s_mx[j][bin][1] = __uint_as_float(wb);
+            }
         }
         __syncthreads();
         for (int j = 0; j < nr; ++j) {
@@ -472,26 +488,63 @@ __global__ void __launch_bounds__(kSepThreads)
                     }
                 continue;
             }
-            const float4 A1[2] = {sA1[j][2 * ty], sA1[j][2 * ty + 1]};
-            const float4 A2[2] = {sA2[j][2 * tx], sA2[j][2 * tx + 1]};
+            // a term whose largest product on the tile is below 2^-63 (so
+            // every complex product below 2^-62) is left out, as the windows
+            // leave out terms below 2^-60; below 2^-25 (products below
+            // 2^-24) it is formed and summed in FP32, whose rounding
+            // (< 2^-48 per term) is far below the double-float needs of the
+            // large terms
+            const float mA = s_mx[j][0][0] * s_mx[j][1][0];
+            const float mB = (flags & 4) ? s_mx[j][0][1] * s_mx[j][1][1] : 0.0f;
             const bool rA1 = (flags & 8) != 0;
-            const df rAm1 = rA1 ? df{0.f, 0.f} : df_add_f(s_t[j].rA, -1.0f);
-#pragma unroll
-            for (int p = 0; p < 2; ++p)
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const float4 t = dfc_mul(A1[p], A2[q]);
-                    dfc_acc(aP[p][q], t);
-                    // the matrix-P A term is rA t: (rA - 1) t into the difference
-                    if (!rA1) dfc_acc(aX[p][q], dfc_scale(t, rAm1));
-                }
-            if (flags & 4) {
-                const float4 B1[2] = {sB1[j][2 * ty], sB1[j][2 * ty + 1]};
-                const float4 B2[2] = {sB2[j][2 * tx], sB2[j][2 * tx + 1]};
+            if (mA >= 0x1p-63f && mA < 0x1p-25f) {
+                const float4 A1[2] = {sA1[j][2 * ty], sA1[j][2 * ty + 1]};
+                const float4 A2[2] = {sA2[j][2 * tx], sA2[j][2 * tx + 1]};
+                const float rm1 = rA1 ? 0.0f : s_t[j].rA.hi - 1.0f + s_t[j].rA.lo;
 #pragma unroll
                 for (int p = 0; p < 2; ++p)
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) dfc_acc(aX[p][q], dfc_mul(B1[p], B2[q]));
+                    for (int q = 0; q < 2; ++q) {
+                        const float tr = fmaf(A1[p].x, A2[q].x, -A1[p].z * A2[q].z);
+                        const float ti = fmaf(A1[p].x, A2[q].z, A1[p].z * A2[q].x);
+                        fP[p][q].x += tr;
+                        fP[p][q].y += ti;
+                        if (!rA1) {
+                            fX[p][q].x = fmaf(rm1, tr, fX[p][q].x);
+                            fX[p][q].y = fmaf(rm1, ti, fX[p][q].y);
+                        }
+                    }
+            } else if (mA >= 0x1p-25f) {
+                const float4 A1[2] = {sA1[j][2 * ty], sA1[j][2 * ty + 1]};
+                const float4 A2[2] = {sA2[j][2 * tx], sA2[j][2 * tx + 1]};
+                const df rAm1 = rA1 ? df{0.f, 0.f} : df_add_f(s_t[j].rA, -1.0f);
+#pragma unroll
+                for (int p = 0; p < 2; ++p)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const float4 t = dfc_mul(A1[p], A2[q]);
+                        dfc_acc(aP[p][q], t);
+                        // the matrix-P A term is rA t: (rA - 1) t into the difference
+                        if (!rA1) dfc_acc(aX[p][q], dfc_scale(t, rAm1));
+                    }
+            }
+            if (mB >= 0x1p-63f) {
+                const float4 B1[2] = {sB1[j][2 * ty], sB1[j][2 * ty + 1]};
+                const float4 B2[2] = {sB2[j][2 * tx], sB2[j][2 * tx + 1]};
+                if (mB < 0x1p-25f) {
+#pragma unroll
+                    for (int p = 0; p < 2; ++p)
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            fX[p][q].x = fmaf(B1[p].x, B2[q].x, fmaf(-B1[p].z, B2[q].z, fX[p][q].x));
+                            fX[p][q].y = fmaf(B1[p].x, B2[q].z, fmaf(B1[p].z, B2[q].x, fX[p][q].y));
+                        }
+                } else {
+#pragma unroll
+                    for (int p = 0; p < 2; ++p)
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) dfc_acc(aX[p][q], dfc_mul(B1[p], B2[q]));
+                }
             }
         }
         // renormalise every round, add to the FP64 sums every kSepFlush rounds
@@ -503,12 +556,14 @@ __global__ void __launch_bounds__(kSepThreads)
                 aP[p][q] = dfc_norm(aP[p][q]);
                 aX[p][q] = dfc_norm(aX[p][q]);
                 if (flush) {
-                    dP[p][q][0] += (double)aP[p][q].x + (double)aP[p][q].y;
-                    dP[p][q][1] += (double)aP[p][q].z + (double)aP[p][q].w;
-                    dX[p][q][0] += (double)aX[p][q].x + (double)aX[p][q].y;
-                    dX[p][q][1] += (double)aX[p][q].z + (double)aX[p][q].w;
+                    dP[p][q][0] += (double)aP[p][q].x + (double)aP[p][q].y + (double)fP[p][q].x;
+                    dP[p][q][1] += (double)aP[p][q].z + (double)aP[p][q].w + (double)fP[p][q].y;
+                    dX[p][q][0] += (double)aX[p][q].x + (double)aX[p][q].y + (double)fX[p][q].x;
+                    dX[p][q][1] += (double)aX[p][q].z + (double)aX[p][q].w + (double)fX[p][q].y;
                     aP[p][q] = make_float4(0.f, 0.f, 0.f, 0.f);
                     aX[p][q] = aP[p][q];
+                    fP[p][q] = make_float2(0.f, 0.f);
+                    fX[p][q] = fP[p][q];
                 }
             }
         __syncthreads();
