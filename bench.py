@@ -37,7 +37,7 @@ UNIT = "samples/s"
 # (profiles/k_gemm_tc_m1000_bf16x3.md: 1.0845 GB read + 0.0360 GB written);
 # the sample operand it reads grows in proportion to the trajectories.  Valid
 # for the workload and kernel version of that capture only.
-GEMM_TRAFFIC_BYTES_PER_SAMPLE = {("m1000", "bf16x3"): (1.084537e9 + 36.007936e6) / 131072}
+GEMM_TRAFFIC_BYTES_PER_SAMPLE = {("m1000", "bf16x3"): (1.082062e9 + 34.582016e6) / 131072}
 
 
 def _env_int(name, default):
