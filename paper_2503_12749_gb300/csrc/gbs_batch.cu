@@ -7,7 +7,12 @@
 // ONE persistent grouped GEMM covers the tiles of all networks (a tile list
 // ordered by decreasing K so the long tiles start first and the short ones
 // fill the tail), then each network's finalize and generating-function sums.
-// The whole call is captured into a CUDA graph and launched once.  The
+// The whole call is captured into a CUDA graph and launched once; in the
+// graph the per-network launches of a phase (samplers; finalize + generating
+// functions) are independent branches over up to 8 auxiliary streams, so
+// small networks' kernels run side by side instead of one after another
+// (each network's own launches keep their order, so the results do not
+// change).  The
 // grouped GEMM's cluster size is chosen by timing both candidates on the
 // batch's first round (cached per batch).
 #include "gbs_internal.cuh"
@@ -29,6 +34,10 @@ struct gbs_batch {
     size_t desc_cap = 0, tiles_cap = 0;
     int last_rounds = 0;
     int64_t last_tiles = 0;
+    // fork/join streams and events of the captured graph
+    std::vector<cudaStream_t> aux;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
 };
 
 using namespace gbs;
@@ -121,32 +130,51 @@ int round_gemm(gbs_batch *b, const RoundPlan &rp, int r, int cluster) {
     return rc;
 }
 
-int round_front(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *seeds,
-                const uint64_t *first) {
+// Run body(i, net) for every network of the round; with auxiliary streams
+// (graph capture) network i's launches go to branch i mod |aux|, forked from
+// and joined back into the batch stream.
+template <typename Body>
+int per_network(gbs_batch *b, const RoundPlan &rp, int r, bool branches, Body &&body) {
     const int nn = (int)b->nets.size();
-    for (int i = 0; i < nn; ++i) {
-        const int64_t c = rp.count[r][i];
-        if (c <= 0) continue;
-        gbs_net *net = b->nets[i];
-        const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)net->chunk;
-        int rc;
-        if ((rc = launch_sample_bf16(net, seeds[i], e0, c))) return rc;
+    const int nb = branches ? (int)b->aux.size() : 0;
+    if (nb > 0) {
+        GBS_CUDA_TRY(cudaEventRecord(b->fork, b->stream));
+        for (int k = 0; k < nb; ++k) GBS_CUDA_TRY(cudaStreamWaitEvent(b->aux[k], b->fork, 0));
     }
-    return GBS_OK;
+    int rc = GBS_OK;
+    for (int i = 0; i < nn && rc == GBS_OK; ++i) {
+        if (rp.count[r][i] <= 0) continue;
+        gbs_net *net = b->nets[i];
+        cudaStream_t own = net->stream;
+        if (nb > 0) net->stream = b->aux[i % nb];
+        rc = body(i, net);
+        net->stream = own;
+    }
+    if (nb > 0) {
+        for (int k = 0; k < nb; ++k) {
+            GBS_CUDA_TRY(cudaEventRecord(b->join[k], b->aux[k]));
+            GBS_CUDA_TRY(cudaStreamWaitEvent(b->stream, b->join[k], 0));
+        }
+    }
+    return rc;
 }
 
-int round_back(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *first) {
-    const int nn = (int)b->nets.size();
-    for (int i = 0; i < nn; ++i) {
-        const int64_t c = rp.count[r][i];
-        if (c <= 0) continue;
-        gbs_net *net = b->nets[i];
+int round_front(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *seeds,
+                const uint64_t *first, bool branches = false) {
+    return per_network(b, rp, r, branches, [&](int i, gbs_net *net) {
+        const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)net->chunk;
+        return launch_sample_bf16(net, seeds[i], e0, rp.count[r][i]);
+    });
+}
+
+int round_back(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *first,
+               bool branches = false) {
+    return per_network(b, rp, r, branches, [&](int i, gbs_net *net) {
         const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)net->chunk;
         int rc;
-        if ((rc = launch_finalize(net, c))) return rc;
-        if ((rc = launch_gf(net, e0, c))) return rc;
-    }
-    return GBS_OK;
+        if ((rc = launch_finalize(net, rp.count[r][i]))) return rc;
+        return launch_gf(net, e0, rp.count[r][i]);
+    });
 }
 
 // Time both cluster sizes on round 0 (samplers of round 0 run first so the
@@ -206,6 +234,21 @@ int gbs_make_batch(gbs_net_t *nets, int count, gbs_batch_t *out) {
     b->stream = nets[0]->stream;
     b->P = tc_products(nets[0]);
     b->sm_count = nets[0]->sm_count;
+    const int nb = std::min(count, 8);
+    bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < nb; ++k) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) b->aux.push_back(st);
+        ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+        if (ok) b->join.push_back(ev);
+    }
+    if (!ok) {
+        cudaGetLastError();
+        gbs_free_batch(b);
+        return set_error(GBS_ECUDA, "could not create the batch's streams and events");
+    }
     *out = b;
     return GBS_OK;
 }
@@ -246,9 +289,9 @@ int gbs_sample_batch(gbs_batch_t b, const uint64_t *seeds, const uint64_t *first
     cudaGraphExec_t exec = nullptr;
     GBS_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     for (int r = 0; r < rp.rounds && rc == GBS_OK; ++r) {
-        if ((rc = round_front(b, rp, r, seeds, first_sample))) break;
+        if ((rc = round_front(b, rp, r, seeds, first_sample, true))) break;
         if ((rc = round_gemm(b, rp, r, b->cluster))) break;
-        rc = round_back(b, rp, r, first_sample);
+        rc = round_back(b, rp, r, first_sample, true);
     }
     cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
     if (rc) {
@@ -284,6 +327,9 @@ void gbs_free_batch(gbs_batch_t b) {
     cudaStreamSynchronize(b->stream);
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->d_tiles) cudaFree(b->d_tiles);
+    for (cudaStream_t st : b->aux) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
 }
 
