@@ -357,9 +357,26 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
     for (int j = 0; j < N; ++j)
         if (!std::isfinite(r[j]) || r[j] < 0.0)
             return set_error(GBS_EINVAL, "r[%d] = %g: squeezing must be finite and >= 0", j, r[j]);
-    if (!T_device)
-        for (size_t q = 0; q < (size_t)2 * M * N; ++q)
-            if (!std::isfinite(T[q])) return set_error(GBS_EINVAL, "T has a non-finite entry");
+    if (!T_device) {
+        // T in host memory: upload it as given and build the operand layout
+        // (and check for non-finite entries) on the GPU, as for device T
+        double *tmp = nullptr;
+        int rc0;
+        if ((rc0 = dev_alloc(&tmp, (size_t)2 * M * N, "T upload"))) return rc0;
+        if (cudaMemcpy(tmp, T, sizeof(double) * 2 * (size_t)M * N, cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            dev_free(tmp);
+            return set_error(GBS_ECUDA, "upload of T failed");
+        }
+        rc0 = make_network(N, M, tmp, true, r, precision, stream, out);
+        if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+            cudaGetLastError();
+            if (!rc0) rc0 = set_error(GBS_ECUDA, "network set-up failed");
+        }
+        dev_free(tmp);
+        return rc0;
+    }
 
     gbs_net *net = new (std::nothrow) gbs_net();
     if (!net) return set_error(GBS_ENOMEM, "host allocation failed");
@@ -420,17 +437,6 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
         rc = finish_device_T(net, d_bad);
         dev_free(d_bad);
         if (rc) return fail(rc);
-    } else if (precision == GBS_FP64) {
-        std::vector<double> t64((size_t)M * 2 * N);
-        for (int i = 0; i < M; ++i)
-            for (int j = 0; j < N; ++j) {
-                t64[((size_t)i * 2 + 0) * N + j] = T[2 * ((size_t)i * N + j)];
-                t64[((size_t)i * 2 + 1) * N + j] = T[2 * ((size_t)i * N + j) + 1];
-            }
-        if ((rc = dev_alloc(&net->d_T64, t64.size(), "T64"))) return fail(rc);
-        if (cudaMemcpy(net->d_T64, t64.data(), t64.size() * sizeof(double),
-                       cudaMemcpyHostToDevice) != cudaSuccess)
-            return fail(set_error(GBS_ECUDA, "upload of T failed"));
     } else {
         // A = [Re T_i.; Im T_i.] rows interleaved per output mode, T rounded to
         // FP32 and split into BF16 planes T = T0 + T1 + T2, each plane
@@ -458,30 +464,6 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
             if (rc) return fail(rc);
         }
     }
-    if (precision != GBS_FP64 && !T_device) {
-        const size_t plane = (size_t)net->rowsA * net->ldK;
-        std::vector<__nv_bfloat16> a((size_t)net->planesA * plane, __float2bfloat16(0.0f));
-        for (int i = 0; i < M; ++i)
-            for (int c = 0; c < 2; ++c)
-                for (int j = 0; j < N; ++j) {
-                    const float x = (float)T[2 * ((size_t)i * N + j) + c];
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
-                    const float r1 = x - __bfloat162float(h0);
-                    const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
-                    const float r2 = r1 - __bfloat162float(h1);
-                    const __nv_bfloat16 h2 = __float2bfloat16_rn(r2);
-                    const size_t o =
-                        ((size_t)(j >> 5) * net->rowsA + (size_t)(2 * i + c)) * 32 + (j & 31);
-                    a[o] = h0;
-                    a[plane + o] = h1;
-                    a[2 * plane + o] = h2;
-                }
-        if ((rc = dev_alloc(&net->d_A, a.size(), "A planes"))) return fail(rc);
-        if (cudaMemcpy(net->d_A, a.data(), a.size() * sizeof(__nv_bfloat16),
-                       cudaMemcpyHostToDevice) != cudaSuccess)
-            return fail(set_error(GBS_ECUDA, "upload of T planes failed"));
-    }
-
     // chunk workspace
     net->chunk = pick_chunk(net);
     if (precision == GBS_FP64) {
