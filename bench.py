@@ -278,7 +278,7 @@ def gbs_arm(args, wl_def):
         achieved = flops / (gemm_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s",
                 "frac": None, "traffic": None, "kernel": "k_gemm_fp64",
-                "peak_source": "FP64 FMA pipe (see DESIGN.md)"}
+                "peak_source": "FP64 FMA pipe (nominal FP64 rate; no measured FP64 peak)"}
     phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
               for k, v in prof.items()}
     launches = int(sum(v[1] for v in prof.values()))
