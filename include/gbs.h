@@ -109,21 +109,51 @@ int gbs_sample(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, i
                int K1);
 
 /*
- * gbs_make_network_binned -- a network whose output modes are divided into
- * two bins S_1, S_2 for the joint distribution G(m_1, m_2) of Eq.
- * General_GCP with d = 2 and every mode binned ("Higher-dimensional
- * binning").  bin: host, M ints, bin[i] = 0 (S_1) or 1 (S_2), both bins
- * non-empty.  Other arguments as gbs_make_network.  The library stores the
- * rows of each bin contiguously, padded with zero rows to whole 64-mode
- * tiles, so gbs_network_info reports the padded M; gbs_sample still gives
- * the total-count distribution.  Errors as gbs_make_network.
+ * gbs_make_network_binned -- as gbs_make_network, with the output modes split
+ * into d = 2..4 bins S_1 .. S_d for the joint distribution G(m_1, .., m_d)
+ * of Eq. General_GCP with every mode binned ("Higher-dimensional binning").
+ * bin: host, M ints, bin[i] in 0..d-1 (the bin of output mode i; d is the
+ * largest value + 1), every bin non-empty.  Other arguments as
+ * gbs_make_network.  The library stores the rows of each bin contiguously,
+ * padded with zero rows to whole 64-mode tiles, so gbs_network_info reports
+ * the padded M; gbs_sample still gives the total-count distribution.
+ * Errors as gbs_make_network.
  */
 int gbs_make_network_binned(int N, int M, const double *T, const double *r, const int *bin,
                             int precision, void *stream, gbs_net_t *out);
 
 /*
- * gbs_sample_2d -- trajectories first..first+E-1 of a binned network into
- * the two-bin sums: per trajectory the generating function
+ * gbs_sample_nd -- trajectories first..first+E-1 of a binned network into the
+ * binned sums: per trajectory the generating function
+ *   G_mP(z) = cosh(n + sum_b (z_b-1) n_Sb) / cosh(n),
+ *   G_+P(z) = exp(sum_b (z_b-1) n_Sb),
+ * n_Sb = sum over the output modes i of bin b of alpha'_i beta'_i, at
+ * z_b = exp(2 pi i k_b / K_b) (the one-bin form of Eq. c-number-variable
+ * with the exponent summed over the bins), summed per sub-ensemble (e mod
+ * n_sub).  K: host, d powers of two >= 2 with prod K_b <= 2^22; the first
+ * call fixes (n_sub, K) until gbs_reset.  Generating functions in FP64 (FP64
+ * networks) or double-float (BF16 networks), summed in FP64.  Errors: EINVAL
+ * (not a binned network, sizes), ENOMEM, ECUDA.
+ */
+int gbs_sample_nd(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub,
+                  const int *K);
+
+/*
+ * gbs_binned_counts_nd -- the d-dimensional inverse DFT of the binned sums and
+ * their statistics over sub-ensembles:
+ *   P_r(m) = (1/prod K_b) sum_k <G>_r(z) prod_b z_b^{-m_b},
+ * m_b = m_offset[b] .. m_offset[b] + K_b - 1, P = mean_r Re P_r, sigma =
+ * std_r / sqrt(N_R).  m_offset: host, d values.  Host outputs of prod K_b
+ * doubles each, row-major over (m_1, .., m_d); any may be NULL.
+ * Synchronises the stream.  Errors: EINVAL, ECUDA.
+ */
+int gbs_binned_counts_nd(gbs_net_t net, const int64_t *m_offset, double *P_mP, double *sig_mP,
+                         double *P_plusP, double *sig_plusP);
+
+/*
+ * gbs_sample_2d -- gbs_sample_nd for a network of two bins (grid K1 x K2):
+ * trajectories first..first+E-1 into the two-bin sums, per trajectory the
+ * generating function
  *   G_mP(z_1, z_2) = cosh(n + (z_1-1) n_S1 + (z_2-1) n_S2) / cosh(n),
  *   G_+P(z_1, z_2) = exp((z_1-1) n_S1 + (z_2-1) n_S2),
  * n_Sb = sum over the output modes i of bin b of alpha'_i beta'_i, at
@@ -132,14 +162,15 @@ int gbs_make_network_binned(int N, int M, const double *T, const double *r, cons
  * n_sub).  K1, K2: powers of two, K1 K2 <= 2^22; the first call fixes
  * (n_sub, K1, K2) until gbs_reset.  Generating functions in FP64 (FP64
  * networks) or double-float (BF16 networks), summed in FP64.  Errors: EINVAL
- * (not a binned network, sizes), ENOMEM, ECUDA.
+ * (not a network of two bins, sizes), ENOMEM, ECUDA.
  */
 int gbs_sample_2d(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub,
                   int K1, int K2);
 
 /*
- * gbs_binned_counts_2d -- the two-dimensional inverse DFT of the two-bin
- * sums and their statistics over sub-ensembles:
+ * gbs_binned_counts_2d -- gbs_binned_counts_nd for a network of two bins:
+ * the two-dimensional inverse DFT of the two-bin sums and their statistics
+ * over sub-ensembles:
  *   P_r(m_1, m_2) = (1/(K1 K2)) sum_k <G>_r(z) z_1^{-m_1} z_2^{-m_2},
  * m_b = m_b_offset .. m_b_offset + K_b - 1, P = mean_r Re P_r, sigma =
  * std_r / sqrt(N_R).  Host outputs of K1*K2 doubles each, [m_1][m_2]

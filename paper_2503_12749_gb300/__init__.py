@@ -93,6 +93,9 @@ def lib():
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
         L.gbs_debug_occupations.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                             dp]
+        L.gbs_sample_nd.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                    ctypes.c_int, ip]
+        L.gbs_binned_counts_nd.argtypes = [vp, i64p, dp, dp, dp, dp]
         L.gbs_sample_2d.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.gbs_binned_counts_2d.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp]
@@ -134,7 +137,8 @@ def lib():
                      "gbs_binned_counts_noalloc", "gbs_set_gemm_config", "gbs_gemm_config",
                      "gbs_make_batch", "gbs_sample_batch", "gbs_batch_info",
                      "gbs_make_network_device", "gbs_make_network_binned", "gbs_sample_2d",
-                     "gbs_binned_counts_2d", "gbs_histogram", "gbs_moments",
+                     "gbs_binned_counts_2d", "gbs_sample_nd", "gbs_binned_counts_nd",
+                     "gbs_histogram", "gbs_moments",
                      "gbs_debug_occupations", "gbs_mlp_create", "gbs_mlp_param_count",
                      "gbs_mlp_set_params", "gbs_mlp_get_params", "gbs_mlp_get_adam_state",
                      "gbs_mlp_forward", "gbs_mlp_gradients", "gbs_mlp_train",
@@ -210,7 +214,7 @@ def gbs_make_network_device(T_dev_ptr: int, M: int, N: int, r: np.ndarray, preci
 
 def gbs_make_network_binned(T: np.ndarray, r: np.ndarray, bins, precision=GBS_FP64,
                             stream: int = 0) -> Network:
-    """T: complex (M, N); bins: M ints in {0, 1} (the bin of each output mode)."""
+    """T: complex (M, N); bins: M ints in 0..d-1 (the bin of each output mode, d <= 4)."""
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     T = np.ascontiguousarray(T, dtype=np.complex128)
@@ -262,6 +266,23 @@ def gbs_debug_occupations(net: Network, seed: int, e0: int, count: int) -> np.nd
     out = np.zeros(2 * M * count)
     _check(lib().gbs_debug_occupations(net.handle, seed, e0, count, _dptr(out)))
     return out.view(np.complex128).reshape(M, count)
+
+
+def gbs_sample_nd(net: Network, seed: int, first_sample: int, E: int, n_sub: int, K) -> None:
+    """Binned sums of a network of d bins on the grid K (d powers of two)."""
+    KK = (ctypes.c_int * len(K))(*[int(k) for k in K])
+    _check(lib().gbs_sample_nd(net.handle, seed, first_sample, E, n_sub, KK))
+
+
+def gbs_binned_counts_nd(net: Network, K, m_offset=None):
+    """(P_mP, sigma_mP, P_plusP, sigma_plusP), each of shape K, bins m_offset.."""
+    K = [int(k) for k in K]
+    mo = [0] * len(K) if m_offset is None else [int(v) for v in m_offset]
+    MO = (ctypes.c_int64 * len(K))(*mo)
+    size = int(np.prod(K))
+    outs = [np.zeros(size) for _ in range(4)]
+    _check(lib().gbs_binned_counts_nd(net.handle, MO, *[_dptr(o) for o in outs]))
+    return tuple(o.reshape(K) for o in outs)
 
 
 def gbs_sample_2d(net: Network, seed: int, first_sample: int, E: int, n_sub: int, K1: int,

@@ -126,11 +126,14 @@ void release_estimator(gbs_net *net) {
     dev_free(net->d_f2a);
     dev_free(net->d_f2b);
     dev_free(net->d_out2);
+    dev_free(net->d_mo2);
     if (net->d_sep2) cudaFree(net->d_sep2);
     net->d_sep2 = nullptr;
     net->counts2.clear();
     net->est2_fixed = false;
-    net->n_sub2 = net->Ka = net->Kb = 0;
+    net->n_sub2 = 0;
+    net->grid2 = 0;
+    for (int b = 0; b < kMaxBins; ++b) net->Kd[b] = 0;
 }
 
 void release_all(gbs_net *net) {
@@ -230,30 +233,41 @@ int run_chunk_front2d(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) {
     return GBS_OK;
 }
 
-int fix_estimator2d(gbs_net *net, int n_sub, int Ka, int Kb) {
+int fix_estimator2d(gbs_net *net, int n_sub, const int *K) {
+    const int d = net->nbins;
     if (net->est2_fixed) {
-        if (n_sub != net->n_sub2 || Ka != net->Ka || Kb != net->Kb)
+        bool same = n_sub == net->n_sub2;
+        for (int b = 0; b < d; ++b) same = same && K[b] == net->Kd[b];
+        if (!same)
             return set_error(GBS_EINVAL,
-                             "n_sub/K1/K2 (%d, %d, %d) differ from the values fixed by the first "
-                             "call (%d, %d, %d); call gbs_reset first",
-                             n_sub, Ka, Kb, net->n_sub2, net->Ka, net->Kb);
+                             "n_sub and the grid differ from the values fixed by the first call "
+                             "(n_sub %d); call gbs_reset first",
+                             net->n_sub2);
         return GBS_OK;
     }
     if (n_sub < 1 || n_sub > 65535) return set_error(GBS_EINVAL, "n_sub must be in [1, 65535]");
-    if (!is_pow2(Ka) || !is_pow2(Kb) || Ka < 2 || Kb < 2 || (int64_t)Ka * Kb > (1 << 22))
-        return set_error(GBS_EINVAL, "K1, K2 must be powers of two >= 2 with K1 K2 <= 2^22");
+    int64_t grid = 1;
+    int tot = 0;
+    for (int b = 0; b < d; ++b) {
+        if (!is_pow2(K[b]) || K[b] < 2 || K[b] > (1 << 20))
+            return set_error(GBS_EINVAL, "K[%d] = %d: grid sizes must be powers of two >= 2", b, K[b]);
+        grid *= K[b];
+        tot += K[b];
+        if (grid > (1 << 22)) return set_error(GBS_EINVAL, "the grid must have at most 2^22 points");
+    }
     net->n_sub2 = n_sub;
-    net->Ka = Ka;
-    net->Kb = Kb;
-    const size_t accn = (size_t)2 * n_sub * Ka * Kb;
+    for (int b = 0; b < kMaxBins; ++b) net->Kd[b] = b < d ? K[b] : 0;
+    net->grid2 = grid;
+    const size_t accn = (size_t)2 * n_sub * grid;
     int rc;
     if ((rc = dev_alloc(&net->d_acc2, accn, "acc2")) ||
         (rc = dev_alloc(&net->d_counts2, (size_t)n_sub, "counts2")) ||
-        (rc = dev_alloc(&net->d_tw2, (size_t)(Ka + Kb), "tw2")) ||
-        (rc = dev_alloc(&net->d_wf2, (size_t)(Ka + Kb), "wf2")) ||
+        (rc = dev_alloc(&net->d_tw2, (size_t)tot, "tw2")) ||
+        (rc = dev_alloc(&net->d_wf2, (size_t)tot, "wf2")) ||
         (rc = dev_alloc(&net->d_f2a, accn, "fft2a")) ||
         (rc = dev_alloc(&net->d_f2b, accn, "fft2b")) ||
-        (rc = dev_alloc(&net->d_out2, (size_t)4 * Ka * Kb, "out2")))
+        (rc = dev_alloc(&net->d_out2, (size_t)4 * grid, "out2")) ||
+        (rc = dev_alloc(&net->d_mo2, (size_t)kMaxBins, "window offsets")))
         return rc;
     if (net->precision != GBS_FP64) {
         uint8_t *sep = nullptr;
@@ -521,19 +535,26 @@ int gbs_make_network_binned(int N, int M, const double *T, const double *r, cons
     if (N < 1 || M < 2 || N > 65536 || M > 65536)
         return set_error(GBS_EINVAL, "N in [1, 65536] and M in [2, 65536] required");
     if (!T || !r || !bin) return set_error(GBS_EINVAL, "T, r and bin must be non-NULL host pointers");
-    int Mb[2] = {0, 0};
+    int Mb[kMaxBins] = {0, 0, 0, 0};
+    int d = 0;
     for (int i = 0; i < M; ++i) {
-        if (bin[i] != 0 && bin[i] != 1) return set_error(GBS_EINVAL, "bin[%d] = %d: must be 0 or 1", i, bin[i]);
+        if (bin[i] < 0 || bin[i] >= kMaxBins)
+            return set_error(GBS_EINVAL, "bin[%d] = %d: must be in [0, %d]", i, bin[i], kMaxBins - 1);
         ++Mb[bin[i]];
+        d = std::max(d, bin[i] + 1);
     }
-    if (!Mb[0] || !Mb[1]) return set_error(GBS_EINVAL, "both bins need at least one output mode");
-    // rows of bin 1, zero rows to a whole tile, rows of bin 2, zero rows
-    const int pad0 = (Mb[0] + kFp64TileModes - 1) / kFp64TileModes * kFp64TileModes;
-    const int pad1 = (Mb[1] + kFp64TileModes - 1) / kFp64TileModes * kFp64TileModes;
-    const int Mp = pad0 + pad1;
+    if (d < 2) return set_error(GBS_EINVAL, "need at least two bins");
+    for (int b = 0; b < d; ++b)
+        if (!Mb[b]) return set_error(GBS_EINVAL, "bin %d has no output mode", b);
+    // each bin's rows, then zero rows to a whole tile
+    int tiles[kMaxBins + 1] = {0, 0, 0, 0, 0};
+    for (int b = 0; b < d; ++b) tiles[b + 1] = tiles[b] + (Mb[b] + kFp64TileModes - 1) / kFp64TileModes;
+    for (int b = d; b < kMaxBins; ++b) tiles[b + 1] = tiles[b];
+    const int Mp = tiles[d] * kFp64TileModes;
     if (Mp > 65536) return set_error(GBS_EINVAL, "padded output modes exceed 65536");
     std::vector<double> Tp((size_t)2 * Mp * N, 0.0);
-    int next[2] = {0, pad0};
+    int next[kMaxBins];
+    for (int b = 0; b < kMaxBins; ++b) next[b] = tiles[b] * kFp64TileModes;
     for (int i = 0; i < M; ++i) {
         const int row = next[bin[i]]++;
         std::copy(T + (size_t)2 * i * N, T + (size_t)2 * (i + 1) * N, Tp.begin() + (size_t)2 * row * N);
@@ -541,12 +562,12 @@ int gbs_make_network_binned(int N, int M, const double *T, const double *r, cons
     gbs_net_t net = nullptr;
     int rc = make_network(N, Mp, Tp.data(), false, r, precision, stream, &net);
     if (rc) return rc;
-    net->nbins = 2;
-    net->bin_tile0 = pad0 / kFp64TileModes;
+    net->nbins = d;
+    for (int b = 0; b <= kMaxBins; ++b) net->bin_tiles[b] = tiles[b];
     net->M_user = M;
-    if ((rc = dev_alloc(&net->d_nS2, (size_t)2 * net->chunk, "nS2")) ||
-        (rc = dev_alloc(&net->d_win2, (size_t)net->chunk, "windows2")) ||
-        (rc = dev_alloc(&net->d_wmax2, (size_t)4, "window union 2"))) {
+    if ((rc = dev_alloc(&net->d_nS2, (size_t)d * net->chunk, "nS per bin")) ||
+        (rc = dev_alloc(&net->d_win2, (size_t)net->chunk, "windows per bin")) ||
+        (rc = dev_alloc(&net->d_wmax2, (size_t)2 * kMaxBins, "window union per bin"))) {
         gbs_free_network(net);
         return rc;
     }
@@ -904,15 +925,16 @@ int gbs_set_accumulators(gbs_net_t net, int n_sub, int K1, const double *acc,
     return GBS_OK;
 }
 
-int gbs_sample_2d(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub,
-                  int K1, int K2) {
+int gbs_sample_nd(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub,
+                  const int *K) {
     int rc;
     if ((rc = validate_net(net))) return rc;
-    if (net->nbins != 2) return set_error(GBS_EINVAL, "the network has no output bins (gbs_make_network_binned)");
+    if (net->nbins < 2) return set_error(GBS_EINVAL, "the network has no output bins (gbs_make_network_binned)");
+    if (!K) return set_error(GBS_EINVAL, "K is NULL");
     if (E < 0) return set_error(GBS_EINVAL, "E must be >= 0");
     if (first_sample + (uint64_t)E < first_sample)
         return set_error(GBS_EINVAL, "sample index range overflows 64 bits");
-    if ((rc = fix_estimator2d(net, n_sub, K1, K2))) return rc;
+    if ((rc = fix_estimator2d(net, n_sub, K))) return rc;
     for (int64_t done = 0; done < E; done += net->chunk) {
         const int64_t c = std::min<int64_t>(net->chunk, E - done);
         const uint64_t e0 = first_sample + (uint64_t)done;
@@ -929,21 +951,20 @@ int gbs_sample_2d(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E
     return GBS_OK;
 }
 
-int gbs_binned_counts_2d(gbs_net_t net, int64_t m1_offset, int64_t m2_offset, double *P_mP,
-                         double *sig_mP, double *P_plusP, double *sig_plusP) {
+int gbs_binned_counts_nd(gbs_net_t net, const int64_t *m_offset, double *P_mP, double *sig_mP,
+                         double *P_plusP, double *sig_plusP) {
     int rc;
     if ((rc = validate_net(net))) return rc;
-    if (!net->est2_fixed) return set_error(GBS_EINVAL, "no two-bin samples drawn yet");
+    if (!net->est2_fixed) return set_error(GBS_EINVAL, "no binned samples drawn yet");
+    if (!m_offset) return set_error(GBS_EINVAL, "m_offset is NULL");
     for (int q = 0; q < net->n_sub2; ++q)
         if (net->counts2[q] <= 0)
             return set_error(GBS_EINVAL, "sub-ensemble %d has no trajectories", q);
-    int lg = 0;
-    for (int v = net->Ka; v > 1; v >>= 1) ++lg;
-    for (int v = net->Kb; v > 1; v >>= 1) ++lg;
+    int nl = 0;
     prof_mark(net, GBS_PHASE_INVERT, 0, true);
-    if ((rc = launch_invert2d(net, m1_offset, m2_offset, net->d_out2))) return rc;
-    prof_mark(net, GBS_PHASE_INVERT, 3 + lg, false);  // prep, FFT passes, transpose, stats
-    const size_t grid = (size_t)net->Ka * net->Kb;
+    if ((rc = launch_invert2d(net, m_offset, net->d_out2, &nl))) return rc;
+    prof_mark(net, GBS_PHASE_INVERT, nl, false);  // prep, FFT passes, rotations, stats
+    const size_t grid = (size_t)net->grid2;
     double *dst[4] = {P_mP, sig_mP, P_plusP, sig_plusP};
     for (int q = 0; q < 4; ++q)
         if (dst[q])
@@ -951,6 +972,24 @@ int gbs_binned_counts_2d(gbs_net_t net, int64_t m1_offset, int64_t m2_offset, do
                                          cudaMemcpyDeviceToHost, net->stream));
     GBS_CUDA_TRY(cudaStreamSynchronize(net->stream));
     return GBS_OK;
+}
+
+int gbs_sample_2d(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub,
+                  int K1, int K2) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (net->nbins != 2) return set_error(GBS_EINVAL, "the network does not have two output bins");
+    const int K[2] = {K1, K2};
+    return gbs_sample_nd(net, seed, first_sample, E, n_sub, K);
+}
+
+int gbs_binned_counts_2d(gbs_net_t net, int64_t m1_offset, int64_t m2_offset, double *P_mP,
+                         double *sig_mP, double *P_plusP, double *sig_plusP) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (net->nbins != 2) return set_error(GBS_EINVAL, "the network does not have two output bins");
+    const int64_t mo[2] = {m1_offset, m2_offset};
+    return gbs_binned_counts_nd(net, mo, P_mP, sig_mP, P_plusP, sig_plusP);
 }
 
 int gbs_reset(gbs_net_t net) {

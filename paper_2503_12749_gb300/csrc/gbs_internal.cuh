@@ -55,11 +55,13 @@ struct Window {
     int w2;
 };
 
-// Two-bin windows: half-widths in k_1 and k_2 of the e^{L} term around
-// (0, 0) and of the e^{-L} term around (pi, pi); -1 = empty.
-struct Window2 {
-    int w1a, w1b;
-    int w2a, w2b;
+// Binned estimator (2..kMaxBins output bins): per dimension the half-width
+// in k of the e^{L} term's window around 0 (w1) and of the e^{-L} term's
+// window around pi (w2); -1 = empty.
+constexpr int kMaxBins = 4;
+struct WindowD {
+    int w1[kMaxBins];
+    int w2[kMaxBins];
 };
 
 // ---------------------------------------------------------------------------
@@ -150,25 +152,28 @@ struct gbs_net {
 
     gbs::Profiler prof;
 
-    // Two output bins (gbs_make_network_binned): the output modes of bin 1
-    // and of bin 2 are stored as consecutive rows, each bin padded with zero
-    // rows to whole 64-mode tiles; tiles [0, bin_tile0) are bin 1.
+    // Output bins (gbs_make_network_binned, 2..kMaxBins): the output modes
+    // of each bin are stored as consecutive rows, each bin padded with zero
+    // rows to whole 64-mode tiles; bin b is tiles [bin_tiles[b], bin_tiles[b+1]).
     int nbins = 1;
-    int bin_tile0 = 0;
+    int bin_tiles[gbs::kMaxBins + 1] = {};
     int M_user = 0;  // output modes as given (M includes the padding rows)
-    // two-bin estimator state (gbs_sample_2d)
-    double2 *d_nS2 = nullptr;       // [chunk][2]: n_S1, n_S2
-    gbs::Window2 *d_win2 = nullptr; // [chunk]
-    int *d_wmax2 = nullptr;         // [4]: union of the chunk's windows
+    // binned estimator state (gbs_sample_nd)
+    double2 *d_nS2 = nullptr;       // [chunk][nbins]: n_Sb
+    gbs::WindowD *d_win2 = nullptr; // [chunk]
+    int *d_wmax2 = nullptr;         // [2 kMaxBins]: union of the chunk's windows (w1, then w2)
     bool est2_fixed = false;
-    int n_sub2 = 0, Ka = 0, Kb = 0;
-    double2 *d_acc2 = nullptr;      // [2][n_sub2][Ka][Kb]
+    int n_sub2 = 0;
+    int Kd[gbs::kMaxBins] = {};     // points per dimension
+    int64_t grid2 = 0;              // prod Kd
+    double2 *d_acc2 = nullptr;      // [2][n_sub2][grid2]
     int64_t *d_counts2 = nullptr;   // [n_sub2]
     std::vector<int64_t> counts2;
-    double2 *d_tw2 = nullptr;       // [Ka + Kb]: (cos theta - 1, sin theta) of each dimension
-    double2 *d_wf2 = nullptr;       // [Ka + Kb]: e^{-i theta}
-    double2 *d_f2a = nullptr, *d_f2b = nullptr;  // [2][n_sub2][Ka * Kb] FFT work
-    double *d_out2 = nullptr;       // [4][Ka * Kb]
+    double2 *d_tw2 = nullptr;       // [sum Kd]: (cos theta - 1, sin theta) of each dimension
+    double2 *d_wf2 = nullptr;       // [sum Kd]: e^{-i theta}
+    double2 *d_f2a = nullptr, *d_f2b = nullptr;  // [2][n_sub2][grid2] FFT work
+    double *d_out2 = nullptr;       // [4][grid2]
+    int64_t *d_mo2 = nullptr;       // [kMaxBins] DFT window offsets
     void *d_sep2 = nullptr;         // [chunk] per-trajectory constants (BF16 networks)
 };
 
@@ -260,14 +265,14 @@ int launch_moments(const MomentSpec &sp, bool fp64, const void *occ, int64_t occ
 int launch_moment_stats(const MomentSpec &sp, bool fp64, const double *acc, const int64_t *cnt,
                         double *out, cudaStream_t stream, int sm_count);
 
-// Two-bin estimator (k_bin2d.cu): finalize (per-bin n_S and windows),
-// generating functions on the (Ka x Kb) grid, and the two-dimensional
-// inversion into out_dev[4][Ka * Kb].
+// Binned estimator (k_bin2d.cu): finalize (per-bin n_S and windows),
+// generating functions on the K_1 x .. x K_d grid, and the d-dimensional
+// inversion into out_dev[4][grid2] (*launches: kernels launched).
 int launch_finalize2d(gbs_net *net, int64_t count);
 int launch_gf2d(gbs_net *net, uint64_t e0, int64_t count);
 size_t sep2_bytes_per_trajectory();
 int launch_tables2d(gbs_net *net);
-int launch_invert2d(gbs_net *net, int64_t m1_off, int64_t m2_off, double *out_dev);
+int launch_invert2d(gbs_net *net, const int64_t *m_off, double *out_dev, int *launches);
 
 // Fix (or check) a network's estimator shape, allocating its sums on first use.
 int fix_estimator(gbs_net *net, int n_sub, int K1);

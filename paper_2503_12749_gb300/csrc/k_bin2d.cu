@@ -1,28 +1,29 @@
-// Two-dimensional binning ("Higher-dimensional binning", Eq. General_GCP with
-// d = 2 and every output mode in one of the bins S_1, S_2): the joint
-// distribution G(m_1, m_2) of the counts in the two bins.
+// Binning into d = 2..4 output bins ("Higher-dimensional binning", Eq.
+// General_GCP with every output mode in one of the bins S_1 .. S_d): the
+// joint distribution G(m_1, .., m_d) of the counts in the bins.
 //
 // Per trajectory, with n = alpha.beta and n_Sb = sum_{i in S_b} alpha'_i
 // beta'_i, the bin-total projectors have the generating function
-//   G_mP(z_1, z_2) = cosh(n + L) / cosh(n),   G_+P(z_1, z_2) = e^{L},
-//   L = (z_1 - 1) n_S1 + (z_2 - 1) n_S2,
+//   G_mP(z) = cosh(n + L) / cosh(n),   G_+P(z) = e^{L},
+//   L = sum_b (z_b - 1) n_Sb,
 // the one-bin form of Eq. c-number-variable with the exponent summed over
-// the bins (the parity weight depends on m_1 + m_2).  The GEMM is the
+// the bins (the parity weight depends on the total count).  The GEMM is the
 // one-bin GEMM unchanged: the rows of each bin are contiguous and padded to
-// whole 64-mode tiles, so its per-tile partials sum to n_S1 and n_S2.
+// whole 64-mode tiles, so its per-tile partials sum to every n_Sb.
 //
-// Evaluated on a (Ka x Kb) grid of z_b = e^{i theta_b} in FP64 (FP64
+// Evaluated on a K_1 x .. x K_d grid of z_b = e^{i theta_b} in FP64 (FP64
 // networks) or in double-float on the FP32 pipes (BF16 networks, the
 // one-bin kernel's table-driven exp and sin/cos, FP64 for arguments beyond
-// their ranges); with
-// L = l + i phi the same stable form as the one-bin kernels,
+// their ranges); with L = l + i phi the same stable form as the one-bin
+// kernels,
 //   G_mP = [e^{l + c1} e^{i phi} + e^{-l + c2} e^{-i phi}] / (1 + e^{-2|n|}),
 // c1 = min(0, 2n), c2 = -2 max(n, 0).  Terms below 2^-60 are skipped with
-// per-dimension windows: for the e^{L} term the window in theta_1 uses the
-// bound l_1(theta_1) <= -c x_1 + sqrt(2c) |y_1| (c = 1 - cos theta_1) with the
-// threshold raised by the largest value of the theta_2 part, and likewise in
-// theta_2 and for the e^{-L} term around (pi, pi).  Sub-ensemble sums are
-// inverted by a two-dimensional FFT (rows, transpose, rows).
+// per-dimension windows: for the e^{L} term the window in theta_b uses the
+// bound l_b(theta_b) <= -c x_b + sqrt(2c) |y_b| (c = 1 - cos theta_b) with
+// the threshold raised by the largest values of the other bins' parts, and
+// likewise for the e^{-L} term around (pi, .., pi).  Sub-ensemble sums are
+// inverted by a d-dimensional FFT: per dimension, FFTs along the innermost
+// one and a rotation that moves it outermost.
 #include "gbs_internal.cuh"
 #include "dfloat.cuh"
 
@@ -34,6 +35,14 @@ namespace {
 constexpr double kTwoPi2 = 6.283185307179586476925286766559;
 constexpr int kG2Threads = 128;
 constexpr int kG2Tile = 128;
+
+// Shape of one launch over the grid (passed by value).
+struct GridD {
+    int d;                   // bins
+    int K[kMaxBins];         // points per dimension
+    int Koff[kMaxBins];      // offsets of each dimension's tables
+    int tile[kMaxBins + 1];  // bin b = GEMM tiles [tile[b], tile[b + 1])
+};
 
 // max over c in [0, 2] of -c x + sqrt(2c) |y|
 __device__ __forceinline__ double max_term1(double x, double y) {
@@ -82,45 +91,59 @@ __device__ __forceinline__ int win_term2(double x, double y, double c, double T,
     return u < 0.0 ? -1 : half_width2(u * u, K);
 }
 
-__global__ void k_finalize2d(const double2 *__restrict__ part, int mtiles, int tile0, int64_t ld,
-                             const double *__restrict__ n, int64_t count, int Ka, int Kb,
-                             double2 *__restrict__ nS2, Window2 *__restrict__ win,
+__global__ void k_finalize2d(const double2 *__restrict__ part, const GridD g, int64_t ld,
+                             const double *__restrict__ n, int64_t count,
+                             double2 *__restrict__ nSd, WindowD *__restrict__ win,
                              int *__restrict__ wmax) {
-    int m[4] = {-1, -1, -1, -1};
+    int m[2 * kMaxBins];
+#pragma unroll
+    for (int q = 0; q < 2 * kMaxBins; ++q) m[q] = -1;
     const double T = kSkipLog;
+    const int d = g.d;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double x1 = 0.0, y1 = 0.0, x2 = 0.0, y2 = 0.0;
-        for (int t = 0; t < tile0; ++t) {
-            const double2 p = part[(size_t)t * ld + i];
-            x1 += p.x;
-            y1 += p.y;
+        double x[kMaxBins] = {}, y[kMaxBins] = {}, M1[kMaxBins] = {}, M2[kMaxBins] = {};
+        double s1 = 0.0, s2 = 0.0;
+#pragma unroll
+        for (int b = 0; b < kMaxBins; ++b) {
+            if (b >= d) continue;
+            for (int t = g.tile[b]; t < g.tile[b + 1]; ++t) {
+                const double2 p = part[(size_t)t * ld + i];
+                x[b] += p.x;
+                y[b] += p.y;
+            }
+            nSd[(size_t)d * i + b] = make_double2(x[b], y[b]);
+            M1[b] = max_term1(x[b], y[b]);
+            M2[b] = max_term2(x[b], y[b]);
+            s1 += M1[b];
+            s2 += M2[b];
         }
-        for (int t = tile0; t < mtiles; ++t) {
-            const double2 p = part[(size_t)t * ld + i];
-            x2 += p.x;
-            y2 += p.y;
-        }
-        nS2[2 * i] = make_double2(x1, y1);
-        nS2[2 * i + 1] = make_double2(x2, y2);
         const double c2 = -2.0 * fmax(n[i], 0.0);
-        Window2 w;
-        w.w1a = win_term1(x1, y1, T + max_term1(x2, y2), Ka);
-        w.w1b = win_term1(x2, y2, T + max_term1(x1, y1), Kb);
-        w.w2a = win_term2(x1, y1, c2 + max_term2(x2, y2), T, Ka);
-        w.w2b = win_term2(x2, y2, c2 + max_term2(x1, y1), T, Kb);
-        if (w.w2a < 0 || w.w2b < 0) w.w2a = w.w2b = -1;
+        WindowD w;
+        bool none2 = false;
+#pragma unroll
+        for (int b = 0; b < kMaxBins; ++b) {
+            w.w1[b] = -1;
+            w.w2[b] = -1;
+            if (b < d) {
+                w.w1[b] = win_term1(x[b], y[b], T + (s1 - M1[b]), g.K[b]);
+                w.w2[b] = win_term2(x[b], y[b], c2 + (s2 - M2[b]), T, g.K[b]);
+                none2 = none2 || w.w2[b] < 0;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kMaxBins; ++b) {
+            if (none2) w.w2[b] = -1;
+            m[b] = max(m[b], w.w1[b]);
+            m[kMaxBins + b] = max(m[kMaxBins + b], w.w2[b]);
+        }
         win[i] = w;
-        m[0] = max(m[0], w.w1a);
-        m[1] = max(m[1], w.w1b);
-        m[2] = max(m[2], w.w2a);
-        m[3] = max(m[3], w.w2b);
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) m[q] = __reduce_max_sync(0xffffffffu, m[q]);
+    for (int q = 0; q < 2 * kMaxBins; ++q) m[q] = __reduce_max_sync(0xffffffffu, m[q]);
     if ((threadIdx.x & 31) == 0)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) atomicMax(&wmax[q], m[q]);
+        for (int q = 0; q < 2 * kMaxBins; ++q) atomicMax(&wmax[q], m[q]);
 }
 
 __device__ __forceinline__ int slots_of(int K, int W1, int W2) {
@@ -150,43 +173,87 @@ __device__ __forceinline__ int dpi(int k, int K) {
     return d < 0 ? -d : d;
 }
 
-// One thread per (k_1, k_2) slot of the union window, one block row per
-// sub-ensemble r; each thread adds its sub-ensemble's trajectories in
+// Slots of the union window per dimension.
+struct Slots {
+    int S[kMaxBins];
+    int W1[kMaxBins], W2[kMaxBins];
+};
+
+__device__ __forceinline__ Slots slots_of_grid(const GridD &g, const int *wmax) {
+    Slots s;
+#pragma unroll
+    for (int b = 0; b < kMaxBins; ++b) {
+        s.W1[b] = wmax[b];
+        s.W2[b] = wmax[kMaxBins + b];
+        s.S[b] = b < g.d ? slots_of(g.K[b], s.W1[b], s.W2[b]) : 1;
+    }
+    return s;
+}
+
+// Dimensions [0, nb) of the flattened slot index idx (last of them fastest)
+// -> k_b; returns the row-major grid index over those dimensions.
+__device__ __forceinline__ int64_t slot_ks(const GridD &g, const Slots &s, int nb, int64_t idx,
+                                           int (&k)[kMaxBins]) {
+    int64_t rem = idx;
+#pragma unroll
+    for (int b = kMaxBins - 1; b >= 0; --b) {
+        if (b >= nb) continue;
+        const int sb = (int)(rem % s.S[b]);
+        rem /= s.S[b];
+        k[b] = slot_k(sb, g.K[b], s.W1[b], s.W2[b]);
+    }
+    int64_t o = 0;
+#pragma unroll
+    for (int b = 0; b < kMaxBins; ++b)
+        if (b < nb) o = o * g.K[b] + k[b];
+    return o;
+}
+
+// One thread per slot of the union window (FP64 networks), one block row
+// per sub-ensemble r; each thread adds its sub-ensemble's trajectories in
 // increasing order.
 __global__ void __launch_bounds__(kG2Threads)
-    k_gf2d(const double *__restrict__ n_in, const double2 *__restrict__ nS2,
-           const Window2 *__restrict__ win_in, const int *__restrict__ wmax, int64_t count,
-           uint64_t e0, int n_sub, int Ka, int Kb, const double2 *__restrict__ tw,
+    k_gf2d(const double *__restrict__ n_in, const double2 *__restrict__ nSd,
+           const WindowD *__restrict__ win_in, const int *__restrict__ wmax, int64_t count,
+           uint64_t e0, int n_sub, const GridD g, const double2 *__restrict__ tw,
            double2 *__restrict__ acc, int64_t *__restrict__ counts) {
-    __shared__ double s_x1[kG2Tile], s_y1[kG2Tile], s_x2[kG2Tile], s_y2[kG2Tile];
+    __shared__ double s_x[kG2Tile][kMaxBins], s_y[kG2Tile][kMaxBins];
     __shared__ double s_c1[kG2Tile], s_c2[kG2Tile], s_inv[kG2Tile];
-    __shared__ Window2 s_w[kG2Tile];
+    __shared__ WindowD s_w[kG2Tile];
+    const int d = g.d;
     const int r = blockIdx.y;
-    const int W1a = wmax[0], W1b = wmax[1], W2a = wmax[2], W2b = wmax[3];
-    const int Sa = slots_of(Ka, W1a, W2a), Sb = slots_of(Kb, W1b, W2b);
+    const Slots sl = slots_of_grid(g, wmax);
+    int64_t total = 1;
+    for (int b = 0; b < d; ++b) total *= sl.S[b];
     const int64_t slot = (int64_t)blockIdx.x * kG2Threads + threadIdx.x;
     const int64_t first = (int64_t)(((uint64_t)r + (uint64_t)n_sub - e0 % (uint64_t)n_sub) %
                                     (uint64_t)n_sub);
     const int64_t cnt_r = first < count ? (count - 1 - first) / n_sub + 1 : 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) counts[r] += cnt_r;
-    if ((int64_t)blockIdx.x * kG2Threads >= (int64_t)Sa * Sb) return;  // block past the grid
-    const bool valid = slot < (int64_t)Sa * Sb;
-    const int k1 = valid ? slot_k((int)(slot / Sb), Ka, W1a, W2a) : 0;
-    const int k2 = valid ? slot_k((int)(slot % Sb), Kb, W1b, W2b) : 0;
-    const int a0 = valid ? d0(k1, Ka) : 0x3fffffff, b0 = valid ? d0(k2, Kb) : 0x3fffffff;
-    const int api = valid ? dpi(k1, Ka) : 0x3fffffff, bpi = valid ? dpi(k2, Kb) : 0x3fffffff;
-    const double2 ta = tw[k1], tb = tw[Ka + k2];
+    if ((int64_t)blockIdx.x * kG2Threads >= total) return;  // block past the grid
+    const bool valid = slot < total;
+    int k[kMaxBins] = {0, 0, 0, 0}, a0[kMaxBins], api[kMaxBins];
+    int64_t o = 0;
+    if (valid) o = slot_ks(g, sl, d, slot, k);
+    double2 t[kMaxBins];
+#pragma unroll
+    for (int b = 0; b < kMaxBins; ++b) {
+        a0[b] = (valid && b < d) ? d0(k[b], g.K[b]) : 0;
+        api[b] = (valid && b < d) ? dpi(k[b], g.K[b]) : 0;
+        t[b] = b < d ? tw[g.Koff[b] + k[b]] : make_double2(0.0, 0.0);
+    }
     double am_re = 0.0, am_im = 0.0, ap_re = 0.0, ap_im = 0.0;
     for (int64_t base = 0; base < cnt_r; base += kG2Tile) {
         const int64_t q = base + threadIdx.x;
         if (q < cnt_r) {
             const int64_t i = first + q * n_sub;
             const double nn = n_in[i];
-            const double2 s1 = nS2[2 * i], s2 = nS2[2 * i + 1];
-            s_x1[threadIdx.x] = s1.x;
-            s_y1[threadIdx.x] = s1.y;
-            s_x2[threadIdx.x] = s2.x;
-            s_y2[threadIdx.x] = s2.y;
+#pragma unroll
+            for (int b = 0; b < kMaxBins; ++b) {
+                const double2 v = b < d ? nSd[(size_t)d * i + b] : make_double2(0.0, 0.0);
+                s_x[threadIdx.x][b] = v.x;
+                s_y[threadIdx.x][b] = v.y;
+            }
             s_c1[threadIdx.x] = fmin(0.0, 2.0 * nn);
             s_c2[threadIdx.x] = -2.0 * fmax(nn, 0.0);
             s_inv[threadIdx.x] = 1.0 / (1.0 + exp(-2.0 * fabs(nn)));
@@ -196,13 +263,22 @@ __global__ void __launch_bounds__(kG2Threads)
         const int ntile = (cnt_r - base) < kG2Tile ? (int)(cnt_r - base) : kG2Tile;
         if (valid) {
             for (int j = 0; j < ntile; ++j) {
-                const Window2 w = s_w[j];
-                const bool in1 = a0 <= w.w1a && b0 <= w.w1b;
-                const bool in2 = api <= w.w2a && bpi <= w.w2b;
+                const WindowD &w = s_w[j];
+                bool in1 = true, in2 = true;
+#pragma unroll
+                for (int b = 0; b < kMaxBins; ++b)
+                    if (b < d) {
+                        in1 = in1 && a0[b] <= w.w1[b];
+                        in2 = in2 && api[b] <= w.w2[b];
+                    }
                 if (!(in1 || in2)) continue;
-                const double x1 = s_x1[j], y1 = s_y1[j], x2 = s_x2[j], y2 = s_y2[j];
-                const double l = (ta.x * x1 - ta.y * y1) + (tb.x * x2 - tb.y * y2);
-                const double ph = (ta.y * x1 + ta.x * y1) + (tb.y * x2 + tb.x * y2);
+                double l = 0.0, ph = 0.0;
+#pragma unroll
+                for (int b = 0; b < kMaxBins; ++b)
+                    if (b < d) {
+                        l += t[b].x * s_x[j][b] - t[b].y * s_y[j][b];
+                        ph += t[b].y * s_x[j][b] + t[b].x * s_y[j][b];
+                    }
                 double sp, cp;
                 sincos(ph, &sp, &cp);
                 double e1 = 0.0, e2 = 0.0;
@@ -222,8 +298,8 @@ __global__ void __launch_bounds__(kG2Threads)
         __syncthreads();
     }
     if (valid) {
-        const size_t grid = (size_t)Ka * Kb;
-        const size_t o = (size_t)k1 * Kb + k2;
+        int64_t grid = 1;
+        for (int b = 0; b < d; ++b) grid *= g.K[b];
         double2 *p0 = acc + (size_t)r * grid + o;
         double2 *p1 = acc + ((size_t)n_sub + r) * grid + o;
         const double2 v0 = *p0, v1 = *p1;
@@ -233,70 +309,85 @@ __global__ void __launch_bounds__(kG2Threads)
 }
 
 // The same sums in double-float arithmetic (BF16 networks), from the
-// factorisation of the exponent by bins.  With l_b + i phi_b = (z_b - 1) n_Sb,
-//   e^{L}  = [e^{l_1 + M_2} e^{i phi_1}] [e^{l_2 - M_2} e^{i phi_2}],
-//   inv e^{-L + c2} = [e^{-l_1 + M'_2 + c2 + log inv} e^{-i phi_1}]
-//                     [e^{-l_2 - M'_2} e^{-i phi_2}],
-// M_b = max over theta of l_b (max_term1), M'_b = max of -l_b (max_term2),
-// inv = 1 / (1 + e^{-2|n|}): every bin-2 factor is at most 1 and every
-// bin-1 factor at most e^{M_1 + M_2} (or e^{M'_1 + M'_2 + c2 + log inv}).
-// A trajectory is therefore a pair of vectors per bin on the CTA's slots, and
-// its terms on the CTA's (k_1, k_2) tile are outer products:
+// factorisation of the exponent by bins.  Bins 1..d-1 form the first factor
+// (their exponents summed, their slots flattened) and bin d the second; with
+// l_A + i phi_A = sum_{b<d} (z_b - 1) n_Sb and l_B + i phi_B = (z_d - 1) n_Sd,
+//   e^{L}  = [e^{l_A + M_B} e^{i phi_A}] [e^{l_B - M_B} e^{i phi_B}],
+//   inv e^{-L + c2} = [e^{-l_A + M'_B + c2 + log inv} e^{-i phi_A}]
+//                     [e^{-l_B - M'_B} e^{-i phi_B}],
+// M_B = max over theta of l_B (max_term1), M'_B = max of -l_B (max_term2),
+// inv = 1 / (1 + e^{-2|n|}): every second factor is at most 1 and every
+// first factor at most e^{M_A + M_B} (or e^{M'_A + M'_B + c2 + log inv}), M_A
+// and M'_A the sums of the first bins' maxima.  A trajectory is therefore a
+// pair of vectors per factor on a CTA's slots, and its terms on the CTA's
+// tile are outer products:
 //   G_+P = A_1 A_2,   G_mP = inv e^{c1} A_1 A_2 + B_1 B_2.
-// Per pair this is one or two double-float complex products instead of an
-// exponential and a sine/cosine.  Factors below FP32's normal range (e^-87)
-// are flushed to zero: with the exponents capped at 40 (else the trajectory
-// takes the per-pair FP64 route), a flushed factor drops only terms below
-// e^{40 - 87} < 2^-60, the threshold of the windows.  The sums are kept as
-// +P and (matrix-P - +P): the difference needs only the B_1 B_2 term when
-// inv e^{c1} = 1.
+// Per grid point this is one or two double-float complex products instead
+// of an exponential and a sine/cosine.  Factors below FP32's normal range
+// (e^-87) are flushed to zero: with the exponents capped at 40 (else the
+// trajectory takes the per-point FP64 route), a flushed factor drops only
+// terms below e^{40 - 87} < 2^-60, the threshold of the windows.  The sums
+// are kept as +P and (matrix-P - +P): the difference needs only the B_1 B_2
+// term when inv e^{c1} = 1.  A trajectory's A (or B) outer product is left
+// out on a tile where its largest factors multiply to below 2^-63, and
+// formed in FP32 where they multiply to below 2^-25.
 //
-// A trajectory's A (or B) outer product is left out on a tile where its
-// largest factors multiply to below 2^-63, and formed in FP32 where they
-// multiply to below 2^-25.
-// CTA: a tile of 32 x 32 (k_1, k_2) slots of one sub-ensemble, 256 threads of
-// 2 x 2 pairs; rounds of 16 trajectories: the bin vectors of the round on the
-// tile's slots are evaluated into shared memory (double-float table exp and
-// sin/cos), then each thread accumulates its pairs in double-float and adds
-// the round to FP64 accumulators, trajectories in increasing order.
-constexpr int kSepTile = 32;     // slots per bin per CTA
-constexpr int kSepThreads = 256; // 16 x 16 threads, 2 x 2 pairs each
+// CTA: a tile of 32 x 32 (first-factor slot, last-bin slot) of one
+// sub-ensemble, 256 threads of 2 x 2 points; rounds of 16 trajectories: the
+// factor vectors of the round on the tile's slots are evaluated into shared
+// memory (double-float table exp and sin/cos), then each thread accumulates
+// its points in double-float, renormalised every round and added to FP64
+// accumulators every 4 rounds, trajectories in increasing order.
+constexpr int kSepTile = 32;     // slots per factor per CTA
+constexpr int kSepThreads = 256; // 16 x 16 threads, 2 x 2 points each
 constexpr int kSepRound = 16;    // trajectories per round
 
 // Per-trajectory constants of the factorised evaluation (one pass per chunk):
 // the bins' n_S in double-float and the exponent offsets.
 struct __align__(16) SepTraj {
-    df x1, y1, x2, y2;  // n_S1, n_S2
-    df m2, mp2;         // M_2, M'_2 (offsets of the bin-2 factors)
-    df o1a, o1b;        // offsets of the bin-1 factors: +M_2, +M'_2 + c2 + log inv
+    df x[kMaxBins], y[kMaxBins];  // n_Sb
+    df m2, mp2;         // M_B, M'_B (offsets of the second factors)
+    df o1a, o1b;        // offsets of the first factors: +M_B, +M'_B + c2 + log inv
     df rA;              // inv e^{c1} (<= 1)
-    int flags;          // 2: per-pair FP64 route, 4: B term used, 8: rA == 1
+    int flags;          // 2: per-point FP64 route, 4: B term used, 8: rA == 1
     int pad;
 };
 
-__global__ void k_sep_prep(const double *__restrict__ n_in, const double2 *__restrict__ nS2,
-                           int64_t count, SepTraj *__restrict__ out) {
+__global__ void k_sep_prep(const double *__restrict__ n_in, const double2 *__restrict__ nSd,
+                           int64_t count, int d, SepTraj *__restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double nn = n_in[i];
-        const double2 a = nS2[2 * i], b = nS2[2 * i + 1];
-        const double M1 = max_term1(a.x, a.y), M2 = max_term1(b.x, b.y);
-        const double P1 = max_term2(a.x, a.y), P2 = max_term2(b.x, b.y);
+        SepTraj st;
+        double MA = 0.0, PA = 0.0, phA = 0.0, MB = 0.0, PB = 0.0, phB = 0.0;
+        bool bad = false;
+#pragma unroll
+        for (int b = 0; b < kMaxBins; ++b) {
+            const double2 v = b < d ? nSd[(size_t)d * i + b] : make_double2(0.0, 0.0);
+            st.x[b] = df_from_double(v.x);
+            st.y[b] = df_from_double(v.y);
+            if (b >= d) continue;
+            const double m1 = max_term1(v.x, v.y), m2 = max_term2(v.x, v.y);
+            const double ph = fabs(v.x) + 2.0 * fabs(v.y);
+            bad = bad || !(m1 >= 0.0);
+            if (b < d - 1) {
+                MA += m1;
+                PA += m2;
+                phA += ph;
+            } else {
+                MB = m1;
+                PB = m2;
+                phB = ph;
+            }
+        }
         const double c1 = fmin(0.0, 2.0 * nn), c2 = -2.0 * fmax(nn, 0.0);
         const double linv = -log1p(exp(-2.0 * fabs(nn)));
-        const double lwB = P1 + P2 + c2 + linv;
-        const bool big = fabs(a.x) + 2.0 * fabs(a.y) >= 6000.0 ||
-                         fabs(b.x) + 2.0 * fabs(b.y) >= 6000.0 || M1 + M2 > 40.0 || lwB > 40.0 ||
-                         !(M1 + M2 >= 0.0);
-        SepTraj st;
-        st.x1 = df_from_double(a.x);
-        st.y1 = df_from_double(a.y);
-        st.x2 = df_from_double(b.x);
-        st.y2 = df_from_double(b.y);
-        st.m2 = df_from_double(M2);
-        st.mp2 = df_from_double(P2);
-        st.o1a = df_from_double(M2);
-        st.o1b = df_from_double(P2 + c2 + linv);
+        const double lwB = PA + PB + c2 + linv;
+        const bool big = bad || phA >= 6000.0 || phB >= 6000.0 || MA + MB > 40.0 || lwB > 40.0;
+        st.m2 = df_from_double(MB);
+        st.mp2 = df_from_double(PB);
+        st.o1a = df_from_double(MB);
+        st.o1b = df_from_double(PB + c2 + linv);
         const double rA = exp(c1 + linv);
         st.rA = df_from_double(rA);
         st.flags = (big ? 2 : 0) | (lwB >= -42.0 ? 4 : 0) | (rA == 1.0 ? 8 : 0);
@@ -337,55 +428,80 @@ __device__ __forceinline__ float4 dfc_norm(const float4 a) {
 
 constexpr int kSepFlush = 4;  // rounds between additions to the FP64 sums
 
+template <int D>
 __global__ void __launch_bounds__(kSepThreads, 2)
     k_gf2d_df(const SepTraj *__restrict__ sep, const double *__restrict__ n_in,
-              const double2 *__restrict__ nS2, const int *__restrict__ wmax, int64_t count,
-              uint64_t e0, int n_sub, int Ka, int Kb, const double2 *__restrict__ tw,
+              const double2 *__restrict__ nSd, const int *__restrict__ wmax, int64_t count,
+              uint64_t e0, int n_sub, const GridD g, const double2 *__restrict__ tw,
               const DfConsts K, double2 *__restrict__ acc, int64_t *__restrict__ counts) {
     __shared__ float4 sA1[kSepRound][kSepTile], sB1[kSepRound][kSepTile];
     __shared__ float4 sA2[kSepRound][kSepTile], sB2[kSepRound][kSepTile];
     __shared__ SepTraj s_t[kSepRound];
-    __shared__ df s_cm[2][kSepTile], s_sn[2][kSepTile];  // the tile's twiddles per bin
+    // the tile's twiddles: first factor [slot][component bin], second [slot]
+    __shared__ df s_cmA[kSepTile][kMaxBins - 1], s_snA[kSepTile][kMaxBins - 1];
+    __shared__ df s_cmB[kSepTile], s_snB[kSepTile];
     __shared__ int s_ok[2][kSepTile];
-    __shared__ float s_mx[kSepRound][2][2];  // largest |factor| on the tile: [j][bin][A, B]
+    __shared__ float s_mx[kSepRound][2][2];  // largest |factor| on the tile: [j][factor][A, B]
     __shared__ DfTables s_tab;
+    constexpr int d = D;
     const int r = blockIdx.y;
     const int tid = threadIdx.x;
     const int64_t first = (int64_t)(((uint64_t)r + (uint64_t)n_sub - e0 % (uint64_t)n_sub) %
                                     (uint64_t)n_sub);
     const int64_t cnt_r = first < count ? (count - 1 - first) / n_sub + 1 : 0;
     if (blockIdx.x == 0 && tid == 0) counts[r] += cnt_r;
-    const int W1a = wmax[0], W1b = wmax[1], W2a = wmax[2], W2b = wmax[3];
-    const int Sa = slots_of(Ka, W1a, W2a), Sb = slots_of(Kb, W1b, W2b);
-    const int nta = (Sa + kSepTile - 1) / kSepTile, ntb = (Sb + kSepTile - 1) / kSepTile;
-    if ((int)blockIdx.x >= nta * ntb) return;  // past the union window
-    const int sa0 = (blockIdx.x / ntb) * kSepTile, sb0 = (blockIdx.x % ntb) * kSepTile;
+    const Slots sl = slots_of_grid(g, wmax);
+    int64_t Sa = 1;
+    for (int b = 0; b < d - 1; ++b) Sa *= sl.S[b];
+    const int Sb = sl.S[d - 1];
+    const int64_t nta = (Sa + kSepTile - 1) / kSepTile;
+    const int ntb = (Sb + kSepTile - 1) / kSepTile;
+    if ((int64_t)blockIdx.x >= nta * ntb) return;  // past the union window
+    const int64_t sa0 = ((int64_t)blockIdx.x / ntb) * kSepTile;
+    const int sb0 = ((int)(blockIdx.x % ntb)) * kSepTile;
+    const int KB = g.K[d - 1];
     if (tid < 64) s_tab.exp2[tid] = df{K.exp2_hi[tid], K.exp2_lo[tid]};
     if (tid < 33) {
         s_tab.sn[tid] = df{K.sin_hi[tid], K.sin_lo[tid]};
         s_tab.cs[tid] = df{K.cos_hi[tid], K.cos_lo[tid]};
     }
-    if (tid < 2 * kSepTile) {
-        const int bin = tid / kSepTile, sl = tid % kSepTile;
-        const int slot = (bin == 0 ? sa0 : sb0) + sl;
-        const bool ok = slot < (bin == 0 ? Sa : Sb);
-        const int kk = !ok ? 0 : (bin == 0 ? slot_k(slot, Ka, W1a, W2a) : slot_k(slot, Kb, W1b, W2b));
-        const double2 t = tw[(bin == 0 ? 0 : Ka) + kk];
-        s_cm[bin][sl] = df_from_double(t.x);
-        s_sn[bin][sl] = df_from_double(t.y);
-        s_ok[bin][sl] = ok;
+    if (tid < kSepTile) {
+        const int64_t s = sa0 + tid;
+        const bool ok = s < Sa;
+        int k[kMaxBins] = {0, 0, 0, 0};
+        if (ok) slot_ks(g, sl, d - 1, s, k);
+#pragma unroll
+        for (int b = 0; b < kMaxBins - 1; ++b) {
+            const double2 t = b < d - 1 ? tw[g.Koff[b] + k[b]] : make_double2(0.0, 0.0);
+            s_cmA[tid][b] = df_from_double(t.x);
+            s_snA[tid][b] = df_from_double(t.y);
+        }
+        s_ok[0][tid] = ok;
+    } else if (tid < 2 * kSepTile) {
+        const int j2 = tid - kSepTile;
+        const int s = sb0 + j2;
+        const bool ok = s < Sb;
+        const int kk = ok ? slot_k(s, KB, sl.W1[d - 1], sl.W2[d - 1]) : 0;
+        const double2 t = tw[g.Koff[d - 1] + kk];
+        s_cmB[j2] = df_from_double(t.x);
+        s_snB[j2] = df_from_double(t.y);
+        s_ok[1][j2] = ok;
     }
-    // this thread's pairs: bin-1 slots sa0 + 2 ty + p, bin-2 slots sb0 + 2 tx + q
+    // this thread's points: first-factor slots sa0 + 2 ty + p, last-bin
+    // slots sb0 + 2 tx + q
     const int tx = tid & 15, ty = tid >> 4;
-    int k1[2], k2[2];
+    int64_t oA[2];
+    int kB[2];
     bool v1[2], v2[2];
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-        const int sa = sa0 + 2 * ty + p, sb = sb0 + 2 * tx + p;
+        const int64_t sa = sa0 + 2 * ty + p;
+        const int sb = sb0 + 2 * tx + p;
         v1[p] = sa < Sa;
         v2[p] = sb < Sb;
-        k1[p] = v1[p] ? slot_k(sa, Ka, W1a, W2a) : 0;
-        k2[p] = v2[p] ? slot_k(sb, Kb, W1b, W2b) : 0;
+        int k[kMaxBins] = {0, 0, 0, 0};
+        oA[p] = v1[p] ? slot_ks(g, sl, d - 1, sa, k) : 0;
+        kB[p] = v2[p] ? slot_k(sb, KB, sl.W1[d - 1], sl.W2[d - 1]) : 0;
     }
     double dP[2][2][2] = {}, dX[2][2][2] = {};  // +P and (matrix-P - +P), (re, im)
     float4 aP[2][2], aX[2][2];  // double-float sums
@@ -410,25 +526,36 @@ __global__ void __launch_bounds__(kSepThreads, 2)
             s_t[tid] = st;
         }
         __syncthreads();
-        // bin vectors of the round on the tile's slots: item = (trajectory,
-        // bin, slot); A and B share l, phi and the sine/cosine
+        // factor vectors of the round on the tile's slots: item =
+        // (trajectory, factor, slot); A and B share l, phi and the sine/cosine
         for (int it = tid; it < kSepRound * 2 * kSepTile; it += kSepThreads) {
             const int j = it / (2 * kSepTile);
-            const int bin = (it / kSepTile) & 1;
-            const int sl = it % kSepTile;
+            const int fac = (it / kSepTile) & 1;
+            const int sidx = it % kSepTile;
             const SepTraj &st = s_t[j];
             float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A;
-            if (!(st.flags & 2) && s_ok[bin][sl]) {
-                const df cm1 = s_cm[bin][sl], sn = s_sn[bin][sl];
-                const df x = bin == 0 ? st.x1 : st.x2, y = bin == 0 ? st.y1 : st.y2;
-                const df l = df_sub(df_mul(cm1, x), df_mul(sn, y));
-                const df ph = df_add(df_mul(sn, x), df_mul(cm1, y));
+            if (!(st.flags & 2) && s_ok[fac][sidx]) {
+                df l = {0.f, 0.f}, ph = {0.f, 0.f};
+                if (fac == 0) {
+#pragma unroll
+                    for (int b = 0; b < d - 1; ++b) {
+                        const df cm1 = s_cmA[sidx][b], sn = s_snA[sidx][b];
+                        const df lb = df_sub(df_mul(cm1, st.x[b]), df_mul(sn, st.y[b]));
+                        const df pb = df_add(df_mul(sn, st.x[b]), df_mul(cm1, st.y[b]));
+                        l = b == 0 ? lb : df_add(l, lb);
+                        ph = b == 0 ? pb : df_add(ph, pb);
+                    }
+                } else {
+                    const df cm1 = s_cmB[sidx], sn = s_snB[sidx];
+                    l = df_sub(df_mul(cm1, st.x[d - 1]), df_mul(sn, st.y[d - 1]));
+                    ph = df_add(df_mul(sn, st.x[d - 1]), df_mul(cm1, st.y[d - 1]));
+                }
                 df sp, cp;
                 df_sincos_tab(ph, s_tab, K, sp, cp);
-                // exponents: bin 1: l + M_2 and -l + M'_2 + c2 + log inv;
-                // bin 2: l - M_2 and -l - M'_2
-                const df ea = bin == 0 ? df_add(l, st.o1a) : df_sub(l, st.m2);
-                const df eb = bin == 0 ? df_sub(st.o1b, l) : df_sub(df_neg(l), st.mp2);
+                // exponents: first factor: l + M_B and -l + M'_B + c2 + log inv;
+                // second: l - M_B and -l - M'_B
+                const df ea = fac == 0 ? df_add(l, st.o1a) : df_sub(l, st.m2);
+                const df eb = fac == 0 ? df_sub(st.o1b, l) : df_sub(df_neg(l), st.mp2);
                 if (ea.hi >= -87.0f) {
                     const df e = df_exp_tab(ea, s_tab, K);
                     const df re = df_mul(e, cp), im = df_mul(e, sp);
@@ -440,31 +567,30 @@ __global__ void __launch_bounds__(kSepThreads, 2)
                     B = make_float4(re.hi, re.lo, -im.hi, -im.lo);
                 }
             }
-            if (bin == 0) {
-                sA1[j][sl] = A;
-                sB1[j][sl] = B;
+            if (fac == 0) {
+                sA1[j][sidx] = A;
+                sB1[j][sidx] = B;
             } else {
-                sA2[j][sl] = A;
-                sB2[j][sl] = B;
+                sA2[j][sidx] = A;
+                sB2[j][sidx] = B;
             }
-            // the 32 slots of one (trajectory, bin) are one warp's items
+            // the 32 slots of one (trajectory, factor) are one warp's items
             const unsigned ma = __float_as_uint(fmaxf(fabsf(A.x), fabsf(A.z)));
             const unsigned mb = __float_as_uint(fmaxf(fabsf(B.x), fabsf(B.z)));
             const unsigned wa = __reduce_max_sync(0xffffffffu, ma);
             const unsigned wb = __reduce_max_sync(0xffffffffu, mb);
-            if (sl == 0) {
-                s_mx[j][bin][0] = __uint_as_float(wa);
-                s_mx[j][bin][1] = __uint_as_float(wb);
+            if (sidx == 0) {
+                s_mx[j][fac][0] = __uint_as_float(wa);
+                s_mx[j][fac][1] = __uint_as_float(wb);
             }
         }
         __syncthreads();
         for (int j = 0; j < nr; ++j) {
             const int flags = s_t[j].flags;
             if (flags & 2) {
-                // per-pair FP64 route (huge phases or exponents)
+                // per-point FP64 route (huge phases or exponents)
                 const int64_t i = first + (base + j) * n_sub;
                 const double nn = n_in[i];
-                const double2 a = nS2[2 * i], b = nS2[2 * i + 1];
                 const double c1d = fmin(0.0, 2.0 * nn), c2d = -2.0 * fmax(nn, 0.0);
                 const double inv = 1.0 / (1.0 + exp(-2.0 * fabs(nn)));
 #pragma unroll
@@ -472,9 +598,22 @@ __global__ void __launch_bounds__(kSepThreads, 2)
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
                         if (!(v1[p] && v2[q])) continue;
-                        const double2 ta = tw[k1[p]], tb = tw[Ka + k2[q]];
-                        const double ld = (ta.x * a.x - ta.y * a.y) + (tb.x * b.x - tb.y * b.y);
-                        const double pd = (ta.y * a.x + ta.x * a.y) + (tb.y * b.x + tb.x * b.y);
+                        double ld = 0.0, pd = 0.0;
+                        int64_t rem = oA[p];  // row-major over the first d - 1 bins
+#pragma unroll
+                        for (int b = d - 1; b >= 0; --b) {
+                            int kb;
+                            if (b == d - 1) {
+                                kb = kB[q];
+                            } else {
+                                kb = (int)(rem % g.K[b]);
+                                rem /= g.K[b];
+                            }
+                            const double2 t = tw[g.Koff[b] + kb];
+                            const double2 v = nSd[(size_t)d * i + b];
+                            ld += t.x * v.x - t.y * v.y;
+                            pd += t.y * v.x + t.x * v.y;
+                        }
                         double sd, cd;
                         sincos(pd, &sd, &cd);
                         const double gp = ld >= -745.0 ? exp(ld) : 0.0;
@@ -568,13 +707,14 @@ __global__ void __launch_bounds__(kSepThreads, 2)
             }
         __syncthreads();
     }
-    const size_t grid = (size_t)Ka * Kb;
+    int64_t grid = 1;
+    for (int b = 0; b < d; ++b) grid *= g.K[b];
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             if (!(v1[p] && v2[q])) continue;
-            const size_t o = (size_t)k1[p] * Kb + k2[q];
+            const size_t o = (size_t)oA[p] * KB + kB[q];
             double2 *pm = acc + (size_t)r * grid + o;
             double2 *pp = acc + ((size_t)n_sub + r) * grid + o;
             const double2 vm = *pm, vp = *pp;
@@ -583,11 +723,13 @@ __global__ void __launch_bounds__(kSepThreads, 2)
         }
 }
 
-__global__ void k_tables2d(int Ka, int Kb, double2 *__restrict__ tw, double2 *__restrict__ wf) {
-    const int total = Ka + Kb;
+__global__ void k_tables2d(const GridD g, int total, double2 *__restrict__ tw,
+                           double2 *__restrict__ wf) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int K = i < Ka ? Ka : Kb;
-        const int k = i < Ka ? i : i - Ka;
+        int b = 0;
+        while (b + 1 < g.d && i >= g.Koff[b + 1]) ++b;
+        const int K = g.K[b];
+        const int k = i - g.Koff[b];
         const double f = (double)k / (double)K;
         double sh, ch, s2, c2;
         sincospi(f, &sh, &ch);
@@ -597,62 +739,63 @@ __global__ void k_tables2d(int Ka, int Kb, double2 *__restrict__ tw, double2 *__
     }
 }
 
-// a = acc / (count_r Ka Kb) * e^{-i (theta_1 m1_off + theta_2 m2_off)}
+// a = acc / (count_r prod K) * e^{-i sum_b theta_b m_off_b}
 __global__ void k_prep2d(const double2 *__restrict__ acc, const int64_t *__restrict__ counts,
-                         int n_sub, int Ka, int Kb, int64_t mo1, int64_t mo2,
+                         int n_sub, const GridD g, int64_t grid, const int64_t *__restrict__ mo,
                          const double2 *__restrict__ wf, double2 *__restrict__ out) {
-    const int64_t grid = (int64_t)Ka * Kb;
     const int64_t total = 2 * (int64_t)n_sub * grid;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t g = idx % grid;
+        int64_t gi = idx % grid;
         const int r = (int)((idx / grid) % n_sub);
-        const int k1 = (int)(g / Kb), k2 = (int)(g % Kb);
         const double scale = 1.0 / ((double)counts[r] * (double)grid);
-        const double2 w1 = wf[(int)(((int64_t)k1 * mo1) % Ka)];
-        const double2 w2 = wf[Ka + (int)(((int64_t)k2 * mo2) % Kb)];
-        const double2 w = make_double2(w1.x * w2.x - w1.y * w2.y, w1.x * w2.y + w1.y * w2.x);
+        double2 w = make_double2(1.0, 0.0);
+        for (int b = g.d - 1; b >= 0; --b) {
+            const int k = (int)(gi % g.K[b]);
+            gi /= g.K[b];
+            const double2 wb = wf[g.Koff[b] + (int)(((int64_t)k * mo[b]) % g.K[b])];
+            w = make_double2(w.x * wb.x - w.y * wb.y, w.x * wb.y + w.y * wb.x);
+        }
         const double2 a = acc[idx];
         out[idx] = make_double2((a.x * w.x - a.y * w.y) * scale, (a.x * w.y + a.y * w.x) * scale);
     }
 }
 
 // [batch][R][C] -> [batch][C][R]
-__global__ void k_transpose2d(const double2 *__restrict__ x, double2 *__restrict__ y, int R,
+__global__ void k_transpose2d(const double2 *__restrict__ x, double2 *__restrict__ y, int64_t R,
                               int C, int64_t batch) {
-    const int64_t per = (int64_t)R * C;
+    const int64_t per = R * C;
     const int64_t total = batch * per;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = idx / per;
-        const int64_t g = idx % per;
-        const int rr = (int)(g / C), cc = (int)(g % C);
+        const int64_t gidx = idx % per;
+        const int64_t rr = gidx / C;
+        const int cc = (int)(gidx % C);
         y[b * per + (int64_t)cc * R + rr] = x[idx];
     }
 }
 
-// x: [est][r][m2][m1] -> out [P_mP | sig_mP | P_pP | sig_pP], each [m1][m2]
-__global__ void k_stats2d(const double2 *__restrict__ x, int n_sub, int Ka, int Kb,
+// x: [est][r][grid] -> out [P_mP | sig_mP | P_pP | sig_pP], each [grid]
+__global__ void k_stats2d(const double2 *__restrict__ x, int n_sub, int64_t grid,
                           double *__restrict__ out) {
-    const int64_t grid = (int64_t)Ka * Kb;
     const int64_t total = 2 * grid;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int est = (int)(idx / grid);
-        const int64_t g = idx % grid;
-        const int m1 = (int)(g / Kb), m2 = (int)(g % Kb);
-        const double2 *p = x + (size_t)est * n_sub * grid + (size_t)m2 * Ka + m1;
+        const int64_t gi = idx % grid;
+        const double2 *p = x + (size_t)est * n_sub * grid + gi;
         double mean = 0.0;
         for (int r = 0; r < n_sub; ++r) mean += p[(size_t)r * grid].x;
         mean /= (double)n_sub;
         double var = 0.0;
         for (int r = 0; r < n_sub; ++r) {
-            const double d = p[(size_t)r * grid].x - mean;
-            var += d * d;
+            const double dd = p[(size_t)r * grid].x - mean;
+            var += dd * dd;
         }
         const double sd = n_sub > 1 ? sqrt(var / (double)(n_sub - 1)) : 0.0;
-        out[(size_t)(2 * est) * grid + g] = mean;
-        out[(size_t)(2 * est + 1) * grid + g] = sd / sqrt((double)n_sub);
+        out[(size_t)(2 * est) * grid + gi] = mean;
+        out[(size_t)(2 * est + 1) * grid + gi] = sd / sqrt((double)n_sub);
     }
 }
 
@@ -663,82 +806,108 @@ int blocks2(const gbs_net *net, int64_t work) {
     return b < 1 ? 1 : (int)b;
 }
 
+GridD grid_of(const gbs_net *net) {
+    GridD g = {};
+    g.d = net->nbins;
+    int off = 0;
+    for (int b = 0; b < kMaxBins; ++b) {
+        g.K[b] = b < g.d ? net->Kd[b] : 1;
+        g.Koff[b] = off;
+        if (b < g.d) off += net->Kd[b];
+    }
+    for (int b = 0; b <= kMaxBins; ++b) g.tile[b] = net->bin_tiles[b];
+    return g;
+}
+
 }  // namespace
 
 size_t sep2_bytes_per_trajectory() { return sizeof(SepTraj); }
 
 int launch_finalize2d(gbs_net *net, int64_t count) {
     if (count <= 0) return GBS_OK;
-    GBS_CUDA_TRY(cudaMemsetAsync(net->d_wmax2, 0xff, 4 * sizeof(int), net->stream));
+    GBS_CUDA_TRY(cudaMemsetAsync(net->d_wmax2, 0xff, 2 * kMaxBins * sizeof(int), net->stream));
     k_finalize2d<<<blocks2(net, count), 256, 0, net->stream>>>(
-        net->d_nS_part, net->mtiles, net->bin_tile0, net->chunk, net->d_n, count, net->Ka,
-        net->Kb, net->d_nS2, net->d_win2, net->d_wmax2);
+        net->d_nS_part, grid_of(net), net->chunk, net->d_n, count, net->d_nS2, net->d_win2,
+        net->d_wmax2);
     GBS_LAUNCH_CHECK();
     return GBS_OK;
 }
 
 int launch_gf2d(gbs_net *net, uint64_t e0, int64_t count) {
     if (count <= 0) return GBS_OK;
-    // blocks for the whole grid; blocks past the chunk's union window return
-    const int64_t cells = (int64_t)net->Ka * net->Kb;
-    dim3 grid((unsigned)((cells + kG2Threads - 1) / kG2Threads), (unsigned)net->n_sub2);
+    const GridD g = grid_of(net);
     if (net->precision == GBS_FP64) {
+        // blocks for the whole grid; blocks past the chunk's union window return
+        dim3 grid((unsigned)((net->grid2 + kG2Threads - 1) / kG2Threads), (unsigned)net->n_sub2);
         k_gf2d<<<grid, kG2Threads, 0, net->stream>>>(net->d_n, net->d_nS2, net->d_win2,
-                                                      net->d_wmax2, count, e0, net->n_sub2,
-                                                      net->Ka, net->Kb, net->d_tw2, net->d_acc2,
-                                                      net->d_counts2);
+                                                      net->d_wmax2, count, e0, net->n_sub2, g,
+                                                      net->d_tw2, net->d_acc2, net->d_counts2);
     } else {
         static const DfConsts K = make_df_consts();
         // tiles of 32 x 32 slots over the whole grid; tiles past the chunk's
         // union window return at once
-        const int64_t tiles = (int64_t)((net->Ka + kSepTile - 1) / kSepTile) *
-                              ((net->Kb + kSepTile - 1) / kSepTile);
+        const int KB = net->Kd[net->nbins - 1];
+        const int64_t KA = net->grid2 / KB;
+        const int64_t tiles = ((KA + kSepTile - 1) / kSepTile) * ((KB + kSepTile - 1) / kSepTile);
         dim3 g2((unsigned)tiles, (unsigned)net->n_sub2);
         SepTraj *sep = static_cast<SepTraj *>(net->d_sep2);
-        k_sep_prep<<<blocks2(net, count), 256, 0, net->stream>>>(net->d_n, net->d_nS2, count, sep);
+        k_sep_prep<<<blocks2(net, count), 256, 0, net->stream>>>(net->d_n, net->d_nS2, count,
+                                                                 net->nbins, sep);
         GBS_LAUNCH_CHECK();
-        k_gf2d_df<<<g2, kSepThreads, 0, net->stream>>>(sep, net->d_n, net->d_nS2, net->d_wmax2,
-                                                        count, e0, net->n_sub2, net->Ka, net->Kb,
-                                                        net->d_tw2, K, net->d_acc2,
-                                                        net->d_counts2);
+        auto kern = net->nbins == 2 ? k_gf2d_df<2> : net->nbins == 3 ? k_gf2d_df<3> : k_gf2d_df<4>;
+        kern<<<g2, kSepThreads, 0, net->stream>>>(sep, net->d_n, net->d_nS2, net->d_wmax2, count,
+                                                   e0, net->n_sub2, g, net->d_tw2, K, net->d_acc2,
+                                                   net->d_counts2);
     }
     GBS_LAUNCH_CHECK();
     return GBS_OK;
 }
 
 int launch_tables2d(gbs_net *net) {
-    const int total = net->Ka + net->Kb;
-    k_tables2d<<<(total + 255) / 256, 256, 0, net->stream>>>(net->Ka, net->Kb, net->d_tw2,
-                                                              net->d_wf2);
+    const GridD g = grid_of(net);
+    int total = 0;
+    for (int b = 0; b < g.d; ++b) total += g.K[b];
+    k_tables2d<<<(total + 255) / 256, 256, 0, net->stream>>>(g, total, net->d_tw2, net->d_wf2);
     GBS_LAUNCH_CHECK();
     return GBS_OK;
 }
 
-int launch_invert2d(gbs_net *net, int64_t m1_off, int64_t m2_off, double *out_dev) {
-    const int Ka = net->Ka, Kb = net->Kb;
-    const int64_t grid = (int64_t)Ka * Kb;
+int launch_invert2d(gbs_net *net, const int64_t *m_off, double *out_dev, int *launches) {
+    const GridD g = grid_of(net);
+    const int64_t grid = net->grid2;
     const int64_t batch = 2 * (int64_t)net->n_sub2;
-    int64_t mo1 = m1_off % Ka, mo2 = m2_off % Kb;
-    if (mo1 < 0) mo1 += Ka;
-    if (mo2 < 0) mo2 += Kb;
+    int64_t mo[kMaxBins] = {0, 0, 0, 0};
+    for (int b = 0; b < g.d; ++b) {
+        mo[b] = m_off[b] % g.K[b];
+        if (mo[b] < 0) mo[b] += g.K[b];
+    }
+    // pageable source: the copy is staged before the call returns
+    GBS_CUDA_TRY(cudaMemcpyAsync(net->d_mo2, mo, sizeof(mo), cudaMemcpyHostToDevice, net->stream));
     k_prep2d<<<blocks2(net, batch * grid), 256, 0, net->stream>>>(
-        net->d_acc2, net->d_counts2, net->n_sub2, Ka, Kb, mo1, mo2, net->d_wf2, net->d_f2a);
+        net->d_acc2, net->d_counts2, net->n_sub2, g, grid, net->d_mo2, net->d_wf2, net->d_f2a);
     GBS_LAUNCH_CHECK();
-    int rc;
-    double2 *res = nullptr;
-    // DFT along k_2 (rows of Kb), transpose, DFT along k_1 (rows of Ka)
-    if ((rc = launch_fft_rows(net->d_wf2 + Ka, Kb, batch * Ka, net->d_f2a, net->d_f2b, &res,
-                              net->stream, net->sm_count)))
-        return rc;
-    double2 *other = res == net->d_f2a ? net->d_f2b : net->d_f2a;
-    k_transpose2d<<<blocks2(net, batch * grid), 256, 0, net->stream>>>(res, other, Ka, Kb, batch);
+    int nl = 1;
+    double2 *cur = net->d_f2a;
+    // per dimension, innermost first: FFTs along it, then rotate it outermost
+    for (int b = g.d - 1; b >= 0; --b) {
+        double2 *other = cur == net->d_f2a ? net->d_f2b : net->d_f2a;
+        double2 *res = nullptr;
+        int rc;
+        if ((rc = launch_fft_rows(net->d_wf2 + g.Koff[b], g.K[b], batch * (grid / g.K[b]), cur,
+                                  other, &res, net->stream, net->sm_count)))
+            return rc;
+        for (int v = g.K[b]; v > 1; v >>= 1) ++nl;
+        double2 *dst = res == net->d_f2a ? net->d_f2b : net->d_f2a;
+        k_transpose2d<<<blocks2(net, batch * grid), 256, 0, net->stream>>>(res, dst, grid / g.K[b],
+                                                                            g.K[b], batch);
+        GBS_LAUNCH_CHECK();
+        ++nl;
+        cur = dst;
+    }
+    k_stats2d<<<blocks2(net, 2 * grid), 256, 0, net->stream>>>(cur, net->n_sub2, grid, out_dev);
     GBS_LAUNCH_CHECK();
-    double2 *spare = other == net->d_f2a ? net->d_f2b : net->d_f2a;
-    if ((rc = launch_fft_rows(net->d_wf2, Ka, batch * Kb, other, spare, &res, net->stream,
-                              net->sm_count)))
-        return rc;
-    k_stats2d<<<blocks2(net, 2 * grid), 256, 0, net->stream>>>(res, net->n_sub2, Ka, Kb, out_dev);
-    GBS_LAUNCH_CHECK();
+    ++nl;
+    if (launches) *launches = nl;
     return GBS_OK;
 }
 
