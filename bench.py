@@ -37,7 +37,8 @@ UNIT = "samples/s"
 # (profiles/k_gemm_tc_m1000_bf16x3.md: 1.0845 GB read + 0.0360 GB written);
 # the sample operand it reads grows in proportion to the trajectories.  Valid
 # for the workload and kernel version of that capture only.
-GEMM_TRAFFIC_BYTES_PER_SAMPLE = {("m1000", "bf16x3"): (1.082062e9 + 34.582016e6) / 131072}
+# keyed by (workload, precision, whether the GEMM also runs the next chunk's sampler)
+GEMM_TRAFFIC_BYTES_PER_SAMPLE = {("m1000", "bf16x3", False): (1.082062e9 + 34.582016e6) / 131072}
 
 
 def _env_int(name, default):
@@ -262,7 +263,12 @@ def gbs_arm(args, wl_def):
                 "kernel": "k_gemm_tc", "launches": gemm_launches,
                 "cluster": gbs.gbs_gemm_config(net),
                 "avg_launch_ms": gemm_ms / max(gemm_launches, 1)}
-        per_sample = GEMM_TRAFFIC_BYTES_PER_SAMPLE.get((wl_def.name.split(":")[0], precision))
+        folded = gbs.gbs_sampler_fusion(net)
+        if folded:
+            roof["kernel"] = "k_gemm_tc (sampling variant: its spare warps also draw the " \
+                             "next chunk's samples)"
+        per_sample = GEMM_TRAFFIC_BYTES_PER_SAMPLE.get(
+            (wl_def.name.split(":")[0], precision, folded))
         if per_sample is not None:
             roof["traffic"] = per_sample * E * args.steps / max(gemm_launches, 1)
             roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one " \

@@ -100,6 +100,8 @@ def lib():
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.gbs_binned_counts_2d.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp]
         L.gbs_gemm_config.argtypes = [vp, ip]
+        L.gbs_set_sampler_fusion.argtypes = [vp, ctypes.c_int]
+        L.gbs_sampler_fusion.argtypes = [vp, ip]
         L.gbs_make_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
         L.gbs_sample_batch.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64),
                                        ctypes.POINTER(ctypes.c_uint64), i64p, ip, ip]
@@ -135,6 +137,7 @@ def lib():
                      "gbs_get_accumulators", "gbs_set_accumulators", "gbs_reset",
                      "gbs_network_info", "gbs_profile_enable", "gbs_profile_read",
                      "gbs_binned_counts_noalloc", "gbs_set_gemm_config", "gbs_gemm_config",
+                     "gbs_set_sampler_fusion", "gbs_sampler_fusion",
                      "gbs_make_batch", "gbs_sample_batch", "gbs_batch_info",
                      "gbs_make_network_device", "gbs_make_network_binned", "gbs_sample_2d",
                      "gbs_binned_counts_2d", "gbs_sample_nd", "gbs_binned_counts_nd",
@@ -385,6 +388,18 @@ def gbs_gemm_config(net: Network) -> int:
     c = ctypes.c_int()
     _check(lib().gbs_gemm_config(net.handle, ctypes.byref(c)))
     return c.value
+
+
+def gbs_set_sampler_fusion(net: Network, enable: bool) -> None:
+    """Sample the next chunk inside the GEMM of this one (BF16X3; default on)."""
+    _check(lib().gbs_set_sampler_fusion(net.handle, 1 if enable else 0))
+
+
+def gbs_sampler_fusion(net: Network) -> bool:
+    """Whether the next multi-chunk gbs_sample runs the folded sampler."""
+    a = ctypes.c_int()
+    _check(lib().gbs_sampler_fusion(net.handle, ctypes.byref(a)))
+    return bool(a.value)
 
 
 class Batch:

@@ -146,6 +146,9 @@ void release_all(gbs_net *net) {
     dev_free(net->d_A);
     if (net->d_B) cudaFree(net->d_B);
     net->d_B = nullptr;
+    if (net->d_B_alt) cudaFree(net->d_B_alt);
+    net->d_B_alt = nullptr;
+    dev_free(net->d_n_alt);
     dev_free(net->d_n);
     dev_free(net->d_nS_part);
     dev_free(net->d_nS);
@@ -173,6 +176,44 @@ int run_chunk_front(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) {
     if ((rc = launch_finalize(net, count))) return rc;
     prof_mark(net, GBS_PHASE_FINALIZE, 1, false);
     return GBS_OK;
+}
+
+// The chunks of gbs_sample with the sampler folded into the GEMM (BF16X3):
+// the first chunk is sampled alone; the GEMM of chunk i samples chunk i + 1
+// into the second operand, and the two operands swap roles after every
+// chunk (back to their original roles at the end, so that the other entry
+// points always find the first operand current).  The samples, and so every
+// sum, are bitwise those of the plain chunk loop.
+int sample_chunks_pipelined(gbs_net *net, uint64_t seed, uint64_t first, int64_t E) {
+    int rc = GBS_OK, swaps = 0;
+    prof_mark(net, GBS_PHASE_SAMPLE, 0, true);
+    rc = launch_sample_bf16(net, seed, first, std::min<int64_t>(net->chunk, E));
+    prof_mark(net, GBS_PHASE_SAMPLE, 1, false);
+    for (int64_t done = 0; rc == GBS_OK && done < E; done += net->chunk) {
+        const int64_t c = std::min<int64_t>(net->chunk, E - done);
+        const uint64_t e0 = first + (uint64_t)done;
+        const int64_t next = std::min<int64_t>(net->chunk, E - done - c);
+        prof_mark(net, GBS_PHASE_GEMM, 0, true);
+        if (next > 0) {
+            const SampleJob job = sample_job_bf16(net, net->d_B_alt, net->d_n_alt, seed,
+                                                  e0 + (uint64_t)c, next);
+            rc = launch_gemm_tc_sampling(net, c, job);
+        } else {
+            rc = launch_gemm_tc(net, c);
+        }
+        if (rc) break;
+        prof_mark(net, GBS_PHASE_GEMM, 1, false);
+        prof_mark(net, GBS_PHASE_FINALIZE, 0, true);
+        if ((rc = launch_finalize(net, c))) break;
+        prof_mark(net, GBS_PHASE_FINALIZE, 1, false);
+        prof_mark(net, GBS_PHASE_GF, 0, true);
+        if ((rc = launch_gf(net, e0, c))) break;
+        prof_mark(net, GBS_PHASE_GF, 1, false);
+        tc_swap_sample_buffers(net);
+        ++swaps;
+    }
+    if (swaps & 1) tc_swap_sample_buffers(net);
+    return rc;
 }
 
 // T (device, M x N complex, (re, im) interleaved, row-major) -> [M][2][N] FP64.
@@ -582,13 +623,17 @@ int gbs_sample(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, i
     if (first_sample + (uint64_t)E < first_sample)
         return set_error(GBS_EINVAL, "sample index range overflows 64 bits");
     if ((rc = fix_estimator(net, n_sub, K1))) return rc;
-    for (int64_t done = 0; done < E; done += net->chunk) {
-        const int64_t c = std::min<int64_t>(net->chunk, E - done);
-        const uint64_t e0 = first_sample + (uint64_t)done;
-        if ((rc = run_chunk_front(net, seed, e0, c))) return rc;
-        prof_mark(net, GBS_PHASE_GF, 0, true);
-        if ((rc = launch_gf(net, e0, c))) return rc;
-        prof_mark(net, GBS_PHASE_GF, 1, false);
+    if (E > net->chunk && net->precision == GBS_BF16X3 && tc_sampling_ready(net, true)) {
+        if ((rc = sample_chunks_pipelined(net, seed, first_sample, E))) return rc;
+    } else {
+        for (int64_t done = 0; done < E; done += net->chunk) {
+            const int64_t c = std::min<int64_t>(net->chunk, E - done);
+            const uint64_t e0 = first_sample + (uint64_t)done;
+            if ((rc = run_chunk_front(net, seed, e0, c))) return rc;
+            prof_mark(net, GBS_PHASE_GF, 0, true);
+            if ((rc = launch_gf(net, e0, c))) return rc;
+            prof_mark(net, GBS_PHASE_GF, 1, false);
+        }
     }
     count_samples(net, first_sample, E);
     return GBS_OK;
@@ -1015,6 +1060,22 @@ int gbs_set_gemm_config(gbs_net_t net, int cluster) {
     if ((rc = validate_net(net))) return rc;
     if (net->precision == GBS_FP64) return set_error(GBS_EINVAL, "the FP64 path has no tcgen05 GEMM");
     return tc_set_cluster(net, cluster);
+}
+
+int gbs_set_sampler_fusion(gbs_net_t net, int enable) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (enable != 0 && enable != 1) return set_error(GBS_EINVAL, "enable must be 0 or 1");
+    net->fuse_sampler = enable;
+    return GBS_OK;
+}
+
+int gbs_sampler_fusion(gbs_net_t net, int *active) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (!active) return set_error(GBS_EINVAL, "active is NULL");
+    *active = tc_sampling_ready(net, false) ? 1 : 0;
+    return GBS_OK;
 }
 
 int gbs_gemm_config(gbs_net_t net, int *cluster) {

@@ -98,6 +98,20 @@ struct OccOut64 {
     int64_t plane = 0;
 };
 
+// One chunk's work for the BF16 sampler (sampler_dev.cuh): trajectories
+// e0 .. e0 + count - 1 into the sample operand at B (planesB planes of
+// plane_stride elements, rows rows each, K-blocked with ldK) and n_out[count].
+// count == 0: nothing to sample.
+struct SampleJob {
+    const float2 *sq = nullptr;  // [N] (sqrt(s+/2), sqrt(s-/2))
+    __nv_bfloat16 *B = nullptr;
+    double *n_out = nullptr;
+    size_t plane_stride = 0, rows = 0;
+    uint64_t seed = 0, e0 = 0;
+    int64_t count = 0;
+    int N = 0, ldK = 0, planesB = 0;
+};
+
 // CUDA-event timing of kernel phases (gbs_profile_*).
 struct Profiler {
     bool on = false;
@@ -132,6 +146,11 @@ struct gbs_net {
     void *d_B = nullptr;  // sample operand
     size_t B_bytes = 0;
     double *d_n = nullptr;          // [chunk]
+    // second sample operand and n[] (BF16X3): the GEMM of one chunk fills
+    // them with the next chunk's samples; swapped with d_B, d_n per chunk
+    void *d_B_alt = nullptr;
+    double *d_n_alt = nullptr;
+    int fuse_sampler = 1;           // gbs_set_sampler_fusion
     double2 *d_nS_part = nullptr;   // [mtiles][chunk]
     int mtiles = 0;
     double2 *d_nS = nullptr;        // [chunk]
@@ -185,12 +204,24 @@ namespace gbs {
 // Sampler: writes the sample operand for trajectories e0..e0+count-1 and n[].
 int launch_sample_fp64(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count);
 int launch_sample_bf16(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count);
+// The BF16 sampler's job for trajectories e0..e0+count-1 into (B, n).
+SampleJob sample_job_bf16(gbs_net *net, void *B, double *n, uint64_t seed, uint64_t e0,
+                          int64_t count);
 
 // Propagation GEMM with the fused occupation epilogue -> nS_part[mtiles][chunk].
 int launch_gemm_fp64(gbs_net *net, int64_t count, OccOut64 occ = OccOut64());
 int tc_plan_create(gbs_net *net);
 void tc_plan_destroy(gbs_net *net);
 int launch_gemm_tc(gbs_net *net, int64_t count, OccOut occ = OccOut());
+// 3-product GEMM of the chunk in (d_B, d_n) whose spare warps run `job`
+// (the next chunk, into d_B_alt, d_n_alt); needs tc_sampling_ready().
+int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job);
+// Whether this network can run the sampling GEMM: 3 products, the kernel's
+// register split verified, the second operand allocated (allocates it when
+// `allocate`).
+bool tc_sampling_ready(gbs_net *net, bool allocate);
+// Swap (d_B, d_n, tensor maps) with their second copies.
+void tc_swap_sample_buffers(gbs_net *net);
 int tc_set_cluster(gbs_net *net, int cluster);  // 0 = autotune, 1, 2
 int tc_get_cluster(gbs_net *net);
 int tc_autotune(gbs_net *net, int64_t count, int *cluster);

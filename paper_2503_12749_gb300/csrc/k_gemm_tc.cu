@@ -51,10 +51,20 @@
 //               epilogue also writes every n'_i: with 3 products each warp
 //               stages its 32 x 16 values in shared memory and stores rows
 //               of 64 bytes, 8 rows per instruction.
+// Sampling variant (3 products, 512 threads): warps 4..11 are the
+// epilogue, and warps 2, 3, 12..15 run the BF16 sampler (sampler_dev.cuh)
+// on the NEXT chunk's trajectories, into the second sample operand, while
+// the tensor cores work on this one: the sampler is issue-bound and the GEMM
+// leaves most issue slots idle.  Registers: launched at 128 per thread
+// (65,536 per CTA), the two epilogue warpgroups take 168 each and the other
+// two give up theirs down to 88 (setmaxnreg; 2 x 128 x 168 + 2 x 128 x 88 =
+// 65,536); the host launches this variant only after checking that the
+// kernel was built with exactly 128 registers per thread.
 // Every mbarrier wait is bounded; on a timeout the kernel raises an error
 // flag, drains its own TMA loads and MMAs, frees TMEM and returns.
 #include "gbs_internal.cuh"
 #include "tc_ptx.cuh"
+#include "sampler_dev.cuh"
 
 #include <cudaTypedefs.h>
 
@@ -68,6 +78,8 @@ namespace gbs {
 struct TcPlan {
     GemmNetDesc desc;               // host copy
     GemmNetDesc *d_desc = nullptr;  // device copy (single-network launches)
+    GemmNetDesc desc_alt;           // the same over the second sample operand
+    GemmNetDesc *d_desc_alt = nullptr;
     int P = 0;
     int cluster = 0;                // 1 or 2; 0 = pick by the autotuner
     int forced = 0;                 // set by gbs_set_gemm_config
@@ -109,6 +121,21 @@ constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(128, 256);
 constexpr int kEpiWarps = kEpiWarpsFwd;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
+// sampling variant
+constexpr int kSampThreads = 512;
+constexpr int kSampWarps = 6;
+constexpr int kRegsLaunch = 65536 / kSampThreads;  // 128
+constexpr int kRegsEpi = 168, kRegsRest = 88;
+static_assert(2 * 128 * kRegsEpi + 2 * 128 * kRegsRest == kSampThreads * kRegsLaunch,
+              "register split of the sampling GEMM");
+template <bool kSamp>
+__host__ __device__ constexpr int threads_of() {
+    return kSamp ? kSampThreads : kThreads;
+}
+template <bool kSamp>
+__host__ __device__ constexpr int epi_warp0() {
+    return kSamp ? 4 : 2;
+}
 
 // A tile of the grouped GEMM: which network, which group of kCl mode
 // tiles, which 128-trajectory tile.
@@ -182,10 +209,12 @@ __device__ __forceinline__ void warp_transpose_reduce32(float (&v)[32], int lane
     }
 }
 
-template <int P, int kCl>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int P, int kCl, bool kSamp>
+__global__ void __launch_bounds__(threads_of<kSamp>(), 1)
     k_gemm_tc(const GemmNetDesc *__restrict__ nets, const int4 *__restrict__ tiles, int ntiles,
-              int64_t count0, unsigned long long *err_ptr, OccOut occ) {
+              int64_t count0, unsigned long long *err_ptr, OccOut occ, const SampleJob job) {
+    static_assert(!kSamp || P == 3, "the sampling variant runs the 3-product GEMM");
+    constexpr int kE0 = epi_warp0<kSamp>();  // first epilogue warp
     using C = Cfg<P>;
     constexpr int kStages = C::kStages;
     constexpr int kPl = C::kPlanes;
@@ -246,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int cluster = blockIdx.x / kCl;
     const int nclusters = gridDim.x / kCl;
 
-    if (warp == 0) {
+    auto producer = [&]() {
         if (lane == 0) {
             // ---------------------------------------------------- TMA producer
             int stage = 0;
@@ -309,7 +338,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                                    200000000ull);
                 }
         }
-    } else if (warp == 1) {
+    };
+    auto mma_issuer = [&]() {
         if (lane == 0) {
             // ---------------------------------------------------- MMA issuer
             // Per segment (two K blocks): the correction products of both
@@ -416,13 +446,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             ptx::mma_commit(ptx::smem_u32(drain));
             ptx::mbar_wait(ptx::smem_u32(drain), 0u, err, 200000000ull);
         }
-    } else {
+    };
+    auto epilogue = [&]() {
         // -------------------------------------------------------- epilogue
         const int quarter = warp & 3;        // TMEM lanes this warp may access
-        const int half = (warp - 2) >> 2;    // which 64 trajectories of the tile
+        const int half = (warp - kE0) >> 2;  // which 64 trajectories of the tile
         const int row = quarter * 32 + lane; // A row of the tile = TMEM lane
         const bool im_row = (row & 1) != 0;  // odd A rows hold Im T_i.
-        const int et = threadIdx.x - 64;     // 0..255
+        const int et = threadIdx.x - 32 * kE0;  // 0..255
         const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
         uint32_t seg = 0;
         for (int tile = cluster; tile < ntiles; tile += nclusters) {
@@ -485,7 +516,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const size_t tcol = (size_t)st * 128 + half * 64 + g * 16;
                     float *dst = occ.p + (size_t)(lane & 1) * occ.plane +
                                  (size_t)(mt * 64 + (row >> 1)) * occ.ld + tcol;
-                    float *srow = ostage + (warp - 2) * kOccWarpFloats + lane * kOccRow;
+                    float *srow = ostage + (warp - kE0) * kOccWarpFloats + lane * kOccRow;
 #pragma unroll
                     for (int q4 = 0; q4 < 4; ++q4) {
                         float o[4];
@@ -505,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         // row, 8 rows per store instruction (instead of 32
                         // rows of 16 bytes)
                         __syncwarp();
-                        const float *wst = ostage + (warp - 2) * kOccWarpFloats;
+                        const float *wst = ostage + (warp - kE0) * kOccWarpFloats;
 #pragma unroll
                         for (int pass = 0; pass < 4; ++pass) {
                             const int sr = pass * 8 + (lane >> 2);  // producing lane
@@ -537,6 +568,39 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             named_bar_sync(1, kEpiThreads);
         }
+    };
+
+    if constexpr (kSamp) {
+        // The register reallocation comes first in each warpgroup-uniform
+        // branch (all warps of a warpgroup execute the same instruction,
+        // and it dominates the code that relies on it): warpgroups 1, 2
+        // are the epilogue; 0 (producer, MMA issuer, 2 sampler warps) and 3
+        // (4 sampler warps) give up registers.
+        const int wg = warp >> 2;
+        if (wg == 1 || wg == 2) {
+            ptx::setmaxnreg_inc<kRegsEpi>();
+            epilogue();
+        } else {
+            ptx::setmaxnreg_dec<kRegsRest>();
+            if (warp == 0) {
+                producer();
+            } else if (warp == 1) {
+                mma_issuer();
+            } else {
+                // ---------------------------------------------- sampler warps
+                // (2, 3, 12..15): the next chunk's operand, evict-first stores
+                const int sw = warp < 4 ? warp - 2 : warp - 10;
+                samp::sample_warps_bf16<true, true>(job, (int64_t)blockIdx.x * kSampWarps + sw,
+                                                    (int64_t)gridDim.x * kSampWarps, lane);
+            }
+        }
+    } else {
+        if (warp == 0)
+            producer();
+        else if (warp == 1)
+            mma_issuer();
+        else
+            epilogue();
     }
 
     ptx::tc_fence_before();
@@ -585,31 +649,55 @@ std::mutex g_tc_mu;
 bool g_attr_set[64] = {};
 std::map<std::tuple<int, int, int>, int> g_tune;  // (log2 N, log2 M, products) -> cluster size
 
+template <int P, int kCl, bool kSamp>
+cudaError_t set_smem_attr() {
+    return cudaFuncSetAttribute(k_gemm_tc<P, kCl, kSamp>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<P>());
+}
+
 int ensure_attrs() {
     int dev = 0;
     GBS_CUDA_TRY(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(g_tc_mu);
     if (dev >= 0 && dev < 64 && g_attr_set[dev]) return GBS_OK;
-    GBS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      smem_bytes<3>()));
-    GBS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      smem_bytes<3>()));
-    GBS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<6, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      smem_bytes<6>()));
-    GBS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<6, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      smem_bytes<6>()));
+    GBS_CUDA_TRY((set_smem_attr<3, 1, false>()));
+    GBS_CUDA_TRY((set_smem_attr<3, 2, false>()));
+    GBS_CUDA_TRY((set_smem_attr<6, 1, false>()));
+    GBS_CUDA_TRY((set_smem_attr<6, 2, false>()));
+    GBS_CUDA_TRY((set_smem_attr<3, 1, true>()));
+    GBS_CUDA_TRY((set_smem_attr<3, 2, true>()));
     if (dev >= 0 && dev < 64) g_attr_set[dev] = true;
     return GBS_OK;
 }
 
-template <int P, int kCl>
+// The sampling variant's register split holds only if every thread starts
+// with exactly kRegsLaunch registers: checked once per process from the
+// built kernels' attributes (otherwise the plain GEMM and sampler run).
+bool sampling_kernels_ok() {
+    static int state = -1;  // -1 unknown, 0 no, 1 yes
+    std::lock_guard<std::mutex> lock(g_tc_mu);
+    if (state < 0) {
+        cudaFuncAttributes a1 = {}, a2 = {};
+        const bool ok = cudaFuncGetAttributes(&a1, k_gemm_tc<3, 1, true>) == cudaSuccess &&
+                        cudaFuncGetAttributes(&a2, k_gemm_tc<3, 2, true>) == cudaSuccess &&
+                        a1.numRegs == kRegsLaunch && a2.numRegs == kRegsLaunch &&
+                        a1.maxThreadsPerBlock >= kSampThreads &&
+                        a2.maxThreadsPerBlock >= kSampThreads;
+        if (!ok) cudaGetLastError();
+        state = ok ? 1 : 0;
+    }
+    return state == 1;
+}
+
+template <int P, int kCl, bool kSamp>
 int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets, const int4 *d_tiles,
-                   int ntiles, int64_t count0, unsigned long long *err, OccOut occ) {
+                   int ntiles, int64_t count0, unsigned long long *err, OccOut occ,
+                   const SampleJob &job) {
     if (ntiles <= 0) return GBS_OK;
     const int clusters = std::max(1, std::min(ntiles, sm_count / kCl));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kCl * clusters);
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(threads_of<kSamp>());
     cfg.dynamicSmemBytes = smem_bytes<P>();
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
@@ -619,10 +707,11 @@ int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = kCl > 1 ? 1 : 0;
-    cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_tc<P, kCl>, d_nets, d_tiles, ntiles, count0, err, occ);
+    cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_tc<P, kCl, kSamp>, d_nets, d_tiles, ntiles,
+                                        count0, err, occ, job);
     if (le != cudaSuccess)
-        return set_error(GBS_ECUDA, "launch of the GEMM (%d products, cluster %d) failed: %s", P,
-                         kCl, cudaGetErrorString(le));
+        return set_error(GBS_ECUDA, "launch of the GEMM (%d products, cluster %d%s) failed: %s", P,
+                         kCl, kSamp ? ", sampling" : "", cudaGetErrorString(le));
     return GBS_OK;
 }
 
@@ -643,7 +732,7 @@ int encode_kblocked(CUtensorMap *map, void *base, uint64_t rows, uint64_t KB, ui
     return GBS_OK;
 }
 
-int encode_net_maps(gbs_net *net, GemmNetDesc &d) {
+int encode_net_maps(gbs_net *net, void *B, GemmNetDesc &d) {
     const int KB = net->ldK / 32;
     const size_t planeA = (size_t)net->rowsA * net->ldK;
     const int64_t tiles = (net->chunk + kTcTileSamples - 1) / kTcTileSamples;
@@ -654,7 +743,7 @@ int encode_net_maps(gbs_net *net, GemmNetDesc &d) {
         if ((rc = encode_kblocked(&d.mapA[q], net->d_A + q * planeA, (uint64_t)net->rowsA,
                                   (uint64_t)KB, 128)))
             return rc;
-        __nv_bfloat16 *bbase = static_cast<__nv_bfloat16 *>(net->d_B) +
+        __nv_bfloat16 *bbase = static_cast<__nv_bfloat16 *>(B) +
                                (q < net->planesB ? q : 0) * planeB;
         for (int c = 0; c < 2; ++c)
             if ((rc = encode_kblocked(&d.mapB[c][q], bbase, (uint64_t)rowsB, (uint64_t)KB,
@@ -686,11 +775,12 @@ int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int cluster,
     if ((rc = ensure_attrs())) return rc;
     if (occ.p && (d_tiles || occ.ld % 128 != 0 || occ.ld < count0))
         return set_error(GBS_EINVAL, "occupation output needs closed-form tiles and ld >= count, ld %% 128 == 0");
+    const SampleJob none;
     if (P == 3)
-        return cluster == 1 ? launch_variant<3, 1>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ)
-                            : launch_variant<3, 2>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ);
-    return cluster == 1 ? launch_variant<6, 1>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ)
-                        : launch_variant<6, 2>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ);
+        return cluster == 1 ? launch_variant<3, 1, false>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none)
+                            : launch_variant<3, 2, false>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none);
+    return cluster == 1 ? launch_variant<6, 1, false>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none)
+                        : launch_variant<6, 2, false>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none);
 }
 
 int tc_fill_desc(gbs_net *net, GemmNetDesc *out) {
@@ -707,7 +797,7 @@ int tc_plan_create(gbs_net *net) {
     net->tc = plan;
     plan->P = (net->precision == GBS_BF16X3) ? 3 : 6;
     int rc;
-    if ((rc = encode_net_maps(net, plan->desc))) return rc;
+    if ((rc = encode_net_maps(net, net->d_B, plan->desc))) return rc;
     GBS_CUDA_TRY(cudaMalloc(&plan->d_desc, sizeof(GemmNetDesc)));
     GBS_CUDA_TRY(cudaMemcpy(plan->d_desc, &plan->desc, sizeof(GemmNetDesc), cudaMemcpyHostToDevice));
     return GBS_OK;
@@ -715,6 +805,7 @@ int tc_plan_create(gbs_net *net) {
 
 void tc_plan_destroy(gbs_net *net) {
     if (net->tc && net->tc->d_desc) cudaFree(net->tc->d_desc);
+    if (net->tc && net->tc->d_desc_alt) cudaFree(net->tc->d_desc_alt);
     delete net->tc;
     net->tc = nullptr;
 }
@@ -786,22 +877,95 @@ int tc_autotune(gbs_net *net, int64_t count, int *out) {
     return GBS_OK;
 }
 
+namespace {
+
+int pick_cluster(gbs_net *net, int64_t count) {
+    TcPlan *plan = net->tc;
+    if (!plan->cluster) {
+        int c = 2, rc;
+        if ((rc = tc_autotune(net, count, &c))) return -rc;
+        plan->cluster = c;
+    }
+    return plan->cluster;
+}
+
+}  // namespace
+
 int launch_gemm_tc(gbs_net *net, int64_t count, OccOut occ) {
     if (count <= 0) return GBS_OK;
     TcPlan *plan = net->tc;
     if (!plan) return set_error(GBS_EINVAL, "no tensor-core plan");
     int rc;
     if ((rc = ensure_attrs())) return rc;
-    if (!plan->cluster) {
-        int c = 2;
-        if ((rc = tc_autotune(net, count, &c))) return rc;
-        plan->cluster = c;
-    }
-    const int cl = plan->cluster;
+    const int cl = pick_cluster(net, count);
+    if (cl < 0) return -cl;
     const int groups = (net->mtiles + cl - 1) / cl;
     const int stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
     return launch_gemm_grouped(net->stream, net->sm_count, plan->P, cl, plan->d_desc, nullptr,
                                groups * stiles, count, net->d_flags + 1, occ);
+}
+
+int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job) {
+    if (count <= 0) return GBS_OK;
+    TcPlan *plan = net->tc;
+    if (!plan || plan->P != 3 || !plan->d_desc_alt)
+        return set_error(GBS_EINVAL, "sampling GEMM needs a 3-product plan with a second operand");
+    int rc;
+    if ((rc = ensure_attrs())) return rc;
+    const int cl = pick_cluster(net, count);
+    if (cl < 0) return -cl;
+    const int groups = (net->mtiles + cl - 1) / cl;
+    const int stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
+    return cl == 1 ? launch_variant<3, 1, true>(net->stream, net->sm_count, plan->d_desc, nullptr,
+                                                groups * stiles, count, net->d_flags + 1, OccOut(), job)
+                   : launch_variant<3, 2, true>(net->stream, net->sm_count, plan->d_desc, nullptr,
+                                                groups * stiles, count, net->d_flags + 1, OccOut(), job);
+}
+
+bool tc_sampling_ready(gbs_net *net, bool allocate) {
+    TcPlan *plan = net->tc;
+    if (!plan || plan->P != 3 || !net->fuse_sampler || !net->d_B) return false;
+    if (ensure_attrs() != GBS_OK) {
+        cudaGetLastError();
+        return false;
+    }
+    if (!sampling_kernels_ok()) return false;
+    if (plan->d_desc_alt) return true;
+    if (!allocate) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(net->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return false;  // no allocation inside a capture
+    }
+    // the second operand and n[]; without room the plain path runs
+    void *B = nullptr;
+    double *n = nullptr;
+    GemmNetDesc *d = nullptr;
+    bool ok = cudaMalloc(&B, net->B_bytes) == cudaSuccess &&
+              cudaMalloc(&n, (size_t)net->chunk * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&d, sizeof(GemmNetDesc)) == cudaSuccess;
+    if (ok) ok = cudaMemset(B, 0, net->B_bytes) == cudaSuccess;  // padding rows and columns read as 0
+    if (ok) ok = encode_net_maps(net, B, plan->desc_alt) == GBS_OK;
+    if (ok) ok = cudaMemcpy(d, &plan->desc_alt, sizeof(GemmNetDesc), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (B) cudaFree(B);
+        if (n) cudaFree(n);
+        if (d) cudaFree(d);
+        return false;
+    }
+    net->d_B_alt = B;
+    net->d_n_alt = n;
+    plan->d_desc_alt = d;
+    return true;
+}
+
+void tc_swap_sample_buffers(gbs_net *net) {
+    TcPlan *plan = net->tc;
+    std::swap(net->d_B, net->d_B_alt);
+    std::swap(net->d_n, net->d_n_alt);
+    std::swap(plan->desc, plan->desc_alt);
+    std::swap(plan->d_desc, plan->d_desc_alt);
 }
 
 }  // namespace gbs
