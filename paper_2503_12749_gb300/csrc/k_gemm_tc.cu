@@ -121,21 +121,48 @@ constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(128, 256);
 constexpr int kEpiWarps = kEpiWarpsFwd;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
-// sampling variant
-constexpr int kSampThreads = 512;
-constexpr int kSampWarps = 6;
-constexpr int kRegsLaunch = 65536 / kSampThreads;  // 128
-constexpr int kRegsEpi = 168, kRegsRest = 88;
-static_assert(2 * 128 * kRegsEpi + 2 * 128 * kRegsRest == kSampThreads * kRegsLaunch,
-              "register split of the sampling GEMM");
-template <bool kSamp>
+// sampling variants: kSW warpgroups of sampler warps after the epilogue
+// (kSW = 0: the plain GEMM)
+template <int kSW>
 __host__ __device__ constexpr int threads_of() {
-    return kSamp ? kSampThreads : kThreads;
+    return kSW ? 128 * (3 + kSW) : kThreads;
 }
-template <bool kSamp>
+template <int kSW>
 __host__ __device__ constexpr int epi_warp0() {
-    return kSamp ? 4 : 2;
+    return kSW ? 4 : 2;
 }
+template <int kSW>
+__host__ __device__ constexpr int sampler_warps() {
+    return kSW ? 2 + 4 * kSW : 0;
+}
+// registers per thread at launch (the CTA's 65,536 at most, in units of 8)
+template <int kSW>
+__host__ __device__ constexpr int regs_launch() {
+    return (65536 / threads_of<kSW>()) / 8 * 8;
+}
+constexpr int kRegsEpi = 168;
+// what the warpgroups other than the two epilogue ones keep
+template <int kSW>
+__host__ __device__ constexpr int regs_rest() {
+    return (threads_of<kSW>() * regs_launch<kSW>() - 256 * kRegsEpi) / (threads_of<kSW>() - 256) /
+           8 * 8;
+}
+static_assert(regs_launch<1>() == 128 && regs_rest<1>() == 88, "register split, 6 sampler warps");
+static_assert(regs_launch<2>() == 96 && regs_rest<2>() == 48, "register split, 10 sampler warps");
+static_assert(256 * kRegsEpi + (threads_of<1>() - 256) * regs_rest<1>() <=
+                  threads_of<1>() * regs_launch<1>(), "register pool, 6 sampler warps");
+static_assert(256 * kRegsEpi + (threads_of<2>() - 256) * regs_rest<2>() <=
+                  threads_of<2>() * regs_launch<2>(), "register pool, 10 sampler warps");
+// The sampling GEMM's sampler warps: kSampWG warpgroups after the
+// epilogue, plus warps 2 and 3 when kSampWG0; within a CTA's range of
+// trajectories the warps take fixed strides (kSampDyn = false) or the next
+// trajectory from a shared counter.  The sampler's issue slots come out of
+// the epilogue's, so the fewest warps that still finish within the GEMM
+// are best.
+constexpr int kSampWG = 1;
+constexpr bool kSampWG0 = true;
+constexpr bool kSampDyn = false;
+constexpr int kSampWarpsUsed = 4 * kSampWG + (kSampWG0 ? 2 : 0);
 
 // A tile of the grouped GEMM: which network, which group of kCl mode
 // tiles, which 128-trajectory tile.
@@ -209,12 +236,12 @@ __device__ __forceinline__ void warp_transpose_reduce32(float (&v)[32], int lane
     }
 }
 
-template <int P, int kCl, bool kSamp>
-__global__ void __launch_bounds__(threads_of<kSamp>(), 1)
+template <int P, int kCl, int kSW>
+__global__ void __launch_bounds__(threads_of<kSW>(), 1)
     k_gemm_tc(const GemmNetDesc *__restrict__ nets, const int4 *__restrict__ tiles, int ntiles,
               int64_t count0, unsigned long long *err_ptr, OccOut occ, const SampleJob job) {
-    static_assert(!kSamp || P == 3, "the sampling variant runs the 3-product GEMM");
-    constexpr int kE0 = epi_warp0<kSamp>();  // first epilogue warp
+    static_assert(kSW == 0 || P == 3, "the sampling variant runs the 3-product GEMM");
+    constexpr int kE0 = epi_warp0<kSW>();  // first epilogue warp
     using C = Cfg<P>;
     constexpr int kStages = C::kStages;
     constexpr int kPl = C::kPlanes;
@@ -235,6 +262,7 @@ __global__ void __launch_bounds__(threads_of<kSamp>(), 1)
     uint64_t *tempty = bars + 2 * kStages + 2;
     uint64_t *drain = bars + 2 * kStages + 4;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 5);
+    uint32_t *samp_next = tmem_slot + 1;  // next trajectory of the CTA's sampler range
     float *red = reinterpret_cast<float *>(smem + kStages * C::kStageBytes + kBarBytes);
     float *ostage = reinterpret_cast<float *>(smem + kStages * C::kStageBytes + kBarBytes + kRedBytes);
 
@@ -256,6 +284,7 @@ __global__ void __launch_bounds__(threads_of<kSamp>(), 1)
             ptx::mbar_init(ptx::smem_u32(&tempty[b]), kEpiThreads);
         }
         ptx::mbar_init(ptx::smem_u32(drain), 1);
+        *samp_next = 0u;
         ptx::fence_barrier_init();
     }
     if (warp == 1) {
@@ -570,28 +599,42 @@ __global__ void __launch_bounds__(threads_of<kSamp>(), 1)
         }
     };
 
-    if constexpr (kSamp) {
+    if constexpr (kSW > 0) {
         // The register reallocation comes first in each warpgroup-uniform
         // branch (all warps of a warpgroup execute the same instruction,
         // and it dominates the code that relies on it): warpgroups 1, 2
-        // are the epilogue; 0 (producer, MMA issuer, 2 sampler warps) and 3
-        // (4 sampler warps) give up registers.
+        // are the epilogue; 0 (producer, MMA issuer, 2 sampler warps) and
+        // 3.. (sampler warps) give up registers.
         const int wg = warp >> 2;
         if (wg == 1 || wg == 2) {
             ptx::setmaxnreg_inc<kRegsEpi>();
             epilogue();
         } else {
-            ptx::setmaxnreg_dec<kRegsRest>();
+            ptx::setmaxnreg_dec<regs_rest<kSW>()>();
             if (warp == 0) {
                 producer();
             } else if (warp == 1) {
                 mma_issuer();
-            } else {
+            } else if (warp >= 12 || kSampWG0) {
                 // ---------------------------------------------- sampler warps
-                // (2, 3, 12..15): the next chunk's operand, evict-first stores
-                const int sw = warp < 4 ? warp - 2 : warp - 10;
-                samp::sample_warps_bf16<true, true>(job, (int64_t)blockIdx.x * kSampWarps + sw,
-                                                    (int64_t)gridDim.x * kSampWarps, lane);
+                // (2, 3, 12..): the next chunk's operand, evict-first stores;
+                // each CTA samples a contiguous range of the job
+                const int sw = warp < 4 ? warp - 2 : warp - 12 + (kSampWG0 ? 2 : 0);
+                const int64_t lo = job.count * (int64_t)blockIdx.x / gridDim.x;
+                const int64_t hi = job.count * ((int64_t)blockIdx.x + 1) / gridDim.x;
+                if (kSampDyn) {
+                    for (;;) {
+                        uint32_t idx = 0;
+                        if (lane == 0) idx = atomicAdd(samp_next, 1u);
+                        idx = __shfl_sync(0xffffffffu, idx, 0);
+                        const int64_t i = lo + (int64_t)idx;
+                        if (i >= hi) break;
+                        samp::sample_trajectory_bf16<true, true>(job, i, lane);
+                    }
+                } else {
+                    for (int64_t i = lo + sw; i < hi; i += kSampWarpsUsed)
+                        samp::sample_trajectory_bf16<true, true>(job, i, lane);
+                }
             }
         }
     } else {
@@ -649,9 +692,9 @@ std::mutex g_tc_mu;
 bool g_attr_set[64] = {};
 std::map<std::tuple<int, int, int>, int> g_tune;  // (log2 N, log2 M, products) -> cluster size
 
-template <int P, int kCl, bool kSamp>
+template <int P, int kCl, int kSW>
 cudaError_t set_smem_attr() {
-    return cudaFuncSetAttribute(k_gemm_tc<P, kCl, kSamp>,
+    return cudaFuncSetAttribute(k_gemm_tc<P, kCl, kSW>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<P>());
 }
 
@@ -660,36 +703,36 @@ int ensure_attrs() {
     GBS_CUDA_TRY(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(g_tc_mu);
     if (dev >= 0 && dev < 64 && g_attr_set[dev]) return GBS_OK;
-    GBS_CUDA_TRY((set_smem_attr<3, 1, false>()));
-    GBS_CUDA_TRY((set_smem_attr<3, 2, false>()));
-    GBS_CUDA_TRY((set_smem_attr<6, 1, false>()));
-    GBS_CUDA_TRY((set_smem_attr<6, 2, false>()));
-    GBS_CUDA_TRY((set_smem_attr<3, 1, true>()));
-    GBS_CUDA_TRY((set_smem_attr<3, 2, true>()));
+    GBS_CUDA_TRY((set_smem_attr<3, 1, 0>()));
+    GBS_CUDA_TRY((set_smem_attr<3, 2, 0>()));
+    GBS_CUDA_TRY((set_smem_attr<6, 1, 0>()));
+    GBS_CUDA_TRY((set_smem_attr<6, 2, 0>()));
+    GBS_CUDA_TRY((set_smem_attr<3, 1, kSampWG>()));
+    GBS_CUDA_TRY((set_smem_attr<3, 2, kSampWG>()));
     if (dev >= 0 && dev < 64) g_attr_set[dev] = true;
     return GBS_OK;
 }
 
 // The sampling variant's register split holds only if every thread starts
-// with exactly kRegsLaunch registers: checked once per process from the
+// with exactly regs_launch() registers: checked once per process from the
 // built kernels' attributes (otherwise the plain GEMM and sampler run).
 bool sampling_kernels_ok() {
     static int state = -1;  // -1 unknown, 0 no, 1 yes
     std::lock_guard<std::mutex> lock(g_tc_mu);
     if (state < 0) {
         cudaFuncAttributes a1 = {}, a2 = {};
-        const bool ok = cudaFuncGetAttributes(&a1, k_gemm_tc<3, 1, true>) == cudaSuccess &&
-                        cudaFuncGetAttributes(&a2, k_gemm_tc<3, 2, true>) == cudaSuccess &&
-                        a1.numRegs == kRegsLaunch && a2.numRegs == kRegsLaunch &&
-                        a1.maxThreadsPerBlock >= kSampThreads &&
-                        a2.maxThreadsPerBlock >= kSampThreads;
+        constexpr int R = regs_launch<kSampWG>(), T = threads_of<kSampWG>();
+        const bool ok = cudaFuncGetAttributes(&a1, k_gemm_tc<3, 1, kSampWG>) == cudaSuccess &&
+                        cudaFuncGetAttributes(&a2, k_gemm_tc<3, 2, kSampWG>) == cudaSuccess &&
+                        a1.numRegs == R && a2.numRegs == R && a1.maxThreadsPerBlock >= T &&
+                        a2.maxThreadsPerBlock >= T;
         if (!ok) cudaGetLastError();
         state = ok ? 1 : 0;
     }
     return state == 1;
 }
 
-template <int P, int kCl, bool kSamp>
+template <int P, int kCl, int kSW>
 int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets, const int4 *d_tiles,
                    int ntiles, int64_t count0, unsigned long long *err, OccOut occ,
                    const SampleJob &job) {
@@ -697,7 +740,7 @@ int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets,
     const int clusters = std::max(1, std::min(ntiles, sm_count / kCl));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kCl * clusters);
-    cfg.blockDim = dim3(threads_of<kSamp>());
+    cfg.blockDim = dim3(threads_of<kSW>());
     cfg.dynamicSmemBytes = smem_bytes<P>();
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
@@ -707,11 +750,11 @@ int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = kCl > 1 ? 1 : 0;
-    cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_tc<P, kCl, kSamp>, d_nets, d_tiles, ntiles,
+    cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_tc<P, kCl, kSW>, d_nets, d_tiles, ntiles,
                                         count0, err, occ, job);
     if (le != cudaSuccess)
         return set_error(GBS_ECUDA, "launch of the GEMM (%d products, cluster %d%s) failed: %s", P,
-                         kCl, kSamp ? ", sampling" : "", cudaGetErrorString(le));
+                         kCl, kSW ? ", sampling" : "", cudaGetErrorString(le));
     return GBS_OK;
 }
 
@@ -777,10 +820,10 @@ int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int cluster,
         return set_error(GBS_EINVAL, "occupation output needs closed-form tiles and ld >= count, ld %% 128 == 0");
     const SampleJob none;
     if (P == 3)
-        return cluster == 1 ? launch_variant<3, 1, false>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none)
-                            : launch_variant<3, 2, false>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none);
-    return cluster == 1 ? launch_variant<6, 1, false>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none)
-                        : launch_variant<6, 2, false>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none);
+        return cluster == 1 ? launch_variant<3, 1, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none)
+                            : launch_variant<3, 2, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none);
+    return cluster == 1 ? launch_variant<6, 1, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none)
+                        : launch_variant<6, 2, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none);
 }
 
 int tc_fill_desc(gbs_net *net, GemmNetDesc *out) {
@@ -916,9 +959,9 @@ int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job) {
     if (cl < 0) return -cl;
     const int groups = (net->mtiles + cl - 1) / cl;
     const int stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
-    return cl == 1 ? launch_variant<3, 1, true>(net->stream, net->sm_count, plan->d_desc, nullptr,
+    return cl == 1 ? launch_variant<3, 1, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
                                                 groups * stiles, count, net->d_flags + 1, OccOut(), job)
-                   : launch_variant<3, 2, true>(net->stream, net->sm_count, plan->d_desc, nullptr,
+                   : launch_variant<3, 2, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
                                                 groups * stiles, count, net->d_flags + 1, OccOut(), job);
 }
 

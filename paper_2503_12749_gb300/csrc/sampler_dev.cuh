@@ -96,77 +96,81 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16 &h0, __nv_bfloat16
     h2 = __float2bfloat16_rn(r2);
 }
 
-// Trajectories warp, warp + nwarps, ... of the job, one warp each (lanes
-// stride over input modes, 4 modes per lane and step).  Layout written: per
-// 128-trajectory tile, 256 rows (128 alpha rows, then 128 beta rows); planes
-// B0 = bf16(x), B1 = bf16(x - B0), B2 = bf16(x - B0 - B1) stored
-// plane-major, each plane K-blocked [ldK / 32][rows][32] (mode j of row q at
-// ((j / 32) * rows + q) * 32 + j % 32); n_e = sum_j alpha_j beta_j
-// (Kahan-compensated FP32 partials per lane, summed in FP64).  kSfu: the
-// 2-plane (3-product) operand, SFU ln and sin/cos.  kStream: stores that L2
-// evicts first (the operand is read again only by the next GEMM).
+// Trajectory i of the job by one warp (lanes stride over input modes, 4
+// modes per lane and step).  Layout written: per 128-trajectory tile, 256
+// rows (128 alpha rows, then 128 beta rows); planes B0 = bf16(x), B1 =
+// bf16(x - B0), B2 = bf16(x - B0 - B1) stored plane-major, each plane
+// K-blocked [ldK / 32][rows][32] (mode j of row q at ((j / 32) * rows + q) *
+// 32 + j % 32); n_e = sum_j alpha_j beta_j (Kahan-compensated FP32 partials
+// per lane, summed in FP64).  kSfu: the 2-plane (3-product) operand, SFU ln
+// and sin/cos.  kStream: stores that L2 evicts first (the operand is read
+// again only by the next GEMM).
+template <bool kSfu, bool kStream>
+__device__ __forceinline__ void sample_trajectory_bf16(const SampleJob &jb, int64_t i, int lane) {
+    const int planes = kSfu ? 2 : jb.planesB;
+    const uint64_t e = jb.e0 + (uint64_t)i;
+    const int64_t tile = i >> 7;
+    const int q = (int)(i & 127);
+    const size_t row_a = (size_t)(tile * 256 + q) * 32;
+    const size_t row_b = (size_t)(tile * 256 + 128 + q) * 32;
+    float s = 0.0f, comp = 0.0f;
+    for (int j0 = 4 * lane; j0 < jb.N; j0 += 128) {
+        __align__(8) __nv_bfloat16 a0[4], a1[4], a2[4], b0[4], b1[4], b2[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int j = j0 + t;
+            float a = 0.0f, b = 0.0f;
+            if (j < jb.N) {
+                float w1, w2;
+                if (kSfu)
+                    normals_fp32_sfu(jb.seed, e, (uint32_t)j, w1, w2);
+                else
+                    normals_fp32(jb.seed, e, (uint32_t)j, w1, w2);
+                const float2 c = jb.sq[j];
+                a = fmaf(c.x, w1, c.y * w2);
+                b = fmaf(c.x, w1, -c.y * w2);
+                const float y = fmaf(a, b, -comp);
+                const float tsum = s + y;
+                comp = (tsum - s) - y;
+                s = tsum;
+            }
+            split3(a, a0[t], a1[t], a2[t]);
+            split3(b, b0[t], b1[t], b2[t]);
+        }
+        if (j0 + 3 < jb.ldK) {
+            // ldK is a multiple of 32 and j0 of 4: the 4 modes lie in one
+            // K block, 8-byte aligned
+            const size_t blk = (size_t)(j0 >> 5) * jb.rows * 32 + (size_t)(j0 & 31);
+            const size_t oa = blk + row_a, ob = blk + row_b;
+            auto put = [&](size_t o, const __nv_bfloat16 *v) {
+                const uint2 w = *reinterpret_cast<const uint2 *>(v);
+                uint2 *p = reinterpret_cast<uint2 *>(jb.B + o);
+                if (kStream) __stcs(p, w);
+                else *p = w;
+            };
+            put(oa, a0);
+            put(ob, b0);
+            if (planes > 1) {
+                put(jb.plane_stride + oa, a1);
+                put(jb.plane_stride + ob, b1);
+            }
+            if (planes > 2) {
+                put(2 * jb.plane_stride + oa, a2);
+                put(2 * jb.plane_stride + ob, b2);
+            }
+        }
+    }
+    double part = (double)s - (double)comp;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if (lane == 0) jb.n_out[i] = part;
+}
+
+// Trajectories warp, warp + nwarps, ... of the job, one warp each.
 template <bool kSfu, bool kStream>
 __device__ __forceinline__ void sample_warps_bf16(const SampleJob &jb, int64_t warp, int64_t nwarps,
                                                   int lane) {
-    const int planes = kSfu ? 2 : jb.planesB;
-    for (int64_t i = warp; i < jb.count; i += nwarps) {
-        const uint64_t e = jb.e0 + (uint64_t)i;
-        const int64_t tile = i >> 7;
-        const int q = (int)(i & 127);
-        const size_t row_a = (size_t)(tile * 256 + q) * 32;
-        const size_t row_b = (size_t)(tile * 256 + 128 + q) * 32;
-        float s = 0.0f, comp = 0.0f;
-        for (int j0 = 4 * lane; j0 < jb.N; j0 += 128) {
-            __align__(8) __nv_bfloat16 a0[4], a1[4], a2[4], b0[4], b1[4], b2[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int j = j0 + t;
-                float a = 0.0f, b = 0.0f;
-                if (j < jb.N) {
-                    float w1, w2;
-                    if (kSfu)
-                        normals_fp32_sfu(jb.seed, e, (uint32_t)j, w1, w2);
-                    else
-                        normals_fp32(jb.seed, e, (uint32_t)j, w1, w2);
-                    const float2 c = jb.sq[j];
-                    a = fmaf(c.x, w1, c.y * w2);
-                    b = fmaf(c.x, w1, -c.y * w2);
-                    const float y = fmaf(a, b, -comp);
-                    const float tsum = s + y;
-                    comp = (tsum - s) - y;
-                    s = tsum;
-                }
-                split3(a, a0[t], a1[t], a2[t]);
-                split3(b, b0[t], b1[t], b2[t]);
-            }
-            if (j0 + 3 < jb.ldK) {
-                // ldK is a multiple of 32 and j0 of 4: the 4 modes lie in one
-                // K block, 8-byte aligned
-                const size_t blk = (size_t)(j0 >> 5) * jb.rows * 32 + (size_t)(j0 & 31);
-                const size_t oa = blk + row_a, ob = blk + row_b;
-                auto put = [&](size_t o, const __nv_bfloat16 *v) {
-                    const uint2 w = *reinterpret_cast<const uint2 *>(v);
-                    uint2 *p = reinterpret_cast<uint2 *>(jb.B + o);
-                    if (kStream) __stcs(p, w);
-                    else *p = w;
-                };
-                put(oa, a0);
-                put(ob, b0);
-                if (planes > 1) {
-                    put(jb.plane_stride + oa, a1);
-                    put(jb.plane_stride + ob, b1);
-                }
-                if (planes > 2) {
-                    put(2 * jb.plane_stride + oa, a2);
-                    put(2 * jb.plane_stride + ob, b2);
-                }
-            }
-        }
-        double part = (double)s - (double)comp;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-        if (lane == 0) jb.n_out[i] = part;
-    }
+    for (int64_t i = warp; i < jb.count; i += nwarps) sample_trajectory_bf16<kSfu, kStream>(jb, i, lane);
 }
 
 }  // namespace samp
