@@ -153,6 +153,8 @@ void release_all(gbs_net *net) {
     dev_free(net->d_nS_part);
     dev_free(net->d_nS);
     dev_free(net->d_win);
+    if (net->d_gfrec) cudaFree(net->d_gfrec);
+    net->d_gfrec = nullptr;
     dev_free(net->d_wmax);
     dev_free(net->d_flags);
     dev_free(net->d_nS2);
@@ -548,6 +550,11 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
     if (cudaMemset(net->d_flags, 0, 4 * sizeof(unsigned long long)) != cudaSuccess)
         return fail(set_error(GBS_ECUDA, "memset of flags failed"));
     if (precision != GBS_FP64) {
+        if (cudaMalloc(&net->d_gfrec, (size_t)net->chunk * gf_record_bytes()) != cudaSuccess) {
+            net->d_gfrec = nullptr;
+            cudaGetLastError();
+            return fail(set_error(GBS_ENOMEM, "cudaMalloc(generating-function records) failed"));
+        }
         if ((rc = tc_plan_create(net))) return fail(rc);
     }
     *out = net;

@@ -155,6 +155,7 @@ struct gbs_net {
     int mtiles = 0;
     double2 *d_nS = nullptr;        // [chunk]
     gbs::Window *d_win = nullptr;   // [chunk]
+    void *d_gfrec = nullptr;        // [chunk] generating-function records (BF16 paths)
     int *d_wmax = nullptr;          // [2]: union of the chunk's windows (max w1, max w2)
 
     // estimator state
@@ -239,6 +240,9 @@ int launch_finalize(gbs_net *net, int64_t count);
 
 // Generating functions, summed per sub-ensemble into d_acc.
 int launch_gf(gbs_net *net, uint64_t e0, int64_t count);
+// Bytes per trajectory of the records the finalize kernel writes for the
+// double-float generating functions (d_gfrec).
+size_t gf_record_bytes();
 
 // Twiddle tables for K1 points.
 int launch_tables(gbs_net *net);

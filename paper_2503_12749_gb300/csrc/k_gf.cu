@@ -16,11 +16,13 @@
 // theta = pi for the e^{-l1} term) outside which each term is provably
 // smaller than 2^-60, using |sin theta| <= sqrt(2 (1 - cos theta)).
 //
-// Work split: one thread per k, one block per (256 consecutive k,
-// sub-ensemble r); each thread loops over the sub-ensemble's trajectories of
-// the chunk in increasing order and adds its sums to acc[est][r][k], so every
-// sum is formed in a fixed order (bitwise reproducible for a fixed chunking).
-// Trajectory e belongs to sub-ensemble e mod n_sub.
+// Work split (FP64 kernel): one thread per k, one block per (256
+// consecutive k, sub-ensemble r); each thread loops over the sub-ensemble's
+// trajectories of the chunk in increasing order and adds its sums to
+// acc[est][r][k], so every sum is formed in a fixed order (bitwise
+// reproducible for a fixed chunking).  The double-float kernel splits each
+// k's trajectories over 4 warps (see k_gf_df).  Trajectory e belongs to
+// sub-ensemble e mod n_sub.
 #include "gbs_internal.cuh"
 #include "dfloat.cuh"
 
@@ -70,10 +72,21 @@ __device__ __forceinline__ Window windows_for(double n, double x, double y, int 
     return w;
 }
 
+// Per-trajectory constants of the double-float generating functions:
+// n_S = x + i y, c1 = min(0, 2n), c2 = -2 max(n, 0), 1 / (1 + e^{-2|n|}) as
+// double-float, the FP64 values for the pairs outside the double-float
+// ranges, and the windows.
+struct __align__(16) GfRec {
+    double xd, yd, c1d, c2d;
+    df x, y, c1, c2, inv;
+    int w1, w2;
+};
+static_assert(sizeof(GfRec) == 80, "generating-function record layout");
+
 __global__ void k_finalize(const double2 *__restrict__ part, int mtiles, int64_t ld,
                            const double *__restrict__ n, int64_t count, int K1,
                            double2 *__restrict__ nS, Window *__restrict__ win,
-                           int *__restrict__ wmax) {
+                           int *__restrict__ wmax, GfRec *__restrict__ rec) {
     int m1 = -1, m2 = -1;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -84,8 +97,24 @@ __global__ void k_finalize(const double2 *__restrict__ part, int mtiles, int64_t
             im += p.y;
         }
         nS[i] = make_double2(re, im);
-        const Window w = windows_for(n[i], re, im, K1);
+        const double nn = n[i];
+        const Window w = windows_for(nn, re, im, K1);
         win[i] = w;
+        if (rec) {
+            GfRec g;
+            g.xd = re;
+            g.yd = im;
+            g.c1d = fmin(0.0, 2.0 * nn);
+            g.c2d = -2.0 * fmax(nn, 0.0);
+            g.x = df_from_double(re);
+            g.y = df_from_double(im);
+            g.c1 = df_from_double(g.c1d);
+            g.c2 = df_from_double(g.c2d);
+            g.inv = df_from_double(1.0 / (1.0 + exp(-2.0 * fabs(nn))));
+            g.w1 = w.w1;
+            g.w2 = w.w2;
+            rec[i] = g;
+        }
         m1 = max(m1, w.w1);
         m2 = max(m2, w.w2);
     }
@@ -222,114 +251,126 @@ __device__ __forceinline__ int slot_to_k(int i, int K1, int W1, int W2) {
     return -1;
 }
 
-constexpr int kGfSlots = 128;   // k slots per block
-constexpr int kGfGroups = 4;    // trajectory groups per block (warps per slot range: 4 x 4)
-constexpr int kGfTile = 128;    // trajectories staged in shared memory per tile
+constexpr int kGfSlots = 32;   // k slots per block (the lanes of each warp)
+constexpr int kGfGroups = 4;   // trajectory groups per block, one warp each
+constexpr int kGfTile = 128;   // trajectories per flush of the double-float partials
 
-__global__ void __launch_bounds__(kGfSlots * kGfGroups, 1)
-    k_gf_df(const double *__restrict__ n_in, const double2 *__restrict__ nS_in,
-            const Window *__restrict__ win_in, const int *__restrict__ wmax, int64_t count,
+// Slot blocks of the union window in order of distance from the block
+// holding k = 0 (ties: the lower first): the blocks near k = 0 carry a term
+// for every trajectory, the outer ones only for the trajectories with the
+// widest windows.  Returns the y-th block, or -1 past the last.
+__device__ __forceinline__ int slot_block(int y, int K1, int W1, int W2) {
+    const int half = K1 >> 1;
+    const int n1 = W1 >= half ? K1 : 2 * W1 + 1;
+    const int n2 = W2 < 0 ? 0 : (W2 >= half ? K1 : 2 * W2 + 1);
+    const int slots = (n1 + n2 >= K1) ? K1 : n1 + n2;
+    const int nb = (slots + kGfSlots - 1) / kGfSlots;
+    if (y >= nb) return -1;
+    const int cb = (n1 + n2 >= K1) ? 0 : min(W1 / kGfSlots, nb - 1);
+    int cnt = 0;
+    for (int d = 0; d < nb; ++d) {
+        if (cb - d >= 0) {
+            if (cnt == y) return cb - d;
+            ++cnt;
+        }
+        if (d > 0 && cb + d < nb) {
+            if (cnt == y) return cb + d;
+            ++cnt;
+        }
+    }
+    return -1;
+}
+
+// One block per (32 consecutive slots of the union window, sub-ensemble r):
+// the 4 warps hold the same 32 k and split the sub-ensemble's trajectories
+// (trajectory q to warp q mod 4), so they carry the same work and need no
+// barrier until the final fixed-order sum of their 4 partials.  Each warp
+// stages its own 32 trajectories of a 128-trajectory tile (records written
+// by the finalize kernel) and walks them in order, flushing its
+// double-float partials to FP64 after each tile.  Grid: x = sub-ensemble
+// (fast), y = slot block from the window's centre outwards, so the
+// heaviest blocks start first and the last wave holds the lightest.
+__global__ void __launch_bounds__(kGfSlots * kGfGroups, 4)
+    k_gf_df(const GfRec *__restrict__ rec, const int *__restrict__ wmax, int64_t count,
             uint64_t e0, int n_sub, int K1, const double2 *__restrict__ tw, const DfConsts K,
             double2 *__restrict__ acc, int64_t *__restrict__ counts) {
-    __shared__ df s_x[kGfTile], s_y[kGfTile], s_c1[kGfTile], s_c2[kGfTile], s_inv[kGfTile];
-    __shared__ double s_xd[kGfTile], s_yd[kGfTile], s_c1d[kGfTile], s_c2d[kGfTile];
-    __shared__ int s_w1[kGfTile], s_w2[kGfTile];
+    __shared__ GfRec s_rec[kGfGroups][32];
     __shared__ double s_red[kGfGroups][4][kGfSlots];
     __shared__ DfTables s_tab;
 
-    const int r = blockIdx.y;
+    const int r = blockIdx.x;
     const int W1 = wmax[0], W2 = wmax[1];
-    const int slot = threadIdx.x % kGfSlots;
-    const int grp = threadIdx.x / kGfSlots;
-    const int k = slot_to_k(blockIdx.x * kGfSlots + slot, K1, W1, W2);
-    const int first_k = slot_to_k(blockIdx.x * kGfSlots, K1, W1, W2);
-    if (first_k < 0) {  // the block lies past the union window: nothing to add
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            const int64_t f = (int64_t)(((uint64_t)r + (uint64_t)n_sub - e0 % (uint64_t)n_sub) %
-                                        (uint64_t)n_sub);
-            counts[r] += f < count ? (count - 1 - f) / n_sub + 1 : 0;
-        }
-        return;
-    }
-    const bool kvalid = k >= 0;
-    const int d0 = kvalid ? dist0(k, K1) : 0x3fffffff;
-    const int dpi = kvalid ? dist_pi(k, K1) : 0x3fffffff;
-    if (threadIdx.x < 64) s_tab.exp2[threadIdx.x] = df{K.exp2_hi[threadIdx.x], K.exp2_lo[threadIdx.x]};
-    if (threadIdx.x < 33) {
-        s_tab.sn[threadIdx.x] = df{K.sin_hi[threadIdx.x], K.sin_lo[threadIdx.x]};
-        s_tab.cs[threadIdx.x] = df{K.cos_hi[threadIdx.x], K.cos_lo[threadIdx.x]};
-    }  // visible after the first __syncthreads of the tile loop
-
+    const int lane = threadIdx.x & 31;
+    const int grp = threadIdx.x >> 5;
     const int64_t first = (int64_t)(((uint64_t)r + (uint64_t)n_sub - e0 % (uint64_t)n_sub) %
                                     (uint64_t)n_sub);
     const int64_t cnt_r = first < count ? (count - 1 - first) / n_sub + 1 : 0;
+    const int sb = slot_block(blockIdx.y, K1, W1, W2);
+    if (sb < 0) return;  // past the union window (block 0 always exists)
+    const int k = slot_to_k(sb * kGfSlots + lane, K1, W1, W2);
+    const bool kvalid = k >= 0;
+    const int d0 = kvalid ? dist0(k, K1) : 0x3fffffff;
+    const int dpi = kvalid ? dist_pi(k, K1) : 0x3fffffff;
+    for (int t = threadIdx.x; t < 64; t += blockDim.x)
+        s_tab.exp2[t] = df{K.exp2_hi[t], K.exp2_lo[t]};
+    for (int t = threadIdx.x; t < 33; t += blockDim.x) {
+        s_tab.sn[t] = df{K.sin_hi[t], K.sin_lo[t]};
+        s_tab.cs[t] = df{K.cos_hi[t], K.cos_lo[t]};
+    }
+    __syncthreads();
 
     const double2 t = kvalid ? tw[k] : make_double2(0.0, 0.0);
     const double cm1d = t.x, snd = t.y;
     const df cm1 = df_from_double(t.x), sn = df_from_double(t.y);
     double am_re = 0.0, am_im = 0.0, ap_re = 0.0, ap_im = 0.0;
+    GfRec *mine = s_rec[grp];
 
     for (int64_t base = 0; base < cnt_r; base += kGfTile) {
-        const int64_t q = base + threadIdx.x;
-        if (threadIdx.x < kGfTile && q < cnt_r) {
-            const int64_t i = first + q * n_sub;
-            const double nn = n_in[i];
-            const double2 sv = nS_in[i];
-            const Window w = win_in[i];
-            const double c1 = fmin(0.0, 2.0 * nn), c2 = -2.0 * fmax(nn, 0.0);
-            s_x[threadIdx.x] = df_from_double(sv.x);
-            s_y[threadIdx.x] = df_from_double(sv.y);
-            s_c1[threadIdx.x] = df_from_double(c1);
-            s_c2[threadIdx.x] = df_from_double(c2);
-            s_inv[threadIdx.x] = df_from_double(1.0 / (1.0 + exp(-2.0 * fabs(nn))));
-            s_xd[threadIdx.x] = sv.x;
-            s_yd[threadIdx.x] = sv.y;
-            s_c1d[threadIdx.x] = c1;
-            s_c2d[threadIdx.x] = c2;
-            s_w1[threadIdx.x] = w.w1;
-            s_w2[threadIdx.x] = w.w2;
-        }
-        __syncthreads();
+        const int64_t q = base + grp + 4 * lane;
+        if (q < cnt_r) mine[lane] = rec[first + q * n_sub];
+        __syncwarp();
         const int ntile = (cnt_r - base) < kGfTile ? (int)(cnt_r - base) : kGfTile;
+        const int nmine = ntile > grp ? (ntile - grp + kGfGroups - 1) / kGfGroups : 0;
         if (kvalid) {
             df pm_re = {0.0f, 0.0f}, pm_im = {0.0f, 0.0f}, pp_re = {0.0f, 0.0f},
                pp_im = {0.0f, 0.0f};
-            for (int j = grp; j < ntile; j += kGfGroups) {
-                const bool in1 = d0 <= s_w1[j];
-                const bool in2 = dpi <= s_w2[j];
+            for (int m = 0; m < nmine; ++m) {
+                const GfRec &g = mine[m];
+                const bool in1 = d0 <= g.w1;
+                const bool in2 = dpi <= g.w2;
                 if (!(in1 || in2)) continue;
-                const df x = s_x[j], y = s_y[j];
+                const df x = g.x, y = g.y;
                 const df l1 = df_sub(df_mul(cm1, x), df_mul(sn, y));  // (cos-1) x - sin y
                 const df ph = df_add(df_mul(sn, x), df_mul(cm1, y));  // sin x + (cos-1) y
-                const df c1 = s_c1[j];
+                const df c1 = g.c1;
                 const df a1 = df_add(l1, c1);
-                const df a2 = df_add(df_neg(l1), s_c2[j]);
+                const df a2 = df_add(df_neg(l1), g.c2);
                 const bool big = fabsf(ph.hi) >= 6000.0f ||
                                  (in1 && (a1.hi >= 80.0f || l1.hi >= 80.0f)) ||
                                  (in2 && a2.hi >= 80.0f);
                 if (big) {
                     // outside the double-float ranges (+P heavy tail, huge
                     // phases): this pair in FP64, straight into the FP64 sums
-                    const double xd = s_xd[j], yd = s_yd[j];
+                    const double xd = g.xd, yd = g.yd;
                     const double l1d = cm1d * xd - snd * yd;
                     double sd, cd;
                     sincos(snd * xd + cm1d * yd, &sd, &cd);
                     double e1d = 0.0, e2d = 0.0;
                     if (in1) {
-                        e1d = exp(l1d + s_c1d[j]);
-                        const double gp = (s_c1d[j] == 0.0) ? e1d : exp(l1d);
+                        e1d = exp(l1d + g.c1d);
+                        const double gp = (g.c1d == 0.0) ? e1d : exp(l1d);
                         ap_re += gp * cd;
                         ap_im += gp * sd;
                     }
-                    if (in2) e2d = exp(-l1d + s_c2d[j]);
-                    const double inv = df_to_double(s_inv[j]);
+                    if (in2) e2d = exp(-l1d + g.c2d);
+                    const double inv = df_to_double(g.inv);
                     am_re += (e1d + e2d) * cd * inv;
                     am_im += (e1d - e2d) * sd * inv;
                     continue;
                 }
                 df sp, cp;
                 df_sincos_tab(ph, s_tab, K, sp, cp);
-                const df inv = s_inv[j];
+                const df inv = g.inv;
                 if (in1 && !in2 && c1.hi == 0.0f && inv.hi == 1.0f && inv.lo == 0.0f) {
                     // n >= 0 with e^{-2n} below double rounding and no term
                     // near theta = pi: both estimators add e^{l1} e^{i phi}
@@ -358,13 +399,13 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 1)
             ap_re += df_to_double(pp_re);
             ap_im += df_to_double(pp_im);
         }
-        __syncthreads();
+        __syncwarp();
     }
     // combine the trajectory groups in a fixed order
-    s_red[grp][0][slot] = am_re;
-    s_red[grp][1][slot] = am_im;
-    s_red[grp][2][slot] = ap_re;
-    s_red[grp][3][slot] = ap_im;
+    s_red[grp][0][lane] = am_re;
+    s_red[grp][1][lane] = am_im;
+    s_red[grp][2][lane] = ap_re;
+    s_red[grp][3][lane] = ap_im;
     __syncthreads();
     if (grp == 0 && kvalid) {
         double v[4];
@@ -372,7 +413,7 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 1)
         for (int c = 0; c < 4; ++c) {
             double sum = 0.0;
 #pragma unroll
-            for (int g = 0; g < kGfGroups; ++g) sum += s_red[g][c][slot];
+            for (int g = 0; g < kGfGroups; ++g) sum += s_red[g][c][lane];
             v[c] = sum;
         }
         double2 *a0 = acc + (size_t)r * K1 + k;
@@ -381,7 +422,7 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 1)
         *a0 = make_double2(o0.x + v[0], o0.y + v[1]);
         *a1 = make_double2(o1.x + v[2], o1.y + v[3]);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) counts[r] += cnt_r;
+    if (blockIdx.y == 0 && threadIdx.x == 0) counts[r] += cnt_r;
 }
 
 }  // namespace
@@ -450,7 +491,7 @@ int launch_finalize(gbs_net *net, int64_t count) {
     int blocks = (int)std::min<int64_t>((count + 255) / 256, (int64_t)net->sm_count * 8);
     k_finalize<<<blocks, 256, 0, net->stream>>>(net->d_nS_part, net->mtiles, net->chunk, net->d_n,
                                                  count, net->K1, net->d_nS, net->d_win,
-                                                 net->d_wmax);
+                                                 net->d_wmax, static_cast<GfRec *>(net->d_gfrec));
     GBS_LAUNCH_CHECK();
     return GBS_OK;
 }
@@ -464,14 +505,17 @@ int launch_gf(gbs_net *net, uint64_t e0, int64_t count) {
                                                    net->d_counts);
     } else {
         static const DfConsts K = make_df_consts();
-        dim3 g2((unsigned)((net->K1 + kGfSlots - 1) / kGfSlots), (unsigned)net->n_sub);
+        dim3 g2((unsigned)net->n_sub, (unsigned)((net->K1 + kGfSlots - 1) / kGfSlots));
+        if (!net->d_gfrec) return set_error(GBS_EINVAL, "network has no generating-function records");
         k_gf_df<<<g2, kGfSlots * kGfGroups, 0, net->stream>>>(
-            net->d_n, net->d_nS, net->d_win, net->d_wmax, count, e0, net->n_sub, net->K1,
-            net->d_tw, K, net->d_acc, net->d_counts);
+            static_cast<const GfRec *>(net->d_gfrec), net->d_wmax, count, e0, net->n_sub,
+            net->K1, net->d_tw, K, net->d_acc, net->d_counts);
     }
     GBS_LAUNCH_CHECK();
     return GBS_OK;
 }
+
+size_t gf_record_bytes() { return sizeof(GfRec); }
 
 int launch_tables(gbs_net *net) {
     const int blocks = (net->K1 + 255) / 256;

@@ -88,12 +88,19 @@ def test_fp64_per_sample_gf(gbs, stream):
         gbs.gbs_free_network(net)
 
 
+# Per-term bound of the split paths' generating functions: 1e-11 relative
+# plus an absolute floor of 2^-55 (every term, however small, in
+# double-float).
+GF_TERM_FLOOR = 2.0 ** -55
+
+
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
 def test_split_path_per_sample_gf(gbs, stream, prec):
     """The BF16 paths evaluate the generating functions in double-float:
-    per trajectory (n_sub = E) they match the oracle's FP64 formula applied
-    to the device's own n, n_S within 1e-11 relative (absolute floor 2^-55),
-    including negative n and complex n_S (non-uniform loss)."""
+    per trajectory (n_sub = E) they match the
+    oracle's FP64 formula applied to the device's own n, n_S within 1e-11
+    relative plus GF_TERM_FLOOR, including negative n and complex n_S
+    (non-uniform loss)."""
     for general in (False, True):
         net_def = wl.small_network(10, r=[0.3, 0.9, 0.5, 1.2, 0.7, 0.2, 0.8, 1.0, 0.4, 0.6],
                                    t2=0.85, seed=3, general_loss=general)
@@ -106,8 +113,32 @@ def test_split_path_per_sample_gf(gbs, stream, prec):
             gm, gp = oracle.gf_sample(n[e], nS[e], K1)
             for got, want in ((acc[0, e], gm), (acc[1, e], gp)):
                 err = np.abs(got - want)
-                assert np.all(err <= 1e-11 * np.abs(want) + 2.0 ** -55), (general, e, err.max())
+                assert np.all(err <= 1e-11 * np.abs(want) + GF_TERM_FLOOR), (general, e, err.max())
         gbs.gbs_free_network(net)
+
+
+@pytest.mark.parametrize("general", [False, True])
+def test_split_path_per_sample_gf_large_totals(gbs, stream, general):
+    """The same per-term bound at photon totals of a few hundred (phases of
+    ~10^2 rad at the window edges, a third of the in-window terms below
+    2^-27): every term, including the smallest in-window ones, against the
+    oracle's FP64 formula."""
+    net_def = wl.small_network(256, r=1.0, t2=0.95, seed=31, general_loss=general)
+    E, K1 = 64, 4096
+    net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
+    n, nS = gbs.gbs_debug_samples(net, net_def.seed_s, 0, E)
+    assert np.min(nS.real) > 150.0
+    gbs.gbs_sample(net, net_def.seed_s, 0, E, E, K1)
+    _, _, acc, _ = gbs.gbs_get_accumulators(net)
+    small = 0
+    for e in range(E):
+        gm, gp = oracle.gf_sample(n[e], nS[e], K1)
+        small += int(np.sum((np.abs(gp) < 2.0 ** -27) & (np.abs(gp) > 2.0 ** -60)))
+        for got, want in ((acc[0, e], gm), (acc[1, e], gp)):
+            err = np.abs(got - want)
+            assert np.all(err <= 1e-11 * np.abs(want) + GF_TERM_FLOOR), (general, e, err.max())
+    assert small > 1000  # many in-window terms far below 1
+    gbs.gbs_free_network(net)
 
 
 def test_fp64_distribution_matches_oracle(gbs, stream):
