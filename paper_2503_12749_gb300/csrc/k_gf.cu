@@ -110,7 +110,10 @@ __global__ void k_finalize(const double2 *__restrict__ part, int mtiles, int64_t
             g.y = df_from_double(im);
             g.c1 = df_from_double(g.c1d);
             g.c2 = df_from_double(g.c2d);
-            g.inv = df_from_double(1.0 / (1.0 + exp(-2.0 * fabs(nn))));
+            // 1 + e^{-2|n|} rounds to 1 for |n| > 20 (e^{-40} < 2^-54): no
+            // FP64 exponential for those (GB300's FP64 pipe is narrow)
+            const double an = fabs(nn);
+            g.inv = df_from_double(an > 20.0 ? 1.0 : 1.0 / (1.0 + exp(-2.0 * an)));
             g.w1 = w.w1;
             g.w2 = w.w2;
             rec[i] = g;
@@ -227,12 +230,44 @@ __global__ void __launch_bounds__(256) k_gf_fp64(const double *__restrict__ n_in
 // 1e-10 and below, so the terms need FP64-class accuracy.  GB300's FP64 rate
 // is low, so the same formulas are evaluated in double-float arithmetic on
 // the FP32 pipes (dfloat.cuh, ~2^-46 relative): l1, phi, e^{l1 + c1},
-// e^{-l1 + c2}, e^{l1}, sin phi, cos phi.  Arguments outside the
-// double-float ranges (|phi| >= 6000, exponents >= 80: only the +P heavy
-// tail) are evaluated in FP64 and added to the FP64 sums directly.  Per thread, double-float partial sums over 64
-// trajectories are added to FP64 accumulators.
+// e^{-l1 + c2}, e^{l1}, sin phi, cos phi, so that the absolute error of
+// every term stays at the 2^-46 the double-float rounding commits on terms
+// of order one; terms below 2^-27 reach that with FP32 exp and sin/cos
+// (small_term below).  Arguments outside the double-float ranges (|phi| >=
+// 6000, exponents >= 80: only the +P heavy tail) are evaluated in FP64 and
+// added to the FP64 sums directly.  Per warp lane, double-float partial sums
+// over 32 trajectories are added to FP64 accumulators.
 __device__ __forceinline__ df df_exp_small(df a, const DfTables &T, const DfConsts &K) {
     return a.hi < -87.0f ? df{0.0f, 0.0f} : df_exp_tab(a, T, K);  // below 1e-37: nothing
+}
+
+// Terms below 2^-27 (exponent l1 below kSmallLog) need no double-float
+// result: their absolute error stays below 2^-46, what the double-float
+// evaluation commits on terms of order one, when
+//   e^{l1} = expf(l1.hi) (1 + l1.lo)   (expf: 2 ulp),
+//   phi = 2 pi q + r in double-float (Cody-Waite with the 12-bit pieces of
+//   pi/2 times 4: |q| < 1000, so every product is exact), then the SFU sine
+//   and cosine of r.hi in [-pi, pi] (absolute error 2^-21.41) corrected to
+//   first order by r.lo,
+// i.e. a relative error below 2^-20.5 on a term below 2^-27.  Such terms
+// are summed in FP32 (at most 32 per warp lane between flushes, each below
+// 2^-27) and added to the FP64 sums with the double-float partials.
+constexpr float kSmallLog = -18.72f;  // just below ln 2^-27 = -18.7150
+
+__device__ __forceinline__ void small_term(df l1, df ph, const DfConsts &K, float &re, float &im) {
+    const float qf = rintf(ph.hi * 0.15915494309189535f);  // 1 / (2 pi)
+    df r = df_two_sum(fmaf(-qf, 4.0f * K.pio2_1, ph.hi), ph.lo);  // exact product
+    r = df_add_f(r, -qf * (4.0f * K.pio2_2));                      // exact product
+    r = df_add_f(r, -qf * (4.0f * K.pio2_3));
+    r = df_add_f(r, -qf * (4.0f * K.pio2_4));
+    float sn, cs;
+    __sincosf(r.hi, &sn, &cs);
+    const float s1 = fmaf(cs, r.lo, sn);
+    const float c1 = fmaf(-sn, r.lo, cs);
+    const float e = expf(l1.hi);
+    const float m = fmaf(e, l1.lo, e);
+    re = fmaf(m, c1, re);
+    im = fmaf(m, s1, im);
 }
 
 // k of slot i: slots enumerate the union window around theta = 0
@@ -334,6 +369,7 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 4)
         if (kvalid) {
             df pm_re = {0.0f, 0.0f}, pm_im = {0.0f, 0.0f}, pp_re = {0.0f, 0.0f},
                pp_im = {0.0f, 0.0f};
+            float sm_re = 0.0f, sm_im = 0.0f;  // small terms of both estimators
             for (int m = 0; m < nmine; ++m) {
                 const GfRec &g = mine[m];
                 const bool in1 = d0 <= g.w1;
@@ -368,10 +404,15 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 4)
                     am_im += (e1d - e2d) * sd * inv;
                     continue;
                 }
+                const df inv = g.inv;
+                const bool plain = in1 && !in2 && c1.hi == 0.0f && inv.hi == 1.0f && inv.lo == 0.0f;
+                if (plain && l1.hi < kSmallLog) {
+                    small_term(l1, ph, K, sm_re, sm_im);
+                    continue;
+                }
                 df sp, cp;
                 df_sincos_tab(ph, s_tab, K, sp, cp);
-                const df inv = g.inv;
-                if (in1 && !in2 && c1.hi == 0.0f && inv.hi == 1.0f && inv.lo == 0.0f) {
+                if (plain) {
                     // n >= 0 with e^{-2n} below double rounding and no term
                     // near theta = pi: both estimators add e^{l1} e^{i phi}
                     // (the general formulas below give the same bits)
@@ -394,10 +435,10 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 4)
                 pm_re = df_add(pm_re, df_mul(df_mul(df_add(e1, e2), inv), cp));
                 pm_im = df_add(pm_im, df_mul(df_mul(df_sub(e1, e2), inv), sp));
             }
-            am_re += df_to_double(pm_re);
-            am_im += df_to_double(pm_im);
-            ap_re += df_to_double(pp_re);
-            ap_im += df_to_double(pp_im);
+            am_re += df_to_double(pm_re) + (double)sm_re;
+            am_im += df_to_double(pm_im) + (double)sm_im;
+            ap_re += df_to_double(pp_re) + (double)sm_re;
+            ap_im += df_to_double(pp_im) + (double)sm_im;
         }
         __syncwarp();
     }
