@@ -33,12 +33,17 @@ METRIC = "matrix-P samples/sec and binned-P(m) wall time per N-mode network at |
 UNIT = "samples/s"
 
 # DRAM bytes (read + write) of the GEMM kernel per trajectory, from the ncu
-# capture of one m1000 BF16x3 launch of 131072 trajectories
-# (profiles/k_gemm_tc_m1000_bf16x3.md: 1.0845 GB read + 0.0360 GB written);
-# the sample operand it reads grows in proportion to the trajectories.  Valid
-# for the workload and kernel version of that capture only.
-# keyed by (workload, precision, whether the GEMM also runs the next chunk's sampler)
-GEMM_TRAFFIC_BYTES_PER_SAMPLE = {("m1000", "bf16x3", False): (1.082062e9 + 34.582016e6) / 131072}
+# captures of one m1000 BF16x3 launch of 131072 trajectories: the plain GEMM
+# (profiles/k_gemm_tc_m1000_bf16x3.md: 1.0821 GB read + 0.0346 GB written)
+# and the sampling GEMM (profiles/k_gemm_tc_sampling_m1000.md: 1.1027 GB read
+# + 1.0910 GB written); the operands grow in proportion to the trajectories.
+# Valid for the workload and kernel versions of those captures only.
+# keyed by (workload, precision, whether the GEMM also runs the next chunk's
+# sampler: then the traffic includes the next chunk's operand written)
+GEMM_TRAFFIC_BYTES_PER_SAMPLE = {
+    ("m1000", "bf16x3", False): (1.082062e9 + 34.582016e6) / 131072,
+    ("m1000", "bf16x3", True): (1.102734e9 + 1.091048e9) / 131072,
+}
 
 
 def _env_int(name, default):
@@ -278,6 +283,9 @@ def gbs_arm(args, wl_def):
             # launch: the 2 T planes the 3 products read
             planes = 2 if precision == "bf16x3" else 3
             per_traj = 2 * planes * 2 * netdef.N + 16 * (-(-netdef.M // 64))
+            if folded:
+                # the next chunk's operand and n[] written by the sampler warps
+                per_traj += 2 * planes * 2 * netdef.N + 8
             roof["algorithmic_bytes"] = per_traj * E * args.steps / max(gemm_launches, 1) + \
                 planes * 2 * netdef.M * netdef.N * 2
     else:
