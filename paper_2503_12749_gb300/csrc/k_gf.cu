@@ -325,7 +325,7 @@ __device__ __forceinline__ int slot_block(int y, int K1, int W1, int W2) {
 // double-float partials to FP64 after each tile.  Grid: x = sub-ensemble
 // (fast), y = slot block from the window's centre outwards, so the
 // heaviest blocks start first and the last wave holds the lightest.
-__global__ void __launch_bounds__(kGfSlots * kGfGroups, 4)
+__global__ void __launch_bounds__(kGfSlots * kGfGroups, 5)
     k_gf_df(const GfRec *__restrict__ rec, const int *__restrict__ wmax, int64_t count,
             uint64_t e0, int n_sub, int K1, const double2 *__restrict__ tw, const DfConsts K,
             double2 *__restrict__ acc, int64_t *__restrict__ counts) {
@@ -369,6 +369,7 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 4)
         if (kvalid) {
             df pm_re = {0.0f, 0.0f}, pm_im = {0.0f, 0.0f}, pp_re = {0.0f, 0.0f},
                pp_im = {0.0f, 0.0f};
+            df pb_re = {0.0f, 0.0f}, pb_im = {0.0f, 0.0f};  // terms of both estimators
             float sm_re = 0.0f, sm_im = 0.0f;  // small terms of both estimators
             for (int m = 0; m < nmine; ++m) {
                 const GfRec &g = mine[m];
@@ -379,11 +380,18 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 4)
                 const df l1 = df_sub(df_mul(cm1, x), df_mul(sn, y));  // (cos-1) x - sin y
                 const df ph = df_add(df_mul(sn, x), df_mul(cm1, y));  // sin x + (cos-1) y
                 const df c1 = g.c1;
-                const df a1 = df_add(l1, c1);
-                const df a2 = df_add(df_neg(l1), g.c2);
-                const bool big = fabsf(ph.hi) >= 6000.0f ||
-                                 (in1 && (a1.hi >= 80.0f || l1.hi >= 80.0f)) ||
-                                 (in2 && a2.hi >= 80.0f);
+                const df inv = g.inv;
+                // n >= 0 with e^{-2n} below double rounding and no term near
+                // theta = pi: both estimators add e^{l1} e^{i phi} (the
+                // general formulas give the same value), summed once
+                const bool plain = in1 && !in2 && c1.hi == 0.0f && inv.hi == 1.0f && inv.lo == 0.0f;
+                df a1 = l1, a2 = {0.0f, 0.0f};
+                bool big = fabsf(ph.hi) >= 6000.0f || (in1 && l1.hi >= 80.0f);
+                if (!plain) {
+                    a1 = df_add(l1, c1);
+                    a2 = df_add(df_neg(l1), g.c2);
+                    big = big || (in1 && a1.hi >= 80.0f) || (in2 && a2.hi >= 80.0f);
+                }
                 if (big) {
                     // outside the double-float ranges (+P heavy tail, huge
                     // phases): this pair in FP64, straight into the FP64 sums
@@ -399,13 +407,11 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 4)
                         ap_im += gp * sd;
                     }
                     if (in2) e2d = exp(-l1d + g.c2d);
-                    const double inv = df_to_double(g.inv);
-                    am_re += (e1d + e2d) * cd * inv;
-                    am_im += (e1d - e2d) * sd * inv;
+                    const double dinv = df_to_double(g.inv);
+                    am_re += (e1d + e2d) * cd * dinv;
+                    am_im += (e1d - e2d) * sd * dinv;
                     continue;
                 }
-                const df inv = g.inv;
-                const bool plain = in1 && !in2 && c1.hi == 0.0f && inv.hi == 1.0f && inv.lo == 0.0f;
                 if (plain && l1.hi < kSmallLog) {
                     small_term(l1, ph, K, sm_re, sm_im);
                     continue;
@@ -413,15 +419,9 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 4)
                 df sp, cp;
                 df_sincos_tab(ph, s_tab, K, sp, cp);
                 if (plain) {
-                    // n >= 0 with e^{-2n} below double rounding and no term
-                    // near theta = pi: both estimators add e^{l1} e^{i phi}
-                    // (the general formulas below give the same bits)
                     const df e1 = df_exp_small(l1, s_tab, K);
-                    const df gc = df_mul(e1, cp), gs = df_mul(e1, sp);
-                    pp_re = df_add(pp_re, gc);
-                    pp_im = df_add(pp_im, gs);
-                    pm_re = df_add(pm_re, gc);
-                    pm_im = df_add(pm_im, gs);
+                    pb_re = df_add(pb_re, df_mul(e1, cp));
+                    pb_im = df_add(pb_im, df_mul(e1, sp));
                     continue;
                 }
                 df e1 = {0.0f, 0.0f}, e2 = {0.0f, 0.0f};
@@ -435,10 +435,12 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 4)
                 pm_re = df_add(pm_re, df_mul(df_mul(df_add(e1, e2), inv), cp));
                 pm_im = df_add(pm_im, df_mul(df_mul(df_sub(e1, e2), inv), sp));
             }
-            am_re += df_to_double(pm_re) + (double)sm_re;
-            am_im += df_to_double(pm_im) + (double)sm_im;
-            ap_re += df_to_double(pp_re) + (double)sm_re;
-            ap_im += df_to_double(pp_im) + (double)sm_im;
+            const double both_re = df_to_double(pb_re) + (double)sm_re;
+            const double both_im = df_to_double(pb_im) + (double)sm_im;
+            am_re += df_to_double(pm_re) + both_re;
+            am_im += df_to_double(pm_im) + both_im;
+            ap_re += df_to_double(pp_re) + both_re;
+            ap_im += df_to_double(pp_im) + both_im;
         }
         __syncwarp();
     }
