@@ -180,42 +180,58 @@ int run_chunk_front(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) {
     return GBS_OK;
 }
 
-// The chunks of gbs_sample with the sampler folded into the GEMM (BF16X3):
-// the first chunk is sampled alone; the GEMM of chunk i samples chunk i + 1
-// into the second operand, and the two operands swap roles after every
-// chunk (back to their original roles at the end, so that the other entry
-// points always find the first operand current).  The samples, and so every
-// sum, are bitwise those of the plain chunk loop.
-int sample_chunks_pipelined(gbs_net *net, uint64_t seed, uint64_t first, int64_t E) {
+// A chunk loop with the sampler folded into the GEMM (BF16X3): the first
+// chunk is sampled alone; the GEMM of chunk i also samples chunk i + 1 into
+// the second operand (gemm(count, job); job.count == 0 for the last chunk),
+// after(e0, count) launches what consumes chunk i, and the two operands swap
+// roles after every chunk (back to their original roles at the end, so that
+// the other entry points always find the first operand current).  The
+// samples, and so every sum, are bitwise those of the plain chunk loop.
+template <typename Gemm, typename After>
+int pipelined_chunks(gbs_net *net, uint64_t seed, uint64_t first, int64_t E, int64_t step,
+                     Gemm gemm, After after) {
     int rc = GBS_OK, swaps = 0;
     prof_mark(net, GBS_PHASE_SAMPLE, 0, true);
-    rc = launch_sample_bf16(net, seed, first, std::min<int64_t>(net->chunk, E));
+    rc = launch_sample_bf16(net, seed, first, std::min<int64_t>(step, E));
     prof_mark(net, GBS_PHASE_SAMPLE, 1, false);
-    for (int64_t done = 0; rc == GBS_OK && done < E; done += net->chunk) {
-        const int64_t c = std::min<int64_t>(net->chunk, E - done);
+    for (int64_t done = 0; rc == GBS_OK && done < E; done += step) {
+        const int64_t c = std::min<int64_t>(step, E - done);
         const uint64_t e0 = first + (uint64_t)done;
-        const int64_t next = std::min<int64_t>(net->chunk, E - done - c);
+        const int64_t next = std::min<int64_t>(step, E - done - c);
+        SampleJob job;
+        if (next > 0)
+            job = sample_job_bf16(net, net->d_B_alt, net->d_n_alt, seed, e0 + (uint64_t)c, next);
         prof_mark(net, GBS_PHASE_GEMM, 0, true);
-        if (next > 0) {
-            const SampleJob job = sample_job_bf16(net, net->d_B_alt, net->d_n_alt, seed,
-                                                  e0 + (uint64_t)c, next);
-            rc = launch_gemm_tc_sampling(net, c, job);
-        } else {
-            rc = launch_gemm_tc(net, c);
-        }
-        if (rc) break;
+        if ((rc = gemm(c, job))) break;
         prof_mark(net, GBS_PHASE_GEMM, 1, false);
-        prof_mark(net, GBS_PHASE_FINALIZE, 0, true);
-        if ((rc = launch_finalize(net, c))) break;
-        prof_mark(net, GBS_PHASE_FINALIZE, 1, false);
-        prof_mark(net, GBS_PHASE_GF, 0, true);
-        if ((rc = launch_gf(net, e0, c))) break;
-        prof_mark(net, GBS_PHASE_GF, 1, false);
+        if ((rc = after(e0, c))) break;
         tc_swap_sample_buffers(net);
         ++swaps;
     }
     if (swaps & 1) tc_swap_sample_buffers(net);
     return rc;
+}
+
+// Whether a chunk loop of E trajectories in steps of `step` folds the sampler.
+bool fold_sampler(gbs_net *net, int64_t E, int64_t step) {
+    return E > step && net->precision == GBS_BF16X3 && tc_sampling_ready(net, true);
+}
+
+int sample_chunks_pipelined(gbs_net *net, uint64_t seed, uint64_t first, int64_t E) {
+    auto gemm = [&](int64_t c, const SampleJob &job) {
+        return job.count ? launch_gemm_tc_sampling(net, c, job) : launch_gemm_tc(net, c);
+    };
+    auto after = [&](uint64_t e0, int64_t c) {
+        int rc;
+        prof_mark(net, GBS_PHASE_FINALIZE, 0, true);
+        if ((rc = launch_finalize(net, c))) return rc;
+        prof_mark(net, GBS_PHASE_FINALIZE, 1, false);
+        prof_mark(net, GBS_PHASE_GF, 0, true);
+        if ((rc = launch_gf(net, e0, c))) return rc;
+        prof_mark(net, GBS_PHASE_GF, 1, false);
+        return GBS_OK;
+    };
+    return pipelined_chunks(net, seed, first, E, net->chunk, gemm, after);
 }
 
 // T (device, M x N complex, (re, im) interleaved, row-major) -> [M][2][N] FP64.
@@ -630,7 +646,7 @@ int gbs_sample(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, i
     if (first_sample + (uint64_t)E < first_sample)
         return set_error(GBS_EINVAL, "sample index range overflows 64 bits");
     if ((rc = fix_estimator(net, n_sub, K1))) return rc;
-    if (E > net->chunk && net->precision == GBS_BF16X3 && tc_sampling_ready(net, true)) {
+    if (fold_sampler(net, E, net->chunk)) {
         if ((rc = sample_chunks_pipelined(net, seed, first_sample, E))) return rc;
     } else {
         for (int64_t done = 0; done < E; done += net->chunk) {
@@ -898,19 +914,32 @@ int gbs_moments(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, 
     if (!rc && cudaMemcpyAsync(d_cnt, cnt.data(), sizeof(int64_t) * n_sub, cudaMemcpyHostToDevice,
                                net->stream) != cudaSuccess)
         rc = set_error(GBS_ECUDA, "copy of the sub-ensemble sizes failed");
-    for (int64_t done = 0; !rc && done < E; done += ld) {
-        const int64_t c = std::min<int64_t>(ld, E - done);
-        const uint64_t e0 = first_sample + (uint64_t)done;
-        int nl = 0;
-        rc = run_chunk_occ(net, seed, e0, c, d_occ, ld);
-        if (!rc) {
-            prof_mark(net, GBS_PHASE_MOMENTS, 0, true);
-            rc = launch_moment_prep(net->d_n, c, fp64, d_par, net->stream, net->sm_count);
+    auto consume = [&](uint64_t e0, int64_t c) {
+        int r, nl = 0;
+        prof_mark(net, GBS_PHASE_MOMENTS, 0, true);
+        if ((r = launch_moment_prep(net->d_n, c, fp64, d_par, net->stream, net->sm_count))) return r;
+        if ((r = launch_moments(sp, fp64, d_occ, plane, ld, d_par, net->d_n, c, e0, d_acc, d_scr,
+                                max_seg, net->d_flags + 1, net->stream, net->sm_count, &nl)))
+            return r;
+        prof_mark(net, GBS_PHASE_MOMENTS, 1 + nl, false);
+        return GBS_OK;
+    };
+    if (!rc && fold_sampler(net, E, ld)) {
+        OccOut o;
+        o.p = static_cast<float *>(d_occ);
+        o.ld = ld;
+        o.plane = plane;
+        auto gemm = [&](int64_t c, const SampleJob &job) {
+            return job.count ? launch_gemm_tc_sampling(net, c, job, o) : launch_gemm_tc(net, c, o);
+        };
+        rc = pipelined_chunks(net, seed, first_sample, E, ld, gemm, consume);
+    } else {
+        for (int64_t done = 0; !rc && done < E; done += ld) {
+            const int64_t c = std::min<int64_t>(ld, E - done);
+            const uint64_t e0 = first_sample + (uint64_t)done;
+            rc = run_chunk_occ(net, seed, e0, c, d_occ, ld);
+            if (!rc) rc = consume(e0, c);
         }
-        if (!rc)
-            rc = launch_moments(sp, fp64, d_occ, plane, ld, d_par, net->d_n, c, e0, d_acc, d_scr,
-                                max_seg, net->d_flags + 1, net->stream, net->sm_count, &nl);
-        if (!rc) prof_mark(net, GBS_PHASE_MOMENTS, 1 + nl, false);
     }
     if (!rc) {
         prof_mark(net, GBS_PHASE_MOMENTS, 0, true);
@@ -987,13 +1016,30 @@ int gbs_sample_nd(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E
     if (first_sample + (uint64_t)E < first_sample)
         return set_error(GBS_EINVAL, "sample index range overflows 64 bits");
     if ((rc = fix_estimator2d(net, n_sub, K))) return rc;
-    for (int64_t done = 0; done < E; done += net->chunk) {
-        const int64_t c = std::min<int64_t>(net->chunk, E - done);
-        const uint64_t e0 = first_sample + (uint64_t)done;
-        if ((rc = run_chunk_front2d(net, seed, e0, c))) return rc;
-        prof_mark(net, GBS_PHASE_GF, 0, true);
-        if ((rc = launch_gf2d(net, e0, c))) return rc;
-        prof_mark(net, GBS_PHASE_GF, net->precision == GBS_FP64 ? 1 : 2, false);
+    if (fold_sampler(net, E, net->chunk)) {
+        auto gemm = [&](int64_t c, const SampleJob &job) {
+            return job.count ? launch_gemm_tc_sampling(net, c, job) : launch_gemm_tc(net, c);
+        };
+        auto after = [&](uint64_t e0, int64_t c) {
+            int r;
+            prof_mark(net, GBS_PHASE_FINALIZE, 0, true);
+            if ((r = launch_finalize2d(net, c))) return r;
+            prof_mark(net, GBS_PHASE_FINALIZE, 1, false);
+            prof_mark(net, GBS_PHASE_GF, 0, true);
+            if ((r = launch_gf2d(net, e0, c))) return r;
+            prof_mark(net, GBS_PHASE_GF, 2, false);
+            return GBS_OK;
+        };
+        if ((rc = pipelined_chunks(net, seed, first_sample, E, net->chunk, gemm, after))) return rc;
+    } else {
+        for (int64_t done = 0; done < E; done += net->chunk) {
+            const int64_t c = std::min<int64_t>(net->chunk, E - done);
+            const uint64_t e0 = first_sample + (uint64_t)done;
+            if ((rc = run_chunk_front2d(net, seed, e0, c))) return rc;
+            prof_mark(net, GBS_PHASE_GF, 0, true);
+            if ((rc = launch_gf2d(net, e0, c))) return rc;
+            prof_mark(net, GBS_PHASE_GF, net->precision == GBS_FP64 ? 1 : 2, false);
+        }
     }
     const uint64_t ns = (uint64_t)net->n_sub2;
     const uint64_t full = (uint64_t)E / ns, rem = (uint64_t)E % ns;

@@ -216,7 +216,8 @@ void tc_plan_destroy(gbs_net *net);
 int launch_gemm_tc(gbs_net *net, int64_t count, OccOut occ = OccOut());
 // 3-product GEMM of the chunk in (d_B, d_n) whose spare warps run `job`
 // (the next chunk, into d_B_alt, d_n_alt); needs tc_sampling_ready().
-int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job);
+int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job,
+                            OccOut occ = OccOut());
 // Whether this network can run the sampling GEMM: 3 products, the kernel's
 // register split verified, the second operand allocated (allocates it when
 // `allocate`).

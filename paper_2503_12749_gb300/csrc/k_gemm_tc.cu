@@ -948,11 +948,13 @@ int launch_gemm_tc(gbs_net *net, int64_t count, OccOut occ) {
                                groups * stiles, count, net->d_flags + 1, occ);
 }
 
-int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job) {
+int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job, OccOut occ) {
     if (count <= 0) return GBS_OK;
     TcPlan *plan = net->tc;
     if (!plan || plan->P != 3 || !plan->d_desc_alt)
         return set_error(GBS_EINVAL, "sampling GEMM needs a 3-product plan with a second operand");
+    if (occ.p && (occ.ld % 128 != 0 || occ.ld < count))
+        return set_error(GBS_EINVAL, "occupation output needs ld >= count, ld %% 128 == 0");
     int rc;
     if ((rc = ensure_attrs())) return rc;
     const int cl = pick_cluster(net, count);
@@ -960,9 +962,9 @@ int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job) {
     const int groups = (net->mtiles + cl - 1) / cl;
     const int stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
     return cl == 1 ? launch_variant<3, 1, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
-                                                groups * stiles, count, net->d_flags + 1, OccOut(), job)
+                                                groups * stiles, count, net->d_flags + 1, occ, job)
                    : launch_variant<3, 2, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
-                                                groups * stiles, count, net->d_flags + 1, OccOut(), job);
+                                                groups * stiles, count, net->d_flags + 1, occ, job);
 }
 
 bool tc_sampling_ready(gbs_net *net, bool allocate) {

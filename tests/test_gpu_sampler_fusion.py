@@ -104,3 +104,29 @@ def test_fusion_switch_rejects_bad_values(gbs, stream):
     gbs.gbs_sample(net, net_def.seed_s, 0, 300000, 4, 64)
     assert not gbs.gbs_sampler_fusion(net)
     gbs.gbs_free_network(net)
+
+
+def test_folded_sampler_in_moments_and_binned_paths(gbs, stream):
+    """gbs_moments (the GEMM also writes every n'_i) and gbs_sample_nd (d
+    output bins) fold the sampler the same way: bitwise the same results
+    with it on and off."""
+    net_def = wl.small_network(40, 48, r=0.6, t2=0.9, seed=99)
+    res = {}
+    for fuse in (False, True):
+        net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
+        gbs.gbs_set_sampler_fusion(net, fuse)
+        chunk = gbs.gbs_network_info(net)[3]
+        E = 2 * chunk + 4321
+        res[("mom", fuse)] = gbs.gbs_moments(net, net_def.seed_s, 11, E, 16, 3, 4)
+        assert gbs.gbs_sampler_fusion(net) == fuse
+        gbs.gbs_free_network(net)
+        bins = [b % 3 for b in range(48)]
+        net = gbs.gbs_make_network_binned(net_def.T, net_def.r, bins, "bf16x3", stream)
+        gbs.gbs_set_sampler_fusion(net, fuse)
+        gbs.gbs_sample_nd(net, net_def.seed_s, 5, E, 12, (16, 16, 16))
+        res[("nd", fuse)] = gbs.gbs_binned_counts_nd(net, (16, 16, 16), (0, 0, 0))
+        assert gbs.gbs_sampler_fusion(net) == fuse
+        gbs.gbs_free_network(net)
+    for key in ("mom", "nd"):
+        for x, y in zip(res[(key, False)], res[(key, True)]):
+            assert np.array_equal(np.asarray(x), np.asarray(y)), key
