@@ -13,6 +13,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 namespace gbs {
@@ -54,6 +55,45 @@ void prof_mark(gbs_net *net, int phase, int launches_if_stop, bool start) {
     if (!start) pr.launches[phase] += launches_if_stop;
 }
 
+// Stream-ordered allocations from the device's default memory pool, for the
+// per-network chunk workspace (about 1 GiB at N = 1000): the pool keeps the
+// memory when a network is freed (release threshold raised once per device
+// for this process), so creating and freeing networks in a loop does not go
+// back to the driver for every network.  Allocated and freed on the
+// network's stream.
+int pool_alloc(void **p, size_t bytes, cudaStream_t stream, const char *what) {
+    static std::mutex mu;
+    static bool done[64] = {};
+    *p = nullptr;
+    if (bytes == 0) return GBS_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!done[dev]) {
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t thr = ~0ull;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            }
+            cudaGetLastError();
+            done[dev] = true;
+        }
+    }
+    const cudaError_t err = cudaMallocAsync(p, bytes, stream);
+    if (err != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return set_error(err == cudaErrorMemoryAllocation ? GBS_ENOMEM : GBS_ECUDA,
+                         "cudaMallocAsync(%s, %zu bytes) failed: %s", what, bytes,
+                         cudaGetErrorString(err));
+    }
+    return GBS_OK;
+}
+
+void pool_free_raw(void *p, cudaStream_t stream) {
+    if (p) cudaFreeAsync(p, stream);
+}
+
 namespace {
 
 void prof_clear(gbs_net *net) {
@@ -89,6 +129,17 @@ int dev_alloc(T **p, size_t count, const char *what) {
 template <typename T>
 void dev_free(T *&p) {
     if (p) cudaFree(p);
+    p = nullptr;
+}
+
+template <typename T>
+int pool_alloc_n(T **p, size_t count, cudaStream_t stream, const char *what) {
+    return pool_alloc(reinterpret_cast<void **>(p), count * sizeof(T), stream, what);
+}
+
+template <typename T>
+void pool_free(T *&p, cudaStream_t stream) {
+    if (p) cudaFreeAsync(p, stream);
     p = nullptr;
 }
 
@@ -144,17 +195,14 @@ void release_all(gbs_net *net) {
     dev_free(net->d_sq32);
     dev_free(net->d_T64);
     dev_free(net->d_A);
-    if (net->d_B) cudaFree(net->d_B);
-    net->d_B = nullptr;
-    if (net->d_B_alt) cudaFree(net->d_B_alt);
-    net->d_B_alt = nullptr;
-    dev_free(net->d_n_alt);
-    dev_free(net->d_n);
-    dev_free(net->d_nS_part);
-    dev_free(net->d_nS);
-    dev_free(net->d_win);
-    if (net->d_gfrec) cudaFree(net->d_gfrec);
-    net->d_gfrec = nullptr;
+    pool_free(net->d_B, net->stream);
+    pool_free(net->d_B_alt, net->stream);
+    pool_free(net->d_n_alt, net->stream);
+    pool_free(net->d_n, net->stream);
+    pool_free(net->d_nS_part, net->stream);
+    pool_free(net->d_nS, net->stream);
+    pool_free(net->d_win, net->stream);
+    pool_free(net->d_gfrec, net->stream);
     dev_free(net->d_wmax);
     dev_free(net->d_flags);
     dev_free(net->d_nS2);
@@ -545,32 +593,23 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
         const int64_t tiles = (net->chunk + kTcTileSamples - 1) / kTcTileSamples;
         net->B_bytes = (size_t)net->planesB * tiles * 256 * net->ldK * sizeof(__nv_bfloat16);
     }
-    {
-        cudaError_t err = cudaMalloc(&net->d_B, net->B_bytes);
-        if (err != cudaSuccess) {
-            net->d_B = nullptr;
-            cudaGetLastError();
-            return fail(set_error(GBS_ENOMEM, "cudaMalloc(sample operand, %zu bytes): %s",
-                                  net->B_bytes, cudaGetErrorString(err)));
-        }
-        if (cudaMemset(net->d_B, 0, net->B_bytes) != cudaSuccess)
-            return fail(set_error(GBS_ECUDA, "memset of the sample operand failed"));
-    }
-    if ((rc = dev_alloc(&net->d_n, (size_t)net->chunk, "n")) ||
-        (rc = dev_alloc(&net->d_nS_part, (size_t)net->chunk * net->mtiles, "nS_part")) ||
-        (rc = dev_alloc(&net->d_nS, (size_t)net->chunk, "nS")) ||
-        (rc = dev_alloc(&net->d_win, (size_t)net->chunk, "windows")) ||
+    // the chunk workspace from the stream-ordered pool; the sampler writes
+    // every element the GEMM reads for valid trajectories (K padding
+    // included), so nothing needs clearing
+    if ((rc = pool_alloc(&net->d_B, net->B_bytes, net->stream, "sample operand")) ||
+        (rc = pool_alloc_n(&net->d_n, (size_t)net->chunk, net->stream, "n")) ||
+        (rc = pool_alloc_n(&net->d_nS_part, (size_t)net->chunk * net->mtiles, net->stream, "nS_part")) ||
+        (rc = pool_alloc_n(&net->d_nS, (size_t)net->chunk, net->stream, "nS")) ||
+        (rc = pool_alloc_n(&net->d_win, (size_t)net->chunk, net->stream, "windows")) ||
         (rc = dev_alloc(&net->d_wmax, (size_t)2, "window union")) ||
         (rc = dev_alloc(&net->d_flags, (size_t)4, "flags")))
         return fail(rc);
     if (cudaMemset(net->d_flags, 0, 4 * sizeof(unsigned long long)) != cudaSuccess)
         return fail(set_error(GBS_ECUDA, "memset of flags failed"));
     if (precision != GBS_FP64) {
-        if (cudaMalloc(&net->d_gfrec, (size_t)net->chunk * gf_record_bytes()) != cudaSuccess) {
-            net->d_gfrec = nullptr;
-            cudaGetLastError();
-            return fail(set_error(GBS_ENOMEM, "cudaMalloc(generating-function records) failed"));
-        }
+        if ((rc = pool_alloc(&net->d_gfrec, (size_t)net->chunk * gf_record_bytes(), net->stream,
+                             "generating-function records")))
+            return fail(rc);
         if ((rc = tc_plan_create(net))) return fail(rc);
     }
     *out = net;

@@ -202,6 +202,11 @@ namespace gbs {
 // ---------------------------------------------------------------------------
 // Kernel launchers (each returns a GBS status)
 // ---------------------------------------------------------------------------
+// Stream-ordered device memory from the default pool (kept between
+// networks); freed with pool_free_raw on the same stream.
+int pool_alloc(void **p, size_t bytes, cudaStream_t stream, const char *what);
+void pool_free_raw(void *p, cudaStream_t stream);
+
 // Sampler: writes the sample operand for trajectories e0..e0+count-1 and n[].
 int launch_sample_fp64(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count);
 int launch_sample_bf16(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count);

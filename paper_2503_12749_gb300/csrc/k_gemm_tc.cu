@@ -982,25 +982,25 @@ bool tc_sampling_ready(gbs_net *net, bool allocate) {
         cudaGetLastError();
         return false;  // no allocation inside a capture
     }
-    // the second operand and n[]; without room the plain path runs
-    void *B = nullptr;
-    double *n = nullptr;
+    // the second operand and n[] (from the stream-ordered pool, like the
+    // first; the sampler writes every element the GEMM reads for valid
+    // trajectories); without room the plain path runs
+    void *B = nullptr, *n = nullptr;
     GemmNetDesc *d = nullptr;
-    bool ok = cudaMalloc(&B, net->B_bytes) == cudaSuccess &&
-              cudaMalloc(&n, (size_t)net->chunk * sizeof(double)) == cudaSuccess &&
+    bool ok = pool_alloc(&B, net->B_bytes, net->stream, "second sample operand") == GBS_OK &&
+              pool_alloc(&n, (size_t)net->chunk * sizeof(double), net->stream, "second n") == GBS_OK &&
               cudaMalloc(&d, sizeof(GemmNetDesc)) == cudaSuccess;
-    if (ok) ok = cudaMemset(B, 0, net->B_bytes) == cudaSuccess;  // padding rows and columns read as 0
     if (ok) ok = encode_net_maps(net, B, plan->desc_alt) == GBS_OK;
     if (ok) ok = cudaMemcpy(d, &plan->desc_alt, sizeof(GemmNetDesc), cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
-        if (B) cudaFree(B);
-        if (n) cudaFree(n);
+        pool_free_raw(B, net->stream);
+        pool_free_raw(n, net->stream);
         if (d) cudaFree(d);
         return false;
     }
     net->d_B_alt = B;
-    net->d_n_alt = n;
+    net->d_n_alt = static_cast<double *>(n);
     plan->d_desc_alt = d;
     return true;
 }

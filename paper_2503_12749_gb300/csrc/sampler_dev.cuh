@@ -114,7 +114,9 @@ __device__ __forceinline__ void sample_trajectory_bf16(const SampleJob &jb, int6
     const size_t row_a = (size_t)(tile * 256 + q) * 32;
     const size_t row_b = (size_t)(tile * 256 + 128 + q) * 32;
     float s = 0.0f, comp = 0.0f;
-    for (int j0 = 4 * lane; j0 < jb.N; j0 += 128) {
+    // modes N..ldK-1 (the K padding) are written as zeros, so the operand
+    // needs no clearing before its first use
+    for (int j0 = 4 * lane; j0 < jb.ldK; j0 += 128) {
         __align__(8) __nv_bfloat16 a0[4], a1[4], a2[4], b0[4], b1[4], b2[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
