@@ -326,21 +326,24 @@ int gbs_gemm_config(gbs_net_t net, int *cluster);
 
 /*
  * gbs_set_sampler_fusion / gbs_sampler_fusion -- sampling of the next chunk
- * inside the propagation GEMM (GBS_BF16X3 only).  enable = 1 (the default):
- * when gbs_sample covers more than one chunk, the GEMM of chunk i also
- * draws the samples of chunk i + 1 (the +P sampling of "Applications to
- * GBS", Philox counters as in gbs_sample) into a second sample operand
- * allocated on first use (the size of the first: about 1 GiB at N = 1000),
- * so the sampler's arithmetic runs in issue slots the tensor-core GEMM
- * leaves idle.  The samples and every sum are bitwise those of enable = 0.
- * Without room for the second operand, inside a stream capture that would
- * have to allocate it, or when the library's sampling GEMM was not built
- * with the register split it needs, gbs_sample runs the plain chunk loop.
- * gbs_sampler_fusion sets *active = 1 when the next gbs_sample call of more
- * than one chunk runs the folded loop (the second operand exists), else 0.
- * EINVAL: enable not 0 or 1, NULL pointer.
+ * inside the propagation GEMM (GBS_BF16X3 only).  When gbs_sample (also
+ * gbs_sample_nd, gbs_moments and the rounds of gbs_sample_batch) covers more
+ * than one chunk, the GEMM of chunk i also draws the samples of chunk i + 1
+ * (the +P sampling of "Applications to GBS", Philox counters as in
+ * gbs_sample) into a second sample operand allocated on first use (the size
+ * of the first: about 1 GiB at N = 1000), so the sampler's arithmetic runs
+ * in issue slots the tensor-core GEMM leaves idle.  mode = 0: never; 1 (the
+ * default): for networks with at least 900 output modes (with fewer, the
+ * GEMM of a chunk is too short to hide the sampling of the next); 2:
+ * whenever the network can.  The samples and every sum are bitwise those of
+ * mode 0.  Without room for the second operand, inside a stream capture
+ * that would have to allocate it, or when the library's sampling GEMM was
+ * not built with the register split it needs, the plain chunk loop runs.
+ * gbs_sampler_fusion sets *active = 1 when the next call of more than one
+ * chunk folds the sampler (the setting asks for it and the second operand
+ * exists), else 0.  EINVAL: mode not 0, 1 or 2, NULL pointer.
  */
-int gbs_set_sampler_fusion(gbs_net_t net, int enable);
+int gbs_set_sampler_fusion(gbs_net_t net, int mode);
 int gbs_sampler_fusion(gbs_net_t net, int *active);
 
 /*

@@ -390,9 +390,10 @@ def gbs_gemm_config(net: Network) -> int:
     return c.value
 
 
-def gbs_set_sampler_fusion(net: Network, enable: bool) -> None:
-    """Sample the next chunk inside the GEMM of this one (BF16X3; default on)."""
-    _check(lib().gbs_set_sampler_fusion(net.handle, 1 if enable else 0))
+def gbs_set_sampler_fusion(net: Network, mode) -> None:
+    """Sample the next chunk inside the GEMM of this one (BF16X3): 0 / False
+    never, 1 / True from 900 output modes (the default), 2 whenever possible."""
+    _check(lib().gbs_set_sampler_fusion(net.handle, int(mode)))
 
 
 def gbs_sampler_fusion(net: Network) -> bool:

@@ -262,7 +262,8 @@ int pipelined_chunks(gbs_net *net, uint64_t seed, uint64_t first, int64_t E, int
 
 // Whether a chunk loop of E trajectories in steps of `step` folds the sampler.
 bool fold_sampler(gbs_net *net, int64_t E, int64_t step) {
-    return E > step && net->precision == GBS_BF16X3 && tc_sampling_ready(net, true);
+    return E > step && net->precision == GBS_BF16X3 && fold_wanted(net) &&
+           tc_sampling_ready(net, true);
 }
 
 int sample_chunks_pipelined(gbs_net *net, uint64_t seed, uint64_t first, int64_t E) {
@@ -1154,11 +1155,11 @@ int gbs_set_gemm_config(gbs_net_t net, int cluster) {
     return tc_set_cluster(net, cluster);
 }
 
-int gbs_set_sampler_fusion(gbs_net_t net, int enable) {
+int gbs_set_sampler_fusion(gbs_net_t net, int mode) {
     int rc;
     if ((rc = validate_net(net))) return rc;
-    if (enable != 0 && enable != 1) return set_error(GBS_EINVAL, "enable must be 0 or 1");
-    net->fuse_sampler = enable;
+    if (mode < 0 || mode > 2) return set_error(GBS_EINVAL, "mode must be 0, 1 or 2");
+    net->fuse_sampler = mode;
     return GBS_OK;
 }
 
@@ -1166,7 +1167,7 @@ int gbs_sampler_fusion(gbs_net_t net, int *active) {
     int rc;
     if ((rc = validate_net(net))) return rc;
     if (!active) return set_error(GBS_EINVAL, "active is NULL");
-    *active = tc_sampling_ready(net, false) ? 1 : 0;
+    *active = (fold_wanted(net) && tc_sampling_ready(net, false)) ? 1 : 0;
     return GBS_OK;
 }
 

@@ -7,6 +7,15 @@
 // ONE persistent grouped GEMM covers the tiles of all networks (a tile list
 // ordered by decreasing K so the long tiles start first and the short ones
 // fill the tail), then each network's finalize and generating-function sums.
+// With the 3-product split and more than one round, the networks with at
+// least kFoldMinModes output modes are sampled by their own sampler only in
+// round 0: the grouped GEMM of round r also draws their round r + 1 (its
+// spare warps take those networks' trajectories as one list) into each one's
+// second operand, and their operands swap roles between rounds (round r
+// reads operand r mod 2; the roles are restored at the end of the call).
+// Smaller networks keep a sampler launch per round (their sampling would
+// outlast their share of the GEMM).  The samples are bitwise those of the
+// plain rounds.
 // The whole call is captured into a CUDA graph and launched once; in the
 // graph the per-network launches of a phase (samplers; finalize + generating
 // functions) are independent branches over up to 8 auxiliary streams, so
@@ -32,8 +41,14 @@ struct gbs_batch {
     gbs::GemmNetDesc *d_desc = nullptr;
     int4 *d_tiles = nullptr;
     size_t desc_cap = 0, tiles_cap = 0;
+    // sampler jobs of rounds 1.. (folded sampling): [rounds][nets] and the
+    // per-round list offsets [rounds][nets + 1]
+    gbs::SampleJob *d_jobs = nullptr;
+    int64_t *d_prefix = nullptr;
+    size_t jobs_cap = 0, prefix_cap = 0;
     int last_rounds = 0;
     int64_t last_tiles = 0;
+    bool last_fold = false;
     // fork/join streams and events of the captured graph
     std::vector<cudaStream_t> aux;
     cudaEvent_t fork = nullptr;
@@ -50,9 +65,15 @@ struct RoundPlan {
     std::vector<int> tile_off;      // [rounds + 1]
     std::vector<std::vector<int64_t>> count;  // [rounds][nets]
     int rounds = 0;
+    bool fold = false;              // some network's sampling runs in the GEMMs
+    std::vector<char> fold_net;     // [nets]: round r reads operand r mod 2, r + 1 sampled in r's GEMM
+    std::vector<SampleJob> jobs;    // [rounds][nets] (round 0 unused)
+    std::vector<int64_t> prefix;    // [rounds][nets + 1]
 };
 
-int build_rounds(gbs_batch *b, const int64_t *E, int cluster, RoundPlan &rp) {
+int build_rounds(gbs_batch *b, const int64_t *E, int cluster, RoundPlan &rp,
+                 const std::vector<char> *fold_net = nullptr, const uint64_t *seeds = nullptr,
+                 const uint64_t *first = nullptr) {
     const int nn = (int)b->nets.size();
     int rounds = 0;
     for (int i = 0; i < nn; ++i)
@@ -76,7 +97,8 @@ int build_rounds(gbs_batch *b, const int64_t *E, int cluster, RoundPlan &rp) {
             rp.count[r][i] = c;
             GemmNetDesc d;
             int rc;
-            if ((rc = tc_fill_desc(net, &d))) return rc;
+            const bool alt = fold_net && (*fold_net)[i] && (r & 1);
+            if ((rc = tc_fill_desc(net, &d, alt))) return rc;
             d.count = c;
             d.stiles = (int)((c + kTcTileSamples - 1) / kTcTileSamples);
             rp.desc[(size_t)r * nn + i] = d;
@@ -90,6 +112,32 @@ int build_rounds(gbs_batch *b, const int64_t *E, int cluster, RoundPlan &rp) {
         }
     }
     rp.tile_off[rounds] = (int)rp.tiles.size();
+    rp.fold_net.assign(nn, 0);
+    rp.fold = false;
+    for (int i = 0; fold_net && i < nn; ++i) {
+        rp.fold_net[i] = (*fold_net)[i];
+        rp.fold = rp.fold || rp.fold_net[i];
+    }
+    if (rp.fold) {
+        rp.jobs.assign((size_t)rounds * nn, SampleJob());
+        rp.prefix.assign((size_t)rounds * (nn + 1), 0);
+        for (int r = 1; r < rounds; ++r) {
+            int64_t acc = 0;
+            for (int i = 0; i < nn; ++i) {
+                gbs_net *net = b->nets[i];
+                const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)net->chunk;
+                const int64_t c = rp.fold_net[i] ? rp.count[r][i] : 0;
+                if (c > 0) {
+                    void *B = (r & 1) ? net->d_B_alt : net->d_B;
+                    double *n = (r & 1) ? net->d_n_alt : net->d_n;
+                    rp.jobs[(size_t)r * nn + i] = sample_job_bf16(net, B, n, seeds[i], e0, c);
+                }
+                rp.prefix[(size_t)r * (nn + 1) + i] = acc;
+                acc += c;
+            }
+            rp.prefix[(size_t)r * (nn + 1) + nn] = acc;
+        }
+    }
     return GBS_OK;
 }
 
@@ -109,12 +157,32 @@ int upload_rounds(gbs_batch *b, const RoundPlan &rp) {
     }
     // synchronous copies: the descriptors must be in place before the graph
     // that reads them is launched, and the host vectors are temporaries
+    if (rp.fold) {
+        if (rp.jobs.size() > b->jobs_cap) {
+            if (b->d_jobs) cudaFree(b->d_jobs);
+            b->d_jobs = nullptr;
+            GBS_CUDA_TRY(cudaMalloc(&b->d_jobs, rp.jobs.size() * sizeof(SampleJob)));
+            b->jobs_cap = rp.jobs.size();
+        }
+        if (rp.prefix.size() > b->prefix_cap) {
+            if (b->d_prefix) cudaFree(b->d_prefix);
+            b->d_prefix = nullptr;
+            GBS_CUDA_TRY(cudaMalloc(&b->d_prefix, rp.prefix.size() * sizeof(int64_t)));
+            b->prefix_cap = rp.prefix.size();
+        }
+    }
     GBS_CUDA_TRY(cudaStreamSynchronize(b->stream));
     GBS_CUDA_TRY(cudaMemcpy(b->d_desc, rp.desc.data(), nd * sizeof(GemmNetDesc),
                             cudaMemcpyHostToDevice));
     if (!rp.tiles.empty())
         GBS_CUDA_TRY(cudaMemcpy(b->d_tiles, rp.tiles.data(), rp.tiles.size() * sizeof(int4),
                                 cudaMemcpyHostToDevice));
+    if (rp.fold) {
+        GBS_CUDA_TRY(cudaMemcpy(b->d_jobs, rp.jobs.data(), rp.jobs.size() * sizeof(SampleJob),
+                                cudaMemcpyHostToDevice));
+        GBS_CUDA_TRY(cudaMemcpy(b->d_prefix, rp.prefix.data(), rp.prefix.size() * sizeof(int64_t),
+                                cudaMemcpyHostToDevice));
+    }
     return GBS_OK;
 }
 
@@ -123,9 +191,21 @@ int round_gemm(gbs_batch *b, const RoundPlan &rp, int r, int cluster) {
     const int off = rp.tile_off[r], nt = rp.tile_off[r + 1] - off;
     gbs_net *n0 = b->nets[0];
     prof_mark(n0, GBS_PHASE_GEMM, 0, true);
-    const int rc = launch_gemm_grouped(b->stream, b->sm_count, b->P, cluster,
-                                       b->d_desc + (size_t)r * nn, b->d_tiles + off, nt, 0,
-                                       n0->d_flags + 1);
+    int rc;
+    if (rp.fold && r + 1 < rp.rounds && rp.prefix[(size_t)(r + 1) * (nn + 1) + nn] > 0) {
+        // this round's GEMM also draws round r + 1 of every network
+        SampleJobs sj;
+        sj.jobs = b->d_jobs + (size_t)(r + 1) * nn;
+        sj.prefix = b->d_prefix + (size_t)(r + 1) * (nn + 1);
+        sj.n = nn;
+        rc = launch_gemm_grouped_sampling(b->stream, b->sm_count, cluster,
+                                          b->d_desc + (size_t)r * nn, b->d_tiles + off, nt,
+                                          n0->d_flags + 1, sj);
+    } else {
+        rc = launch_gemm_grouped(b->stream, b->sm_count, b->P, cluster,
+                                 b->d_desc + (size_t)r * nn, b->d_tiles + off, nt, 0,
+                                 n0->d_flags + 1);
+    }
     prof_mark(n0, GBS_PHASE_GEMM, 1, false);
     return rc;
 }
@@ -162,6 +242,8 @@ int per_network(gbs_batch *b, const RoundPlan &rp, int r, bool branches, Body &&
 int round_front(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *seeds,
                 const uint64_t *first, bool branches = false) {
     return per_network(b, rp, r, branches, [&](int i, gbs_net *net) {
+        // networks whose rounds 1.. are drawn by the GEMMs
+        if (r > 0 && rp.fold && rp.fold_net[i]) return (int)GBS_OK;
         const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)net->chunk;
         return launch_sample_bf16(net, seeds[i], e0, rp.count[r][i]);
     });
@@ -175,6 +257,31 @@ int round_back(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *first,
         if ((rc = launch_finalize(net, rp.count[r][i]))) return rc;
         return launch_gf(net, e0, rp.count[r][i]);
     });
+}
+
+// Folded rounds: the networks' operands swap roles after each round, so that
+// round r's finalize and generating functions read operand r mod 2's n[].
+void swap_all(gbs_batch *b, const RoundPlan &rp) {
+    for (size_t i = 0; i < b->nets.size(); ++i)
+        if (rp.fold_net[i]) tc_swap_sample_buffers(b->nets[i]);
+}
+
+// Every round of the call: samplers (round 0 only when folded), GEMM,
+// finalize + generating functions.
+int run_rounds(gbs_batch *b, const RoundPlan &rp, const uint64_t *seeds, const uint64_t *first,
+               bool branches) {
+    int rc = GBS_OK, swaps = 0;
+    for (int r = 0; r < rp.rounds && rc == GBS_OK; ++r) {
+        if ((rc = round_front(b, rp, r, seeds, first, branches))) break;
+        if ((rc = round_gemm(b, rp, r, b->cluster))) break;
+        if ((rc = round_back(b, rp, r, first, branches))) break;
+        if (rp.fold) {
+            swap_all(b, rp);
+            ++swaps;
+        }
+    }
+    if (swaps & 1) swap_all(b, rp);
+    return rc;
 }
 
 // Time both cluster sizes on round 0 (samplers of round 0 run first so the
@@ -266,21 +373,30 @@ int gbs_sample_batch(gbs_batch_t b, const uint64_t *seeds, const uint64_t *first
     if (!b->cluster) {
         if ((rc = tune_batch(b, E, seeds, first_sample))) return rc;
     }
+    // fold a network's sampling into the GEMMs when it has more than one
+    // round, its setting asks for it (by default from kFoldMinModes output
+    // modes) and its second operand exists (allocated here, outside the
+    // capture)
+    std::vector<char> fold_net(nn, 0);
+    bool fold = false;
+    for (int i = 0; i < nn; ++i) {
+        gbs_net *net = b->nets[i];
+        fold_net[i] = b->P == 3 && E[i] > net->chunk && fold_wanted(net) &&
+                      tc_sampling_ready(net, true);
+        fold = fold || fold_net[i];
+    }
     RoundPlan rp;
-    if ((rc = build_rounds(b, E, b->cluster, rp))) return rc;
+    if ((rc = build_rounds(b, E, b->cluster, rp, &fold_net, seeds, first_sample))) return rc;
     if ((rc = upload_rounds(b, rp))) return rc;
     b->last_rounds = rp.rounds;
     b->last_tiles = (int64_t)rp.tiles.size();
+    b->last_fold = fold;
 
     if (b->stream == nullptr || b->nets[0]->prof.on) {
         // the legacy default stream cannot be captured, and phase timing
         // (gbs_profile_enable on the first network) needs the launches
         // bracketed one by one: issue the rounds directly
-        for (int r = 0; r < rp.rounds; ++r) {
-            if ((rc = round_front(b, rp, r, seeds, first_sample))) return rc;
-            if ((rc = round_gemm(b, rp, r, b->cluster))) return rc;
-            if ((rc = round_back(b, rp, r, first_sample))) return rc;
-        }
+        if ((rc = run_rounds(b, rp, seeds, first_sample, false))) return rc;
         for (int i = 0; i < nn; ++i) count_samples(b->nets[i], first_sample[i], E[i]);
         return GBS_OK;
     }
@@ -288,11 +404,7 @@ int gbs_sample_batch(gbs_batch_t b, const uint64_t *seeds, const uint64_t *first
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     GBS_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    for (int r = 0; r < rp.rounds && rc == GBS_OK; ++r) {
-        if ((rc = round_front(b, rp, r, seeds, first_sample, true))) break;
-        if ((rc = round_gemm(b, rp, r, b->cluster))) break;
-        rc = round_back(b, rp, r, first_sample, true);
-    }
+    rc = run_rounds(b, rp, seeds, first_sample, true);
     cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
     if (rc) {
         if (graph) cudaGraphDestroy(graph);
@@ -327,6 +439,8 @@ void gbs_free_batch(gbs_batch_t b) {
     cudaStreamSynchronize(b->stream);
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_jobs) cudaFree(b->d_jobs);
+    if (b->d_prefix) cudaFree(b->d_prefix);
     for (cudaStream_t st : b->aux) cudaStreamDestroy(st);
     for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);

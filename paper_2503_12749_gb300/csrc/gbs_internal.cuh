@@ -112,6 +112,16 @@ struct SampleJob {
     int N = 0, ldK = 0, planesB = 0;
 };
 
+// The sampler work of a sampling GEMM: one job (n == 0: `one`), or n jobs in
+// device memory whose trajectories are taken as one list (job j owns list
+// positions prefix[j] .. prefix[j + 1] - 1).
+struct SampleJobs {
+    const SampleJob *jobs = nullptr;
+    const int64_t *prefix = nullptr;  // [n + 1]
+    int n = 0;
+    SampleJob one;
+};
+
 // CUDA-event timing of kernel phases (gbs_profile_*).
 struct Profiler {
     bool on = false;
@@ -150,7 +160,7 @@ struct gbs_net {
     // them with the next chunk's samples; swapped with d_B, d_n per chunk
     void *d_B_alt = nullptr;
     double *d_n_alt = nullptr;
-    int fuse_sampler = 1;           // gbs_set_sampler_fusion
+    int fuse_sampler = 1;           // gbs_set_sampler_fusion: 0 off, 1 automatic, 2 always
     double2 *d_nS_part = nullptr;   // [mtiles][chunk]
     int mtiles = 0;
     double2 *d_nS = nullptr;        // [chunk]
@@ -223,6 +233,17 @@ int launch_gemm_tc(gbs_net *net, int64_t count, OccOut occ = OccOut());
 // (the next chunk, into d_B_alt, d_n_alt); needs tc_sampling_ready().
 int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job,
                             OccOut occ = OccOut());
+// Output modes from which a network's sampling pays off inside its GEMM:
+// the 6 sampler warps per SM draw a chunk of N-mode trajectories in about
+// 1.6 ms x N / 1000 while the GEMM takes about 1.8 ms x N M / 10^6 (both
+// measured at N = M = 1000, 131072 trajectories), so below M ~ 860 the
+// sampler would become the launch's tail.
+constexpr int kFoldMinModes = 900;
+// gbs_set_sampler_fusion's setting: 0 never, 1 from kFoldMinModes output
+// modes, 2 whenever the network can.
+inline bool fold_wanted(const gbs_net *net) {
+    return net->fuse_sampler == 2 || (net->fuse_sampler == 1 && net->M >= kFoldMinModes);
+}
 // Whether this network can run the sampling GEMM: 3 products, the kernel's
 // register split verified, the second operand allocated (allocates it when
 // `allocate`).
@@ -233,13 +254,17 @@ int tc_set_cluster(gbs_net *net, int cluster);  // 0 = autotune, 1, 2
 int tc_get_cluster(gbs_net *net);
 int tc_autotune(gbs_net *net, int64_t count, int *cluster);
 int tc_products(gbs_net *net);
-int tc_fill_desc(gbs_net *net, GemmNetDesc *out);
+int tc_fill_desc(gbs_net *net, GemmNetDesc *out, bool alt = false);  // alt: the second operand's maps
 // One launch over the tiles of many networks (d_tiles: {net, mode-tile group,
 // trajectory tile} per entry; NULL = closed-form tiles of d_nets[0] with
 // count0 trajectories).
 int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int cluster,
                         const GemmNetDesc *d_nets, const int4 *d_tiles, int ntiles, int64_t count0,
                         unsigned long long *err, OccOut occ = OccOut());
+// The same launch (3 products) whose spare warps run `jobs`.
+int launch_gemm_grouped_sampling(cudaStream_t stream, int sm_count, int cluster,
+                                 const GemmNetDesc *d_nets, const int4 *d_tiles, int ntiles,
+                                 unsigned long long *err, const SampleJobs &jobs);
 
 // Finalise n_S (fixed-order sum of tile partials) and the evaluation windows.
 int launch_finalize(gbs_net *net, int64_t count);

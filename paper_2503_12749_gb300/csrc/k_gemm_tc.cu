@@ -239,7 +239,7 @@ __device__ __forceinline__ void warp_transpose_reduce32(float (&v)[32], int lane
 template <int P, int kCl, int kSW>
 __global__ void __launch_bounds__(threads_of<kSW>(), 1)
     k_gemm_tc(const GemmNetDesc *__restrict__ nets, const int4 *__restrict__ tiles, int ntiles,
-              int64_t count0, unsigned long long *err_ptr, OccOut occ, const SampleJob job) {
+              int64_t count0, unsigned long long *err_ptr, OccOut occ, const SampleJobs sj) {
     static_assert(kSW == 0 || P == 3, "the sampling variant runs the 3-product GEMM");
     constexpr int kE0 = epi_warp0<kSW>();  // first epilogue warp
     using C = Cfg<P>;
@@ -617,23 +617,49 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                 mma_issuer();
             } else if (warp >= 12 || kSampWG0) {
                 // ---------------------------------------------- sampler warps
-                // (2, 3, 12..): the next chunk's operand, evict-first stores;
-                // each CTA samples a contiguous range of the job
+                // (2, 3, 12..): the next chunk's operand(s), evict-first
+                // stores; each CTA samples a contiguous range of the job
+                // list
                 const int sw = warp < 4 ? warp - 2 : warp - 12 + (kSampWG0 ? 2 : 0);
-                const int64_t lo = job.count * (int64_t)blockIdx.x / gridDim.x;
-                const int64_t hi = job.count * ((int64_t)blockIdx.x + 1) / gridDim.x;
-                if (kSampDyn) {
-                    for (;;) {
-                        uint32_t idx = 0;
-                        if (lane == 0) idx = atomicAdd(samp_next, 1u);
-                        idx = __shfl_sync(0xffffffffu, idx, 0);
-                        const int64_t i = lo + (int64_t)idx;
-                        if (i >= hi) break;
-                        samp::sample_trajectory_bf16<true, true>(job, i, lane);
+                const int64_t total = sj.n ? sj.prefix[sj.n] : sj.one.count;
+                const int64_t lo = total * (int64_t)blockIdx.x / gridDim.x;
+                const int64_t hi = total * ((int64_t)blockIdx.x + 1) / gridDim.x;
+                if (sj.n == 0) {
+                    if (kSampDyn) {
+                        for (;;) {
+                            uint32_t idx = 0;
+                            if (lane == 0) idx = atomicAdd(samp_next, 1u);
+                            idx = __shfl_sync(0xffffffffu, idx, 0);
+                            const int64_t i = lo + (int64_t)idx;
+                            if (i >= hi) break;
+                            samp::sample_trajectory_bf16<true, true>(sj.one, i, lane);
+                        }
+                    } else {
+                        for (int64_t i = lo + sw; i < hi; i += kSampWarpsUsed)
+                            samp::sample_trajectory_bf16<true, true>(sj.one, i, lane);
                     }
-                } else {
-                    for (int64_t i = lo + sw; i < hi; i += kSampWarpsUsed)
-                        samp::sample_trajectory_bf16<true, true>(job, i, lane);
+                } else if (lo + sw < hi) {
+                    // the job holding list position lo + sw: the last j with
+                    // prefix[j] <= lo + sw (binary search), then forward
+                    int a = 0, c = sj.n;  // prefix[a] <= pos < prefix[c]
+                    const int64_t pos0 = lo + sw;
+                    while (c - a > 1) {
+                        const int m = (a + c) >> 1;
+                        if (sj.prefix[m] <= pos0) a = m;
+                        else c = m;
+                    }
+                    int j = a;
+                    SampleJob jb = sj.jobs[j];
+                    int64_t base = sj.prefix[j], end = sj.prefix[j + 1];
+                    for (int64_t i = pos0; i < hi; i += kSampWarpsUsed) {
+                        while (i >= end) {
+                            ++j;
+                            jb = sj.jobs[j];
+                            base = end;
+                            end = sj.prefix[j + 1];
+                        }
+                        samp::sample_trajectory_bf16<true, true>(jb, i - base, lane);
+                    }
                 }
             }
         }
@@ -735,7 +761,7 @@ bool sampling_kernels_ok() {
 template <int P, int kCl, int kSW>
 int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets, const int4 *d_tiles,
                    int ntiles, int64_t count0, unsigned long long *err, OccOut occ,
-                   const SampleJob &job) {
+                   const SampleJobs &jobs) {
     if (ntiles <= 0) return GBS_OK;
     const int clusters = std::max(1, std::min(ntiles, sm_count / kCl));
     cudaLaunchConfig_t cfg = {};
@@ -751,7 +777,7 @@ int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets,
     cfg.attrs = attr;
     cfg.numAttrs = kCl > 1 ? 1 : 0;
     cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_tc<P, kCl, kSW>, d_nets, d_tiles, ntiles,
-                                        count0, err, occ, job);
+                                        count0, err, occ, jobs);
     if (le != cudaSuccess)
         return set_error(GBS_ECUDA, "launch of the GEMM (%d products, cluster %d%s) failed: %s", P,
                          kCl, kSW ? ", sampling" : "", cudaGetErrorString(le));
@@ -818,7 +844,7 @@ int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int cluster,
     if ((rc = ensure_attrs())) return rc;
     if (occ.p && (d_tiles || occ.ld % 128 != 0 || occ.ld < count0))
         return set_error(GBS_EINVAL, "occupation output needs closed-form tiles and ld >= count, ld %% 128 == 0");
-    const SampleJob none;
+    const SampleJobs none;
     if (P == 3)
         return cluster == 1 ? launch_variant<3, 1, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none)
                             : launch_variant<3, 2, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none);
@@ -826,10 +852,23 @@ int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int cluster,
                         : launch_variant<6, 2, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none);
 }
 
-int tc_fill_desc(gbs_net *net, GemmNetDesc *out) {
+int tc_fill_desc(gbs_net *net, GemmNetDesc *out, bool alt) {
     if (!net->tc) return set_error(GBS_EINVAL, "network has no tensor-core plan");
-    *out = net->tc->desc;
+    if (alt && !net->tc->d_desc_alt) return set_error(GBS_EINVAL, "network has no second operand");
+    *out = alt ? net->tc->desc_alt : net->tc->desc;
     return GBS_OK;
+}
+
+int launch_gemm_grouped_sampling(cudaStream_t stream, int sm_count, int cluster,
+                                 const GemmNetDesc *d_nets, const int4 *d_tiles, int ntiles,
+                                 unsigned long long *err, const SampleJobs &jobs) {
+    int rc;
+    if ((rc = ensure_attrs())) return rc;
+    if (!sampling_kernels_ok()) return set_error(GBS_EINVAL, "sampling GEMM unavailable");
+    return cluster == 1 ? launch_variant<3, 1, kSampWG>(stream, sm_count, d_nets, d_tiles, ntiles, 0,
+                                                        err, OccOut(), jobs)
+                        : launch_variant<3, 2, kSampWG>(stream, sm_count, d_nets, d_tiles, ntiles, 0,
+                                                        err, OccOut(), jobs);
 }
 
 int tc_products(gbs_net *net) { return net->tc ? net->tc->P : 0; }
@@ -961,10 +1000,12 @@ int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job, O
     if (cl < 0) return -cl;
     const int groups = (net->mtiles + cl - 1) / cl;
     const int stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
+    SampleJobs jobs;
+    jobs.one = job;
     return cl == 1 ? launch_variant<3, 1, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
-                                                groups * stiles, count, net->d_flags + 1, occ, job)
+                                                groups * stiles, count, net->d_flags + 1, occ, jobs)
                    : launch_variant<3, 2, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
-                                                groups * stiles, count, net->d_flags + 1, occ, job);
+                                                groups * stiles, count, net->d_flags + 1, occ, jobs);
 }
 
 bool tc_sampling_ready(gbs_net *net, bool allocate) {

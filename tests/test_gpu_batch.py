@@ -129,3 +129,50 @@ def test_batch_distributions_match_exact(gbs):
     gbs.gbs_free_batch(batch)
     for n in nets:
         gbs.gbs_free_network(n)
+
+
+@pytest.mark.parametrize("own_stream", [True, False])
+def test_multi_round_batch_folds_the_sampler_bitwise(gbs, own_stream):
+    """More than one round per call: the grouped GEMM of round r draws round
+    r + 1 of every network (networks with 1, 2 or 3 rounds, ragged last
+    rounds).  The sums equal per-network runs and a batch in which one
+    network samples every round separately (its folding switched off), bit
+    for bit; the captured graph (own stream) and the direct launches
+    (legacy stream) agree."""
+    import torch
+    s = torch.cuda.Stream() if own_stream else None
+    sptr = s.cuda_stream if own_stream else 0
+    defs = _uneven_defs()
+    probe = gbs.gbs_make_network(defs[0].T, defs[0].r, "bf16x3", sptr)
+    chunk = gbs.gbs_network_info(probe)[3]
+    gbs.gbs_free_network(probe)
+    E = [2 * chunk + 777, chunk + 5, 20000, chunk, 2 * chunk, 3 * chunk - 1]
+    n_sub = [10, 8, 16, 4, 7, 16]
+    K1 = [64, 128, 256, 512, 64, 256]
+    seeds = [d.seed_s for d in defs]
+    first = [13 * i for i in range(len(defs))]
+    sums = {}
+    for mode in ("fold", "plain", "single"):
+        nets = [gbs.gbs_make_network(d.T, d.r, "bf16x3", sptr) for d in defs]
+        for net in nets:
+            gbs.gbs_set_sampler_fusion(net, 2)  # fold also these small networks
+        if mode == "single":
+            for i, net in enumerate(nets):
+                gbs.gbs_sample(net, seeds[i], first[i], E[i], n_sub[i], K1[i])
+        else:
+            if mode == "plain":
+                gbs.gbs_set_sampler_fusion(nets[2], 0)
+            batch = gbs.gbs_make_batch(nets)
+            gbs.gbs_sample_batch(batch, seeds, first, E, n_sub, K1)
+            _, rounds, _ = gbs.gbs_batch_info(batch)
+            assert rounds == 3
+            gbs.gbs_free_batch(batch)
+        sums[mode] = [gbs.gbs_get_accumulators(n) for n in nets]
+        if mode == "fold":  # networks of more than one round fold
+            assert [gbs.gbs_sampler_fusion(n) for n in nets] == [e > chunk for e in E]
+        for n in nets:
+            gbs.gbs_free_network(n)
+    for mode in ("plain", "single"):
+        for i in range(len(defs)):
+            assert np.array_equal(sums["fold"][i][3], sums[mode][i][3]), (mode, i)
+            assert np.array_equal(sums["fold"][i][2], sums[mode][i][2]), (mode, i)

@@ -3,7 +3,9 @@ gbs_sample over several chunks draws chunk i + 1's samples in the spare warps
 of chunk i's GEMM.  The draws are the same Philox counters through the same
 device code, so the sub-ensemble sums must equal those of the plain chunk
 loop bit for bit, for both cluster sizes, ragged last chunks and calls that
-start mid-ensemble; the other entry points run unchanged after it.
+start mid-ensemble; the other entry points run unchanged after it.  Mode 2
+folds on any network (these are small); mode 1, the default, only from 900
+output modes.
 """
 import numpy as np
 import pytest
@@ -32,7 +34,7 @@ def stream():
 def _sums(gbs, stream, net_def, fuse, cluster, calls, n_sub, K1):
     net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
     gbs.gbs_set_gemm_config(net, cluster)
-    gbs.gbs_set_sampler_fusion(net, fuse)
+    gbs.gbs_set_sampler_fusion(net, 2 if fuse else 0)
     for first, E in calls:
         gbs.gbs_sample(net, net_def.seed_s, first, E, n_sub, K1)
     active = gbs.gbs_sampler_fusion(net)
@@ -71,7 +73,8 @@ def test_single_chunk_calls_and_other_entry_points_after_folding(gbs, stream):
     net_def = wl.small_network(64, 64, r=0.6, t2=0.95, seed=97)
     a = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
     b = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
-    gbs.gbs_set_sampler_fusion(b, False)
+    gbs.gbs_set_sampler_fusion(a, 2)
+    gbs.gbs_set_sampler_fusion(b, 0)
     chunk = gbs.gbs_network_info(a)[3]
     for net in (a, b):
         gbs.gbs_sample(net, net_def.seed_s, 0, 3 * chunk, 10, 128)
@@ -96,7 +99,7 @@ def test_fusion_switch_rejects_bad_values(gbs, stream):
     net_def = wl.small_network(16, 16, r=0.5, t2=0.9, seed=98)
     net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
     with pytest.raises(gbs.GbsError) as ei:
-        gbs._check(gbs.lib().gbs_set_sampler_fusion(net.handle, 2))
+        gbs._check(gbs.lib().gbs_set_sampler_fusion(net.handle, 3))
     assert ei.value.code == gbs.GBS_EINVAL
     gbs.gbs_free_network(net)
     # FP64 networks never fold
@@ -114,7 +117,7 @@ def test_folded_sampler_in_moments_and_binned_paths(gbs, stream):
     res = {}
     for fuse in (False, True):
         net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
-        gbs.gbs_set_sampler_fusion(net, fuse)
+        gbs.gbs_set_sampler_fusion(net, 2 if fuse else 0)
         chunk = gbs.gbs_network_info(net)[3]
         E = 2 * chunk + 4321
         res[("mom", fuse)] = gbs.gbs_moments(net, net_def.seed_s, 11, E, 16, 3, 4)
@@ -122,7 +125,7 @@ def test_folded_sampler_in_moments_and_binned_paths(gbs, stream):
         gbs.gbs_free_network(net)
         bins = [b % 3 for b in range(48)]
         net = gbs.gbs_make_network_binned(net_def.T, net_def.r, bins, "bf16x3", stream)
-        gbs.gbs_set_sampler_fusion(net, fuse)
+        gbs.gbs_set_sampler_fusion(net, 2 if fuse else 0)
         gbs.gbs_sample_nd(net, net_def.seed_s, 5, E, 12, (16, 16, 16))
         res[("nd", fuse)] = gbs.gbs_binned_counts_nd(net, (16, 16, 16), (0, 0, 0))
         assert gbs.gbs_sampler_fusion(net) == fuse
@@ -130,3 +133,16 @@ def test_folded_sampler_in_moments_and_binned_paths(gbs, stream):
     for key in ("mom", "nd"):
         for x, y in zip(res[(key, False)], res[(key, True)]):
             assert np.array_equal(np.asarray(x), np.asarray(y)), key
+
+
+def test_automatic_mode_folds_from_900_output_modes(gbs, stream):
+    """Mode 1 (the default) folds the sampler for networks with at least 900
+    output modes only: below that the GEMM of a chunk is too short to hide
+    the next chunk's sampling."""
+    for M, want in ((896, False), (960, True)):
+        net_def = wl.small_network(32, M, r=0.5, t2=0.9, seed=100 + M)
+        net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
+        chunk = gbs.gbs_network_info(net)[3]
+        gbs.gbs_sample(net, net_def.seed_s, 0, chunk + 1000, 8, 256)
+        assert gbs.gbs_sampler_fusion(net) == want, M
+        gbs.gbs_free_network(net)
