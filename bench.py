@@ -189,6 +189,8 @@ def gbs_arm(args, wl_def):
     if args.samples:
         E = args.samples
     net = gbs.gbs_make_network(netdef.T, netdef.r, precision, sptr)
+    if args.sampler_fusion is not None:
+        gbs.gbs_set_sampler_fusion(net, args.sampler_fusion)
     out = torch.empty(4 * K1, dtype=torch.float64, device="cuda")
     seed = netdef.seed_s
     # rank r draws trajectories [r * R, (r + 1) * R) with R = (W + K + 2) * E
@@ -312,7 +314,10 @@ def gbs_arm(args, wl_def):
                               f"T = sqrt({wl_def.t2}) U",
                    "binned_P_wall_ms": ms_step,
                    "phases_from": "2 further steps with phase timing (CUDA events around "
-                                  "each phase), scaled to the timed steps"},
+                                  "each phase), scaled to the timed steps",
+                   "sampler": ("drawn in the spare warps of the previous chunk's GEMM"
+                               if tc_path and gbs.gbs_sampler_fusion(net)
+                               else "one launch per chunk")},
         "roofline": roof,
         "phases": phases,
         "result": acc_summary,
@@ -334,6 +339,8 @@ def gbs_arm(args, wl_def):
 
         def e2e_step(s):
             n2 = gbs.gbs_make_network(Tn, rn, precision, sptr)
+            if args.sampler_fusion is not None:
+                gbs.gbs_set_sampler_fusion(n2, args.sampler_fusion)
             gbs.gbs_sample(n2, seed, s * E, E, n_sub, K1)
             res = gbs.gbs_binned_counts(n2, 0, K1)
             gbs.gbs_free_network(n2)
@@ -913,6 +920,9 @@ def main():
     ap.add_argument("--ref-samples", type=int, default=2048)
     ap.add_argument("--cpu-samples", type=int, default=8192)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sampler-fusion", type=int, choices=[0, 1, 2], default=None,
+                    help="gbs_set_sampler_fusion mode of the timed network (default: the "
+                         "library's, 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
