@@ -154,15 +154,14 @@ static_assert(256 * kRegsEpi + (threads_of<1>() - 256) * regs_rest<1>() <=
 static_assert(256 * kRegsEpi + (threads_of<2>() - 256) * regs_rest<2>() <=
                   threads_of<2>() * regs_launch<2>(), "register pool, 10 sampler warps");
 // The sampling GEMM's sampler warps: kSampWG warpgroups after the
-// epilogue, plus warps 2 and 3 when kSampWG0; within a CTA's range of
-// trajectories the warps take fixed strides (kSampDyn = false) or the next
-// trajectory from a shared counter.  The sampler's issue slots come out of
-// the epilogue's, so the fewest warps that still finish within the GEMM
-// are best.
+// epilogue, plus warps 2 and 3 of warpgroup 0; within a CTA's range of
+// trajectories the warps take fixed strides.  The sampler's issue slots come
+// out of the epilogue's, so the fewest warps that still finish within the
+// GEMM are best (measured at N = M = 1000: 4 warps leave the sampler as the
+// launch's tail, 10 warps, or a shared counter that keeps all 6 busy to the
+// end, lengthen the launch).
 constexpr int kSampWG = 1;
-constexpr bool kSampWG0 = true;
-constexpr bool kSampDyn = false;
-constexpr int kSampWarpsUsed = 4 * kSampWG + (kSampWG0 ? 2 : 0);
+constexpr int kSampWarpsUsed = 4 * kSampWG + 2;
 
 // A tile of the grouped GEMM: which network, which group of kCl mode
 // tiles, which 128-trajectory tile.
@@ -262,7 +261,6 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
     uint64_t *tempty = bars + 2 * kStages + 2;
     uint64_t *drain = bars + 2 * kStages + 4;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 5);
-    uint32_t *samp_next = tmem_slot + 1;  // next trajectory of the CTA's sampler range
     float *red = reinterpret_cast<float *>(smem + kStages * C::kStageBytes + kBarBytes);
     float *ostage = reinterpret_cast<float *>(smem + kStages * C::kStageBytes + kBarBytes + kRedBytes);
 
@@ -284,7 +282,6 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
             ptx::mbar_init(ptx::smem_u32(&tempty[b]), kEpiThreads);
         }
         ptx::mbar_init(ptx::smem_u32(drain), 1);
-        *samp_next = 0u;
         ptx::fence_barrier_init();
     }
     if (warp == 1) {
@@ -615,29 +612,18 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                 producer();
             } else if (warp == 1) {
                 mma_issuer();
-            } else if (warp >= 12 || kSampWG0) {
+            } else {
                 // ---------------------------------------------- sampler warps
                 // (2, 3, 12..): the next chunk's operand(s), evict-first
                 // stores; each CTA samples a contiguous range of the job
                 // list
-                const int sw = warp < 4 ? warp - 2 : warp - 12 + (kSampWG0 ? 2 : 0);
+                const int sw = warp < 4 ? warp - 2 : warp - 10;
                 const int64_t total = sj.n ? sj.prefix[sj.n] : sj.one.count;
                 const int64_t lo = total * (int64_t)blockIdx.x / gridDim.x;
                 const int64_t hi = total * ((int64_t)blockIdx.x + 1) / gridDim.x;
                 if (sj.n == 0) {
-                    if (kSampDyn) {
-                        for (;;) {
-                            uint32_t idx = 0;
-                            if (lane == 0) idx = atomicAdd(samp_next, 1u);
-                            idx = __shfl_sync(0xffffffffu, idx, 0);
-                            const int64_t i = lo + (int64_t)idx;
-                            if (i >= hi) break;
-                            samp::sample_trajectory_bf16<true, true>(sj.one, i, lane);
-                        }
-                    } else {
-                        for (int64_t i = lo + sw; i < hi; i += kSampWarpsUsed)
-                            samp::sample_trajectory_bf16<true, true>(sj.one, i, lane);
-                    }
+                    for (int64_t i = lo + sw; i < hi; i += kSampWarpsUsed)
+                        samp::sample_trajectory_bf16<true, true>(sj.one, i, lane);
                 } else if (lo + sw < hi) {
                     // the job holding list position lo + sw: the last j with
                     // prefix[j] <= lo + sw (binary search), then forward
