@@ -55,8 +55,9 @@ extern "C" {
 /* Arithmetic of the propagation GEMM alpha' = T alpha, beta' = T* beta. */
 #define GBS_FP64 0   /* FP64 sampler, FP64 SIMT GEMM, FP64 generating functions */
 #define GBS_BF16X3 2 /* FP32 sampler, tcgen05 BF16 split GEMM with 3 products
-                        (T0 B0 + T0 B1 + T1 B0), FP32 accumulation; FP32
-                        generating functions summed in FP64 */
+                        (T0 B0 + T0 B1 + T1 B0), FP32 accumulation;
+                        generating functions in double-float on the FP32
+                        pipes (FP32 for terms below 2^-27), summed in FP64 */
 #define GBS_BF16X6 3 /* as GBS_BF16X3 with 6 products (adds T1 B1, T0 B2, T2 B0) */
 
 typedef struct gbs_net *gbs_net_t;
