@@ -191,6 +191,8 @@ def gbs_arm(args, wl_def):
     net = gbs.gbs_make_network(netdef.T, netdef.r, precision, sptr)
     if args.sampler_fusion is not None:
         gbs.gbs_set_sampler_fusion(net, args.sampler_fusion)
+    if args.gemm_cluster is not None and precision != "fp64":
+        gbs.gbs_set_gemm_config(net, args.gemm_cluster)
     out = torch.empty(4 * K1, dtype=torch.float64, device="cuda")
     seed = netdef.seed_s
     # rank r draws trajectories [r * R, (r + 1) * R) with R = (W + K + 2) * E
@@ -920,6 +922,9 @@ def main():
     ap.add_argument("--ref-samples", type=int, default=2048)
     ap.add_argument("--cpu-samples", type=int, default=8192)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--gemm-cluster", type=int, choices=[0, 1, 2], default=None,
+                    help="gbs_set_gemm_config cluster size of the timed network (default: "
+                         "autotuned)")
     ap.add_argument("--sampler-fusion", type=int, choices=[0, 1, 2], default=None,
                     help="gbs_set_sampler_fusion mode of the timed network (default: the "
                          "library's, 1)")
