@@ -398,14 +398,20 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                                 break;
                             }
                             ptx::tc_fence_after();
+                            // the stage's plane descriptors once; the second
+                            // K16 half is 32 bytes on (2 in the descriptor's
+                            // 16-byte address field, which cannot carry:
+                            // shared addresses stay below 2^18)
+                            const uint64_t dA[2] = {ptx::desc_k_sw64(ptx::smem_u32(a_tile(stage, 0))),
+                                                    ptx::desc_k_sw64(ptx::smem_u32(a_tile(stage, 1)))};
+                            const uint64_t dB[2] = {ptx::desc_k_sw64(ptx::smem_u32(b_tile(stage, 0))),
+                                                    ptx::desc_k_sw64(ptx::smem_u32(b_tile(stage, 1)))};
 #pragma unroll
                             for (int pr = 0; pr < 3; ++pr) {
-                                const uint32_t a0 = ptx::smem_u32(a_tile(stage, kIa3[pr]));
-                                const uint32_t b0 = ptx::smem_u32(b_tile(stage, kIb3[pr]));
 #pragma unroll
                                 for (int kk = 0; kk < 2; ++kk) {
-                                    ptx::mma_bf16(d, ptx::desc_k_sw64(a0 + kk * 32),
-                                                  ptx::desc_k_sw64(b0 + kk * 32), kIdesc, acc);
+                                    ptx::mma_bf16(d, dA[kIa3[pr]] + 2u * kk, dB[kIb3[pr]] + 2u * kk,
+                                                  kIdesc, acc);
                                     acc = 1u;
                                 }
                             }
