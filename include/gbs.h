@@ -105,6 +105,14 @@ int gbs_make_network_device(int N, int M, const double *T_dev, const double *r, 
  * the same values (EINVAL otherwise).  Asynchronous on the network's stream
  * except for the first call's allocations.  Errors: EINVAL, ENOMEM, ECUDA,
  * ETIMEOUT.
+ * A call cuts its trajectories into the fewest chunks of at most the
+ * network's chunk size (gbs_network_info), of equal size; every sum runs in
+ * a fixed order, so the same sequence of calls gives bitwise the same sums,
+ * and so does a call split into calls at its own chunk boundaries (other
+ * splits agree to rounding).  With the sampler folded into the GEMM
+ * (gbs_set_sampler_fusion), the last chunk's GEMM also draws the first
+ * chunk of a following call on the same seed from first_sample + E, which
+ * that call then does not draw again (the samples are the same either way).
  */
 int gbs_sample(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub,
                int K1);

@@ -69,16 +69,24 @@ struct RoundPlan {
     std::vector<char> fold_net;     // [nets]: round r reads operand r mod 2, r + 1 sampled in r's GEMM
     std::vector<SampleJob> jobs;    // [rounds][nets] (round 0 unused)
     std::vector<int64_t> prefix;    // [rounds][nets + 1]
+    std::vector<int64_t> step;      // [nets]: trajectories per round (chunk_step)
 };
 
 int build_rounds(gbs_batch *b, const int64_t *E, int cluster, RoundPlan &rp,
                  const std::vector<char> *fold_net = nullptr, const uint64_t *seeds = nullptr,
                  const uint64_t *first = nullptr) {
     const int nn = (int)b->nets.size();
+    // round r holds chunk r of every network, chunks of chunk_step (as
+    // gbs_sample cuts them, so that a batch and per-network calls sum in
+    // the same order)
     int rounds = 0;
-    for (int i = 0; i < nn; ++i)
-        rounds = std::max<int>(rounds, (int)((E[i] + b->nets[i]->chunk - 1) / b->nets[i]->chunk));
+    std::vector<int64_t> step(nn);
+    for (int i = 0; i < nn; ++i) {
+        step[i] = chunk_step(b->nets[i], E[i]);
+        rounds = std::max<int>(rounds, (int)((E[i] + step[i] - 1) / step[i]));
+    }
     rp.rounds = rounds;
+    rp.step = step;
     rp.desc.resize((size_t)rounds * nn);
     rp.count.assign(rounds, std::vector<int64_t>(nn, 0));
     rp.tile_off.assign(rounds + 1, 0);
@@ -92,8 +100,8 @@ int build_rounds(gbs_batch *b, const int64_t *E, int cluster, RoundPlan &rp,
         rp.tile_off[r] = (int)rp.tiles.size();
         for (int i = 0; i < nn; ++i) {
             gbs_net *net = b->nets[i];
-            const int64_t done = (int64_t)r * net->chunk;
-            const int64_t c = std::max<int64_t>(0, std::min<int64_t>(net->chunk, E[i] - done));
+            const int64_t done = (int64_t)r * step[i];
+            const int64_t c = std::max<int64_t>(0, std::min<int64_t>(step[i], E[i] - done));
             rp.count[r][i] = c;
             GemmNetDesc d;
             int rc;
@@ -125,7 +133,7 @@ int build_rounds(gbs_batch *b, const int64_t *E, int cluster, RoundPlan &rp,
             int64_t acc = 0;
             for (int i = 0; i < nn; ++i) {
                 gbs_net *net = b->nets[i];
-                const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)net->chunk;
+                const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)rp.step[i];
                 const int64_t c = rp.fold_net[i] ? rp.count[r][i] : 0;
                 if (c > 0) {
                     void *B = (r & 1) ? net->d_B_alt : net->d_B;
@@ -244,7 +252,7 @@ int round_front(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *seeds,
     return per_network(b, rp, r, branches, [&](int i, gbs_net *net) {
         // networks whose rounds 1.. are drawn by the GEMMs
         if (r > 0 && rp.fold && rp.fold_net[i]) return (int)GBS_OK;
-        const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)net->chunk;
+        const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)rp.step[i];
         return launch_sample_bf16(net, seeds[i], e0, rp.count[r][i]);
     });
 }
@@ -252,7 +260,7 @@ int round_front(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *seeds,
 int round_back(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *first,
                bool branches = false) {
     return per_network(b, rp, r, branches, [&](int i, gbs_net *net) {
-        const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)net->chunk;
+        const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)rp.step[i];
         int rc;
         if ((rc = launch_finalize(net, rp.count[r][i]))) return rc;
         return launch_gf(net, e0, rp.count[r][i]);

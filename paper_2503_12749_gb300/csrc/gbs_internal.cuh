@@ -161,6 +161,13 @@ struct gbs_net {
     void *d_B_alt = nullptr;
     double *d_n_alt = nullptr;
     int fuse_sampler = 1;           // gbs_set_sampler_fusion: 0 off, 1 automatic, 2 always
+    // samples drawn ahead by the last GEMM of a folded gbs_sample into the
+    // second operand: trajectories pre_e0 .. pre_e0 + pre_count - 1 of seed
+    // pre_seed (valid until anything else samples into this network)
+    bool pre_valid = false;
+    uint64_t pre_seed = 0, pre_e0 = 0;
+    int64_t pre_count = 0;
+    void *pre_buf = nullptr;        // the operand (d_B or d_B_alt) holding them
     double2 *d_nS_part = nullptr;   // [mtiles][chunk]
     int mtiles = 0;
     double2 *d_nS = nullptr;        // [chunk]
@@ -233,6 +240,15 @@ int launch_gemm_tc(gbs_net *net, int64_t count, OccOut occ = OccOut());
 // (the next chunk, into d_B_alt, d_n_alt); needs tc_sampling_ready().
 int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job,
                             OccOut occ = OccOut());
+// Trajectories per chunk of a gbs_sample call (and of a batch round) over E
+// trajectories: the fewest chunks of at most net->chunk, of equal size (the
+// last shorter by less than the number of chunks).
+inline int64_t chunk_step(const gbs_net *net, int64_t E) {
+    if (E <= net->chunk) return E > 0 ? E : net->chunk;
+    const int64_t nch = (E + net->chunk - 1) / net->chunk;
+    return (E + nch - 1) / nch;
+}
+
 // Output modes from which a network's sampling pays off inside its GEMM:
 // the 6 sampler warps per SM draw a chunk of N-mode trajectories in about
 // 1.6 ms x N / 1000 while the GEMM takes about 1.8 ms x N M / 10^6 (both

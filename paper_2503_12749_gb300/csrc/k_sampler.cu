@@ -98,6 +98,7 @@ int grid_for_warps(gbs_net *net, int64_t warps_needed, int threads) {
 }  // namespace
 
 int launch_sample_fp64(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) {
+    net->pre_valid = false;  // the operands are overwritten
     if (count <= 0) return GBS_OK;
     const int threads = 256;
     k_sample_fp64<<<grid_for_warps(net, count, threads), threads, 0, net->stream>>>(
@@ -125,6 +126,7 @@ SampleJob sample_job_bf16(gbs_net *net, void *B, double *n, uint64_t seed, uint6
 }
 
 int launch_sample_bf16(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) {
+    net->pre_valid = false;  // the operands are overwritten
     if (count <= 0) return GBS_OK;
     const int threads = 256;
     const SampleJob job = sample_job_bf16(net, net->d_B, net->d_n, seed, e0, count);

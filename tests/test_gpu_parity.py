@@ -217,18 +217,22 @@ def test_uniform_loss_identity_gpu(gbs, stream):
 # edge cases and API behaviour
 # ---------------------------------------------------------------------------
 def test_split_calls_equal_one_call(gbs, stream):
-    """Calls continue the counter stream; splitting at chunk boundaries is
-    bitwise identical, any split agrees to rounding; get/set round-trips."""
+    """Calls continue the counter stream; splitting a call at its own chunk
+    boundaries (a call of E cuts the fewest chunks of at most the network's
+    chunk size, of equal size) is bitwise identical, any split agrees to
+    rounding; get/set round-trips."""
     net_def = wl.small_network(40, r=0.8, t2=0.9, seed=5)
     for prec in ("fp64", "bf16x3"):
         net = gbs.gbs_make_network(net_def.T, net_def.r, prec, stream)
         chunk = gbs.gbs_network_info(net)[3]
         E = 2 * chunk + 77
+        nch = -(-E // chunk)
+        step = -(-E // nch)
         gbs.gbs_sample(net, net_def.seed_s, 0, E, 8, 128)
         _, _, acc1, cnt1 = gbs.gbs_get_accumulators(net)
         gbs.gbs_reset(net)
-        gbs.gbs_sample(net, net_def.seed_s, 0, chunk, 8, 128)
-        gbs.gbs_sample(net, net_def.seed_s, chunk, chunk + 77, 8, 128)
+        for f in range(0, E, step):
+            gbs.gbs_sample(net, net_def.seed_s, f, min(step, E - f), 8, 128)
         _, _, acc2, cnt2 = gbs.gbs_get_accumulators(net)
         assert np.array_equal(cnt1, cnt2)
         assert np.array_equal(acc1, acc2)

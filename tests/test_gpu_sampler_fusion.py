@@ -146,3 +146,39 @@ def test_automatic_mode_folds_from_900_output_modes(gbs, stream):
         gbs.gbs_sample(net, net_def.seed_s, 0, chunk + 1000, 8, 256)
         assert gbs.gbs_sampler_fusion(net) == want, M
         gbs.gbs_free_network(net)
+
+
+def test_next_calls_first_chunk_drawn_ahead(gbs, stream):
+    """The last GEMM of a folded gbs_sample draws the chunk a following call on
+    the same seed from first + E starts with; that call skips its own
+    sampler.  Sums equal the plain loop's bit for bit for a following call
+    that matches (same or smaller E), one that does not (other start), and
+    one after another entry point overwrote the operands."""
+    net_def = wl.small_network(40, 40, r=0.6, t2=0.9, seed=101)
+    probe = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
+    chunk = gbs.gbs_network_info(probe)[3]
+    gbs.gbs_free_network(probe)
+    E = 3 * chunk + 999
+    plan = [(0, E), (E, E), (2 * E, E // 2), (2 * E + E // 2 + 7, E), ("debug",),
+            (3 * E + E // 2 + 7, E)]
+    res = {}
+    for mode in (0, 2):
+        net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
+        gbs.gbs_set_sampler_fusion(net, mode)
+        gbs.gbs_profile_enable(net, True)
+        launches = []
+        for step in plan:
+            if step[0] == "debug":
+                gbs.gbs_debug_samples(net, net_def.seed_s, 5, 100)
+                gbs.gbs_profile_read(net)  # its own sampler launch is not counted below
+                continue
+            gbs.gbs_sample(net, net_def.seed_s, step[0], step[1], 8, 128)
+            launches.append(gbs.gbs_profile_read(net)["sample"][1])
+        res[mode] = (gbs.gbs_get_accumulators(net), launches)
+        gbs.gbs_free_network(net)
+    (a0, l0), (a2, l2) = res[0], res[2]
+    assert np.array_equal(a0[3], a2[3])
+    assert np.array_equal(a0[2].view(np.float64), a2[2].view(np.float64))
+    # sampler launches (the plain loop: one per chunk): the folded calls
+    # that follow a matching call draw nothing themselves
+    assert l2 == [1, 0, 0, 1, 1], l2
