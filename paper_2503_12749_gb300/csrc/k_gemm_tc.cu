@@ -192,6 +192,20 @@ __device__ __forceinline__ TileRef decode_tile(int t, const GemmNetDesc *nets, c
     return r;
 }
 
+// a0 += b0, a1 += b1 as one packed FP32x2 addition (round to nearest per
+// element, the same results as two scalar additions)
+__device__ __forceinline__ void add_f32x2(float &a0, float &a1, float b0, float b1) {
+    asm("{\n"
+        ".reg .b64 x, y;\n"
+        "mov.b64 x, {%0, %1};\n"
+        "mov.b64 y, {%2, %3};\n"
+        "add.rn.f32x2 x, x, y;\n"
+        "mov.b64 {%0, %1}, x;\n"
+        "}\n"
+        : "+f"(a0), "+f"(a1)
+        : "f"(b0), "f"(b1));
+}
+
 __device__ __forceinline__ void named_bar_sync(int id, int threads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
@@ -510,19 +524,19 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                 ptx::tmem_ld32(tb, t);
                 ptx::tmem_ld_wait();
 #pragma unroll
-                for (int i = 0; i < 32; ++i) ra[i] += t[i];
+                for (int i = 0; i < 32; i += 2) add_f32x2(ra[i], ra[i + 1], t[i], t[i + 1]);
                 ptx::tmem_ld32(tb + 32u, t);
                 ptx::tmem_ld_wait();
 #pragma unroll
-                for (int i = 0; i < 32; ++i) ra[32 + i] += t[i];
+                for (int i = 0; i < 32; i += 2) add_f32x2(ra[32 + i], ra[33 + i], t[i], t[i + 1]);
                 ptx::tmem_ld32(tb + 128u, t);
                 ptx::tmem_ld_wait();
 #pragma unroll
-                for (int i = 0; i < 32; ++i) rb[i] += t[i];
+                for (int i = 0; i < 32; i += 2) add_f32x2(rb[i], rb[i + 1], t[i], t[i + 1]);
                 ptx::tmem_ld32(tb + 160u, t);
                 ptx::tmem_ld_wait();
 #pragma unroll
-                for (int i = 0; i < 32; ++i) rb[32 + i] += t[i];
+                for (int i = 0; i < 32; i += 2) add_f32x2(rb[32 + i], rb[33 + i], t[i], t[i + 1]);
                 ptx::tc_fence_before();
                 ptx::mbar_arrive(ptx::smem_u32(&tempty[b]));
             }
