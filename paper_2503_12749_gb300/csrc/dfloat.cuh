@@ -221,4 +221,58 @@ __device__ __forceinline__ void df_sincos_tab(df phi, const DfTables &T, const D
     }
 }
 
+// ---------------------------------------------------------------------------
+// Two double-float numbers side by side (lane x and lane y of each float2),
+// on the packed FP32x2 instructions: every operation below performs, per
+// lane, exactly the IEEE operations of its scalar counterpart above (a - b
+// as fma(b, -1, a), one rounding), with half the instructions.
+// ---------------------------------------------------------------------------
+struct df2 {
+    float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 f2_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ df2 df2_make(df x, df y) { return {f2(x.hi, y.hi), f2(x.lo, y.lo)}; }
+__device__ __forceinline__ df df2_x(df2 v) { return {v.hi.x, v.lo.x}; }
+__device__ __forceinline__ df df2_y(df2 v) { return {v.hi.y, v.lo.y}; }
+
+__device__ __forceinline__ df2 df2_two_sum(float2 a, float2 b) {
+    const float2 s = f2_add(a, b);
+    const float2 bb = f2_sub(s, a);
+    const float2 e = f2_add(f2_sub(a, f2_sub(s, bb)), f2_sub(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df2 df2_fast_two_sum(float2 a, float2 b) {  // |a| >= |b|
+    const float2 s = f2_add(a, b);
+    const float2 e = f2_sub(b, f2_sub(s, a));
+    return {s, e};
+}
+
+__device__ __forceinline__ df2 df2_add(df2 x, df2 y) {
+    const df2 s = df2_two_sum(x.hi, y.hi);
+    const float2 e = f2_add(s.lo, f2_add(x.lo, y.lo));
+    return df2_fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ df2 df2_add_f(df2 x, float2 y) {
+    const df2 s = df2_two_sum(x.hi, y);
+    return df2_fast_two_sum(s.hi, f2_add(s.lo, x.lo));
+}
+
+__device__ __forceinline__ df2 df2_mul(df2 x, df2 y) {
+    const float2 p = f2_mul(x.hi, y.hi);
+    const float2 pe = f2_fma(x.hi, y.hi, f2_neg(p));
+    const float2 e = f2_fma(x.hi, y.lo, f2_fma(x.lo, y.hi, pe));
+    return df2_fast_two_sum(p, e);
+}
+
 }  // namespace gbs

@@ -241,6 +241,61 @@ __device__ __forceinline__ df df_exp_small(df a, const DfTables &T, const DfCons
     return a.hi < -87.0f ? df{0.0f, 0.0f} : df_exp_tab(a, T, K);  // below 1e-37: nothing
 }
 
+// The common case's term e^{l1} (cos phi, sin phi) in double-float with the
+// independent halves side by side on the packed FP32x2 instructions (per
+// lane the operations of df_sincos_tab and df_exp_tab): the reduction of phi
+// by pi/2 beside that of l1 by ln2/64, the sine and cosine polynomials, their
+// table combination and the final products.  Returns (re, im) as (x, y).
+__device__ __forceinline__ df2 cexp_pair(df l1, df ph, const DfTables &T, const DfConsts &K) {
+    const float qf = rintf(ph.hi * 0.636619772367581343076f);  // 2 / pi
+    const float kf = rintf(l1.hi * 92.33248261689366f);        // 64 / ln 2
+    const float2 nq = f2(-qf, -kf);
+    df2 r = df2_two_sum(f2_fma(nq, f2(K.pio2_1, K.ln2_64_1), f2(ph.hi, l1.hi)),
+                        f2(ph.lo, l1.lo));                       // exact products
+    r = df2_add_f(r, f2_mul(nq, f2(K.pio2_2, K.ln2_64_2)));    // exact products
+    r = df2_add_f(r, f2_mul(nq, f2(K.pio2_3, K.ln2_64_3)));
+    const df s = df_add_f(df2_x(r), -qf * K.pio2_4);
+    const df er = df2_y(r);
+    // sine and cosine of s by the pi/64 table
+    float jf = rintf(s.hi * 20.371832715762604f);  // 64 / pi
+    jf = fminf(fmaxf(jf, -16.0f), 16.0f);
+    df rr = df_two_sum(fmaf(-jf, K.pi64_1, s.hi), s.lo);  // exact product
+    rr = df_add_f(rr, -jf * K.pi64_2);                     // exact product
+    rr = df_add_f(rr, -jf * K.pi64_3);
+    const df r2 = df_mul(rr, rr);
+    const float x = r2.hi;
+    const float ts = x * x * fmaf(-x, 1.0f / 5040.0f, 1.0f / 120.0f);
+    const float tc = x * x * fmaf(fmaf(x, 1.0f / 40320.0f, -1.0f / 720.0f), x, 1.0f / 24.0f);
+    const df sixth = {-0x1.555556p-3f, 0x1.555556p-28f};  // -1/6
+    df2 w = df2_make(df_mul(r2, sixth), df{-0.5f * r2.hi, -0.5f * r2.lo});
+    w = df2_add_f(df2_add_f(w, f2(ts, tc)), f2(1.0f, 1.0f));
+    const df sr = df_mul(rr, df2_x(w)), cr = df2_y(w);
+    const int j = (int)jf + 16;
+    const df S = T.sn[j], C = T.cs[j];
+    const df2 P = df2_mul(df2_make(S, C), df2_make(cr, cr));  // (S cr, C cr)
+    df2 Q = df2_mul(df2_make(C, S), df2_make(sr, sr));        // (C sr, S sr)
+    Q.hi.y = -Q.hi.y;
+    Q.lo.y = -Q.lo.y;
+    const df2 sc = df2_add(P, Q);  // (sin s, cos s)
+    df sp, cp;
+    switch (((int)qf) & 3) {
+        case 0: sp = df2_x(sc); cp = df2_y(sc); break;
+        case 1: sp = df2_y(sc); cp = df_neg(df2_x(sc)); break;
+        case 2: sp = df_neg(df2_x(sc)); cp = df_neg(df2_y(sc)); break;
+        default: sp = df_neg(df2_y(sc)); cp = df2_x(sc); break;
+    }
+    // e^{l1} by the 2^(j/64) table
+    const float xe = er.hi;
+    const float qt = xe * fmaf(fmaf(xe, 1.0f / 120.0f, 1.0f / 24.0f), xe, 1.0f / 6.0f);
+    const df q = df_fast_two_sum(0.5f, qt);
+    const df pe = df_add_f(df_add(er, df_mul(df_mul(er, er), q)), 1.0f);
+    const int n = (int)kf;
+    const df t = df_mul(T.exp2[n & 63], pe);
+    const float scale = __int_as_float(((n >> 6) + 127) << 23);
+    const df e1 = l1.hi < -87.0f ? df{0.0f, 0.0f} : df{t.hi * scale, t.lo * scale};
+    return df2_mul(df2_make(e1, e1), df2_make(cp, sp));
+}
+
 // Terms below 2^-27 (exponent l1 below kSmallLog) need no double-float
 // result: their absolute error stays below 2^-46, what the double-float
 // evaluation commits on terms of order one, when
@@ -357,6 +412,7 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 5)
     const double2 t = kvalid ? tw[k] : make_double2(0.0, 0.0);
     const double cm1d = t.x, snd = t.y;
     const df cm1 = df_from_double(t.x), sn = df_from_double(t.y);
+    const df2 cs_pair = df2_make(cm1, sn), sc_pair = df2_make(sn, cm1);
     double am_re = 0.0, am_im = 0.0, ap_re = 0.0, ap_im = 0.0;
     GfRec *mine = s_rec[grp];
 
@@ -369,16 +425,20 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 5)
         if (kvalid) {
             df pm_re = {0.0f, 0.0f}, pm_im = {0.0f, 0.0f}, pp_re = {0.0f, 0.0f},
                pp_im = {0.0f, 0.0f};
-            df pb_re = {0.0f, 0.0f}, pb_im = {0.0f, 0.0f};  // terms of both estimators
+            df2 pb = {f2(0.0f, 0.0f), f2(0.0f, 0.0f)};  // terms of both estimators (re, im)
             float sm_re = 0.0f, sm_im = 0.0f;  // small terms of both estimators
             for (int m = 0; m < nmine; ++m) {
                 const GfRec &g = mine[m];
                 const bool in1 = d0 <= g.w1;
                 const bool in2 = dpi <= g.w2;
                 if (!(in1 || in2)) continue;
-                const df x = g.x, y = g.y;
-                const df l1 = df_sub(df_mul(cm1, x), df_mul(sn, y));  // (cos-1) x - sin y
-                const df ph = df_add(df_mul(sn, x), df_mul(cm1, y));  // sin x + (cos-1) y
+                // (l1, phi) = ((cos-1) x - sin y, sin x + (cos-1) y), side by side
+                const df2 A = df2_mul(cs_pair, df2_make(g.x, g.x));
+                df2 B = df2_mul(sc_pair, df2_make(g.y, g.y));
+                B.hi.x = -B.hi.x;
+                B.lo.x = -B.lo.x;
+                const df2 lp = df2_add(A, B);
+                const df l1 = df2_x(lp), ph = df2_y(lp);
                 const df c1 = g.c1;
                 const df inv = g.inv;
                 // n >= 0 with e^{-2n} below double rounding and no term near
@@ -416,14 +476,12 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 5)
                     small_term(l1, ph, K, sm_re, sm_im);
                     continue;
                 }
-                df sp, cp;
-                df_sincos_tab(ph, s_tab, K, sp, cp);
                 if (plain) {
-                    const df e1 = df_exp_small(l1, s_tab, K);
-                    pb_re = df_add(pb_re, df_mul(e1, cp));
-                    pb_im = df_add(pb_im, df_mul(e1, sp));
+                    pb = df2_add(pb, cexp_pair(l1, ph, s_tab, K));
                     continue;
                 }
+                df sp, cp;
+                df_sincos_tab(ph, s_tab, K, sp, cp);
                 df e1 = {0.0f, 0.0f}, e2 = {0.0f, 0.0f};
                 if (in1) {
                     e1 = df_exp_small(a1, s_tab, K);
@@ -435,8 +493,8 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 5)
                 pm_re = df_add(pm_re, df_mul(df_mul(df_add(e1, e2), inv), cp));
                 pm_im = df_add(pm_im, df_mul(df_mul(df_sub(e1, e2), inv), sp));
             }
-            const double both_re = df_to_double(pb_re) + (double)sm_re;
-            const double both_im = df_to_double(pb_im) + (double)sm_im;
+            const double both_re = df_to_double(df2_x(pb)) + (double)sm_re;
+            const double both_im = df_to_double(df2_y(pb)) + (double)sm_im;
             am_re += df_to_double(pm_re) + both_re;
             am_im += df_to_double(pm_im) + both_im;
             ap_re += df_to_double(pp_re) + both_re;
