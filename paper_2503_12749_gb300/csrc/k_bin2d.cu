@@ -396,35 +396,49 @@ __global__ void k_sep_prep(const double *__restrict__ n_in, const double2 *__res
     }
 }
 
-// unnormalised double-float complex product a b: (re.hi, re.lo, im.hi, im.lo)
-__device__ __forceinline__ float4 dfc_mul(const float4 a, const float4 b) {
-    const float p1 = a.x * b.x, e1 = fmaf(a.x, b.x, -p1);
-    const float p2 = a.z * b.z, e2 = fmaf(a.z, b.z, -p2);
-    const df sr = df_two_sum(p1, -p2);
-    const float lr = fmaf(a.x, b.y, fmaf(a.y, b.x, e1)) - fmaf(a.z, b.w, fmaf(a.w, b.z, e2)) + sr.lo;
-    const float p3 = a.x * b.z, e3 = fmaf(a.x, b.z, -p3);
-    const float p4 = a.z * b.x, e4 = fmaf(a.z, b.x, -p4);
-    const df si = df_two_sum(p3, p4);
-    const float li = fmaf(a.x, b.w, fmaf(a.y, b.z, e3)) + fmaf(a.z, b.y, fmaf(a.w, b.x, e4)) + si.lo;
-    return make_float4(sr.hi, lr, si.hi, li);
+// Complex double-float numbers with the real and imaginary parts side by
+// side on the packed FP32x2 instructions (per lane the scalar double-float
+// operations): hi = (re.hi, im.hi), lo = (re.lo, im.lo), stored as float4
+// (re.hi, im.hi, re.lo, im.lo).
+__device__ __forceinline__ df2 c_load(const float4 v) { return {f2(v.x, v.y), f2(v.z, v.w)}; }
+
+// The lane pairs a complex product reads of its left factor a ...
+struct CLeft {
+    float2 rr_hi, ii_hi, rr_lo, ii_lo;  // (re, re), (im, im) of hi and lo
+};
+__device__ __forceinline__ CLeft c_left(const float4 v) {
+    return {f2(v.x, v.x), f2(v.y, v.y), f2(v.z, v.z), f2(v.w, v.w)};
+}
+// ... and of its right factor b
+struct CRight {
+    float2 h, hs, l, ls;  // (re, im) and (im, re) of hi and lo
+};
+__device__ __forceinline__ CRight c_right(const float4 v) {
+    return {f2(v.x, v.y), f2(v.y, v.x), f2(v.z, v.w), f2(v.w, v.z)};
 }
 
-// acc += t (both unnormalised double-float complex)
-__device__ __forceinline__ void dfc_acc(float4 &acc, const float4 t) {
-    const df r = df_two_sum(acc.x, t.x);
-    const df i = df_two_sum(acc.z, t.z);
-    acc = make_float4(r.hi, acc.y + t.y + r.lo, i.hi, acc.w + t.w + i.lo);
+// unnormalised double-float complex product a b: the real part
+// (ar br - ai bi) in lane x, the imaginary part (ar bi + ai br) in lane y;
+// the two-products' errors and the cross terms of the low parts in FP32
+__device__ __forceinline__ df2 c_mul(const CLeft &a, const CRight &b) {
+    const float2 p13 = f2_mul(a.rr_hi, b.h);   // (ar br, ar bi)
+    const float2 e13 = f2_fma(a.rr_hi, b.h, f2_neg(p13));
+    const float2 p24 = f2_mul(a.ii_hi, b.hs);  // (ai bi, ai br)
+    const float2 e24 = f2_fma(a.ii_hi, b.hs, f2_neg(p24));
+    const float2 sg = f2(-1.0f, 1.0f);
+    const df2 s = df2_two_sum(p13, f2_mul(p24, sg));
+    const float2 l1 = f2_fma(a.rr_hi, b.l, f2_fma(a.rr_lo, b.h, e13));
+    const float2 l2 = f2_fma(a.ii_hi, b.ls, f2_fma(a.ii_lo, b.hs, e24));
+    return {s.hi, f2_add(f2_fma(l2, sg, l1), s.lo)};
 }
 
-__device__ __forceinline__ float4 dfc_scale(const float4 a, const df s) {
-    const df re = df_mul(df{a.x, a.y}, s), im = df_mul(df{a.z, a.w}, s);
-    return make_float4(re.hi, re.lo, im.hi, im.lo);
+// acc += t (both unnormalised)
+__device__ __forceinline__ void c_acc(df2 &acc, const df2 t) {
+    const df2 r = df2_two_sum(acc.hi, t.hi);
+    acc = {r.hi, f2_add(f2_add(acc.lo, t.lo), r.lo)};
 }
 
-__device__ __forceinline__ float4 dfc_norm(const float4 a) {
-    const df re = df_fast_two_sum(a.x, a.y), im = df_fast_two_sum(a.z, a.w);
-    return make_float4(re.hi, re.lo, im.hi, im.lo);
-}
+__device__ __forceinline__ df2 c_norm(const df2 a) { return df2_fast_two_sum(a.hi, a.lo); }
 
 constexpr int kSepFlush = 4;  // rounds between additions to the FP64 sums
 
@@ -504,13 +518,13 @@ __global__ void __launch_bounds__(kSepThreads, 2)
         kB[p] = v2[p] ? slot_k(sb, KB, sl.W1[d - 1], sl.W2[d - 1]) : 0;
     }
     double dP[2][2][2] = {}, dX[2][2][2] = {};  // +P and (matrix-P - +P), (re, im)
-    float4 aP[2][2], aX[2][2];  // double-float sums
+    df2 aP[2][2], aX[2][2];  // double-float sums (re, im side by side)
     float2 fP[2][2], fX[2][2];  // FP32 sums of the terms below 2^-24
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            aP[p][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            aP[p][q] = {f2(0.f, 0.f), f2(0.f, 0.f)};
             aX[p][q] = aP[p][q];
             fP[p][q] = make_float2(0.f, 0.f);
             fX[p][q] = fP[p][q];
@@ -559,12 +573,12 @@ __global__ void __launch_bounds__(kSepThreads, 2)
                 if (ea.hi >= -87.0f) {
                     const df e = df_exp_tab(ea, s_tab, K);
                     const df re = df_mul(e, cp), im = df_mul(e, sp);
-                    A = make_float4(re.hi, re.lo, im.hi, im.lo);
+                    A = make_float4(re.hi, im.hi, re.lo, im.lo);
                 }
                 if ((st.flags & 4) && eb.hi >= -87.0f) {
                     const df e = df_exp_tab(eb, s_tab, K);
                     const df re = df_mul(e, cp), im = df_mul(e, sp);
-                    B = make_float4(re.hi, re.lo, -im.hi, -im.lo);
+                    B = make_float4(re.hi, -im.hi, re.lo, -im.lo);
                 }
             }
             if (fac == 0) {
@@ -575,8 +589,8 @@ __global__ void __launch_bounds__(kSepThreads, 2)
                 sB2[j][sidx] = B;
             }
             // the 32 slots of one (trajectory, factor) are one warp's items
-            const unsigned ma = __float_as_uint(fmaxf(fabsf(A.x), fabsf(A.z)));
-            const unsigned mb = __float_as_uint(fmaxf(fabsf(B.x), fabsf(B.z)));
+            const unsigned ma = __float_as_uint(fmaxf(fabsf(A.x), fabsf(A.y)));
+            const unsigned mb = __float_as_uint(fmaxf(fabsf(B.x), fabsf(B.y)));
             const unsigned wa = __reduce_max_sync(0xffffffffu, ma);
             const unsigned wb = __reduce_max_sync(0xffffffffu, mb);
             if (sidx == 0) {
@@ -644,8 +658,8 @@ __global__ void __launch_bounds__(kSepThreads, 2)
                 for (int p = 0; p < 2; ++p)
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
-                        const float tr = fmaf(A1[p].x, A2[q].x, -A1[p].z * A2[q].z);
-                        const float ti = fmaf(A1[p].x, A2[q].z, A1[p].z * A2[q].x);
+                        const float tr = fmaf(A1[p].x, A2[q].x, -A1[p].y * A2[q].y);
+                        const float ti = fmaf(A1[p].x, A2[q].y, A1[p].y * A2[q].x);
                         fP[p][q].x += tr;
                         fP[p][q].y += ti;
                         if (!rA1) {
@@ -654,17 +668,18 @@ __global__ void __launch_bounds__(kSepThreads, 2)
                         }
                     }
             } else if (mA >= 0x1p-25f) {
-                const float4 A1[2] = {sA1[j][2 * ty], sA1[j][2 * ty + 1]};
-                const float4 A2[2] = {sA2[j][2 * tx], sA2[j][2 * tx + 1]};
+                const CLeft L[2] = {c_left(sA1[j][2 * ty]), c_left(sA1[j][2 * ty + 1])};
+                const CRight R[2] = {c_right(sA2[j][2 * tx]), c_right(sA2[j][2 * tx + 1])};
                 const df rAm1 = rA1 ? df{0.f, 0.f} : df_add_f(s_t[j].rA, -1.0f);
+                const df2 rAm1x2 = df2_make(rAm1, rAm1);
 #pragma unroll
                 for (int p = 0; p < 2; ++p)
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
-                        const float4 t = dfc_mul(A1[p], A2[q]);
-                        dfc_acc(aP[p][q], t);
+                        const df2 t = c_mul(L[p], R[q]);
+                        c_acc(aP[p][q], t);
                         // the matrix-P A term is rA t: (rA - 1) t into the difference
-                        if (!rA1) dfc_acc(aX[p][q], dfc_scale(t, rAm1));
+                        if (!rA1) c_acc(aX[p][q], df2_mul(t, rAm1x2));
                     }
             }
             if (mB >= 0x1p-63f) {
@@ -675,14 +690,16 @@ __global__ void __launch_bounds__(kSepThreads, 2)
                     for (int p = 0; p < 2; ++p)
 #pragma unroll
                         for (int q = 0; q < 2; ++q) {
-                            fX[p][q].x = fmaf(B1[p].x, B2[q].x, fmaf(-B1[p].z, B2[q].z, fX[p][q].x));
-                            fX[p][q].y = fmaf(B1[p].x, B2[q].z, fmaf(B1[p].z, B2[q].x, fX[p][q].y));
+                            fX[p][q].x = fmaf(B1[p].x, B2[q].x, fmaf(-B1[p].y, B2[q].y, fX[p][q].x));
+                            fX[p][q].y = fmaf(B1[p].x, B2[q].y, fmaf(B1[p].y, B2[q].x, fX[p][q].y));
                         }
                 } else {
+                    const CLeft L[2] = {c_left(B1[0]), c_left(B1[1])};
+                    const CRight R[2] = {c_right(B2[0]), c_right(B2[1])};
 #pragma unroll
                     for (int p = 0; p < 2; ++p)
 #pragma unroll
-                        for (int q = 0; q < 2; ++q) dfc_acc(aX[p][q], dfc_mul(B1[p], B2[q]));
+                        for (int q = 0; q < 2; ++q) c_acc(aX[p][q], c_mul(L[p], R[q]));
                 }
             }
         }
@@ -692,14 +709,14 @@ __global__ void __launch_bounds__(kSepThreads, 2)
         for (int p = 0; p < 2; ++p)
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-                aP[p][q] = dfc_norm(aP[p][q]);
-                aX[p][q] = dfc_norm(aX[p][q]);
+                aP[p][q] = c_norm(aP[p][q]);
+                aX[p][q] = c_norm(aX[p][q]);
                 if (flush) {
-                    dP[p][q][0] += (double)aP[p][q].x + (double)aP[p][q].y + (double)fP[p][q].x;
-                    dP[p][q][1] += (double)aP[p][q].z + (double)aP[p][q].w + (double)fP[p][q].y;
-                    dX[p][q][0] += (double)aX[p][q].x + (double)aX[p][q].y + (double)fX[p][q].x;
-                    dX[p][q][1] += (double)aX[p][q].z + (double)aX[p][q].w + (double)fX[p][q].y;
-                    aP[p][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    dP[p][q][0] += (double)aP[p][q].hi.x + (double)aP[p][q].lo.x + (double)fP[p][q].x;
+                    dP[p][q][1] += (double)aP[p][q].hi.y + (double)aP[p][q].lo.y + (double)fP[p][q].y;
+                    dX[p][q][0] += (double)aX[p][q].hi.x + (double)aX[p][q].lo.x + (double)fX[p][q].x;
+                    dX[p][q][1] += (double)aX[p][q].hi.y + (double)aX[p][q].lo.y + (double)fX[p][q].y;
+                    aP[p][q] = {f2(0.f, 0.f), f2(0.f, 0.f)};
                     aX[p][q] = aP[p][q];
                     fP[p][q] = make_float2(0.f, 0.f);
                     fX[p][q] = fP[p][q];
