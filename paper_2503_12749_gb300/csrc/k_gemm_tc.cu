@@ -43,7 +43,8 @@
 //               A0 B0), releasing each stage at once;
 //   warps 2..9  epilogue: warp w reads TMEM lanes 32 (w mod 4).. (its A rows)
 //               and half (w - 2) / 4 of the tile's trajectories: running
-//               sums of 64 alpha' and 64 beta' columns per thread.  After the
+//               sums of 64 alpha' and 64 beta' columns per thread (packed
+//               FP32x2 additions, round to nearest per element).  After the
 //               last K block: occupations, butterfly transpose-reduction over
 //               the 32 lanes, then the 4 lane quarters in a fixed order -> one
 //               n_S partial per (mode tile, trajectory).  alpha', beta' never
@@ -53,9 +54,10 @@
 //               of 64 bytes, 8 rows per instruction.
 // Sampling variant (3 products, 512 threads): warps 4..11 are the
 // epilogue, and warps 2, 3, 12..15 run the BF16 sampler (sampler_dev.cuh)
-// on the NEXT chunk's trajectories, into the second sample operand, while
-// the tensor cores work on this one: the sampler is issue-bound and the GEMM
-// leaves most issue slots idle.  Registers: launched at 128 per thread
+// on the NEXT chunk's trajectories (of the one network, or of several
+// networks of a batch round taken as one list), into the second sample
+// operand, while the tensor cores work on this one: the sampler is
+// issue-bound and the GEMM leaves most issue slots idle.  Registers: launched at 128 per thread
 // (65,536 per CTA), the two epilogue warpgroups take 168 each and the other
 // two give up theirs down to 88 (setmaxnreg; 2 x 128 x 168 + 2 x 128 x 88 =
 // 65,536); the host launches this variant only after checking that the
