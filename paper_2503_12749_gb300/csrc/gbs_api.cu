@@ -60,38 +60,59 @@ void prof_mark(gbs_net *net, int phase, int launches_if_stop, bool start) {
 // memory when a network is freed (release threshold raised once per device
 // for this process), so creating and freeing networks in a loop does not go
 // back to the driver for every network.  Allocated and freed on the
-// network's stream.
+// network's stream; plain cudaMalloc / cudaFree on a device without
+// memory pools.
+namespace {
+// per device: 0 not yet known, -1 plain cudaMalloc (no memory pools), 1 pool
+int g_pool_state[64] = {};
+std::mutex g_pool_mu;
+
+bool pool_supported() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return false;
+    }
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (g_pool_state[dev] == 0) {
+        int ok = 0;
+        cudaMemPool_t pool;
+        if (cudaDeviceGetAttribute(&ok, cudaDevAttrMemoryPoolsSupported, dev) == cudaSuccess && ok &&
+            cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            g_pool_state[dev] = 1;
+        } else {
+            g_pool_state[dev] = -1;
+        }
+        cudaGetLastError();
+    }
+    return g_pool_state[dev] == 1;
+}
+}  // namespace
+
 int pool_alloc(void **p, size_t bytes, cudaStream_t stream, const char *what) {
-    static std::mutex mu;
-    static bool done[64] = {};
     *p = nullptr;
     if (bytes == 0) return GBS_OK;
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
-        std::lock_guard<std::mutex> lock(mu);
-        if (!done[dev]) {
-            cudaMemPool_t pool;
-            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-                uint64_t thr = ~0ull;
-                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-            }
-            cudaGetLastError();
-            done[dev] = true;
-        }
-    }
-    const cudaError_t err = cudaMallocAsync(p, bytes, stream);
+    // without stream-ordered pools on this device: plain allocations
+    const bool pool = pool_supported();
+    const cudaError_t err = pool ? cudaMallocAsync(p, bytes, stream) : cudaMalloc(p, bytes);
     if (err != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
         return set_error(err == cudaErrorMemoryAllocation ? GBS_ENOMEM : GBS_ECUDA,
-                         "cudaMallocAsync(%s, %zu bytes) failed: %s", what, bytes,
-                         cudaGetErrorString(err));
+                         "%s(%s, %zu bytes) failed: %s", pool ? "cudaMallocAsync" : "cudaMalloc",
+                         what, bytes, cudaGetErrorString(err));
     }
     return GBS_OK;
 }
 
 void pool_free_raw(void *p, cudaStream_t stream) {
-    if (p) cudaFreeAsync(p, stream);
+    if (!p) return;
+    if (pool_supported())
+        cudaFreeAsync(p, stream);
+    else
+        cudaFree(p);
 }
 
 namespace {
@@ -139,7 +160,7 @@ int pool_alloc_n(T **p, size_t count, cudaStream_t stream, const char *what) {
 
 template <typename T>
 void pool_free(T *&p, cudaStream_t stream) {
-    if (p) cudaFreeAsync(p, stream);
+    pool_free_raw(p, stream);
     p = nullptr;
 }
 
