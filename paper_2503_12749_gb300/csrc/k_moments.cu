@@ -49,6 +49,7 @@
 // from n itself.
 #include "gbs_internal.cuh"
 #include "tc_ptx.cuh"
+#include "dfloat.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -147,6 +148,53 @@ __device__ __forceinline__ void element(A re, A im, A w, A s, A eA, A eB, A eP, 
         const A fi = (c & 1) ? f_oi : fei;
         add(Lay::B0 + c, wr * fr - wi * fi);
         add(Lay::B1 + c, wr * ppr - wi * ppi);
+    }
+}
+
+// The FP32 route's element with its sums in pairs on the packed FP32x2
+// instructions: pair k < KM holds the moment quantities q = 2k, 2k + 1
+// (+P Re n'^m for q < MM; matrix-P tanh(n) Re n'^m of odd m above), pair
+// KM + c the matrix-P and +P marginal terms of count c (q = B0 + c, B1 + c);
+// marginal factors unscaled (1/c! applied to the sums).
+template <int MM, int CM>
+__device__ __forceinline__ void element_f2(float re, float im, float w, float s, float eA, float eB,
+                                           float eP, float2 (&pp)[MomLayout<MM, CM>::Q / 2]) {
+    constexpr int KM = (MM + MM / 2) / 2;
+    // moments: Re n'^m, m = 1..MM
+    float prs[MM];
+    float pr = re, pi = im;
+    prs[0] = re;
+#pragma unroll
+    for (int m = 2; m <= MM; ++m) {
+        const float tr = pr * re - pi * im;
+        pi = pr * im + pi * re;
+        pr = tr;
+        prs[m - 1] = pr;
+    }
+#pragma unroll
+    for (int k = 0; k < MM / 2; ++k) pp[k] = f2_add(pp[k], f2(prs[2 * k], prs[2 * k + 1]));
+#pragma unroll
+    for (int k = 0; k < MM / 4; ++k)
+        pp[MM / 2 + k] = f2_fma(f2(w, w), f2(prs[4 * k], prs[4 * k + 2]), pp[MM / 2 + k]);
+    // marginals: e^{-x + L} (cos, -s sin), e^{x - 2a + L} (cos, s sin) of Im n'
+    float sn, cs;
+    sin_cos(im, &sn, &cs);
+    const float t1r = eA * cs, t1i = -s * (eA * sn);
+    const float t2r = eB * cs, t2i = s * (eB * sn);
+    const float fer = t1r + t2r, fei = t1i + t2i;
+    const float f_or = s * (t1r - t2r), f_oi = s * (t1i - t2i);
+    const float ppr = eP * cs, ppi = -(eP * sn);
+    float wr = 1.0f, wi = 0.0f;  // n'^c, unscaled
+#pragma unroll
+    for (int c = 0; c <= CM; ++c) {
+        if (c > 0) {
+            const float xr = wr * re - wi * im;
+            wi = wr * im + wi * re;
+            wr = xr;
+        }
+        const float fr = (c & 1) ? f_or : fer;
+        const float fi = (c & 1) ? f_oi : fei;
+        pp[KM + c] = f2_fma(f2(wr, wr), f2(fr, ppr), f2_fma(f2(-wi, -wi), f2(fi, ppi), pp[KM + c]));
     }
 }
 
@@ -293,17 +341,33 @@ __global__ void __launch_bounds__(kMaxThreads)
         const int64_t off = (int64_t)((r - e0mod + n_sub) % n_sub) + (int64_t)k * n_sub;
 #pragma unroll
         for (int q = 0; q < Q; ++q) sacc[q * T + t] = 0.0;
+        // FP64 route: per-quantity sums; FP32 route: sums in pairs (element_f2)
         Real part[Q];
+        float2 pp[Q / 2];
 #pragma unroll
         for (int q = 0; q < Q; ++q) part[q] = Real(0);
+#pragma unroll
+        for (int k = 0; k < Q / 2; ++k) pp[k] = f2(0.0f, 0.0f);
         int np = 0;
         auto add_part = [&](int q, Real v) { part[q] += v; };
         auto add_smem = [&](int q, double v) { sacc[q * T + t] += v; };
         auto flush = [&]() {
+            if constexpr (sizeof(Real) == sizeof(float)) {
+                constexpr int KM = (MM + MM / 2) / 2;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                sacc[q * T + t] += (double)part[q];
-                part[q] = Real(0);
+                for (int k = 0; k < Q / 2; ++k) {
+                    const int q0 = k < KM ? 2 * k : Lay::B0 + (k - KM);
+                    const int q1 = k < KM ? 2 * k + 1 : Lay::B1 + (k - KM);
+                    sacc[q0 * T + t] += (double)pp[k].x;
+                    sacc[q1 * T + t] += (double)pp[k].y;
+                    pp[k] = f2(0.0f, 0.0f);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    sacc[q * T + t] += (double)part[q];
+                    part[q] = Real(0);
+                }
             }
         };
         const int64_t g0 = gtile;
@@ -335,8 +399,8 @@ __global__ void __launch_bounds__(kMaxThreads)
                             const bool neg = c_p.w < 0.0f;
                             const float sg = neg ? -1.0f : 1.0f;
                             const float eL = 1.0f - c_p.l2;
-                            element<float, MM, CM, false>(c_re, c_im, c_p.w, sg, (neg ? iP : eP) * eL,
-                                                          (neg ? eP : iP) * c_p.l2, eP, add_part);
+                            element_f2<MM, CM>(c_re, c_im, c_p.w, sg, (neg ? iP : eP) * eL,
+                                               (neg ? eP : iP) * c_p.l2, eP, pp);
                         } else {
                             element_log<MM, CM, false>((double)c_re, (double)c_im, nvals[i],
                                                        add_smem);
