@@ -35,14 +35,14 @@ UNIT = "samples/s"
 # DRAM bytes (read + write) of the GEMM kernel per trajectory, from the ncu
 # captures of one m1000 BF16x3 launch of 131072 trajectories: the plain GEMM
 # (profiles/k_gemm_tc_m1000_bf16x3.md: 1.0821 GB read + 0.0346 GB written)
-# and the sampling GEMM (profiles/k_gemm_tc_sampling_m1000.md: 1.0836 GB read
-# + 1.0619 GB written); the operands grow in proportion to the trajectories.
+# and the sampling GEMM (profiles/k_gemm_tc_sampling_m1000.md: 1.4707 GB read
+# + 1.0843 GB written); the operands grow in proportion to the trajectories.
 # Valid for the workload and kernel versions of those captures only.
 # keyed by (workload, precision, whether the GEMM also runs the next chunk's
 # sampler: then the traffic includes the next chunk's operand written)
 GEMM_TRAFFIC_BYTES_PER_SAMPLE = {
     ("m1000", "bf16x3", False): (1.082062e9 + 34.582016e6) / 131072,
-    ("m1000", "bf16x3", True): (1.083569e9 + 1.061864e9) / 131072,
+    ("m1000", "bf16x3", True): (1.470732e9 + 1.084348e9) / 131072,
 }
 
 
