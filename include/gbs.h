@@ -409,10 +409,12 @@ int gbs_profile_enable(gbs_net_t net, int enable);
 int gbs_profile_read(gbs_net_t net, double *ms, int64_t *launches);
 
 /* gbs_free_network -- synchronise the network's stream and release all memory
- * of the network (NULL is a no-op).  The chunk workspace (sample operands,
- * per-trajectory n, n_S, windows and records: about 1 GiB at N = 1000, twice
- * that with the folded sampler) comes from the device's default
- * stream-ordered memory pool, allocated and freed on the network's stream;
+ * of the network (NULL is a no-op).  All device memory of a network (the
+ * split T, the chunk workspace of sample operands, per-trajectory n, n_S,
+ * windows and records -- about 1 GiB at N = 1000, twice that with the folded
+ * sampler -- and the estimator's sums and tables) comes from the device's
+ * default stream-ordered memory pool, allocated and freed on the network's
+ * stream, so neither creating nor freeing a network synchronises the device;
  * the library raises that pool's release threshold once per device, so the
  * process keeps the memory for the next network instead of returning it to
  * the driver.  The stream must stay valid until this call. */

@@ -133,27 +133,6 @@ void prof_destroy(gbs_net *net) {
 }
 
 template <typename T>
-int dev_alloc(T **p, size_t count, const char *what) {
-    *p = nullptr;
-    if (count == 0) return GBS_OK;
-    cudaError_t err = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
-    if (err != cudaSuccess) {
-        *p = nullptr;
-        cudaGetLastError();
-        return set_error(err == cudaErrorMemoryAllocation ? GBS_ENOMEM : GBS_ECUDA,
-                         "cudaMalloc(%s, %zu bytes) failed: %s", what, count * sizeof(T),
-                         cudaGetErrorString(err));
-    }
-    return GBS_OK;
-}
-
-template <typename T>
-void dev_free(T *&p) {
-    if (p) cudaFree(p);
-    p = nullptr;
-}
-
-template <typename T>
 int pool_alloc_n(T **p, size_t count, cudaStream_t stream, const char *what) {
     return pool_alloc(reinterpret_cast<void **>(p), count * sizeof(T), stream, what);
 }
@@ -162,6 +141,17 @@ template <typename T>
 void pool_free(T *&p, cudaStream_t stream) {
     pool_free_raw(p, stream);
     p = nullptr;
+}
+
+// A network's own buffers, stream-ordered on its stream (used there, or on
+// streams forked from it after the allocation).
+template <typename T>
+int net_alloc(gbs_net *net, T **p, size_t count, const char *what) {
+    return pool_alloc_n(p, count, net->stream, what);
+}
+template <typename T>
+void net_free(gbs_net *net, T *&p) {
+    pool_free(p, net->stream);
 }
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -180,27 +170,26 @@ int64_t pick_chunk(const gbs_net *net) {
 }
 
 void release_estimator(gbs_net *net) {
-    dev_free(net->d_acc);
-    dev_free(net->d_counts);
-    dev_free(net->d_tw);
-    dev_free(net->d_wfft);
-    dev_free(net->d_fft0);
-    dev_free(net->d_fft1);
-    dev_free(net->d_out);
+    net_free(net, net->d_acc);
+    net_free(net, net->d_counts);
+    net_free(net, net->d_tw);
+    net_free(net, net->d_wfft);
+    net_free(net, net->d_fft0);
+    net_free(net, net->d_fft1);
+    net_free(net, net->d_out);
     net->counts.clear();
     net->est_fixed = false;
     net->n_sub = 0;
     net->K1 = 0;
-    dev_free(net->d_acc2);
-    dev_free(net->d_counts2);
-    dev_free(net->d_tw2);
-    dev_free(net->d_wf2);
-    dev_free(net->d_f2a);
-    dev_free(net->d_f2b);
-    dev_free(net->d_out2);
-    dev_free(net->d_mo2);
-    if (net->d_sep2) cudaFree(net->d_sep2);
-    net->d_sep2 = nullptr;
+    net_free(net, net->d_acc2);
+    net_free(net, net->d_counts2);
+    net_free(net, net->d_tw2);
+    net_free(net, net->d_wf2);
+    net_free(net, net->d_f2a);
+    net_free(net, net->d_f2b);
+    net_free(net, net->d_out2);
+    net_free(net, net->d_mo2);
+    pool_free(net->d_sep2, net->stream);
     net->counts2.clear();
     net->est2_fixed = false;
     net->n_sub2 = 0;
@@ -212,10 +201,10 @@ void release_all(gbs_net *net) {
     release_estimator(net);
     prof_destroy(net);
     if (net->tc) tc_plan_destroy(net);
-    dev_free(net->d_sq64);
-    dev_free(net->d_sq32);
-    dev_free(net->d_T64);
-    dev_free(net->d_A);
+    net_free(net, net->d_sq64);
+    net_free(net, net->d_sq32);
+    net_free(net, net->d_T64);
+    net_free(net, net->d_A);
     pool_free(net->d_B, net->stream);
     pool_free(net->d_B_alt, net->stream);
     pool_free(net->d_n_alt, net->stream);
@@ -224,11 +213,11 @@ void release_all(gbs_net *net) {
     pool_free(net->d_nS, net->stream);
     pool_free(net->d_win, net->stream);
     pool_free(net->d_gfrec, net->stream);
-    dev_free(net->d_wmax);
-    dev_free(net->d_flags);
-    dev_free(net->d_nS2);
-    dev_free(net->d_win2);
-    dev_free(net->d_wmax2);
+    net_free(net, net->d_wmax);
+    net_free(net, net->d_flags);
+    net_free(net, net->d_nS2);
+    net_free(net, net->d_win2);
+    net_free(net, net->d_wmax2);
 }
 
 // Sampler + propagation + finalize for one chunk of `count` trajectories.
@@ -431,20 +420,19 @@ int fix_estimator2d(gbs_net *net, int n_sub, const int *K) {
     net->grid2 = grid;
     const size_t accn = (size_t)2 * n_sub * grid;
     int rc;
-    if ((rc = dev_alloc(&net->d_acc2, accn, "acc2")) ||
-        (rc = dev_alloc(&net->d_counts2, (size_t)n_sub, "counts2")) ||
-        (rc = dev_alloc(&net->d_tw2, (size_t)tot, "tw2")) ||
-        (rc = dev_alloc(&net->d_wf2, (size_t)tot, "wf2")) ||
-        (rc = dev_alloc(&net->d_f2a, accn, "fft2a")) ||
-        (rc = dev_alloc(&net->d_f2b, accn, "fft2b")) ||
-        (rc = dev_alloc(&net->d_out2, (size_t)4 * grid, "out2")) ||
-        (rc = dev_alloc(&net->d_mo2, (size_t)kMaxBins, "window offsets")))
+    if ((rc = net_alloc(net, &net->d_acc2, accn, "acc2")) ||
+        (rc = net_alloc(net, &net->d_counts2, (size_t)n_sub, "counts2")) ||
+        (rc = net_alloc(net, &net->d_tw2, (size_t)tot, "tw2")) ||
+        (rc = net_alloc(net, &net->d_wf2, (size_t)tot, "wf2")) ||
+        (rc = net_alloc(net, &net->d_f2a, accn, "fft2a")) ||
+        (rc = net_alloc(net, &net->d_f2b, accn, "fft2b")) ||
+        (rc = net_alloc(net, &net->d_out2, (size_t)4 * grid, "out2")) ||
+        (rc = net_alloc(net, &net->d_mo2, (size_t)kMaxBins, "window offsets")))
         return rc;
     if (net->precision != GBS_FP64) {
-        uint8_t *sep = nullptr;
-        if ((rc = dev_alloc(&sep, (size_t)net->chunk * sep2_bytes_per_trajectory(), "sep2")))
+        if ((rc = pool_alloc(&net->d_sep2, (size_t)net->chunk * sep2_bytes_per_trajectory(),
+                             net->stream, "sep2")))
             return rc;
-        net->d_sep2 = sep;
     }
     GBS_CUDA_TRY(cudaMemsetAsync(net->d_acc2, 0, accn * sizeof(double2), net->stream));
     GBS_CUDA_TRY(cudaMemsetAsync(net->d_counts2, 0, (size_t)n_sub * sizeof(int64_t), net->stream));
@@ -477,13 +465,13 @@ int fix_estimator(gbs_net *net, int n_sub, int K1) {
     net->K1 = K1;
     const size_t accn = (size_t)2 * n_sub * K1;
     int rc;
-    if ((rc = dev_alloc(&net->d_acc, accn, "acc")) ||
-        (rc = dev_alloc(&net->d_counts, (size_t)n_sub, "counts")) ||
-        (rc = dev_alloc(&net->d_tw, (size_t)K1, "tw")) ||
-        (rc = dev_alloc(&net->d_wfft, (size_t)K1, "wfft")) ||
-        (rc = dev_alloc(&net->d_fft0, accn, "fft0")) ||
-        (rc = dev_alloc(&net->d_fft1, accn, "fft1")) ||
-        (rc = dev_alloc(&net->d_out, (size_t)4 * K1, "out"))) {
+    if ((rc = net_alloc(net, &net->d_acc, accn, "acc")) ||
+        (rc = net_alloc(net, &net->d_counts, (size_t)n_sub, "counts")) ||
+        (rc = net_alloc(net, &net->d_tw, (size_t)K1, "tw")) ||
+        (rc = net_alloc(net, &net->d_wfft, (size_t)K1, "wfft")) ||
+        (rc = net_alloc(net, &net->d_fft0, accn, "fft0")) ||
+        (rc = net_alloc(net, &net->d_fft1, accn, "fft1")) ||
+        (rc = net_alloc(net, &net->d_out, (size_t)4 * K1, "out"))) {
         release_estimator(net);
         return rc;
     }
@@ -545,21 +533,22 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
     if (!T_device) {
         // T in host memory: upload it as given and build the operand layout
         // (and check for non-finite entries) on the GPU, as for device T
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
         double *tmp = nullptr;
         int rc0;
-        if ((rc0 = dev_alloc(&tmp, (size_t)2 * M * N, "T upload"))) return rc0;
-        if (cudaMemcpy(tmp, T, sizeof(double) * 2 * (size_t)M * N, cudaMemcpyHostToDevice) !=
-            cudaSuccess) {
+        if ((rc0 = pool_alloc_n(&tmp, (size_t)2 * M * N, st, "T upload"))) return rc0;
+        if (cudaMemcpyAsync(tmp, T, sizeof(double) * 2 * (size_t)M * N, cudaMemcpyHostToDevice,
+                            st) != cudaSuccess) {
             cudaGetLastError();
-            dev_free(tmp);
+            pool_free(tmp, st);
             return set_error(GBS_ECUDA, "upload of T failed");
         }
         rc0 = make_network(N, M, tmp, true, r, precision, stream, out);
-        if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
             cudaGetLastError();
             if (!rc0) rc0 = set_error(GBS_ECUDA, "network set-up failed");
         }
-        dev_free(tmp);
+        pool_free(tmp, st);
         return rc0;
     }
 
@@ -594,33 +583,34 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
         sq64[j] = make_double2(std::sqrt(0.5 * sp), std::sqrt(0.5 * sm));
         sq32[j] = make_float2((float)sq64[j].x, (float)sq64[j].y);
     }
-    if ((rc = dev_alloc(&net->d_sq64, (size_t)N, "sq64")) ||
-        (rc = dev_alloc(&net->d_sq32, (size_t)N, "sq32")))
+    if ((rc = net_alloc(net, &net->d_sq64, (size_t)N, "sq64")) ||
+        (rc = net_alloc(net, &net->d_sq32, (size_t)N, "sq32")))
         return fail(rc);
-    if (cudaMemcpy(net->d_sq64, sq64.data(), sizeof(double2) * N, cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemcpy(net->d_sq32, sq32.data(), sizeof(float2) * N, cudaMemcpyHostToDevice) !=
-            cudaSuccess)
+    if (cudaMemcpyAsync(net->d_sq64, sq64.data(), sizeof(double2) * N, cudaMemcpyHostToDevice,
+                        net->stream) != cudaSuccess ||
+        cudaMemcpyAsync(net->d_sq32, sq32.data(), sizeof(float2) * N, cudaMemcpyHostToDevice,
+                        net->stream) != cudaSuccess ||
+        cudaStreamSynchronize(net->stream) != cudaSuccess)  // the host vectors go out of scope
         return fail(set_error(GBS_ECUDA, "upload of sampler coefficients failed"));
 
     unsigned long long *d_bad = nullptr;
     if (T_device) {
-        if ((rc = dev_alloc(&d_bad, (size_t)1, "T check")) ) return fail(rc);
+        if ((rc = net_alloc(net, &d_bad, (size_t)1, "T check"))) return fail(rc);
         if (cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), net->stream) != cudaSuccess) {
-            dev_free(d_bad);
+            net_free(net, d_bad);
             return fail(set_error(GBS_ECUDA, "memset failed"));
         }
     }
     const int conv_blocks =
         (int)std::min<int64_t>(((int64_t)M * N + 255) / 256, (int64_t)net->sm_count * 16);
     if (precision == GBS_FP64 && T_device) {
-        if ((rc = dev_alloc(&net->d_T64, (size_t)M * 2 * N, "T64"))) {
-            dev_free(d_bad);
+        if ((rc = net_alloc(net, &net->d_T64, (size_t)M * 2 * N, "T64"))) {
+            net_free(net, d_bad);
             return fail(rc);
         }
         k_t64_from_dev<<<conv_blocks, 256, 0, net->stream>>>(T, N, M, net->d_T64, d_bad);
         rc = finish_device_T(net, d_bad);
-        dev_free(d_bad);
+        net_free(net, d_bad);
         if (rc) return fail(rc);
     } else {
         // A = [Re T_i.; Im T_i.] rows interleaved per output mode, T rounded to
@@ -633,19 +623,19 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
         net->rowsA = 2 * M;
         const size_t plane = (size_t)net->rowsA * net->ldK;
         if (T_device) {
-            if ((rc = dev_alloc(&net->d_A, (size_t)net->planesA * plane, "A planes"))) {
-                dev_free(d_bad);
+            if ((rc = net_alloc(net, &net->d_A, (size_t)net->planesA * plane, "A planes"))) {
+                net_free(net, d_bad);
                 return fail(rc);
             }
             if (cudaMemsetAsync(net->d_A, 0, (size_t)net->planesA * plane * sizeof(__nv_bfloat16),
                                 net->stream) != cudaSuccess) {
-                dev_free(d_bad);
+                net_free(net, d_bad);
                 return fail(set_error(GBS_ECUDA, "memset of T planes failed"));
             }
             k_split_from_dev<<<conv_blocks, 256, 0, net->stream>>>(T, N, M, net->rowsA, net->d_A,
                                                                   plane, d_bad);
             rc = finish_device_T(net, d_bad);
-            dev_free(d_bad);
+            net_free(net, d_bad);
             if (rc) return fail(rc);
         }
     }
@@ -665,10 +655,10 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
         (rc = pool_alloc_n(&net->d_nS_part, (size_t)net->chunk * net->mtiles, net->stream, "nS_part")) ||
         (rc = pool_alloc_n(&net->d_nS, (size_t)net->chunk, net->stream, "nS")) ||
         (rc = pool_alloc_n(&net->d_win, (size_t)net->chunk, net->stream, "windows")) ||
-        (rc = dev_alloc(&net->d_wmax, (size_t)2, "window union")) ||
-        (rc = dev_alloc(&net->d_flags, (size_t)4, "flags")))
+        (rc = net_alloc(net, &net->d_wmax, (size_t)2, "window union")) ||
+        (rc = net_alloc(net, &net->d_flags, (size_t)4, "flags")))
         return fail(rc);
-    if (cudaMemset(net->d_flags, 0, 4 * sizeof(unsigned long long)) != cudaSuccess)
+    if (cudaMemsetAsync(net->d_flags, 0, 4 * sizeof(unsigned long long), net->stream) != cudaSuccess)
         return fail(set_error(GBS_ECUDA, "memset of flags failed"));
     if (precision != GBS_FP64) {
         if ((rc = pool_alloc(&net->d_gfrec, (size_t)net->chunk * gf_record_bytes(), net->stream,
@@ -732,9 +722,9 @@ int gbs_make_network_binned(int N, int M, const double *T, const double *r, cons
     net->nbins = d;
     for (int b = 0; b <= kMaxBins; ++b) net->bin_tiles[b] = tiles[b];
     net->M_user = M;
-    if ((rc = dev_alloc(&net->d_nS2, (size_t)d * net->chunk, "nS per bin")) ||
-        (rc = dev_alloc(&net->d_win2, (size_t)net->chunk, "windows per bin")) ||
-        (rc = dev_alloc(&net->d_wmax2, (size_t)2 * kMaxBins, "window union per bin"))) {
+    if ((rc = net_alloc(net, &net->d_nS2, (size_t)d * net->chunk, "nS per bin")) ||
+        (rc = net_alloc(net, &net->d_win2, (size_t)net->chunk, "windows per bin")) ||
+        (rc = net_alloc(net, &net->d_wmax2, (size_t)2 * kMaxBins, "window union per bin"))) {
         gbs_free_network(net);
         return rc;
     }
@@ -865,7 +855,7 @@ int gbs_histogram(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E
     spec.hi = hi;
     const size_t total = (size_t)2 * nm * (nbins + 2);
     unsigned long long *d_cnt = nullptr;
-    if ((rc = dev_alloc(&d_cnt, total, "histogram"))) return rc;
+    if ((rc = net_alloc(net, &d_cnt, total, "histogram"))) return rc;
     if (cudaMemsetAsync(d_cnt, 0, total * sizeof(unsigned long long), net->stream) != cudaSuccess)
         rc = set_error(GBS_ECUDA, "memset of the histogram failed");
     const int saved_K1 = net->K1;
@@ -885,7 +875,7 @@ int gbs_histogram(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E
         else
             for (size_t q = 0; q < total; ++q) counts[q] = (int64_t)h[q];
     }
-    dev_free(d_cnt);
+    net_free(net, d_cnt);
     return rc;
 }
 
@@ -945,8 +935,8 @@ int gbs_debug_occupations(gbs_net_t net, uint64_t seed, uint64_t e0, int64_t cou
     const int64_t ld = occ_chunk(net, count);
     const int64_t plane = (int64_t)net->mtiles * 64 * ld;
     void *d_occ = nullptr;
-    if (fp64) rc = dev_alloc(reinterpret_cast<double **>(&d_occ), (size_t)2 * plane, "occupations");
-    else rc = dev_alloc(reinterpret_cast<float **>(&d_occ), (size_t)2 * plane, "occupations");
+    if (fp64) rc = net_alloc(net, reinterpret_cast<double **>(&d_occ), (size_t)2 * plane, "occupations");
+    else rc = net_alloc(net, reinterpret_cast<float **>(&d_occ), (size_t)2 * plane, "occupations");
     if (rc) return rc;
     const size_t elt = fp64 ? sizeof(double) : sizeof(float);
     std::vector<uint8_t> h((size_t)2 * plane * elt);
@@ -975,7 +965,7 @@ int gbs_debug_occupations(gbs_net_t net, uint64_t seed, uint64_t e0, int64_t cou
                 occ[2 * ((size_t)j * count + done + i) + 1] = im;
             }
     }
-    dev_free(d_occ);
+    net_free(net, d_occ);
     return rc;
 }
 
@@ -1003,14 +993,14 @@ int gbs_moments(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, 
     double *d_acc = nullptr, *d_out = nullptr, *d_scr = nullptr;
     const int max_seg = moment_max_segments(n_sub, net->M, mmax, cmax);
     int64_t *d_cnt = nullptr;
-    if (fp64) rc = dev_alloc(reinterpret_cast<double **>(&d_occ), (size_t)2 * plane, "occupations");
-    else rc = dev_alloc(reinterpret_cast<float **>(&d_occ), (size_t)2 * plane, "occupations");
-    if (!rc) rc = dev_alloc(&d_par, (size_t)ld * moment_par_bytes(fp64), "trajectory parameters");
-    if (!rc) rc = dev_alloc(&d_acc, (size_t)n_sub * net->M * Q, "moment sums");
+    if (fp64) rc = net_alloc(net, reinterpret_cast<double **>(&d_occ), (size_t)2 * plane, "occupations");
+    else rc = net_alloc(net, reinterpret_cast<float **>(&d_occ), (size_t)2 * plane, "occupations");
+    if (!rc) rc = net_alloc(net, &d_par, (size_t)ld * moment_par_bytes(fp64), "trajectory parameters");
+    if (!rc) rc = net_alloc(net, &d_acc, (size_t)n_sub * net->M * Q, "moment sums");
     if (!rc && max_seg > 1)
-        rc = dev_alloc(&d_scr, (size_t)max_seg * n_sub * net->M * Q, "moment segment sums");
-    if (!rc) rc = dev_alloc(&d_cnt, (size_t)n_sub, "sub-ensemble sizes");
-    if (!rc) rc = dev_alloc(&d_out, 2 * nm + 2 * nc, "moment outputs");
+        rc = net_alloc(net, &d_scr, (size_t)max_seg * n_sub * net->M * Q, "moment segment sums");
+    if (!rc) rc = net_alloc(net, &d_cnt, (size_t)n_sub, "sub-ensemble sizes");
+    if (!rc) rc = net_alloc(net, &d_out, 2 * nm + 2 * nc, "moment outputs");
     if (!rc && cudaMemsetAsync(d_acc, 0, sizeof(double) * n_sub * net->M * Q, net->stream) != cudaSuccess)
         rc = set_error(GBS_ECUDA, "memset of the moment sums failed");
     std::vector<int64_t> cnt((size_t)n_sub, E / n_sub);
@@ -1070,12 +1060,12 @@ int gbs_moments(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, 
             if (sig_marg) std::memcpy(sig_marg, h.data() + 2 * nm + nc, sizeof(double) * nc);
         }
     }
-    dev_free(d_occ);
-    dev_free(d_par);
-    dev_free(d_acc);
-    dev_free(d_scr);
-    dev_free(d_cnt);
-    dev_free(d_out);
+    net_free(net, d_occ);
+    net_free(net, d_par);
+    net_free(net, d_acc);
+    net_free(net, d_scr);
+    net_free(net, d_cnt);
+    net_free(net, d_out);
     return rc;
 }
 

@@ -888,14 +888,21 @@ int tc_plan_create(gbs_net *net) {
     plan->P = (net->precision == GBS_BF16X3) ? 3 : 6;
     int rc;
     if ((rc = encode_net_maps(net, net->d_B, plan->desc))) return rc;
-    GBS_CUDA_TRY(cudaMalloc(&plan->d_desc, sizeof(GemmNetDesc)));
-    GBS_CUDA_TRY(cudaMemcpy(plan->d_desc, &plan->desc, sizeof(GemmNetDesc), cudaMemcpyHostToDevice));
+    // the descriptor block lives beside the network's buffers on its stream
+    // (the host copy outlives the asynchronous upload: it is the plan's)
+    if ((rc = pool_alloc(reinterpret_cast<void **>(&plan->d_desc), sizeof(GemmNetDesc),
+                         net->stream, "GEMM descriptors")))
+        return rc;
+    GBS_CUDA_TRY(cudaMemcpyAsync(plan->d_desc, &plan->desc, sizeof(GemmNetDesc),
+                                 cudaMemcpyHostToDevice, net->stream));
     return GBS_OK;
 }
 
 void tc_plan_destroy(gbs_net *net) {
-    if (net->tc && net->tc->d_desc) cudaFree(net->tc->d_desc);
-    if (net->tc && net->tc->d_desc_alt) cudaFree(net->tc->d_desc_alt);
+    if (net->tc) {
+        pool_free_raw(net->tc->d_desc, net->stream);
+        pool_free_raw(net->tc->d_desc_alt, net->stream);
+    }
     delete net->tc;
     net->tc = nullptr;
 }
@@ -1038,14 +1045,17 @@ bool tc_sampling_ready(gbs_net *net, bool allocate) {
     GemmNetDesc *d = nullptr;
     bool ok = pool_alloc(&B, net->B_bytes, net->stream, "second sample operand") == GBS_OK &&
               pool_alloc(&n, (size_t)net->chunk * sizeof(double), net->stream, "second n") == GBS_OK &&
-              cudaMalloc(&d, sizeof(GemmNetDesc)) == cudaSuccess;
+              pool_alloc(reinterpret_cast<void **>(&d), sizeof(GemmNetDesc), net->stream,
+                         "second GEMM descriptors") == GBS_OK;
     if (ok) ok = encode_net_maps(net, B, plan->desc_alt) == GBS_OK;
-    if (ok) ok = cudaMemcpy(d, &plan->desc_alt, sizeof(GemmNetDesc), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok)
+        ok = cudaMemcpyAsync(d, &plan->desc_alt, sizeof(GemmNetDesc), cudaMemcpyHostToDevice,
+                             net->stream) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         pool_free_raw(B, net->stream);
         pool_free_raw(n, net->stream);
-        if (d) cudaFree(d);
+        pool_free_raw(d, net->stream);
         return false;
     }
     net->d_B_alt = B;
