@@ -55,12 +55,13 @@ void prof_mark(gbs_net *net, int phase, int launches_if_stop, bool start) {
     if (!start) pr.launches[phase] += launches_if_stop;
 }
 
-// Stream-ordered allocations from the device's default memory pool, for the
-// per-network chunk workspace (about 1 GiB at N = 1000): the pool keeps the
-// memory when a network is freed (release threshold raised once per device
-// for this process), so creating and freeing networks in a loop does not go
-// back to the driver for every network.  Allocated and freed on the
-// network's stream; plain cudaMalloc / cudaFree on a device without
+// Stream-ordered allocations from the device's default memory pool, for
+// every buffer a network owns (the chunk workspace alone is about 1 GiB at
+// N = 1000): the pool keeps the memory when a network is freed (release
+// threshold raised once per device for this process), so creating and
+// freeing networks in a loop neither goes back to the driver for every
+// network nor synchronises the device as cudaFree does.  Allocated and freed
+// on the network's stream; plain cudaMalloc / cudaFree on a device without
 // memory pools.
 namespace {
 // per device: 0 not yet known, -1 plain cudaMalloc (no memory pools), 1 pool
