@@ -400,7 +400,6 @@ __global__ void k_sep_prep(const double *__restrict__ n_in, const double2 *__res
 // side on the packed FP32x2 instructions (per lane the scalar double-float
 // operations): hi = (re.hi, im.hi), lo = (re.lo, im.lo), stored as float4
 // (re.hi, im.hi, re.lo, im.lo).
-__device__ __forceinline__ df2 c_load(const float4 v) { return {f2(v.x, v.y), f2(v.z, v.w)}; }
 
 // The lane pairs a complex product reads of its left factor a ...
 struct CLeft {
