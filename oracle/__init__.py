@@ -15,7 +15,7 @@ import ctypes
 import os
 import subprocess
 import threading
-from typing import Optional, Tuple
+from typing import Tuple
 
 import numpy as np
 

@@ -23,7 +23,6 @@ Plain numpy, FP64; the trajectories come from the C oracle
 """
 from __future__ import annotations
 
-import itertools
 from typing import Sequence, Tuple
 
 import numpy as np

@@ -30,7 +30,7 @@ from __future__ import annotations
 
 import itertools
 import math
-from typing import Iterable, Optional
+from typing import Iterable
 
 import numpy as np
 from scipy.special import gammaln

@@ -7,7 +7,6 @@ batch issues the same kernels per network (one grouped GEMM per round), so
 its sub-ensemble sums must equal per-network runs bitwise, and every
 network's P(m) must match its exact distribution within sampling error.
 """
-import math
 
 import numpy as np
 import pytest

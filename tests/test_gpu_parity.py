@@ -11,7 +11,6 @@ Tolerances:
     P(m) within one sampling error of the FP64 result on the same
     trajectories (|dP| <= sigma, sigma floored at 1e-13).
 """
-import math
 
 import numpy as np
 import pytest
