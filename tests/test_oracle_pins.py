@@ -122,6 +122,37 @@ def test_gf_at_one_is_one(orc):
         assert abs(gm[0] - 1.0) < 1e-14 and abs(gp[0] - 1.0) < 1e-14
 
 
+def test_gf_sign_flip_symmetries(orc):
+    """Changing the sign of every alpha_j maps (n, n_S) to (-n, -n_S).  The
+    matrix-P GF cosh(n + (z-1) n_S) / cosh n is unchanged (cosh is even); the
+    +P GF e^{(z-1) n_S} goes to its reciprocal, so the product of the two
+    +P values is 1 at every z_k."""
+    K1 = 64
+    for n, nS in _some_samples():
+        gm1, gp1 = orc.gf_sample(n, nS, K1)
+        gm2, gp2 = orc.gf_sample(-n, -nS, K1)
+        assert np.max(np.abs(gm1 - gm2)) < 1e-12 * max(1.0, np.max(np.abs(gm1))), (n, nS)
+        assert np.max(np.abs(gp1 * gp2 - 1.0)) < 1e-12, (n, nS)
+
+
+def test_matrixP_gf_bounded_for_uniform_loss(orc):
+    """For T = t U, n_S = t^2 n is real and, on |z| = 1,
+    Re(n + (z-1) n_S) = n (1 - t^2 (1 - cos theta)) has modulus at most |n|;
+    since |cosh(x + iy)| <= cosh x, |G_mP(z_k)| <= 1 for every sample and k.
+    With the sign of (z - 1) flipped the bound fails on the same samples."""
+    net = wl.small_network(10, r=0.9, t2=0.7, seed=6)
+    n, nS = orc.samples(net.T, net.r, net.seed_s, 0, 200)
+    K1 = 128
+    z = np.exp(2j * np.pi * np.arange(K1) / K1)
+    worst, flipped = 0.0, 0.0
+    for a, b in zip(n, nS):
+        gm, _ = orc.gf_sample(a, b, K1)
+        worst = max(worst, float(np.max(np.abs(gm))))
+        flipped = max(flipped, float(np.max(np.abs(np.cosh(a + (1 - z) * b) / np.cosh(a)))))
+    assert worst <= 1.0 + 1e-12
+    assert flipped > 1.5
+
+
 def test_gf_taylor_coefficients_equal_direct_projector(orc):
     """The GF's Taylor coefficients (read off by an FFT at K1 far beyond the
     support) equal the per-bin projector of Eq. c-number-variable, for both
