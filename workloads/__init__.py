@@ -73,19 +73,21 @@ class Workload:
     precision: str         # default precision of the GPU run
     index: int = 0         # network index i (selects the seeds)
 
-    def network(self) -> Network:
-        seed_u = SEED_U_BASE + self.index
-        U = haar_unitary(self.M, seed_u)
-        if self.N != self.M:
-            U = U[:, : self.N]
+    def squeezing(self) -> np.ndarray:
+        """The N squeezing parameters r_j of network() (no unitary drawn)."""
         if self.r_lo == self.r_hi:
             r = np.full(self.N, float(self.r_lo))
         else:
-            rng = np.random.default_rng(seed_u + SEED_R_OFFSET)
+            rng = np.random.default_rng(SEED_U_BASE + self.index + SEED_R_OFFSET)
             r = rng.uniform(self.r_lo, self.r_hi, size=self.N)
+        return np.ascontiguousarray(r, dtype=np.float64)
+
+    def network(self) -> Network:
+        U = haar_unitary(self.M, SEED_U_BASE + self.index)
+        if self.N != self.M:
+            U = U[:, : self.N]
         T = np.ascontiguousarray(math.sqrt(self.t2) * U, dtype=np.complex128)
-        return Network(T=T, r=np.ascontiguousarray(r, dtype=np.float64),
-                       t2=self.t2, seed_s=SEED_S_BASE + self.index)
+        return Network(T=T, r=self.squeezing(), t2=self.t2, seed_s=SEED_S_BASE + self.index)
 
 
 # The named workloads.  Sizes follow the paper's regimes (M up to 8000 modes,
