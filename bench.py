@@ -399,7 +399,7 @@ def batch_arm(args):
     n_sub = [w.n_sub for w in wls]
     K1s, offs = [], []
     for w, d in zip(wls, defs):
-        k1, off = wl.dft_window(w.N, float(d.r.max()), w.t2, float(np.mean(np.sinh(d.r) ** 2)))
+        k1, off = wl.count_window(d.r, w.t2)
         K1s.append(k1)
         offs.append(off)
     nets = [gbs.gbs_make_network(d.T, d.r, "bf16x3", sptr) for d in defs]

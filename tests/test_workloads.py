@@ -70,3 +70,17 @@ def test_dft_windows_cover_the_batched_networks_support():
     mean = 0.5 * float(np.sum(mu))
     sd = math.sqrt(0.5 * float(np.sum(mu + mu ** 2)))
     assert _mass_outside(mu, K1, int(mean - 3 * sd), int(6 * sd)) > 1e-3
+
+
+def test_count_windows_cover_the_batched_networks_support():
+    """count_window (the batch bench's windows, from the count's own mean and
+    variance) is tighter than dft_window yet leaves out no mass above
+    rounding."""
+    ws = sorted(wl.batched_networks(), key=lambda w: w.N)
+    for w in ws[::8] + [ws[-1]]:
+        r = w.squeezing()
+        K1, off = wl.count_window(r, w.t2)
+        K0, _ = _window(w)[1:]
+        assert K1 <= K0
+        mu = ex.eigenvalues_uniform_loss(r, w.t2)
+        assert abs(_mass_outside(mu, K1, off, K1)) < 1e-11, w.name

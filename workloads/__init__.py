@@ -135,6 +135,24 @@ def dft_window(N: int, r_max: float, t2: float, r_mean2: float):
     return K1, m_off
 
 
+def count_window(r: np.ndarray, t2: float):
+    """(K1, m_offset) of a DFT window from the total count's own mean and
+    variance under uniform loss T = t U: per squeezed mode the count has mean
+    t2 sinh^2 r and variance t2 (1 - t2) sinh^2 r + 2 t2^2 sinh^2 r cosh^2 r
+    (the lossless squeezed-vacuum variance 2 sinh^2 r cosh^2 r, thinned by
+    the loss), and modes add.  Half-width 12 standard deviations + 64 around
+    the mean, rounded up to a power of two: tighter than dft_window's bound
+    for lossy networks or spread squeezing."""
+    r = np.asarray(r, dtype=np.float64)
+    s2 = np.sinh(r) ** 2
+    mean = float(t2 * np.sum(s2))
+    var = float(np.sum(t2 * (1.0 - t2) * s2 + 2.0 * t2 * t2 * s2 * np.cosh(r) ** 2))
+    half = 12.0 * math.sqrt(var) + 64.0
+    K1 = 1 << int(math.ceil(math.log2(2.0 * half)))
+    m_off = max(0, int(round(mean)) - K1 // 2)
+    return K1, m_off
+
+
 def small_network(N: int, M: Optional[int] = None, r=0.5, t2: float = 1.0, seed: int = 0,
                   general_loss: bool = False) -> Network:
     """A small test network.  r may be a scalar or a length-N sequence.
