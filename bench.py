@@ -8,10 +8,13 @@ finalize -> generating functions summed per sub-ensemble -> inverse DFT and
 statistics of P(m).  Metric: trajectories per second (whole job).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbs|reference]
-       [--workload m1000] [--precision bf16x3]
-Under torchrun (N > 1) every rank runs the same per-rank workload on its own
-GPU with disjoint trajectory ranges (weak scaling); the sub-ensemble sums are
-combined once after the timed region.
+       [--workload m8000] [--precision bf16x3]
+The default workload is the largest single-GPU configuration, m8000
+(N = M = 8000, r = 1, T = sqrt(0.99) U, E = 2^20 per step, K+1 = 16384).
+Under torchrun (N > 1, --gpus N must equal WORLD_SIZE) every rank runs the
+same per-rank workload on its own GPU with disjoint trajectory ranges (weak
+scaling); gloo carries the barriers and the one sum of sub-ensemble sums
+after the timed region.
 """
 from __future__ import annotations
 
@@ -32,18 +35,14 @@ if ROOT not in sys.path:
 METRIC = "matrix-P samples/sec and binned-P(m) wall time per N-mode network at |dP|/sigma<=1"
 UNIT = "samples/s"
 
-# DRAM bytes (read + write) of the GEMM kernel per trajectory, from the ncu
-# captures of one m1000 BF16x3 launch of 131072 trajectories: the plain GEMM
-# (profiles/k_gemm_tc_m1000_bf16x3.md: 1.0821 GB read + 0.0346 GB written)
-# and the sampling GEMM (profiles/k_gemm_tc_sampling_m1000.md: 1.4707 GB read
-# + 1.0843 GB written); the operands grow in proportion to the trajectories.
-# Valid for the workload and kernel versions of those captures only.
+# DRAM bytes (read + write) of the GEMM kernel per trajectory, from ncu
+# captures (dram__bytes_read.sum + dram__bytes_write.sum of one launch,
+# divided by its trajectories; the operands grow in proportion to them),
 # keyed by (workload, precision, whether the GEMM also runs the next chunk's
-# sampler: then the traffic includes the next chunk's operand written)
-GEMM_TRAFFIC_BYTES_PER_SAMPLE = {
-    ("m1000", "bf16x3", False): (1.082062e9 + 34.582016e6) / 131072,
-    ("m1000", "bf16x3", True): (1.470732e9 + 1.084348e9) / 131072,
-}
+# sampler, CTA pair 1/2, band).  An entry holds only for the kernel version
+# it was captured on: the table is emptied whenever the kernel changes, and a
+# run without an entry reports traffic null.
+GEMM_TRAFFIC_BYTES_PER_SAMPLE = {}
 
 
 def _env_int(name, default):
@@ -128,6 +127,14 @@ def run_oracle_sample(T, r, seed, e0, E, n_sub, K1, threads=0):
     oracle.accumulate_gf(n, nS, e0, n_sub, K1, threads)
 
 
+def _oracle_samples(wl_def, seconds):
+    """Trajectories for about `seconds` of oracle work on 16 host cores (the
+    oracle's propagation runs at roughly 9.4e10 FLOP/s there, 8 M N FLOP per
+    trajectory), a power of two in [64, 131072]."""
+    e = seconds * 9.4e10 / (8.0 * wl_def.M * wl_def.N)
+    return int(min(131072, max(64, 1 << int(round(math.log2(max(e, 1.0)))))))
+
+
 def reference_arm(args, wl_def):
     """The oracle timed on the host cores on bounded samples of the workload."""
     import oracle
@@ -135,9 +142,17 @@ def reference_arm(args, wl_def):
     if rank != 0:
         return 0
     oracle.build()
-    net = wl_def.network()
+    use_dev = False
+    if wl_def.N >= 2000:
+        try:
+            import torch
+            use_dev = torch.cuda.is_available()
+        except Exception:
+            use_dev = False
+    # the network's QR on the GPU where there is one (input generation, not timed)
+    net = wl_def.network(device=use_dev)
     cores = oracle.max_threads()
-    Es = args.ref_samples
+    Es = args.ref_samples or _oracle_samples(wl_def, 2.5)
     for s in range(args.warmup):
         run_oracle_sample(net.T, net.r, net.seed_s, s * Es, Es, wl_def.n_sub, wl_def.K1)
     t0 = time.perf_counter()
@@ -163,41 +178,70 @@ def reference_arm(args, wl_def):
     return 0
 
 
+def _fp64_samples(wl_def, n_sub):
+    """Trajectories of the FP64-path comparison: about 4e12 FLOP of FP64
+    propagation (a few seconds on GB300's FP64 pipe), a power of two, at
+    least 32 per sub-ensemble and at most the workload's E."""
+    target = 4e12 / (8.0 * wl_def.M * wl_def.N)
+    e = 1 << max(0, int(round(math.log2(max(target, 1.0)))))
+    return int(min(wl_def.E, max(e, 32 * n_sub)))
+
+
 def gbs_arm(args, wl_def):
     import numpy as np
     import torch
 
     import paper_2503_12749_gb300 as gbs
+    from paper_2503_12749_gb300 import distributed as gdist
 
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
     local = _env_int("LOCAL_RANK", 0)
+    if world != args.gpus:
+        sys.stderr.write(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world}; launch N > 1 "
+                         "GPUs as torchrun --nproc-per-node N bench.py --gpus N\n")
+        return 2
     dist = None
     if world > 1:
+        # gloo (host memory) carries the barriers, the max over ranks and the
+        # one sum of sub-ensemble sums: there is no device collective
         import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group(backend="nccl")
+        dist.init_process_group(backend="gloo")
     else:
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     gbs.build()
     precision = args.precision or wl_def.precision
     stream = torch.cuda.Stream()
     sptr = stream.cuda_stream
-    netdef = wl_def.network()
+    netdef = wl_def.network(device=wl_def.N >= 2000)
     E, n_sub, K1 = wl_def.E, wl_def.n_sub, wl_def.K1
     if args.samples:
         E = args.samples
     net = gbs.gbs_make_network(netdef.T, netdef.r, precision, sptr)
     if args.sampler_fusion is not None:
         gbs.gbs_set_sampler_fusion(net, args.sampler_fusion)
-    if args.gemm_cluster is not None and precision != "fp64":
-        gbs.gbs_set_gemm_config(net, args.gemm_cluster)
+    if args.pair_autotune is not None:
+        gbs.gbs_set_pair_autotune(bool(args.pair_autotune))
+    if args.gemm_pair is not None and precision != "fp64":
+        gbs.gbs_set_gemm_config(net, args.gemm_pair, args.gemm_band)
     out = torch.empty(4 * K1, dtype=torch.float64, device="cuda")
     seed = netdef.seed_s
     # rank r draws trajectories [r * R, (r + 1) * R) with R = (W + K + 2) * E
     # (warm-up, timed and 2 phase-timing steps)
-    from paper_2503_12749_gb300 import distributed as gdist
     base, _ = gdist.rank_range(rank, world, (args.warmup + args.steps + 2) * E)
 
     def step(s):
@@ -208,24 +252,21 @@ def gbs_arm(args, wl_def):
         for s in range(args.warmup):
             step(s)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    barrier()
     clocks = ClockSampler(dev)
     clocks.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    barrier()
     ev0.record(stream)
     for s in range(args.steps):
         step(args.warmup + s)
     ev1.record(stream)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    barrier()
     clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1))
     # kernel times per phase: further steps with phase timing on (events
     # around every phase), scaled to the timed steps
     nprof = 2
@@ -237,12 +278,9 @@ def gbs_arm(args, wl_def):
     gbs.gbs_profile_enable(net, False)
     prof = {k: (v[0] * args.steps / nprof, v[1] * args.steps // nprof) for k, v in prof.items()}
     if dist:
-        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
         # combine sub-ensemble sums of all ranks (the estimator's one exchange)
         _, _, acc, cnt = gbs.gbs_get_accumulators(net)
-        acc_all, cnt_all = gdist.combine_accumulators(acc, cnt, device="cuda")
+        acc_all, cnt_all = gdist.combine_accumulators(acc, cnt)
         gbs.gbs_set_accumulators(net, acc_all, cnt_all)
     ms_step = ms_total / args.steps
     value = world * E * args.steps / (ms_total / 1e3)
@@ -253,7 +291,7 @@ def gbs_arm(args, wl_def):
     P = gbs.gbs_binned_counts(net, 0, K1)
     acc_summary = {"sum_P": float(np.sum(P[0])), "max_sigma_mP": float(np.max(P[1])),
                    "max_sigma_plusP": float(np.max(P[3])),
-                   "trajectories": int((args.warmup + args.steps + nprof) * E)}
+                   "trajectories": int(world * (args.warmup + args.steps + nprof) * E)}
 
     # roofline of the dominant kernel (the propagation GEMM)
     peaks, peak_kind = _peaks()
@@ -261,42 +299,51 @@ def gbs_arm(args, wl_def):
     flops = 8.0 * netdef.M * netdef.N * E * args.steps
     tc_path = precision != "fp64"
     P_products = {"bf16x3": 3, "bf16x6": 6}.get(precision, 1)
+    folded = bool(tc_path and gbs.gbs_sampler_fusion(net))
     if tc_path:
         achieved = flops / (gemm_ms / 1e3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        pair, band = gbs.gbs_gemm_config(net)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": f"{peak_kind} bf16 sustained (kernel timed inside a long step)",
                 "algorithmic_flops_per_sample": 8 * netdef.M * netdef.N,
                 "mma_products": P_products, "mma_issued_frac": P_products * achieved / peak,
                 "kernel": "k_gemm_tc", "launches": gemm_launches,
-                "cluster": gbs.gbs_gemm_config(net),
-                "avg_launch_ms": gemm_ms / max(gemm_launches, 1)}
-        folded = gbs.gbs_sampler_fusion(net)
+                "gemm_config": {"cta_pair": pair == 2, "band": band},
+                "avg_launch_ms": gemm_ms / max(gemm_launches, 1),
+                "sm_mhz_median": clk.get("sm_mhz"),
+                "achieved_at_max_clock": (achieved * clk["sm_max_mhz"] / clk["sm_mhz"]
+                                          if clk.get("sm_mhz") else None)}
         if folded:
             roof["kernel"] = "k_gemm_tc (sampling variant: its spare warps also draw the " \
                              "next chunk's samples)"
-        per_sample = GEMM_TRAFFIC_BYTES_PER_SAMPLE.get(
-            (wl_def.name.split(":")[0], precision, folded))
+        # per trajectory: the sample operand (alpha and beta rows, 2 BF16
+        # planes each) and one n_S partial (16 B) per 64-mode tile; per
+        # launch: the T planes the products read
+        planes = 2 if precision == "bf16x3" else 3
+        per_traj = 2 * planes * 2 * netdef.N + 16 * (-(-netdef.M // 64))
+        if folded:
+            # the next chunk's operand and n[] written by the sampler warps
+            per_traj += 2 * planes * 2 * netdef.N + 8
+        roof["algorithmic_bytes"] = per_traj * E * args.steps / max(gemm_launches, 1) + \
+            planes * 2 * netdef.M * netdef.N * 2
+        key = (wl_def.name.split(":")[0], precision, folded, pair, band)
+        per_sample = GEMM_TRAFFIC_BYTES_PER_SAMPLE.get(key)
         if per_sample is not None:
-            roof["traffic"] = per_sample * E * args.steps / max(gemm_launches, 1)
-            roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one " \
-                                     "131072-trajectory launch, scaled to the average launch"
-            # per trajectory: the sample operand (alpha and beta rows, 2 BF16
-            # planes each) and one n_S partial (16 B) per 64-mode tile; per
-            # launch: the 2 T planes the 3 products read
-            planes = 2 if precision == "bf16x3" else 3
-            per_traj = 2 * planes * 2 * netdef.N + 16 * (-(-netdef.M // 64))
-            if folded:
-                # the next chunk's operand and n[] written by the sampler warps
-                per_traj += 2 * planes * 2 * netdef.N + 8
-            roof["algorithmic_bytes"] = per_traj * E * args.steps / max(gemm_launches, 1) + \
-                planes * 2 * netdef.M * netdef.N * 2
+            roof["traffic"] = per_sample[0] * E * args.steps / max(gemm_launches, 1)
+            roof["traffic_source"] = per_sample[1]
+        else:
+            roof["traffic_source"] = "no ncu capture of this kernel version, workload and " \
+                                     "configuration"
     else:
         achieved = flops / (gemm_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "kernel": "k_gemm_fp64",
-                "peak_source": "FP64 FMA pipe (nominal FP64 rate; no measured FP64 peak)"}
+        peak = gbs.gbs_measure_fp64_rate(sptr)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "kernel": "k_gemm_fp64",
+                "peak_source": "measured FP64 FMA rate (gbs_measure_fp64_rate: independent "
+                               "FMA chains on every SM, CUDA events)"}
     phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
               for k, v in prof.items()}
     launches = int(sum(v[1] for v in prof.values()))
@@ -318,8 +365,7 @@ def gbs_arm(args, wl_def):
                    "phases_from": "2 further steps with phase timing (CUDA events around "
                                   "each phase), scaled to the timed steps",
                    "sampler": ("drawn in the spare warps of the previous chunk's GEMM"
-                               if tc_path and gbs.gbs_sampler_fusion(net)
-                               else "one launch per chunk")},
+                               if folded else "one launch per chunk")},
         "roofline": roof,
         "phases": phases,
         "result": acc_summary,
@@ -327,9 +373,53 @@ def gbs_arm(args, wl_def):
         "clocks": clk,
     }
 
+    # the plain FP64-GPU path on the same network and trajectories: its rate,
+    # the split path's speed-up over it and |dP| / sigma_FP64 between the two
+    if tc_path and not args.no_fp64_path and world == 1:
+        Ef = args.fp64_samples or _fp64_samples(wl_def, n_sub)
+        f0 = base + (args.warmup + args.steps + nprof) * E
+        res = {}
+        fp64_gemm_ms = None
+        for prec in ("fp64", precision):
+            n2 = gbs.gbs_make_network(netdef.T, netdef.r, prec, sptr)
+            gbs.gbs_sample(n2, seed, f0, min(Ef, 4 * n_sub), n_sub, K1)  # warm-up, tuning
+            gbs.gbs_reset(n2)
+            torch.cuda.synchronize()
+            if prec == "fp64":
+                gbs.gbs_profile_enable(n2, True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gbs.gbs_sample(n2, seed, f0, Ef, n_sub, K1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if prec == "fp64":
+                fp64_gemm_ms = gbs.gbs_profile_read(n2)["gemm"][0]
+                gbs.gbs_profile_enable(n2, False)
+            res[prec] = (e0.elapsed_time(e1), gbs.gbs_binned_counts(n2, 0, K1))
+            gbs.gbs_free_network(n2)
+        (ms64, P64), (msb, Pb) = res["fp64"], res[precision]
+        sig = np.maximum(P64[1], 1e-13)
+        fp64_peak = gbs.gbs_measure_fp64_rate(sptr)
+        fp64_gemm_tflops = 8.0 * netdef.M * netdef.N * Ef / (fp64_gemm_ms / 1e3) / 1e12
+        line["fp64_path"] = {
+            "samples": Ef, "value": Ef / (ms64 / 1e3), "unit": UNIT,
+            "gemm_ms": fp64_gemm_ms, "gemm_tflops": fp64_gemm_tflops,
+            "fp64_peak_tflops": fp64_peak,
+            "gemm_frac_of_fp64_peak": fp64_gemm_tflops / fp64_peak if fp64_peak else None,
+            "speedup_of_split_path": value / (Ef / (ms64 / 1e3)),
+            "max_abs_dP_over_sigma_fp64": float(np.max(np.abs(Pb[0] - P64[0]) / sig)),
+            "max_abs_dP_plusP_over_sigma_fp64": float(np.max(np.abs(Pb[2] - P64[2]) /
+                                                             np.maximum(P64[3], 1e-13))),
+            "what": f"gbs_sample of {Ef} trajectories on a GBS_FP64 network (FP64 sampler, "
+                    "SIMT FP64 GEMM, FP64 generating functions; CUDA events) and on a "
+                    f"{precision} network, the same trajectories; speed-up = the timed "
+                    "split-path value / this FP64 rate"}
+
     # end to end through the C ABI with host buffers: upload the network,
-    # sample, invert and read P(m) back, every step
-    if not args.no_e2e and rank == 0:
+    # sample, invert and read P(m) back, every step, as many steps as the
+    # device leg
+    if not args.no_e2e:
         # the step's inputs in pinned host memory
         Tn = torch.empty(2 * netdef.T.size, dtype=torch.float64, pin_memory=True).numpy()
         Tn = Tn.view(np.complex128).reshape(netdef.T.shape)
@@ -343,27 +433,31 @@ def gbs_arm(args, wl_def):
             n2 = gbs.gbs_make_network(Tn, rn, precision, sptr)
             if args.sampler_fusion is not None:
                 gbs.gbs_set_sampler_fusion(n2, args.sampler_fusion)
-            gbs.gbs_sample(n2, seed, s * E, E, n_sub, K1)
+            if args.gemm_pair is not None and precision != "fp64":
+                gbs.gbs_set_gemm_config(n2, args.gemm_pair, args.gemm_band)
+            gbs.gbs_sample(n2, seed, base + s * E, E, n_sub, K1)
             res = gbs.gbs_binned_counts(n2, 0, K1)
             gbs.gbs_free_network(n2)
             return res
 
         e2e_step(0)
+        barrier()
         t0 = time.perf_counter()
-        ne = max(1, min(3, args.steps))
+        ne = args.steps
         for s in range(ne):
             e2e_step(1 + s)
-        dt = time.perf_counter() - t0
-        line["e2e"] = {"value": E * ne / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h,
+        barrier()
+        dt = max_over_ranks(time.perf_counter() - t0)
+        line["e2e"] = {"value": world * E * ne / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "steps": ne,
                        "what": "gbs_make_network (pinned host T, r) + gbs_sample + "
                                "gbs_binned_counts (host outputs) + gbs_free_network per step, "
-                               "wall clock"}
+                               "wall clock, max over ranks"}
 
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         import oracle
         oracle.build()
-        Es = args.cpu_samples
+        Es = args.cpu_samples or _oracle_samples(wl_def, 12.0)
         run_oracle_sample(netdef.T, netdef.r, seed, 0, 64, n_sub, K1)
         t0 = time.perf_counter()
         run_oracle_sample(netdef.T, netdef.r, seed, 0, Es, n_sub, K1)
@@ -426,7 +520,7 @@ def batch_arm(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms_total = ev0.elapsed_time(ev1)
-    cl, rounds, tiles = gbs.gbs_batch_info(batch)
+    pair, rounds, tiles = gbs.gbs_batch_info(batch)
     # kernels per step: per network and chunk a sampler, a finalize and a
     # generating-function launch; one grouped GEMM per round; per network the
     # inversion (prep, log2 K1 FFT passes, statistics)
@@ -454,7 +548,7 @@ def batch_arm(args):
         "config": {"workload": f"batch{len(wls)}: {len(wls)} Haar networks, N=M log-uniform "
                                "[100,2000], r_j~U[0.5,1.5], t~U[0.5,0.995], E=2^18 each",
                    "N": [d.N for d in defs], "K1": K1s, "n_sub": n_sub[0],
-                   "samples_per_step": sum(E), "gemm_cluster_chosen": cl, "rounds": rounds,
+                   "samples_per_step": sum(E), "gemm_cta_pair_chosen": pair == 2, "rounds": rounds,
                    "gemm_tiles_per_call": tiles,
                    "note": "one CUDA graph per gbs_sample_batch call; GEMM kernel time from "
                            "2 further steps issued without the graph under phase timing"},
@@ -910,7 +1004,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
-    ap.add_argument("--workload", default="m1000",
+    ap.add_argument("--workload", default="m8000",
                     choices=sorted(wl.NAMED) + ["batch64", "surrogate", "bin2d", "fig6", "moments"])
     ap.add_argument("--sur-train", type=int, default=2000)
     ap.add_argument("--sur-train-samples", type=int, default=2 ** 16)
@@ -919,12 +1013,22 @@ def main():
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--precision", default=None, choices=["fp64", "bf16x3", "bf16x6"])
     ap.add_argument("--samples", type=int, default=0, help="override trajectories per step")
-    ap.add_argument("--ref-samples", type=int, default=2048)
-    ap.add_argument("--cpu-samples", type=int, default=8192)
+    ap.add_argument("--ref-samples", type=int, default=0,
+                    help="trajectories per reference-arm step (default: about 2 s of oracle "
+                         "work on 16 cores)")
+    ap.add_argument("--cpu-samples", type=int, default=0,
+                    help="trajectories of the cpu_baseline sample (default: about 10-20 s of "
+                         "oracle work on 16 cores)")
+    ap.add_argument("--fp64-samples", type=int, default=0)
+    ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--gemm-cluster", type=int, choices=[0, 1, 2], default=None,
-                    help="gbs_set_gemm_config cluster size of the timed network (default: "
-                         "autotuned)")
+    ap.add_argument("--gemm-pair", type=int, choices=[0, 1, 2], default=None,
+                    help="gbs_set_gemm_config: 1 = one CTA per tile, 2 = CTA pairs, 0 = "
+                         "autotuned (the default)")
+    ap.add_argument("--gemm-band", type=int, default=0,
+                    help="gbs_set_gemm_config band (with --gemm-pair 1 or 2)")
+    ap.add_argument("--pair-autotune", type=int, choices=[0, 1], default=None,
+                    help="gbs_set_pair_autotune before the run")
     ap.add_argument("--sampler-fusion", type=int, choices=[0, 1, 2], default=None,
                     help="gbs_set_sampler_fusion mode of the timed network (default: the "
                          "library's, 1)")
@@ -935,31 +1039,31 @@ def main():
     if args.workload == "batch64":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference",
-                              "unavailable": "the reference arm is defined for the m1000 workload"}))
+                              "unavailable": "the reference arm is defined for the single-network workloads"}))
             return 0
         return batch_arm(args)
     if args.workload == "fig6":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference",
-                              "unavailable": "the reference arm is defined for the m1000 workload"}))
+                              "unavailable": "the reference arm is defined for the single-network workloads"}))
             return 0
         return fig6_arm(args)
     if args.workload == "bin2d":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference",
-                              "unavailable": "the reference arm is defined for the m1000 workload"}))
+                              "unavailable": "the reference arm is defined for the single-network workloads"}))
             return 0
         return bin2d_arm(args)
     if args.workload == "moments":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference",
-                              "unavailable": "the reference arm is defined for the m1000 workload"}))
+                              "unavailable": "the reference arm is defined for the single-network workloads"}))
             return 0
         return moments_arm(args)
     if args.workload == "surrogate":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference",
-                              "unavailable": "the reference arm is defined for the m1000 workload"}))
+                              "unavailable": "the reference arm is defined for the single-network workloads"}))
             return 0
         return surrogate_arm(args)
     wl_def = wl.NAMED[args.workload]

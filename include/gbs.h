@@ -239,7 +239,8 @@ int gbs_histogram(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E
  * is the aliased sum over m + j K1; choose K1 and m_offset to cover the
  * support.  Output arrays are host buffers of K1 doubles each; any of them
  * may be NULL to skip it.  Synchronises the network's stream.
- * Errors: EINVAL (no samples in some sub-ensemble), ENONFINITE, ECUDA.
+ * Errors: EINVAL (no samples in some sub-ensemble), ETIMEOUT and ENONFINITE
+ * (as gbs_check_finite), ECUDA.
  */
 int gbs_binned_counts(gbs_net_t net, int64_t m_offset, double *P_mP, double *sig_mP,
                       double *P_plusP, double *sig_plusP);
@@ -271,8 +272,10 @@ int gbs_binned_counts_device(gbs_net_t net, int64_t m_offset, double *out_dev);
  * call): 2 * n_sub * K1 <= 2^20 and K1 <= 2^16 (33 MB of device memory held
  * by every GPU that loads the library until exit); larger sizes return
  * GBS_EINVAL.  The first call on a device looks up the array's device address
- * (make it before capturing any stream).  Calls share the array: two calls
- * that run at the same time on one GPU race.  No network object is needed.
+ * (make it before capturing any stream) and keeps it for the life of the
+ * process, so resetting the device (cudaDeviceReset) after that first call is
+ * not supported.  Calls share the array: two calls that run at the same time
+ * on one GPU race.  No network object is needed.
  */
 int gbs_binned_counts_noalloc(const double *acc_dev, const int64_t *counts_dev, int n_sub,
                               int K1, int64_t m_offset, double *out_dev, void *stream);
@@ -280,7 +283,10 @@ int gbs_binned_counts_noalloc(const double *acc_dev, const int64_t *counts_dev, 
 /*
  * gbs_check_finite -- count non-finite entries of the sub-ensemble sums
  * (synchronises).  Returns GBS_OK and *count = 0 when all are finite,
- * GBS_ENONFINITE with *count > 0 otherwise.
+ * GBS_ENONFINITE with *count > 0 otherwise.  Before counting it reads the
+ * network's timeout flag: when a GEMM launch gave up waiting on its pipeline
+ * since the last check (gbs_set_wait_limit), it clears the flag and returns
+ * GBS_ETIMEOUT (*count = 0).
  */
 int gbs_check_finite(gbs_net_t net, int64_t *count);
 
@@ -323,15 +329,44 @@ int gbs_network_info(gbs_net_t net, int *N, int *M, int *precision, int64_t *chu
 
 /*
  * gbs_set_gemm_config / gbs_gemm_config -- tile configuration of the tcgen05
- * propagation GEMM (BF16 paths): cluster = 1 (each CTA loads its whole
- * trajectory tile) or 2 (pairs of CTAs on adjacent mode tiles share one
- * trajectory tile, each loading half and multicasting it to both); 0 = let
- * the autotuner time both on the network's first chunk and keep the faster
- * (cached per size bucket of N and M for the process).  gbs_gemm_config
- * returns the configuration in use (0 before the first chunk).
+ * propagation GEMM (BF16 paths; not part of the method: every configuration
+ * gives bitwise the same sums).  pair = 1: one CTA per (64-mode tile,
+ * 128-trajectory tile); 2: CTA pairs (cta_group::2, clusters of 2 CTAs) on
+ * adjacent mode tiles of one trajectory tile, each CTA loading its own A
+ * tile and half of the trajectory tile, the pair's MMA reading both halves.
+ * band = 0: the tiles of one chunk in the plain order (all mode tiles of a
+ * trajectory tile side by side); band > 0: in bands of `band` mode-tile
+ * groups (a group = the 1 or 2 mode tiles of a CTA or pair), the trajectory
+ * tiles of a band in order, so that a band's A tiles are read again from L2.
+ * pair = 0 returns to the autotuner, which times the candidates on the
+ * network's first chunk and keeps the fastest (cached per size bucket of N
+ * and M for the process).  gbs_gemm_config returns the configuration in use
+ * ((0, 0) before the first chunk).  EINVAL: FP64 network, pair not 0..2,
+ * band < 0, NULL pointers.
  */
-int gbs_set_gemm_config(gbs_net_t net, int cluster);
-int gbs_gemm_config(gbs_net_t net, int *cluster);
+int gbs_set_gemm_config(gbs_net_t net, int pair, int band);
+int gbs_gemm_config(gbs_net_t net, int *pair, int *band);
+
+/*
+ * gbs_set_pair_autotune -- whether the GEMM autotuner (and the batch's) also
+ * times CTA pairs; process-wide, clears the autotuner's cache.  Networks
+ * already configured keep their configuration.
+ */
+int gbs_set_pair_autotune(int enable);
+
+/*
+ * gbs_set_wait_limit -- bound, in nanoseconds, of every pipeline wait in the
+ * network's tcgen05 GEMM launches (default 2e9; a wait that has not seen its
+ * phase complete after that long raises the network's timeout flag, the
+ * kernel stops issuing work, waits for what it already issued and returns).
+ * The next synchronous read (gbs_binned_counts, gbs_check_finite,
+ * gbs_moments) then returns GBS_ETIMEOUT and clears the flag; the sums of a
+ * call that timed out are not meaningful (gbs_reset clears them).  A limit
+ * of 0 exercises that path without a fault: each GEMM launch then first
+ * waits on a barrier that nothing arrives on, gives up at once and issues
+ * no MMA.  EINVAL: NULL network.
+ */
+int gbs_set_wait_limit(gbs_net_t net, uint64_t limit_ns);
 
 /*
  * gbs_set_sampler_fusion / gbs_sampler_fusion -- sampling of the next chunk
@@ -364,8 +399,9 @@ int gbs_sampler_fusion(gbs_net_t net, int *active);
  * decreasing K), then each network's generating-function sums.  All rounds
  * of a call are captured into one CUDA graph and launched once (on the
  * legacy default stream, which cannot be captured, they are issued
- * directly).  The batch GEMM's cluster size is chosen by timing both
- * candidates on the first call's first round.
+ * directly).  The batch GEMM's tile configuration (one CTA per tile, or CTA
+ * pairs where the autotuner takes them) is chosen by timing the candidates
+ * on the first call's first round.
  *
  * gbs_make_batch -- group `count` networks (1..4096) that share a BF16
  *   precision, a device and a stream.  The networks stay owned by the
@@ -374,7 +410,8 @@ int gbs_sampler_fusion(gbs_net_t net, int *active);
  *   first_sample[i], E[i], n_sub[i], K1[i] (host arrays of `count`).  The
  *   same trajectories as per-network gbs_sample calls are drawn.
  *   Synchronises the stream before capturing (descriptor upload).
- * gbs_batch_info -- cluster size chosen, rounds and GEMM tiles of the last call.
+ * gbs_batch_info -- GEMM tile configuration chosen (pair = 1 or 2), rounds and
+ *   GEMM tiles of the last call.
  * With phase timing enabled on the batch's first network (gbs_profile_enable),
  * gbs_sample_batch issues its rounds directly instead of as a graph and
  * attributes the grouped GEMM launches to that network's GEMM phase.
@@ -384,7 +421,7 @@ typedef struct gbs_batch *gbs_batch_t;
 int gbs_make_batch(gbs_net_t *nets, int count, gbs_batch_t *out);
 int gbs_sample_batch(gbs_batch_t batch, const uint64_t *seeds, const uint64_t *first_sample,
                      const int64_t *E, const int *n_sub, const int *K1);
-int gbs_batch_info(gbs_batch_t batch, int *cluster, int *rounds, int64_t *tiles);
+int gbs_batch_info(gbs_batch_t batch, int *pair, int *rounds, int64_t *tiles);
 void gbs_free_batch(gbs_batch_t batch);
 
 /*
@@ -407,6 +444,17 @@ int gbs_profile_enable(gbs_net_t net, int enable);
  * time in milliseconds (ms[GBS_NPHASES]) and the number of kernel launches
  * (launches[GBS_NPHASES]) since the last enable/read; clears the records. */
 int gbs_profile_read(gbs_net_t net, double *ms, int64_t *launches);
+
+/*
+ * gbs_measure_fp64_rate -- instrumentation, not part of the method: the
+ * device's FP64 fused multiply-add rate in TFLOP/s (2 FLOP per FMA), from a
+ * kernel of independent FMA chains on every SM timed with CUDA events on
+ * `stream` (best of 3 after a warm-up launch).  It is the peak against which
+ * the FP64 path's propagation (k_gemm_fp64, bound by that rate) is reported.
+ * Allocates a small output buffer (stream-ordered) and synchronises.
+ * Errors: EINVAL (NULL tflops), ECUDA.
+ */
+int gbs_measure_fp64_rate(void *stream, double *tflops);
 
 /* gbs_free_network -- synchronise the network's stream and release all memory
  * of the network (NULL is a no-op).  All device memory of a network (the

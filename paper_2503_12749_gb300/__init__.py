@@ -83,7 +83,10 @@ def lib():
         L.gbs_network_info.argtypes = [vp, ip, ip, ip, i64p]
         L.gbs_binned_counts_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int64, vp, vp]
-        L.gbs_set_gemm_config.argtypes = [vp, ctypes.c_int]
+        L.gbs_set_gemm_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.gbs_set_pair_autotune.argtypes = [ctypes.c_int]
+        L.gbs_set_wait_limit.argtypes = [vp, ctypes.c_uint64]
+        L.gbs_measure_fp64_rate.argtypes = [vp, dp]
         L.gbs_make_network_binned.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ip, ctypes.c_int,
                                               vp, ctypes.POINTER(vp)]
         L.gbs_histogram.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ip,
@@ -99,7 +102,7 @@ def lib():
         L.gbs_sample_2d.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.gbs_binned_counts_2d.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp]
-        L.gbs_gemm_config.argtypes = [vp, ip]
+        L.gbs_gemm_config.argtypes = [vp, ip, ip]
         L.gbs_set_sampler_fusion.argtypes = [vp, ctypes.c_int]
         L.gbs_sampler_fusion.argtypes = [vp, ip]
         L.gbs_make_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
@@ -137,6 +140,7 @@ def lib():
                      "gbs_get_accumulators", "gbs_set_accumulators", "gbs_reset",
                      "gbs_network_info", "gbs_profile_enable", "gbs_profile_read",
                      "gbs_binned_counts_noalloc", "gbs_set_gemm_config", "gbs_gemm_config",
+                     "gbs_set_pair_autotune", "gbs_set_wait_limit", "gbs_measure_fp64_rate",
                      "gbs_set_sampler_fusion", "gbs_sampler_fusion",
                      "gbs_make_batch", "gbs_sample_batch", "gbs_batch_info",
                      "gbs_make_network_device", "gbs_make_network_binned", "gbs_sample_2d",
@@ -379,15 +383,36 @@ def gbs_network_info(net: Network):
     return N.value, M.value, p.value, c.value
 
 
-def gbs_set_gemm_config(net: Network, cluster: int) -> None:
-    """0 = autotune, 1 or 2 = cluster size of the tcgen05 GEMM."""
-    _check(lib().gbs_set_gemm_config(net.handle, int(cluster)))
+def gbs_set_gemm_config(net: Network, pair: int, band: int = 0) -> None:
+    """Tile configuration of the tcgen05 GEMM: pair 1 (one CTA per tile) or 2
+    (CTA pairs), band = mode-tile groups per band of the tile order (0: plain
+    order); pair 0 = autotune."""
+    _check(lib().gbs_set_gemm_config(net.handle, int(pair), int(band)))
 
 
-def gbs_gemm_config(net: Network) -> int:
-    c = ctypes.c_int()
-    _check(lib().gbs_gemm_config(net.handle, ctypes.byref(c)))
-    return c.value
+def gbs_gemm_config(net: Network):
+    """(pair, band) in use; (0, 0) before the first chunk."""
+    p = ctypes.c_int()
+    b = ctypes.c_int()
+    _check(lib().gbs_gemm_config(net.handle, ctypes.byref(p), ctypes.byref(b)))
+    return p.value, b.value
+
+
+def gbs_set_pair_autotune(enable: bool) -> None:
+    """Whether the GEMM autotuners also time CTA pairs (process-wide)."""
+    _check(lib().gbs_set_pair_autotune(int(bool(enable))))
+
+
+def gbs_measure_fp64_rate(stream=0) -> float:
+    """The device's FP64 FMA rate (TFLOP/s) from a CUDA-event-timed probe."""
+    t = ctypes.c_double()
+    _check(lib().gbs_measure_fp64_rate(ctypes.c_void_p(stream), ctypes.byref(t)))
+    return t.value
+
+
+def gbs_set_wait_limit(net: Network, limit_ns: int) -> None:
+    """Bound (ns) of every pipeline wait in the network's GEMM launches."""
+    _check(lib().gbs_set_wait_limit(net.handle, int(limit_ns)))
 
 
 def gbs_set_sampler_fusion(net: Network, mode) -> None:
@@ -437,7 +462,8 @@ def gbs_sample_batch(batch: Batch, seeds, first_sample, E, n_sub, K1) -> None:
 
 
 def gbs_batch_info(batch: Batch):
-    """(cluster size chosen, rounds, GEMM tiles) of the last gbs_sample_batch."""
+    """(GEMM tile configuration chosen: pair 1 or 2, rounds, GEMM tiles) of the last
+    gbs_sample_batch."""
     c = ctypes.c_int()
     r = ctypes.c_int()
     t = ctypes.c_int64()

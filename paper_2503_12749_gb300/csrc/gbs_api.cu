@@ -777,6 +777,17 @@ int gbs_check_finite(gbs_net_t net, int64_t *count) {
     int rc;
     if ((rc = validate_net(net))) return rc;
     if (count) *count = 0;
+    // a GEMM launch that gave up waiting on its pipeline since the last check
+    unsigned long long timed_out = 0;
+    GBS_CUDA_TRY(cudaMemcpyAsync(&timed_out, net->d_flags + 1, sizeof(timed_out),
+                                 cudaMemcpyDeviceToHost, net->stream));
+    GBS_CUDA_TRY(cudaStreamSynchronize(net->stream));
+    if (timed_out) {
+        GBS_CUDA_TRY(cudaMemsetAsync(net->d_flags + 1, 0, sizeof(unsigned long long), net->stream));
+        GBS_CUDA_TRY(cudaStreamSynchronize(net->stream));
+        return set_error(GBS_ETIMEOUT, "a GEMM kernel gave up waiting on its pipeline; the sums "
+                                       "since the last check are not meaningful");
+    }
     if (!net->est_fixed) return GBS_OK;
     prof_mark(net, GBS_PHASE_INVERT, 0, true);
     if ((rc = launch_count_nonfinite(net))) return rc;
@@ -1203,11 +1214,23 @@ int gbs_network_info(gbs_net_t net, int *N, int *M, int *precision, int64_t *chu
     return GBS_OK;
 }
 
-int gbs_set_gemm_config(gbs_net_t net, int cluster) {
+int gbs_set_gemm_config(gbs_net_t net, int pair, int band) {
     int rc;
     if ((rc = validate_net(net))) return rc;
     if (net->precision == GBS_FP64) return set_error(GBS_EINVAL, "the FP64 path has no tcgen05 GEMM");
-    return tc_set_cluster(net, cluster);
+    return tc_set_config(net, pair, band);
+}
+
+int gbs_set_pair_autotune(int enable) {
+    tc_set_pair_autotune(enable != 0);
+    return GBS_OK;
+}
+
+int gbs_set_wait_limit(gbs_net_t net, uint64_t limit_ns) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    net->wait_ns = limit_ns;
+    return GBS_OK;
 }
 
 int gbs_set_sampler_fusion(gbs_net_t net, int mode) {
@@ -1226,10 +1249,11 @@ int gbs_sampler_fusion(gbs_net_t net, int *active) {
     return GBS_OK;
 }
 
-int gbs_gemm_config(gbs_net_t net, int *cluster) {
+int gbs_gemm_config(gbs_net_t net, int *pair, int *band) {
     int rc;
     if ((rc = validate_net(net))) return rc;
-    if (cluster) *cluster = tc_get_cluster(net);
+    if (!pair || !band) return set_error(GBS_EINVAL, "NULL argument");
+    tc_get_config(net, pair, band);
     return GBS_OK;
 }
 

@@ -22,8 +22,9 @@
 // small networks' kernels run side by side instead of one after another
 // (each network's own launches keep their order, so the results do not
 // change).  The
-// grouped GEMM's cluster size is chosen by timing both candidates on the
-// batch's first round (cached per batch).
+// grouped GEMM's tile configuration (one CTA per tile, or CTA pairs) is
+// chosen by timing the candidates on the batch's first round (cached per
+// batch).
 #include "gbs_internal.cuh"
 
 #include <algorithm>
@@ -35,7 +36,7 @@ struct gbs_batch {
     std::vector<gbs_net *> nets;
     cudaStream_t stream = nullptr;
     int P = 0;
-    int cluster = 0;  // 0 = not tuned yet
+    int pair = 0;     // GEMM tiles per CTA (1) or per CTA pair (2); 0 = not tuned yet
     int sm_count = 0;
     // device copies of the per-round descriptors and tile lists
     gbs::GemmNetDesc *d_desc = nullptr;
@@ -72,7 +73,7 @@ struct RoundPlan {
     std::vector<int64_t> step;      // [nets]: trajectories per round (chunk_step)
 };
 
-int build_rounds(gbs_batch *b, const int64_t *E, int cluster, RoundPlan &rp,
+int build_rounds(gbs_batch *b, const int64_t *E, int pair, RoundPlan &rp,
                  const std::vector<char> *fold_net = nullptr, const uint64_t *seeds = nullptr,
                  const uint64_t *first = nullptr) {
     const int nn = (int)b->nets.size();
@@ -114,7 +115,7 @@ int build_rounds(gbs_batch *b, const int64_t *E, int cluster, RoundPlan &rp,
         for (int oi = 0; oi < nn; ++oi) {
             const int i = order[oi];
             const GemmNetDesc &d = rp.desc[(size_t)r * nn + i];
-            const int groups = (d.mtiles + cluster - 1) / cluster;
+            const int groups = (d.mtiles + pair - 1) / pair;
             for (int st = 0; st < d.stiles; ++st)
                 for (int g = 0; g < groups; ++g) rp.tiles.push_back(make_int4(i, g, st, 0));
         }
@@ -194,7 +195,7 @@ int upload_rounds(gbs_batch *b, const RoundPlan &rp) {
     return GBS_OK;
 }
 
-int round_gemm(gbs_batch *b, const RoundPlan &rp, int r, int cluster) {
+int round_gemm(gbs_batch *b, const RoundPlan &rp, int r, int pair) {
     const int nn = (int)b->nets.size();
     const int off = rp.tile_off[r], nt = rp.tile_off[r + 1] - off;
     gbs_net *n0 = b->nets[0];
@@ -206,11 +207,11 @@ int round_gemm(gbs_batch *b, const RoundPlan &rp, int r, int cluster) {
         sj.jobs = b->d_jobs + (size_t)(r + 1) * nn;
         sj.prefix = b->d_prefix + (size_t)(r + 1) * (nn + 1);
         sj.n = nn;
-        rc = launch_gemm_grouped_sampling(b->stream, b->sm_count, cluster,
+        rc = launch_gemm_grouped_sampling(b->stream, b->sm_count, pair, n0->wait_ns,
                                           b->d_desc + (size_t)r * nn, b->d_tiles + off, nt,
                                           n0->d_flags + 1, sj);
     } else {
-        rc = launch_gemm_grouped(b->stream, b->sm_count, b->P, cluster,
+        rc = launch_gemm_grouped(b->stream, b->sm_count, b->P, pair, 0, n0->wait_ns,
                                  b->d_desc + (size_t)r * nn, b->d_tiles + off, nt, 0,
                                  n0->d_flags + 1);
     }
@@ -281,7 +282,7 @@ int run_rounds(gbs_batch *b, const RoundPlan &rp, const uint64_t *seeds, const u
     int rc = GBS_OK, swaps = 0;
     for (int r = 0; r < rp.rounds && rc == GBS_OK; ++r) {
         if ((rc = round_front(b, rp, r, seeds, first, branches))) break;
-        if ((rc = round_gemm(b, rp, r, b->cluster))) break;
+        if ((rc = round_gemm(b, rp, r, b->pair))) break;
         if ((rc = round_back(b, rp, r, first, branches))) break;
         if (rp.fold) {
             swap_all(b, rp);
@@ -292,33 +293,41 @@ int run_rounds(gbs_batch *b, const RoundPlan &rp, const uint64_t *seeds, const u
     return rc;
 }
 
-// Time both cluster sizes on round 0 (samplers of round 0 run first so the
-// operands are real) and keep the faster.
+// Time the tile configurations (one CTA per tile; CTA pairs where the
+// autotuner takes them) on round 0 (samplers of round 0 run first so the
+// operands are real) and keep the fastest.
 int tune_batch(gbs_batch *b, const int64_t *E, const uint64_t *seeds, const uint64_t *first) {
-    int rc;
-    float ms[2] = {0.0f, 0.0f};
+    int rc = GBS_OK;
+    float best = 0.0f;
+    int best_pair = 1;
     cudaEvent_t e0, e1;
     GBS_CUDA_TRY(cudaEventCreate(&e0));
     GBS_CUDA_TRY(cudaEventCreate(&e1));
-    for (int c = 1; c <= 2; ++c) {
+    const int npair = tc_pair_autotune() ? 2 : 1;
+    for (int pair = 1; pair <= npair; ++pair) {
         RoundPlan rp;
-        if ((rc = build_rounds(b, E, c, rp))) break;
+        if ((rc = build_rounds(b, E, pair, rp))) break;
         if ((rc = upload_rounds(b, rp))) break;
         if ((rc = round_front(b, rp, 0, seeds, first))) break;
-        if ((rc = round_gemm(b, rp, 0, c))) break;  // warm-up
+        if ((rc = round_gemm(b, rp, 0, pair))) break;  // warm-up
         cudaEventRecord(e0, b->stream);
-        if ((rc = round_gemm(b, rp, 0, c))) break;
+        if ((rc = round_gemm(b, rp, 0, pair))) break;
         cudaEventRecord(e1, b->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) {
             rc = set_error(GBS_ECUDA, "batch autotuner timing failed");
             break;
         }
-        cudaEventElapsedTime(&ms[c - 1], e0, e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (pair == 1 || ms < best) {
+            best = ms;
+            best_pair = pair;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    b->cluster = (ms[0] < ms[1]) ? 1 : 2;
+    b->pair = best_pair;
     return GBS_OK;
 }
 
@@ -378,7 +387,7 @@ int gbs_sample_batch(gbs_batch_t b, const uint64_t *seeds, const uint64_t *first
         if (E[i] < 0) return set_error(GBS_EINVAL, "E[%d] < 0", i);
         if ((rc = fix_estimator(b->nets[i], n_sub[i], K1[i]))) return rc;
     }
-    if (!b->cluster) {
+    if (!b->pair) {
         if ((rc = tune_batch(b, E, seeds, first_sample))) return rc;
     }
     // fold a network's sampling into the GEMMs when it has more than one
@@ -394,7 +403,7 @@ int gbs_sample_batch(gbs_batch_t b, const uint64_t *seeds, const uint64_t *first
         fold = fold || fold_net[i];
     }
     RoundPlan rp;
-    if ((rc = build_rounds(b, E, b->cluster, rp, &fold_net, seeds, first_sample))) return rc;
+    if ((rc = build_rounds(b, E, b->pair, rp, &fold_net, seeds, first_sample))) return rc;
     if ((rc = upload_rounds(b, rp))) return rc;
     b->last_rounds = rp.rounds;
     b->last_tiles = (int64_t)rp.tiles.size();
@@ -434,9 +443,9 @@ int gbs_sample_batch(gbs_batch_t b, const uint64_t *seeds, const uint64_t *first
     return GBS_OK;
 }
 
-int gbs_batch_info(gbs_batch_t b, int *cluster, int *rounds, int64_t *tiles) {
+int gbs_batch_info(gbs_batch_t b, int *pair, int *rounds, int64_t *tiles) {
     if (!b) return set_error(GBS_EINVAL, "null batch");
-    if (cluster) *cluster = b->cluster;
+    if (pair) *pair = b->pair;
     if (rounds) *rounds = b->last_rounds;
     if (tiles) *tiles = b->last_tiles;
     return GBS_OK;

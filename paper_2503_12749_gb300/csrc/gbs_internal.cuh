@@ -73,7 +73,7 @@ struct TcPlan;  // tcgen05 GEMM plan (tensor maps, tiling), defined in k_gemm_tc
 // device memory so that one launch can serve many networks.
 struct __align__(128) GemmNetDesc {
     CUtensorMap mapA[3];     // A planes [K/32][rows][32], box 32 x 128 x 1
-    CUtensorMap mapB[2][3];  // B planes, box 32 x 256 x 1 (clusters of 1) / 32 x 128 x 1 (of 2)
+    CUtensorMap mapB[2][3];  // B planes, box 32 x 256 x 1 (one CTA per tile) / 32 x 128 x 1 (CTA pairs)
     int KB;                  // 32-wide K blocks
     int mtiles;              // 64-mode tiles
     int stiles;              // 128-trajectory tiles (grouped launches)
@@ -186,6 +186,9 @@ struct gbs_net {
     double2 *d_wfft = nullptr;      // [K1]: e^{-2 pi i k / K1}
     double *d_out = nullptr;        // [4][K1]
     unsigned long long *d_flags = nullptr;  // [4]: non-finite count, timeout flag, ...
+    // bound of every pipeline wait in this network's GEMM launches
+    // (gbs_set_wait_limit; the default gives up after 2 s)
+    uint64_t wait_ns = 2000000000ull;
 
     gbs::Profiler prof;
 
@@ -266,19 +269,27 @@ inline bool fold_wanted(const gbs_net *net) {
 bool tc_sampling_ready(gbs_net *net, bool allocate);
 // Swap (d_B, d_n, tensor maps) with their second copies.
 void tc_swap_sample_buffers(gbs_net *net);
-int tc_set_cluster(gbs_net *net, int cluster);  // 0 = autotune, 1, 2
-int tc_get_cluster(gbs_net *net);
-int tc_autotune(gbs_net *net, int64_t count, int *cluster);
+// GEMM configuration: pair = 1 (one CTA per tile) or 2 (CTA pairs,
+// cta_group::2), band = mode-tile groups per band of the tile order (0: plain
+// order); tc_set_config(net, 0, 0) returns to the autotuner.
+int tc_set_config(gbs_net *net, int pair, int band);
+void tc_get_config(gbs_net *net, int *pair, int *band);
+// Whether the autotuner also times CTA pairs (process-wide; clears its cache).
+void tc_set_pair_autotune(bool on);
+bool tc_pair_autotune();
+int tc_autotune(gbs_net *net, int64_t count, int *pair, int *band);
 int tc_products(gbs_net *net);
 int tc_fill_desc(gbs_net *net, GemmNetDesc *out, bool alt = false);  // alt: the second operand's maps
 // One launch over the tiles of many networks (d_tiles: {net, mode-tile group,
 // trajectory tile} per entry; NULL = closed-form tiles of d_nets[0] with
-// count0 trajectories).
-int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int cluster,
-                        const GemmNetDesc *d_nets, const int4 *d_tiles, int ntiles, int64_t count0,
-                        unsigned long long *err, OccOut occ = OccOut());
-// The same launch (3 products) whose spare warps run `jobs`.
-int launch_gemm_grouped_sampling(cudaStream_t stream, int sm_count, int cluster,
+// count0 trajectories in bands of `band` groups); wait_ns bounds every
+// pipeline wait of the kernel.
+int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int pair, int band,
+                        uint64_t wait_ns, const GemmNetDesc *d_nets, const int4 *d_tiles,
+                        int ntiles, int64_t count0, unsigned long long *err,
+                        OccOut occ = OccOut());
+// The same launch (3 products, listed tiles) whose spare warps run `jobs`.
+int launch_gemm_grouped_sampling(cudaStream_t stream, int sm_count, int pair, uint64_t wait_ns,
                                  const GemmNetDesc *d_nets, const int4 *d_tiles, int ntiles,
                                  unsigned long long *err, const SampleJobs &jobs);
 

@@ -127,6 +127,24 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const double *__restrict__ T6
     }
 }
 
+// FP64 FMA throughput probe: 8 independent FMA chains per thread (enough to
+// cover the pipe's latency), `iters` steps each; the sum is stored so that
+// nothing is eliminated.
+__global__ void __launch_bounds__(256) k_dfma_rate(double *__restrict__ out, int iters) {
+    const double m = 0.9999999999, c = 1e-12;
+    double a[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = 1.0 + 1e-3 * q + 1e-9 * threadIdx.x;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = fma(a[q], m, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += a[q];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 
 int launch_gemm_fp64(gbs_net *net, int64_t count, OccOut64 occ) {
@@ -143,3 +161,45 @@ int launch_gemm_fp64(gbs_net *net, int64_t count, OccOut64 occ) {
 }
 
 }  // namespace gbs
+
+using namespace gbs;
+
+extern "C" int gbs_measure_fp64_rate(void *stream, double *tflops) {
+    if (!tflops) return set_error(GBS_EINVAL, "tflops is NULL");
+    *tflops = 0.0;
+    int dev = 0, sms = 0;
+    GBS_CUDA_TRY(cudaGetDevice(&dev));
+    GBS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int blocks = 8 * sms, threads = 256, iters = 1 << 14;
+    double *out = nullptr;
+    GBS_CUDA_TRY(cudaMallocAsync(&out, sizeof(double) * blocks * threads, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = GBS_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = set_error(GBS_ECUDA, "event creation failed");
+    } else {
+        float best = 0.0f;
+        for (int rep = 0; rep < 4 && rc == GBS_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            k_dfma_rate<<<blocks, threads, 0, st>>>(out, iters);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = set_error(GBS_ECUDA, "FP64 rate probe failed: %s",
+                               cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && (best == 0.0f || ms < best)) best = ms;  // rep 0 warms up
+        }
+        if (rc == GBS_OK && best > 0.0f)
+            *tflops = 2.0 * 8.0 * (double)iters * blocks * threads / (best * 1e-3) / 1e12;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(out, st);
+    cudaStreamSynchronize(st);
+    return rc;
+}
+

@@ -22,19 +22,15 @@
 // the DeepSeek-V3 report's FP8 GEMMs).  Two TMEM buffers alternate per
 // segment of 64 K, so the MMAs of segment s+1 overlap the promotion of s.
 //
-// Kernel structure (one CTA per SM, clusters of 2 CTAs, persistent over tile
-// groups, 320 threads).  The CTAs of a cluster compute mode tiles 2g, 2g+1
-// of the same trajectory tile: each loads its own A planes and half of the
-// B planes, which TMA multicasts into both CTAs' shared memory, so the L2
-// delivers each B tile once per pair.  A stage is refilled only after
-// every CTA's MMAs released it (their commits arrive on all CTAs' barriers).
+// A tile is one 64-mode tile (128 A rows) times one 128-trajectory tile
+// (256 B rows).  Kernel structure (persistent over tiles, one CTA per SM,
+// 320 threads):
 //   warp 0      TMA producer: per 32-wide K block one box per BF16 plane used
 //               (A: 32 x 128, B: 32 x 256, 64-byte swizzle; the operands are
 //               stored K-blocked, [K/32][rows][32], so each box is one
 //               contiguous run of 8 or 16 KB and no row fetch moves unused
-//               bytes), every plane loaded
-//               once per K block, into a 4-stage (3 products) or 3-stage
-//               (6 products) shared-memory ring;
+//               bytes), every plane loaded once per K block, into a
+//               multi-stage shared-memory ring;
 //   warp 1      allocates 512 TMEM columns; one thread issues
 //               tcgen05.mma M=128 N=256 K=16 into the segment's buffer: with
 //               6 products, per segment of two K blocks the correction
@@ -52,6 +48,27 @@
 //               epilogue also writes every n'_i: with 3 products each warp
 //               stages its 32 x 16 values in shared memory and stores rows
 //               of 64 bytes, 8 rows per instruction.
+// CTA pairs (cta_group::2; clusters of 2 CTAs on the two SMs of a pair):
+// the pair computes mode tiles 2g and 2g+1 of one trajectory tile as one
+// M = 256 MMA issued by the pair's first CTA.  Each CTA loads its own A
+// tile (128 rows) and one half of the tile's B rows (the 128 alpha rows in
+// the first CTA, the 128 beta rows in the second) into its own shared
+// memory, and the pair's MMA reads B from both: every B byte crosses from
+// L2 to shared memory once per pair, and every load has one destination
+// (its own CTA).  Both CTAs' loads complete on the first CTA's stage barrier;
+// the first CTA's MMA commits arrive on the stage-free and accumulator-full
+// barriers of both CTAs; the epilogue warps of both CTAs arrive on the first
+// CTA's accumulator-free barrier.  Each CTA's TMEM then holds its own 128
+// rows x 256 columns, so the epilogue is the same in both.
+// Tile order (closed-form tiles of one network): bands of `band` mode-tile
+// groups (a group = the 1 or 2 mode tiles one CTA or pair computes); within
+// a band the trajectory tiles in order, the band's groups fastest.  A wave
+// of resident CTAs then shares each A tile among about (units / band)
+// trajectory tiles and each B tile among `band` groups, and the next wave of
+// the band reads the same A tiles again (from L2 while the band fits); a
+// band at least the number of groups is the plain order (every mode tile of
+// one trajectory tile side by side), which streams all of A through L2 once
+// per wave.
 // Sampling variant (3 products, 512 threads): warps 4..11 are the
 // epilogue, and warps 2, 3, 12..15 run the BF16 sampler (sampler_dev.cuh)
 // on the NEXT chunk's trajectories (of the one network, or of several
@@ -63,7 +80,8 @@
 // 65,536); the host launches this variant only after checking that the
 // kernel was built with exactly 128 registers per thread.
 // Every mbarrier wait is bounded; on a timeout the kernel raises an error
-// flag, drains its own TMA loads and MMAs, frees TMEM and returns.
+// flag, waits (bounded) for its own TMA loads and MMAs, frees TMEM and
+// returns; the host then rejects the launch's results.
 #include "gbs_internal.cuh"
 #include "tc_ptx.cuh"
 #include "sampler_dev.cuh"
@@ -74,6 +92,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 namespace gbs {
 
@@ -83,21 +102,23 @@ struct TcPlan {
     GemmNetDesc desc_alt;           // the same over the second sample operand
     GemmNetDesc *d_desc_alt = nullptr;
     int P = 0;
-    int cluster = 0;                // 1 or 2; 0 = pick by the autotuner
-    int forced = 0;                 // set by gbs_set_gemm_config
+    int pair = 0;                   // 1: a CTA per tile, 2: CTA pairs; 0 = pick by the autotuner
+    int band = 0;                   // groups per band of the tile order (0: plain order)
+    bool forced = false;            // set by gbs_set_gemm_config
 };
 
 namespace {
 
 // One pipeline stage holds every BF16 plane of one 32-wide K block: A planes
-// of 128 rows x 64 B, B planes of 256 rows x 64 B (64-byte swizzle).
-template <int P>
+// of 128 rows x 64 B, B planes of the CTA's B rows (256, or 128 in a pair)
+// x 64 B (64-byte swizzle).
+template <int P, int kPair>
 struct Cfg {
     static constexpr int kPlanes = (P == 3) ? 2 : 3;  // planes of A and of B used
     static constexpr int kAPlane = 128 * 64;
-    static constexpr int kBPlane = 256 * 64;
+    static constexpr int kBPlane = (256 / kPair) * 64;
     static constexpr int kStageBytes = kPlanes * (kAPlane + kBPlane);
-    static constexpr int kStages = (P == 3) ? 4 : 3;
+    static constexpr int kStages = (P == 3) ? (kPair == 1 ? 4 : 6) : (kPair == 1 ? 3 : 4);
 };
 constexpr int kBarBytes = 1024;
 constexpr int kEpiWarpsFwd = 8;  // epilogue warps (kEpiWarps below)
@@ -112,14 +133,19 @@ template <int P>
 constexpr int occ_stage_bytes() {
     return P == 3 ? kEpiWarpsFwd * kOccWarpFloats * 4 : 0;
 }
-template <int P>
+template <int P, int kPair>
 constexpr int smem_bytes() {
-    return 1024 + Cfg<P>::kStages * Cfg<P>::kStageBytes + kBarBytes + kRedBytes +
+    return 1024 + Cfg<P, kPair>::kStages * Cfg<P, kPair>::kStageBytes + kBarBytes + kRedBytes +
            occ_stage_bytes<P>();
 }
-static_assert(smem_bytes<3>() <= 227 * 1024, "shared memory of the 3-product GEMM");
-static_assert(smem_bytes<6>() <= 227 * 1024, "shared memory of the 6-product GEMM");
-constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(128, 256);
+static_assert(smem_bytes<3, 1>() <= 227 * 1024, "shared memory of the 3-product GEMM");
+static_assert(smem_bytes<6, 1>() <= 227 * 1024, "shared memory of the 6-product GEMM");
+static_assert(smem_bytes<3, 2>() <= 227 * 1024, "shared memory of the 3-product pair GEMM");
+static_assert(smem_bytes<6, 2>() <= 227 * 1024, "shared memory of the 6-product pair GEMM");
+template <int kPair>
+constexpr uint32_t idesc() {
+    return ptx::idesc_bf16_f32(128 * kPair, 256);
+}
 constexpr int kEpiWarps = kEpiWarpsFwd;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
@@ -165,8 +191,8 @@ static_assert(256 * kRegsEpi + (threads_of<2>() - 256) * regs_rest<2>() <=
 constexpr int kSampWG = 1;
 constexpr int kSampWarpsUsed = 4 * kSampWG + 2;
 
-// A tile of the grouped GEMM: which network, which group of kCl mode
-// tiles, which 128-trajectory tile.
+// A tile of the grouped GEMM: which network, which mode tile (of this CTA),
+// which 128-trajectory tile.
 struct TileRef {
     const GemmNetDesc *d;
     int mt;  // this CTA's mode tile (may be >= mtiles: then A reads zeros, nothing is written)
@@ -174,23 +200,39 @@ struct TileRef {
     int64_t count;
 };
 
-template <int kCl>
+// Tile t of a launch.  Listed tiles: {network, group, trajectory tile}.
+// Closed-form tiles of one network: bands of `band` groups (module
+// comment), a group being kPair consecutive mode tiles; CTA `rank` of the
+// pair takes mode tile kPair * group + rank.
+template <int kPair>
 __device__ __forceinline__ TileRef decode_tile(int t, const GemmNetDesc *nets, const int4 *tiles,
-                                               int64_t count0, uint32_t rank) {
+                                               int64_t count0, int band, uint32_t rank) {
     TileRef r;
+    int g;
     if (tiles) {
         const int4 e = tiles[t];
         r.d = nets + e.x;
-        r.mt = kCl * e.y + (int)rank;
+        g = e.y;
         r.st = e.z;
         r.count = r.d->count;
     } else {
         r.d = nets;
-        const int groups = (nets->mtiles + kCl - 1) / kCl;
-        r.mt = kCl * (t % groups) + (int)rank;
-        r.st = t / groups;
         r.count = count0;
+        const int groups = (nets->mtiles + kPair - 1) / kPair;
+        if (band <= 0 || band >= groups) {
+            g = t % groups;
+            r.st = t / groups;
+        } else {
+            const int stiles = (int)((count0 + kTcTileSamples - 1) / kTcTileSamples);
+            const int per = band * stiles;
+            const int bi = t / per;
+            const int rem = t - bi * per;
+            const int bw = min(band, groups - bi * band);
+            g = bi * band + rem % bw;
+            r.st = rem / bw;
+        }
     }
+    r.mt = kPair * g + (int)rank;
     return r;
 }
 
@@ -251,15 +293,18 @@ __device__ __forceinline__ void warp_transpose_reduce32(float (&v)[32], int lane
     }
 }
 
-template <int P, int kCl, int kSW>
+template <int P, int kPair, int kSW>
 __global__ void __launch_bounds__(threads_of<kSW>(), 1)
     k_gemm_tc(const GemmNetDesc *__restrict__ nets, const int4 *__restrict__ tiles, int ntiles,
-              int64_t count0, unsigned long long *err_ptr, OccOut occ, const SampleJobs sj) {
+              int64_t count0, int band, uint64_t wait_ns, unsigned long long *err_ptr,
+              OccOut occ, const SampleJobs sj) {
     static_assert(kSW == 0 || P == 3, "the sampling variant runs the 3-product GEMM");
+    static_assert(kPair == 1 || kPair == 2, "one CTA or a CTA pair per tile group");
     constexpr int kE0 = epi_warp0<kSW>();  // first epilogue warp
-    using C = Cfg<P>;
+    using C = Cfg<P, kPair>;
     constexpr int kStages = C::kStages;
     constexpr int kPl = C::kPlanes;
+    constexpr uint32_t kIdesc = idesc<kPair>();
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -277,13 +322,13 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
     uint64_t *tempty = bars + 2 * kStages + 2;
     uint64_t *drain = bars + 2 * kStages + 4;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 5);
+    uint64_t *never = bars + 2 * kStages + 6;  // no thread ever arrives on it
     float *red = reinterpret_cast<float *>(smem + kStages * C::kStageBytes + kBarBytes);
     float *ostage = reinterpret_cast<float *>(smem + kStages * C::kStageBytes + kBarBytes + kRedBytes);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     volatile unsigned long long *err = err_ptr;
-    constexpr uint16_t kMask = (uint16_t)((1u << kCl) - 1u);
     // split products A_i B_j, smallest first, A0 B0 last
     constexpr int kIa3[3] = {0, 1, 0}, kIb3[3] = {1, 0, 0};
     constexpr int kIa6[6] = {1, 0, 2, 0, 1, 0}, kIb6[6] = {1, 2, 0, 1, 0, 0};
@@ -291,31 +336,34 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             ptx::mbar_init(ptx::smem_u32(&full[s]), 1);
-            ptx::mbar_init(ptx::smem_u32(&empty[s]), kCl);  // released by every CTA of the cluster
+            ptx::mbar_init(ptx::smem_u32(&empty[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(ptx::smem_u32(&tfull[b]), 1);
-            ptx::mbar_init(ptx::smem_u32(&tempty[b]), kEpiThreads);
+            // one arrival per epilogue warp of every CTA of the pair
+            ptx::mbar_init(ptx::smem_u32(&tempty[b]), kEpiWarps * kPair);
         }
         ptx::mbar_init(ptx::smem_u32(drain), 1);
+        ptx::mbar_init(ptx::smem_u32(never), 1);
         ptx::fence_barrier_init();
     }
     if (warp == 1) {
-        ptx::tmem_alloc(ptx::smem_u32(tmem_slot), 512);
-        ptx::tmem_relinquish();
+        ptx::tmem_alloc<kPair>(ptx::smem_u32(tmem_slot), 512);
+        ptx::tmem_relinquish<kPair>();
     }
     ptx::tc_fence_before();
     __syncthreads();
-    if (kCl > 1) ptx::cluster_sync();  // the peers' barriers exist before anything is multicast
+    // both CTAs' barriers and TMEM columns exist before either signals the other
+    if (kPair > 1) ptx::cluster_sync();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    // A cluster of kCl CTAs works on a tile group: the same trajectory tile,
-    // mode tiles kCl*g + rank; each CTA loads 1/kCl of the B rows and (for
-    // kCl > 1) multicasts them to all.
-    const uint32_t rank = kCl > 1 ? ptx::cluster_ctarank() : 0u;
-    const int cluster = blockIdx.x / kCl;
-    const int nclusters = gridDim.x / kCl;
+    // A pair (kPair = 2) works on tile groups: the same trajectory tile, mode
+    // tiles 2g + rank; CTA rank 0 issues the pair's MMAs.
+    const uint32_t rank = kPair > 1 ? ptx::cluster_ctarank() : 0u;
+    const bool leader = rank == 0u;
+    const int unit = blockIdx.x / kPair;
+    const int nunits = gridDim.x / kPair;
 
     auto producer = [&]() {
         if (lane == 0) {
@@ -325,12 +373,12 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
             uint32_t used = 0, last_phase = 0;  // stages ever filled, parity of their last fill
             bool ok = true;
             const GemmNetDesc *cur = nullptr;
-            for (int tile = cluster; ok && tile < ntiles; tile += nclusters) {
-                const TileRef tr = decode_tile<kCl>(tile, nets, tiles, count0, rank);
+            for (int tile = unit; ok && tile < ntiles; tile += nunits) {
+                const TileRef tr = decode_tile<kPair>(tile, nets, tiles, count0, band, rank);
                 const GemmNetDesc *d = tr.d;
                 const CUtensorMap *mA[3] = {&d->mapA[0], &d->mapA[1], &d->mapA[2]};
-                const CUtensorMap *mB[3] = {&d->mapB[kCl - 1][0], &d->mapB[kCl - 1][1],
-                                            &d->mapB[kCl - 1][2]};
+                const CUtensorMap *mB[3] = {&d->mapB[kPair - 1][0], &d->mapB[kPair - 1][1],
+                                            &d->mapB[kPair - 1][2]};
                 if (d != cur) {
                     for (int q = 0; q < kPl; ++q) {
                         ptx::prefetch_tmap(mA[q]);
@@ -338,29 +386,39 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                     }
                     cur = d;
                 }
+                // this CTA's B rows: the whole tile, or in a pair its half
+                const int brow = tr.st * 256 + (int)rank * (256 / kPair);
                 for (int kb = 0; kb < d->KB; ++kb) {
-                    if (!ptx::mbar_wait(ptx::smem_u32(&empty[stage]), phase ^ 1u, err)) {
+                    if (!ptx::mbar_wait(ptx::smem_u32(&empty[stage]), phase ^ 1u, err, wait_ns)) {
                         ok = false;
                         break;
                     }
                     const uint32_t fb = ptx::smem_u32(&full[stage]);
-                    ptx::mbar_arrive_expect_tx(fb, C::kStageBytes);
                     // operands are K-blocked ([K/32][rows][32]): each box is
                     // one contiguous block of global memory
+                    if constexpr (kPair == 1) {
+                        ptx::mbar_arrive_expect_tx(fb, C::kStageBytes);
 #pragma unroll
-                    for (int q = 0; q < kPl; ++q)
-                        ptx::tma_load_3d(ptx::smem_u32(a_tile(stage, q)), mA[q], fb, 0,
-                                         tr.mt * 128, kb);
-                    const int brow = tr.st * 256 + (int)rank * (256 / kCl);
-                    const uint32_t bpart = rank * (uint32_t)(C::kBPlane / kCl);
+                        for (int q = 0; q < kPl; ++q)
+                            ptx::tma_load_3d(ptx::smem_u32(a_tile(stage, q)), mA[q], fb, 0,
+                                             tr.mt * 128, kb);
 #pragma unroll
-                    for (int q = 0; q < kPl; ++q) {
-                        if (kCl > 1)
-                            ptx::tma_load_3d_mc(ptx::smem_u32(b_tile(stage, q)) + bpart, mB[q], fb,
-                                                0, brow, kb, kMask);
-                        else
+                        for (int q = 0; q < kPl; ++q)
                             ptx::tma_load_3d(ptx::smem_u32(b_tile(stage, q)), mB[q], fb, 0, brow,
                                              kb);
+                    } else {
+                        // both CTAs' halves of the stage complete on the
+                        // first CTA's barrier, which expects them all
+                        if (leader) ptx::mbar_arrive_expect_tx(fb, 2 * C::kStageBytes);
+                        const uint32_t fb0 = ptx::cluster_addr(fb, 0u);
+#pragma unroll
+                        for (int q = 0; q < kPl; ++q)
+                            ptx::tma_load_3d_pair(ptx::smem_u32(a_tile(stage, q)), mA[q], fb0, 0,
+                                                  tr.mt * 128, kb);
+#pragma unroll
+                        for (int q = 0; q < kPl; ++q)
+                            ptx::tma_load_3d_pair(ptx::smem_u32(b_tile(stage, q)), mB[q], fb0, 0,
+                                                  brow, kb);
                     }
                     used |= 1u << stage;
                     last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
@@ -370,19 +428,56 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                     }
                 }
             }
-            // drain: every load issued by this thread has landed, and both
-            // CTAs' MMAs have released every stage (their arrivals are in)
-            for (int s = 0; s < kStages; ++s)
-                if (used & (1u << s)) {
-                    ptx::mbar_wait(ptx::smem_u32(&full[s]), (last_phase >> s) & 1u, err,
-                                   200000000ull);
-                    ptx::mbar_wait(ptx::smem_u32(&empty[s]), (last_phase >> s) & 1u, err,
-                                   200000000ull);
+            // drain.  Normally: every load issued by this thread has landed
+            // and the MMAs have released every stage (in a pair the second
+            // CTA sees only the releases, which follow its loads' completion
+            // on the first CTA's barrier).  After an error (the flag is up and
+            // the host rejects the launch) the releases may never come: one
+            // CTA waits only for its own loads to land; a pair, whose second
+            // CTA cannot see its loads complete, waits a fixed 100 us (a load
+            // takes microseconds) before the final cluster barrier.
+            bool failed = !ok || *err != 0ull;
+            for (int s = 0; !failed && s < kStages; ++s) {
+                if (!(used & (1u << s))) continue;
+                const uint32_t par = (last_phase >> s) & 1u;
+                if (leader && !ptx::mbar_wait(ptx::smem_u32(&full[s]), par, err, 200000000ull))
+                    failed = true;
+                else if (!ptx::mbar_wait(ptx::smem_u32(&empty[s]), par, err, 200000000ull))
+                    failed = true;
+            }
+            if (failed) {
+                if constexpr (kPair == 1) {
+                    for (int s = 0; s < kStages; ++s)
+                        if (used & (1u << s))
+                            ptx::mbar_wait(ptx::smem_u32(&full[s]), (last_phase >> s) & 1u, err,
+                                           200000000ull, false);
+                } else {
+                    const uint64_t t0 = ptx::globaltimer();
+                    while (ptx::globaltimer() - t0 < 100000ull) {
+                    }
                 }
+            }
         }
     };
+    // the stage-free / accumulator-full commit of the pair's MMAs: on this
+    // CTA's barrier and, in a pair, on the same barrier of the second CTA
+    auto commit_both = [&](uint64_t *bar) {
+        const uint32_t a = ptx::smem_u32(bar);
+        if constexpr (kPair == 1) {
+            ptx::mma_commit(a);
+        } else {
+            ptx::mma_commit_pair(a);
+            ptx::mma_commit_pair(ptx::cluster_addr(a, 1u));
+        }
+    };
+    auto mma = [&](uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+        if constexpr (kPair == 1)
+            ptx::mma_bf16(d, a, b, kIdesc, acc);
+        else
+            ptx::mma_bf16_pair(d, a, b, kIdesc, acc);
+    };
     auto mma_issuer = [&]() {
-        if (lane == 0) {
+        if (lane == 0 && leader) {
             // ---------------------------------------------------- MMA issuer
             // Per segment (two K blocks): the correction products of both
             // blocks first, then A0 B0 of both, into a fresh accumulator.
@@ -390,16 +485,23 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
             uint32_t phase = 0;
             uint32_t seg = 0;  // segments issued so far (selects the TMEM buffer)
             bool ok = true;
-            for (int tile = cluster; ok && tile < ntiles; tile += nclusters) {
-                const TileRef tr = decode_tile<kCl>(tile, nets, tiles, count0, rank);
+            // a wait limit of 0 asks for the timeout path itself: the first
+            // wait is on a barrier that no thread arrives on, so it gives up
+            // (raising the flag) before any MMA is issued
+            if (wait_ns == 0ull) ok = ptx::mbar_wait(ptx::smem_u32(never), 0u, err, 0ull);
+            for (int tile = unit; ok && tile < ntiles; tile += nunits) {
+                const TileRef tr = decode_tile<kPair>(tile, nets, tiles, count0, band, rank);
                 const int KB = tr.d->KB;
                 const int nseg = (KB + 1) / 2;  // promotion segments of two 32-wide K blocks
                 for (int sg = 0; ok && sg < nseg; ++sg, ++seg) {
                     const uint32_t b = seg & 1u;
-                    if (!ptx::mbar_wait(ptx::smem_u32(&tempty[b]), ((seg >> 1) & 1u) ^ 1u, err)) {
+                    // the epilogue warps of both CTAs have read this buffer
+                    if (!ptx::mbar_wait<(kPair > 1)>(ptx::smem_u32(&tempty[b]),
+                                                     ((seg >> 1) & 1u) ^ 1u, err, wait_ns)) {
                         ok = false;
                         break;
                     }
+                    ptx::tc_fence_after();
                     const int nst = (2 * sg + 1 < KB) ? 2 : 1;
                     if (P == 3) {
                         // 3 products: each K block's MMAs as soon as its
@@ -409,7 +511,7 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                         const uint32_t d = tmem_base + b * 256u;
                         uint32_t acc = 0u;
                         for (int q = 0; q < nst; ++q) {
-                            if (!ptx::mbar_wait(ptx::smem_u32(&full[stage]), phase, err)) {
+                            if (!ptx::mbar_wait(ptx::smem_u32(&full[stage]), phase, err, wait_ns)) {
                                 ok = false;
                                 break;
                             }
@@ -426,22 +528,18 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                             for (int pr = 0; pr < 3; ++pr) {
 #pragma unroll
                                 for (int kk = 0; kk < 2; ++kk) {
-                                    ptx::mma_bf16(d, dA[kIa3[pr]] + 2u * kk, dB[kIb3[pr]] + 2u * kk,
-                                                  kIdesc, acc);
+                                    mma(d, dA[kIa3[pr]] + 2u * kk, dB[kIb3[pr]] + 2u * kk, acc);
                                     acc = 1u;
                                 }
                             }
-                            if (kCl > 1)
-                                ptx::mma_commit_mc(ptx::smem_u32(&empty[stage]), kMask);
-                            else
-                                ptx::mma_commit(ptx::smem_u32(&empty[stage]));
+                            commit_both(&empty[stage]);
                             if (++stage == kStages) {
                                 stage = 0;
                                 phase ^= 1u;
                             }
                         }
                         if (!ok) break;
-                        ptx::mma_commit(ptx::smem_u32(&tfull[b]));
+                        commit_both(&tfull[b]);
                         continue;
                     }
                     int stg[2];
@@ -450,7 +548,7 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                     for (int q = 0; q < nst; ++q) {
                         // stage stg[q] has fill parity phase (q = 0) or, after a wrap, phase ^ 1
                         const uint32_t par = (q == 1 && stg[1] == 0) ? (phase ^ 1u) : phase;
-                        if (!ptx::mbar_wait(ptx::smem_u32(&full[stg[q]]), par, err)) {
+                        if (!ptx::mbar_wait(ptx::smem_u32(&full[stg[q]]), par, err, wait_ns)) {
                             ok = false;
                             break;
                         }
@@ -468,20 +566,15 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                             const uint32_t b0 = ptx::smem_u32(b_tile(stg[q], ib));
 #pragma unroll
                             for (int kk = 0; kk < 2; ++kk) {
-                                ptx::mma_bf16(d, ptx::desc_k_sw64(a0 + kk * 32),
-                                              ptx::desc_k_sw64(b0 + kk * 32), kIdesc, acc);
+                                mma(d, ptx::desc_k_sw64(a0 + kk * 32),
+                                    ptx::desc_k_sw64(b0 + kk * 32), acc);
                                 acc = 1u;
                             }
                         }
                     }
-                    // the stage is free once every CTA's MMAs have read it
-                    for (int q = 0; q < nst; ++q) {
-                        if (kCl > 1)
-                            ptx::mma_commit_mc(ptx::smem_u32(&empty[stg[q]]), kMask);
-                        else
-                            ptx::mma_commit(ptx::smem_u32(&empty[stg[q]]));
-                    }
-                    ptx::mma_commit(ptx::smem_u32(&tfull[b]));
+                    // the stage is free once the MMAs have read it
+                    for (int q = 0; q < nst; ++q) commit_both(&empty[stg[q]]);
+                    commit_both(&tfull[b]);
                     for (int q = 0; q < nst; ++q) {
                         if (++stage == kStages) {
                             stage = 0;
@@ -491,8 +584,12 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                 }
             }
             // drain: all MMAs issued by this thread have completed
-            ptx::mma_commit(ptx::smem_u32(drain));
-            ptx::mbar_wait(ptx::smem_u32(drain), 0u, err, 200000000ull);
+            if constexpr (kPair == 1)
+                ptx::mma_commit(ptx::smem_u32(drain));
+            else
+                ptx::mma_commit_pair(ptx::smem_u32(drain));
+            // (also after an error: issued MMAs always complete)
+            ptx::mbar_wait(ptx::smem_u32(drain), 0u, err, 200000000ull, false);
         }
     };
     auto epilogue = [&]() {
@@ -504,8 +601,8 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
         const int et = threadIdx.x - 32 * kE0;  // 0..255
         const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
         uint32_t seg = 0;
-        for (int tile = cluster; tile < ntiles; tile += nclusters) {
-            const TileRef tr = decode_tile<kCl>(tile, nets, tiles, count0, rank);
+        for (int tile = unit; tile < ntiles; tile += nunits) {
+            const TileRef tr = decode_tile<kPair>(tile, nets, tiles, count0, band, rank);
             const int mt = tr.mt;
             const int st = tr.st;
             const int nseg = (tr.d->KB + 1) / 2;
@@ -519,7 +616,7 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                 const uint32_t b = seg & 1u;
                 // on a timeout every epilogue thread keeps going (without
                 // waiting) so that all of them reach the same barriers
-                ptx::mbar_wait(ptx::smem_u32(&tfull[b]), (seg >> 1) & 1u, err);
+                ptx::mbar_wait(ptx::smem_u32(&tfull[b]), (seg >> 1) & 1u, err, wait_ns);
                 ptx::tc_fence_after();
                 const uint32_t tb = lane_base + b * 256u + (uint32_t)(half * 64);
                 float t[32];
@@ -539,8 +636,17 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                 ptx::tmem_ld_wait();
 #pragma unroll
                 for (int i = 0; i < 32; i += 2) add_f32x2(rb[32 + i], rb[33 + i], t[i], t[i + 1]);
+                // the warp's reads are done: one arrival per warp on the
+                // buffer's free barrier (the first CTA's, in a pair)
                 ptx::tc_fence_before();
-                ptx::mbar_arrive(ptx::smem_u32(&tempty[b]));
+                __syncwarp();
+                if (lane == 0) {
+                    const uint32_t tb_bar = ptx::smem_u32(&tempty[b]);
+                    if constexpr (kPair == 1)
+                        ptx::mbar_arrive(tb_bar);
+                    else
+                        ptx::mbar_arrive_cluster(ptx::cluster_addr(tb_bar, 0u));
+                }
             }
             // occupations of this row for the thread's 64 trajectories, in
             // groups of 16: real part a*b from the own row, imaginary part with
@@ -682,15 +788,17 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
 
     ptx::tc_fence_before();
     __syncthreads();
-    // no multicast or remote arrive from a peer is in flight past this point
-    if (kCl > 1) ptx::cluster_sync();
+    // a pair: the second CTA's TMEM is no longer read or written, and no
+    // signal between the two CTAs is pending, before either frees its columns
+    if (kPair > 1) ptx::cluster_sync();
     if (warp == 1) {
         ptx::tc_fence_after();
-        ptx::tmem_dealloc(tmem_base, 512);
+        ptx::tmem_dealloc<kPair>(tmem_base, 512);
     }
 }
 
 }  // namespace
+
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -724,12 +832,17 @@ namespace {
 
 std::mutex g_tc_mu;
 bool g_attr_set[64] = {};
-std::map<std::tuple<int, int, int>, int> g_tune;  // (log2 N, log2 M, products) -> cluster size
+// (log2 N, log2 M, products) -> (CTA pair, band) chosen by the autotuner
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;
+// Whether the autotuner also times CTA pairs (gbs_set_gemm_config can always
+// ask for them).
+bool g_pair_autotune = false;
 
-template <int P, int kCl, int kSW>
+template <int P, int kPair, int kSW>
 cudaError_t set_smem_attr() {
-    return cudaFuncSetAttribute(k_gemm_tc<P, kCl, kSW>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<P>());
+    return cudaFuncSetAttribute(k_gemm_tc<P, kPair, kSW>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_bytes<P, kPair>());
 }
 
 int ensure_attrs() {
@@ -766,29 +879,30 @@ bool sampling_kernels_ok() {
     return state == 1;
 }
 
-template <int P, int kCl, int kSW>
+template <int P, int kPair, int kSW>
 int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets, const int4 *d_tiles,
-                   int ntiles, int64_t count0, unsigned long long *err, OccOut occ,
-                   const SampleJobs &jobs) {
+                   int ntiles, int64_t count0, int band, uint64_t wait_ns, unsigned long long *err,
+                   OccOut occ, const SampleJobs &jobs) {
     if (ntiles <= 0) return GBS_OK;
-    const int clusters = std::max(1, std::min(ntiles, sm_count / kCl));
+    const int units = std::max(1, std::min(ntiles, sm_count / kPair));
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kCl * clusters);
+    cfg.gridDim = dim3(kPair * units);
     cfg.blockDim = dim3(threads_of<kSW>());
-    cfg.dynamicSmemBytes = smem_bytes<P>();
+    cfg.dynamicSmemBytes = smem_bytes<P, kPair>();
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kCl;
+    attr[0].val.clusterDim.x = kPair;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = kCl > 1 ? 1 : 0;
-    cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_tc<P, kCl, kSW>, d_nets, d_tiles, ntiles,
-                                        count0, err, occ, jobs);
+    cfg.numAttrs = kPair > 1 ? 1 : 0;
+    cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_tc<P, kPair, kSW>, d_nets, d_tiles, ntiles,
+                                        count0, band, wait_ns, err, occ, jobs);
     if (le != cudaSuccess)
-        return set_error(GBS_ECUDA, "launch of the GEMM (%d products, cluster %d%s) failed: %s", P,
-                         kCl, kSW ? ", sampling" : "", cudaGetErrorString(le));
+        return set_error(GBS_ECUDA, "launch of the GEMM (%d products, %s%s) failed: %s", P,
+                         kPair > 1 ? "CTA pairs" : "one CTA per tile", kSW ? ", sampling" : "",
+                         cudaGetErrorString(le));
     return GBS_OK;
 }
 
@@ -845,19 +959,22 @@ int bucket(int v) {
 
 }  // namespace
 
-int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int cluster,
-                        const GemmNetDesc *d_nets, const int4 *d_tiles, int ntiles, int64_t count0,
-                        unsigned long long *err, OccOut occ) {
+int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int pair, int band,
+                        uint64_t wait_ns, const GemmNetDesc *d_nets, const int4 *d_tiles,
+                        int ntiles, int64_t count0, unsigned long long *err, OccOut occ) {
     int rc;
     if ((rc = ensure_attrs())) return rc;
     if (occ.p && (d_tiles || occ.ld % 128 != 0 || occ.ld < count0))
         return set_error(GBS_EINVAL, "occupation output needs closed-form tiles and ld >= count, ld %% 128 == 0");
+    if (pair != 1 && pair != 2) return set_error(GBS_EINVAL, "GEMM tiles per CTA pair must be 1 or 2");
     const SampleJobs none;
     if (P == 3)
-        return cluster == 1 ? launch_variant<3, 1, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none)
-                            : launch_variant<3, 2, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none);
-    return cluster == 1 ? launch_variant<6, 1, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none)
-                        : launch_variant<6, 2, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, err, occ, none);
+        return pair == 1
+                   ? launch_variant<3, 1, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, wait_ns, err, occ, none)
+                   : launch_variant<3, 2, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, wait_ns, err, occ, none);
+    return pair == 1
+               ? launch_variant<6, 1, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, wait_ns, err, occ, none)
+               : launch_variant<6, 2, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, wait_ns, err, occ, none);
 }
 
 int tc_fill_desc(gbs_net *net, GemmNetDesc *out, bool alt) {
@@ -867,16 +984,17 @@ int tc_fill_desc(gbs_net *net, GemmNetDesc *out, bool alt) {
     return GBS_OK;
 }
 
-int launch_gemm_grouped_sampling(cudaStream_t stream, int sm_count, int cluster,
+int launch_gemm_grouped_sampling(cudaStream_t stream, int sm_count, int pair, uint64_t wait_ns,
                                  const GemmNetDesc *d_nets, const int4 *d_tiles, int ntiles,
                                  unsigned long long *err, const SampleJobs &jobs) {
     int rc;
     if ((rc = ensure_attrs())) return rc;
     if (!sampling_kernels_ok()) return set_error(GBS_EINVAL, "sampling GEMM unavailable");
-    return cluster == 1 ? launch_variant<3, 1, kSampWG>(stream, sm_count, d_nets, d_tiles, ntiles, 0,
-                                                        err, OccOut(), jobs)
-                        : launch_variant<3, 2, kSampWG>(stream, sm_count, d_nets, d_tiles, ntiles, 0,
-                                                        err, OccOut(), jobs);
+    if (pair != 1 && pair != 2) return set_error(GBS_EINVAL, "GEMM tiles per CTA pair must be 1 or 2");
+    return pair == 1 ? launch_variant<3, 1, kSampWG>(stream, sm_count, d_nets, d_tiles, ntiles, 0, 0,
+                                                     wait_ns, err, OccOut(), jobs)
+                     : launch_variant<3, 2, kSampWG>(stream, sm_count, d_nets, d_tiles, ntiles, 0, 0,
+                                                     wait_ns, err, OccOut(), jobs);
 }
 
 int tc_products(gbs_net *net) { return net->tc ? net->tc->P : 0; }
@@ -907,51 +1025,84 @@ void tc_plan_destroy(gbs_net *net) {
     net->tc = nullptr;
 }
 
-int tc_set_cluster(gbs_net *net, int cluster) {
+int tc_set_config(gbs_net *net, int pair, int band) {
     if (!net->tc) return set_error(GBS_EINVAL, "network has no tensor-core GEMM");
-    if (cluster < 0 || cluster > 2) return set_error(GBS_EINVAL, "cluster must be 0 (auto), 1 or 2");
-    net->tc->forced = cluster;
-    if (cluster) net->tc->cluster = cluster;
-    else net->tc->cluster = 0;
+    if (pair < 0 || pair > 2) return set_error(GBS_EINVAL, "pair must be 0 (auto), 1 or 2");
+    if (band < 0) return set_error(GBS_EINVAL, "band must be >= 0");
+    net->tc->forced = pair != 0;
+    net->tc->pair = pair;
+    net->tc->band = pair ? band : 0;
     return GBS_OK;
 }
 
-int tc_get_cluster(gbs_net *net) { return net->tc ? net->tc->cluster : 0; }
+void tc_get_config(gbs_net *net, int *pair, int *band) {
+    *pair = net->tc ? net->tc->pair : 0;
+    *band = net->tc ? net->tc->band : 0;
+}
 
-// Time the candidate cluster sizes on this chunk and keep the faster one
-// for this network and every network of the same size bucket.
-int tc_autotune(gbs_net *net, int64_t count, int *out) {
+void tc_set_pair_autotune(bool on) {
+    std::lock_guard<std::mutex> lock(g_tc_mu);
+    g_pair_autotune = on;
+    g_tune.clear();
+}
+
+bool tc_pair_autotune() {
+    std::lock_guard<std::mutex> lock(g_tc_mu);
+    return g_pair_autotune;
+}
+
+// The candidates the autotuner times: one CTA or CTA pairs per tile group,
+// each with the plain tile order and bands of 16 and 8 groups (where the
+// network has more groups than that).
+std::vector<std::pair<int, int>> tc_candidates(int mtiles, bool pairs) {
+    std::vector<std::pair<int, int>> c;
+    for (int pair = 1; pair <= (pairs ? 2 : 1); ++pair) {
+        const int groups = (mtiles + pair - 1) / pair;
+        c.push_back({pair, 0});
+        for (int band : {16, 8})
+            if (groups > band) c.push_back({pair, band});
+    }
+    return c;
+}
+
+// Time the candidate configurations on this chunk (one warm-up and one timed
+// launch each) and keep the fastest for this network and every network of
+// the same size bucket.
+int tc_autotune(gbs_net *net, int64_t count, int *pair_out, int *band_out) {
     TcPlan *plan = net->tc;
     const auto key = std::make_tuple(bucket(net->N), bucket(net->M), plan->P);
+    bool pairs;
     {
         std::lock_guard<std::mutex> lock(g_tc_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
-            *out = it->second;
+            *pair_out = it->second.first;
+            *band_out = it->second.second;
             return GBS_OK;
         }
+        pairs = g_pair_autotune;
     }
+    *pair_out = 1;
+    *band_out = 0;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     GBS_CUDA_TRY(cudaStreamIsCapturing(net->stream, &cs));
-    if (cs != cudaStreamCaptureStatusNone) {  // no timing inside a capture: default
-        *out = 2;
-        return GBS_OK;
-    }
-    const int groups_ntiles[2] = {net->mtiles, (net->mtiles + 1) / 2};
+    if (cs != cudaStreamCaptureStatusNone) return GBS_OK;  // no timing inside a capture: default
     const int stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
     cudaEvent_t e0, e1;
     GBS_CUDA_TRY(cudaEventCreate(&e0));
     GBS_CUDA_TRY(cudaEventCreate(&e1));
     float best = 0.0f;
-    int best_c = 2, rc = GBS_OK;
-    for (int c = 1; c <= 2 && rc == GBS_OK; ++c) {
-        const int nt = groups_ntiles[c - 1] * stiles;
-        rc = launch_gemm_grouped(net->stream, net->sm_count, plan->P, c, plan->d_desc, nullptr, nt,
-                                 count, net->d_flags + 1);
+    int rc = GBS_OK;
+    bool first = true;
+    for (const auto &cand : tc_candidates(net->mtiles, pairs)) {
+        const int pair = cand.first, band = cand.second;
+        const int nt = ((net->mtiles + pair - 1) / pair) * stiles;
+        rc = launch_gemm_grouped(net->stream, net->sm_count, plan->P, pair, band, net->wait_ns,
+                                 plan->d_desc, nullptr, nt, count, net->d_flags + 1);
         if (rc) break;
         cudaEventRecord(e0, net->stream);
-        rc = launch_gemm_grouped(net->stream, net->sm_count, plan->P, c, plan->d_desc, nullptr, nt,
-                                 count, net->d_flags + 1);
+        rc = launch_gemm_grouped(net->stream, net->sm_count, plan->P, pair, band, net->wait_ns,
+                                 plan->d_desc, nullptr, nt, count, net->d_flags + 1);
         if (rc) break;
         cudaEventRecord(e1, net->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -960,30 +1111,32 @@ int tc_autotune(gbs_net *net, int64_t count, int *out) {
         }
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (c == 1 || ms < best) {
+        if (first || ms < best) {
             best = ms;
-            best_c = c;
+            *pair_out = pair;
+            *band_out = band;
+            first = false;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
     std::lock_guard<std::mutex> lock(g_tc_mu);
-    g_tune[key] = best_c;
-    *out = best_c;
+    g_tune[key] = std::make_pair(*pair_out, *band_out);
     return GBS_OK;
 }
 
 namespace {
 
-int pick_cluster(gbs_net *net, int64_t count) {
+int pick_config(gbs_net *net, int64_t count) {
     TcPlan *plan = net->tc;
-    if (!plan->cluster) {
-        int c = 2, rc;
-        if ((rc = tc_autotune(net, count, &c))) return -rc;
-        plan->cluster = c;
+    if (!plan->pair) {
+        int pair = 1, band = 0, rc;
+        if ((rc = tc_autotune(net, count, &pair, &band))) return rc;
+        plan->pair = pair;
+        plan->band = band;
     }
-    return plan->cluster;
+    return GBS_OK;
 }
 
 }  // namespace
@@ -994,12 +1147,12 @@ int launch_gemm_tc(gbs_net *net, int64_t count, OccOut occ) {
     if (!plan) return set_error(GBS_EINVAL, "no tensor-core plan");
     int rc;
     if ((rc = ensure_attrs())) return rc;
-    const int cl = pick_cluster(net, count);
-    if (cl < 0) return -cl;
-    const int groups = (net->mtiles + cl - 1) / cl;
+    if ((rc = pick_config(net, count))) return rc;
+    const int groups = (net->mtiles + plan->pair - 1) / plan->pair;
     const int stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
-    return launch_gemm_grouped(net->stream, net->sm_count, plan->P, cl, plan->d_desc, nullptr,
-                               groups * stiles, count, net->d_flags + 1, occ);
+    return launch_gemm_grouped(net->stream, net->sm_count, plan->P, plan->pair, plan->band,
+                               net->wait_ns, plan->d_desc, nullptr, groups * stiles, count,
+                               net->d_flags + 1, occ);
 }
 
 int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job, OccOut occ) {
@@ -1011,16 +1164,18 @@ int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job, O
         return set_error(GBS_EINVAL, "occupation output needs ld >= count, ld %% 128 == 0");
     int rc;
     if ((rc = ensure_attrs())) return rc;
-    const int cl = pick_cluster(net, count);
-    if (cl < 0) return -cl;
-    const int groups = (net->mtiles + cl - 1) / cl;
+    if ((rc = pick_config(net, count))) return rc;
+    const int groups = (net->mtiles + plan->pair - 1) / plan->pair;
     const int stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
     SampleJobs jobs;
     jobs.one = job;
-    return cl == 1 ? launch_variant<3, 1, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
-                                                groups * stiles, count, net->d_flags + 1, occ, jobs)
-                   : launch_variant<3, 2, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
-                                                groups * stiles, count, net->d_flags + 1, occ, jobs);
+    return plan->pair == 1
+               ? launch_variant<3, 1, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
+                                               groups * stiles, count, plan->band, net->wait_ns,
+                                               net->d_flags + 1, occ, jobs)
+               : launch_variant<3, 2, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
+                                               groups * stiles, count, plan->band, net->wait_ns,
+                                               net->d_flags + 1, occ, jobs);
 }
 
 bool tc_sampling_ready(gbs_net *net, bool allocate) {

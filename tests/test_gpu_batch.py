@@ -1,8 +1,9 @@
 """Tile configurations of the tcgen05 GEMM and batched uneven networks.
 
-Cluster sizes 1 and 2 differ only in how the trajectory operand reaches
-shared memory (direct loads vs a multicast shared by a CTA pair); the MMA
-arithmetic is the same, so per-trajectory results must agree bitwise.  A
+The tile configurations (one CTA per tile or CTA pairs, plain or banded
+tile order) differ only in which CTA computes which tile and how the
+operands reach shared memory; each output element's MMA chain is the same,
+so per-trajectory results must agree bitwise.  A
 batch issues the same kernels per network (one grouped GEMM per round), so
 its sub-ensemble sums must equal per-network runs bitwise, and every
 network's P(m) must match its exact distribution within sampling error.
@@ -29,18 +30,24 @@ def gbs():
     return g
 
 
+CONFIGS = [pytest.param((1, 0), id="cta"), pytest.param((1, 1), id="cta-band1"),
+           pytest.param((1, 2), id="cta-band2"), pytest.param((2, 0), id="pair"),
+           pytest.param((2, 1), id="pair-band1")]
+
+
+@pytest.mark.parametrize("config", CONFIGS)
 @pytest.mark.parametrize("shape", [(16, 16), (9, 9), (300, 300), (130, 200), (257, 100)])
-def test_cluster_sizes_agree_bitwise(gbs, shape):
+def test_tile_configurations_agree_bitwise(gbs, shape, config):
     import torch
     stream = torch.cuda.current_stream().cuda_stream
     N, M = shape
     net_def = wl.small_network(N, M=M, r=0.8, t2=0.93, seed=31 + N)
     res = []
-    for cl in (1, 2):
+    for cfg in ((1, 0), config):
         net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
-        gbs.gbs_set_gemm_config(net, cl)
+        gbs.gbs_set_gemm_config(net, *cfg)
         n, nS = gbs.gbs_debug_samples(net, net_def.seed_s, 100, 333)
-        assert gbs.gbs_gemm_config(net) == cl
+        assert gbs.gbs_gemm_config(net) == cfg
         res.append(nS)
         gbs.gbs_free_network(net)
     assert np.array_equal(res[0], res[1])
@@ -48,14 +55,34 @@ def test_cluster_sizes_agree_bitwise(gbs, shape):
     assert np.max(np.abs(res[0] - nSo) / np.maximum(np.abs(nSo), 1.0)) < 2.0 ** -12
 
 
+@pytest.mark.parametrize("config", CONFIGS)
+def test_tile_configurations_agree_on_many_tiles(gbs, config):
+    """A network of 10 mode tiles over 3 waves of trajectory tiles (the
+    bands, pairs and the ragged last band all in use), 6 products: the
+    per-trajectory totals of every configuration are bitwise those of the
+    plain one."""
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    net_def = wl.small_network(320, M=640, r=0.6, t2=0.9, seed=77)
+    res = []
+    for cfg in ((1, 0), config):
+        net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x6", stream)
+        gbs.gbs_set_gemm_config(net, *cfg)
+        n, nS = gbs.gbs_debug_samples(net, net_def.seed_s, 0, 3 * 152 * 128 + 77)
+        res.append(nS)
+        gbs.gbs_free_network(net)
+    assert np.array_equal(res[0], res[1])
+
+
 def test_autotuner_picks_a_configuration(gbs):
     import torch
     stream = torch.cuda.current_stream().cuda_stream
     net_def = wl.small_network(200, r=0.7, t2=0.9, seed=3)
     net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
-    assert gbs.gbs_gemm_config(net) == 0
+    assert gbs.gbs_gemm_config(net) == (0, 0)
     gbs.gbs_sample(net, net_def.seed_s, 0, 5000, 10, 256)
-    assert gbs.gbs_gemm_config(net) in (1, 2)
+    pair, band = gbs.gbs_gemm_config(net)
+    assert pair in (1, 2) and band >= 0
     gbs.gbs_free_network(net)
 
 

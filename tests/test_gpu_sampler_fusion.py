@@ -2,7 +2,7 @@
 gbs_sample over several chunks draws chunk i + 1's samples in the spare warps
 of chunk i's GEMM.  The draws are the same Philox counters through the same
 device code, so the sub-ensemble sums must equal those of the plain chunk
-loop bit for bit, for both cluster sizes, ragged last chunks and calls that
+loop bit for bit, for one CTA per tile and CTA pairs, ragged last chunks and calls that
 start mid-ensemble; the other entry points run unchanged after it.  Mode 2
 folds on any network (these are small); mode 1, the default, only from 900
 output modes.
@@ -31,9 +31,9 @@ def stream():
     return torch.cuda.Stream().cuda_stream
 
 
-def _sums(gbs, stream, net_def, fuse, cluster, calls, n_sub, K1):
+def _sums(gbs, stream, net_def, fuse, config, calls, n_sub, K1):
     net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
-    gbs.gbs_set_gemm_config(net, cluster)
+    gbs.gbs_set_gemm_config(net, *config)
     gbs.gbs_set_sampler_fusion(net, 2 if fuse else 0)
     for first, E in calls:
         gbs.gbs_sample(net, net_def.seed_s, first, E, n_sub, K1)
@@ -44,9 +44,9 @@ def _sums(gbs, stream, net_def, fuse, cluster, calls, n_sub, K1):
     return acc, counts, P, active
 
 
-@pytest.mark.parametrize("cluster", [1, 2])
+@pytest.mark.parametrize("config", [pytest.param((1, 0), id="cta"), pytest.param((2, 0), id="pair")])
 @pytest.mark.parametrize("N,M", [(24, 40), (300, 260)])
-def test_folded_sampler_is_bitwise_the_plain_loop(gbs, stream, cluster, N, M):
+def test_folded_sampler_is_bitwise_the_plain_loop(gbs, stream, config, N, M):
     net_def = wl.small_network(N, M, r=0.7, t2=0.9, seed=90 + N)
     probe = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
     chunk = gbs.gbs_network_info(probe)[3]
@@ -55,8 +55,8 @@ def test_folded_sampler_is_bitwise_the_plain_loop(gbs, stream, cluster, N, M):
     # covers one full chunk and a 1-trajectory tail
     calls = [(0, 2 * chunk + 12345), (2 * chunk + 12345, chunk + 1)]
     n_sub, K1 = 20, 256
-    a0, c0, P0, act0 = _sums(gbs, stream, net_def, False, cluster, calls, n_sub, K1)
-    a1, c1, P1, act1 = _sums(gbs, stream, net_def, True, cluster, calls, n_sub, K1)
+    a0, c0, P0, act0 = _sums(gbs, stream, net_def, False, config, calls, n_sub, K1)
+    a1, c1, P1, act1 = _sums(gbs, stream, net_def, True, config, calls, n_sub, K1)
     assert not act0
     assert act1, "folded sampler not taken"
     assert np.array_equal(c0, c1)

@@ -14,7 +14,7 @@ import pytest
 
 import oracle.exact as ex
 import workloads as wl
-from stats import agreement
+from stats import agreement, pooled_z2
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -283,6 +283,26 @@ def test_matrixP_estimator_unbiased(orc, case):
     assert im[0] < 1e-3
     if case == "lossless":
         assert np.max(np.abs(P[0][1::2])) < 1e-12  # odd counts vanish (Eq. c-number-variable)
+
+
+def test_sigma_scale_pooled_over_seeds(orc):
+    """The reported sigma is the standard error of P(m), from both sides:
+    over 16 independent ensembles (seeds) of a lossy 6-mode network, the
+    pooled mean (dP / sigma)^2 against the exact distribution lies in
+    [0.5, 2] and about two thirds of the bulk bins lie within one sigma.  The
+    same check fails for sigma scaled by 2 or by 1/2."""
+    net = wl.small_network(6, r=0.6, t2=0.9, seed=9)
+    E, n_sub, K1 = 2 ** 13, 16, 64
+    Pex = ex.exact_distribution(ex.eigenvalues_uniform_loss(net.r, 0.9), K1).real
+    runs = []
+    for k in range(16):
+        P, s, _ = orc.run(net.T, net.r, net.seed_s + 1000 * k, 0, E, n_sub, K1)
+        runs.append((P[0], s[0], Pex))
+    res = pooled_z2(runs)
+    assert 0.5 <= res["mean_z2"] <= 2.0, res
+    assert 0.5 <= res["frac_within_1sigma"] <= 0.85, res
+    assert pooled_z2([(P, 2.0 * s, R) for P, s, R in runs])["mean_z2"] < 0.5
+    assert pooled_z2([(P, 0.5 * s, R) for P, s, R in runs])["mean_z2"] > 2.0
 
 
 def test_direct_route_equals_gf_route(orc):

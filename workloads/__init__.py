@@ -82,8 +82,15 @@ class Workload:
             r = rng.uniform(self.r_lo, self.r_hi, size=self.N)
         return np.ascontiguousarray(r, dtype=np.float64)
 
-    def network(self) -> Network:
-        U = haar_unitary(self.M, SEED_U_BASE + self.index)
+    def network(self, device: bool = False) -> Network:
+        """T = sqrt(t2) U and r.  device=True draws the same Ginibre matrix
+        but takes its QR on the GPU (haar_unitary_device; equal up to
+        rounding, much faster for thousands of modes) and returns T on the
+        host."""
+        if device:
+            U = haar_unitary_device(self.M, SEED_U_BASE + self.index).cpu().numpy()
+        else:
+            U = haar_unitary(self.M, SEED_U_BASE + self.index)
         if self.N != self.M:
             U = U[:, : self.N]
         T = np.ascontiguousarray(math.sqrt(self.t2) * U, dtype=np.complex128)
