@@ -44,6 +44,13 @@ UNIT = "samples/s"
 # run without an entry reports traffic null.
 GEMM_TRAFFIC_BYTES_PER_SAMPLE = {}
 
+# FP32-pipe lane operations per evaluated (trajectory, k) pair of the
+# double-float generating-function kernel (k_gf_df), from an ncu capture
+# (FP32 thread instructions, packed FP32x2 ones counted twice, divided by the
+# launch's in-window pairs from gbs_debug_windows); valid for the kernel
+# version of that capture only, else None.
+GF_FP32_OPS_PER_PAIR = None
+
 
 def _env_int(name, default):
     try:
@@ -176,6 +183,28 @@ def reference_arm(args, wl_def):
     }
     print(json.dumps(line))
     return 0
+
+
+def _window_pairs(w, K1):
+    """Per trajectory, the k of the K1 roots of unity at which the
+    generating-function kernel evaluates a term: cyclic distance to k = 0 at
+    most w1, or to k = K1/2 at most w2 (w[:, 0], w[:, 1]; -1 = none,
+    >= K1/2 = all)."""
+    import numpy as np
+    half = K1 // 2
+    w1 = w[:, 0].astype(np.int64)
+    w2 = w[:, 1].astype(np.int64)
+
+    def count_within(wv):
+        return np.where(wv < 0, 0, np.where(wv >= half, K1, 2 * wv + 1))
+
+    def count_dist(lo, hi):  # k whose distance to k = 0 lies in [lo, hi] (0 <= lo, hi <= half)
+        n = 2 * (hi - lo + 1) - (lo == 0) - (hi == half)
+        return np.where(hi >= lo, n, 0)
+
+    both = np.where((w1 >= 0) & (w2 >= 0),
+                    count_dist(np.maximum(half - np.minimum(w2, half), 0), np.minimum(w1, half)), 0)
+    return count_within(w1) + count_within(w2) - both
 
 
 def _fp64_samples(wl_def, n_sub):
@@ -348,6 +377,24 @@ def gbs_arm(args, wl_def):
               for k, v in prof.items()}
     launches = int(sum(v[1] for v in prof.values()))
 
+    # the generating-function phase: in-window (trajectory, k) pairs per
+    # second, the pairs counted from the kernels' own windows on a sample
+    roof_gf = None
+    if tc_path and prof["gf"][0] > 0:
+        nw = min(E, 65536)
+        w = gbs.gbs_debug_windows(net, seed, base, nw)
+        ppt = float(np.mean(_window_pairs(w, K1)))
+        pairs_s = ppt * E * args.steps / (prof["gf"][0] / 1e3)
+        fma_peak = 152 * 128 * (clk.get("sm_max_mhz") or 2070.0) * 1e6
+        roof_gf = {"bound": "alu", "kernel": "k_gf_df", "unit": "pairs/s",
+                   "pairs_per_trajectory": ppt, "achieved_pairs_per_s": pairs_s,
+                   "pairs_sample": nw, "fp32_ops_per_pair": GF_FP32_OPS_PER_PAIR,
+                   "peak_fp32_lane_ops_per_s": fma_peak,
+                   "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"}
+        if GF_FP32_OPS_PER_PAIR:
+            roof_gf["achieved_fp32_lane_ops_per_s"] = pairs_s * GF_FP32_OPS_PER_PAIR
+            roof_gf["frac"] = pairs_s * GF_FP32_OPS_PER_PAIR / fma_peak
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -367,6 +414,7 @@ def gbs_arm(args, wl_def):
                    "sampler": ("drawn in the spare warps of the previous chunk's GEMM"
                                if folded else "one launch per chunk")},
         "roofline": roof,
+        "roofline_gf": roof_gf,
         "phases": phases,
         "result": acc_summary,
         "gpu_launches": launches,

@@ -110,9 +110,13 @@ int gbs_make_network_device(int N, int M, const double *T_dev, const double *r, 
  * a fixed order, so the same sequence of calls gives bitwise the same sums,
  * and so does a call split into calls at its own chunk boundaries (other
  * splits agree to rounding).  With the sampler folded into the GEMM
- * (gbs_set_sampler_fusion), the last chunk's GEMM also draws the first
- * chunk of a following call on the same seed from first_sample + E, which
- * that call then does not draw again (the samples are the same either way).
+ * (gbs_set_sampler_fusion), when this call continues the network's
+ * previous gbs_sample call (same seed, first_sample = that call's
+ * first_sample + E), its last chunk's GEMM also draws the first chunk of a
+ * following call on the same seed from first_sample + E, which that call
+ * then does not draw again (the samples are the same either way): a stream
+ * of consecutive calls then has no sampler launch, and a one-off call draws
+ * nothing it does not use.
  */
 int gbs_sample(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, int n_sub,
                int K1);
@@ -299,6 +303,18 @@ int gbs_check_finite(gbs_net_t net, int64_t *count);
  */
 int gbs_debug_samples(gbs_net_t net, uint64_t seed, uint64_t e0, int64_t count, double *n,
                       double *nS);
+
+/*
+ * gbs_debug_windows -- the evaluation windows of the generating functions
+ * for trajectories e0 .. e0+count-1 of key `seed` (measurement of the
+ * generating-function work): w[2*count] as (w1, w2) per trajectory, host;
+ * the terms e^{(z_k-1) n_S} are evaluated for the k within w1 of k = 0 and
+ * matrix-P's e^{-(z_k-1) n_S - 2n} for the k within w2 of k = K1/2 (cyclic
+ * distance; -1 = none, >= K1/2 = every k), every term outside below 2^-60.
+ * Needs K1 fixed by a gbs_sample call.  Does not touch the sub-ensemble
+ * sums.  Synchronises.  Errors: EINVAL, ECUDA.
+ */
+int gbs_debug_windows(gbs_net_t net, uint64_t seed, uint64_t e0, int64_t count, int *w);
 
 /*
  * gbs_debug_occupations -- the per-mode occupations n'_i = alpha'_i beta'_i

@@ -87,6 +87,8 @@ def lib():
         L.gbs_set_pair_autotune.argtypes = [ctypes.c_int]
         L.gbs_set_wait_limit.argtypes = [vp, ctypes.c_uint64]
         L.gbs_measure_fp64_rate.argtypes = [vp, dp]
+        L.gbs_debug_windows.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                        ip]
         L.gbs_make_network_binned.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ip, ctypes.c_int,
                                               vp, ctypes.POINTER(vp)]
         L.gbs_histogram.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ip,
@@ -141,6 +143,7 @@ def lib():
                      "gbs_network_info", "gbs_profile_enable", "gbs_profile_read",
                      "gbs_binned_counts_noalloc", "gbs_set_gemm_config", "gbs_gemm_config",
                      "gbs_set_pair_autotune", "gbs_set_wait_limit", "gbs_measure_fp64_rate",
+                     "gbs_debug_windows",
                      "gbs_set_sampler_fusion", "gbs_sampler_fusion",
                      "gbs_make_batch", "gbs_sample_batch", "gbs_batch_info",
                      "gbs_make_network_device", "gbs_make_network_binned", "gbs_sample_2d",
@@ -345,6 +348,14 @@ def gbs_debug_samples(net: Network, seed: int, e0: int, count: int):
     nS = np.zeros(2 * count)
     _check(lib().gbs_debug_samples(net.handle, seed, e0, count, _dptr(n), _dptr(nS)))
     return n, nS.view(np.complex128)
+
+
+def gbs_debug_windows(net: Network, seed: int, e0: int, count: int) -> np.ndarray:
+    """Per-trajectory generating-function windows (w1, w2) as int32 [count, 2]."""
+    w = np.zeros(2 * count, dtype=np.int32)
+    _check(lib().gbs_debug_windows(net.handle, seed, e0, count,
+                                   w.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    return w.reshape(count, 2)
 
 
 def gbs_get_accumulators(net: Network, with_data: bool = True):

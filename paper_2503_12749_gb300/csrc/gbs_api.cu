@@ -333,7 +333,10 @@ int sample_chunks_pipelined(gbs_net *net, uint64_t seed, uint64_t first, int64_t
         prof_mark(net, GBS_PHASE_GF, 1, false);
         return GBS_OK;
     };
-    return pipelined_chunks(net, seed, first, E, chunk_step(net, E), gemm, after, true);
+    // draw ahead only within a stream of consecutive calls: this call
+    // continues the previous one, so the next probably continues this one
+    const bool ahead = net->have_last && net->last_seed == seed && net->last_end == first;
+    return pipelined_chunks(net, seed, first, E, chunk_step(net, E), gemm, after, ahead);
 }
 
 // T (device, M x N complex, (re, im) interleaved, row-major) -> [M][2][N] FP64.
@@ -754,6 +757,9 @@ int gbs_sample(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, i
         }
     }
     count_samples(net, first_sample, E);
+    net->have_last = true;
+    net->last_seed = seed;
+    net->last_end = first_sample + (uint64_t)E;
     return GBS_OK;
 }
 
@@ -841,6 +847,25 @@ int gbs_debug_samples(gbs_net_t net, uint64_t seed, uint64_t e0, int64_t count, 
         }
     }
     net->K1 = saved_K1;
+    return GBS_OK;
+}
+
+int gbs_debug_windows(gbs_net_t net, uint64_t seed, uint64_t e0, int64_t count, int *w) {
+    int rc;
+    if ((rc = validate_net(net))) return rc;
+    if (count < 0 || !w) return set_error(GBS_EINVAL, "bad count or NULL output");
+    if (!net->est_fixed) return set_error(GBS_EINVAL, "K1 not fixed yet (call gbs_sample first)");
+    static_assert(sizeof(Window) == 2 * sizeof(int), "window layout");
+    for (int64_t done = 0; done < count; done += net->chunk) {
+        const int64_t c = std::min<int64_t>(net->chunk, count - done);
+        if ((rc = run_chunk_front(net, seed, e0 + (uint64_t)done, c))) return rc;
+        cudaError_t e1 = cudaMemcpyAsync(w + 2 * done, net->d_win, sizeof(Window) * c,
+                                         cudaMemcpyDeviceToHost, net->stream);
+        cudaError_t e2 = cudaStreamSynchronize(net->stream);
+        if (e1 != cudaSuccess || e2 != cudaSuccess)
+            return set_error(GBS_ECUDA, "debug copy failed: %s",
+                             cudaGetErrorString(e2 != cudaSuccess ? e2 : e1));
+    }
     return GBS_OK;
 }
 

@@ -168,6 +168,10 @@ struct gbs_net {
     uint64_t pre_seed = 0, pre_e0 = 0;
     int64_t pre_count = 0;
     void *pre_buf = nullptr;        // the operand (d_B or d_B_alt) holding them
+    // the last gbs_sample call's seed and first + E: a call that continues it
+    // (same seed, first = that end) draws ahead for the call after it
+    bool have_last = false;
+    uint64_t last_seed = 0, last_end = 0;
     double2 *d_nS_part = nullptr;   // [mtiles][chunk]
     int mtiles = 0;
     double2 *d_nS = nullptr;        // [chunk]

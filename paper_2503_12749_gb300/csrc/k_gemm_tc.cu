@@ -15,12 +15,12 @@
 // Accumulator promotion: the tensor core's FP32 accumulation truncates each
 // MMA's result, a bias of ~1 ulp of the running sum per instruction that
 // grows linearly with the number of MMAs chained into one accumulator
-// (measured: ~2^-24 of the amplitude scale per instruction).  So each
-// 64-wide K segment's products go into a fresh TMEM accumulator, and the
-// epilogue warps add every segment's result into FP32
+// (measured: ~2^-24 of the amplitude scale per instruction).  So each K
+// segment's products (seg_blocks<P>() blocks of 32 K) go into a fresh TMEM
+// accumulator, and the epilogue warps add every segment's result into FP32
 // registers with round-to-nearest (the promotion interval idea of, e.g.,
 // the DeepSeek-V3 report's FP8 GEMMs).  Two TMEM buffers alternate per
-// segment of 64 K, so the MMAs of segment s+1 overlap the promotion of s.
+// segment, so the MMAs of segment s+1 overlap the promotion of s.
 //
 // A tile is one 64-mode tile (128 A rows) times one 128-trajectory tile
 // (256 B rows).  Kernel structure (persistent over tiles, one CTA per SM,
@@ -32,11 +32,10 @@
 //               bytes), every plane loaded once per K block, into a
 //               multi-stage shared-memory ring;
 //   warp 1      allocates 512 TMEM columns; one thread issues
-//               tcgen05.mma M=128 N=256 K=16 into the segment's buffer: with
-//               6 products, per segment of two K blocks the correction
-//               products of both blocks first and A0 B0 last; with 3
-//               products, block by block as the stages land (A1 B0, A0 B1,
-//               A0 B0), releasing each stage at once;
+//               tcgen05.mma M=128 N=256 K=16 into the segment's buffer,
+//               block by block as the stages land, the correction products
+//               first and A0 B0 last (3 products: A1 B0, A0 B1, A0 B0),
+//               releasing each stage at once;
 //   warps 2..9  epilogue: warp w reads TMEM lanes 32 (w mod 4).. (its A rows)
 //               and half (w - 2) / 4 of the tile's trajectories: running
 //               sums of 64 alpha' and 64 beta' columns per thread (packed
@@ -190,6 +189,25 @@ static_assert(256 * kRegsEpi + (threads_of<2>() - 256) * regs_rest<2>() <=
 // end, lengthen the launch).
 constexpr int kSampWG = 1;
 constexpr int kSampWarpsUsed = 4 * kSampWG + 2;
+// K blocks (of 32) per accumulator promotion segment.  The tensor core
+// truncates each MMA's FP32 result, which shrinks the magnitude of the
+// accumulated value by about half an ulp for every MMA that lands on an
+// accumulator already at full magnitude; the promoted sums inherit that
+// relative bias (it is linear in the values), so n_S comes out low by a
+// factor 1 - 2c.  Issued block by block with the correction products first
+// and A0 B0 last, a segment of one K block has two such MMAs, one of two
+// blocks eight (the second block's corrections land on the first block's
+// A0 B0).  Measured on lossless networks (n_S = n exactly), (n - n_S) / n =
+// 2.5e-7 with 3 products and 2-block segments, 0.9e-7 with 1-block segments
+// (3 or 6 products), but 1-block segments make the 3-product GEMM 14 %
+// slower (twice the promotion work per MMA).  The 3-product split keeps
+// 2-block segments (its bias moves P(m) by about 0.1 sigma at the named
+// workloads' sizes); the 6-product split, the accuracy mode, promotes every
+// K block.
+template <int P>
+constexpr int seg_blocks() {
+    return P == 3 ? 2 : 1;
+}
 
 // A tile of the grouped GEMM: which network, which mode tile (of this CTA),
 // which 128-trajectory tile.
@@ -479,8 +497,10 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
     auto mma_issuer = [&]() {
         if (lane == 0 && leader) {
             // ---------------------------------------------------- MMA issuer
-            // Per segment (two K blocks): the correction products of both
-            // blocks first, then A0 B0 of both, into a fresh accumulator.
+            // Per promotion segment (seg_blocks<P>() K blocks) a fresh
+            // accumulator; each K block's products as soon as its stage
+            // lands, the correction products first and A0 B0 last, and the
+            // stage released right after.
             int stage = 0;
             uint32_t phase = 0;
             uint32_t seg = 0;  // segments issued so far (selects the TMEM buffer)
@@ -492,7 +512,8 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
             for (int tile = unit; ok && tile < ntiles; tile += nunits) {
                 const TileRef tr = decode_tile<kPair>(tile, nets, tiles, count0, band, rank);
                 const int KB = tr.d->KB;
-                const int nseg = (KB + 1) / 2;  // promotion segments of two 32-wide K blocks
+                constexpr int kSegBlocks = seg_blocks<P>();
+                const int nseg = (KB + kSegBlocks - 1) / kSegBlocks;
                 for (int sg = 0; ok && sg < nseg; ++sg, ++seg) {
                     const uint32_t b = seg & 1u;
                     // the epilogue warps of both CTAs have read this buffer
@@ -502,85 +523,44 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                         break;
                     }
                     ptx::tc_fence_after();
-                    const int nst = (2 * sg + 1 < KB) ? 2 : 1;
-                    if (P == 3) {
-                        // 3 products: each K block's MMAs as soon as its
-                        // stage lands (small products first within the
-                        // block), the stage released right after, so the
-                        // producer refills 3 stages ahead instead of 2
-                        const uint32_t d = tmem_base + b * 256u;
-                        uint32_t acc = 0u;
-                        for (int q = 0; q < nst; ++q) {
-                            if (!ptx::mbar_wait(ptx::smem_u32(&full[stage]), phase, err, wait_ns)) {
-                                ok = false;
-                                break;
-                            }
-                            ptx::tc_fence_after();
-                            // the stage's plane descriptors once; the second
-                            // K16 half is 32 bytes on (2 in the descriptor's
-                            // 16-byte address field, which cannot carry:
-                            // shared addresses stay below 2^18)
-                            const uint64_t dA[2] = {ptx::desc_k_sw64(ptx::smem_u32(a_tile(stage, 0))),
-                                                    ptx::desc_k_sw64(ptx::smem_u32(a_tile(stage, 1)))};
-                            const uint64_t dB[2] = {ptx::desc_k_sw64(ptx::smem_u32(b_tile(stage, 0))),
-                                                    ptx::desc_k_sw64(ptx::smem_u32(b_tile(stage, 1)))};
-#pragma unroll
-                            for (int pr = 0; pr < 3; ++pr) {
-#pragma unroll
-                                for (int kk = 0; kk < 2; ++kk) {
-                                    mma(d, dA[kIa3[pr]] + 2u * kk, dB[kIb3[pr]] + 2u * kk, acc);
-                                    acc = 1u;
-                                }
-                            }
-                            commit_both(&empty[stage]);
-                            if (++stage == kStages) {
-                                stage = 0;
-                                phase ^= 1u;
-                            }
-                        }
-                        if (!ok) break;
-                        commit_both(&tfull[b]);
-                        continue;
-                    }
-                    int stg[2];
-                    stg[0] = stage;
-                    stg[1] = (stage + 1 == kStages) ? 0 : stage + 1;
+                    const int nst = min(kSegBlocks, KB - sg * kSegBlocks);
+                    const uint32_t d = tmem_base + b * 256u;
+                    uint32_t acc = 0u;
                     for (int q = 0; q < nst; ++q) {
-                        // stage stg[q] has fill parity phase (q = 0) or, after a wrap, phase ^ 1
-                        const uint32_t par = (q == 1 && stg[1] == 0) ? (phase ^ 1u) : phase;
-                        if (!ptx::mbar_wait(ptx::smem_u32(&full[stg[q]]), par, err, wait_ns)) {
+                        if (!ptx::mbar_wait(ptx::smem_u32(&full[stage]), phase, err, wait_ns)) {
                             ok = false;
                             break;
                         }
-                    }
-                    if (!ok) break;
-                    ptx::tc_fence_after();
-                    const uint32_t d = tmem_base + b * 256u;
-                    uint32_t acc = 0u;
+                        ptx::tc_fence_after();
+                        // the stage's plane descriptors once; the second K16
+                        // half is 32 bytes on (2 in the descriptor's 16-byte
+                        // address field, which cannot carry: shared addresses
+                        // stay below 2^18)
+                        uint64_t dA[kPl], dB[kPl];
 #pragma unroll
-                    for (int pr = 0; pr < P; ++pr) {
-                        const int ia = (P == 3) ? kIa3[pr % 3] : kIa6[pr];
-                        const int ib = (P == 3) ? kIb3[pr % 3] : kIb6[pr];
-                        for (int q = 0; q < nst; ++q) {
-                            const uint32_t a0 = ptx::smem_u32(a_tile(stg[q], ia));
-                            const uint32_t b0 = ptx::smem_u32(b_tile(stg[q], ib));
+                        for (int pl = 0; pl < kPl; ++pl) {
+                            dA[pl] = ptx::desc_k_sw64(ptx::smem_u32(a_tile(stage, pl)));
+                            dB[pl] = ptx::desc_k_sw64(ptx::smem_u32(b_tile(stage, pl)));
+                        }
+#pragma unroll
+                        for (int pr = 0; pr < P; ++pr) {
+                            const int ia = (P == 3) ? kIa3[pr] : kIa6[pr];
+                            const int ib = (P == 3) ? kIb3[pr] : kIb6[pr];
 #pragma unroll
                             for (int kk = 0; kk < 2; ++kk) {
-                                mma(d, ptx::desc_k_sw64(a0 + kk * 32),
-                                    ptx::desc_k_sw64(b0 + kk * 32), acc);
+                                mma(d, dA[ia] + 2u * kk, dB[ib] + 2u * kk, acc);
                                 acc = 1u;
                             }
                         }
-                    }
-                    // the stage is free once the MMAs have read it
-                    for (int q = 0; q < nst; ++q) commit_both(&empty[stg[q]]);
-                    commit_both(&tfull[b]);
-                    for (int q = 0; q < nst; ++q) {
+                        // the stage is free once the MMAs have read it
+                        commit_both(&empty[stage]);
                         if (++stage == kStages) {
                             stage = 0;
                             phase ^= 1u;
                         }
                     }
+                    if (!ok) break;
+                    commit_both(&tfull[b]);
                 }
             }
             // drain: all MMAs issued by this thread have completed
@@ -605,7 +585,8 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
             const TileRef tr = decode_tile<kPair>(tile, nets, tiles, count0, band, rank);
             const int mt = tr.mt;
             const int st = tr.st;
-            const int nseg = (tr.d->KB + 1) / 2;
+            constexpr int kSegBlocks = seg_blocks<P>();
+            const int nseg = (tr.d->KB + kSegBlocks - 1) / kSegBlocks;
             float ra[64], rb[64];  // running alpha', beta' parts of this row
 #pragma unroll
             for (int i = 0; i < 64; ++i) {

@@ -149,11 +149,13 @@ def test_automatic_mode_folds_from_900_output_modes(gbs, stream):
 
 
 def test_next_calls_first_chunk_drawn_ahead(gbs, stream):
-    """The last GEMM of a folded gbs_sample draws the chunk a following call on
-    the same seed from first + E starts with; that call skips its own
-    sampler.  Sums equal the plain loop's bit for bit for a following call
-    that matches (same or smaller E), one that does not (other start), and
-    one after another entry point overwrote the operands."""
+    """A folded gbs_sample that continues the previous call (same seed,
+    first = its first + E) draws, in its last GEMM, the chunk a following
+    call from first + E starts with; that call skips its own sampler.  A call
+    that does not continue the previous one (the first call, another start)
+    draws nothing ahead.  Sums equal the plain loop's bit for bit for a
+    following call that matches (same or smaller E), one that does not (other
+    start), and one after another entry point overwrote the operands."""
     net_def = wl.small_network(40, 40, r=0.6, t2=0.9, seed=101)
     probe = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
     chunk = gbs.gbs_network_info(probe)[3]
@@ -179,6 +181,8 @@ def test_next_calls_first_chunk_drawn_ahead(gbs, stream):
     (a0, l0), (a2, l2) = res[0], res[2]
     assert np.array_equal(a0[3], a2[3])
     assert np.array_equal(a0[2].view(np.float64), a2[2].view(np.float64))
-    # sampler launches (the plain loop: one per chunk): the folded calls
-    # that follow a matching call draw nothing themselves
-    assert l2 == [1, 0, 0, 1, 1], l2
+    # sampler launches (the plain loop: one per chunk): the first call draws
+    # nothing ahead, the second (continuing it) draws the third call's first
+    # chunk, the fourth starts elsewhere, the last follows the fourth, which
+    # drew nothing ahead (it did not continue the third)
+    assert l2 == [1, 1, 0, 1, 1], l2
