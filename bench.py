@@ -44,12 +44,15 @@ UNIT = "samples/s"
 # run without an entry reports traffic null.
 GEMM_TRAFFIC_BYTES_PER_SAMPLE = {}
 
-# FP32-pipe lane operations per evaluated (trajectory, k) pair of the
-# double-float generating-function kernel (k_gf_df), from an ncu capture
-# (FP32 thread instructions, packed FP32x2 ones counted twice, divided by the
-# launch's in-window pairs from gbs_debug_windows); valid for the kernel
-# version of that capture only, else None.
-GF_FP32_OPS_PER_PAIR = None
+# FP32 lane-operation slots of the FMA pipe per evaluated (trajectory, k)
+# pair of the double-float generating-function kernel (k_gf_df): the FMA
+# pipe's active share (ncu sm__pipe_fma_cycles_active, 64.67 %) x elapsed SM
+# cycles (1.221e6) x 152 SMs x 128 FP32 lanes, divided by the launch's
+# in-window pairs (131072 trajectories x 326.4 pairs per trajectory, counted
+# by gbs_debug_windows): 359.  A packed FP32x2 instruction occupies two lane
+# slots.  Capture: m1000 chunk of 131072 trajectories
+# (profiles/k_gf_df_m1000.md); valid for that kernel version only.
+GF_FP32_OPS_PER_PAIR = 359.0
 
 
 def _env_int(name, default):
@@ -185,6 +188,23 @@ def reference_arm(args, wl_def):
     return 0
 
 
+def _network(wl_def, cache=None):
+    """The workload's network; large ones take their QR on the GPU.  With a
+    cache path, T is read from it when it exists and written to it
+    otherwise (profiling runs load T without the GPU linear-algebra
+    library)."""
+    import numpy as np
+    import workloads as wl
+    if cache and os.path.exists(cache):
+        T = np.load(cache)
+        return wl.Network(T=T, r=wl_def.squeezing(), t2=wl_def.t2,
+                          seed_s=wl.SEED_S_BASE + wl_def.index)
+    net = wl_def.network(device=wl_def.N >= 2000)
+    if cache:
+        np.save(cache, net.T)
+    return net
+
+
 def _window_pairs(w, K1):
     """Per trajectory, the k of the K1 roots of unity at which the
     generating-function kernel evaluates a term: cyclic distance to k = 0 at
@@ -256,7 +276,7 @@ def gbs_arm(args, wl_def):
     precision = args.precision or wl_def.precision
     stream = torch.cuda.Stream()
     sptr = stream.cuda_stream
-    netdef = wl_def.network(device=wl_def.N >= 2000)
+    netdef = _network(wl_def, args.t_cache)
     E, n_sub, K1 = wl_def.E, wl_def.n_sub, wl_def.K1
     if args.samples:
         E = args.samples
@@ -266,7 +286,7 @@ def gbs_arm(args, wl_def):
     if args.pair_autotune is not None:
         gbs.gbs_set_pair_autotune(bool(args.pair_autotune))
     if args.gemm_pair is not None and precision != "fp64":
-        gbs.gbs_set_gemm_config(net, args.gemm_pair, args.gemm_band)
+        gbs.gbs_set_gemm_config(net, args.gemm_pair, args.gemm_band, args.gemm_keep_a)
     out = torch.empty(4 * K1, dtype=torch.float64, device="cuda")
     seed = netdef.seed_s
     # rank r draws trajectories [r * R, (r + 1) * R) with R = (W + K + 2) * E
@@ -332,14 +352,14 @@ def gbs_arm(args, wl_def):
     if tc_path:
         achieved = flops / (gemm_ms / 1e3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-        pair, band = gbs.gbs_gemm_config(net)
+        pair, band, keep_a = gbs.gbs_gemm_config(net)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": f"{peak_kind} bf16 sustained (kernel timed inside a long step)",
                 "algorithmic_flops_per_sample": 8 * netdef.M * netdef.N,
                 "mma_products": P_products, "mma_issued_frac": P_products * achieved / peak,
                 "kernel": "k_gemm_tc", "launches": gemm_launches,
-                "gemm_config": {"cta_pair": pair == 2, "band": band},
+                "gemm_config": {"cta_pair": pair == 2, "band": band, "keep_a_in_l2": bool(keep_a)},
                 "avg_launch_ms": gemm_ms / max(gemm_launches, 1),
                 "sm_mhz_median": clk.get("sm_mhz"),
                 "achieved_at_max_clock": (achieved * clk["sm_max_mhz"] / clk["sm_mhz"]
@@ -482,7 +502,7 @@ def gbs_arm(args, wl_def):
             if args.sampler_fusion is not None:
                 gbs.gbs_set_sampler_fusion(n2, args.sampler_fusion)
             if args.gemm_pair is not None and precision != "fp64":
-                gbs.gbs_set_gemm_config(n2, args.gemm_pair, args.gemm_band)
+                gbs.gbs_set_gemm_config(n2, args.gemm_pair, args.gemm_band, args.gemm_keep_a)
             gbs.gbs_sample(n2, seed, base + s * E, E, n_sub, K1)
             res = gbs.gbs_binned_counts(n2, 0, K1)
             gbs.gbs_free_network(n2)
@@ -568,12 +588,16 @@ def batch_arm(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms_total = ev0.elapsed_time(ev1)
-    pair, rounds, tiles = gbs.gbs_batch_info(batch)
-    # kernels per step: per network and chunk a sampler, a finalize and a
-    # generating-function launch; one grouped GEMM per round; per network the
-    # inversion (prep, log2 K1 FFT passes, statistics)
+    (pair, band), rounds, tiles = gbs.gbs_batch_info(batch)
+    # kernels per step: per network and chunk a finalize and a sampler
+    # (networks of >= 900 output modes with more than one chunk: round 0
+    # only, the grouped GEMMs draw the rest); per round one grouped GEMM and
+    # one grouped generating-function launch; per network the inversion
+    # (prep, log2 K1 FFT passes, statistics)
     chunks = [-(-e // gbs.gbs_network_info(n)[3]) for e, n in zip(E, nets)]
-    launches_per_step = 3 * sum(chunks) + rounds + sum(int(math.log2(k)) + 2 for k in K1s)
+    samplers = [1 if (c > 1 and d.M >= 900) else c for c, d in zip(chunks, defs)]
+    launches_per_step = sum(chunks) + sum(samplers) + 2 * rounds + \
+        sum(int(math.log2(k)) + 2 for k in K1s)
     # kernel time of the grouped GEMM: extra steps with phase timing on (the
     # rounds are then issued one by one rather than as a graph)
     gbs.gbs_profile_enable(nets[0], True)
@@ -583,6 +607,7 @@ def batch_arm(args):
     prof = gbs.gbs_profile_read(nets[0])
     gbs.gbs_profile_enable(nets[0], False)
     gemm_ms = prof["gemm"][0] * args.steps / nprof
+    gf_ms = prof["gf"][0] * args.steps / nprof
     total = sum(E) * args.steps
     flops = sum(8.0 * d.M * d.N * e for d, e in zip(defs, E)) * args.steps
     peaks, peak_kind = _peaks()
@@ -596,7 +621,8 @@ def batch_arm(args):
         "config": {"workload": f"batch{len(wls)}: {len(wls)} Haar networks, N=M log-uniform "
                                "[100,2000], r_j~U[0.5,1.5], t~U[0.5,0.995], E=2^18 each",
                    "N": [d.N for d in defs], "K1": K1s, "n_sub": n_sub[0],
-                   "samples_per_step": sum(E), "gemm_cta_pair_chosen": pair == 2, "rounds": rounds,
+                   "samples_per_step": sum(E), "gemm_config_chosen": {"cta_pair": pair == 2, "band": band},
+                   "rounds": rounds,
                    "gemm_tiles_per_call": tiles,
                    "note": "one CUDA graph per gbs_sample_batch call; GEMM kernel time from "
                            "2 further steps issued without the graph under phase timing"},
@@ -605,6 +631,10 @@ def batch_arm(args):
                      "peak_source": f"{peak_kind} bf16 sustained",
                      "mma_issued_frac": 3 * achieved / peak, "kernel": "k_gemm_tc (grouped)",
                      "gemm_ms_per_step": gemm_ms / args.steps},
+        "phases": {"gemm": {"ms_per_step": gemm_ms / args.steps},
+                   "gf": {"ms_per_step": gf_ms / args.steps,
+                          "note": "one grouped generating-function launch per round over all "
+                                  "networks' chunks"}},
         "gpu_launches": launches_per_step * args.steps, "clocks": clk,
     }
     gbs.gbs_free_batch(batch)
@@ -1075,12 +1105,16 @@ def main():
                          "autotuned (the default)")
     ap.add_argument("--gemm-band", type=int, default=0,
                     help="gbs_set_gemm_config band (with --gemm-pair 1 or 2)")
+    ap.add_argument("--gemm-keep-a", type=int, choices=[0, 1], default=0,
+                    help="gbs_set_gemm_config keep_a (with --gemm-pair 1 or 2)")
     ap.add_argument("--pair-autotune", type=int, choices=[0, 1], default=None,
                     help="gbs_set_pair_autotune before the run")
     ap.add_argument("--sampler-fusion", type=int, choices=[0, 1, 2], default=None,
                     help="gbs_set_sampler_fusion mode of the timed network (default: the "
                          "library's, 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--t-cache", default=None,
+                    help="read T from this .npy file if it exists, else write it there")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -354,19 +354,24 @@ int gbs_network_info(gbs_net_t net, int *N, int *M, int *precision, int64_t *chu
  * trajectory tile side by side); band > 0: in bands of `band` mode-tile
  * groups (a group = the 1 or 2 mode tiles of a CTA or pair), the trajectory
  * tiles of a band in order, so that a band's A tiles are read again from L2.
- * pair = 0 returns to the autotuner, which times the candidates on the
- * network's first chunk and keeps the fastest (cached per size bucket of N
- * and M for the process).  gbs_gemm_config returns the configuration in use
- * ((0, 0) before the first chunk).  EINVAL: FP64 network, pair not 0..2,
- * band < 0, NULL pointers.
+ * keep_a = 1 (with band > 0): the band's A tiles are loaded with the
+ * evict-last L2 policy.  pair = 0 returns to the autotuner, which times the
+ * candidates (one CTA or pairs; bands of 16 and 8 with and without keep_a;
+ * the plain order only where all of A fits in half the L2) on the first
+ * chunk of each kind of launch (plain, and the one that also samples the
+ * next chunk) in a loaded, interleaved sequence and keeps the fastest
+ * (cached per size bucket of N and M for the process).  gbs_gemm_config
+ * returns the configuration in use ((0, 0, 0) before the first chunk).
+ * EINVAL: FP64 network, pair not 0..2, band < 0, keep_a not 0 or 1, NULL
+ * pointers.
  */
-int gbs_set_gemm_config(gbs_net_t net, int pair, int band);
-int gbs_gemm_config(gbs_net_t net, int *pair, int *band);
+int gbs_set_gemm_config(gbs_net_t net, int pair, int band, int keep_a);
+int gbs_gemm_config(gbs_net_t net, int *pair, int *band, int *keep_a);
 
 /*
  * gbs_set_pair_autotune -- whether the GEMM autotuner (and the batch's) also
- * times CTA pairs; process-wide, clears the autotuner's cache.  Networks
- * already configured keep their configuration.
+ * times CTA pairs (on by default); process-wide, clears the autotuner's
+ * cache.  Networks already configured keep their configuration.
  */
 int gbs_set_pair_autotune(int enable);
 
@@ -415,9 +420,8 @@ int gbs_sampler_fusion(gbs_net_t net, int *active);
  * decreasing K), then each network's generating-function sums.  All rounds
  * of a call are captured into one CUDA graph and launched once (on the
  * legacy default stream, which cannot be captured, they are issued
- * directly).  The batch GEMM's tile configuration (one CTA per tile, or CTA
- * pairs where the autotuner takes them) is chosen by timing the candidates
- * on the first call's first round.
+ * directly).  The batch GEMM's tile configuration is chosen by timing the
+ * candidates on the first call's first round (gbs_set_batch_config).
  *
  * gbs_make_batch -- group `count` networks (1..4096) that share a BF16
  *   precision, a device and a stream.  The networks stay owned by the
@@ -426,8 +430,15 @@ int gbs_sampler_fusion(gbs_net_t net, int *active);
  *   first_sample[i], E[i], n_sub[i], K1[i] (host arrays of `count`).  The
  *   same trajectories as per-network gbs_sample calls are drawn.
  *   Synchronises the stream before capturing (descriptor upload).
- * gbs_batch_info -- GEMM tile configuration chosen (pair = 1 or 2), rounds and
- *   GEMM tiles of the last call.
+ * gbs_set_batch_config -- the batch GEMM's configuration: pair 1 (one CTA
+ *   per tile) or 2 (CTA pairs), band 0 (every network's tiles in the plain
+ *   order) or > 0 (bands of that many mode-tile groups within each
+ *   network); pair 0 returns to the autotuner, which times one CTA per tile
+ *   and CTA pairs (gbs_set_pair_autotune), each with bands 0 and 8, on the
+ *   first call's first round.  Every configuration gives bitwise the same
+ *   sums.  EINVAL: pair not 0..2, band < 0.
+ * gbs_batch_info -- GEMM configuration in use (pair, band; 0, 0 before the
+ *   first call), rounds and GEMM tiles of the last call.
  * With phase timing enabled on the batch's first network (gbs_profile_enable),
  * gbs_sample_batch issues its rounds directly instead of as a graph and
  * attributes the grouped GEMM launches to that network's GEMM phase.
@@ -437,7 +448,8 @@ typedef struct gbs_batch *gbs_batch_t;
 int gbs_make_batch(gbs_net_t *nets, int count, gbs_batch_t *out);
 int gbs_sample_batch(gbs_batch_t batch, const uint64_t *seeds, const uint64_t *first_sample,
                      const int64_t *E, const int *n_sub, const int *K1);
-int gbs_batch_info(gbs_batch_t batch, int *pair, int *rounds, int64_t *tiles);
+int gbs_set_batch_config(gbs_batch_t batch, int pair, int band);
+int gbs_batch_info(gbs_batch_t batch, int *pair, int *band, int *rounds, int64_t *tiles);
 void gbs_free_batch(gbs_batch_t batch);
 
 /*
@@ -463,12 +475,17 @@ int gbs_profile_read(gbs_net_t net, double *ms, int64_t *launches);
 
 /*
  * gbs_measure_fp64_rate -- instrumentation, not part of the method: the
- * device's FP64 fused multiply-add rate in TFLOP/s (2 FLOP per FMA), from a
- * kernel of independent FMA chains on every SM timed with CUDA events on
- * `stream` (best of 3 after a warm-up launch).  It is the peak against which
- * the FP64 path's propagation (k_gemm_fp64, bound by that rate) is reported.
- * Allocates a small output buffer (stream-ordered) and synchronises.
- * Errors: EINVAL (NULL tflops), ECUDA.
+ * device's FP64 fused multiply-add peak in TFLOP/s (2 FLOP per FMA) at its
+ * maximum SM clock.  A kernel of independent FMA chains (outer-product
+ * updates into 8, 16 or 32 accumulators per thread, 2 to 8 blocks of 256
+ * threads per SM) counts the FMAs each SM completes per cycle of its own
+ * clock (clock64 from its first block's start to its last block's end), so
+ * the figure does not depend on the clock the probe ran at; the mean over
+ * SMs, the best over those configurations (3 launches each
+ * after a warm-up launch), times the SM count and the maximum clock.  It is
+ * the peak against which the FP64 path's propagation (k_gemm_fp64, bound by
+ * that rate) is reported.  Allocates small buffers (stream-ordered) and
+ * synchronises `stream`.  Errors: EINVAL (NULL tflops), ECUDA.
  */
 int gbs_measure_fp64_rate(void *stream, double *tflops);
 

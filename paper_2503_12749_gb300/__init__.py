@@ -83,7 +83,7 @@ def lib():
         L.gbs_network_info.argtypes = [vp, ip, ip, ip, i64p]
         L.gbs_binned_counts_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int64, vp, vp]
-        L.gbs_set_gemm_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.gbs_set_gemm_config.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.gbs_set_pair_autotune.argtypes = [ctypes.c_int]
         L.gbs_set_wait_limit.argtypes = [vp, ctypes.c_uint64]
         L.gbs_measure_fp64_rate.argtypes = [vp, dp]
@@ -104,13 +104,14 @@ def lib():
         L.gbs_sample_2d.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.gbs_binned_counts_2d.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp]
-        L.gbs_gemm_config.argtypes = [vp, ip, ip]
+        L.gbs_gemm_config.argtypes = [vp, ip, ip, ip]
         L.gbs_set_sampler_fusion.argtypes = [vp, ctypes.c_int]
         L.gbs_sampler_fusion.argtypes = [vp, ip]
         L.gbs_make_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
         L.gbs_sample_batch.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64),
                                        ctypes.POINTER(ctypes.c_uint64), i64p, ip, ip]
-        L.gbs_batch_info.argtypes = [vp, ip, ip, i64p]
+        L.gbs_batch_info.argtypes = [vp, ip, ip, ip, i64p]
+        L.gbs_set_batch_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.gbs_free_batch.argtypes = [vp]
         L.gbs_free_batch.restype = None
         L.gbs_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -145,7 +146,7 @@ def lib():
                      "gbs_set_pair_autotune", "gbs_set_wait_limit", "gbs_measure_fp64_rate",
                      "gbs_debug_windows",
                      "gbs_set_sampler_fusion", "gbs_sampler_fusion",
-                     "gbs_make_batch", "gbs_sample_batch", "gbs_batch_info",
+                     "gbs_make_batch", "gbs_sample_batch", "gbs_batch_info", "gbs_set_batch_config",
                      "gbs_make_network_device", "gbs_make_network_binned", "gbs_sample_2d",
                      "gbs_binned_counts_2d", "gbs_sample_nd", "gbs_binned_counts_nd",
                      "gbs_histogram", "gbs_moments",
@@ -394,19 +395,21 @@ def gbs_network_info(net: Network):
     return N.value, M.value, p.value, c.value
 
 
-def gbs_set_gemm_config(net: Network, pair: int, band: int = 0) -> None:
+def gbs_set_gemm_config(net: Network, pair: int, band: int = 0, keep_a: int = 0) -> None:
     """Tile configuration of the tcgen05 GEMM: pair 1 (one CTA per tile) or 2
     (CTA pairs), band = mode-tile groups per band of the tile order (0: plain
-    order); pair 0 = autotune."""
-    _check(lib().gbs_set_gemm_config(net.handle, int(pair), int(band)))
+    order), keep_a = 1: a band's A tiles with the evict-last L2 policy; pair
+    0 = autotune."""
+    _check(lib().gbs_set_gemm_config(net.handle, int(pair), int(band), int(keep_a)))
 
 
 def gbs_gemm_config(net: Network):
-    """(pair, band) in use; (0, 0) before the first chunk."""
+    """(pair, band, keep_a) in use; (0, 0, 0) before the first chunk."""
     p = ctypes.c_int()
     b = ctypes.c_int()
-    _check(lib().gbs_gemm_config(net.handle, ctypes.byref(p), ctypes.byref(b)))
-    return p.value, b.value
+    k = ctypes.c_int()
+    _check(lib().gbs_gemm_config(net.handle, ctypes.byref(p), ctypes.byref(b), ctypes.byref(k)))
+    return p.value, b.value, k.value
 
 
 def gbs_set_pair_autotune(enable: bool) -> None:
@@ -472,14 +475,21 @@ def gbs_sample_batch(batch: Batch, seeds, first_sample, E, n_sub, K1) -> None:
                                   i32(*[int(x) for x in K1])))
 
 
+def gbs_set_batch_config(batch: Batch, pair: int, band: int = 0) -> None:
+    """The batch GEMM's configuration (pair 1 or 2, band >= 0); pair 0 = autotune."""
+    _check(lib().gbs_set_batch_config(batch.handle, int(pair), int(band)))
+
+
 def gbs_batch_info(batch: Batch):
-    """(GEMM tile configuration chosen: pair 1 or 2, rounds, GEMM tiles) of the last
+    """((pair, band) of the batch GEMM, rounds, GEMM tiles) of the last
     gbs_sample_batch."""
     c = ctypes.c_int()
+    b = ctypes.c_int()
     r = ctypes.c_int()
     t = ctypes.c_int64()
-    _check(lib().gbs_batch_info(batch.handle, ctypes.byref(c), ctypes.byref(r), ctypes.byref(t)))
-    return c.value, r.value, t.value
+    _check(lib().gbs_batch_info(batch.handle, ctypes.byref(c), ctypes.byref(b), ctypes.byref(r),
+                                ctypes.byref(t)))
+    return (c.value, b.value), r.value, t.value
 
 
 def gbs_free_batch(batch: Batch) -> None:

@@ -1239,11 +1239,15 @@ int gbs_network_info(gbs_net_t net, int *N, int *M, int *precision, int64_t *chu
     return GBS_OK;
 }
 
-int gbs_set_gemm_config(gbs_net_t net, int pair, int band) {
+int gbs_set_gemm_config(gbs_net_t net, int pair, int band, int keep_a) {
     int rc;
     if ((rc = validate_net(net))) return rc;
     if (net->precision == GBS_FP64) return set_error(GBS_EINVAL, "the FP64 path has no tcgen05 GEMM");
-    return tc_set_config(net, pair, band);
+    GemmCfg c;
+    c.pair = pair;
+    c.band = band;
+    c.keep = keep_a;
+    return tc_set_config(net, c);
 }
 
 int gbs_set_pair_autotune(int enable) {
@@ -1274,11 +1278,14 @@ int gbs_sampler_fusion(gbs_net_t net, int *active) {
     return GBS_OK;
 }
 
-int gbs_gemm_config(gbs_net_t net, int *pair, int *band) {
+int gbs_gemm_config(gbs_net_t net, int *pair, int *band, int *keep_a) {
     int rc;
     if ((rc = validate_net(net))) return rc;
-    if (!pair || !band) return set_error(GBS_EINVAL, "NULL argument");
-    tc_get_config(net, pair, band);
+    if (!pair || !band || !keep_a) return set_error(GBS_EINVAL, "NULL argument");
+    const GemmCfg c = tc_get_config(net);
+    *pair = c.pair;
+    *band = c.band;
+    *keep_a = c.keep;
     return GBS_OK;
 }
 

@@ -37,6 +37,8 @@ struct gbs_batch {
     cudaStream_t stream = nullptr;
     int P = 0;
     int pair = 0;     // GEMM tiles per CTA (1) or per CTA pair (2); 0 = not tuned yet
+    int band = 0;     // tile order within a network: 0 plain, > 0 bands of that many groups
+    bool forced = false;  // set by gbs_set_batch_config
     int sm_count = 0;
     // device copies of the per-round descriptors and tile lists
     gbs::GemmNetDesc *d_desc = nullptr;
@@ -47,6 +49,12 @@ struct gbs_batch {
     gbs::SampleJob *d_jobs = nullptr;
     int64_t *d_prefix = nullptr;
     size_t jobs_cap = 0, prefix_cap = 0;
+    // generating-function work of the rounds: per round its chunks (one per
+    // network with trajectories in the round) and one work list
+    gbs::GfChunk *d_gfc = nullptr;
+    int4 *d_gfwork = nullptr;
+    int *d_gfnext = nullptr;  // the grouped launch's work counter
+    size_t gfc_cap = 0, gfwork_cap = 0;
     int last_rounds = 0;
     int64_t last_tiles = 0;
     bool last_fold = false;
@@ -71,9 +79,17 @@ struct RoundPlan {
     std::vector<SampleJob> jobs;    // [rounds][nets] (round 0 unused)
     std::vector<int64_t> prefix;    // [rounds][nets + 1]
     std::vector<int64_t> step;      // [nets]: trajectories per round (chunk_step)
+    // one grouped generating-function launch per round: the round's chunks
+    // and the work items {chunk, sub-ensemble, slot block}, slot block
+    // levels outermost (every chunk's centre blocks, the heaviest, first),
+    // within a level the chunks in order of decreasing trajectories
+    std::vector<GfChunk> gfc;       // all rounds, concatenated
+    std::vector<int> gfc_off;       // [rounds + 1]
+    std::vector<int4> gfwork;       // all rounds, concatenated (x = index within the round)
+    std::vector<int> gfwork_off;    // [rounds + 1]
 };
 
-int build_rounds(gbs_batch *b, const int64_t *E, int pair, RoundPlan &rp,
+int build_rounds(gbs_batch *b, const int64_t *E, int pair, int band, RoundPlan &rp,
                  const std::vector<char> *fold_net = nullptr, const uint64_t *seeds = nullptr,
                  const uint64_t *first = nullptr) {
     const int nn = (int)b->nets.size();
@@ -116,11 +132,44 @@ int build_rounds(gbs_batch *b, const int64_t *E, int pair, RoundPlan &rp,
             const int i = order[oi];
             const GemmNetDesc &d = rp.desc[(size_t)r * nn + i];
             const int groups = (d.mtiles + pair - 1) / pair;
-            for (int st = 0; st < d.stiles; ++st)
-                for (int g = 0; g < groups; ++g) rp.tiles.push_back(make_int4(i, g, st, 0));
+            // plain: every group of one trajectory tile side by side; banded:
+            // bands of `band` groups, the trajectory tiles of a band in order
+            const int bw = (band > 0 && band < groups) ? band : groups;
+            for (int g0 = 0; g0 < groups; g0 += bw)
+                for (int st = 0; st < d.stiles; ++st)
+                    for (int g = g0; g < std::min(groups, g0 + bw); ++g)
+                        rp.tiles.push_back(make_int4(i, g, st, 0));
         }
     }
     rp.tile_off[rounds] = (int)rp.tiles.size();
+    // generating-function work of every round
+    rp.gfc.clear();
+    rp.gfwork.clear();
+    rp.gfc_off.assign(rounds + 1, 0);
+    rp.gfwork_off.assign(rounds + 1, 0);
+    for (int r = 0; r < rounds; ++r) {
+        rp.gfc_off[r] = (int)rp.gfc.size();
+        rp.gfwork_off[r] = (int)rp.gfwork.size();
+        std::vector<int> idx;  // networks with trajectories in this round
+        for (int i = 0; i < nn; ++i)
+            if (rp.count[r][i] > 0) idx.push_back(i);
+        std::stable_sort(idx.begin(), idx.end(),
+                         [&](int a, int c) { return rp.count[r][a] > rp.count[r][c]; });
+        int ymax = 0;
+        for (int i : idx) {
+            const uint64_t e0 = first ? first[i] + (uint64_t)r * (uint64_t)step[i] : 0;
+            rp.gfc.push_back(gf_chunk(b->nets[i], e0, rp.count[r][i]));
+            ymax = std::max(ymax, gf_slot_blocks(b->nets[i]->K1));
+        }
+        for (int y = 0; y < ymax; ++y)
+            for (size_t j = 0; j < idx.size(); ++j) {
+                const gbs_net *net = b->nets[idx[j]];
+                if (y >= gf_slot_blocks(net->K1)) continue;
+                for (int q = 0; q < net->n_sub; ++q) rp.gfwork.push_back(make_int4((int)j, q, y, 0));
+            }
+    }
+    rp.gfc_off[rounds] = (int)rp.gfc.size();
+    rp.gfwork_off[rounds] = (int)rp.gfwork.size();
     rp.fold_net.assign(nn, 0);
     rp.fold = false;
     for (int i = 0; fold_net && i < nn; ++i) {
@@ -180,7 +229,26 @@ int upload_rounds(gbs_batch *b, const RoundPlan &rp) {
             b->prefix_cap = rp.prefix.size();
         }
     }
+    if (rp.gfc.size() > b->gfc_cap) {
+        if (b->d_gfc) cudaFree(b->d_gfc);
+        b->d_gfc = nullptr;
+        GBS_CUDA_TRY(cudaMalloc(&b->d_gfc, rp.gfc.size() * sizeof(GfChunk)));
+        b->gfc_cap = rp.gfc.size();
+    }
+    if (!b->d_gfnext) GBS_CUDA_TRY(cudaMalloc(&b->d_gfnext, sizeof(int)));
+    if (rp.gfwork.size() > b->gfwork_cap) {
+        if (b->d_gfwork) cudaFree(b->d_gfwork);
+        b->d_gfwork = nullptr;
+        GBS_CUDA_TRY(cudaMalloc(&b->d_gfwork, rp.gfwork.size() * sizeof(int4)));
+        b->gfwork_cap = rp.gfwork.size();
+    }
     GBS_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    if (!rp.gfc.empty())
+        GBS_CUDA_TRY(cudaMemcpy(b->d_gfc, rp.gfc.data(), rp.gfc.size() * sizeof(GfChunk),
+                                cudaMemcpyHostToDevice));
+    if (!rp.gfwork.empty())
+        GBS_CUDA_TRY(cudaMemcpy(b->d_gfwork, rp.gfwork.data(), rp.gfwork.size() * sizeof(int4),
+                                cudaMemcpyHostToDevice));
     GBS_CUDA_TRY(cudaMemcpy(b->d_desc, rp.desc.data(), nd * sizeof(GemmNetDesc),
                             cudaMemcpyHostToDevice));
     if (!rp.tiles.empty())
@@ -211,7 +279,7 @@ int round_gemm(gbs_batch *b, const RoundPlan &rp, int r, int pair) {
                                           b->d_desc + (size_t)r * nn, b->d_tiles + off, nt,
                                           n0->d_flags + 1, sj);
     } else {
-        rc = launch_gemm_grouped(b->stream, b->sm_count, b->P, pair, 0, n0->wait_ns,
+        rc = launch_gemm_grouped(b->stream, b->sm_count, b->P, pair, 0, 0, n0->wait_ns,
                                  b->d_desc + (size_t)r * nn, b->d_tiles + off, nt, 0,
                                  n0->d_flags + 1);
     }
@@ -258,14 +326,20 @@ int round_front(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *seeds,
     });
 }
 
-int round_back(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *first,
-               bool branches = false) {
-    return per_network(b, rp, r, branches, [&](int i, gbs_net *net) {
-        const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)rp.step[i];
-        int rc;
-        if ((rc = launch_finalize(net, rp.count[r][i]))) return rc;
-        return launch_gf(net, e0, rp.count[r][i]);
+// Every network's finalize (per-network branches), then ONE generating-
+// function launch over all of the round's chunks.
+int round_back(gbs_batch *b, const RoundPlan &rp, int r, bool branches = false) {
+    int rc = per_network(b, rp, r, branches, [&](int i, gbs_net *net) {
+        return launch_finalize(net, rp.count[r][i]);
     });
+    if (rc) return rc;
+    gbs_net *n0 = b->nets[0];
+    prof_mark(n0, GBS_PHASE_GF, 0, true);
+    rc = launch_gf_grouped(b->stream, b->sm_count, b->d_gfc + rp.gfc_off[r],
+                           b->d_gfwork + rp.gfwork_off[r], rp.gfwork_off[r + 1] - rp.gfwork_off[r],
+                           b->d_gfnext);
+    if (!rc) prof_mark(n0, GBS_PHASE_GF, 1, false);
+    return rc;
 }
 
 // Folded rounds: the networks' operands swap roles after each round, so that
@@ -283,7 +357,7 @@ int run_rounds(gbs_batch *b, const RoundPlan &rp, const uint64_t *seeds, const u
     for (int r = 0; r < rp.rounds && rc == GBS_OK; ++r) {
         if ((rc = round_front(b, rp, r, seeds, first, branches))) break;
         if ((rc = round_gemm(b, rp, r, b->pair))) break;
-        if ((rc = round_back(b, rp, r, first, branches))) break;
+        if ((rc = round_back(b, rp, r, branches))) break;
         if (rp.fold) {
             swap_all(b, rp);
             ++swaps;
@@ -293,41 +367,59 @@ int run_rounds(gbs_batch *b, const RoundPlan &rp, const uint64_t *seeds, const u
     return rc;
 }
 
-// Time the tile configurations (one CTA per tile; CTA pairs where the
-// autotuner takes them) on round 0 (samplers of round 0 run first so the
-// operands are real) and keep the fastest.
+// The batch GEMM's candidate configurations: one CTA per tile or CTA pairs
+// (where the autotuner takes pairs), each with the plain tile order and
+// bands of 8 groups within every network.
+std::vector<std::pair<int, int>> batch_candidates() {
+    std::vector<std::pair<int, int>> c;
+    for (int pair = 1; pair <= (tc_pair_autotune() ? 2 : 1); ++pair)
+        for (int band : {0, 8}) c.push_back({pair, band});
+    return c;
+}
+
+// Time the candidates on round 0 (the samplers of round 0 run first so the
+// operands are real) and keep the fastest; as the single-network autotuner:
+// a first pass launches each candidate once, then two passes time two
+// launches of each, candidates interleaved, times summed.  Every candidate
+// gives bitwise the same sums.
 int tune_batch(gbs_batch *b, const int64_t *E, const uint64_t *seeds, const uint64_t *first) {
+    const std::vector<std::pair<int, int>> cand = batch_candidates();
+    std::vector<RoundPlan> plans(cand.size());
+    std::vector<float> total(cand.size(), 0.0f);
     int rc = GBS_OK;
-    float best = 0.0f;
-    int best_pair = 1;
     cudaEvent_t e0, e1;
     GBS_CUDA_TRY(cudaEventCreate(&e0));
     GBS_CUDA_TRY(cudaEventCreate(&e1));
-    const int npair = tc_pair_autotune() ? 2 : 1;
-    for (int pair = 1; pair <= npair; ++pair) {
-        RoundPlan rp;
-        if ((rc = build_rounds(b, E, pair, rp))) break;
-        if ((rc = upload_rounds(b, rp))) break;
-        if ((rc = round_front(b, rp, 0, seeds, first))) break;
-        if ((rc = round_gemm(b, rp, 0, pair))) break;  // warm-up
-        cudaEventRecord(e0, b->stream);
-        if ((rc = round_gemm(b, rp, 0, pair))) break;
-        cudaEventRecord(e1, b->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            rc = set_error(GBS_ECUDA, "batch autotuner timing failed");
-            break;
-        }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (pair == 1 || ms < best) {
-            best = ms;
-            best_pair = pair;
+    for (size_t c = 0; c < cand.size() && rc == GBS_OK; ++c)
+        rc = build_rounds(b, E, cand[c].first, cand[c].second, plans[c]);
+    // round 0's operands (the samplers do not depend on the tile list)
+    if (rc == GBS_OK && (rc = upload_rounds(b, plans[0])) == GBS_OK)
+        rc = round_front(b, plans[0], 0, seeds, first);
+    for (int pass = 0; pass <= 2 && rc == GBS_OK; ++pass) {
+        for (size_t c = 0; c < cand.size() && rc == GBS_OK; ++c) {
+            if ((rc = upload_rounds(b, plans[c]))) break;
+            const int reps = pass == 0 ? 1 : 2;
+            cudaEventRecord(e0, b->stream);
+            for (int q = 0; q < reps && rc == GBS_OK; ++q) rc = round_gemm(b, plans[c], 0, cand[c].first);
+            if (rc) break;
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = set_error(GBS_ECUDA, "batch autotuner timing failed");
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (pass > 0) total[c] += ms;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    b->pair = best_pair;
+    size_t best = 0;
+    for (size_t c = 1; c < cand.size(); ++c)
+        if (total[c] < total[best]) best = c;
+    b->pair = cand[best].first;
+    b->band = cand[best].second;
     return GBS_OK;
 }
 
@@ -403,7 +495,7 @@ int gbs_sample_batch(gbs_batch_t b, const uint64_t *seeds, const uint64_t *first
         fold = fold || fold_net[i];
     }
     RoundPlan rp;
-    if ((rc = build_rounds(b, E, b->pair, rp, &fold_net, seeds, first_sample))) return rc;
+    if ((rc = build_rounds(b, E, b->pair, b->band, rp, &fold_net, seeds, first_sample))) return rc;
     if ((rc = upload_rounds(b, rp))) return rc;
     b->last_rounds = rp.rounds;
     b->last_tiles = (int64_t)rp.tiles.size();
@@ -443,9 +535,20 @@ int gbs_sample_batch(gbs_batch_t b, const uint64_t *seeds, const uint64_t *first
     return GBS_OK;
 }
 
-int gbs_batch_info(gbs_batch_t b, int *pair, int *rounds, int64_t *tiles) {
+int gbs_set_batch_config(gbs_batch_t b, int pair, int band) {
+    if (!b) return set_error(GBS_EINVAL, "null batch");
+    if (pair < 0 || pair > 2) return set_error(GBS_EINVAL, "pair must be 0 (auto), 1 or 2");
+    if (band < 0) return set_error(GBS_EINVAL, "band must be >= 0");
+    b->pair = pair;
+    b->band = pair ? band : 0;
+    b->forced = pair != 0;
+    return GBS_OK;
+}
+
+int gbs_batch_info(gbs_batch_t b, int *pair, int *band, int *rounds, int64_t *tiles) {
     if (!b) return set_error(GBS_EINVAL, "null batch");
     if (pair) *pair = b->pair;
+    if (band) *band = b->band;
     if (rounds) *rounds = b->last_rounds;
     if (tiles) *tiles = b->last_tiles;
     return GBS_OK;
@@ -458,6 +561,9 @@ void gbs_free_batch(gbs_batch_t b) {
     if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->d_jobs) cudaFree(b->d_jobs);
     if (b->d_prefix) cudaFree(b->d_prefix);
+    if (b->d_gfc) cudaFree(b->d_gfc);
+    if (b->d_gfwork) cudaFree(b->d_gfwork);
+    if (b->d_gfnext) cudaFree(b->d_gfnext);
     for (cudaStream_t st : b->aux) cudaStreamDestroy(st);
     for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);

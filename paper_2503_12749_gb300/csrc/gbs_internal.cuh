@@ -275,20 +275,26 @@ bool tc_sampling_ready(gbs_net *net, bool allocate);
 void tc_swap_sample_buffers(gbs_net *net);
 // GEMM configuration: pair = 1 (one CTA per tile) or 2 (CTA pairs,
 // cta_group::2), band = mode-tile groups per band of the tile order (0: plain
-// order); tc_set_config(net, 0, 0) returns to the autotuner.
-int tc_set_config(gbs_net *net, int pair, int band);
-void tc_get_config(gbs_net *net, int *pair, int *band);
+// order), keep = 1: a band's A tiles loaded with the evict-last L2 policy;
+// pair 0 returns to the autotuner.
+struct GemmCfg {
+    int pair = 0;
+    int band = 0;
+    int keep = 0;
+};
+int tc_set_config(gbs_net *net, const GemmCfg &cfg);
+GemmCfg tc_get_config(gbs_net *net);
 // Whether the autotuner also times CTA pairs (process-wide; clears its cache).
 void tc_set_pair_autotune(bool on);
 bool tc_pair_autotune();
-int tc_autotune(gbs_net *net, int64_t count, int *pair, int *band);
+
 int tc_products(gbs_net *net);
 int tc_fill_desc(gbs_net *net, GemmNetDesc *out, bool alt = false);  // alt: the second operand's maps
 // One launch over the tiles of many networks (d_tiles: {net, mode-tile group,
 // trajectory tile} per entry; NULL = closed-form tiles of d_nets[0] with
 // count0 trajectories in bands of `band` groups); wait_ns bounds every
 // pipeline wait of the kernel.
-int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int pair, int band,
+int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int pair, int band, int keep_a,
                         uint64_t wait_ns, const GemmNetDesc *d_nets, const int4 *d_tiles,
                         int ntiles, int64_t count0, unsigned long long *err,
                         OccOut occ = OccOut());
@@ -302,6 +308,26 @@ int launch_finalize(gbs_net *net, int64_t count);
 
 // Generating functions, summed per sub-ensemble into d_acc.
 int launch_gf(gbs_net *net, uint64_t e0, int64_t count);
+// One chunk's generating-function work (double-float kernel) for a grouped
+// launch over many networks.
+struct GfChunk {
+    const void *rec;  // the finalize kernel's per-trajectory records
+    const int *wmax;
+    int64_t count;
+    uint64_t e0;
+    int n_sub, K1;
+    const double2 *tw;
+    double2 *acc;
+    int64_t *counts;
+};
+GfChunk gf_chunk(gbs_net *net, uint64_t e0, int64_t count);
+// Slot blocks a chunk of a network with K1 points may need (the launch's
+// blocks past the chunk's union window return at once).
+int gf_slot_blocks(int K1);
+// One persistent launch over work items {chunk index, sub-ensemble, slot
+// block}, taken in list order through the counter at d_next (zeroed here).
+int launch_gf_grouped(cudaStream_t stream, int sm_count, const GfChunk *d_chunks,
+                      const int4 *d_work, int nwork, int *d_next);
 // Bytes per trajectory of the records the finalize kernel writes for the
 // double-float generating functions (d_gfrec).
 size_t gf_record_bytes();

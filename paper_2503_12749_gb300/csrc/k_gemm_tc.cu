@@ -101,8 +101,9 @@ struct TcPlan {
     GemmNetDesc desc_alt;           // the same over the second sample operand
     GemmNetDesc *d_desc_alt = nullptr;
     int P = 0;
-    int pair = 0;                   // 1: a CTA per tile, 2: CTA pairs; 0 = pick by the autotuner
-    int band = 0;                   // groups per band of the tile order (0: plain order)
+    // tile configuration of the plain launches ([0]) and of the launches
+    // that also sample the next chunk ([1]); pair 0 = pick by the autotuner
+    GemmCfg cfg[2];
     bool forced = false;            // set by gbs_set_gemm_config
 };
 
@@ -314,8 +315,8 @@ __device__ __forceinline__ void warp_transpose_reduce32(float (&v)[32], int lane
 template <int P, int kPair, int kSW>
 __global__ void __launch_bounds__(threads_of<kSW>(), 1)
     k_gemm_tc(const GemmNetDesc *__restrict__ nets, const int4 *__restrict__ tiles, int ntiles,
-              int64_t count0, int band, uint64_t wait_ns, unsigned long long *err_ptr,
-              OccOut occ, const SampleJobs sj) {
+              int64_t count0, int band, int keep_a, uint64_t wait_ns,
+              unsigned long long *err_ptr, OccOut occ, const SampleJobs sj) {
     static_assert(kSW == 0 || P == 3, "the sampling variant runs the 3-product GEMM");
     static_assert(kPair == 1 || kPair == 2, "one CTA or a CTA pair per tile group");
     constexpr int kE0 = epi_warp0<kSW>();  // first epilogue warp
@@ -391,6 +392,13 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
             uint32_t used = 0, last_phase = 0;  // stages ever filled, parity of their last fill
             bool ok = true;
             const GemmNetDesc *cur = nullptr;
+            // banded order with keep_a: the band's A tiles are read again by
+            // every wave of the band, so they are loaded with the evict-last
+            // L2 policy (the trajectory tiles, read by one wave only, stay
+            // normal).  Whether that pays depends on how much of the L2 the
+            // band's A tiles leave to the trajectory tiles: a tuned choice.
+            const bool keepA = keep_a && band > 0 && !tiles;
+            const uint64_t polA = ptx::policy_evict_last();
             for (int tile = unit; ok && tile < ntiles; tile += nunits) {
                 const TileRef tr = decode_tile<kPair>(tile, nets, tiles, count0, band, rank);
                 const GemmNetDesc *d = tr.d;
@@ -417,9 +425,14 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                     if constexpr (kPair == 1) {
                         ptx::mbar_arrive_expect_tx(fb, C::kStageBytes);
 #pragma unroll
-                        for (int q = 0; q < kPl; ++q)
-                            ptx::tma_load_3d(ptx::smem_u32(a_tile(stage, q)), mA[q], fb, 0,
-                                             tr.mt * 128, kb);
+                        for (int q = 0; q < kPl; ++q) {
+                            if (keepA)
+                                ptx::tma_load_3d_hint(ptx::smem_u32(a_tile(stage, q)), mA[q], fb,
+                                                      0, tr.mt * 128, kb, polA);
+                            else
+                                ptx::tma_load_3d(ptx::smem_u32(a_tile(stage, q)), mA[q], fb, 0,
+                                                 tr.mt * 128, kb);
+                        }
 #pragma unroll
                         for (int q = 0; q < kPl; ++q)
                             ptx::tma_load_3d(ptx::smem_u32(b_tile(stage, q)), mB[q], fb, 0, brow,
@@ -430,9 +443,14 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                         if (leader) ptx::mbar_arrive_expect_tx(fb, 2 * C::kStageBytes);
                         const uint32_t fb0 = ptx::cluster_addr(fb, 0u);
 #pragma unroll
-                        for (int q = 0; q < kPl; ++q)
-                            ptx::tma_load_3d_pair(ptx::smem_u32(a_tile(stage, q)), mA[q], fb0, 0,
-                                                  tr.mt * 128, kb);
+                        for (int q = 0; q < kPl; ++q) {
+                            if (keepA)
+                                ptx::tma_load_3d_pair_hint(ptx::smem_u32(a_tile(stage, q)), mA[q],
+                                                           fb0, 0, tr.mt * 128, kb, polA);
+                            else
+                                ptx::tma_load_3d_pair(ptx::smem_u32(a_tile(stage, q)), mA[q], fb0,
+                                                      0, tr.mt * 128, kb);
+                        }
 #pragma unroll
                         for (int q = 0; q < kPl; ++q)
                             ptx::tma_load_3d_pair(ptx::smem_u32(b_tile(stage, q)), mB[q], fb0, 0,
@@ -517,8 +535,8 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                 for (int sg = 0; ok && sg < nseg; ++sg, ++seg) {
                     const uint32_t b = seg & 1u;
                     // the epilogue warps of both CTAs have read this buffer
-                    if (!ptx::mbar_wait<(kPair > 1)>(ptx::smem_u32(&tempty[b]),
-                                                     ((seg >> 1) & 1u) ^ 1u, err, wait_ns)) {
+                    if (!ptx::mbar_wait(ptx::smem_u32(&tempty[b]), ((seg >> 1) & 1u) ^ 1u, err,
+                                        wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -615,10 +633,9 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                 for (int i = 0; i < 32; i += 2) add_f32x2(rb[i], rb[i + 1], t[i], t[i + 1]);
                 ptx::tmem_ld32(tb + 160u, t);
                 ptx::tmem_ld_wait();
-#pragma unroll
-                for (int i = 0; i < 32; i += 2) add_f32x2(rb[32 + i], rb[33 + i], t[i], t[i + 1]);
-                // the warp's reads are done: one arrival per warp on the
-                // buffer's free barrier (the first CTA's, in a pair)
+                // the warp's reads are done (the last values are in
+                // registers): one arrival per warp on the buffer's free
+                // barrier (the first CTA's, in a pair) before the last adds
                 ptx::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) {
@@ -626,8 +643,10 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
                     if constexpr (kPair == 1)
                         ptx::mbar_arrive(tb_bar);
                     else
-                        ptx::mbar_arrive_cluster(ptx::cluster_addr(tb_bar, 0u));
+                        ptx::mbar_arrive_remote(ptx::cluster_addr(tb_bar, 0u));
                 }
+#pragma unroll
+                for (int i = 0; i < 32; i += 2) add_f32x2(rb[32 + i], rb[33 + i], t[i], t[i + 1]);
             }
             // occupations of this row for the thread's 64 trajectories, in
             // groups of 16: real part a*b from the own row, imaginary part with
@@ -814,10 +833,11 @@ namespace {
 std::mutex g_tc_mu;
 bool g_attr_set[64] = {};
 // (log2 N, log2 M, products) -> (CTA pair, band) chosen by the autotuner
-std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;
+// (log2 N, log2 M, products, sampling launch) -> configuration
+std::map<std::tuple<int, int, int, int>, GemmCfg> g_tune;
 // Whether the autotuner also times CTA pairs (gbs_set_gemm_config can always
 // ask for them).
-bool g_pair_autotune = false;
+bool g_pair_autotune = true;
 
 template <int P, int kPair, int kSW>
 cudaError_t set_smem_attr() {
@@ -862,8 +882,8 @@ bool sampling_kernels_ok() {
 
 template <int P, int kPair, int kSW>
 int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets, const int4 *d_tiles,
-                   int ntiles, int64_t count0, int band, uint64_t wait_ns, unsigned long long *err,
-                   OccOut occ, const SampleJobs &jobs) {
+                   int ntiles, int64_t count0, int band, int keep_a, uint64_t wait_ns,
+                   unsigned long long *err, OccOut occ, const SampleJobs &jobs) {
     if (ntiles <= 0) return GBS_OK;
     const int units = std::max(1, std::min(ntiles, sm_count / kPair));
     cudaLaunchConfig_t cfg = {};
@@ -879,7 +899,7 @@ int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets,
     cfg.attrs = attr;
     cfg.numAttrs = kPair > 1 ? 1 : 0;
     cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_tc<P, kPair, kSW>, d_nets, d_tiles, ntiles,
-                                        count0, band, wait_ns, err, occ, jobs);
+                                        count0, band, keep_a, wait_ns, err, occ, jobs);
     if (le != cudaSuccess)
         return set_error(GBS_ECUDA, "launch of the GEMM (%d products, %s%s) failed: %s", P,
                          kPair > 1 ? "CTA pairs" : "one CTA per tile", kSW ? ", sampling" : "",
@@ -940,7 +960,7 @@ int bucket(int v) {
 
 }  // namespace
 
-int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int pair, int band,
+int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int pair, int band, int keep_a,
                         uint64_t wait_ns, const GemmNetDesc *d_nets, const int4 *d_tiles,
                         int ntiles, int64_t count0, unsigned long long *err, OccOut occ) {
     int rc;
@@ -951,11 +971,11 @@ int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int pair, int 
     const SampleJobs none;
     if (P == 3)
         return pair == 1
-                   ? launch_variant<3, 1, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, wait_ns, err, occ, none)
-                   : launch_variant<3, 2, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, wait_ns, err, occ, none);
+                   ? launch_variant<3, 1, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, keep_a, wait_ns, err, occ, none)
+                   : launch_variant<3, 2, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, keep_a, wait_ns, err, occ, none);
     return pair == 1
-               ? launch_variant<6, 1, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, wait_ns, err, occ, none)
-               : launch_variant<6, 2, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, wait_ns, err, occ, none);
+               ? launch_variant<6, 1, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, keep_a, wait_ns, err, occ, none)
+               : launch_variant<6, 2, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, keep_a, wait_ns, err, occ, none);
 }
 
 int tc_fill_desc(gbs_net *net, GemmNetDesc *out, bool alt) {
@@ -973,9 +993,9 @@ int launch_gemm_grouped_sampling(cudaStream_t stream, int sm_count, int pair, ui
     if (!sampling_kernels_ok()) return set_error(GBS_EINVAL, "sampling GEMM unavailable");
     if (pair != 1 && pair != 2) return set_error(GBS_EINVAL, "GEMM tiles per CTA pair must be 1 or 2");
     return pair == 1 ? launch_variant<3, 1, kSampWG>(stream, sm_count, d_nets, d_tiles, ntiles, 0, 0,
-                                                     wait_ns, err, OccOut(), jobs)
+                                                     0, wait_ns, err, OccOut(), jobs)
                      : launch_variant<3, 2, kSampWG>(stream, sm_count, d_nets, d_tiles, ntiles, 0, 0,
-                                                     wait_ns, err, OccOut(), jobs);
+                                                     0, wait_ns, err, OccOut(), jobs);
 }
 
 int tc_products(gbs_net *net) { return net->tc ? net->tc->P : 0; }
@@ -1006,19 +1026,21 @@ void tc_plan_destroy(gbs_net *net) {
     net->tc = nullptr;
 }
 
-int tc_set_config(gbs_net *net, int pair, int band) {
+int tc_set_config(gbs_net *net, const GemmCfg &cfg) {
     if (!net->tc) return set_error(GBS_EINVAL, "network has no tensor-core GEMM");
-    if (pair < 0 || pair > 2) return set_error(GBS_EINVAL, "pair must be 0 (auto), 1 or 2");
-    if (band < 0) return set_error(GBS_EINVAL, "band must be >= 0");
-    net->tc->forced = pair != 0;
-    net->tc->pair = pair;
-    net->tc->band = pair ? band : 0;
+    if (cfg.pair < 0 || cfg.pair > 2) return set_error(GBS_EINVAL, "pair must be 0 (auto), 1 or 2");
+    if (cfg.band < 0) return set_error(GBS_EINVAL, "band must be >= 0");
+    if (cfg.keep < 0 || cfg.keep > 1) return set_error(GBS_EINVAL, "keep_a must be 0 or 1");
+    net->tc->forced = cfg.pair != 0;
+    GemmCfg c = cfg;
+    if (!c.pair) c = GemmCfg();
+    net->tc->cfg[0] = net->tc->cfg[1] = c;
     return GBS_OK;
 }
 
-void tc_get_config(gbs_net *net, int *pair, int *band) {
-    *pair = net->tc ? net->tc->pair : 0;
-    *band = net->tc ? net->tc->band : 0;
+GemmCfg tc_get_config(gbs_net *net) {
+    if (!net->tc) return GemmCfg();
+    return net->tc->cfg[1].pair ? net->tc->cfg[1] : net->tc->cfg[0];
 }
 
 void tc_set_pair_autotune(bool on) {
@@ -1033,91 +1055,130 @@ bool tc_pair_autotune() {
 }
 
 // The candidates the autotuner times: one CTA or CTA pairs per tile group,
-// each with the plain tile order and bands of 16 and 8 groups (where the
-// network has more groups than that).
-std::vector<std::pair<int, int>> tc_candidates(int mtiles, bool pairs) {
-    std::vector<std::pair<int, int>> c;
+// each with bands of 16 and 8 groups (where the network has more groups than
+// that; the bands with and without the evict-last policy on their A tiles)
+// and the plain tile order.  The plain order streams all of A through L2 once
+// per wave of CTAs; when A is larger than half the L2 that moves several
+// times the bytes of a banded order from HBM, and although short timings can
+// favour it (m8000: by about 1 %), over a long run the extra DRAM power lowers
+// the clock under the power limit (m8000: 1063 against 1012 ms per step), so
+// it is offered only for networks whose A fits in half the L2.
+std::vector<GemmCfg> tc_candidates(int mtiles, bool pairs, bool plain) {
+    std::vector<GemmCfg> c;
     for (int pair = 1; pair <= (pairs ? 2 : 1); ++pair) {
         const int groups = (mtiles + pair - 1) / pair;
-        c.push_back({pair, 0});
+        bool banded = false;
         for (int band : {16, 8})
-            if (groups > band) c.push_back({pair, band});
+            if (groups > band) {
+                banded = true;
+                for (int keep : {0, 1}) c.push_back({pair, band, keep});
+            }
+        if (plain || !banded) c.push_back({pair, 0, 0});
     }
     return c;
 }
 
-// Time the candidate configurations on this chunk (one warm-up and one timed
-// launch each) and keep the fastest for this network and every network of
-// the same size bucket.
-int tc_autotune(gbs_net *net, int64_t count, int *pair_out, int *band_out) {
+// One launch over the closed-form tiles of the network's current chunk in
+// configuration g; with a job, the sampling variant that also runs it.
+int launch_closed(gbs_net *net, const GemmCfg &g, int ntiles, int64_t count, const SampleJob *job,
+                  OccOut occ) {
     TcPlan *plan = net->tc;
-    const auto key = std::make_tuple(bucket(net->N), bucket(net->M), plan->P);
+    if (!job)
+        return launch_gemm_grouped(net->stream, net->sm_count, plan->P, g.pair, g.band, g.keep,
+                                   net->wait_ns, plan->d_desc, nullptr, ntiles, count,
+                                   net->d_flags + 1, occ);
+    SampleJobs jobs;
+    jobs.one = *job;
+    return g.pair == 1
+               ? launch_variant<3, 1, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
+                                               ntiles, count, g.band, g.keep, net->wait_ns,
+                                               net->d_flags + 1, occ, jobs)
+               : launch_variant<3, 2, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
+                                               ntiles, count, g.band, g.keep, net->wait_ns,
+                                               net->d_flags + 1, occ, jobs);
+}
+
+// Time the candidate configurations on this chunk (as the launch to be
+// configured runs: plain, or with `job` as the sampling variant; the job's
+// samples are written again by that launch) and keep the fastest for this
+// network and every network of the same size bucket.  The candidates
+// are compared in the state a long run reaches: a first pass launches each
+// once (it brings the GPU to the clock its power limit allows under this
+// load), then kTunePasses passes time kTuneReps launches of each candidate,
+// the candidates interleaved, and the times of the passes are summed.  (One
+// launch each from an idle GPU favoured configurations that move more data:
+// fast while the clock is high, slower once the power limit lowers it.)
+constexpr int kTunePasses = 2, kTuneReps = 2;
+
+int tc_autotune(gbs_net *net, int64_t count, const SampleJob *job, GemmCfg *out) {
+    TcPlan *plan = net->tc;
+    const auto key = std::make_tuple(bucket(net->N), bucket(net->M), plan->P, job ? 1 : 0);
     bool pairs;
     {
         std::lock_guard<std::mutex> lock(g_tc_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
-            *pair_out = it->second.first;
-            *band_out = it->second.second;
+            *out = it->second;
             return GBS_OK;
         }
         pairs = g_pair_autotune;
     }
-    *pair_out = 1;
-    *band_out = 0;
+    *out = GemmCfg{1, 0, 0};
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     GBS_CUDA_TRY(cudaStreamIsCapturing(net->stream, &cs));
     if (cs != cudaStreamCaptureStatusNone) return GBS_OK;  // no timing inside a capture: default
     const int stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, net->device) != cudaSuccess) {
+        cudaGetLastError();
+        l2 = 0;
+    }
+    const double a_bytes = (double)(plan->P == 3 ? 2 : 3) * net->rowsA * net->ldK * 2.0;
+    const std::vector<GemmCfg> cand = tc_candidates(net->mtiles, pairs, a_bytes <= 0.5 * l2);
+    std::vector<float> total(cand.size(), 0.0f);
     cudaEvent_t e0, e1;
     GBS_CUDA_TRY(cudaEventCreate(&e0));
     GBS_CUDA_TRY(cudaEventCreate(&e1));
-    float best = 0.0f;
     int rc = GBS_OK;
-    bool first = true;
-    for (const auto &cand : tc_candidates(net->mtiles, pairs)) {
-        const int pair = cand.first, band = cand.second;
-        const int nt = ((net->mtiles + pair - 1) / pair) * stiles;
-        rc = launch_gemm_grouped(net->stream, net->sm_count, plan->P, pair, band, net->wait_ns,
-                                 plan->d_desc, nullptr, nt, count, net->d_flags + 1);
-        if (rc) break;
-        cudaEventRecord(e0, net->stream);
-        rc = launch_gemm_grouped(net->stream, net->sm_count, plan->P, pair, band, net->wait_ns,
-                                 plan->d_desc, nullptr, nt, count, net->d_flags + 1);
-        if (rc) break;
-        cudaEventRecord(e1, net->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            rc = set_error(GBS_ECUDA, "autotuner timing failed");
-            break;
-        }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (first || ms < best) {
-            best = ms;
-            *pair_out = pair;
-            *band_out = band;
-            first = false;
+    for (int pass = 0; pass <= kTunePasses && rc == GBS_OK; ++pass) {
+        for (size_t c = 0; c < cand.size() && rc == GBS_OK; ++c) {
+            const GemmCfg &g = cand[c];
+            const int nt = ((net->mtiles + g.pair - 1) / g.pair) * stiles;
+            const int reps = pass == 0 ? 1 : kTuneReps;
+            cudaEventRecord(e0, net->stream);
+            for (int q = 0; q < reps && rc == GBS_OK; ++q)
+                rc = launch_closed(net, g, nt, count, job, OccOut());
+            if (rc) break;
+            cudaEventRecord(e1, net->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = set_error(GBS_ECUDA, "autotuner timing failed");
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (pass > 0) total[c] += ms;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
+    size_t best = 0;
+    for (size_t c = 1; c < cand.size(); ++c)
+        if (total[c] < total[best]) best = c;
+    *out = cand[best];
     std::lock_guard<std::mutex> lock(g_tc_mu);
-    g_tune[key] = std::make_pair(*pair_out, *band_out);
+    g_tune[key] = *out;
     return GBS_OK;
 }
 
 namespace {
 
-int pick_config(gbs_net *net, int64_t count) {
+const GemmCfg *pick_config(gbs_net *net, int64_t count, const SampleJob *job, int *rc) {
     TcPlan *plan = net->tc;
-    if (!plan->pair) {
-        int pair = 1, band = 0, rc;
-        if ((rc = tc_autotune(net, count, &pair, &band))) return rc;
-        plan->pair = pair;
-        plan->band = band;
-    }
-    return GBS_OK;
+    GemmCfg &c = plan->cfg[job ? 1 : 0];
+    *rc = GBS_OK;
+    if (!c.pair) *rc = tc_autotune(net, count, job, &c);
+    return &c;
 }
 
 }  // namespace
@@ -1128,12 +1189,11 @@ int launch_gemm_tc(gbs_net *net, int64_t count, OccOut occ) {
     if (!plan) return set_error(GBS_EINVAL, "no tensor-core plan");
     int rc;
     if ((rc = ensure_attrs())) return rc;
-    if ((rc = pick_config(net, count))) return rc;
-    const int groups = (net->mtiles + plan->pair - 1) / plan->pair;
+    const GemmCfg *c = pick_config(net, count, nullptr, &rc);
+    if (rc) return rc;
+    const int groups = (net->mtiles + c->pair - 1) / c->pair;
     const int stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
-    return launch_gemm_grouped(net->stream, net->sm_count, plan->P, plan->pair, plan->band,
-                               net->wait_ns, plan->d_desc, nullptr, groups * stiles, count,
-                               net->d_flags + 1, occ);
+    return launch_closed(net, *c, groups * stiles, count, nullptr, occ);
 }
 
 int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job, OccOut occ) {
@@ -1145,18 +1205,12 @@ int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job, O
         return set_error(GBS_EINVAL, "occupation output needs ld >= count, ld %% 128 == 0");
     int rc;
     if ((rc = ensure_attrs())) return rc;
-    if ((rc = pick_config(net, count))) return rc;
-    const int groups = (net->mtiles + plan->pair - 1) / plan->pair;
+    if (!sampling_kernels_ok()) return set_error(GBS_EINVAL, "sampling GEMM unavailable");
+    const GemmCfg *c = pick_config(net, count, &job, &rc);
+    if (rc) return rc;
+    const int groups = (net->mtiles + c->pair - 1) / c->pair;
     const int stiles = (int)((count + kTcTileSamples - 1) / kTcTileSamples);
-    SampleJobs jobs;
-    jobs.one = job;
-    return plan->pair == 1
-               ? launch_variant<3, 1, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
-                                               groups * stiles, count, plan->band, net->wait_ns,
-                                               net->d_flags + 1, occ, jobs)
-               : launch_variant<3, 2, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
-                                               groups * stiles, count, plan->band, net->wait_ns,
-                                               net->d_flags + 1, occ, jobs);
+    return launch_closed(net, *c, groups * stiles, count, &job, occ);
 }
 
 bool tc_sampling_ready(gbs_net *net, bool allocate) {

@@ -48,31 +48,17 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
                  : "memory");
 }
 
-// kCluster: acquire at cluster scope, for a barrier that threads of another
-// CTA of the cluster arrive on with release semantics.
-template <bool kCluster = false>
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
-    if constexpr (kCluster)
-        asm volatile(
-            "{\n"
-            ".reg .pred p;\n"
-            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-            "selp.u32 %0, 1, 0, p;\n"
-            "}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-    else
-        asm volatile(
-            "{\n"
-            ".reg .pred p;\n"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            "selp.u32 %0, 1, 0, p;\n"
-            "}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
     return ok != 0;
 }
 
@@ -83,15 +69,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 // of the grid fares (drains of loads and MMAs already issued, which always
 // complete).  The time is first checked after the second failed poll, so a
 // limit of 0 gives up on any phase that is not complete almost at once.
-template <bool kCluster = false>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
                                           volatile unsigned long long *err,
                                           uint64_t limit_ns = 2000000000ull,
                                           bool stop_on_err = true) {
-    if (mbar_try_wait<kCluster>(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait<kCluster>(bar, parity)) return true;
+        if (mbar_try_wait(bar, parity)) return true;
         if ((it & 255u) == 1u) {
             if (stop_on_err && *err) return false;
             if (globaltimer() - t0 > limit_ns) {
@@ -122,6 +107,25 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// An L2 cache policy that keeps the lines it is attached to in L2 ahead of
+// normal ones (for operand tiles that later CTAs read again).
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// tma_load_3d with an L2 cache policy (policy_evict_last()).
+__device__ __forceinline__ void tma_load_3d_hint(uint32_t dst, const CUtensorMap *map,
+                                                 uint32_t bar, int c0, int c1, int c2,
+                                                 uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        ".L2::cache_hint [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "l"(policy)
+        : "memory");
+}
+
 // The same load issued by either CTA of a CTA pair (cta_group::2): the box
 // lands in the issuing CTA's own shared memory at dst, and the byte count
 // goes to the mbarrier at bar, a shared::cluster address that may lie in the
@@ -136,6 +140,18 @@ __device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap
         : "memory");
 }
 
+// tma_load_3d_pair with an L2 cache policy.
+__device__ __forceinline__ void tma_load_3d_pair_hint(uint32_t dst, const CUtensorMap *map,
+                                                      uint32_t bar, int c0, int c1, int c2,
+                                                      uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.tile"
+        ".mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "l"(policy)
+        : "memory");
+}
+
 // Address of the same shared-memory offset in CTA `rank` of the cluster.
 __device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank) {
     uint32_t r;
@@ -143,11 +159,13 @@ __device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank) 
     return r;
 }
 
-// Arrive (release at cluster scope) on an mbarrier given by its
-// shared::cluster address, possibly in another CTA of the cluster.
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar)
-                 : "memory");
+// Arrive on an mbarrier given by its shared::cluster address, possibly in
+// another CTA of the cluster (default release semantics: what the arrival
+// orders is TMEM reads, fenced by tcgen05.fence::before_thread_sync, not
+// memory another CTA reads; a cluster-scope release and acquire here made
+// the CTA-pair GEMM's accumulator hand-off 30 % slower).
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {

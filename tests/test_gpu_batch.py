@@ -30,9 +30,9 @@ def gbs():
     return g
 
 
-CONFIGS = [pytest.param((1, 0), id="cta"), pytest.param((1, 1), id="cta-band1"),
-           pytest.param((1, 2), id="cta-band2"), pytest.param((2, 0), id="pair"),
-           pytest.param((2, 1), id="pair-band1")]
+CONFIGS = [pytest.param((1, 0, 0), id="cta"), pytest.param((1, 1, 0), id="cta-band1"),
+           pytest.param((1, 2, 1), id="cta-band2-keep"), pytest.param((2, 0, 0), id="pair"),
+           pytest.param((2, 1, 1), id="pair-band1-keep")]
 
 
 @pytest.mark.parametrize("config", CONFIGS)
@@ -43,7 +43,7 @@ def test_tile_configurations_agree_bitwise(gbs, shape, config):
     N, M = shape
     net_def = wl.small_network(N, M=M, r=0.8, t2=0.93, seed=31 + N)
     res = []
-    for cfg in ((1, 0), config):
+    for cfg in ((1, 0, 0), config):
         net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
         gbs.gbs_set_gemm_config(net, *cfg)
         n, nS = gbs.gbs_debug_samples(net, net_def.seed_s, 100, 333)
@@ -65,7 +65,7 @@ def test_tile_configurations_agree_on_many_tiles(gbs, config):
     stream = torch.cuda.current_stream().cuda_stream
     net_def = wl.small_network(320, M=640, r=0.6, t2=0.9, seed=77)
     res = []
-    for cfg in ((1, 0), config):
+    for cfg in ((1, 0, 0), config):
         net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x6", stream)
         gbs.gbs_set_gemm_config(net, *cfg)
         n, nS = gbs.gbs_debug_samples(net, net_def.seed_s, 0, 3 * 152 * 128 + 77)
@@ -79,10 +79,10 @@ def test_autotuner_picks_a_configuration(gbs):
     stream = torch.cuda.current_stream().cuda_stream
     net_def = wl.small_network(200, r=0.7, t2=0.9, seed=3)
     net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
-    assert gbs.gbs_gemm_config(net) == (0, 0)
+    assert gbs.gbs_gemm_config(net) == (0, 0, 0)
     gbs.gbs_sample(net, net_def.seed_s, 0, 5000, 10, 256)
-    pair, band = gbs.gbs_gemm_config(net)
-    assert pair in (1, 2) and band >= 0
+    pair, band, keep = gbs.gbs_gemm_config(net)
+    assert pair in (1, 2) and band >= 0 and keep in (0, 1)
     gbs.gbs_free_network(net)
 
 
@@ -107,8 +107,8 @@ def test_batch_equals_per_network_runs(gbs, own_stream):
     singles = [gbs.gbs_make_network(d.T, d.r, "bf16x3", sptr) for d in defs]
     batch = gbs.gbs_make_batch(nets)
     gbs.gbs_sample_batch(batch, seeds, first, E, n_sub, K1)
-    cl, rounds, tiles = gbs.gbs_batch_info(batch)
-    assert cl in (1, 2) and rounds >= 1 and tiles > 0
+    (pair, band), rounds, tiles = gbs.gbs_batch_info(batch)
+    assert pair in (1, 2) and band >= 0 and rounds >= 1 and tiles > 0
     for i, d in enumerate(defs):
         gbs.gbs_sample(singles[i], seeds[i], first[i], E[i], n_sub[i], K1[i])
         _, _, acc_b, cnt_b = gbs.gbs_get_accumulators(nets[i])
@@ -122,6 +122,39 @@ def test_batch_equals_per_network_runs(gbs, own_stream):
         assert cnt.sum() == 2 * E[i]
     gbs.gbs_free_batch(batch)
     for n in nets + singles:
+        gbs.gbs_free_network(n)
+
+
+@pytest.mark.parametrize("config", [pytest.param((1, 0), id="cta"), pytest.param((1, 8), id="cta-band8"),
+                                    pytest.param((2, 0), id="pair"),
+                                    pytest.param((2, 8), id="pair-band8")])
+def test_batch_candidates_agree_bitwise(gbs, config):
+    """Every configuration the batch autotuner times (one CTA per tile or CTA
+    pairs, plain tile order or bands of 8 groups within each network) gives
+    bitwise the sums of per-network runs; one network has 18 mode tiles (9
+    pair groups), so the bands are in use."""
+    import torch
+    sptr = torch.cuda.current_stream().cuda_stream
+    defs = [wl.small_network(1100, r=0.6, t2=0.9, seed=71), wl.small_network(150, r=0.9, t2=0.8, seed=72),
+            wl.small_network(520, r=0.7, t2=0.95, seed=73)]
+    E, n_sub, K1 = [4000, 9000, 5000], [8, 8, 8], [2048, 512, 1024]
+    seeds = [d.seed_s for d in defs]
+    first = [0, 0, 0]
+    nets = [gbs.gbs_make_network(d.T, d.r, "bf16x3", sptr) for d in defs]
+    batch = gbs.gbs_make_batch(nets)
+    gbs.gbs_set_batch_config(batch, *config)
+    gbs.gbs_sample_batch(batch, seeds, first, E, n_sub, K1)
+    assert gbs.gbs_batch_info(batch)[0] == config
+    for i, d in enumerate(defs):
+        single = gbs.gbs_make_network(d.T, d.r, "bf16x3", sptr)
+        gbs.gbs_sample(single, seeds[i], first[i], E[i], n_sub[i], K1[i])
+        _, _, acc_b, cnt_b = gbs.gbs_get_accumulators(nets[i])
+        _, _, acc_s, cnt_s = gbs.gbs_get_accumulators(single)
+        gbs.gbs_free_network(single)
+        assert np.array_equal(cnt_b, cnt_s)
+        assert np.array_equal(acc_b.view(np.float64), acc_s.view(np.float64)), (config, i)
+    gbs.gbs_free_batch(batch)
+    for n in nets:
         gbs.gbs_free_network(n)
 
 

@@ -49,12 +49,12 @@ def test_gemm_wait_timeout_is_reported_and_recoverable(gbs, stream, precision):
     net_def = wl.small_network(96, M=160, r=0.7, t2=0.9, seed=41)
     E, n_sub, K1 = 6000, 8, 128
     ref = gbs.gbs_make_network(net_def.T, net_def.r, precision, stream)
-    gbs.gbs_set_gemm_config(ref, 1, 0)
+    gbs.gbs_set_gemm_config(ref, 1, 0, 0)
     P_ref, acc_ref, cnt_ref = _sums(gbs, ref, net_def.seed_s, E, n_sub, K1)
     gbs.gbs_free_network(ref)
 
     net = gbs.gbs_make_network(net_def.T, net_def.r, precision, stream)
-    gbs.gbs_set_gemm_config(net, 1, 0)
+    gbs.gbs_set_gemm_config(net, 1, 0, 0)
     gbs.gbs_set_wait_limit(net, 0)
     gbs.gbs_sample(net, net_def.seed_s, 0, E, n_sub, K1)  # asynchronous: no error yet
     with pytest.raises(gbs.GbsError) as ei:
@@ -78,8 +78,8 @@ def test_timeout_of_one_network_leaves_another_untouched(gbs, stream):
     d = wl.small_network(64, r=0.6, t2=0.95, seed=43)
     a = gbs.gbs_make_network(d.T, d.r, "bf16x3", stream)
     b = gbs.gbs_make_network(d.T, d.r, "bf16x3", stream)
-    gbs.gbs_set_gemm_config(a, 1, 0)
-    gbs.gbs_set_gemm_config(b, 1, 0)
+    gbs.gbs_set_gemm_config(a, 1, 0, 0)
+    gbs.gbs_set_gemm_config(b, 1, 0, 0)
     gbs.gbs_set_wait_limit(a, 0)
     gbs.gbs_sample(a, d.seed_s, 0, 2048, 4, 64)
     gbs.gbs_sample(b, d.seed_s, 0, 2048, 4, 64)
