@@ -42,7 +42,16 @@ UNIT = "samples/s"
 # sampler, CTA pair 1/2, band).  An entry holds only for the kernel version
 # it was captured on: the table is emptied whenever the kernel changes, and a
 # run without an entry reports traffic null.
-GEMM_TRAFFIC_BYTES_PER_SAMPLE = {}
+GEMM_TRAFFIC_BYTES_PER_SAMPLE = {
+    ("m8000", "bf16x3", True, 2, 16, 0): (
+        (57.453761e9 + 1.111236e9) / 16768,
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 16768-trajectory sampling "
+        "launch (profiles/k_gemm_tc_pair_m8000.md), scaled to the average launch"),
+    ("m1000", "bf16x3", True, 2, 0, 0): (
+        (1.093573e9 + 1.110423e9) / 131072,
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 131072-trajectory sampling "
+        "launch (profiles/k_gemm_tc_pair_m1000.md), scaled to the average launch"),
+}
 
 # FP32 lane-operation slots of the FMA pipe per evaluated (trajectory, k)
 # pair of the double-float generating-function kernel (k_gf_df): the FMA
@@ -377,7 +386,7 @@ def gbs_arm(args, wl_def):
             per_traj += 2 * planes * 2 * netdef.N + 8
         roof["algorithmic_bytes"] = per_traj * E * args.steps / max(gemm_launches, 1) + \
             planes * 2 * netdef.M * netdef.N * 2
-        key = (wl_def.name.split(":")[0], precision, folded, pair, band)
+        key = (wl_def.name.split(":")[0], precision, folded, pair, band, keep_a)
         per_sample = GEMM_TRAFFIC_BYTES_PER_SAMPLE.get(key)
         if per_sample is not None:
             roof["traffic"] = per_sample[0] * E * args.steps / max(gemm_launches, 1)
@@ -589,25 +598,29 @@ def batch_arm(args):
     clk = clocks.stop()
     ms_total = ev0.elapsed_time(ev1)
     (pair, band), rounds, tiles = gbs.gbs_batch_info(batch)
-    # kernels per step: per network and chunk a finalize and a sampler
-    # (networks of >= 900 output modes with more than one chunk: round 0
-    # only, the grouped GEMMs draw the rest); per round one grouped GEMM and
-    # one grouped generating-function launch; per network the inversion
-    # (prep, log2 K1 FFT passes, statistics)
+    # kernels per step: per network and chunk a finalize, a generating-
+    # function launch and a sampler (networks of >= 900 output modes with
+    # more than one chunk: round 0 only, the grouped GEMMs draw the rest);
+    # per round one grouped GEMM; per network the inversion (prep, log2 K1
+    # FFT passes, statistics)
     chunks = [-(-e // gbs.gbs_network_info(n)[3]) for e, n in zip(E, nets)]
     samplers = [1 if (c > 1 and d.M >= 900) else c for c, d in zip(chunks, defs)]
-    launches_per_step = sum(chunks) + sum(samplers) + 2 * rounds + \
+    launches_per_step = 2 * sum(chunks) + sum(samplers) + rounds + \
         sum(int(math.log2(k)) + 2 for k in K1s)
-    # kernel time of the grouped GEMM: extra steps with phase timing on (the
-    # rounds are then issued one by one rather than as a graph)
-    gbs.gbs_profile_enable(nets[0], True)
+    # kernel times: extra steps with phase timing on every network (the
+    # rounds are then issued one by one rather than as a graph; the grouped
+    # GEMM is attributed to the first network, each network's generating
+    # functions to itself)
+    for n in nets:
+        gbs.gbs_profile_enable(n, True)
     nprof = 2
     for s in range(nprof):
         step(args.warmup + args.steps + s)
-    prof = gbs.gbs_profile_read(nets[0])
-    gbs.gbs_profile_enable(nets[0], False)
-    gemm_ms = prof["gemm"][0] * args.steps / nprof
-    gf_ms = prof["gf"][0] * args.steps / nprof
+    profs = [gbs.gbs_profile_read(n) for n in nets]
+    for n in nets:
+        gbs.gbs_profile_enable(n, False)
+    gemm_ms = profs[0]["gemm"][0] * args.steps / nprof
+    gf_ms = sum(p["gf"][0] for p in profs) * args.steps / nprof
     total = sum(E) * args.steps
     flops = sum(8.0 * d.M * d.N * e for d, e in zip(defs, E)) * args.steps
     peaks, peak_kind = _peaks()
@@ -633,8 +646,9 @@ def batch_arm(args):
                      "gemm_ms_per_step": gemm_ms / args.steps},
         "phases": {"gemm": {"ms_per_step": gemm_ms / args.steps},
                    "gf": {"ms_per_step": gf_ms / args.steps,
-                          "note": "one grouped generating-function launch per round over all "
-                                  "networks' chunks"}},
+                          "note": "sum over the networks' generating-function launches, which "
+                                  "run side by side on 8 branches (so the sum exceeds their "
+                                  "share of the wall time)"}},
         "gpu_launches": launches_per_step * args.steps, "clocks": clk,
     }
     gbs.gbs_free_batch(batch)

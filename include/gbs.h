@@ -441,7 +441,9 @@ int gbs_sampler_fusion(gbs_net_t net, int *active);
  *   first call), rounds and GEMM tiles of the last call.
  * With phase timing enabled on the batch's first network (gbs_profile_enable),
  * gbs_sample_batch issues its rounds directly instead of as a graph and
- * attributes the grouped GEMM launches to that network's GEMM phase.
+ * attributes the grouped GEMM launches to that network's GEMM phase; each
+ * network with phase timing enabled records its own generating-function
+ * launches.
  * gbs_free_batch -- release the batch (not its networks).
  */
 typedef struct gbs_batch *gbs_batch_t;

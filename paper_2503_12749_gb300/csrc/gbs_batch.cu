@@ -49,12 +49,6 @@ struct gbs_batch {
     gbs::SampleJob *d_jobs = nullptr;
     int64_t *d_prefix = nullptr;
     size_t jobs_cap = 0, prefix_cap = 0;
-    // generating-function work of the rounds: per round its chunks (one per
-    // network with trajectories in the round) and one work list
-    gbs::GfChunk *d_gfc = nullptr;
-    int4 *d_gfwork = nullptr;
-    int *d_gfnext = nullptr;  // the grouped launch's work counter
-    size_t gfc_cap = 0, gfwork_cap = 0;
     int last_rounds = 0;
     int64_t last_tiles = 0;
     bool last_fold = false;
@@ -79,14 +73,6 @@ struct RoundPlan {
     std::vector<SampleJob> jobs;    // [rounds][nets] (round 0 unused)
     std::vector<int64_t> prefix;    // [rounds][nets + 1]
     std::vector<int64_t> step;      // [nets]: trajectories per round (chunk_step)
-    // one grouped generating-function launch per round: the round's chunks
-    // and the work items {chunk, sub-ensemble, slot block}, slot block
-    // levels outermost (every chunk's centre blocks, the heaviest, first),
-    // within a level the chunks in order of decreasing trajectories
-    std::vector<GfChunk> gfc;       // all rounds, concatenated
-    std::vector<int> gfc_off;       // [rounds + 1]
-    std::vector<int4> gfwork;       // all rounds, concatenated (x = index within the round)
-    std::vector<int> gfwork_off;    // [rounds + 1]
 };
 
 int build_rounds(gbs_batch *b, const int64_t *E, int pair, int band, RoundPlan &rp,
@@ -142,34 +128,6 @@ int build_rounds(gbs_batch *b, const int64_t *E, int pair, int band, RoundPlan &
         }
     }
     rp.tile_off[rounds] = (int)rp.tiles.size();
-    // generating-function work of every round
-    rp.gfc.clear();
-    rp.gfwork.clear();
-    rp.gfc_off.assign(rounds + 1, 0);
-    rp.gfwork_off.assign(rounds + 1, 0);
-    for (int r = 0; r < rounds; ++r) {
-        rp.gfc_off[r] = (int)rp.gfc.size();
-        rp.gfwork_off[r] = (int)rp.gfwork.size();
-        std::vector<int> idx;  // networks with trajectories in this round
-        for (int i = 0; i < nn; ++i)
-            if (rp.count[r][i] > 0) idx.push_back(i);
-        std::stable_sort(idx.begin(), idx.end(),
-                         [&](int a, int c) { return rp.count[r][a] > rp.count[r][c]; });
-        int ymax = 0;
-        for (int i : idx) {
-            const uint64_t e0 = first ? first[i] + (uint64_t)r * (uint64_t)step[i] : 0;
-            rp.gfc.push_back(gf_chunk(b->nets[i], e0, rp.count[r][i]));
-            ymax = std::max(ymax, gf_slot_blocks(b->nets[i]->K1));
-        }
-        for (int y = 0; y < ymax; ++y)
-            for (size_t j = 0; j < idx.size(); ++j) {
-                const gbs_net *net = b->nets[idx[j]];
-                if (y >= gf_slot_blocks(net->K1)) continue;
-                for (int q = 0; q < net->n_sub; ++q) rp.gfwork.push_back(make_int4((int)j, q, y, 0));
-            }
-    }
-    rp.gfc_off[rounds] = (int)rp.gfc.size();
-    rp.gfwork_off[rounds] = (int)rp.gfwork.size();
     rp.fold_net.assign(nn, 0);
     rp.fold = false;
     for (int i = 0; fold_net && i < nn; ++i) {
@@ -229,26 +187,7 @@ int upload_rounds(gbs_batch *b, const RoundPlan &rp) {
             b->prefix_cap = rp.prefix.size();
         }
     }
-    if (rp.gfc.size() > b->gfc_cap) {
-        if (b->d_gfc) cudaFree(b->d_gfc);
-        b->d_gfc = nullptr;
-        GBS_CUDA_TRY(cudaMalloc(&b->d_gfc, rp.gfc.size() * sizeof(GfChunk)));
-        b->gfc_cap = rp.gfc.size();
-    }
-    if (!b->d_gfnext) GBS_CUDA_TRY(cudaMalloc(&b->d_gfnext, sizeof(int)));
-    if (rp.gfwork.size() > b->gfwork_cap) {
-        if (b->d_gfwork) cudaFree(b->d_gfwork);
-        b->d_gfwork = nullptr;
-        GBS_CUDA_TRY(cudaMalloc(&b->d_gfwork, rp.gfwork.size() * sizeof(int4)));
-        b->gfwork_cap = rp.gfwork.size();
-    }
     GBS_CUDA_TRY(cudaStreamSynchronize(b->stream));
-    if (!rp.gfc.empty())
-        GBS_CUDA_TRY(cudaMemcpy(b->d_gfc, rp.gfc.data(), rp.gfc.size() * sizeof(GfChunk),
-                                cudaMemcpyHostToDevice));
-    if (!rp.gfwork.empty())
-        GBS_CUDA_TRY(cudaMemcpy(b->d_gfwork, rp.gfwork.data(), rp.gfwork.size() * sizeof(int4),
-                                cudaMemcpyHostToDevice));
     GBS_CUDA_TRY(cudaMemcpy(b->d_desc, rp.desc.data(), nd * sizeof(GemmNetDesc),
                             cudaMemcpyHostToDevice));
     if (!rp.tiles.empty())
@@ -326,20 +265,24 @@ int round_front(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *seeds,
     });
 }
 
-// Every network's finalize (per-network branches), then ONE generating-
-// function launch over all of the round's chunks.
-int round_back(gbs_batch *b, const RoundPlan &rp, int r, bool branches = false) {
-    int rc = per_network(b, rp, r, branches, [&](int i, gbs_net *net) {
-        return launch_finalize(net, rp.count[r][i]);
+// Every network's finalize and generating functions (per-network branches).
+// A single grouped generating-function launch per round over all networks'
+// chunks (a persistent kernel over a heaviest-first work list) was measured
+// 2 % slower per batch64 step (325 against 318 ms on one box): the branches
+// overlap one network's finalize with the others' generating functions, and
+// the grouped launch also walks the slot blocks past every chunk's window,
+// which the host cannot know.
+int round_back(gbs_batch *b, const RoundPlan &rp, int r, const uint64_t *first,
+               bool branches = false) {
+    return per_network(b, rp, r, branches, [&](int i, gbs_net *net) {
+        const uint64_t e0 = first[i] + (uint64_t)r * (uint64_t)rp.step[i];
+        int rc;
+        if ((rc = launch_finalize(net, rp.count[r][i]))) return rc;
+        prof_mark(net, GBS_PHASE_GF, 0, true);
+        if ((rc = launch_gf(net, e0, rp.count[r][i]))) return rc;
+        prof_mark(net, GBS_PHASE_GF, 1, false);
+        return (int)GBS_OK;
     });
-    if (rc) return rc;
-    gbs_net *n0 = b->nets[0];
-    prof_mark(n0, GBS_PHASE_GF, 0, true);
-    rc = launch_gf_grouped(b->stream, b->sm_count, b->d_gfc + rp.gfc_off[r],
-                           b->d_gfwork + rp.gfwork_off[r], rp.gfwork_off[r + 1] - rp.gfwork_off[r],
-                           b->d_gfnext);
-    if (!rc) prof_mark(n0, GBS_PHASE_GF, 1, false);
-    return rc;
 }
 
 // Folded rounds: the networks' operands swap roles after each round, so that
@@ -357,7 +300,7 @@ int run_rounds(gbs_batch *b, const RoundPlan &rp, const uint64_t *seeds, const u
     for (int r = 0; r < rp.rounds && rc == GBS_OK; ++r) {
         if ((rc = round_front(b, rp, r, seeds, first, branches))) break;
         if ((rc = round_gemm(b, rp, r, b->pair))) break;
-        if ((rc = round_back(b, rp, r, branches))) break;
+        if ((rc = round_back(b, rp, r, first, branches))) break;
         if (rp.fold) {
             swap_all(b, rp);
             ++swaps;
@@ -561,9 +504,6 @@ void gbs_free_batch(gbs_batch_t b) {
     if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->d_jobs) cudaFree(b->d_jobs);
     if (b->d_prefix) cudaFree(b->d_prefix);
-    if (b->d_gfc) cudaFree(b->d_gfc);
-    if (b->d_gfwork) cudaFree(b->d_gfwork);
-    if (b->d_gfnext) cudaFree(b->d_gfnext);
     for (cudaStream_t st : b->aux) cudaStreamDestroy(st);
     for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);

@@ -308,26 +308,6 @@ int launch_finalize(gbs_net *net, int64_t count);
 
 // Generating functions, summed per sub-ensemble into d_acc.
 int launch_gf(gbs_net *net, uint64_t e0, int64_t count);
-// One chunk's generating-function work (double-float kernel) for a grouped
-// launch over many networks.
-struct GfChunk {
-    const void *rec;  // the finalize kernel's per-trajectory records
-    const int *wmax;
-    int64_t count;
-    uint64_t e0;
-    int n_sub, K1;
-    const double2 *tw;
-    double2 *acc;
-    int64_t *counts;
-};
-GfChunk gf_chunk(gbs_net *net, uint64_t e0, int64_t count);
-// Slot blocks a chunk of a network with K1 points may need (the launch's
-// blocks past the chunk's union window return at once).
-int gf_slot_blocks(int K1);
-// One persistent launch over work items {chunk index, sub-ensemble, slot
-// block}, taken in list order through the counter at d_next (zeroed here).
-int launch_gf_grouped(cudaStream_t stream, int sm_count, const GfChunk *d_chunks,
-                      const int4 *d_work, int nwork, int *d_next);
 // Bytes per trajectory of the records the finalize kernel writes for the
 // double-float generating functions (d_gfrec).
 size_t gf_record_bytes();

@@ -543,33 +543,6 @@ __global__ void __launch_bounds__(kGfSlots * kGfGroups, 5)
     gf_df_block(rec, wmax, count, e0, n_sub, K1, tw, K, acc, counts, blockIdx.x, blockIdx.y, sh);
 }
 
-// The same block work for the chunks of many networks in one persistent
-// launch (a batch round): each block takes the next work item {chunk,
-// sub-ensemble, slot block} from a shared counter until the list is done.
-// The list is ordered heaviest first (every chunk's centre slot blocks
-// first); items past a chunk's union window, which the host cannot know,
-// return at once.  Every (chunk, sub-ensemble, k) is summed by exactly one
-// item, in the fixed order of gf_df_block, so the sums do not depend on
-// which block takes which item.
-__global__ void __launch_bounds__(kGfSlots * kGfGroups, 5)
-    k_gf_df_grouped(const GfChunk *__restrict__ chunks, const int4 *__restrict__ work, int nwork,
-                    int *__restrict__ next, const DfConsts K) {
-    __shared__ GfShared sh;
-    __shared__ int s_item;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
-        __syncthreads();
-        const int it = s_item;
-        __syncthreads();  // every thread has it before thread 0 takes the next one
-        if (it >= nwork) break;
-        const int4 w = work[it];
-        const GfChunk c = chunks[w.x];
-        gf_df_block(static_cast<const GfRec *>(c.rec), c.wmax, c.count, c.e0, c.n_sub, c.K1, c.tw,
-                    K, c.acc, c.counts, w.y, w.z, sh);
-        __syncthreads();  // the shared staging is free for the next item
-    }
-}
-
 }  // namespace
 
 // Float pieces of ln 2 and pi/2 for exact Cody-Waite products (12
@@ -658,43 +631,6 @@ int launch_gf(gbs_net *net, uint64_t e0, int64_t count) {
     }
     GBS_LAUNCH_CHECK();
     return GBS_OK;
-}
-
-int launch_gf_grouped(cudaStream_t stream, int sm_count, const GfChunk *d_chunks,
-                      const int4 *d_work, int nwork, int *d_next) {
-    if (nwork <= 0) return GBS_OK;
-    static const DfConsts K = make_df_consts();
-    static int per_sm = 0;
-    if (!per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gf_df_grouped,
-                                                          kGfSlots * kGfGroups, 0) != cudaSuccess ||
-            per_sm < 1) {
-            cudaGetLastError();
-            per_sm = 1;
-        }
-    }
-    const int blocks = std::min(nwork, per_sm * sm_count);
-    GBS_CUDA_TRY(cudaMemsetAsync(d_next, 0, sizeof(int), stream));
-    k_gf_df_grouped<<<blocks, kGfSlots * kGfGroups, 0, stream>>>(d_chunks, d_work, nwork, d_next,
-                                                                 K);
-    GBS_LAUNCH_CHECK();
-    return GBS_OK;
-}
-
-int gf_slot_blocks(int K1) { return (K1 + kGfSlots - 1) / kGfSlots; }
-
-GfChunk gf_chunk(gbs_net *net, uint64_t e0, int64_t count) {
-    GfChunk c;
-    c.rec = net->d_gfrec;
-    c.wmax = net->d_wmax;
-    c.count = count;
-    c.e0 = e0;
-    c.n_sub = net->n_sub;
-    c.K1 = net->K1;
-    c.tw = net->d_tw;
-    c.acc = net->d_acc;
-    c.counts = net->d_counts;
-    return c;
 }
 
 size_t gf_record_bytes() { return sizeof(GfRec); }
