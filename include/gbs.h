@@ -310,7 +310,9 @@ int gbs_debug_samples(gbs_net_t net, uint64_t seed, uint64_t e0, int64_t count, 
  * generating-function work): w[2*count] as (w1, w2) per trajectory, host;
  * the terms e^{(z_k-1) n_S} are evaluated for the k within w1 of k = 0 and
  * matrix-P's e^{-(z_k-1) n_S - 2n} for the k within w2 of k = K1/2 (cyclic
- * distance; -1 = none, >= K1/2 = every k), every term outside below 2^-60.
+ * distance; -1 = none, >= K1/2 = every k), every term outside below 2^-60
+ * (GBS_FP64) or 2^-47 (the BF16 split paths, whose double-float evaluation
+ * rounds terms of order one to 2^-46).
  * Needs K1 fixed by a gbs_sample call.  Does not touch the sub-ensemble
  * sums.  Synchronises.  Errors: EINVAL, ECUDA.
  */
@@ -477,17 +479,16 @@ int gbs_profile_read(gbs_net_t net, double *ms, int64_t *launches);
 
 /*
  * gbs_measure_fp64_rate -- instrumentation, not part of the method: the
- * device's FP64 fused multiply-add peak in TFLOP/s (2 FLOP per FMA) at its
- * maximum SM clock.  A kernel of independent FMA chains (outer-product
- * updates into 8, 16 or 32 accumulators per thread, 2 to 8 blocks of 256
- * threads per SM) counts the FMAs each SM completes per cycle of its own
- * clock (clock64 from its first block's start to its last block's end), so
- * the figure does not depend on the clock the probe ran at; the mean over
- * SMs, the best over those configurations (3 launches each
- * after a warm-up launch), times the SM count and the maximum clock.  It is
- * the peak against which the FP64 path's propagation (k_gemm_fp64, bound by
- * that rate) is reported.  Allocates small buffers (stream-ordered) and
- * synchronises `stream`.  Errors: EINVAL (NULL tflops), ECUDA.
+ * device's FP64 fused multiply-add rate in TFLOP/s (2 FLOP per FMA), timed
+ * with CUDA events on `stream`.  Kernels of independent FMA chains (8, 16
+ * or 32 accumulators per thread, 2 to 8 blocks of 256 threads per SM; as
+ * outer-product updates with distinct operand registers and as recurrences
+ * sharing one multiplier and addend) run 3 times each after a warm-up
+ * launch; the best rate is returned.  It is the peak against which the FP64
+ * path's propagation (k_gemm_fp64, bound by that rate) is reported, at the
+ * clock the device ran the probe at.  Allocates small buffers
+ * (stream-ordered) and synchronises `stream`.  Errors: EINVAL (NULL
+ * tflops), ECUDA.
  */
 int gbs_measure_fp64_rate(void *stream, double *tflops);
 

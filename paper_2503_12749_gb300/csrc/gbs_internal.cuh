@@ -38,8 +38,11 @@ const char *error_message();
 // Constants
 // ---------------------------------------------------------------------------
 // Terms of a generating function whose log-magnitude is below -60 ln 2
-// (|term| < 2^-60) are not evaluated.
-constexpr double kSkipLog = 41.58883083359672;  // 60 * ln 2
+// (|term| < 2^-60) are not evaluated by the FP64 kernels; the double-float
+// kernel, whose own rounding of terms of order one is 2^-46, skips those
+// below 2^-47 (each skipped term moves every P(m) by less than 2^-47 / K1).
+constexpr double kSkipLog = 41.58883083359672;    // 60 * ln 2
+constexpr double kSkipLogDf = 32.57791748631743;  // 47 * ln 2
 constexpr int kFp64TileModes = 64;              // output modes per FP64 GEMM tile
 constexpr int kFp64TileSamples = 32;            // samples per FP64 GEMM tile
 constexpr int kTcTileModes = 64;                // output modes per tcgen05 tile (128 A rows)

@@ -132,40 +132,47 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const double *__restrict__ T6
 }
 
 // FP64 FMA throughput probe: kChains independent accumulators per thread,
-// each step an outer-product update acc[a][b] += x[a] y[b] (the register
-// pattern of a GEMM's inner loop, distinct operand registers), `iters` steps;
-// the sums are stored so that nothing is eliminated.
-template <int kChains>
-__global__ void __launch_bounds__(256) k_dfma_rate(double *__restrict__ out,
-                                                  long long *__restrict__ cycles, int iters) {
+// `iters` steps; the sums are stored so that nothing is eliminated.
+// kOuter: each step is an outer-product update acc[a][b] += x[a] y[b] (the
+// register pattern of a GEMM's inner loop); otherwise every chain steps
+// acc = acc m + c with the same m and c (operands shared by consecutive
+// instructions).
+template <int kChains, bool kOuter>
+__global__ void __launch_bounds__(256) k_dfma_rate(double *__restrict__ out, int iters) {
     constexpr int kA = kChains / 4;
-    const long long c0 = clock64();
     double x[kA], y[4], acc[kChains];
 #pragma unroll
     for (int a = 0; a < kA; ++a) x[a] = 1.0 + 1e-3 * a + 1e-9 * threadIdx.x;
 #pragma unroll
     for (int b = 0; b < 4; ++b) y[b] = 1e-7 * (b + 1);
 #pragma unroll
-    for (int q = 0; q < kChains; ++q) acc[q] = 0.0;
+    for (int q = 0; q < kChains; ++q) acc[q] = kOuter ? 0.0 : 1e-3 * q + 1e-9 * threadIdx.x;
+    const double m = 0.999999 + 1e-12 * threadIdx.x, c = 1e-7;
 #pragma unroll 2
     for (int i = 0; i < iters; ++i) {
+        if (kOuter) {
 #pragma unroll
-        for (int a = 0; a < kA; ++a)
+            for (int a = 0; a < kA; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a * 4 + b] = fma(x[a], y[b], acc[a * 4 + b]);
+                for (int b = 0; b < 4; ++b) acc[a * 4 + b] = fma(x[a], y[b], acc[a * 4 + b]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kChains; ++q) acc[q] = fma(acc[q], m, c);
+        }
     }
     double s = 0.0;
 #pragma unroll
     for (int q = 0; q < kChains; ++q) s += acc[q];
     out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t sm;
-        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
-        cycles[3 * blockIdx.x] = sm;
-        cycles[3 * blockIdx.x + 1] = c0;
-        cycles[3 * blockIdx.x + 2] = clock64();
-    }
+}
+
+template <int kChains>
+void launch_dfma_rate(bool outer, int blocks, int threads, cudaStream_t st, double *out,
+                      int iters) {
+    if (outer)
+        k_dfma_rate<kChains, true><<<blocks, threads, 0, st>>>(out, iters);
+    else
+        k_dfma_rate<kChains, false><<<blocks, threads, 0, st>>>(out, iters);
 }
 
 }  // namespace
@@ -190,69 +197,51 @@ using namespace gbs;
 extern "C" int gbs_measure_fp64_rate(void *stream, double *tflops) {
     if (!tflops) return set_error(GBS_EINVAL, "tflops is NULL");
     *tflops = 0.0;
-    int dev = 0, sms = 0, khz = 0;
+    int dev = 0, sms = 0;
     GBS_CUDA_TRY(cudaGetDevice(&dev));
     GBS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    GBS_CUDA_TRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int threads = 256, iters = 1 << 13, max_blocks = 8 * sms;
+    const int threads = 256, iters = 1 << 12, max_blocks = 8 * sms;
     double *out = nullptr;
-    long long *cyc = nullptr;
     GBS_CUDA_TRY(cudaMallocAsync(&out, sizeof(double) * max_blocks * threads, st));
-    GBS_CUDA_TRY(cudaMallocAsync(&cyc, sizeof(long long) * 3 * max_blocks, st));
-    std::vector<long long> h((size_t)3 * max_blocks);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
     int rc = GBS_OK;
+    if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess)
+        rc = set_error(GBS_ECUDA, "event creation failed");
     double best = 0.0;
-    // configurations: (accumulators per thread, blocks per SM); per launch
-    // and SM the FMAs its blocks completed over the cycles of its own clock
-    // from the first block's start to the last block's end (clock64 and
-    // %smid recorded per block), so the rate does not depend on the clock the
-    // probe happened to run at; the mean over SMs, the best over the
-    // configurations and 3 launches each after a warm-up launch, at the
-    // device's maximum clock
-    const int cfg[6][2] = {{8, 4}, {8, 8}, {16, 4}, {16, 8}, {32, 2}, {32, 3}};
-    for (int c = 0; c < 6 && rc == GBS_OK; ++c) {
-        const int chains = cfg[c][0], per_sm = cfg[c][1], blocks = per_sm * sms;
-        for (int rep = 0; rep < 4; ++rep) {
+    // configurations: (operand pattern, accumulators per thread, blocks per
+    // SM); each timed with CUDA events on `stream` over 3 launches after a
+    // warm-up launch; the best rate over all of them
+    const int cfg[8][3] = {{1, 8, 4}, {1, 16, 4}, {1, 16, 8}, {1, 32, 2},
+                           {0, 8, 4}, {0, 8, 8}, {0, 16, 4}, {0, 16, 8}};
+    for (int c = 0; c < 8 && rc == GBS_OK; ++c) {
+        const bool outer = cfg[c][0] != 0;
+        const int chains = cfg[c][1], blocks = cfg[c][2] * sms;
+        for (int rep = 0; rep < 4 && rc == GBS_OK; ++rep) {
+            cudaEventRecord(ev[0], st);
             if (chains == 8)
-                k_dfma_rate<8><<<blocks, threads, 0, st>>>(out, cyc, iters);
+                launch_dfma_rate<8>(outer, blocks, threads, st, out, iters);
             else if (chains == 16)
-                k_dfma_rate<16><<<blocks, threads, 0, st>>>(out, cyc, iters);
+                launch_dfma_rate<16>(outer, blocks, threads, st, out, iters);
             else
-                k_dfma_rate<32><<<blocks, threads, 0, st>>>(out, cyc, iters);
-            if (cudaMemcpyAsync(h.data(), cyc, sizeof(long long) * 3 * blocks,
-                                cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess) {
+                launch_dfma_rate<32>(outer, blocks, threads, st, out, iters);
+            cudaEventRecord(ev[1], st);
+            float ms = 0.0f;
+            if (cudaEventSynchronize(ev[1]) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) {
                 rc = set_error(GBS_ECUDA, "FP64 rate probe failed: %s",
                                cudaGetErrorString(cudaGetLastError()));
                 break;
             }
-            // %smid numbers the physical SMs (not necessarily 0 .. sms - 1)
-            constexpr int kMaxSmId = 1024;
-            std::vector<long long> lo(kMaxSmId, LLONG_MAX), hi(kMaxSmId, LLONG_MIN);
-            std::vector<int> nb(kMaxSmId, 0);
-            for (int q = 0; q < blocks; ++q) {
-                const long long sm = h[3 * q];
-                if (sm < 0 || sm >= kMaxSmId) continue;
-                lo[sm] = std::min(lo[sm], h[3 * q + 1]);
-                hi[sm] = std::max(hi[sm], h[3 * q + 2]);
-                ++nb[sm];
-            }
-            double sum = 0.0;
-            int used = 0;
-            for (int q = 0; q < kMaxSmId; ++q)
-                if (nb[q] > 0 && hi[q] > lo[q]) {
-                    sum += (double)chains * iters * threads * nb[q] / (double)(hi[q] - lo[q]);
-                    ++used;
-                }
-            const double fma_per_clk_sm = used ? sum / used : 0.0;
-            const double rate = 2.0 * fma_per_clk_sm * sms * (double)khz * 1e3 / 1e12;
+            const double fmas = (double)chains * iters * threads * blocks;
+            const double rate = ms > 0.0f ? 2.0 * fmas / (ms * 1e-3) / 1e12 : 0.0;
             if (rep > 0 && rate > best) best = rate;  // rep 0 warms up
         }
     }
     if (rc == GBS_OK) *tflops = best;
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
     cudaFreeAsync(out, st);
-    cudaFreeAsync(cyc, st);
     cudaStreamSynchronize(st);
     return rc;
 }

@@ -11,18 +11,19 @@
 //   G_mP = [e^{l1 + c1} e^{i phi} + e^{-l1 + c2} e^{-i phi}] / (1 + e^{-2|n|}),
 //   c1 = min(0, 2n),  c2 = -2 max(n, 0),
 //   G_+P = e^{l1} e^{i phi}.
-// Terms below 2^-60 are skipped: per trajectory, finalize() derives from
-// (n, x, y) two windows of k (around theta = 0 for the e^{l1} terms, around
-// theta = pi for the e^{-l1} term) outside which each term is provably
-// smaller than 2^-60, using |sin theta| <= sqrt(2 (1 - cos theta)).
+// Terms below 2^-60 (FP64 kernel) or 2^-47 (double-float kernel) are
+// skipped: per trajectory, finalize() derives from (n, x, y) two windows of
+// k (around theta = 0 for the e^{l1} terms, around theta = pi for the
+// e^{-l1} term) outside which each term is provably smaller than that,
+// using |sin theta| <= sqrt(2 (1 - cos theta)).
 //
 // Work split (FP64 kernel): one thread per k, one block per (256
 // consecutive k, sub-ensemble r); each thread loops over the sub-ensemble's
 // trajectories of the chunk in increasing order and adds its sums to
 // acc[est][r][k], so every sum is formed in a fixed order (bitwise
-// reproducible for a fixed chunking).  The double-float kernel splits each
-// k's trajectories over 4 warps (see k_gf_df).  Trajectory e belongs to
-// sub-ensemble e mod n_sub.
+// reproducible for a fixed chunking).  The double-float kernel gives each
+// lane the mirror pair k, K1 - k and splits the trajectories over 8
+// half-warps (see k_gf_df).  Trajectory e belongs to sub-ensemble e mod n_sub.
 #include "gbs_internal.cuh"
 #include "dfloat.cuh"
 
@@ -43,8 +44,7 @@ __device__ __forceinline__ int half_width(double cstar, int K1) {
     return w >= (double)half ? half : (int)w;
 }
 
-__device__ __forceinline__ Window windows_for(double n, double x, double y, int K1) {
-    const double T = kSkipLog;
+__device__ __forceinline__ Window windows_for(double n, double x, double y, int K1, double T) {
     const double ay = fabs(y);
     const int half = K1 >> 1;
     Window w;
@@ -98,7 +98,7 @@ __global__ void k_finalize(const double2 *__restrict__ part, int mtiles, int64_t
         }
         nS[i] = make_double2(re, im);
         const double nn = n[i];
-        const Window w = windows_for(nn, re, im, K1);
+        const Window w = windows_for(nn, re, im, K1, rec ? kSkipLogDf : kSkipLog);
         win[i] = w;
         if (rec) {
             GfRec g;
@@ -325,69 +325,202 @@ __device__ __forceinline__ void small_term(df l1, df ph, const DfConsts &K, floa
     im = fmaf(m, s1, im);
 }
 
-// k of slot i: slots enumerate the union window around theta = 0
-// (k = -W1..W1 mod K1) and then the one around theta = pi (K1/2-W2..K1/2+W2);
-// when the two cover the circle the mapping is k = i.  Returns -1 past the end.
-__device__ __forceinline__ int slot_to_k(int i, int K1, int W1, int W2) {
+// Mirror pairs.  theta_{K1-k} = -theta_k, so with
+//   a = (cos theta - 1) x,  b = sin theta y,  c = sin theta x,  d = (cos theta - 1) y
+// the exponents at k and K1 - k are
+//   (z_k - 1) n_S      = (a - b) + i (c + d),
+//   (z_{K1-k} - 1) n_S = (a + b) + i (d - c),
+// and both terms share E = e^a e^{ic}:
+//   e^{(z_k - 1) n_S}      = E       e^{-b + i d},
+//   e^{(z_{K1-k} - 1) n_S} = conj(E) e^{ b + i d}.
+// n_S is real for uniform loss (T = t U: alpha'.beta' = t^2 alpha.beta) up
+// to the GEMM's rounding, so b and d are usually tiny and e^{-+b + i d} is
+// a three-term series: one table-driven complex exponential serves both k.
+// Every lane of the double-float kernel holds such a pair of k.
+
+// e^w for w = u + i v (double-float parts, |u.hi|, |v.hi| <= 2^-13, so
+// |w| <= 2^-12.5): 1 + w + w^2 (1/2 + w/6), remainder below |w|^4/23 <
+// 2^-54; the terms beyond w in FP32 (|w^2/2| <= 2^-26, rounding below
+// 2^-49).  Returns (re, im).
+__device__ __forceinline__ df2 cexp_tiny(df u, df v) {
+    const float ur = u.hi, vi = v.hi;
+    const float w2r = fmaf(ur, ur, -vi * vi), w2i = 2.0f * ur * vi;
+    const float hr = fmaf(ur, 1.0f / 6.0f, 0.5f), hv = vi * (1.0f / 6.0f);
+    const float tr = fmaf(w2r, hr, -w2i * hv), ti = fmaf(w2r, hv, w2i * hr);
+    const df s = df_two_sum(1.0f, ur);  // exact
+    // |ti| <= 2^-12.9 |v.hi|, so v.hi leads the imaginary part
+    return df2_make(df_fast_two_sum(s.hi, s.lo + (u.lo + tr)),
+                    df_fast_two_sum(vi, v.lo + ti));
+}
+
+// (p.x + i p.y) (q.x + i q.y) in double-float.
+__device__ __forceinline__ df2 cmul_df2(df2 p, df2 q) {
+    const df2 s = df2_mul(p, df2_make(df2_x(q), df2_x(q)));                // (px qx, py qx)
+    df2 t = df2_mul(df2_make(df2_y(p), df2_x(p)), df2_make(df2_y(q), df2_y(q)));  // (py qy, px qy)
+    t.hi.x = -t.hi.x;
+    t.lo.x = -t.lo.x;
+    return df2_add(s, t);
+}
+
+// Pair slots of the union window: slot s holds k = s and K1 - s for
+// s = 0..W1 (around theta = 0), then k = K1/2 + s and K1/2 - s for
+// s = 0..W2 (around theta = pi); when the two windows cover the circle,
+// s = 0..K1/2.  k = 0 and k = K1/2 pair with themselves.
+__device__ __forceinline__ int pair_slot_count(int K1, int W1, int W2, bool &whole) {
     const int half = K1 >> 1;
     const int n1 = W1 >= half ? K1 : 2 * W1 + 1;
     const int n2 = W2 < 0 ? 0 : (W2 >= half ? K1 : 2 * W2 + 1);
-    if (n1 + n2 >= K1) return i < K1 ? i : -1;
-    if (i < n1) {
-        const int k = i - W1;
-        return k < 0 ? k + K1 : k;
-    }
-    if (i < n1 + n2) return half - W2 + (i - n1);
-    return -1;
+    whole = n1 + n2 >= K1;
+    if (whole) return half + 1;
+    return (W1 < 0 ? 0 : W1 + 1) + (W2 < 0 ? 0 : W2 + 1);
 }
 
-constexpr int kGfSlots = 32;   // k slots per block (the lanes of each warp)
-constexpr int kGfGroups = 4;   // trajectory groups per block, one warp each
-constexpr int kGfTile = 128;   // trajectories per flush of the double-float partials
-
-// Slot blocks of the union window in order of distance from the block
-// holding k = 0 (ties: the lower first): the blocks near k = 0 carry a term
-// for every trajectory, the outer ones only for the trajectories with the
-// widest windows.  Returns the y-th block, or -1 past the last.
-__device__ __forceinline__ int slot_block(int y, int K1, int W1, int W2) {
+// (k, K1 - k) of pair slot i (whole: the windows cover the circle), or
+// kp = -1 past the end.
+__device__ __forceinline__ void pair_slot_to_k(int i, int K1, int W1, int W2, bool whole, int &kp,
+                                               int &km) {
     const int half = K1 >> 1;
-    const int n1 = W1 >= half ? K1 : 2 * W1 + 1;
-    const int n2 = W2 < 0 ? 0 : (W2 >= half ? K1 : 2 * W2 + 1);
-    const int slots = (n1 + n2 >= K1) ? K1 : n1 + n2;
-    const int nb = (slots + kGfSlots - 1) / kGfSlots;
-    if (y >= nb) return -1;
-    const int cb = (n1 + n2 >= K1) ? 0 : min(W1 / kGfSlots, nb - 1);
-    int cnt = 0;
-    for (int d = 0; d < nb; ++d) {
-        if (cb - d >= 0) {
-            if (cnt == y) return cb - d;
-            ++cnt;
+    kp = km = -1;
+    if (whole) {
+        if (i <= half) {
+            kp = i;
+            km = (K1 - i) & (K1 - 1);
         }
-        if (d > 0 && cb + d < nb) {
-            if (cnt == y) return cb + d;
-            ++cnt;
-        }
+        return;
     }
-    return -1;
+    const int p1 = W1 < 0 ? 0 : W1 + 1;
+    const int p2 = W2 < 0 ? 0 : W2 + 1;
+    if (i < p1) {
+        kp = i;
+        km = (K1 - i) & (K1 - 1);
+    } else if (i < p1 + p2) {
+        kp = half + (i - p1);
+        km = half - (i - p1);
+    }
 }
 
-// One block per (32 consecutive slots of the union window, sub-ensemble r):
-// the 4 warps hold the same 32 k and split the sub-ensemble's trajectories
-// (trajectory q to warp q mod 4), so they carry the same work and need no
-// barrier until the final fixed-order sum of their 4 partials.  Each warp
-// stages its own 32 trajectories of a 128-trajectory tile (records written
-// by the finalize kernel) and walks them in order, flushing its
-// double-float partials to FP64 after each tile.  Grid: x = sub-ensemble
-// (fast), y = slot block from the window's centre outwards, so the
-// heaviest blocks start first and the last wave holds the lightest.
+constexpr int kGfSlots = 16;   // pair slots per block (the lanes of each half-warp)
+#ifndef GBS_GF_MINBLOCKS
+#define GBS_GF_MINBLOCKS 5     // resident blocks per SM the register budget is sized for
+#endif
+constexpr int kGfGroups = 8;   // trajectory groups per block, one half-warp each
+constexpr int kGfPer = 32;     // trajectories per half-warp between flushes to FP64
+constexpr int kGfTile = kGfGroups * kGfPer;  // trajectories per tile
+
+// Double-float partial sums of one k over the trajectories of one tile.
+struct SidePartial {
+    df2 both;                         // terms common to both estimators (re, im)
+    df pm_re, pm_im, pp_re, pp_im;    // general formulas: matrix-P, +P
+    float sm_re, sm_im;               // terms below 2^-27, both estimators
+    bool gen;                         // a general-formula term was added
+};
+
+__device__ __forceinline__ void side_clear(SidePartial &s) {
+    s.both = {f2(0.0f, 0.0f), f2(0.0f, 0.0f)};
+    s.pm_re = s.pm_im = s.pp_re = s.pp_im = df{0.0f, 0.0f};
+    s.sm_re = s.sm_im = 0.0f;
+    s.gen = false;
+}
+
+// The lane's FP64 sums in shared memory, f[c * kGfSlots]: c = 0, 1 the
+// terms common to both estimators (re, im), c = 2, 3 matrix-P's own, c = 4,
+// 5 +P's own; matrix-P's generating function is the sum of c = 0, 1 and 2,
+// 3, +P's of c = 0, 1 and 4, 5.
+constexpr int kGfSums = 6;
+
+// One (trajectory, k) term with exponent (l1, ph) = (z_k - 1) n_S: FP64
+// outside the double-float ranges (straight into the lane's FP64 sums f),
+// FP32 below 2^-27, the term shared by both estimators when `plain`, else
+// the general formulas.  (cm1d, snd) = (cos theta_k - 1, sin theta_k) in
+// FP64.
+__device__ __forceinline__ void side_term(df l1, df ph, bool in1, bool in2, bool plain,
+                                          const GfRec &g, double cm1d, double snd,
+                                          const DfTables &T, const DfConsts &K, SidePartial &s,
+                                          double *f) {
+    const df c1 = g.c1;
+    df a1 = l1, a2 = {0.0f, 0.0f};
+    bool big = fabsf(ph.hi) >= 6000.0f || (in1 && l1.hi >= 80.0f);
+    if (!plain) {
+        a1 = df_add(l1, c1);
+        a2 = df_add(df_neg(l1), g.c2);
+        big = big || (in1 && a1.hi >= 80.0f) || (in2 && a2.hi >= 80.0f);
+    }
+    if (big) {
+        // outside the double-float ranges (+P heavy tail, huge phases):
+        // this term in FP64, straight into the FP64 sums
+        const double xd = g.xd, yd = g.yd;
+        const double l1d = cm1d * xd - snd * yd;
+        double sd, cd;
+        sincos(snd * xd + cm1d * yd, &sd, &cd);
+        double e1d = 0.0, e2d = 0.0;
+        if (in1) {
+            e1d = exp(l1d + g.c1d);
+            const double gp = (g.c1d == 0.0) ? e1d : exp(l1d);
+            f[4 * kGfSlots] += gp * cd;
+            f[5 * kGfSlots] += gp * sd;
+        }
+        if (in2) e2d = exp(-l1d + g.c2d);
+        const double dinv = df_to_double(g.inv);
+        f[2 * kGfSlots] += (e1d + e2d) * cd * dinv;
+        f[3 * kGfSlots] += (e1d - e2d) * sd * dinv;
+        return;
+    }
+    if (plain && l1.hi < kSmallLog) {
+        small_term(l1, ph, K, s.sm_re, s.sm_im);
+        return;
+    }
+    if (plain) {
+        s.both = df2_add(s.both, cexp_pair(l1, ph, T, K));
+        return;
+    }
+    df sp, cp;
+    df_sincos_tab(ph, T, K, sp, cp);
+    df e1 = {0.0f, 0.0f}, e2 = {0.0f, 0.0f};
+    s.gen = true;
+    if (in1) {
+        e1 = df_exp_small(a1, T, K);
+        const df gp = (c1.hi == 0.0f) ? e1 : df_exp_small(l1, T, K);
+        s.pp_re = df_add(s.pp_re, df_mul(gp, cp));
+        s.pp_im = df_add(s.pp_im, df_mul(gp, sp));
+    }
+    if (in2) e2 = df_exp_small(a2, T, K);
+    s.pm_re = df_add(s.pm_re, df_mul(df_mul(df_add(e1, e2), g.inv), cp));
+    s.pm_im = df_add(s.pm_im, df_mul(df_mul(df_sub(e1, e2), g.inv), sp));
+}
+
+// A tile's partials into the lane's FP64 sums f.  GB300's FP64 pipe is
+// narrow, so the FP32 small-term sums join the double-float partials on the
+// FP32 pipes, and the general formulas' partials are converted only when
+// used.
+__device__ __forceinline__ void side_flush(const SidePartial &s, double *f) {
+    f[0] += df_to_double(df_add_f(df2_x(s.both), s.sm_re));
+    f[kGfSlots] += df_to_double(df_add_f(df2_y(s.both), s.sm_im));
+    if (s.gen) {
+        f[2 * kGfSlots] += df_to_double(s.pm_re);
+        f[3 * kGfSlots] += df_to_double(s.pm_im);
+        f[4 * kGfSlots] += df_to_double(s.pp_re);
+        f[5 * kGfSlots] += df_to_double(s.pp_im);
+    }
+}
+
+// One block per (16 pair slots of the union window, sub-ensemble r): the 8
+// half-warps hold the same 32 k and split the sub-ensemble's trajectories
+// (trajectory q to half-warp q mod 8), so they carry the same work and need
+// no barrier until the final fixed-order sum of their 8 partials.  Each
+// warp stages the 64 trajectories of its two half-warps in a 256-trajectory
+// tile (records written by the finalize kernel); each half-warp walks its
+// 32 in order, flushing its double-float partials to FP64 after each tile.
+// Grid: x = sub-ensemble (fast), y = block of pair slots from k = 0
+// outwards, so the heaviest blocks start first and the last wave holds the
+// lightest; blocks of 16 pair slots (32 k) keep that tail short.
 struct GfShared {
-    GfRec rec[kGfGroups][32];
-    double red[kGfGroups][4][kGfSlots];
+    GfRec rec[kGfGroups / 2][2 * kGfPer];  // per warp: its two half-warps' trajectories
+    double sum[kGfGroups][2][kGfSums][kGfSlots];  // FP64 sums: [group][k, K1 - k][c]
     DfTables tab;
 };
 
-// One block's work: sub-ensemble r, slot block y (in order of weight) of one
-// chunk of one network.
+// One block's work: sub-ensemble r, pair-slot block y of one chunk of one
+// network.
 __device__ __forceinline__ void gf_df_block(const GfRec *__restrict__ rec,
                                             const int *__restrict__ wmax, int64_t count,
                                             uint64_t e0, int n_sub, int K1,
@@ -395,147 +528,134 @@ __device__ __forceinline__ void gf_df_block(const GfRec *__restrict__ rec,
                                             double2 *__restrict__ acc,
                                             int64_t *__restrict__ counts, int r, int y,
                                             GfShared &sh) {
-    auto &s_rec = sh.rec;
-    auto &s_red = sh.red;
-    auto &s_tab = sh.tab;
     const int W1 = wmax[0], W2 = wmax[1];
     const int lane = threadIdx.x & 31;
-    const int grp = threadIdx.x >> 5;
+    const int slot = threadIdx.x & (kGfSlots - 1);
+    const int grp = threadIdx.x / kGfSlots;  // half-warp
+    const int warp = threadIdx.x >> 5;
     const int64_t first = (int64_t)(((uint64_t)r + (uint64_t)n_sub - e0 % (uint64_t)n_sub) %
                                     (uint64_t)n_sub);
     const int64_t cnt_r = first < count ? (count - 1 - first) / n_sub + 1 : 0;
-    const int sb = slot_block(y, K1, W1, W2);
-    if (sb < 0) return;  // past the union window (block 0 always exists)
-    const int k = slot_to_k(sb * kGfSlots + lane, K1, W1, W2);
-    const bool kvalid = k >= 0;
-    const int d0 = kvalid ? dist0(k, K1) : 0x3fffffff;
-    const int dpi = kvalid ? dist_pi(k, K1) : 0x3fffffff;
+    bool whole;
+    const int nslots = pair_slot_count(K1, W1, W2, whole);
+    if (y * kGfSlots >= nslots && y > 0) return;  // past the union window (block 0 always runs)
+    int kp, km;
+    pair_slot_to_k(y * kGfSlots + slot, K1, W1, W2, whole, kp, km);
+    const bool kvalid = kp >= 0;
+    const bool self = kp == km;  // k = 0 or K1/2
+    const int d0 = kvalid ? dist0(kp, K1) : 0x3fffffff;     // the same for km
+    const int dpi = kvalid ? dist_pi(kp, K1) : 0x3fffffff;
     for (int t = threadIdx.x; t < 64; t += blockDim.x)
-        s_tab.exp2[t] = df{K.exp2_hi[t], K.exp2_lo[t]};
+        sh.tab.exp2[t] = df{K.exp2_hi[t], K.exp2_lo[t]};
     for (int t = threadIdx.x; t < 33; t += blockDim.x) {
-        s_tab.sn[t] = df{K.sin_hi[t], K.sin_lo[t]};
-        s_tab.cs[t] = df{K.cos_hi[t], K.cos_lo[t]};
+        sh.tab.sn[t] = df{K.sin_hi[t], K.sin_lo[t]};
+        sh.tab.cs[t] = df{K.cos_hi[t], K.cos_lo[t]};
     }
+    double *fp = sh.sum[grp][0][0] + slot;  // f[c] at fp[c * kGfSlots]
+    double *fm = sh.sum[grp][1][0] + slot;
+#pragma unroll
+    for (int c = 0; c < kGfSums; ++c) fp[c * kGfSlots] = fm[c * kGfSlots] = 0.0;
     __syncthreads();
 
-    const double2 t = kvalid ? tw[k] : make_double2(0.0, 0.0);
+    const double2 t = kvalid ? tw[kp] : make_double2(0.0, 0.0);
     const double cm1d = t.x, snd = t.y;
     const df cm1 = df_from_double(t.x), sn = df_from_double(t.y);
     const df2 cs_pair = df2_make(cm1, sn), sc_pair = df2_make(sn, cm1);
-    double am_re = 0.0, am_im = 0.0, ap_re = 0.0, ap_im = 0.0;
-    GfRec *mine = s_rec[grp];
+    const GfRec *mine = sh.rec[warp] + kGfPer * (lane / kGfSlots);
 
     for (int64_t base = 0; base < cnt_r; base += kGfTile) {
-        const int64_t q = base + grp + 4 * lane;
-        if (q < cnt_r) mine[lane] = rec[first + q * n_sub];
+#pragma unroll
+        for (int e = lane; e < 2 * kGfPer; e += 32) {
+            // entry e: trajectory j = e mod kGfPer of half-warp 2 warp + e / kGfPer
+            const int64_t q = base + 2 * warp + e / kGfPer + kGfGroups * (e % kGfPer);
+            if (q < cnt_r) sh.rec[warp][e] = rec[first + q * n_sub];
+        }
         __syncwarp();
         const int ntile = (cnt_r - base) < kGfTile ? (int)(cnt_r - base) : kGfTile;
         const int nmine = ntile > grp ? (ntile - grp + kGfGroups - 1) / kGfGroups : 0;
         if (kvalid) {
-            df pm_re = {0.0f, 0.0f}, pm_im = {0.0f, 0.0f}, pp_re = {0.0f, 0.0f},
-               pp_im = {0.0f, 0.0f};
-            df2 pb = {f2(0.0f, 0.0f), f2(0.0f, 0.0f)};  // terms of both estimators (re, im)
-            float sm_re = 0.0f, sm_im = 0.0f;  // small terms of both estimators
+            SidePartial sp_, sm_;
+            side_clear(sp_);
+            side_clear(sm_);
             for (int m = 0; m < nmine; ++m) {
                 const GfRec &g = mine[m];
                 const bool in1 = d0 <= g.w1;
                 const bool in2 = dpi <= g.w2;
                 if (!(in1 || in2)) continue;
-                // (l1, phi) = ((cos-1) x - sin y, sin x + (cos-1) y), side by side
+                // (a, c) = (cos - 1, sin) x and (b, d) = (sin, cos - 1) y
                 const df2 A = df2_mul(cs_pair, df2_make(g.x, g.x));
-                df2 B = df2_mul(sc_pair, df2_make(g.y, g.y));
-                B.hi.x = -B.hi.x;
-                B.lo.x = -B.lo.x;
-                const df2 lp = df2_add(A, B);
-                const df l1 = df2_x(lp), ph = df2_y(lp);
-                const df c1 = g.c1;
-                const df inv = g.inv;
+                const df2 B = df2_mul(sc_pair, df2_make(g.y, g.y));
                 // n >= 0 with e^{-2n} below double rounding and no term near
                 // theta = pi: both estimators add e^{l1} e^{i phi} (the
                 // general formulas give the same value), summed once
-                const bool plain = in1 && !in2 && c1.hi == 0.0f && inv.hi == 1.0f && inv.lo == 0.0f;
-                df a1 = l1, a2 = {0.0f, 0.0f};
-                bool big = fabsf(ph.hi) >= 6000.0f || (in1 && l1.hi >= 80.0f);
-                if (!plain) {
-                    a1 = df_add(l1, c1);
-                    a2 = df_add(df_neg(l1), g.c2);
-                    big = big || (in1 && a1.hi >= 80.0f) || (in2 && a2.hi >= 80.0f);
-                }
-                if (big) {
-                    // outside the double-float ranges (+P heavy tail, huge
-                    // phases): this pair in FP64, straight into the FP64 sums
-                    const double xd = g.xd, yd = g.yd;
-                    const double l1d = cm1d * xd - snd * yd;
-                    double sd, cd;
-                    sincos(snd * xd + cm1d * yd, &sd, &cd);
-                    double e1d = 0.0, e2d = 0.0;
-                    if (in1) {
-                        e1d = exp(l1d + g.c1d);
-                        const double gp = (g.c1d == 0.0) ? e1d : exp(l1d);
-                        ap_re += gp * cd;
-                        ap_im += gp * sd;
-                    }
-                    if (in2) e2d = exp(-l1d + g.c2d);
-                    const double dinv = df_to_double(g.inv);
-                    am_re += (e1d + e2d) * cd * dinv;
-                    am_im += (e1d - e2d) * sd * dinv;
+                const bool plain = in1 && !in2 && g.c1.hi == 0.0f && g.inv.hi == 1.0f &&
+                                   g.inv.lo == 0.0f;
+                if (plain && !self && fabsf(B.hi.x) <= 0x1p-13f && fabsf(B.hi.y) <= 0x1p-13f &&
+                    A.hi.x >= kSmallLog + 0x1p-10f && A.hi.x < 79.0f &&
+                    fabsf(A.hi.y) < 5999.0f) {
+                    // both k from one complex exponential (|b| <= 2^-13
+                    // keeps both exponents on the double-float side of
+                    // kSmallLog and inside the double-float ranges)
+                    df2 E = cexp_pair(df2_x(A), df2_y(A), sh.tab, K);
+                    const df b = df2_x(B), d = df2_y(B);
+                    sp_.both = df2_add(sp_.both, cmul_df2(E, cexp_tiny(df_neg(b), d)));
+                    E.hi.y = -E.hi.y;
+                    E.lo.y = -E.lo.y;
+                    sm_.both = df2_add(sm_.both, cmul_df2(E, cexp_tiny(b, d)));
                     continue;
                 }
-                if (plain && l1.hi < kSmallLog) {
-                    small_term(l1, ph, K, sm_re, sm_im);
-                    continue;
+                // each k by the general rules: (l1, phi) = (a - b, c + d) at
+                // k and (a + b, d - c) at K1 - k
+                df2 Bn = B;
+                Bn.hi.x = -Bn.hi.x;
+                Bn.lo.x = -Bn.lo.x;
+                const df2 lp = df2_add(A, Bn);
+                side_term(df2_x(lp), df2_y(lp), in1, in2, plain, g, cm1d, snd, sh.tab, K, sp_,
+                          fp);
+                if (!self) {
+                    df2 An = A;
+                    An.hi.y = -An.hi.y;
+                    An.lo.y = -An.lo.y;
+                    const df2 lm = df2_add(An, B);
+                    side_term(df2_x(lm), df2_y(lm), in1, in2, plain, g, cm1d, -snd, sh.tab, K,
+                              sm_, fm);
                 }
-                if (plain) {
-                    pb = df2_add(pb, cexp_pair(l1, ph, s_tab, K));
-                    continue;
-                }
-                df sp, cp;
-                df_sincos_tab(ph, s_tab, K, sp, cp);
-                df e1 = {0.0f, 0.0f}, e2 = {0.0f, 0.0f};
-                if (in1) {
-                    e1 = df_exp_small(a1, s_tab, K);
-                    const df gp = (c1.hi == 0.0f) ? e1 : df_exp_small(l1, s_tab, K);
-                    pp_re = df_add(pp_re, df_mul(gp, cp));
-                    pp_im = df_add(pp_im, df_mul(gp, sp));
-                }
-                if (in2) e2 = df_exp_small(a2, s_tab, K);
-                pm_re = df_add(pm_re, df_mul(df_mul(df_add(e1, e2), inv), cp));
-                pm_im = df_add(pm_im, df_mul(df_mul(df_sub(e1, e2), inv), sp));
             }
-            const double both_re = df_to_double(df2_x(pb)) + (double)sm_re;
-            const double both_im = df_to_double(df2_y(pb)) + (double)sm_im;
-            am_re += df_to_double(pm_re) + both_re;
-            am_im += df_to_double(pm_im) + both_im;
-            ap_re += df_to_double(pp_re) + both_re;
-            ap_im += df_to_double(pp_im) + both_im;
+            side_flush(sp_, fp);
+            if (!self) side_flush(sm_, fm);
         }
         __syncwarp();
     }
     // combine the trajectory groups in a fixed order
-    s_red[grp][0][lane] = am_re;
-    s_red[grp][1][lane] = am_im;
-    s_red[grp][2][lane] = ap_re;
-    s_red[grp][3][lane] = ap_im;
     __syncthreads();
     if (grp == 0 && kvalid) {
-        double v[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            double sum = 0.0;
+        for (int side = 0; side < 2; ++side) {
+            if (side == 1 && self) break;
+            double v[kGfSums];
 #pragma unroll
-            for (int g = 0; g < kGfGroups; ++g) sum += s_red[g][c][lane];
-            v[c] = sum;
+            for (int c = 0; c < kGfSums; ++c) {
+                double t = 0.0;
+#pragma unroll
+                for (int gi = 0; gi < kGfGroups; ++gi) t += sh.sum[gi][side][c][slot];
+                v[c] = t;
+            }
+            v[2] += v[0];  // matrix-P: common + own
+            v[3] += v[1];
+            v[4] += v[0];  // +P: common + own
+            v[5] += v[1];
+            const int k = side ? km : kp;
+            double2 *a0 = acc + (size_t)r * K1 + k;
+            double2 *a1 = acc + ((size_t)n_sub + r) * K1 + k;
+            const double2 o0 = *a0, o1 = *a1;
+            *a0 = make_double2(o0.x + v[2], o0.y + v[3]);
+            *a1 = make_double2(o1.x + v[4], o1.y + v[5]);
         }
-        double2 *a0 = acc + (size_t)r * K1 + k;
-        double2 *a1 = acc + ((size_t)n_sub + r) * K1 + k;
-        const double2 o0 = *a0, o1 = *a1;
-        *a0 = make_double2(o0.x + v[0], o0.y + v[1]);
-        *a1 = make_double2(o1.x + v[2], o1.y + v[3]);
     }
     if (y == 0 && threadIdx.x == 0) counts[r] += cnt_r;
 }
 
-__global__ void __launch_bounds__(kGfSlots * kGfGroups, 5)
+__global__ void __launch_bounds__(kGfSlots * kGfGroups, GBS_GF_MINBLOCKS)
     k_gf_df(const GfRec *__restrict__ rec, const int *__restrict__ wmax, int64_t count,
             uint64_t e0, int n_sub, int K1, const double2 *__restrict__ tw, const DfConsts K,
             double2 *__restrict__ acc, int64_t *__restrict__ counts) {
@@ -623,7 +743,7 @@ int launch_gf(gbs_net *net, uint64_t e0, int64_t count) {
                                                    net->d_counts);
     } else {
         static const DfConsts K = make_df_consts();
-        dim3 g2((unsigned)net->n_sub, (unsigned)((net->K1 + kGfSlots - 1) / kGfSlots));
+        dim3 g2((unsigned)net->n_sub, (unsigned)((net->K1 / 2 + 1 + kGfSlots - 1) / kGfSlots));
         if (!net->d_gfrec) return set_error(GBS_EINVAL, "network has no generating-function records");
         k_gf_df<<<g2, kGfSlots * kGfGroups, 0, net->stream>>>(
             static_cast<const GfRec *>(net->d_gfrec), net->d_wmax, count, e0, net->n_sub,
