@@ -334,24 +334,13 @@ __device__ __forceinline__ void small_term(df l1, df ph, const DfConsts &K, floa
 //   e^{(z_k - 1) n_S}      = E       e^{-b + i d},
 //   e^{(z_{K1-k} - 1) n_S} = conj(E) e^{ b + i d}.
 // n_S is real for uniform loss (T = t U: alpha'.beta' = t^2 alpha.beta) up
-// to the GEMM's rounding, so b and d are usually tiny and e^{-+b + i d} is
-// a three-term series: one table-driven complex exponential serves both k.
-// Every lane of the double-float kernel holds such a pair of k.
-
-// e^w for w = u + i v (double-float parts, |u.hi|, |v.hi| <= 2^-13, so
-// |w| <= 2^-12.5): 1 + w + w^2 (1/2 + w/6), remainder below |w|^4/23 <
-// 2^-54; the terms beyond w in FP32 (|w^2/2| <= 2^-26, rounding below
-// 2^-49).  Returns (re, im).
-__device__ __forceinline__ df2 cexp_tiny(df u, df v) {
-    const float ur = u.hi, vi = v.hi;
-    const float w2r = fmaf(ur, ur, -vi * vi), w2i = 2.0f * ur * vi;
-    const float hr = fmaf(ur, 1.0f / 6.0f, 0.5f), hv = vi * (1.0f / 6.0f);
-    const float tr = fmaf(w2r, hr, -w2i * hv), ti = fmaf(w2r, hv, w2i * hr);
-    const df s = df_two_sum(1.0f, ur);  // exact
-    // |ti| <= 2^-12.9 |v.hi|, so v.hi leads the imaginary part
-    return df2_make(df_fast_two_sum(s.hi, s.lo + (u.lo + tr)),
-                    df_fast_two_sum(vi, v.lo + ti));
-}
+// to the GEMM's rounding, so b and d are usually tiny.  With
+// omega = -b + i d the two terms are E e^{omega} and conj(E e^{-omega}), so
+// the lane sums them as
+//   X = sum E cosh(omega),  Z = sum E sinh(omega),
+// and its sums at k and K1 - k are X + Z and conj(X - Z): one table-driven
+// complex exponential and two short series serve both k.  Every lane of
+// the double-float kernel holds such a pair of k.
 
 // (p.x + i p.y) (q.x + i q.y) in double-float.
 __device__ __forceinline__ df2 cmul_df2(df2 p, df2 q) {
@@ -360,6 +349,25 @@ __device__ __forceinline__ df2 cmul_df2(df2 p, df2 q) {
     t.hi.x = -t.hi.x;
     t.lo.x = -t.lo.x;
     return df2_add(s, t);
+}
+
+// X += E cosh(omega), Z += E sinh(omega) for omega = u + i v (double-float
+// parts, |u.hi|, |v.hi| <= 2^-13, so |omega| <= 2^-12.5).  cosh omega - 1 =
+// omega^2/2 + omega^4/24 + ...: below 2^-26, so its product with E is formed
+// in FP32 (rounding below 2^-48 |E|; omega^4/24 < 2^-54 dropped).  sinh
+// omega = omega + omega^3/6 + ... (omega^5/120 < 2^-62 dropped) is a
+// double-float factor of E.
+__device__ __forceinline__ void mirror_terms(df2 E, df u, df v, df2 &X, df2 &Z) {
+    const float ur = u.hi, vi = v.hi;
+    const float w2r = fmaf(ur, ur, -vi * vi), w2i = 2.0f * ur * vi;  // omega^2
+    const float hr = 0.5f * w2r, hv = 0.5f * w2i;
+    X = df2_add(X, df2_add_f(E, f2(fmaf(E.hi.x, hr, -E.hi.y * hv), fmaf(E.hi.x, hv, E.hi.y * hr))));
+    // omega^3 / 6; |Re| <= 2^-25 |u.hi| and |Im| <= 2^-25 |v.hi|, so u.hi and
+    // v.hi lead the sums
+    const float t3r = fmaf(w2r, ur, -w2i * vi) * (1.0f / 6.0f);
+    const float t3i = fmaf(w2r, vi, w2i * ur) * (1.0f / 6.0f);
+    const df2 sh = df2_make(df_fast_two_sum(ur, u.lo + t3r), df_fast_two_sum(vi, v.lo + t3i));
+    Z = df2_add(Z, cmul_df2(E, sh));
 }
 
 // Pair slots of the union window: slot s holds k = s and K1 - s for
@@ -577,6 +585,8 @@ __device__ __forceinline__ void gf_df_block(const GfRec *__restrict__ rec,
             SidePartial sp_, sm_;
             side_clear(sp_);
             side_clear(sm_);
+            df2 X = {f2(0.0f, 0.0f), f2(0.0f, 0.0f)}, Z = X;  // mirror sums
+            bool mirror = false;
             for (int m = 0; m < nmine; ++m) {
                 const GfRec &g = mine[m];
                 const bool in1 = d0 <= g.w1;
@@ -596,12 +606,9 @@ __device__ __forceinline__ void gf_df_block(const GfRec *__restrict__ rec,
                     // both k from one complex exponential (|b| <= 2^-13
                     // keeps both exponents on the double-float side of
                     // kSmallLog and inside the double-float ranges)
-                    df2 E = cexp_pair(df2_x(A), df2_y(A), sh.tab, K);
-                    const df b = df2_x(B), d = df2_y(B);
-                    sp_.both = df2_add(sp_.both, cmul_df2(E, cexp_tiny(df_neg(b), d)));
-                    E.hi.y = -E.hi.y;
-                    E.lo.y = -E.lo.y;
-                    sm_.both = df2_add(sm_.both, cmul_df2(E, cexp_tiny(b, d)));
+                    const df2 E = cexp_pair(df2_x(A), df2_y(A), sh.tab, K);
+                    mirror_terms(E, df_neg(df2_x(B)), df2_y(B), X, Z);
+                    mirror = true;
                     continue;
                 }
                 // each k by the general rules: (l1, phi) = (a - b, c + d) at
@@ -620,6 +627,15 @@ __device__ __forceinline__ void gf_df_block(const GfRec *__restrict__ rec,
                     side_term(df2_x(lm), df2_y(lm), in1, in2, plain, g, cm1d, -snd, sh.tab, K,
                               sm_, fm);
                 }
+            }
+            if (mirror) {  // X + Z at k, conj(X - Z) at K1 - k
+                sp_.both = df2_add(sp_.both, df2_add(X, Z));
+                Z.hi = f2_neg(Z.hi);
+                Z.lo = f2_neg(Z.lo);
+                df2 c = df2_add(X, Z);
+                c.hi.y = -c.hi.y;
+                c.lo.y = -c.lo.y;
+                sm_.both = df2_add(sm_.both, c);
             }
             side_flush(sp_, fp);
             if (!self) side_flush(sm_, fm);
