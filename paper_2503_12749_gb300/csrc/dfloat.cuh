@@ -28,6 +28,7 @@ struct DfConsts {
     float exp2_hi[64], exp2_lo[64];        // 2^(j/64), j = 0..63
     float sin_hi[33], sin_lo[33];          // sin(j pi/64), j = -16..16 (index j + 16)
     float cos_hi[33], cos_lo[33];          // cos(j pi/64)
+    float circ[128][4];                    // (sin hi, sin lo, cos hi, cos lo)(j pi/64), j = 0..127
 };
 
 // The constants and tables above (host; k_gf.cu).

@@ -241,27 +241,32 @@ __device__ __forceinline__ df df_exp_small(df a, const DfTables &T, const DfCons
     return a.hi < -87.0f ? df{0.0f, 0.0f} : df_exp_tab(a, T, K);  // below 1e-37: nothing
 }
 
+// Pieces of pi/64 for a one-stage Cody-Waite reduction of phi: the first
+// four have at most 7 significant bits, so their products with the table
+// index J (|J| < 2^17 for |phi| < 6000) are exact; the fifth is the float
+// nearest the rest (what remains is below 4e-20, times |J| below 5e-15).
+constexpr float kPi64a = 0x1.94p-5f, kPi64b = -0x1.ep-13f, kPi64c = -0x1.2cp-23f,
+                kPi64d = 0x1.1p-31f, kPi64e = 0x1.0b4612p-39f;
+
 // The common case's term e^{l1} (cos phi, sin phi) in double-float with the
-// independent halves side by side on the packed FP32x2 instructions (per
-// lane the operations of df_sincos_tab and df_exp_tab): the reduction of phi
-// by pi/2 beside that of l1 by ln2/64, the sine and cosine polynomials, their
-// table combination and the final products.  Returns (re, im) as (x, y).
-__device__ __forceinline__ df2 cexp_pair(df l1, df ph, const DfTables &T, const DfConsts &K) {
-    const float qf = rintf(ph.hi * 0.636619772367581343076f);  // 2 / pi
-    const float kf = rintf(l1.hi * 92.33248261689366f);        // 64 / ln 2
-    const float2 nq = f2(-qf, -kf);
-    df2 r = df2_two_sum(f2_fma(nq, f2(K.pio2_1, K.ln2_64_1), f2(ph.hi, l1.hi)),
-                        f2(ph.lo, l1.lo));                       // exact products
-    r = df2_add_f(r, f2_mul(nq, f2(K.pio2_2, K.ln2_64_2)));    // exact products
-    r = df2_add_f(r, f2_mul(nq, f2(K.pio2_3, K.ln2_64_3)));
-    const df s = df_add_f(df2_x(r), -qf * K.pio2_4);
+// independent halves side by side on the packed FP32x2 instructions: phi =
+// J pi/64 + r (|r| <= pi/128) beside l1 = (64 m + j) ln2/64 + r' (Tang's
+// exponential, as df_exp_tab), the sine and cosine of r by their Taylor
+// series (as df_sincos_tab), combined with the full-circle table
+// circ[J mod 128] = (sin, cos)(J pi/64) by angle addition, and the final
+// products.  Returns (re, im) as (x, y).
+__device__ __forceinline__ df2 cexp_pair(df l1, df ph, const DfTables &T, const float4 *circ,
+                                         const DfConsts &K) {
+    const float jf = rintf(ph.hi * 20.371832715762604f);  // 64 / pi
+    const float kf = rintf(l1.hi * 92.33248261689366f);   // 64 / ln 2
+    const float2 nq = f2(-jf, -kf);
+    df2 r = df2_two_sum(f2_fma(nq, f2(kPi64a, K.ln2_64_1), f2(ph.hi, l1.hi)),
+                        f2(ph.lo, l1.lo));                    // exact products
+    r = df2_add_f(r, f2_mul(nq, f2(kPi64b, K.ln2_64_2)));   // exact products
+    r = df2_add_f(r, f2_mul(nq, f2(kPi64c, K.ln2_64_3)));
+    df rr = df_add_f(df2_x(r), -jf * kPi64d);               // exact product
+    rr = df_add_f(rr, -jf * kPi64e);
     const df er = df2_y(r);
-    // sine and cosine of s by the pi/64 table
-    float jf = rintf(s.hi * 20.371832715762604f);  // 64 / pi
-    jf = fminf(fmaxf(jf, -16.0f), 16.0f);
-    df rr = df_two_sum(fmaf(-jf, K.pi64_1, s.hi), s.lo);  // exact product
-    rr = df_add_f(rr, -jf * K.pi64_2);                     // exact product
-    rr = df_add_f(rr, -jf * K.pi64_3);
     const df r2 = df_mul(rr, rr);
     const float x = r2.hi;
     const float ts = x * x * fmaf(-x, 1.0f / 5040.0f, 1.0f / 120.0f);
@@ -270,20 +275,13 @@ __device__ __forceinline__ df2 cexp_pair(df l1, df ph, const DfTables &T, const 
     df2 w = df2_make(df_mul(r2, sixth), df{-0.5f * r2.hi, -0.5f * r2.lo});
     w = df2_add_f(df2_add_f(w, f2(ts, tc)), f2(1.0f, 1.0f));
     const df sr = df_mul(rr, df2_x(w)), cr = df2_y(w);
-    const int j = (int)jf + 16;
-    const df S = T.sn[j], C = T.cs[j];
+    const float4 tb = circ[((int)jf) & 127];  // (sin hi, sin lo, cos hi, cos lo)
+    const df S = {tb.x, tb.y}, C = {tb.z, tb.w};
     const df2 P = df2_mul(df2_make(S, C), df2_make(cr, cr));  // (S cr, C cr)
     df2 Q = df2_mul(df2_make(C, S), df2_make(sr, sr));        // (C sr, S sr)
     Q.hi.y = -Q.hi.y;
     Q.lo.y = -Q.lo.y;
-    const df2 sc = df2_add(P, Q);  // (sin s, cos s)
-    df sp, cp;
-    switch (((int)qf) & 3) {
-        case 0: sp = df2_x(sc); cp = df2_y(sc); break;
-        case 1: sp = df2_y(sc); cp = df_neg(df2_x(sc)); break;
-        case 2: sp = df_neg(df2_x(sc)); cp = df_neg(df2_y(sc)); break;
-        default: sp = df_neg(df2_y(sc)); cp = df2_x(sc); break;
-    }
+    const df2 sc = df2_add(P, Q);  // (sin phi, cos phi)
     // e^{l1} by the 2^(j/64) table
     const float xe = er.hi;
     const float qt = xe * fmaf(fmaf(xe, 1.0f / 120.0f, 1.0f / 24.0f), xe, 1.0f / 6.0f);
@@ -293,7 +291,7 @@ __device__ __forceinline__ df2 cexp_pair(df l1, df ph, const DfTables &T, const 
     const df t = df_mul(T.exp2[n & 63], pe);
     const float scale = __int_as_float(((n >> 6) + 127) << 23);
     const df e1 = l1.hi < -87.0f ? df{0.0f, 0.0f} : df{t.hi * scale, t.lo * scale};
-    return df2_mul(df2_make(e1, e1), df2_make(cp, sp));
+    return df2_mul(df2_make(e1, e1), df2_make(df2_y(sc), df2_x(sc)));
 }
 
 // Terms below 2^-27 (exponent l1 below kSmallLog) need no double-float
@@ -443,7 +441,8 @@ constexpr int kGfSums = 6;
 // FP64.
 __device__ __forceinline__ void side_term(df l1, df ph, bool in1, bool in2, bool plain,
                                           const GfRec &g, double cm1d, double snd,
-                                          const DfTables &T, const DfConsts &K, SidePartial &s,
+                                          const DfTables &T, const float4 *circ,
+                                          const DfConsts &K, SidePartial &s,
                                           double *f) {
     const df c1 = g.c1;
     df a1 = l1, a2 = {0.0f, 0.0f};
@@ -478,7 +477,7 @@ __device__ __forceinline__ void side_term(df l1, df ph, bool in1, bool in2, bool
         return;
     }
     if (plain) {
-        s.both = df2_add(s.both, cexp_pair(l1, ph, T, K));
+        s.both = df2_add(s.both, cexp_pair(l1, ph, T, circ, K));
         return;
     }
     df sp, cp;
@@ -525,6 +524,7 @@ struct GfShared {
     GfRec rec[kGfGroups / 2][2 * kGfPer];  // per warp: its two half-warps' trajectories
     double sum[kGfGroups][2][kGfSums][kGfSlots];  // FP64 sums: [group][k, K1 - k][c]
     DfTables tab;
+    float4 circ[128];  // (sin, cos)(j pi/64) as double-float, j = 0..127
 };
 
 // One block's work: sub-ensemble r, pair-slot block y of one chunk of one
@@ -559,6 +559,8 @@ __device__ __forceinline__ void gf_df_block(const GfRec *__restrict__ rec,
         sh.tab.sn[t] = df{K.sin_hi[t], K.sin_lo[t]};
         sh.tab.cs[t] = df{K.cos_hi[t], K.cos_lo[t]};
     }
+    for (int t = threadIdx.x; t < 128; t += blockDim.x)
+        sh.circ[t] = make_float4(K.circ[t][0], K.circ[t][1], K.circ[t][2], K.circ[t][3]);
     double *fp = sh.sum[grp][0][0] + slot;  // f[c] at fp[c * kGfSlots]
     double *fm = sh.sum[grp][1][0] + slot;
 #pragma unroll
@@ -606,7 +608,7 @@ __device__ __forceinline__ void gf_df_block(const GfRec *__restrict__ rec,
                     // both k from one complex exponential (|b| <= 2^-13
                     // keeps both exponents on the double-float side of
                     // kSmallLog and inside the double-float ranges)
-                    const df2 E = cexp_pair(df2_x(A), df2_y(A), sh.tab, K);
+                    const df2 E = cexp_pair(df2_x(A), df2_y(A), sh.tab, sh.circ, K);
                     mirror_terms(E, df_neg(df2_x(B)), df2_y(B), X, Z);
                     mirror = true;
                     continue;
@@ -617,15 +619,15 @@ __device__ __forceinline__ void gf_df_block(const GfRec *__restrict__ rec,
                 Bn.hi.x = -Bn.hi.x;
                 Bn.lo.x = -Bn.lo.x;
                 const df2 lp = df2_add(A, Bn);
-                side_term(df2_x(lp), df2_y(lp), in1, in2, plain, g, cm1d, snd, sh.tab, K, sp_,
-                          fp);
+                side_term(df2_x(lp), df2_y(lp), in1, in2, plain, g, cm1d, snd, sh.tab, sh.circ,
+                          K, sp_, fp);
                 if (!self) {
                     df2 An = A;
                     An.hi.y = -An.hi.y;
                     An.lo.y = -An.lo.y;
                     const df2 lm = df2_add(An, B);
-                    side_term(df2_x(lm), df2_y(lm), in1, in2, plain, g, cm1d, -snd, sh.tab, K,
-                              sm_, fm);
+                    side_term(df2_x(lm), df2_y(lm), in1, in2, plain, g, cm1d, -snd, sh.tab,
+                              sh.circ, K, sm_, fm);
                 }
             }
             if (mirror) {  // X + Z at k, conj(X - Z) at K1 - k
@@ -714,6 +716,13 @@ DfConsts make_df_consts() {
         K.exp2_lo[j] = (float)(v - (double)K.exp2_hi[j]);
     }
     const double pi = 3.14159265358979323846264338327950288;
+    for (int j = 0; j < 128; ++j) {
+        const double sv = std::sin((double)j * pi / 64.0), cv = std::cos((double)j * pi / 64.0);
+        K.circ[j][0] = (float)sv;
+        K.circ[j][1] = (float)(sv - (double)K.circ[j][0]);
+        K.circ[j][2] = (float)cv;
+        K.circ[j][3] = (float)(cv - (double)K.circ[j][2]);
+    }
     for (int j = -16; j <= 16; ++j) {
         const double sv = std::sin((double)j * pi / 64.0), cv = std::cos((double)j * pi / 64.0);
         K.sin_hi[j + 16] = (float)sv;
