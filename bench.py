@@ -531,14 +531,18 @@ def gbs_arm(args, wl_def):
 
         e2e_step(0)
         barrier()
+        eclocks = ClockSampler(dev)
+        eclocks.start()
         t0 = time.perf_counter()
         ne = args.steps
         for s in range(ne):
             e2e_step(1 + s)
         barrier()
         dt = max_over_ranks(time.perf_counter() - t0)
+        eclk = eclocks.stop()
         line["e2e"] = {"value": world * E * ne / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "steps": ne,
+                       "clocks": {"sm_mhz": eclk.get("sm_mhz"), "reasons": eclk.get("reasons")},
                        "what": "gbs_make_network (pinned host T, r) + gbs_sample + "
                                "gbs_binned_counts (host outputs) + gbs_free_network per step, "
                                "wall clock, max over ranks"}
