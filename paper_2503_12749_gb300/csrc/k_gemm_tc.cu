@@ -195,19 +195,21 @@ constexpr int kSampWarpsUsed = 4 * kSampWG + 2;
 // accumulated value by about half an ulp for every MMA that lands on an
 // accumulator already at full magnitude; the promoted sums inherit that
 // relative bias (it is linear in the values), so n_S comes out low by a
-// factor 1 - 2c.  Issued block by block with the correction products first
-// and A0 B0 last, a segment of one K block has two such MMAs, one of two
-// blocks eight (the second block's corrections land on the first block's
-// A0 B0).  Measured on lossless networks (n_S = n exactly), (n - n_S) / n =
-// 2.5e-7 with 3 products and 2-block segments, 0.9e-7 with 1-block segments
-// (3 or 6 products), but 1-block segments make the 3-product GEMM 14 %
-// slower (twice the promotion work per MMA).  The 3-product split keeps
-// 2-block segments (its bias moves P(m) by about 0.1 sigma at the named
-// workloads' sizes); the 6-product split, the accuracy mode, promotes every
-// K block.
+// factor 1 - 2c, and the longer the segment, the more MMAs land on a full
+// accumulator (each K block's products are issued with the corrections
+// first and A0 B0 last).  Measured on lossless networks (n_S = n exactly),
+// (n - n_S) / n with 3 products = 0.9-1.2e-7 (1-block segments), 2.5e-7
+// (2), 3.8-4.2e-7 (3), 5.8-6.0e-7 (4).  Short segments cost time: the MMAs
+// of one segment must outlast the promotion of the previous one, which
+// holds from 3 blocks on (m8000 GEMM ms per step x median SM MHz / 10^6:
+// 2 blocks 1.53, 3 blocks 1.39, 4 blocks 1.38; m1000 GEMM 15.3-15.6, 14.40,
+// 14.34 ms per step; 1 block 14 % slower than 2).  The 3-product split takes
+// 3-block segments
+// (its bias moves P(m) by about 0.15 sigma at the named workloads' sizes);
+// the 6-product split, the accuracy mode, promotes every K block.
 template <int P>
 constexpr int seg_blocks() {
-    return P == 3 ? 2 : 1;
+    return P == 3 ? 3 : 1;
 }
 
 // A tile of the grouped GEMM: which network, which mode tile (of this CTA),
