@@ -44,11 +44,11 @@ UNIT = "samples/s"
 # run without an entry reports traffic null.
 GEMM_TRAFFIC_BYTES_PER_SAMPLE = {
     ("m8000", "bf16x3", True, 2, 16, 0): (
-        (57.453761e9 + 1.111236e9) / 16768,
+        (60.784051e9 + 1.111496e9) / 16768,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 16768-trajectory sampling "
         "launch (profiles/k_gemm_tc_pair_m8000.md), scaled to the average launch"),
     ("m1000", "bf16x3", True, 2, 0, 0): (
-        (1.093573e9 + 1.110423e9) / 131072,
+        (1.126301e9 + 1.087086e9) / 131072,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 131072-trajectory sampling "
         "launch (profiles/k_gemm_tc_pair_m1000.md), scaled to the average launch"),
 }
@@ -518,18 +518,29 @@ def gbs_arm(args, wl_def):
         h2d = Tn.nbytes + rn.nbytes
         d2h = 4 * K1 * 8
 
+        parts = {"make": 0.0, "sample_invert_read": 0.0, "free": 0.0}
+
         def e2e_step(s):
+            ta = time.perf_counter()
             n2 = gbs.gbs_make_network(Tn, rn, precision, sptr)
             if args.sampler_fusion is not None:
                 gbs.gbs_set_sampler_fusion(n2, args.sampler_fusion)
             if args.gemm_pair is not None and precision != "fp64":
                 gbs.gbs_set_gemm_config(n2, args.gemm_pair, args.gemm_band, args.gemm_keep_a)
+            tb = time.perf_counter()
             gbs.gbs_sample(n2, seed, base + s * E, E, n_sub, K1)
             res = gbs.gbs_binned_counts(n2, 0, K1)
+            tc = time.perf_counter()
             gbs.gbs_free_network(n2)
+            td = time.perf_counter()
+            parts["make"] += tb - ta
+            parts["sample_invert_read"] += tc - tb
+            parts["free"] += td - tc
             return res
 
         e2e_step(0)
+        for k in parts:
+            parts[k] = 0.0
         barrier()
         eclocks = ClockSampler(dev)
         eclocks.start()
@@ -543,6 +554,7 @@ def gbs_arm(args, wl_def):
         line["e2e"] = {"value": world * E * ne / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "steps": ne,
                        "clocks": {"sm_mhz": eclk.get("sm_mhz"), "reasons": eclk.get("reasons")},
+                       "ms_per_step": {k: 1e3 * v / ne for k, v in parts.items()},
                        "what": "gbs_make_network (pinned host T, r) + gbs_sample + "
                                "gbs_binned_counts (host outputs) + gbs_free_network per step, "
                                "wall clock, max over ranks"}
