@@ -69,6 +69,10 @@ typedef struct gbs_net *gbs_net_t;
  *   N, M       input and output mode counts, 1 <= N, M <= 65536.
  *   T          host, M*N complex numbers row-major, each as (re, im) doubles:
  *              T[2*(i*N + j)] = Re T_ij, T[2*(i*N + j) + 1] = Im T_ij.
+ *              Read during the call only.  Page-locked memory that the
+ *              device can address (cudaHostAlloc, cudaHostRegister) is read
+ *              by the conversion kernel in place; other memory is first
+ *              copied to a device buffer.
  *   r          host, N squeezing parameters, each finite and >= 0.
  *   precision  GBS_FP64, GBS_BF16X3 or GBS_BF16X6.  The BF16 paths split T
  *              (rounded to FP32) into BF16 planes T = T0 + T1 + T2.

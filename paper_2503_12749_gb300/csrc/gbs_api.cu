@@ -535,7 +535,24 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
         if (!std::isfinite(r[j]) || r[j] < 0.0)
             return set_error(GBS_EINVAL, "r[%d] = %g: squeezing must be finite and >= 0", j, r[j]);
     if (!T_device) {
-        // T in host memory: upload it as given and build the operand layout
+        // T in page-locked host memory that the device can address (both
+        // ends of the array in such an allocation, at a consistent device
+        // address): the conversion kernels read it there directly, one pass
+        // over the host link, with no staging buffer.  The call synchronises
+        // before it returns, so T is not read afterwards.
+        const size_t count = (size_t)2 * M * N;
+        cudaPointerAttributes a0{}, a1{};
+        if (cudaPointerGetAttributes(&a0, T) == cudaSuccess &&
+            cudaPointerGetAttributes(&a1, T + (count - 1)) == cudaSuccess &&
+            a0.type == cudaMemoryTypeHost && a1.type == cudaMemoryTypeHost && a0.devicePointer &&
+            a1.devicePointer &&
+            static_cast<const double *>(a1.devicePointer) -
+                    static_cast<const double *>(a0.devicePointer) ==
+                (ptrdiff_t)(count - 1))
+            return make_network(N, M, static_cast<const double *>(a0.devicePointer), true, r,
+                                precision, stream, out);
+        cudaGetLastError();  // pageable memory: not an error
+        // other host memory: upload it as given and build the operand layout
         // (and check for non-finite entries) on the GPU, as for device T
         cudaStream_t st = static_cast<cudaStream_t>(stream);
         double *tmp = nullptr;

@@ -61,3 +61,27 @@ def test_results_and_memory_stable_over_network_churn(env):
     free1 = torch.cuda.mem_get_info()[0]
     # a little slack for the driver's own bookkeeping
     assert free1 >= free0 - (64 << 20), (free0, free1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_pinned_host_T_read_in_place_equals_staged_upload(env, prec):
+    """gbs_make_network reads T in place when it lies in page-locked host
+    memory the device can address, and stages it through a device buffer
+    otherwise; both give bitwise the same network (per-trajectory n, n_S and
+    the sub-ensemble sums)."""
+    g, torch = env
+    nd = wl.small_network(300, M=260, r=0.8, t2=0.9, seed=5, general_loss=True)
+    s = torch.cuda.current_stream().cuda_stream
+    pinned = torch.empty(2 * nd.T.size, dtype=torch.float64, pin_memory=True)
+    Tp = pinned.numpy().view(np.complex128).reshape(nd.T.shape)
+    Tp[:] = nd.T
+    res = []
+    for T in (np.array(nd.T, copy=True), Tp):
+        net = g.gbs_make_network(T, nd.r, prec, s)
+        n, nS = g.gbs_debug_samples(net, nd.seed_s, 11, 1000)
+        g.gbs_sample(net, nd.seed_s, 0, 5000, 10, 256)
+        _, _, acc, cnt = g.gbs_get_accumulators(net)
+        g.gbs_free_network(net)
+        res.append((n, nS, acc, cnt))
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
