@@ -88,9 +88,11 @@ int gbs_make_network(int N, int M, const double *T, const double *r, int precisi
  * gbs_make_network_device -- as gbs_make_network, with T in DEVICE memory
  * (same layout: M*N complex row-major, (re, im) doubles; read during the
  * call only, the library keeps its own converted copy).  The conversion
- * (FP64 reordering or BF16 splitting) runs on the GPU; non-finite entries
- * are counted there and rejected with EINVAL.  r stays a host array.
- * Synchronises the stream.  Errors as gbs_make_network.
+ * (FP64 reordering or BF16 splitting) runs on the GPU on `stream`, ordered
+ * after the work already queued there only: T must be complete with respect
+ * to `stream` (produced on it, or the stream made to wait for its producer).
+ * Non-finite entries are counted there and rejected with EINVAL.  r stays a
+ * host array.  Synchronises the stream.  Errors as gbs_make_network.
  */
 int gbs_make_network_device(int N, int M, const double *T_dev, const double *r, int precision,
                             void *stream, gbs_net_t *out);
