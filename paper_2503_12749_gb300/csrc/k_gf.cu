@@ -33,40 +33,47 @@
 namespace gbs {
 namespace {
 
-constexpr double kTwoPi = 6.283185307179586476925286766559;
-
-__device__ __forceinline__ int half_width(double cstar, int K1) {
-    // largest |delta theta| with 1 - cos(delta theta) <= cstar, in k units, +1 margin
+// The windows are bounds, so FP32 serves (GB300's FP64 pipe is narrow and
+// its asin and sqrt are slow): every FP32 step below errs by a few ulp, in
+// all below 4e-6 relative in theta, and the k count is rounded up by that
+// plus a margin of 2 (one for the floor, one for the rounding).
+__device__ __forceinline__ int half_width(float cstar, int K1) {
+    // largest |delta theta| with 1 - cos(delta theta) <= cstar, in k units
     const int half = K1 >> 1;
-    if (!(cstar < 2.0)) return half;  // also catches NaN
-    const double th = 2.0 * asin(sqrt(0.5 * cstar));
-    const double w = floor(th * (double)K1 / kTwoPi) + 1.0;
-    return w >= (double)half ? half : (int)w;
+    if (!(cstar < 2.0f)) return half;  // also catches NaN
+    const float th = 2.0f * asinf(sqrtf(0.5f * cstar));
+    const float v = th * (float)K1 * 0.159154943f;  // K1 / (2 pi)
+    const float w = floorf(v * (1.0f + 4e-6f)) + 2.0f;
+    return w >= (float)half ? half : (int)w;
 }
 
-__device__ __forceinline__ Window windows_for(double n, double x, double y, int K1, double T) {
-    const double ay = fabs(y);
+__device__ __forceinline__ Window windows_for(double n, double xd, double yd, int K1, double Td) {
+    const float x = (float)xd, y = (float)yd, T = (float)Td;
+    const float ay = fabsf(y);
     const int half = K1 >> 1;
     Window w;
     // e^{l1} terms: l1 <= -c x + sqrt(2c)|y|, c = 1 - cos theta
-    if (!(x > 0.0)) {
+    if (!(xd > 0.0)) {
         w.w1 = half;
     } else {
-        const double u = (1.4142135623730951 * ay + sqrt(2.0 * y * y + 4.0 * x * T)) / (2.0 * x);
+        const float u = (1.41421356f * ay + sqrtf(2.0f * y * y + 4.0f * x * T)) / (2.0f * x);
         w.w1 = half_width(u * u, K1);
     }
-    // e^{-l1 + c2} term: -l1 + c2 <= (2 - c')x + sqrt(2c')|y| + c2, c' = 1 + cos theta
+    // e^{-l1 + c2} term: -l1 + c2 <= (2 - c')x + sqrt(2c')|y| + c2, c' = 1 + cos theta;
+    // D = 2 x + c2 + T = 2 (x - max(n, 0)) + T with the difference taken in
+    // FP64, T raised by 1/4 so that FP32 rounding near disc = 0 cannot drop
+    // a window
     const double c2 = -2.0 * fmax(n, 0.0);
-    if (!(x > 0.0)) {
-        w.w2 = (ay + c2 >= -T) ? half : -1;
+    if (!(xd > 0.0)) {
+        w.w2 = ((double)ay + c2 >= -Td) ? half : -1;
     } else {
-        const double D = 2.0 * x + c2 + T;
-        const double disc = 2.0 * y * y + 4.0 * x * D;
-        if (disc < 0.0) {
+        const float D = (float)(2.0 * xd + c2) + (T + 0.25f);
+        const float disc = 2.0f * y * y + 4.0f * x * D;
+        if (disc < 0.0f) {
             w.w2 = -1;
         } else {
-            const double u = (1.4142135623730951 * ay + sqrt(disc)) / (2.0 * x);
-            w.w2 = (u < 0.0) ? -1 : half_width(u * u, K1);
+            const float u = (1.41421356f * ay + sqrtf(disc)) / (2.0f * x);
+            w.w2 = (u < 0.0f) ? -1 : half_width(u * u, K1);
         }
     }
     return w;
