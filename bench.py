@@ -55,13 +55,13 @@ GEMM_TRAFFIC_BYTES_PER_SAMPLE = {
 
 # FP32 lane-operation slots of the FMA pipe per evaluated (trajectory, k)
 # pair of the double-float generating-function kernel (k_gf_df): the FMA
-# pipe's elapsed share (ncu sm__pipe_fma_cycles_active, 58.90 %) x elapsed
-# SM cycles (7.759e5) x 152 SMs x 128 FP32 lanes, divided by the launch's
-# in-window pairs (131072 trajectories x 288.9 pairs per trajectory, counted
-# by gbs_debug_windows): 235.  A packed FP32x2 instruction occupies two lane
-# slots.  Capture: m1000 chunk of 131072 trajectories
+# pipe's elapsed share (ncu sm__pipe_fma_cycles_active, 54.67 %) x elapsed
+# SM cycles (7.188e5) x 152 SMs x 128 FP32 lanes, divided by the launch's
+# in-window pairs (131072 trajectories x 290.9 pairs per trajectory, counted
+# by gbs_debug_windows): 200.5.  A packed FP32x2 instruction occupies two
+# lane slots.  Capture: m1000 chunk of 131072 trajectories
 # (profiles/k_gf_df_m1000.md); valid for that kernel version only.
-GF_FP32_OPS_PER_PAIR = 235.0
+GF_FP32_OPS_PER_PAIR = 200.5
 
 # FP64 peak: the FMA-chain probe (gbs_measure_fp64_rate, CUDA events; 8 to
 # 32 independent chains per thread, 128 to 1024 threads per block, 1 to 8

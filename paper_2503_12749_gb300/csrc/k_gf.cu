@@ -340,12 +340,17 @@ __device__ __forceinline__ void small_term(df l1, df ph, const DfConsts &K, floa
 //   e^{(z_{K1-k} - 1) n_S} = conj(E) e^{ b + i d}.
 // n_S is real for uniform loss (T = t U: alpha'.beta' = t^2 alpha.beta) up
 // to the GEMM's rounding, so b and d are usually tiny.  With
-// omega = -b + i d the two terms are E e^{omega} and conj(E e^{-omega}), so
-// the lane sums them as
-//   X = sum E cosh(omega),  Z = sum E sinh(omega),
-// and its sums at k and K1 - k are X + Z and conj(X - Z): one table-driven
-// complex exponential and two short series serve both k.  Every lane of
-// the double-float kernel holds such a pair of k.
+// omega = -b + i d = y w, w = i (z_k - 1) (a constant of the lane), the two
+// terms are E e^{omega} and conj(E e^{-omega}), so the lane's sums at k and
+// K1 - k are X + Z and conj(X - Z) with
+//   X = sum E cosh(omega) = S0 + (w^2 / 2) S2,
+//   Z = sum E sinh(omega) = w S1 + (w^3 / 6) S3,   S_j = sum E y^j
+// (|omega| <= 2^-12.5, so omega^4/24 < 2^-54 is left out): one table-driven
+// complex exponential and four accumulations per trajectory serve both k,
+// and the lane's factors w^j are applied once per tile.  S0 and S1 are
+// double-float sums; S2 and S3 FP32, since w^2 S2 / 2 and w^3 S3 / 6 are
+// below 2^-26 |E| and 2^-37 |E| per term.  Every lane of the double-float
+// kernel holds such a pair of k.
 
 // (p.x + i p.y) (q.x + i q.y) in double-float.
 __device__ __forceinline__ df2 cmul_df2(df2 p, df2 q) {
@@ -356,23 +361,40 @@ __device__ __forceinline__ df2 cmul_df2(df2 p, df2 q) {
     return df2_add(s, t);
 }
 
-// X += E cosh(omega), Z += E sinh(omega) for omega = u + i v (double-float
-// parts, |u.hi|, |v.hi| <= 2^-13, so |omega| <= 2^-12.5).  cosh omega - 1 =
-// omega^2/2 + omega^4/24 + ...: below 2^-26, so its product with E is formed
-// in FP32 (rounding below 2^-48 |E|; omega^4/24 < 2^-54 dropped).  sinh
-// omega = omega + omega^3/6 + ... (omega^5/120 < 2^-62 dropped) is a
-// double-float factor of E.
-__device__ __forceinline__ void mirror_terms(df2 E, df u, df v, df2 &X, df2 &Z) {
-    const float ur = u.hi, vi = v.hi;
-    const float w2r = fmaf(ur, ur, -vi * vi), w2i = 2.0f * ur * vi;  // omega^2
-    const float hr = 0.5f * w2r, hv = 0.5f * w2i;
-    X = df2_add(X, df2_add_f(E, f2(fmaf(E.hi.x, hr, -E.hi.y * hv), fmaf(E.hi.x, hv, E.hi.y * hr))));
-    // omega^3 / 6; |Re| <= 2^-25 |u.hi| and |Im| <= 2^-25 |v.hi|, so u.hi and
-    // v.hi lead the sums
-    const float t3r = fmaf(w2r, ur, -w2i * vi) * (1.0f / 6.0f);
-    const float t3i = fmaf(w2r, vi, w2i * ur) * (1.0f / 6.0f);
-    const df2 sh = df2_make(df_fast_two_sum(ur, u.lo + t3r), df_fast_two_sum(vi, v.lo + t3i));
-    Z = df2_add(Z, cmul_df2(E, sh));
+// Moment sums of one lane's mirror pairs over a tile (see above).
+struct MirrorSums {
+    df2 s0, s1;       // sum E, sum E y (double-float)
+    float2 s2, s3;    // sum E y^2, sum E y^3 (FP32)
+};
+
+__device__ __forceinline__ void mirror_add(MirrorSums &m, df2 E, df y) {
+    m.s0 = df2_add(m.s0, E);
+    // E y: the product of the high parts exact, the cross terms in FP32
+    const float2 yh = f2(y.hi, y.hi);
+    const float2 p = f2_mul(E.hi, yh);
+    const float2 e = f2_fma(E.hi, f2(y.lo, y.lo), f2_fma(E.lo, yh, f2_fma(E.hi, yh, f2_neg(p))));
+    m.s1 = df2_add(m.s1, df2{p, e});
+    const float y2 = y.hi * y.hi;
+    m.s2 = f2_fma(E.hi, f2(y2, y2), m.s2);
+    m.s3 = f2_fma(E.hi, f2(y2 * y.hi, y2 * y.hi), m.s3);
+}
+
+// (X + Z, conj(X - Z)) from the moment sums and the lane's w = i (z - 1).
+__device__ __forceinline__ void mirror_finish(const MirrorSums &m, df2 w, df2 &at_k, df2 &at_mk) {
+    const float wr = w.hi.x, wi = w.hi.y;
+    const float w2r = wr * wr - wi * wi, w2i = 2.0f * wr * wi;
+    const float w3r = w2r * wr - w2i * wi, w3i = w2r * wi + w2i * wr;
+    const float2 c2 = f2(0.5f * (w2r * m.s2.x - w2i * m.s2.y), 0.5f * (w2r * m.s2.y + w2i * m.s2.x));
+    const float2 c3 = f2((w3r * m.s3.x - w3i * m.s3.y) * (1.0f / 6.0f),
+                         (w3r * m.s3.y + w3i * m.s3.x) * (1.0f / 6.0f));
+    const df2 X = df2_add_f(m.s0, c2);
+    df2 Z = df2_add_f(cmul_df2(w, m.s1), c3);
+    at_k = df2_add(X, Z);
+    Z.hi = f2_neg(Z.hi);
+    Z.lo = f2_neg(Z.lo);
+    at_mk = df2_add(X, Z);
+    at_mk.hi.y = -at_mk.hi.y;
+    at_mk.lo.y = -at_mk.lo.y;
 }
 
 // Pair slots of the union window: slot s holds k = s and K1 - s for
@@ -578,6 +600,9 @@ __device__ __forceinline__ void gf_df_block(const GfRec *__restrict__ rec,
     const double cm1d = t.x, snd = t.y;
     const df cm1 = df_from_double(t.x), sn = df_from_double(t.y);
     const df2 cs_pair = df2_make(cm1, sn), sc_pair = df2_make(sn, cm1);
+    // |b|, |d| <= |y| max(|sin|, 1 - cos); the factor rounded up
+    const float ymul = fmaxf(fabsf(sn.hi), fabsf(cm1.hi)) * (1.0f + 0x1p-20f);
+    const df2 w_lane = df2_make(df_neg(sn), cm1);  // i (z_k - 1)
     const GfRec *mine = sh.rec[warp] + kGfPer * (lane / kGfSlots);
 
     for (int64_t base = 0; base < cnt_r; base += kGfTile) {
@@ -594,34 +619,35 @@ __device__ __forceinline__ void gf_df_block(const GfRec *__restrict__ rec,
             SidePartial sp_, sm_;
             side_clear(sp_);
             side_clear(sm_);
-            df2 X = {f2(0.0f, 0.0f), f2(0.0f, 0.0f)}, Z = X;  // mirror sums
+            MirrorSums ms;
+            ms.s0 = ms.s1 = {f2(0.0f, 0.0f), f2(0.0f, 0.0f)};
+            ms.s2 = ms.s3 = f2(0.0f, 0.0f);
             bool mirror = false;
             for (int m = 0; m < nmine; ++m) {
                 const GfRec &g = mine[m];
                 const bool in1 = d0 <= g.w1;
                 const bool in2 = dpi <= g.w2;
                 if (!(in1 || in2)) continue;
-                // (a, c) = (cos - 1, sin) x and (b, d) = (sin, cos - 1) y
+                // (a, c) = (cos - 1, sin) x
                 const df2 A = df2_mul(cs_pair, df2_make(g.x, g.x));
-                const df2 B = df2_mul(sc_pair, df2_make(g.y, g.y));
                 // n >= 0 with e^{-2n} below double rounding and no term near
                 // theta = pi: both estimators add e^{l1} e^{i phi} (the
                 // general formulas give the same value), summed once
                 const bool plain = in1 && !in2 && g.c1.hi == 0.0f && g.inv.hi == 1.0f &&
                                    g.inv.lo == 0.0f;
-                if (plain && !self && fabsf(B.hi.x) <= 0x1p-13f && fabsf(B.hi.y) <= 0x1p-13f &&
+                if (plain && !self && fabsf(g.y.hi) * ymul <= 0x1p-13f &&
                     A.hi.x >= kSmallLog + 0x1p-10f && A.hi.x < 79.0f &&
                     fabsf(A.hi.y) < 5999.0f) {
-                    // both k from one complex exponential (|b| <= 2^-13
-                    // keeps both exponents on the double-float side of
+                    // both k from one complex exponential (|b|, |d| <=
+                    // 2^-13 keep both exponents on the double-float side of
                     // kSmallLog and inside the double-float ranges)
-                    const df2 E = cexp_pair(df2_x(A), df2_y(A), sh.tab, sh.circ, K);
-                    mirror_terms(E, df_neg(df2_x(B)), df2_y(B), X, Z);
+                    mirror_add(ms, cexp_pair(df2_x(A), df2_y(A), sh.tab, sh.circ, K), g.y);
                     mirror = true;
                     continue;
                 }
                 // each k by the general rules: (l1, phi) = (a - b, c + d) at
-                // k and (a + b, d - c) at K1 - k
+                // k and (a + b, d - c) at K1 - k, (b, d) = (sin, cos - 1) y
+                const df2 B = df2_mul(sc_pair, df2_make(g.y, g.y));
                 df2 Bn = B;
                 Bn.hi.x = -Bn.hi.x;
                 Bn.lo.x = -Bn.lo.x;
@@ -637,14 +663,11 @@ __device__ __forceinline__ void gf_df_block(const GfRec *__restrict__ rec,
                               sh.circ, K, sm_, fm);
                 }
             }
-            if (mirror) {  // X + Z at k, conj(X - Z) at K1 - k
-                sp_.both = df2_add(sp_.both, df2_add(X, Z));
-                Z.hi = f2_neg(Z.hi);
-                Z.lo = f2_neg(Z.lo);
-                df2 c = df2_add(X, Z);
-                c.hi.y = -c.hi.y;
-                c.lo.y = -c.lo.y;
-                sm_.both = df2_add(sm_.both, c);
+            if (mirror) {
+                df2 at_k, at_mk;
+                mirror_finish(ms, w_lane, at_k, at_mk);
+                sp_.both = df2_add(sp_.both, at_k);
+                sm_.both = df2_add(sm_.both, at_mk);
             }
             side_flush(sp_, fp);
             if (!self) side_flush(sm_, fm);
