@@ -439,8 +439,12 @@ constexpr int kGfSlots = 16;   // pair slots per block (the lanes of each half-w
 #define GBS_GF_MINBLOCKS 5     // resident blocks per SM the register budget is sized for
 #endif
 constexpr int kGfGroups = 8;   // trajectory groups per block, one half-warp each
-constexpr int kGfPer = 32;     // trajectories per half-warp between flushes to FP64
+constexpr int kGfPer = 32;     // trajectories per half-warp and tile
 constexpr int kGfTile = kGfGroups * kGfPer;  // trajectories per tile
+#ifndef GBS_GF_FLUSH_TILES
+#define GBS_GF_FLUSH_TILES 2   // tiles between flushes of the partials to FP64
+#endif
+constexpr int kGfFlushTiles = GBS_GF_FLUSH_TILES;
 
 // Double-float partial sums of one k over the trajectories of one tile.
 struct SidePartial {
@@ -524,13 +528,19 @@ __device__ __forceinline__ void side_term(df l1, df ph, bool in1, bool in2, bool
     s.pm_im = df_add(s.pm_im, df_mul(df_mul(df_sub(e1, e2), g.inv), sp));
 }
 
-// A tile's partials into the lane's FP64 sums f.  GB300's FP64 pipe is
-// narrow, so the FP32 small-term sums join the double-float partials on the
-// FP32 pipes, and the general formulas' partials are converted only when
-// used.
+// The FP32 small-term sums (at most kGfPer terms each) into the
+// double-float partials, on the FP32 pipes.
+__device__ __forceinline__ void side_fold_small(SidePartial &s) {
+    s.both = df2_add_f(s.both, f2(s.sm_re, s.sm_im));
+    s.sm_re = s.sm_im = 0.0f;
+}
+
+// The partials (small sums folded in) into the lane's FP64 sums f.  GB300's
+// FP64 pipe is narrow: the general formulas' partials are converted only
+// when used.
 __device__ __forceinline__ void side_flush(const SidePartial &s, double *f) {
-    f[0] += df_to_double(df_add_f(df2_x(s.both), s.sm_re));
-    f[kGfSlots] += df_to_double(df_add_f(df2_y(s.both), s.sm_im));
+    f[0] += df_to_double(df2_x(s.both));
+    f[kGfSlots] += df_to_double(df2_y(s.both));
     if (s.gen) {
         f[2 * kGfSlots] += df_to_double(s.pm_re);
         f[3 * kGfSlots] += df_to_double(s.pm_im);
@@ -605,6 +615,16 @@ __device__ __forceinline__ void gf_df_block(const GfRec *__restrict__ rec,
     const df2 w_lane = df2_make(df_neg(sn), cm1);  // i (z_k - 1)
     const GfRec *mine = sh.rec[warp] + kGfPer * (lane / kGfSlots);
 
+    // double-float partials over kGfFlushTiles tiles (the FP32 small-term
+    // sums folded into them after every tile), then into the FP64 sums
+    SidePartial sp_, sm_;
+    side_clear(sp_);
+    side_clear(sm_);
+    MirrorSums ms;
+    ms.s0 = ms.s1 = {f2(0.0f, 0.0f), f2(0.0f, 0.0f)};
+    ms.s2 = ms.s3 = f2(0.0f, 0.0f);
+    bool mirror = false;
+    int pending = 0;
     for (int64_t base = 0; base < cnt_r; base += kGfTile) {
 #pragma unroll
         for (int e = lane; e < 2 * kGfPer; e += 32) {
@@ -616,13 +636,6 @@ __device__ __forceinline__ void gf_df_block(const GfRec *__restrict__ rec,
         const int ntile = (cnt_r - base) < kGfTile ? (int)(cnt_r - base) : kGfTile;
         const int nmine = ntile > grp ? (ntile - grp + kGfGroups - 1) / kGfGroups : 0;
         if (kvalid) {
-            SidePartial sp_, sm_;
-            side_clear(sp_);
-            side_clear(sm_);
-            MirrorSums ms;
-            ms.s0 = ms.s1 = {f2(0.0f, 0.0f), f2(0.0f, 0.0f)};
-            ms.s2 = ms.s3 = f2(0.0f, 0.0f);
-            bool mirror = false;
             for (int m = 0; m < nmine; ++m) {
                 const GfRec &g = mine[m];
                 const bool in1 = d0 <= g.w1;
@@ -663,14 +676,24 @@ __device__ __forceinline__ void gf_df_block(const GfRec *__restrict__ rec,
                               sh.circ, K, sm_, fm);
                 }
             }
-            if (mirror) {
-                df2 at_k, at_mk;
-                mirror_finish(ms, w_lane, at_k, at_mk);
-                sp_.both = df2_add(sp_.both, at_k);
-                sm_.both = df2_add(sm_.both, at_mk);
+            side_fold_small(sp_);
+            side_fold_small(sm_);
+            if (++pending == kGfFlushTiles || base + kGfTile >= cnt_r) {
+                if (mirror) {
+                    df2 at_k, at_mk;
+                    mirror_finish(ms, w_lane, at_k, at_mk);
+                    sp_.both = df2_add(sp_.both, at_k);
+                    sm_.both = df2_add(sm_.both, at_mk);
+                    ms.s0 = ms.s1 = {f2(0.0f, 0.0f), f2(0.0f, 0.0f)};
+                    ms.s2 = ms.s3 = f2(0.0f, 0.0f);
+                    mirror = false;
+                }
+                side_flush(sp_, fp);
+                if (!self) side_flush(sm_, fm);
+                side_clear(sp_);
+                side_clear(sm_);
+                pending = 0;
             }
-            side_flush(sp_, fp);
-            if (!self) side_flush(sm_, fm);
         }
         __syncwarp();
     }
