@@ -119,6 +119,47 @@ def test_split_path_per_sample_gf(gbs, stream, prec):
         gbs.gbs_free_network(net)
 
 
+@pytest.mark.parametrize("K1", [2, 4, 8, 64])
+def test_split_path_per_sample_gf_small_K1(gbs, stream, K1):
+    """The double-float kernel at the smallest DFT sizes: every k pairs with
+    K1 - k, k = 0 and K1/2 with themselves, and the windows cover the whole
+    circle; per trajectory (n_sub = E, a ragged count of trajectories) the
+    same per-term bound as above, uniform and non-uniform loss."""
+    for general in (False, True):
+        net_def = wl.small_network(3, r=[0.5, 1.0, 0.2], t2=0.9, seed=13, general_loss=general)
+        E = 37
+        net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
+        n, nS = gbs.gbs_debug_samples(net, net_def.seed_s, 0, E)
+        gbs.gbs_sample(net, net_def.seed_s, 0, E, E, K1)
+        _, _, acc, cnt = gbs.gbs_get_accumulators(net)
+        gbs.gbs_free_network(net)
+        assert np.all(cnt == 1)
+        for e in range(E):
+            gm, gp = oracle.gf_sample(n[e], nS[e], K1)
+            for got, want in ((acc[0, e], gm), (acc[1, e], gp)):
+                err = np.abs(got - want)
+                assert np.all(err <= 1e-11 * np.abs(want) + GF_TERM_FLOOR), (K1, general, e)
+
+
+def test_split_path_gf_sums_over_many_tiles(gbs, stream):
+    """Sub-ensembles of 700 trajectories (two whole 256-trajectory tiles of
+    the double-float kernel and a ragged third, partials flushed to FP64 in
+    between): the device's sums against the oracle's sums of its FP64 terms
+    at the device's own n, n_S, within the per-term bound summed (|G| <= 1 on
+    uniform-loss trajectories)."""
+    net_def = wl.small_network(16, r=1.0, t2=0.9, seed=17)
+    E, n_sub, K1 = 2800, 4, 256
+    net = gbs.gbs_make_network(net_def.T, net_def.r, "bf16x3", stream)
+    n, nS = gbs.gbs_debug_samples(net, net_def.seed_s, 0, E)
+    gbs.gbs_sample(net, net_def.seed_s, 0, E, n_sub, K1)
+    _, _, acc, cnt = gbs.gbs_get_accumulators(net)
+    gbs.gbs_free_network(net)
+    want, cnt_o = oracle.accumulate_gf(n, nS, 0, n_sub, K1)
+    assert np.array_equal(cnt, cnt_o)
+    tol = (1e-11 + GF_TERM_FLOOR) * cnt[None, :, None]
+    assert np.all(np.abs(acc - want) <= tol), float(np.max(np.abs(acc - want)))
+
+
 @pytest.mark.parametrize("general", [False, True])
 def test_split_path_per_sample_gf_large_totals(gbs, stream, general):
     """The same per-term bound at photon totals of a few hundred (phases of
