@@ -39,16 +39,22 @@ UNIT = "samples/s"
 # captures (dram__bytes_read.sum + dram__bytes_write.sum of one launch,
 # divided by its trajectories; the operands grow in proportion to them),
 # keyed by (workload, precision, whether the GEMM also runs the next chunk's
-# sampler, CTA pair 1/2, band).  An entry holds only for the kernel version
+# sampler, CTA pair 1/2, band, keep_a bits).  An entry holds only for the kernel version
 # it was captured on: the table is emptied whenever the kernel changes, and a
 # run without an entry reports traffic null.
 GEMM_TRAFFIC_BYTES_PER_SAMPLE = {
-    ("m8000", "bf16x3", True, 2, 16, 0): (
-        (60.784051e9 + 1.111496e9) / 16768,
+    ("m8000", "bf16x3", True, 2, 16, 8): (
+        (19.29e9 + 1.11e9) / 16768,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 16768-trajectory sampling "
-        "launch (profiles/k_gemm_tc_pair_m8000.md), scaled to the average launch"),
+        "launch with aligned waves (profiles/k_gemm_tc_pair_m8000.md), scaled to the average "
+        "launch"),
+    ("m8000", "bf16x3", True, 2, 16, 0): (
+        (67.03e9 + 1.11e9) / 16768,
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 16768-trajectory sampling "
+        "launch without aligned waves (profiles/k_gemm_tc_pair_m8000.md), scaled to the "
+        "average launch"),
     ("m1000", "bf16x3", True, 2, 0, 0): (
-        (1.126301e9 + 1.087086e9) / 131072,
+        (1.28e9 + 1.09e9) / 131072,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 131072-trajectory sampling "
         "launch (profiles/k_gemm_tc_pair_m1000.md), scaled to the average launch"),
 }
@@ -378,7 +384,10 @@ def gbs_arm(args, wl_def):
                 "algorithmic_flops_per_sample": 8 * netdef.M * netdef.N,
                 "mma_products": P_products, "mma_issued_frac": P_products * achieved / peak,
                 "kernel": "k_gemm_tc", "launches": gemm_launches,
-                "gemm_config": {"cta_pair": pair == 2, "band": band, "keep_a_in_l2": bool(keep_a)},
+                "gemm_config": {"cta_pair": pair == 2, "band": band,
+                                "keep_a_in_l2": bool(keep_a & 1),
+                                "b_evict_first": bool(keep_a & 2),
+                                "waves_aligned": bool(keep_a & 8)},
                 "avg_launch_ms": gemm_ms / max(gemm_launches, 1),
                 "sm_mhz_median": clk.get("sm_mhz"),
                 "achieved_at_max_clock": (achieved * clk["sm_max_mhz"] / clk["sm_mhz"]
@@ -1153,7 +1162,7 @@ def main():
                          "autotuned (the default)")
     ap.add_argument("--gemm-band", type=int, default=0,
                     help="gbs_set_gemm_config band (with --gemm-pair 1 or 2)")
-    ap.add_argument("--gemm-keep-a", type=int, choices=[0, 1], default=0,
+    ap.add_argument("--gemm-keep-a", type=int, choices=list(range(16)), default=0,
                     help="gbs_set_gemm_config keep_a (with --gemm-pair 1 or 2)")
     ap.add_argument("--pair-autotune", type=int, choices=[0, 1], default=None,
                     help="gbs_set_pair_autotune before the run")

@@ -362,16 +362,22 @@ int gbs_network_info(gbs_net_t net, int *N, int *M, int *precision, int64_t *chu
  * trajectory tile side by side); band > 0: in bands of `band` mode-tile
  * groups (a group = the 1 or 2 mode tiles of a CTA or pair), the trajectory
  * tiles of a band in order, so that a band's A tiles are read again from L2.
- * keep_a = 1 (with band > 0): the band's A tiles are loaded with the
- * evict-last L2 policy.  pair = 0 returns to the autotuner, which times the
- * candidates (one CTA or pairs; bands of 16 and 8 with and without keep_a;
- * the plain order only where all of A fits in half the L2) on the first
- * chunk of each kind of launch (plain, and the one that also samples the
- * next chunk) in a loaded, interleaved sequence and keeps the fastest
- * (cached per size bucket of N and M for the process).  gbs_gemm_config
- * returns the configuration in use ((0, 0, 0) before the first chunk).
- * EINVAL: FP64 network, pair not 0..2, band < 0, keep_a not 0 or 1, NULL
- * pointers.
+ * keep_a is a set of bits: 1 (with band > 0) loads the band's A tiles with
+ * the evict-last L2 policy (4: for half of their lines); 2 loads the
+ * trajectory tiles with the evict-first policy; 8 aligns the waves of CTAs:
+ * before each tile of the second to the last full wave every CTA waits, for
+ * at most 50 us (a wait that times out is not an error), until all have
+ * issued the loads of their previous tile, so that tiles shared within a
+ * wave are read while the L2 holds them.  None of them changes a result.
+ * pair = 0 returns to the autotuner, which times the candidates (one CTA or
+ * pairs; bands of 16 and 8 with and without the evict-last policy; the
+ * plain order only where all of A fits in half the L2) on the first chunk
+ * of each kind of launch (plain, and the one that also samples the next
+ * chunk) in a loaded, interleaved sequence, keeps the fastest and adds the
+ * wave alignment to banded orders (cached per size bucket of N and M for
+ * the process).  gbs_gemm_config returns the configuration in use ((0, 0,
+ * 0) before the first chunk).  EINVAL: FP64 network, pair not 0..2,
+ * band < 0, keep_a not in 0..15, NULL pointers.
  */
 int gbs_set_gemm_config(gbs_net_t net, int pair, int band, int keep_a);
 int gbs_gemm_config(gbs_net_t net, int *pair, int *band, int *keep_a);

@@ -84,6 +84,7 @@ struct __align__(128) GemmNetDesc {
     int64_t count;           // trajectories (grouped launches)
     int64_t ld_part;         // leading dimension of nS_part
     double2 *nS_part;        // [mtiles][ld_part] per-tile n_S partials
+    unsigned int *wave_sync; // wave-alignment counter (single-network launches), or null
 };
 
 // Optional per-mode occupation output of the propagation GEMMs: n'_i of

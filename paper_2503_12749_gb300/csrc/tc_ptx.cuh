@@ -30,6 +30,22 @@ __device__ __forceinline__ void setmaxnreg_dec() {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegs));
 }
 
+// Wait until *ctr >= target (a counter the other CTAs of the launch
+// increment) or `limit_ns` have passed, whichever comes first, polling about
+// every 64 ns.  A rendezvous for performance only: the caller proceeds either
+// way, so nothing depends on the other CTAs running at the same time.
+__device__ __forceinline__ void counter_wait_soft(const unsigned int *ctr, unsigned int target,
+                                                  uint64_t limit_ns) {
+    const volatile unsigned int *c = ctr;
+    if (*c >= target) return;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        __nanosleep(64);
+        if (*c >= target) return;
+        if ((it & 15u) == 0u && globaltimer() - t0 > limit_ns) return;
+    }
+}
+
 // ---------------------------------------------------------------- mbarrier
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
@@ -112,6 +128,19 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
 __device__ __forceinline__ uint64_t policy_evict_last() {
     uint64_t p;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// evict-last for half of the lines (the rest evict-normal)
+__device__ __forceinline__ uint64_t policy_evict_last_half() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 0.5;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
 

@@ -32,7 +32,10 @@ def gbs():
 
 CONFIGS = [pytest.param((1, 0, 0), id="cta"), pytest.param((1, 1, 0), id="cta-band1"),
            pytest.param((1, 2, 1), id="cta-band2-keep"), pytest.param((2, 0, 0), id="pair"),
-           pytest.param((2, 1, 1), id="pair-band1-keep")]
+           pytest.param((2, 1, 1), id="pair-band1-keep"),
+           pytest.param((1, 2, 8), id="cta-band2-aligned"),
+           pytest.param((2, 1, 9), id="pair-band1-keep-aligned"),
+           pytest.param((2, 1, 6), id="pair-band1-policies")]
 
 
 @pytest.mark.parametrize("config", CONFIGS)
@@ -82,7 +85,9 @@ def test_autotuner_picks_a_configuration(gbs):
     assert gbs.gbs_gemm_config(net) == (0, 0, 0)
     gbs.gbs_sample(net, net_def.seed_s, 0, 5000, 10, 256)
     pair, band, keep = gbs.gbs_gemm_config(net)
-    assert pair in (1, 2) and band >= 0 and keep in (0, 1)
+    assert pair in (1, 2) and band >= 0 and keep in (0, 1, 8, 9)
+    # the waves of banded orders are aligned, those of the plain order not
+    assert bool(keep & 8) == (band > 0)
     gbs.gbs_free_network(net)
 
 
