@@ -112,7 +112,8 @@ int gbs_make_network_device(int N, int M, const double *T_dev, const double *r, 
  * except for the first call's allocations.  Errors: EINVAL, ENOMEM, ECUDA,
  * ETIMEOUT.
  * A call cuts its trajectories into the fewest chunks of at most the
- * network's chunk size (gbs_network_info), of equal size; every sum runs in
+ * network's chunk size (gbs_network_info): chunks of ceil(E / chunks)
+ * rounded up to a multiple of 128, the last one shorter; every sum runs in
  * a fixed order, so the same sequence of calls gives bitwise the same sums,
  * and so does a call split into calls at its own chunk boundaries (other
  * splits agree to rounding).  With the sampler folded into the GEMM

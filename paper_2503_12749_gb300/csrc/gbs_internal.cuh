@@ -252,12 +252,15 @@ int launch_gemm_tc(gbs_net *net, int64_t count, OccOut occ = OccOut());
 int launch_gemm_tc_sampling(gbs_net *net, int64_t count, const SampleJob &job,
                             OccOut occ = OccOut());
 // Trajectories per chunk of a gbs_sample call (and of a batch round) over E
-// trajectories: the fewest chunks of at most net->chunk, of equal size (the
-// last shorter by less than the number of chunks).
+// trajectories: the fewest chunks of at most net->chunk (a multiple of the
+// tile), the even split rounded up to whole 128-trajectory tiles, so that
+// no chunk but the last ends in a partly filled trajectory tile.
 inline int64_t chunk_step(const gbs_net *net, int64_t E) {
     if (E <= net->chunk) return E > 0 ? E : net->chunk;
     const int64_t nch = (E + net->chunk - 1) / net->chunk;
-    return (E + nch - 1) / nch;
+    const int64_t even = (E + nch - 1) / nch;
+    const int64_t tiled = (even + kTcTileSamples - 1) / kTcTileSamples * kTcTileSamples;
+    return tiled < net->chunk ? tiled : net->chunk;
 }
 
 // Output modes from which a network's sampling pays off inside its GEMM:

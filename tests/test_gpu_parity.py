@@ -259,15 +259,17 @@ def test_uniform_loss_identity_gpu(gbs, stream):
 def test_split_calls_equal_one_call(gbs, stream):
     """Calls continue the counter stream; splitting a call at its own chunk
     boundaries (a call of E cuts the fewest chunks of at most the network's
-    chunk size, of equal size) is bitwise identical, any split agrees to
-    rounding; get/set round-trips."""
+    chunk size: the even split rounded up to a multiple of 128, the last
+    chunk shorter) is bitwise identical, any split agrees to rounding;
+    get/set round-trips."""
     net_def = wl.small_network(40, r=0.8, t2=0.9, seed=5)
     for prec in ("fp64", "bf16x3"):
         net = gbs.gbs_make_network(net_def.T, net_def.r, prec, stream)
         chunk = gbs.gbs_network_info(net)[3]
         E = 2 * chunk + 77
         nch = -(-E // chunk)
-        step = -(-E // nch)
+        step = min(chunk, -(-(-(-E // nch)) // 128) * 128)
+        assert step % 128 == 0 and -(-E // step) == nch
         gbs.gbs_sample(net, net_def.seed_s, 0, E, 8, 128)
         _, _, acc1, cnt1 = gbs.gbs_get_accumulators(net)
         gbs.gbs_reset(net)
