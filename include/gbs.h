@@ -367,9 +367,10 @@ int gbs_network_info(gbs_net_t net, int *N, int *M, int *precision, int64_t *chu
  * the evict-last L2 policy (4: for half of their lines); 2 loads the
  * trajectory tiles with the evict-first policy; 8 aligns the waves of CTAs:
  * before each tile of the second to the last full wave every CTA waits, for
- * at most 50 us (a wait that times out is not an error), until all have
- * issued the loads of their previous tile, so that tiles shared within a
- * wave are read while the L2 holds them.  None of them changes a result.
+ * at most 50 us, until all have issued the loads of their previous tile, so
+ * that tiles shared within a wave are read while the L2 holds them (a wait
+ * that times out is not an error: that CTA stops waiting for the rest of the
+ * launch).  None of them changes a result.
  * pair = 0 returns to the autotuner, which times the candidates (one CTA or
  * pairs; bands of 16 and 8 with and without the evict-last policy; the
  * plain order only where all of A fits in half the L2) on the first chunk

@@ -419,15 +419,21 @@ __global__ void __launch_bounds__(threads_of<kSW>(), 1)
             // tile's loads, so that the CTAs of a wave read the A and B tiles
             // they share close together in time, while the L2 still holds
             // them (at m8000 the DRAM traffic falls to a third, and the
-            // power it saves raises the clock under the power limit)
+            // power it saves raises the clock under the power limit).  A
+            // producer whose wait times out (CTAs of the launch that are not
+            // resident, e.g. SMs held by another context) stops waiting for
+            // the rest of the launch but keeps counting its tiles, so that
+            // such a launch loses at most one wait per CTA
             const bool align = (keep_a & 8) && !tiles && nets->wave_sync != nullptr;
+            bool waiting = align;
             const int full_waves = ntiles / nunits;
             int j = 0;
             for (int tile = unit; ok && tile < ntiles; tile += nunits, ++j) {
                 if (align && j >= 1 && j < full_waves) {
                     atomicAdd(nets->wave_sync, 1u);
-                    ptx::counter_wait_soft(nets->wave_sync, (unsigned)j * gridDim.x,
-                                           kAlignWaitNs);
+                    if (waiting && !ptx::counter_wait_soft(nets->wave_sync, (unsigned)j * gridDim.x,
+                                                           kAlignWaitNs))
+                        waiting = false;
                 }
                 const TileRef tr = decode_tile<kPair>(tile, nets, tiles, count0, band, rank);
                 const GemmNetDesc *d = tr.d;

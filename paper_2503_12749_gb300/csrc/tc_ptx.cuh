@@ -32,17 +32,18 @@ __device__ __forceinline__ void setmaxnreg_dec() {
 
 // Wait until *ctr >= target (a counter the other CTAs of the launch
 // increment) or `limit_ns` have passed, whichever comes first, polling about
-// every 64 ns.  A rendezvous for performance only: the caller proceeds either
-// way, so nothing depends on the other CTAs running at the same time.
-__device__ __forceinline__ void counter_wait_soft(const unsigned int *ctr, unsigned int target,
+// every 64 ns; returns whether the target was reached.  A rendezvous for
+// performance only: the caller proceeds either way, so nothing depends on the
+// other CTAs running at the same time.
+__device__ __forceinline__ bool counter_wait_soft(const unsigned int *ctr, unsigned int target,
                                                   uint64_t limit_ns) {
     const volatile unsigned int *c = ctr;
-    if (*c >= target) return;
+    if (*c >= target) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
         __nanosleep(64);
-        if (*c >= target) return;
-        if ((it & 15u) == 0u && globaltimer() - t0 > limit_ns) return;
+        if (*c >= target) return true;
+        if ((it & 15u) == 0u && globaltimer() - t0 > limit_ns) return false;
     }
 }
 
