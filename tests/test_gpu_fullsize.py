@@ -43,6 +43,22 @@ def _sampled_parity(gbs, net, net_def, picks):
         assert abs(n[0] - no[0]) <= 1e-5 * max(abs(no[0]), 1.0)
 
 
+def _chunk_parity(gbs, net, T, r, seed, e0):
+    """One chunk of the network's size (less 77, so that its last trajectory
+    tile is ragged) through the GEMM in the tile configuration the network's
+    launches use; trajectories at both ends, across a tile boundary and in
+    the middle against the oracle one by one."""
+    count = gbs.gbs_network_info(net)[3] - 77
+    n, nS = gbs.gbs_debug_samples(net, seed, e0, count)
+    for q in (0, 127, 128, count // 2 + 7, count - 1):
+        no, nSo = oracle.samples(T, r, seed, e0 + q, 1)
+        _, _, ap, bp = oracle.sample_amplitudes(T, r, seed, e0 + q)
+        S = float(np.sum(np.abs(ap) * np.abs(bp)))
+        assert abs(nS[q] - nSo[0]) <= 2.0 ** -14 * S, (q, nS[q], nSo[0])
+        assert abs(n[q] - no[0]) <= 1e-5 * max(abs(no[0]), 1.0)
+    assert np.all(np.isfinite(nS))
+
+
 @pytest.mark.parametrize("name", ["m1000", "m4000"])
 def test_full_workload(gbs, name):
     import torch
@@ -63,6 +79,8 @@ def test_full_workload(gbs, name):
     res = agreement(P[0], P[1], Pex)
     assert res["ok"], res
     assert abs(P[0].sum() - 1.0) < 1e-9
+    # a whole chunk in the configuration the ensemble's launches were tuned to
+    _chunk_parity(gbs, net, net_def.T, net_def.r, net_def.seed_s, w.E // 3)
     gbs.gbs_free_network(net)
 
 
@@ -110,6 +128,11 @@ def test_m8000_workload(gbs):
         assert abs(n[0] - no[0]) <= 1e-5 * max(abs(no[0]), 1.0)
     gbs.gbs_sample(net, seed, 0, w.E, w.n_sub, w.K1)
     P = gbs.gbs_binned_counts(net, 0, w.K1)
+    # a whole chunk through the configuration the bench's launches use: a
+    # banded tile order with aligned waves (A does not fit in L2)
+    pair, band, keep = gbs.gbs_gemm_config(net)
+    assert band > 0 and keep & 8, (pair, band, keep)
+    _chunk_parity(gbs, net, T, r, seed, w.E // 2 + 5)
     gbs.gbs_free_network(net)
     mu = ex.eigenvalues_uniform_loss(r, w.t2)
     z = ex.roots_of_unity(w.K1)
