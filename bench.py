@@ -53,6 +53,14 @@ GEMM_TRAFFIC_BYTES_PER_SAMPLE = {
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 16768-trajectory sampling "
         "launch without aligned waves (profiles/k_gemm_tc_pair_m8000.md), scaled to the "
         "average launch"),
+    ("m4000", "bf16x3", True, 2, 16, 9): (
+        (8.53e9 + 1.11e9) / 33408,
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 33408-trajectory sampling "
+        "launch with aligned waves and the evict-last policy on A, scaled to the average launch"),
+    ("m4000", "bf16x3", True, 2, 16, 8): (
+        (8.54e9 + 1.11e9) / 33408,
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 33408-trajectory sampling "
+        "launch with aligned waves, scaled to the average launch"),
     ("m1000", "bf16x3", True, 2, 0, 0): (
         (1.28e9 + 1.09e9) / 131072,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 131072-trajectory sampling "
