@@ -642,7 +642,7 @@ def batch_arm(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms_total = ev0.elapsed_time(ev1)
-    (pair, band), rounds, tiles = gbs.gbs_batch_info(batch)
+    (pair, band, stages), rounds, tiles = gbs.gbs_batch_info(batch)
     # kernels per step: per network and chunk a finalize, a generating-
     # function launch and a sampler (networks of >= 900 output modes with
     # more than one chunk: round 0 only, the grouped GEMMs draw the rest);
@@ -679,7 +679,8 @@ def batch_arm(args):
         "config": {"workload": f"batch{len(wls)}: {len(wls)} Haar networks, N=M log-uniform "
                                "[100,2000], r_j~U[0.5,1.5], t~U[0.5,0.995], E=2^18 each",
                    "N": [d.N for d in defs], "K1": K1s, "n_sub": n_sub[0],
-                   "samples_per_step": sum(E), "gemm_config_chosen": {"cta_pair": pair == 2, "band": band},
+                   "samples_per_step": sum(E), "gemm_config_chosen": {"cta_pair": pair == 2, "band": band,
+                                                          "ring_stages": stages},
                    "rounds": rounds,
                    "gemm_tiles_per_call": tiles,
                    "note": "one CUDA graph per gbs_sample_batch call; GEMM kernel time from "

@@ -449,12 +449,16 @@ int gbs_sampler_fusion(gbs_net_t net, int *active);
  * gbs_set_batch_config -- the batch GEMM's configuration: pair 1 (one CTA
  *   per tile) or 2 (CTA pairs), band 0 (every network's tiles in the plain
  *   order) or > 0 (bands of that many mode-tile groups within each
- *   network); pair 0 returns to the autotuner, which times one CTA per tile
- *   and CTA pairs (gbs_set_pair_autotune), each with bands 0 and 8, on the
- *   first call's first round.  Every configuration gives bitwise the same
- *   sums.  EINVAL: pair not 0..2, band < 0.
- * gbs_batch_info -- GEMM configuration in use (pair, band; 0, 0 before the
- *   first call), rounds and GEMM tiles of the last call.
+ *   network), stages 0 (the deepest operand ring that fits in shared
+ *   memory: 4 stages for one CTA and 6 for a pair with 3 products, 3 and 4
+ *   with 6 products) or that depth, or one stage less; pair 0 returns to the
+ *   autotuner, which times one CTA per tile and CTA pairs
+ *   (gbs_set_pair_autotune), each with bands 0 and 8 and both ring depths,
+ *   on the first call's first round.  Every configuration gives bitwise the
+ *   same sums.  EINVAL: pair not 0..2, band < 0, stages not 0 or one of the
+ *   two depths of (products, pair).
+ * gbs_batch_info -- GEMM configuration in use (pair, band, ring stages;
+ *   0, 0, 0 before the first call), rounds and GEMM tiles of the last call.
  * With phase timing enabled on the batch's first network (gbs_profile_enable),
  * gbs_sample_batch issues its rounds directly instead of as a graph and
  * attributes the grouped GEMM launches to that network's GEMM phase; each
@@ -466,8 +470,9 @@ typedef struct gbs_batch *gbs_batch_t;
 int gbs_make_batch(gbs_net_t *nets, int count, gbs_batch_t *out);
 int gbs_sample_batch(gbs_batch_t batch, const uint64_t *seeds, const uint64_t *first_sample,
                      const int64_t *E, const int *n_sub, const int *K1);
-int gbs_set_batch_config(gbs_batch_t batch, int pair, int band);
-int gbs_batch_info(gbs_batch_t batch, int *pair, int *band, int *rounds, int64_t *tiles);
+int gbs_set_batch_config(gbs_batch_t batch, int pair, int band, int stages);
+int gbs_batch_info(gbs_batch_t batch, int *pair, int *band, int *stages, int *rounds,
+                   int64_t *tiles);
 void gbs_free_batch(gbs_batch_t batch);
 
 /*

@@ -110,8 +110,8 @@ def lib():
         L.gbs_make_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
         L.gbs_sample_batch.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64),
                                        ctypes.POINTER(ctypes.c_uint64), i64p, ip, ip]
-        L.gbs_batch_info.argtypes = [vp, ip, ip, ip, i64p]
-        L.gbs_set_batch_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.gbs_batch_info.argtypes = [vp, ip, ip, ip, ip, i64p]
+        L.gbs_set_batch_config.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.gbs_free_batch.argtypes = [vp]
         L.gbs_free_batch.restype = None
         L.gbs_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -475,21 +475,23 @@ def gbs_sample_batch(batch: Batch, seeds, first_sample, E, n_sub, K1) -> None:
                                   i32(*[int(x) for x in K1])))
 
 
-def gbs_set_batch_config(batch: Batch, pair: int, band: int = 0) -> None:
-    """The batch GEMM's configuration (pair 1 or 2, band >= 0); pair 0 = autotune."""
-    _check(lib().gbs_set_batch_config(batch.handle, int(pair), int(band)))
+def gbs_set_batch_config(batch: Batch, pair: int, band: int = 0, stages: int = 0) -> None:
+    """The batch GEMM's configuration (pair 1 or 2, band >= 0, operand-ring
+    stages: 0 = the deepest); pair 0 = autotune."""
+    _check(lib().gbs_set_batch_config(batch.handle, int(pair), int(band), int(stages)))
 
 
 def gbs_batch_info(batch: Batch):
-    """((pair, band) of the batch GEMM, rounds, GEMM tiles) of the last
-    gbs_sample_batch."""
+    """((pair, band, ring stages) of the batch GEMM, rounds, GEMM tiles) of
+    the last gbs_sample_batch."""
     c = ctypes.c_int()
     b = ctypes.c_int()
+    st = ctypes.c_int()
     r = ctypes.c_int()
     t = ctypes.c_int64()
-    _check(lib().gbs_batch_info(batch.handle, ctypes.byref(c), ctypes.byref(b), ctypes.byref(r),
-                                ctypes.byref(t)))
-    return (c.value, b.value), r.value, t.value
+    _check(lib().gbs_batch_info(batch.handle, ctypes.byref(c), ctypes.byref(b), ctypes.byref(st),
+                                ctypes.byref(r), ctypes.byref(t)))
+    return (c.value, b.value, st.value), r.value, t.value
 
 
 def gbs_free_batch(batch: Batch) -> None:

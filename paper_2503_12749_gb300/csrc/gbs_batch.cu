@@ -22,9 +22,9 @@
 // small networks' kernels run side by side instead of one after another
 // (each network's own launches keep their order, so the results do not
 // change).  The
-// grouped GEMM's tile configuration (one CTA per tile, or CTA pairs) is
-// chosen by timing the candidates on the batch's first round (cached per
-// batch).
+// grouped GEMM's configuration (one CTA per tile or CTA pairs; plain or
+// banded tile order; the deepest operand ring or one stage less) is chosen
+// by timing the candidates on the batch's first round (cached per batch).
 #include "gbs_internal.cuh"
 
 #include <algorithm>
@@ -38,6 +38,7 @@ struct gbs_batch {
     int P = 0;
     int pair = 0;     // GEMM tiles per CTA (1) or per CTA pair (2); 0 = not tuned yet
     int band = 0;     // tile order within a network: 0 plain, > 0 bands of that many groups
+    int shallow = 0;  // operand ring: 0 the deepest that fits, 1 one stage less
     bool forced = false;  // set by gbs_set_batch_config
     int sm_count = 0;
     // device copies of the per-round descriptors and tile lists
@@ -202,7 +203,7 @@ int upload_rounds(gbs_batch *b, const RoundPlan &rp) {
     return GBS_OK;
 }
 
-int round_gemm(gbs_batch *b, const RoundPlan &rp, int r, int pair) {
+int round_gemm(gbs_batch *b, const RoundPlan &rp, int r, int pair, int shallow) {
     const int nn = (int)b->nets.size();
     const int off = rp.tile_off[r], nt = rp.tile_off[r + 1] - off;
     gbs_net *n0 = b->nets[0];
@@ -216,11 +217,11 @@ int round_gemm(gbs_batch *b, const RoundPlan &rp, int r, int pair) {
         sj.n = nn;
         rc = launch_gemm_grouped_sampling(b->stream, b->sm_count, pair, n0->wait_ns,
                                           b->d_desc + (size_t)r * nn, b->d_tiles + off, nt,
-                                          n0->d_flags + 1, sj);
+                                          n0->d_flags + 1, sj, shallow);
     } else {
         rc = launch_gemm_grouped(b->stream, b->sm_count, b->P, pair, 0, 0, n0->wait_ns,
                                  b->d_desc + (size_t)r * nn, b->d_tiles + off, nt, 0,
-                                 n0->d_flags + 1);
+                                 n0->d_flags + 1, OccOut(), shallow);
     }
     prof_mark(n0, GBS_PHASE_GEMM, 1, false);
     return rc;
@@ -299,7 +300,7 @@ int run_rounds(gbs_batch *b, const RoundPlan &rp, const uint64_t *seeds, const u
     int rc = GBS_OK, swaps = 0;
     for (int r = 0; r < rp.rounds && rc == GBS_OK; ++r) {
         if ((rc = round_front(b, rp, r, seeds, first, branches))) break;
-        if ((rc = round_gemm(b, rp, r, b->pair))) break;
+        if ((rc = round_gemm(b, rp, r, b->pair, b->shallow))) break;
         if ((rc = round_back(b, rp, r, first, branches))) break;
         if (rp.fold) {
             swap_all(b, rp);
@@ -312,11 +313,16 @@ int run_rounds(gbs_batch *b, const RoundPlan &rp, const uint64_t *seeds, const u
 
 // The batch GEMM's candidate configurations: one CTA per tile or CTA pairs
 // (where the autotuner takes pairs), each with the plain tile order and
-// bands of 8 groups within every network.
-std::vector<std::pair<int, int>> batch_candidates() {
-    std::vector<std::pair<int, int>> c;
+// bands of 8 groups within every network, each with the deepest operand ring
+// that fits in shared memory and a ring one stage shallower.
+struct BatchCand {
+    int pair, band, shallow;
+};
+std::vector<BatchCand> batch_candidates() {
+    std::vector<BatchCand> c;
     for (int pair = 1; pair <= (tc_pair_autotune() ? 2 : 1); ++pair)
-        for (int band : {0, 8}) c.push_back({pair, band});
+        for (int band : {0, 8})
+            for (int shallow : {0, 1}) c.push_back({pair, band, shallow});
     return c;
 }
 
@@ -326,7 +332,7 @@ std::vector<std::pair<int, int>> batch_candidates() {
 // launches of each, candidates interleaved, times summed.  Every candidate
 // gives bitwise the same sums.
 int tune_batch(gbs_batch *b, const int64_t *E, const uint64_t *seeds, const uint64_t *first) {
-    const std::vector<std::pair<int, int>> cand = batch_candidates();
+    const std::vector<BatchCand> cand = batch_candidates();
     std::vector<RoundPlan> plans(cand.size());
     std::vector<float> total(cand.size(), 0.0f);
     int rc = GBS_OK;
@@ -334,7 +340,7 @@ int tune_batch(gbs_batch *b, const int64_t *E, const uint64_t *seeds, const uint
     GBS_CUDA_TRY(cudaEventCreate(&e0));
     GBS_CUDA_TRY(cudaEventCreate(&e1));
     for (size_t c = 0; c < cand.size() && rc == GBS_OK; ++c)
-        rc = build_rounds(b, E, cand[c].first, cand[c].second, plans[c]);
+        rc = build_rounds(b, E, cand[c].pair, cand[c].band, plans[c]);
     // round 0's operands (the samplers do not depend on the tile list)
     if (rc == GBS_OK && (rc = upload_rounds(b, plans[0])) == GBS_OK)
         rc = round_front(b, plans[0], 0, seeds, first);
@@ -343,7 +349,8 @@ int tune_batch(gbs_batch *b, const int64_t *E, const uint64_t *seeds, const uint
             if ((rc = upload_rounds(b, plans[c]))) break;
             const int reps = pass == 0 ? 1 : 2;
             cudaEventRecord(e0, b->stream);
-            for (int q = 0; q < reps && rc == GBS_OK; ++q) rc = round_gemm(b, plans[c], 0, cand[c].first);
+            for (int q = 0; q < reps && rc == GBS_OK; ++q)
+                rc = round_gemm(b, plans[c], 0, cand[c].pair, cand[c].shallow);
             if (rc) break;
             cudaEventRecord(e1, b->stream);
             if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -361,8 +368,9 @@ int tune_batch(gbs_batch *b, const int64_t *E, const uint64_t *seeds, const uint
     size_t best = 0;
     for (size_t c = 1; c < cand.size(); ++c)
         if (total[c] < total[best]) best = c;
-    b->pair = cand[best].first;
-    b->band = cand[best].second;
+    b->pair = cand[best].pair;
+    b->band = cand[best].band;
+    b->shallow = cand[best].shallow;
     return GBS_OK;
 }
 
@@ -434,7 +442,7 @@ int gbs_sample_batch(gbs_batch_t b, const uint64_t *seeds, const uint64_t *first
     for (int i = 0; i < nn; ++i) {
         gbs_net *net = b->nets[i];
         fold_net[i] = b->P == 3 && E[i] > net->chunk && fold_wanted(net) &&
-                      tc_sampling_ready(net, true);
+                      (!b->shallow || tc_shallow_sampling_ok()) && tc_sampling_ready(net, true);
         fold = fold || fold_net[i];
     }
     RoundPlan rp;
@@ -478,20 +486,32 @@ int gbs_sample_batch(gbs_batch_t b, const uint64_t *seeds, const uint64_t *first
     return GBS_OK;
 }
 
-int gbs_set_batch_config(gbs_batch_t b, int pair, int band) {
+int gbs_set_batch_config(gbs_batch_t b, int pair, int band, int stages) {
     if (!b) return set_error(GBS_EINVAL, "null batch");
     if (pair < 0 || pair > 2) return set_error(GBS_EINVAL, "pair must be 0 (auto), 1 or 2");
     if (band < 0) return set_error(GBS_EINVAL, "band must be >= 0");
+    int shallow = 0;
+    if (pair && stages) {
+        if (stages == tc_ring_stages(b->P, pair, 1))
+            shallow = 1;
+        else if (stages != tc_ring_stages(b->P, pair, 0))
+            return set_error(GBS_EINVAL, "stages must be 0 (deepest), %d or %d for %d products and pair %d",
+                             tc_ring_stages(b->P, pair, 0), tc_ring_stages(b->P, pair, 1), b->P, pair);
+    } else if (stages < 0) {
+        return set_error(GBS_EINVAL, "stages must be >= 0");
+    }
     b->pair = pair;
     b->band = pair ? band : 0;
+    b->shallow = pair ? shallow : 0;
     b->forced = pair != 0;
     return GBS_OK;
 }
 
-int gbs_batch_info(gbs_batch_t b, int *pair, int *band, int *rounds, int64_t *tiles) {
+int gbs_batch_info(gbs_batch_t b, int *pair, int *band, int *stages, int *rounds, int64_t *tiles) {
     if (!b) return set_error(GBS_EINVAL, "null batch");
     if (pair) *pair = b->pair;
     if (band) *band = b->band;
+    if (stages) *stages = b->pair ? tc_ring_stages(b->P, b->pair, b->shallow) : 0;
     if (rounds) *rounds = b->last_rounds;
     if (tiles) *tiles = b->last_tiles;
     return GBS_OK;

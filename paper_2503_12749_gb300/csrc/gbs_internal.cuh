@@ -300,15 +300,22 @@ int tc_fill_desc(gbs_net *net, GemmNetDesc *out, bool alt = false);  // alt: the
 // One launch over the tiles of many networks (d_tiles: {net, mode-tile group,
 // trajectory tile} per entry; NULL = closed-form tiles of d_nets[0] with
 // count0 trajectories in bands of `band` groups); wait_ns bounds every
-// pipeline wait of the kernel.
+// pipeline wait of the kernel.  shallow = 1 runs the operand ring one stage
+// shallower than the deepest that fits (a batch autotuner candidate; the
+// results are bitwise the same).
 int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int pair, int band, int keep_a,
                         uint64_t wait_ns, const GemmNetDesc *d_nets, const int4 *d_tiles,
                         int ntiles, int64_t count0, unsigned long long *err,
-                        OccOut occ = OccOut());
+                        OccOut occ = OccOut(), int shallow = 0);
 // The same launch (3 products, listed tiles) whose spare warps run `jobs`.
 int launch_gemm_grouped_sampling(cudaStream_t stream, int sm_count, int pair, uint64_t wait_ns,
                                  const GemmNetDesc *d_nets, const int4 *d_tiles, int ntiles,
-                                 unsigned long long *err, const SampleJobs &jobs);
+                                 unsigned long long *err, const SampleJobs &jobs,
+                                 int shallow = 0);
+// Stages of the GEMM's operand ring for (products, pair, shallow).
+int tc_ring_stages(int P, int pair, int shallow);
+// Whether the sampling GEMM variants with the shallower ring can run.
+bool tc_shallow_sampling_ok();
 
 // Finalise n_S (fixed-order sum of tile partials) and the evaluation windows.
 int launch_finalize(gbs_net *net, int64_t count);

@@ -119,6 +119,8 @@ struct Cfg {
     static constexpr int kAPlane = 128 * 64;
     static constexpr int kBPlane = (256 / kPair) * 64;
     static constexpr int kStageBytes = kPlanes * (kAPlane + kBPlane);
+    // the deepest ring that fits in shared memory (the default); the batch
+    // autotuner also times a ring one stage shallower
     static constexpr int kStages = (P == 3) ? (kPair == 1 ? 4 : 6) : (kPair == 1 ? 3 : 4);
 };
 constexpr int kBarBytes = 1024;
@@ -134,10 +136,9 @@ template <int P>
 constexpr int occ_stage_bytes() {
     return P == 3 ? kEpiWarpsFwd * kOccWarpFloats * 4 : 0;
 }
-template <int P, int kPair>
+template <int P, int kPair, int kSt = Cfg<P, kPair>::kStages>
 constexpr int smem_bytes() {
-    return 1024 + Cfg<P, kPair>::kStages * Cfg<P, kPair>::kStageBytes + kBarBytes + kRedBytes +
-           occ_stage_bytes<P>();
+    return 1024 + kSt * Cfg<P, kPair>::kStageBytes + kBarBytes + kRedBytes + occ_stage_bytes<P>();
 }
 static_assert(smem_bytes<3, 1>() <= 227 * 1024, "shared memory of the 3-product GEMM");
 static_assert(smem_bytes<6, 1>() <= 227 * 1024, "shared memory of the 6-product GEMM");
@@ -320,16 +321,17 @@ __device__ __forceinline__ void warp_transpose_reduce32(float (&v)[32], int lane
     }
 }
 
-template <int P, int kPair, int kSW>
+template <int P, int kPair, int kSW, int kSt = Cfg<P, kPair>::kStages>
 __global__ void __launch_bounds__(threads_of<kSW>(), 1)
     k_gemm_tc(const GemmNetDesc *__restrict__ nets, const int4 *__restrict__ tiles, int ntiles,
               int64_t count0, int band, int keep_a, uint64_t wait_ns,
               unsigned long long *err_ptr, OccOut occ, const SampleJobs sj) {
     static_assert(kSW == 0 || P == 3, "the sampling variant runs the 3-product GEMM");
     static_assert(kPair == 1 || kPair == 2, "one CTA or a CTA pair per tile group");
-    constexpr int kE0 = epi_warp0<kSW>();  // first epilogue warp
     using C = Cfg<P, kPair>;
-    constexpr int kStages = C::kStages;
+    static_assert(kSt >= 2 && kSt <= C::kStages, "ring of 2 .. kStages stages");
+    constexpr int kE0 = epi_warp0<kSW>();  // first epilogue warp
+    constexpr int kStages = kSt;
     constexpr int kPl = C::kPlanes;
     constexpr uint32_t kIdesc = idesc<kPair>();
     extern __shared__ uint8_t smem_raw[];
@@ -884,11 +886,16 @@ std::map<std::tuple<int, int, int, int>, GemmCfg> g_tune;
 // ask for them).
 bool g_pair_autotune = true;
 
-template <int P, int kPair, int kSW>
+template <int P, int kPair, int kSW, int kSt = Cfg<P, kPair>::kStages>
 cudaError_t set_smem_attr() {
-    return cudaFuncSetAttribute(k_gemm_tc<P, kPair, kSW>,
+    return cudaFuncSetAttribute(k_gemm_tc<P, kPair, kSW, kSt>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_bytes<P, kPair>());
+                                smem_bytes<P, kPair, kSt>());
+}
+// the ring one stage shallower than the deepest (batch autotuner candidate)
+template <int P, int kPair>
+constexpr int shallow_stages() {
+    return Cfg<P, kPair>::kStages - 1;
 }
 
 int ensure_attrs() {
@@ -902,6 +909,12 @@ int ensure_attrs() {
     GBS_CUDA_TRY((set_smem_attr<6, 2, 0>()));
     GBS_CUDA_TRY((set_smem_attr<3, 1, kSampWG>()));
     GBS_CUDA_TRY((set_smem_attr<3, 2, kSampWG>()));
+    GBS_CUDA_TRY((set_smem_attr<3, 1, 0, shallow_stages<3, 1>()>()));
+    GBS_CUDA_TRY((set_smem_attr<3, 2, 0, shallow_stages<3, 2>()>()));
+    GBS_CUDA_TRY((set_smem_attr<6, 1, 0, shallow_stages<6, 1>()>()));
+    GBS_CUDA_TRY((set_smem_attr<6, 2, 0, shallow_stages<6, 2>()>()));
+    GBS_CUDA_TRY((set_smem_attr<3, 1, kSampWG, shallow_stages<3, 1>()>()));
+    GBS_CUDA_TRY((set_smem_attr<3, 2, kSampWG, shallow_stages<3, 2>()>()));
     if (dev >= 0 && dev < 64) g_attr_set[dev] = true;
     return GBS_OK;
 }
@@ -925,7 +938,28 @@ bool sampling_kernels_ok() {
     return state == 1;
 }
 
-template <int P, int kPair, int kSW>
+// The same check for the sampling variants with the shallower ring (the
+// batch autotuner leaves them out of its candidates when it fails).
+bool shallow_sampling_kernels_ok() {
+    static int state = -1;
+    std::lock_guard<std::mutex> lock(g_tc_mu);
+    if (state < 0) {
+        cudaFuncAttributes a1 = {}, a2 = {};
+        constexpr int R = regs_launch<kSampWG>(), T = threads_of<kSampWG>();
+        const bool ok =
+            cudaFuncGetAttributes(&a1, k_gemm_tc<3, 1, kSampWG, shallow_stages<3, 1>()>) ==
+                cudaSuccess &&
+            cudaFuncGetAttributes(&a2, k_gemm_tc<3, 2, kSampWG, shallow_stages<3, 2>()>) ==
+                cudaSuccess &&
+            a1.numRegs == R && a2.numRegs == R && a1.maxThreadsPerBlock >= T &&
+            a2.maxThreadsPerBlock >= T;
+        if (!ok) cudaGetLastError();
+        state = ok ? 1 : 0;
+    }
+    return state == 1;
+}
+
+template <int P, int kPair, int kSW, int kSt = Cfg<P, kPair>::kStages>
 int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets, const int4 *d_tiles,
                    int ntiles, int64_t count0, int band, int keep_a, uint64_t wait_ns,
                    unsigned long long *err, OccOut occ, const SampleJobs &jobs) {
@@ -934,7 +968,7 @@ int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets,
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kPair * units);
     cfg.blockDim = dim3(threads_of<kSW>());
-    cfg.dynamicSmemBytes = smem_bytes<P, kPair>();
+    cfg.dynamicSmemBytes = smem_bytes<P, kPair, kSt>();
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     int na = 0;
@@ -947,7 +981,7 @@ int launch_variant(cudaStream_t stream, int sm_count, const GemmNetDesc *d_nets,
     }
     cfg.attrs = attr;
     cfg.numAttrs = na;
-    cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_tc<P, kPair, kSW>, d_nets, d_tiles, ntiles,
+    cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_tc<P, kPair, kSW, kSt>, d_nets, d_tiles, ntiles,
                                         count0, band, keep_a, wait_ns, err, occ, jobs);
     if (le != cudaSuccess)
         return set_error(GBS_ECUDA, "launch of the GEMM (%d products, %s%s) failed: %s", P,
@@ -1007,24 +1041,53 @@ int bucket(int v) {
     return b;
 }
 
+// Dispatch of a grouped launch to the instantiation of (pair, ring depth):
+// shallow = 0 the deepest ring, 1 one stage less.
+template <int P, int kSW>
+int launch_grouped_ring(cudaStream_t stream, int sm_count, int pair, int shallow,
+                        const GemmNetDesc *d_nets, const int4 *d_tiles, int ntiles,
+                        int64_t count0, int band, int keep_a, uint64_t wait_ns,
+                        unsigned long long *err, OccOut occ, const SampleJobs &jobs) {
+    if (pair == 1)
+        return shallow
+                   ? launch_variant<P, 1, kSW, shallow_stages<P, 1>()>(
+                         stream, sm_count, d_nets, d_tiles, ntiles, count0, band, keep_a, wait_ns,
+                         err, occ, jobs)
+                   : launch_variant<P, 1, kSW>(stream, sm_count, d_nets, d_tiles, ntiles, count0,
+                                               band, keep_a, wait_ns, err, occ, jobs);
+    return shallow ? launch_variant<P, 2, kSW, shallow_stages<P, 2>()>(
+                         stream, sm_count, d_nets, d_tiles, ntiles, count0, band, keep_a, wait_ns,
+                         err, occ, jobs)
+                   : launch_variant<P, 2, kSW>(stream, sm_count, d_nets, d_tiles, ntiles, count0,
+                                               band, keep_a, wait_ns, err, occ, jobs);
+}
+
 }  // namespace
+
+int tc_ring_stages(int P, int pair, int shallow) {
+    const int deep = P == 3 ? (pair == 1 ? Cfg<3, 1>::kStages : Cfg<3, 2>::kStages)
+                            : (pair == 1 ? Cfg<6, 1>::kStages : Cfg<6, 2>::kStages);
+    return deep - (shallow ? 1 : 0);
+}
+
+bool tc_shallow_sampling_ok() { return sampling_kernels_ok() && shallow_sampling_kernels_ok(); }
 
 int launch_gemm_grouped(cudaStream_t stream, int sm_count, int P, int pair, int band, int keep_a,
                         uint64_t wait_ns, const GemmNetDesc *d_nets, const int4 *d_tiles,
-                        int ntiles, int64_t count0, unsigned long long *err, OccOut occ) {
+                        int ntiles, int64_t count0, unsigned long long *err, OccOut occ,
+                        int shallow) {
     int rc;
     if ((rc = ensure_attrs())) return rc;
     if (occ.p && (d_tiles || occ.ld % 128 != 0 || occ.ld < count0))
         return set_error(GBS_EINVAL, "occupation output needs closed-form tiles and ld >= count, ld %% 128 == 0");
     if (pair != 1 && pair != 2) return set_error(GBS_EINVAL, "GEMM tiles per CTA pair must be 1 or 2");
+    if (shallow != 0 && shallow != 1) return set_error(GBS_EINVAL, "ring depth option must be 0 or 1");
     const SampleJobs none;
     if (P == 3)
-        return pair == 1
-                   ? launch_variant<3, 1, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, keep_a, wait_ns, err, occ, none)
-                   : launch_variant<3, 2, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, keep_a, wait_ns, err, occ, none);
-    return pair == 1
-               ? launch_variant<6, 1, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, keep_a, wait_ns, err, occ, none)
-               : launch_variant<6, 2, 0>(stream, sm_count, d_nets, d_tiles, ntiles, count0, band, keep_a, wait_ns, err, occ, none);
+        return launch_grouped_ring<3, 0>(stream, sm_count, pair, shallow, d_nets, d_tiles, ntiles,
+                                         count0, band, keep_a, wait_ns, err, occ, none);
+    return launch_grouped_ring<6, 0>(stream, sm_count, pair, shallow, d_nets, d_tiles, ntiles,
+                                     count0, band, keep_a, wait_ns, err, occ, none);
 }
 
 int tc_fill_desc(gbs_net *net, GemmNetDesc *out, bool alt) {
@@ -1037,15 +1100,16 @@ int tc_fill_desc(gbs_net *net, GemmNetDesc *out, bool alt) {
 
 int launch_gemm_grouped_sampling(cudaStream_t stream, int sm_count, int pair, uint64_t wait_ns,
                                  const GemmNetDesc *d_nets, const int4 *d_tiles, int ntiles,
-                                 unsigned long long *err, const SampleJobs &jobs) {
+                                 unsigned long long *err, const SampleJobs &jobs, int shallow) {
     int rc;
     if ((rc = ensure_attrs())) return rc;
     if (!sampling_kernels_ok()) return set_error(GBS_EINVAL, "sampling GEMM unavailable");
     if (pair != 1 && pair != 2) return set_error(GBS_EINVAL, "GEMM tiles per CTA pair must be 1 or 2");
-    return pair == 1 ? launch_variant<3, 1, kSampWG>(stream, sm_count, d_nets, d_tiles, ntiles, 0, 0,
-                                                     0, wait_ns, err, OccOut(), jobs)
-                     : launch_variant<3, 2, kSampWG>(stream, sm_count, d_nets, d_tiles, ntiles, 0, 0,
-                                                     0, wait_ns, err, OccOut(), jobs);
+    if (shallow != 0 && shallow != 1) return set_error(GBS_EINVAL, "ring depth option must be 0 or 1");
+    if (shallow && !shallow_sampling_kernels_ok())
+        return set_error(GBS_EINVAL, "sampling GEMM with the shallower ring unavailable");
+    return launch_grouped_ring<3, kSampWG>(stream, sm_count, pair, shallow, d_nets, d_tiles,
+                                           ntiles, 0, 0, 0, wait_ns, err, OccOut(), jobs);
 }
 
 int tc_products(gbs_net *net) { return net->tc ? net->tc->P : 0; }

@@ -112,8 +112,10 @@ def test_batch_equals_per_network_runs(gbs, own_stream):
     singles = [gbs.gbs_make_network(d.T, d.r, "bf16x3", sptr) for d in defs]
     batch = gbs.gbs_make_batch(nets)
     gbs.gbs_sample_batch(batch, seeds, first, E, n_sub, K1)
-    (pair, band), rounds, tiles = gbs.gbs_batch_info(batch)
+    (pair, band, stages), rounds, tiles = gbs.gbs_batch_info(batch)
     assert pair in (1, 2) and band >= 0 and rounds >= 1 and tiles > 0
+    # the deepest ring that fits, or one stage less (3 products)
+    assert stages in ((3, 4) if pair == 1 else (5, 6))
     for i, d in enumerate(defs):
         gbs.gbs_sample(singles[i], seeds[i], first[i], E[i], n_sub[i], K1[i])
         _, _, acc_b, cnt_b = gbs.gbs_get_accumulators(nets[i])
@@ -130,14 +132,19 @@ def test_batch_equals_per_network_runs(gbs, own_stream):
         gbs.gbs_free_network(n)
 
 
-@pytest.mark.parametrize("config", [pytest.param((1, 0), id="cta"), pytest.param((1, 8), id="cta-band8"),
-                                    pytest.param((2, 0), id="pair"),
-                                    pytest.param((2, 8), id="pair-band8")])
+@pytest.mark.parametrize("config", [pytest.param((1, 0, 4), id="cta"), pytest.param((1, 8, 4), id="cta-band8"),
+                                    pytest.param((2, 0, 6), id="pair"),
+                                    pytest.param((2, 8, 6), id="pair-band8"),
+                                    pytest.param((1, 0, 3), id="cta-ring3"),
+                                    pytest.param((1, 8, 3), id="cta-band8-ring3"),
+                                    pytest.param((2, 0, 5), id="pair-ring5"),
+                                    pytest.param((2, 8, 5), id="pair-band8-ring5")])
 def test_batch_candidates_agree_bitwise(gbs, config):
     """Every configuration the batch autotuner times (one CTA per tile or CTA
-    pairs, plain tile order or bands of 8 groups within each network) gives
-    bitwise the sums of per-network runs; one network has 18 mode tiles (9
-    pair groups), so the bands are in use."""
+    pairs, plain tile order or bands of 8 groups within each network, the
+    deepest operand ring or one stage less) gives bitwise the sums of
+    per-network runs; one network has 18 mode tiles (9 pair groups), so the
+    bands are in use."""
     import torch
     sptr = torch.cuda.current_stream().cuda_stream
     defs = [wl.small_network(1100, r=0.6, t2=0.9, seed=71), wl.small_network(150, r=0.9, t2=0.8, seed=72),
@@ -240,3 +247,43 @@ def test_multi_round_batch_folds_the_sampler_bitwise(gbs, own_stream):
         for i in range(len(defs)):
             assert np.array_equal(sums["fold"][i][3], sums[mode][i][3]), (mode, i)
             assert np.array_equal(sums["fold"][i][2], sums[mode][i][2]), (mode, i)
+
+
+@pytest.mark.parametrize("config", [pytest.param((1, 0, 3), id="cta-ring3"),
+                                    pytest.param((2, 8, 5), id="pair-band8-ring5")])
+def test_folded_batch_with_the_shallower_ring(gbs, config):
+    """A batch of 1 to 3 rounds per network run with the operand ring one
+    stage shallower, so that its grouped GEMMs of rounds 0 and 1 are the
+    sampling variants with that ring: every network folds and the sums equal
+    per-network runs bit for bit."""
+    import torch
+    sptr = torch.cuda.current_stream().cuda_stream
+    defs = _uneven_defs()
+    probe = gbs.gbs_make_network(defs[0].T, defs[0].r, "bf16x3", sptr)
+    chunk = gbs.gbs_network_info(probe)[3]
+    gbs.gbs_free_network(probe)
+    E = [2 * chunk + 777, chunk + 5, 20000, chunk, 2 * chunk, 3 * chunk - 1]
+    n_sub = [10, 8, 16, 4, 7, 16]
+    K1 = [64, 128, 256, 512, 64, 256]
+    seeds = [d.seed_s for d in defs]
+    first = [17 * i for i in range(len(defs))]
+    nets = [gbs.gbs_make_network(d.T, d.r, "bf16x3", sptr) for d in defs]
+    for net in nets:
+        gbs.gbs_set_sampler_fusion(net, 2)
+    batch = gbs.gbs_make_batch(nets)
+    gbs.gbs_set_batch_config(batch, *config)
+    gbs.gbs_sample_batch(batch, seeds, first, E, n_sub, K1)
+    got, rounds, _ = gbs.gbs_batch_info(batch)
+    assert got == config and rounds == 3
+    assert [gbs.gbs_sampler_fusion(n) for n in nets] == [e > chunk for e in E]
+    for i, d in enumerate(defs):
+        single = gbs.gbs_make_network(d.T, d.r, "bf16x3", sptr)
+        gbs.gbs_sample(single, seeds[i], first[i], E[i], n_sub[i], K1[i])
+        _, _, acc_b, cnt_b = gbs.gbs_get_accumulators(nets[i])
+        _, _, acc_s, cnt_s = gbs.gbs_get_accumulators(single)
+        gbs.gbs_free_network(single)
+        assert np.array_equal(cnt_b, cnt_s), (config, i)
+        assert np.array_equal(acc_b.view(np.float64), acc_s.view(np.float64)), (config, i)
+    gbs.gbs_free_batch(batch)
+    for n in nets:
+        gbs.gbs_free_network(n)
