@@ -395,7 +395,8 @@ def gbs_arm(args, wl_def):
                 "gemm_config": {"cta_pair": pair == 2, "band": band,
                                 "keep_a_in_l2": bool(keep_a & 1),
                                 "b_evict_first": bool(keep_a & 2),
-                                "waves_aligned": bool(keep_a & 8)},
+                                "waves_aligned": bool(keep_a & 8),
+                                "ring": "one stage shallower" if keep_a & 16 else "deepest"},
                 "avg_launch_ms": gemm_ms / max(gemm_launches, 1),
                 "sm_mhz_median": clk.get("sm_mhz"),
                 "achieved_at_max_clock": (achieved * clk["sm_max_mhz"] / clk["sm_mhz"]
@@ -1171,7 +1172,7 @@ def main():
                          "autotuned (the default)")
     ap.add_argument("--gemm-band", type=int, default=0,
                     help="gbs_set_gemm_config band (with --gemm-pair 1 or 2)")
-    ap.add_argument("--gemm-keep-a", type=int, choices=list(range(16)), default=0,
+    ap.add_argument("--gemm-keep-a", type=int, choices=list(range(32)), default=0,
                     help="gbs_set_gemm_config keep_a (with --gemm-pair 1 or 2)")
     ap.add_argument("--pair-autotune", type=int, choices=[0, 1], default=None,
                     help="gbs_set_pair_autotune before the run")

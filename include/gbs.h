@@ -370,16 +370,19 @@ int gbs_network_info(gbs_net_t net, int *N, int *M, int *precision, int64_t *chu
  * at most 50 us, until all have issued the loads of their previous tile, so
  * that tiles shared within a wave are read while the L2 holds them (a wait
  * that times out is not an error: that CTA stops waiting for the rest of the
- * launch).  None of them changes a result.
+ * launch); 16 runs the operand ring in shared memory one stage shallower
+ * than the deepest that fits (4 stages for one CTA and 6 for a pair with 3
+ * products, 3 and 4 with 6 products).  None of them changes a result.
  * pair = 0 returns to the autotuner, which times the candidates (one CTA or
  * pairs; bands of 16 and 8 with and without the evict-last policy; the
- * plain order only where all of A fits in half the L2) on the first chunk
+ * plain order only where all of A fits in half the L2; each with the
+ * deepest ring and with one stage less) on the first chunk
  * of each kind of launch (plain, and the one that also samples the next
  * chunk) in a loaded, interleaved sequence, keeps the fastest and adds the
  * wave alignment to banded orders (cached per size bucket of N and M for
  * the process).  gbs_gemm_config returns the configuration in use ((0, 0,
  * 0) before the first chunk).  EINVAL: FP64 network, pair not 0..2,
- * band < 0, keep_a not in 0..15, NULL pointers.
+ * band < 0, keep_a not in 0..31, NULL pointers.
  */
 int gbs_set_gemm_config(gbs_net_t net, int pair, int band, int keep_a);
 int gbs_gemm_config(gbs_net_t net, int *pair, int *band, int *keep_a);

@@ -1149,7 +1149,7 @@ int tc_set_config(gbs_net *net, const GemmCfg &cfg) {
     if (!net->tc) return set_error(GBS_EINVAL, "network has no tensor-core GEMM");
     if (cfg.pair < 0 || cfg.pair > 2) return set_error(GBS_EINVAL, "pair must be 0 (auto), 1 or 2");
     if (cfg.band < 0) return set_error(GBS_EINVAL, "band must be >= 0");
-    if (cfg.keep < 0 || cfg.keep > 15) return set_error(GBS_EINVAL, "keep_a must be in [0, 15]");
+    if (cfg.keep < 0 || cfg.keep > 31) return set_error(GBS_EINVAL, "keep_a must be in [0, 31]");
     net->tc->forced = cfg.pair != 0;
     GemmCfg c = cfg;
     if (!c.pair) c = GemmCfg();
@@ -1181,8 +1181,10 @@ bool tc_pair_autotune() {
 // times the bytes of a banded order from HBM, and although short timings can
 // favour it (m8000: by about 1 %), over a long run the extra DRAM power lowers
 // the clock under the power limit (m8000: 1063 against 1012 ms per step), so
-// it is offered only for networks whose A fits in half the L2.
-std::vector<GemmCfg> tc_candidates(int mtiles, bool pairs, bool plain) {
+// it is offered only for networks whose A fits in half the L2.  Each
+// candidate runs with the deepest operand ring that fits in shared memory
+// and, where `shallow` allows, with one stage less (keep_a bit 16).
+std::vector<GemmCfg> tc_candidates(int mtiles, bool pairs, bool plain, bool shallow) {
     std::vector<GemmCfg> c;
     for (int pair = 1; pair <= (pairs ? 2 : 1); ++pair) {
         const int groups = (mtiles + pair - 1) / pair;
@@ -1194,29 +1196,34 @@ std::vector<GemmCfg> tc_candidates(int mtiles, bool pairs, bool plain) {
             }
         if (plain || !banded) c.push_back({pair, 0, 0});
     }
+    const size_t deep = c.size();
+    for (size_t i = 0; shallow && i < deep; ++i) c.push_back({c[i].pair, c[i].band, c[i].keep | 16});
     return c;
 }
 
 // One launch over the closed-form tiles of the network's current chunk in
 // configuration g; with a job, the sampling variant that also runs it.
+// keep_a bit 16 selects the operand ring one stage shallower; the kernel
+// sees the other bits.
 int launch_closed(gbs_net *net, const GemmCfg &g, int ntiles, int64_t count, const SampleJob *job,
                   OccOut occ) {
     TcPlan *plan = net->tc;
     if ((g.keep & 8) && plan->d_sync)
         GBS_CUDA_TRY(cudaMemsetAsync(plan->d_sync, 0, sizeof(unsigned int), net->stream));
+    const int shallow = (g.keep & 16) ? 1 : 0;
+    const int keep = g.keep & 15;
     if (!job)
-        return launch_gemm_grouped(net->stream, net->sm_count, plan->P, g.pair, g.band, g.keep,
+        return launch_gemm_grouped(net->stream, net->sm_count, plan->P, g.pair, g.band, keep,
                                    net->wait_ns, plan->d_desc, nullptr, ntiles, count,
-                                   net->d_flags + 1, occ);
+                                   net->d_flags + 1, occ, shallow);
+    if (g.pair != 1 && g.pair != 2) return set_error(GBS_EINVAL, "GEMM tiles per CTA pair must be 1 or 2");
+    if (shallow && !shallow_sampling_kernels_ok())
+        return set_error(GBS_EINVAL, "sampling GEMM with the shallower ring unavailable");
     SampleJobs jobs;
     jobs.one = *job;
-    return g.pair == 1
-               ? launch_variant<3, 1, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
-                                               ntiles, count, g.band, g.keep, net->wait_ns,
-                                               net->d_flags + 1, occ, jobs)
-               : launch_variant<3, 2, kSampWG>(net->stream, net->sm_count, plan->d_desc, nullptr,
-                                               ntiles, count, g.band, g.keep, net->wait_ns,
-                                               net->d_flags + 1, occ, jobs);
+    return launch_grouped_ring<3, kSampWG>(net->stream, net->sm_count, g.pair, shallow,
+                                           plan->d_desc, nullptr, ntiles, count, g.band, keep,
+                                           net->wait_ns, net->d_flags + 1, occ, jobs);
 }
 
 // Time the candidate configurations on this chunk (as the launch to be
@@ -1255,7 +1262,8 @@ int tc_autotune(gbs_net *net, int64_t count, const SampleJob *job, GemmCfg *out)
         l2 = 0;
     }
     const double a_bytes = (double)(plan->P == 3 ? 2 : 3) * net->rowsA * net->ldK * 2.0;
-    const std::vector<GemmCfg> cand = tc_candidates(net->mtiles, pairs, a_bytes <= 0.5 * l2);
+    const std::vector<GemmCfg> cand =
+        tc_candidates(net->mtiles, pairs, a_bytes <= 0.5 * l2, !job || shallow_sampling_kernels_ok());
     std::vector<float> total(cand.size(), 0.0f);
     cudaEvent_t e0, e1;
     GBS_CUDA_TRY(cudaEventCreate(&e0));

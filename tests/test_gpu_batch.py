@@ -35,7 +35,10 @@ CONFIGS = [pytest.param((1, 0, 0), id="cta"), pytest.param((1, 1, 0), id="cta-ba
            pytest.param((2, 1, 1), id="pair-band1-keep"),
            pytest.param((1, 2, 8), id="cta-band2-aligned"),
            pytest.param((2, 1, 9), id="pair-band1-keep-aligned"),
-           pytest.param((2, 1, 6), id="pair-band1-policies")]
+           pytest.param((2, 1, 6), id="pair-band1-policies"),
+           pytest.param((1, 0, 16), id="cta-shallow-ring"),
+           pytest.param((2, 0, 16), id="pair-shallow-ring"),
+           pytest.param((2, 1, 25), id="pair-band1-keep-aligned-shallow-ring")]
 
 
 @pytest.mark.parametrize("config", CONFIGS)
@@ -85,7 +88,7 @@ def test_autotuner_picks_a_configuration(gbs):
     assert gbs.gbs_gemm_config(net) == (0, 0, 0)
     gbs.gbs_sample(net, net_def.seed_s, 0, 5000, 10, 256)
     pair, band, keep = gbs.gbs_gemm_config(net)
-    assert pair in (1, 2) and band >= 0 and keep in (0, 1, 8, 9)
+    assert pair in (1, 2) and band >= 0 and (keep & ~16) in (0, 1, 8, 9)
     # the waves of banded orders are aligned, those of the plain order not
     assert bool(keep & 8) == (band > 0)
     gbs.gbs_free_network(net)

@@ -44,7 +44,9 @@ def _sums(gbs, stream, net_def, fuse, config, calls, n_sub, K1):
     return acc, counts, P, active
 
 
-@pytest.mark.parametrize("config", [pytest.param((1, 0, 0), id="cta"), pytest.param((2, 0, 0), id="pair")])
+@pytest.mark.parametrize("config", [pytest.param((1, 0, 0), id="cta"), pytest.param((2, 0, 0), id="pair"),
+                                    pytest.param((1, 0, 16), id="cta-shallow-ring"),
+                                    pytest.param((2, 0, 16), id="pair-shallow-ring")])
 @pytest.mark.parametrize("N,M", [(24, 40), (300, 260)])
 def test_folded_sampler_is_bitwise_the_plain_loop(gbs, stream, config, N, M):
     net_def = wl.small_network(N, M, r=0.7, t2=0.9, seed=90 + N)
