@@ -48,6 +48,11 @@ GEMM_TRAFFIC_BYTES_PER_SAMPLE = {
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 16768-trajectory sampling "
         "launch with aligned waves (profiles/k_gemm_tc_pair_m8000.md), scaled to the average "
         "launch"),
+    ("m8000", "bf16x3", True, 2, 16, 24): (
+        (19.29e9 + 1.11e9) / 16768,
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 16768-trajectory sampling "
+        "launch with aligned waves and the 5-stage operand ring "
+        "(profiles/k_gemm_tc_pair_m8000.md), scaled to the average launch"),
     ("m8000", "bf16x3", True, 2, 16, 0): (
         (67.03e9 + 1.11e9) / 16768,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 16768-trajectory sampling "
