@@ -89,6 +89,9 @@ GF_FP32_OPS_PER_PAIR = 200.5
 # m8000 (8MN FLOP per trajectory over CUDA-event kernel time), so the
 # larger of the probe and GB300's nominal FP64 rate is the peak.
 FP64_NOMINAL_TFLOPS = 1.25
+# FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz
+FP32_UNIT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP32_PEAK_SOURCE = "unit counts: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.07 GHz (maximum clock)"
 FP64_PEAK_SOURCE = ("max(gbs_measure_fp64_rate, nominal GB300 FP64 1.25 TFLOP/s): the "
                     "FMA-chain probe reads below the rate the FP64 GEMM sustains")
 
@@ -323,7 +326,7 @@ def gbs_arm(args, wl_def):
         gbs.gbs_set_sampler_fusion(net, args.sampler_fusion)
     if args.pair_autotune is not None:
         gbs.gbs_set_pair_autotune(bool(args.pair_autotune))
-    if args.gemm_pair is not None and precision != "fp64":
+    if args.gemm_pair is not None and precision not in ("fp64", "fp32"):
         gbs.gbs_set_gemm_config(net, args.gemm_pair, args.gemm_band, args.gemm_keep_a)
     out = torch.empty(4 * K1, dtype=torch.float64, device="cuda")
     seed = netdef.seed_s
@@ -384,7 +387,7 @@ def gbs_arm(args, wl_def):
     peaks, peak_kind = _peaks()
     gemm_ms, gemm_launches = prof["gemm"]
     flops = 8.0 * netdef.M * netdef.N * E * args.steps
-    tc_path = precision != "fp64"
+    tc_path = precision not in ("fp64", "fp32")
     P_products = {"bf16x3": 3, "bf16x6": 6}.get(precision, 1)
     folded = bool(tc_path and gbs.gbs_sampler_fusion(net))
     if tc_path:
@@ -427,6 +430,12 @@ def gbs_arm(args, wl_def):
         else:
             roof["traffic_source"] = "no ncu capture of this kernel version, workload and " \
                                      "configuration"
+    elif precision == "fp32":
+        achieved = flops / (gemm_ms / 1e3) / 1e12
+        peak = FP32_UNIT_TFLOPS
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_gemm_fp64<float>",
+                "peak_source": FP32_PEAK_SOURCE}
     else:
         achieved = flops / (gemm_ms / 1e3) / 1e12
         probe = gbs.gbs_measure_fp64_rate(sptr)
@@ -462,7 +471,8 @@ def gbs_arm(args, wl_def):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"bf16x3": "bf16x3 split (fp32 accumulate, f64 sums)",
-                  "bf16x6": "bf16x6 split (fp32 accumulate, f64 sums)"}.get(precision, "f64"),
+                  "bf16x6": "bf16x6 split (fp32 accumulate, f64 sums)",
+                  "fp32": "f32 GEMM (fp32 accumulate, f64 sums)"}.get(precision, "f64"),
         "data": "synthetic",
         "config": {"workload": wl_def.name, "precision": precision, "samples_per_step": E,
                    "n_sub": n_sub, "K1": K1, "N": netdef.N, "M": netdef.M,
@@ -548,7 +558,7 @@ def gbs_arm(args, wl_def):
             n2 = gbs.gbs_make_network(Tn, rn, precision, sptr)
             if args.sampler_fusion is not None:
                 gbs.gbs_set_sampler_fusion(n2, args.sampler_fusion)
-            if args.gemm_pair is not None and precision != "fp64":
+            if args.gemm_pair is not None and precision not in ("fp64", "fp32"):
                 gbs.gbs_set_gemm_config(n2, args.gemm_pair, args.gemm_band, args.gemm_keep_a)
             tb = time.perf_counter()
             gbs.gbs_sample(n2, seed, base + s * E, E, n_sub, K1)
@@ -1161,7 +1171,7 @@ def main():
     ap.add_argument("--sur-heldout", type=int, default=50)
     ap.add_argument("--sur-judge-samples", type=int, default=2 ** 18)
     ap.add_argument("--batch-count", type=int, default=64)
-    ap.add_argument("--precision", default=None, choices=["fp64", "bf16x3", "bf16x6"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "bf16x3", "bf16x6"])
     ap.add_argument("--samples", type=int, default=0, help="override trajectories per step")
     ap.add_argument("--ref-samples", type=int, default=0,
                     help="trajectories per reference-arm step (default: about 2 s of oracle "

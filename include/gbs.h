@@ -54,6 +54,10 @@ extern "C" {
 
 /* Arithmetic of the propagation GEMM alpha' = T alpha, beta' = T* beta. */
 #define GBS_FP64 0   /* FP64 sampler, FP64 SIMT GEMM, FP64 generating functions */
+#define GBS_FP32 1   /* as GBS_FP64 with the SIMT GEMM in FP32: T and the samples
+                        rounded to FP32, FP32 products accumulated in FP32 along
+                        the N input modes; occupations and everything after
+                        them in FP64 */
 #define GBS_BF16X3 2 /* FP32 sampler, tcgen05 BF16 split GEMM with 3 products
                         (T0 B0 + T0 B1 + T1 B0), FP32 accumulation;
                         generating functions in double-float on the FP32
@@ -74,8 +78,9 @@ typedef struct gbs_net *gbs_net_t;
  *              by the conversion kernel in place; other memory is first
  *              copied to a device buffer.
  *   r          host, N squeezing parameters, each finite and >= 0.
- *   precision  GBS_FP64, GBS_BF16X3 or GBS_BF16X6.  The BF16 paths split T
- *              (rounded to FP32) into BF16 planes T = T0 + T1 + T2.
+ *   precision  GBS_FP64, GBS_FP32, GBS_BF16X3 or GBS_BF16X6.  The BF16 paths
+ *              split T (rounded to FP32) into BF16 planes T = T0 + T1 + T2;
+ *              GBS_FP32 keeps T in FP64 and rounds it as the GEMM stages it.
  *   stream     cudaStream_t (as void*) used for every launch of this network.
  *   out        receives the handle.
  * Errors: EINVAL on bad sizes/values/null pointers; ENOMEM; ECUDA;

@@ -33,10 +33,11 @@ GBS_ENONFINITE = -5
 GBS_ENOTSUP = -6
 
 GBS_FP64 = 0
+GBS_FP32 = 1
 GBS_BF16X3 = 2
 GBS_BF16X6 = 3
 
-PRECISIONS = {"fp64": GBS_FP64, "bf16x3": GBS_BF16X3, "bf16x6": GBS_BF16X6}
+PRECISIONS = {"fp64": GBS_FP64, "fp32": GBS_FP32, "bf16x3": GBS_BF16X3, "bf16x6": GBS_BF16X6}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgbs.so")

@@ -160,7 +160,7 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 int64_t pick_chunk(const gbs_net *net) {
     // trajectories per chunk: sample operand <= 1 GiB, multiple of 128, in [128, 2^17]
     size_t per_traj;
-    if (net->precision == GBS_FP64)
+    if (simt_precision(net->precision))
         per_traj = (size_t)16 * net->N;
     else
         per_traj = (size_t)4 * net->planesB * net->ldK;
@@ -224,7 +224,7 @@ void release_all(gbs_net *net) {
 // Sampler + propagation + finalize for one chunk of `count` trajectories.
 int run_chunk_front(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) {
     int rc;
-    const bool fp64 = net->precision == GBS_FP64;
+    const bool fp64 = simt_precision(net->precision);
     prof_mark(net, GBS_PHASE_SAMPLE, 0, true);
     rc = fp64 ? launch_sample_fp64(net, seed, e0, count) : launch_sample_bf16(net, seed, e0, count);
     if (rc) return rc;
@@ -382,7 +382,7 @@ __global__ void k_split_from_dev(const double *__restrict__ T, int N, int M, int
 // Sampler + propagation + two-bin finalize for one chunk.
 int run_chunk_front2d(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count) {
     int rc;
-    const bool fp64 = net->precision == GBS_FP64;
+    const bool fp64 = simt_precision(net->precision);
     prof_mark(net, GBS_PHASE_SAMPLE, 0, true);
     rc = fp64 ? launch_sample_fp64(net, seed, e0, count) : launch_sample_bf16(net, seed, e0, count);
     if (rc) return rc;
@@ -433,7 +433,7 @@ int fix_estimator2d(gbs_net *net, int n_sub, const int *K) {
         (rc = net_alloc(net, &net->d_out2, (size_t)4 * grid, "out2")) ||
         (rc = net_alloc(net, &net->d_mo2, (size_t)kMaxBins, "window offsets")))
         return rc;
-    if (net->precision != GBS_FP64) {
+    if (!simt_precision(net->precision)) {
         if ((rc = pool_alloc(&net->d_sep2, (size_t)net->chunk * sep2_bytes_per_trajectory(),
                              net->stream, "sep2")))
             return rc;
@@ -529,7 +529,8 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
     if (N < 1 || M < 1 || N > 65536 || M > 65536)
         return set_error(GBS_EINVAL, "N and M must be in [1, 65536] (got %d, %d)", N, M);
     if (!T || !r) return set_error(GBS_EINVAL, "T and r must be non-NULL pointers");
-    if (precision != GBS_FP64 && precision != GBS_BF16X3 && precision != GBS_BF16X6)
+    if (precision != GBS_FP64 && precision != GBS_FP32 && precision != GBS_BF16X3 &&
+        precision != GBS_BF16X6)
         return set_error(GBS_EINVAL, "unknown precision %d", precision);
     for (int j = 0; j < N; ++j)
         if (!std::isfinite(r[j]) || r[j] < 0.0)
@@ -624,7 +625,7 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
     }
     const int conv_blocks =
         (int)std::min<int64_t>(((int64_t)M * N + 255) / 256, (int64_t)net->sm_count * 16);
-    if (precision == GBS_FP64 && T_device) {
+    if (simt_precision(precision) && T_device) {
         if ((rc = net_alloc(net, &net->d_T64, (size_t)M * 2 * N, "T64"))) {
             net_free(net, d_bad);
             return fail(rc);
@@ -662,7 +663,7 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
     }
     // chunk workspace
     net->chunk = pick_chunk(net);
-    if (precision == GBS_FP64) {
+    if (simt_precision(precision)) {
         net->B_bytes = (size_t)net->chunk * 2 * N * sizeof(double);
     } else {
         const int64_t tiles = (net->chunk + kTcTileSamples - 1) / kTcTileSamples;
@@ -681,7 +682,7 @@ int make_network(int N, int M, const double *T, bool T_device, const double *r, 
         return fail(rc);
     if (cudaMemsetAsync(net->d_flags, 0, 4 * sizeof(unsigned long long), net->stream) != cudaSuccess)
         return fail(set_error(GBS_ECUDA, "memset of flags failed"));
-    if (precision != GBS_FP64) {
+    if (!simt_precision(precision)) {
         if ((rc = pool_alloc(&net->d_gfrec, (size_t)net->chunk * gf_record_bytes(), net->stream,
                              "generating-function records")))
             return fail(rc);
@@ -940,7 +941,7 @@ namespace {
 int run_chunk_occ(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count, void *occ,
                   int64_t ld_occ) {
     int rc;
-    const bool fp64 = net->precision == GBS_FP64;
+    const bool fp64 = simt_precision(net->precision);
     const int64_t plane = (int64_t)net->mtiles * 64 * ld_occ;
     prof_mark(net, GBS_PHASE_SAMPLE, 0, true);
     rc = fp64 ? launch_sample_fp64(net, seed, e0, count) : launch_sample_bf16(net, seed, e0, count);
@@ -968,7 +969,7 @@ int run_chunk_occ(gbs_net *net, uint64_t seed, uint64_t e0, int64_t count, void 
 // Trajectories per occupation chunk: <= the network's chunk, a multiple of
 // 128, occupation planes <= 2 GiB.
 int64_t occ_chunk(const gbs_net *net, int64_t E) {
-    const size_t elt = net->precision == GBS_FP64 ? sizeof(double) : sizeof(float);
+    const size_t elt = simt_precision(net->precision) ? sizeof(double) : sizeof(float);
     const size_t per_traj = (size_t)2 * net->mtiles * 64 * elt;
     int64_t c = (int64_t)(((size_t)1 << 31) / per_traj);
     c = std::min<int64_t>(c, net->chunk);
@@ -985,7 +986,7 @@ int gbs_debug_occupations(gbs_net_t net, uint64_t seed, uint64_t e0, int64_t cou
     if (count < 0 || !occ) return set_error(GBS_EINVAL, "bad count or NULL output");
     if (net->nbins != 1) return set_error(GBS_EINVAL, "occupations of a binned network are not exposed");
     if (count == 0) return GBS_OK;
-    const bool fp64 = net->precision == GBS_FP64;
+    const bool fp64 = simt_precision(net->precision);
     const int64_t ld = occ_chunk(net, count);
     const int64_t plane = (int64_t)net->mtiles * 64 * ld;
     void *d_occ = nullptr;
@@ -1032,7 +1033,7 @@ int gbs_moments(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E, 
     if (cmax < 0 || cmax > 15) return set_error(GBS_EINVAL, "cmax must be in [0, 15]");
     if (n_sub < 1 || n_sub > 65535) return set_error(GBS_EINVAL, "n_sub must be in [1, 65535]");
     if (E < n_sub) return set_error(GBS_EINVAL, "E must be >= n_sub (no empty sub-ensemble)");
-    const bool fp64 = net->precision == GBS_FP64;
+    const bool fp64 = simt_precision(net->precision);
     MomentSpec sp;
     sp.M = net->M;
     sp.n_sub = n_sub;
@@ -1186,7 +1187,7 @@ int gbs_sample_nd(gbs_net_t net, uint64_t seed, uint64_t first_sample, int64_t E
             if ((rc = run_chunk_front2d(net, seed, e0, c))) return rc;
             prof_mark(net, GBS_PHASE_GF, 0, true);
             if ((rc = launch_gf2d(net, e0, c))) return rc;
-            prof_mark(net, GBS_PHASE_GF, net->precision == GBS_FP64 ? 1 : 2, false);
+            prof_mark(net, GBS_PHASE_GF, simt_precision(net->precision) ? 1 : 2, false);
         }
     }
     const uint64_t ns = (uint64_t)net->n_sub2;
@@ -1259,7 +1260,8 @@ int gbs_network_info(gbs_net_t net, int *N, int *M, int *precision, int64_t *chu
 int gbs_set_gemm_config(gbs_net_t net, int pair, int band, int keep_a) {
     int rc;
     if ((rc = validate_net(net))) return rc;
-    if (net->precision == GBS_FP64) return set_error(GBS_EINVAL, "the FP64 path has no tcgen05 GEMM");
+    if (simt_precision(net->precision))
+        return set_error(GBS_EINVAL, "the FP64 and FP32 paths have no tcgen05 GEMM");
     GemmCfg c;
     c.pair = pair;
     c.band = band;

@@ -385,8 +385,8 @@ int gbs_make_batch(gbs_net_t *nets, int count, gbs_batch_t *out) {
         return set_error(GBS_EINVAL, "need 1..4096 networks");
     for (int i = 0; i < count; ++i) {
         if (!nets[i]) return set_error(GBS_EINVAL, "network %d is NULL", i);
-        if (nets[i]->precision == GBS_FP64)
-            return set_error(GBS_EINVAL, "batches need a BF16 split precision (network %d is FP64)",
+        if (simt_precision(nets[i]->precision))
+            return set_error(GBS_EINVAL, "batches need a BF16 split precision (network %d is FP64 or FP32)",
                              i);
         if (nets[i]->precision != nets[0]->precision)
             return set_error(GBS_EINVAL, "all networks of a batch must share the precision");

@@ -134,6 +134,13 @@ struct Profiler {
     int64_t launches[GBS_NPHASES] = {};
 };
 
+// The SIMT precisions (GBS_FP64, GBS_FP32) share the FP64 sampler, network
+// operand, generating functions and inversion; only the GEMM's arithmetic
+// differs.  The BF16 split precisions run the tcgen05 path.
+inline bool simt_precision(int precision) {
+    return precision == GBS_FP64 || precision == GBS_FP32;
+}
+
 }  // namespace gbs
 
 struct gbs_net {

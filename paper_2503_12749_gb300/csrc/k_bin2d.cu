@@ -852,7 +852,7 @@ int launch_finalize2d(gbs_net *net, int64_t count) {
 int launch_gf2d(gbs_net *net, uint64_t e0, int64_t count) {
     if (count <= 0) return GBS_OK;
     const GridD g = grid_of(net);
-    if (net->precision == GBS_FP64) {
+    if (simt_precision(net->precision)) {
         // blocks for the whole grid; blocks past the chunk's union window return
         dim3 grid((unsigned)((net->grid2 + kG2Threads - 1) / kG2Threads), (unsigned)net->n_sub2);
         k_gf2d<<<grid, kG2Threads, 0, net->stream>>>(net->d_n, net->d_nS2, net->d_win2,

@@ -10,8 +10,11 @@
 // request (moments and marginals), every n'_i.
 //
 // Tile: 64 output modes x 32 trajectories per 256-thread block; each thread
-// owns 4 modes x 2 trajectories (32 FP64 accumulators).  This path is bound
-// by the FP64 FMA rate.
+// owns 4 modes x 2 trajectories (32 accumulators).  R is the arithmetic of
+// the contraction: double (GBS_FP64, bound by the FP64 FMA rate) or float
+// (GBS_FP32: T and the samples rounded to FP32 as they are staged, FP32
+// products accumulated in FP32 along the N input modes); the occupation
+// epilogue and everything after it is FP64 in both.
 #include "gbs_internal.cuh"
 
 #include <algorithm>
@@ -25,12 +28,16 @@ constexpr int TM = kFp64TileModes;    // 64 modes -> 128 A rows
 constexpr int TS = kFp64TileSamples;  // 32 trajectories -> 64 B rows
 constexpr int KT = 16;                // K per smem stage
 
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <typename R>
 __global__ void __launch_bounds__(256) k_gemm_fp64(const double *__restrict__ T64,
                                                    const double *__restrict__ B, int N, int M,
                                                    int64_t count, int64_t ld_part,
                                                    double2 *__restrict__ nS_part, OccOut64 occ) {
-    __shared__ double As[KT][2 * TM + 1];
-    __shared__ double Bs[KT][2 * TS + 1];
+    __shared__ R As[KT][2 * TM + 1];
+    __shared__ R Bs[KT][2 * TS + 1];
     __shared__ double2 red[16][TS];
 
     const int tid = threadIdx.x;
@@ -40,7 +47,7 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const double *__restrict__ T6
     const int i0 = mtile * TM;
     const int64_t s0 = (int64_t)blockIdx.x * TS;
 
-    double acc[4][2][2][2];  // [mode][Re/Im row][trajectory][alpha/beta]
+    R acc[4][2][2][2];  // [mode][Re/Im row][trajectory][alpha/beta]
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -48,7 +55,7 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const double *__restrict__ T6
 #pragma unroll
             for (int c = 0; c < 2; ++c)
 #pragma unroll
-                for (int d = 0; d < 2; ++d) acc[a][b][c][d] = 0.0;
+                for (int d = 0; d < 2; ++d) acc[a][b][c][d] = R(0);
 
     for (int k0 = 0; k0 < N; k0 += KT) {
         // A tile: 128 rows x 16 k (row = 2*mode_local + re/im), 8 per thread
@@ -61,7 +68,7 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const double *__restrict__ T6
             const int k = k0 + kk;
             double v = 0.0;
             if (i < M && k < N) v = T64[((size_t)i * 2 + (row & 1)) * N + k];
-            As[kk][row] = v;
+            As[kk][row] = R(v);
         }
         // B tile: 64 rows x 16 k (row = 2*traj_local + alpha/beta), 4 per thread
 #pragma unroll
@@ -73,12 +80,12 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const double *__restrict__ T6
             const int k = k0 + kk;
             double v = 0.0;
             if (s < count && k < N) v = B[((size_t)s * 2 + (row & 1)) * N + k];
-            Bs[kk][row] = v;
+            Bs[kk][row] = R(v);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < KT; ++kk) {
-            double a[8], b[4];
+            R a[8], b[4];
 #pragma unroll
             for (int t = 0; t < 8; ++t) a[t] = As[kk][ty * 8 + t];
 #pragma unroll
@@ -91,7 +98,7 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const double *__restrict__ T6
                     for (int s = 0; s < 2; ++s)
 #pragma unroll
                         for (int ab = 0; ab < 2; ++ab)
-                            acc[m][ri][s][ab] = fma(a[2 * m + ri], b[2 * s + ab], acc[m][ri][s][ab]);
+                            acc[m][ri][s][ab] = fma_r(a[2 * m + ri], b[2 * s + ab], acc[m][ri][s][ab]);
         }
         __syncthreads();
     }
@@ -104,8 +111,8 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(const double *__restrict__ T6
         const int64_t traj = s0 + tx * 2 + s;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            const double ar = acc[m][0][s][0], ai = acc[m][1][s][0];
-            const double br = acc[m][0][s][1], bi = acc[m][1][s][1];
+            const double ar = (double)acc[m][0][s][0], ai = (double)acc[m][1][s][0];
+            const double br = (double)acc[m][0][s][1], bi = (double)acc[m][1][s][1];
             const double ore = ar * br + ai * bi;
             const double oim = ai * br - ar * bi;
             if (occ.p && traj < count) {
@@ -183,9 +190,14 @@ int launch_gemm_fp64(gbs_net *net, int64_t count, OccOut64 occ) {
     const int64_t sblocks = (count + TS - 1) / TS;
     if (sblocks > 0x7fffffff) return set_error(GBS_EINVAL, "chunk too large");
     dim3 grid((unsigned)sblocks, (unsigned)net->mtiles);
-    k_gemm_fp64<<<grid, 256, 0, net->stream>>>(net->d_T64, static_cast<const double *>(net->d_B),
-                                                net->N, net->M, count, net->chunk,
-                                                net->d_nS_part, occ);
+    if (net->precision == GBS_FP32)
+        k_gemm_fp64<float><<<grid, 256, 0, net->stream>>>(
+            net->d_T64, static_cast<const double *>(net->d_B), net->N, net->M, count, net->chunk,
+            net->d_nS_part, occ);
+    else
+        k_gemm_fp64<double><<<grid, 256, 0, net->stream>>>(
+            net->d_T64, static_cast<const double *>(net->d_B), net->N, net->M, count, net->chunk,
+            net->d_nS_part, occ);
     GBS_LAUNCH_CHECK();
     return GBS_OK;
 }

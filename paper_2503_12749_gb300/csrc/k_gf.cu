@@ -815,7 +815,7 @@ int launch_finalize(gbs_net *net, int64_t count) {
 int launch_gf(gbs_net *net, uint64_t e0, int64_t count) {
     if (count <= 0) return GBS_OK;
     dim3 grid((unsigned)((net->K1 + 255) / 256), (unsigned)net->n_sub);
-    if (net->precision == GBS_FP64) {
+    if (simt_precision(net->precision)) {
         k_gf_fp64<<<grid, 256, 0, net->stream>>>(net->d_n, net->d_nS, net->d_win, count, e0,
                                                    net->n_sub, net->K1, net->d_tw, net->d_acc,
                                                    net->d_counts);
