@@ -44,7 +44,7 @@ def test_fp64_matches_oracle(orc, gbs, stream, bins):
         np.testing.assert_allclose(P[2 * est + 1], so[est], rtol=1e-7, atol=1e-12)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "fp32"])
 def test_antidiagonal_sums_equal_the_total_count(gbs, stream, prec):
     """Sum over m_1 + m_2 = m (mod K) of the two-bin P equals the one-bin P of
     the same trajectories (gbs_sample on the same binned network)."""

@@ -50,10 +50,14 @@ def _amp_scale(net_def, e_list):
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("bf16x3", 2.0 ** -14),
-                                      ("bf16x6", 2.0 ** -20)])
+                                      ("bf16x6", 2.0 ** -20), ("fp32", None)])
 @pytest.mark.parametrize("shape", [(16, 16), (7, 9), (9, 7), (100, 130)])
 def test_occupations_per_element(gbs, stream, prec, tol, shape):
     N, M = shape
+    if tol is None:
+        # FP32 GEMM: |d n'_j| <= 2 (N + 2) 2^-24 (1 + 2^-10) A_j B_j (rounding
+        # of T and the samples to FP32, N fused multiply-adds)
+        tol = 2.0 * (N + 2) * 2.0 ** -24 * (1.0 + 2.0 ** -10)
     net_def = wl.small_network(N, M=M, r=0.9, t2=0.95, seed=40 + N)
     net = gbs.gbs_make_network(net_def.T, net_def.r, prec, stream)
     E, e0 = 200, 777  # two 128-trajectory tiles, ragged tail
@@ -98,8 +102,8 @@ def test_one_trajectory_per_sub_ensemble(gbs, stream):
     gbs.gbs_free_network(net)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
-def test_bf16_within_sigma_of_fp64(gbs, stream, prec):
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6", "fp32"])
+def test_reduced_precision_within_sigma_of_fp64(gbs, stream, prec):
     for net_def, E, n_sub in ((wl.SMALL16.network(), 2 ** 14, 16),
                               (wl.small_network(200, r=0.5, t2=0.99, seed=11), 2 ** 14, 32)):
         res = {}
