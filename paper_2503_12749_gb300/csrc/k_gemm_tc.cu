@@ -119,8 +119,8 @@ struct Cfg {
     static constexpr int kAPlane = 128 * 64;
     static constexpr int kBPlane = (256 / kPair) * 64;
     static constexpr int kStageBytes = kPlanes * (kAPlane + kBPlane);
-    // the deepest ring that fits in shared memory (the default); the batch
-    // autotuner also times a ring one stage shallower
+    // the deepest ring that fits in shared memory (the default); the
+    // autotuners also time a ring one stage shallower
     static constexpr int kStages = (P == 3) ? (kPair == 1 ? 4 : 6) : (kPair == 1 ? 3 : 4);
 };
 constexpr int kBarBytes = 1024;
@@ -892,7 +892,7 @@ cudaError_t set_smem_attr() {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem_bytes<P, kPair, kSt>());
 }
-// the ring one stage shallower than the deepest (batch autotuner candidate)
+// the ring one stage shallower than the deepest (an autotuner candidate)
 template <int P, int kPair>
 constexpr int shallow_stages() {
     return Cfg<P, kPair>::kStages - 1;
