@@ -61,3 +61,35 @@ def test_last_error_is_callable_without_gpu(libpath):
     out = ctypes.c_void_p()
     code = lib.gbs_make_network(0, 0, None, None, 0, None, ctypes.byref(out))
     assert code == -1
+
+
+def _prototypes():
+    """{name: parameter count} of every function include/*.h declares."""
+    src = ""
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        with open(h) as f:
+            src += f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    out = {}
+    for name, params in re.findall(r"\b(gbs_[a-z0-9_]+)\s*\(([^()]*)\)\s*;", src):
+        params = params.strip()
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header(libpath):
+    """Every argtypes list the binding sets has as many entries as the C
+    prototype has parameters (a changed signature must change both)."""
+    import paper_2503_12749_gb300 as g
+    L = g.lib()
+    protos = _prototypes()
+    assert set(protos) == set(_declared())
+    checked = 0
+    for name, n in protos.items():
+        argtypes = getattr(L, name).argtypes
+        if argtypes is None:
+            continue
+        assert len(argtypes) == n, (name, len(argtypes), n)
+        checked += 1
+    assert checked >= 40
