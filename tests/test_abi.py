@@ -93,3 +93,23 @@ def test_binding_argument_counts_match_the_header(libpath):
         assert len(argtypes) == n, (name, len(argtypes), n)
         checked += 1
     assert checked >= 40
+
+
+def test_binding_constants_match_the_header():
+    """Status codes, precisions and sizes: every numeric #define of
+    include/*.h that the binding also names has the same value there."""
+    import paper_2503_12749_gb300 as g
+    src = ""
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        with open(h) as f:
+            src += f.read()
+    defs = {k: int(v) for k, v in
+            re.findall(r"^#define\s+(GBS_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", src, flags=re.M)}
+    shared = [k for k in defs if hasattr(g, k)]
+    for k in shared:
+        assert getattr(g, k) == defs[k], (k, getattr(g, k), defs[k])
+    for k in ("GBS_OK", "GBS_EINVAL", "GBS_ETIMEOUT", "GBS_FP64", "GBS_FP32", "GBS_BF16X3",
+              "GBS_BF16X6", "GBS_NPHASES", "GBS_SUR_OUT"):
+        assert k in shared, k
+    assert g.PRECISIONS == {"fp64": defs["GBS_FP64"], "fp32": defs["GBS_FP32"],
+                            "bf16x3": defs["GBS_BF16X3"], "bf16x6": defs["GBS_BF16X6"]}
